@@ -1,0 +1,231 @@
+"""FP64 CPU oracle for the hybrid fluid-kinetic step of arXiv 2510.11174.
+
+TEST INFRASTRUCTURE.  Only the test suite, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this
+package.  The product path (``paper_2510_11174_gb300``) never imports, links
+or runs it, and the two share no code: the oracle is a separate, plain,
+double-precision implementation written from the paper's Methodology section
+and the textbook methods it names, so that the CUDA path can be checked
+against it.
+
+The arithmetic lives in the C files next to this module (compiled with gcc
+into ``liboracle.so``); this module only marshals numpy arrays.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        _lib = C.CDLL(path)
+        _declare(_lib)
+    return _lib
+
+
+class Grid(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+                ("dx", C.c_double), ("dy", C.c_double), ("dz", C.c_double), ("dt", C.c_double),
+                ("bc", C.c_int * 3)]
+
+    @classmethod
+    def make(cls, nx, ny, nz, dx, dy, dz, dt, bc=(0, 0, 0)):
+        g = cls()
+        g.nx, g.ny, g.nz = int(nx), int(ny), int(nz)
+        g.dx, g.dy, g.dz, g.dt = float(dx), float(dy), float(dz), float(dt)
+        for a in range(3):
+            g.bc[a] = int(bc[a])
+        return g
+
+    @property
+    def shape(self):
+        return (self.nz, self.ny, self.nx)
+
+
+class Species(C.Structure):
+    _fields_ = [("q", C.c_double), ("m", C.c_double), ("n", C.c_long),
+                ("x", C.c_void_p), ("y", C.c_void_p), ("z", C.c_void_p),
+                ("ux", C.c_void_p), ("uy", C.c_void_p), ("uz", C.c_void_p),
+                ("w", C.c_void_p), ("zq", C.c_void_p)]
+
+
+_P = C.c_void_p
+_D3 = C.c_void_p * 3
+
+
+def _declare(L):
+    L.orc_philox4x32_10.argtypes = [_P, _P, _P]
+    L.orc_u01.argtypes = [C.c_uint32]
+    L.orc_u01.restype = C.c_double
+    L.orc_fdtd_b_half.argtypes = [C.POINTER(Grid), _D3, _D3]
+    L.orc_fdtd_e.argtypes = [C.POINTER(Grid), _D3, _D3, _D3]
+    L.orc_gather.argtypes = [C.POINTER(Grid), _D3, _D3, C.c_double, C.c_double, C.c_double, _P, _P]
+    L.orc_boris.argtypes = [C.c_double, _P, _P, _P]
+    L.orc_esirkepov.argtypes = [C.POINTER(Grid), C.c_double] + [C.c_double] * 6 + [_D3]
+    L.orc_push_deposit.argtypes = [C.POINTER(Grid), _D3, _D3, _D3, C.POINTER(Species)]
+    L.orc_energy_fields.argtypes = [C.POINTER(Grid), _D3, _D3, _P]
+    L.orc_energy_particles.argtypes = [C.POINTER(Species)]
+    L.orc_energy_particles.restype = C.c_double
+    L.orc_charge_density.argtypes = [C.POINTER(Grid), C.POINTER(Species), _P]
+    L.orc_div_e.argtypes = [C.POINTER(Grid), _D3, _P]
+    L.orc_plasma_scales.argtypes = [C.c_double, _P]
+    L.orc_laser_scales.argtypes = [C.c_double, _P]
+    for name, fn in _EXTRA_DECLS:
+        fn(L)
+
+
+_EXTRA_DECLS = []
+
+
+def _ptr(a):
+    assert a.flags["C_CONTIGUOUS"], "oracle arrays must be C-contiguous"
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _f3(F):
+    """(3, nz, ny, nx) float64 array -> array of 3 pointers."""
+    assert F.dtype == np.float64 and F.shape[0] == 3 and F.flags["C_CONTIGUOUS"]
+    return _D3(*[F[c].ctypes.data_as(C.c_void_p) for c in range(3)])
+
+
+# --------------------------------------------------------------------------- Philox
+def philox(ctr, key):
+    c = np.asarray(ctr, dtype=np.uint32).copy()
+    k = np.asarray(key, dtype=np.uint32).copy()
+    o = np.zeros(4, dtype=np.uint32)
+    lib().orc_philox4x32_10(_ptr(c), _ptr(k), _ptr(o))
+    return o
+
+
+def u01(x):
+    return lib().orc_u01(int(x))
+
+
+# --------------------------------------------------------------------------- fields
+def zeros_field(g):
+    return np.zeros((3,) + g.shape, dtype=np.float64)
+
+
+def fdtd_b_half(g, E, B):
+    lib().orc_fdtd_b_half(C.byref(g), _f3(E), _f3(B))
+
+
+def fdtd_e(g, E, B, J):
+    lib().orc_fdtd_e(C.byref(g), _f3(E), _f3(B), _f3(J))
+
+
+def energy_fields(g, E, B):
+    out = np.zeros(2)
+    lib().orc_energy_fields(C.byref(g), _f3(E), _f3(B), _ptr(out))
+    return out
+
+
+def div_e(g, E):
+    out = np.zeros(g.shape)
+    lib().orc_div_e(C.byref(g), _f3(E), _ptr(out))
+    return out
+
+
+# --------------------------------------------------------------------------- particles
+class Particles:
+    """Host particle set in FP64: positions in cell units, u = gamma*beta."""
+
+    FIELDS = ("x", "y", "z", "ux", "uy", "uz", "w")
+
+    def __init__(self, q, m, x, y, z, ux, uy, uz, w, zq=None, ids=None, tau=None):
+        self.q, self.m = float(q), float(m)
+        for name, v in zip(self.FIELDS, (x, y, z, ux, uy, uz, w)):
+            setattr(self, name, np.ascontiguousarray(v, dtype=np.float64).copy())
+        self.zq = None if zq is None else np.ascontiguousarray(zq, dtype=np.float64).copy()
+        self.tau = None if tau is None else np.ascontiguousarray(tau, dtype=np.float64).copy()
+        self.ids = (np.arange(len(self.x), dtype=np.uint64) if ids is None
+                    else np.ascontiguousarray(ids, dtype=np.uint64).copy())
+
+    @property
+    def n(self):
+        return len(self.x)
+
+    def cstruct(self):
+        s = Species()
+        s.q, s.m, s.n = self.q, self.m, self.n
+        for name in self.FIELDS:
+            setattr(s, name, _ptr(getattr(self, name)).value)
+        s.zq = None if self.zq is None else _ptr(self.zq).value
+        return s
+
+    def append(self, other):
+        for name in self.FIELDS:
+            setattr(self, name, np.concatenate([getattr(self, name), getattr(other, name)]))
+        if self.zq is not None:
+            self.zq = np.concatenate([self.zq, other.zq])
+        if self.tau is not None:
+            self.tau = np.concatenate([self.tau, other.tau])
+        self.ids = np.concatenate([self.ids, other.ids])
+
+    def select(self, mask):
+        for name in self.FIELDS:
+            setattr(self, name, np.ascontiguousarray(getattr(self, name)[mask]))
+        if self.zq is not None:
+            self.zq = np.ascontiguousarray(self.zq[mask])
+        if self.tau is not None:
+            self.tau = np.ascontiguousarray(self.tau[mask])
+        self.ids = np.ascontiguousarray(self.ids[mask])
+
+
+def gather(g, E, B, pos):
+    e = np.zeros(3)
+    b = np.zeros(3)
+    lib().orc_gather(C.byref(g), _f3(E), _f3(B), float(pos[0]), float(pos[1]), float(pos[2]),
+                     _ptr(e), _ptr(b))
+    return e, b
+
+
+def boris(qm_dt_half, e, b, u):
+    e = np.ascontiguousarray(e, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    uu = np.ascontiguousarray(u, dtype=np.float64).copy()
+    lib().orc_boris(float(qm_dt_half), _ptr(e), _ptr(b), _ptr(uu))
+    return uu
+
+
+def esirkepov(g, qw, p0, p1, J):
+    lib().orc_esirkepov(C.byref(g), float(qw), *[float(v) for v in p0], *[float(v) for v in p1], _f3(J))
+
+
+def push_deposit(g, E, B, J, sp):
+    s = sp.cstruct()
+    lib().orc_push_deposit(C.byref(g), _f3(E), _f3(B), _f3(J), C.byref(s))
+
+
+def energy_particles(sp):
+    s = sp.cstruct()
+    return lib().orc_energy_particles(C.byref(s))
+
+
+def charge_density(g, sp, rho=None):
+    if rho is None:
+        rho = np.zeros(g.shape)
+    s = sp.cstruct()
+    lib().orc_charge_density(C.byref(g), C.byref(s), _ptr(rho))
+    return rho
+
+
+def plasma_scales(n_m3):
+    """(w_p, E_0, B_0, J_0, rho_0) in SI for electron density n [m^-3]."""
+    out = np.zeros(5)
+    lib().orc_plasma_scales(float(n_m3), _ptr(out))
+    return out
+
+
+def laser_scales(lambda_m):
+    """(w0, n_c, E_ref, c/w0) in SI for wavelength lambda [m]."""
+    out = np.zeros(4)
+    lib().orc_laser_scales(float(lambda_m), _ptr(out))
+    return out

@@ -1,0 +1,77 @@
+/*
+ * FP64 CPU oracle for the hybrid fluid-kinetic laser-plasma step of
+ * arXiv 2510.11174 ("Machine Learning-Integrated Hybrid Fluid-Kinetic Framework
+ * for Quantum Electrodynamic Laser-Plasma Simulations").
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path (the CUDA library and
+ * its Python binding) may include, link or call this code; only the test
+ * suite, the smoke check and the benchmark's CPU-baseline leg use it.  It
+ * shares no code, header, table or constant with the CUDA path.
+ *
+ * The paper prints no equations.  Every routine here is the plain textbook
+ * algorithm that the paper names (Methodology section), written as scalar
+ * loops in double precision so that it can be checked against the cited
+ * source by eye.  Units are laser-normalised: length c/w0, time 1/w0,
+ * momentum u = p/(m_e c) = gamma*beta, fields in m_e c w0 / e, density in n_c,
+ * charge in e, mass in m_e.  In these units Maxwell's equations read
+ * dB/dt = -curl E, dE/dt = curl B - J, div E = rho.
+ *
+ * Particle positions are stored in cell units (xi = x/dx) so that the CIC
+ * shape of a particle needs no division.
+ */
+#ifndef ORC_H
+#define ORC_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- grid ---------------------------------------------------------------- */
+typedef struct {
+    int nx, ny, nz;
+    double dx, dy, dz, dt;
+    int bc[3];               /* 0 = periodic, 1 = first-order Mur fields + reflecting particles */
+} orc_grid;
+
+/* field component staggering (Yee 1966): offset of each component in cell units */
+enum { ORC_EX = 0, ORC_EY, ORC_EZ, ORC_BX, ORC_BY, ORC_BZ };
+
+/* ---- Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) -------------------- */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+double orc_u01(uint32_t x);  /* ((x>>9)+0.5)*2^-23, exactly representable in FP32 */
+
+/* ---- FDTD --------------------------------------------------------------- */
+void orc_fdtd_b_half(const orc_grid *g, const double *E[3], double *B[3]);
+void orc_fdtd_e(const orc_grid *g, double *E[3], const double *B[3], const double *J[3]);
+
+/* ---- particles ---------------------------------------------------------- */
+typedef struct {
+    double q, m;             /* charge (e) and mass (m_e) of the species */
+    long n;
+    double *x, *y, *z;       /* cell units */
+    double *ux, *uy, *uz;    /* gamma*beta */
+    double *w;               /* weight: real particles per macro particle, units n_c (c/w0)^3 */
+    double *zq;              /* per-particle charge state (ions) or NULL: q_p = zq[p] when set */
+} orc_species;
+
+void orc_gather(const orc_grid *g, const double *E[3], const double *B[3],
+                double xi, double yi, double zi, double e[3], double b[3]);
+void orc_boris(double qm_dt_half, const double e[3], const double b[3], double u[3]);
+void orc_esirkepov(const orc_grid *g, double qw, double x0, double y0, double z0,
+                   double x1, double y1, double z1, double *J[3]);
+void orc_push_deposit(const orc_grid *g, const double *E[3], const double *B[3],
+                      double *J[3], orc_species *s);
+
+/* ---- diagnostics --------------------------------------------------------- */
+void orc_energy_fields(const orc_grid *g, const double *E[3], const double *B[3], double out[2]);
+double orc_energy_particles(const orc_species *s);
+void orc_charge_density(const orc_grid *g, const orc_species *s, double *rho);
+void orc_div_e(const orc_grid *g, const double *E[3], double *div);
+void orc_plasma_scales(double n_m3, double out[5]);
+void orc_laser_scales(double lambda_m, double out[4]);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

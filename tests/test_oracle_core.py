@@ -1,0 +1,284 @@
+"""Pins of the FP64 oracle's core (Philox, Yee FDTD, Mur, Boris, CIC, Esirkepov)
+against values and identities that do not come from the oracle itself:
+published known-answer vectors, closed-form dispersion relations, exact
+invariants of the schemes and the paper's printed normalisation example.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _read_rows(name):
+    rows = []
+    for line in open(os.path.join(GOLD, name)):
+        line = line.strip()
+        if line and not line.startswith("#"):
+            rows.append(line.split())
+    return rows
+
+
+# ----------------------------------------------------------------- Philox
+def test_philox_known_answers():
+    for r in _read_rows("philox4x32_10_kat.txt"):
+        v = [int(x, 16) for x in r]
+        out = oracle.philox(v[0:4], v[4:6])
+        assert [int(o) for o in out] == v[6:10]
+
+
+def test_u01_exact_in_fp32_and_open_interval():
+    for x in [0, 1, 255, 256, 0x7FFFFFFF, 0xFFFFFFFF, 0x12345678]:
+        u = oracle.u01(x)
+        assert 0.0 < u < 1.0
+        assert float(np.float32(u)) == u
+    assert oracle.u01(0) == 2.0 ** -24
+    assert oracle.u01(0xFFFFFFFF) == 1.0 - 2.0 ** -24
+
+
+# ----------------------------------------------------------------- units
+def test_plasma_scales_match_paper_worked_example():
+    """Results section: n = 1e24 m^-3 gives E0, B0, J0, rho0 as printed."""
+    wp, E0, B0, J0, rho0 = oracle.plasma_scales(1e24)
+    got = {"E0": E0, "B0": B0, "J0": J0, "rho0": rho0}
+    for name, val, digits in _read_rows("plasma_scales_1e24.txt"):
+        ref, d = float(val), int(digits)
+        # the printed value is the true value rounded to d significant digits
+        assert abs(got[name] - ref) <= 0.5 * 10 ** (math.floor(math.log10(ref)) - d + 1) * 1.0001, name
+
+
+def test_laser_scales_critical_density():
+    w0, nc, Eref, L = oracle.laser_scales(0.8e-6)
+    # textbook: n_c = 1.115e21 cm^-3 / lambda_um^2; a0 = 0.855 lambda_um sqrt(I / 1e18 W cm^-2)
+    assert abs(nc * 1e-6 - 1.1148e21 / 0.64) / (1.1148e21 / 0.64) < 2e-3
+    assert abs(L - 0.8e-6 / (2 * math.pi)) < 1e-18
+
+
+# ----------------------------------------------------------------- Yee FDTD
+def _vacuum_step(g, E, B):
+    J = oracle.zeros_field(g)
+    oracle.fdtd_b_half(g, E, B)
+    oracle.fdtd_e(g, E, B, J)
+    oracle.fdtd_b_half(g, E, B)
+
+
+@pytest.mark.parametrize("comp,modes", [(2, (2, 1, 0)), (0, (0, 1, 3)), (1, (1, 0, 2))])
+def test_yee_discrete_dispersion(comp, modes):
+    """A periodic vacuum eigenmode oscillates at the frequency fixed by
+    sin^2(w dt/2)/dt^2 = sum_i sin^2(k_i d_i/2)/d_i^2 (Yee scheme)."""
+    nx, ny, nz = 12, 10, 8
+    d = (0.39, 0.33, 0.41)
+    dt = 0.95 / math.sqrt(sum(1.0 / v ** 2 for v in d))
+    g = oracle.Grid.make(nx, ny, nz, *d, dt)
+    n = (nx, ny, nz)
+    k = [2 * math.pi * modes[a] / (n[a] * d[a]) for a in range(3)]
+    assert modes[comp] == 0  # polarisation along a wavevector-free axis: div E = 0
+    # E_comp sits at half-integer position along its own axis, integer along the others
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    pos = [x * d[0], y * d[1], z * d[2]]
+    pos[comp] = pos[comp] + 0.5 * d[comp]
+    phase = k[0] * pos[0] + k[1] * pos[1] + k[2] * pos[2]
+    E = oracle.zeros_field(g)
+    B = oracle.zeros_field(g)
+    E[comp] = np.cos(phase)
+    s = sum(math.sin(k[a] * d[a] / 2) ** 2 / d[a] ** 2 for a in range(3))
+    w = 2.0 / dt * math.asin(dt * math.sqrt(s))
+    nsteps = 1000
+    for _ in range(nsteps):
+        _vacuum_step(g, E, B)
+    exact = np.cos(phase) * math.cos(w * nsteps * dt)
+    assert np.max(np.abs(E[comp] - exact)) < 1e-10
+    others = [c for c in range(3) if c != comp]
+    assert np.max(np.abs(E[others])) < 1e-12
+
+
+def test_div_b_stays_zero():
+    g = oracle.Grid.make(8, 7, 6, 0.4, 0.35, 0.3, 0.15)
+    rng = np.random.default_rng(3)
+    E = rng.standard_normal((3,) + g.shape)
+    B = oracle.zeros_field(g)
+    for _ in range(20):
+        _vacuum_step(g, E, B)
+    # div B at cell centres (i+1/2, j+1/2, k+1/2)
+    divb = ((np.roll(B[0], -1, 2) - B[0]) / g.dx + (np.roll(B[1], -1, 1) - B[1]) / g.dy
+            + (np.roll(B[2], -1, 0) - B[2]) / g.dz)
+    assert np.max(np.abs(divb)) < 1e-12 * np.max(np.abs(B))
+
+
+def test_mur_exact_absorption_at_magic_time_step():
+    """With c dt = dx the Mur coefficient is zero and a 1D pulse leaves the box
+    without reflection (first-order Mur is exact in 1D at unit Courant number)."""
+    nx, ny, nz = 48, 2, 2
+    dx = 0.5
+    g = oracle.Grid.make(nx, ny, nz, dx, 1.0, 1.0, dx, bc=(1, 0, 0))
+    E = oracle.zeros_field(g)
+    B = oracle.zeros_field(g)
+    xe = np.arange(nx) * dx
+    xb = (np.arange(nx) + 0.5) * dx
+    f = lambda s: np.exp(-((s - 12.0) / 1.5) ** 2)
+    E[1][:, :, :] = f(xe)[None, None, :]
+    B[2][:, :, :nx - 1] = f(xb)[None, None, :nx - 1]
+    peak = np.max(np.abs(E))
+    for _ in range(3 * nx):
+        _vacuum_step(g, E, B)
+    assert np.max(np.abs(E)) < 1e-12 * peak
+    assert np.max(np.abs(B)) < 1e-12 * peak
+
+
+def test_mur_3d_normal_incidence_reflection_small():
+    nx, ny, nz = 64, 4, 4
+    dx = 0.39
+    dt = 0.95 / math.sqrt(3.0 / dx ** 2)
+    g = oracle.Grid.make(nx, ny, nz, dx, dx, dx, dt, bc=(1, 0, 0))
+    E = oracle.zeros_field(g)
+    B = oracle.zeros_field(g)
+    xe = np.arange(nx) * dx
+    xb = (np.arange(nx) + 0.5) * dx
+    f = lambda s: np.exp(-((s - 12.0) / 2.0) ** 2) * np.cos(2.0 * s)
+    E[1][:] = f(xe)[None, None, :]
+    B[2][:, :, :nx - 1] = f(xb)[None, None, :nx - 1]
+    peak = np.max(np.abs(E))
+    for _ in range(int(2.2 * nx * dx / dt)):
+        _vacuum_step(g, E, B)
+    assert np.max(np.abs(E)) < 1e-2 * peak
+
+
+# ----------------------------------------------------------------- Boris
+def test_boris_pure_magnetic_rotation_is_exact():
+    rng = np.random.default_rng(1)
+    for _ in range(50):
+        u = rng.standard_normal(3) * rng.uniform(0.01, 50)
+        b = rng.standard_normal(3) * rng.uniform(0.01, 5)
+        h = rng.uniform(0.01, 0.3) * rng.choice([-1, 1])
+        gam = math.sqrt(1 + u @ u)
+        u1 = oracle.boris(h, np.zeros(3), b, u)
+        assert abs(np.linalg.norm(u1) - np.linalg.norm(u)) <= 1e-14 * np.linalg.norm(u)
+        # rotation angle about b is 2 atan(|t|), t = (q dt / 2 m gamma) B
+        bh = b / np.linalg.norm(b)
+        pa, pb = u - (u @ bh) * bh, u1 - (u1 @ bh) * bh
+        ang = math.atan2(np.linalg.norm(np.cross(pa, pb)), pa @ pb)
+        assert abs(ang - 2 * math.atan(abs(h) * np.linalg.norm(b) / gam)) < 1e-12
+        assert abs(u1 @ bh - u @ bh) < 1e-13 * np.linalg.norm(u)
+
+
+def test_boris_pure_electric_is_exact_impulse():
+    e = np.array([0.3, -1.2, 2.0])
+    u = np.array([0.1, 0.2, -0.3])
+    h = 0.07
+    u1 = oracle.boris(h, e, np.zeros(3), u)
+    assert np.allclose(u1, u + 2 * h * e, rtol=0, atol=1e-15)
+
+
+def _uniform_grid(n=16, d=0.4, dt=0.2, bc=(0, 0, 0)):
+    return oracle.Grid.make(n, n, n, d, d, d, dt, bc=bc)
+
+
+def test_larmor_radius_discrete_closed_form():
+    """A particle in uniform B moves on a circle of radius
+    R = (v_perp / Omega) sqrt(1 + (Omega dt / 2)^2), Omega = q B / (m gamma)."""
+    g = _uniform_grid()
+    E = oracle.zeros_field(g)
+    B = oracle.zeros_field(g)
+    Bz = 1.7
+    B[2][:] = Bz
+    J = oracle.zeros_field(g)
+    u0 = np.array([0.6, 0.0, 0.0])
+    sp = oracle.Particles(-1.0, 1.0, [8.0], [8.0], [8.0], [u0[0]], [u0[1]], [u0[2]], [1.0])
+    gam = math.sqrt(1 + u0 @ u0)
+    Om = Bz / gam
+    R = (u0[0] / gam / Om) * math.sqrt(1 + (Om * g.dt / 2) ** 2)
+    xs, ys = [], []
+    for _ in range(40):
+        oracle.push_deposit(g, E, B, J, sp)
+        xs.append(sp.x[0] * g.dx)
+        ys.append(sp.y[0] * g.dy)
+    xs, ys = np.array(xs), np.array(ys)
+    # circle through all points: solve for centre with least squares
+    A = np.c_[2 * xs, 2 * ys, np.ones_like(xs)]
+    sol = np.linalg.lstsq(A, xs ** 2 + ys ** 2, rcond=None)[0]
+    r_fit = math.sqrt(sol[2] + sol[0] ** 2 + sol[1] ** 2)
+    assert abs(r_fit - R) / R < 1e-10
+    assert abs(math.hypot(sp.ux[0], sp.uy[0]) - 0.6) < 1e-13
+
+
+# ----------------------------------------------------------------- gather
+def test_cic_gather_reproduces_linear_fields():
+    g = _uniform_grid(n=10, bc=(1, 1, 1))
+    E = oracle.zeros_field(g)
+    B = oracle.zeros_field(g)
+    z, y, x = np.meshgrid(np.arange(10.0), np.arange(10.0), np.arange(10.0), indexing="ij")
+    lin = lambda X, Y, Z: 0.3 + 0.7 * X - 0.2 * Y + 0.11 * Z
+    E[0] = lin(x + 0.5, y, z)
+    E[1] = lin(x, y + 0.5, z)
+    E[2] = lin(x, y, z + 0.5)
+    B[0] = lin(x, y + 0.5, z + 0.5)
+    B[1] = lin(x + 0.5, y, z + 0.5)
+    B[2] = lin(x + 0.5, y + 0.5, z)
+    rng = np.random.default_rng(5)
+    for _ in range(20):
+        p = rng.uniform(1.0, 7.9, 3)
+        e, b = oracle.gather(g, E, B, p)
+        want = lin(*p)
+        assert np.allclose(e, want, atol=1e-13) and np.allclose(b, want, atol=1e-13)
+
+
+# ----------------------------------------------------------------- Esirkepov
+@pytest.mark.parametrize("delta", [(0.1, 0.05, -0.02), (0.7, 0.0, 0.0), (0.6, -0.5, 0.0), (-0.6, 0.55, 0.8)])
+def test_esirkepov_single_particle_continuity_and_total_current(delta):
+    g = oracle.Grid.make(8, 8, 8, 0.4, 0.5, 0.3, 0.2)
+    p0 = np.array([3.7, 4.45, 2.1])
+    p1 = p0 + np.array(delta)
+    qw = -0.8
+    J = oracle.zeros_field(g)
+    oracle.esirkepov(g, qw, p0, p1, J)
+    rho0 = oracle.charge_density(g, oracle.Particles(1, 1, [p0[0]], [p0[1]], [p0[2]], [0], [0], [0], [qw]))
+    rho1 = oracle.charge_density(g, oracle.Particles(1, 1, [p1[0]], [p1[1]], [p1[2]], [0], [0], [0], [qw]))
+    divj = oracle.div_e(g, J)
+    assert np.max(np.abs((rho1 - rho0) / g.dt + divj)) < 1e-12 * np.max(np.abs(rho0)) / g.dt
+    dV = g.dx * g.dy * g.dz
+    d = (g.dx, g.dy, g.dz)
+    for c in range(3):
+        assert abs(J[c].sum() * dV - qw * delta[c] * d[c] / g.dt) < 1e-12
+
+
+def test_gauss_law_invariant_over_pic_steps():
+    """div E - rho is unchanged by a full PIC step (exact discrete continuity)."""
+    g = oracle.Grid.make(10, 9, 8, 0.4, 0.4, 0.4, 0.2)
+    rng = np.random.default_rng(11)
+    n = 400
+    sp = oracle.Particles(-1.0, 1.0, rng.uniform(0, 10, n), rng.uniform(0, 9, n), rng.uniform(0, 8, n),
+                          *(rng.standard_normal((3, n)) * 0.5), rng.uniform(0.5, 1.5, n) * 1e-3)
+    E = rng.standard_normal((3,) + g.shape) * 0.1
+    B = rng.standard_normal((3,) + g.shape) * 0.1
+
+    def gauss():
+        return oracle.div_e(g, E) - oracle.charge_density(g, sp)
+
+    r0 = gauss()
+    for _ in range(10):
+        J = oracle.zeros_field(g)
+        oracle.push_deposit(g, E, B, J, sp)
+        oracle.fdtd_b_half(g, E, B)
+        oracle.fdtd_e(g, E, B, J)
+        oracle.fdtd_b_half(g, E, B)
+    rmax = np.max(np.abs(oracle.charge_density(g, sp)))
+    assert np.max(np.abs(gauss() - r0)) < 1e-12 * max(rmax, np.max(np.abs(r0)))
+
+
+def test_reflecting_wall_reverses_normal_momentum():
+    g = _uniform_grid(n=8, bc=(1, 1, 1))
+    E = oracle.zeros_field(g)
+    B = oracle.zeros_field(g)
+    J = oracle.zeros_field(g)
+    sp = oracle.Particles(-1.0, 1.0, [0.05], [6.95], [3.0], [-2.0], [3.0], [0.0], [1.0])
+    gam = math.sqrt(1 + 4 + 9)
+    oracle.push_deposit(g, E, B, J, sp)
+    x_exp = -(0.05 - g.dt * 2.0 / gam / g.dx)
+    y_exp = 2 * 7 - (6.95 + g.dt * 3.0 / gam / g.dx)
+    assert abs(sp.x[0] - x_exp) < 1e-14 and sp.ux[0] == 2.0
+    assert abs(sp.y[0] - y_exp) < 1e-14 and sp.uy[0] == -3.0
+    assert abs(oracle.energy_particles(sp) - (gam - 1)) < 1e-14
