@@ -1,0 +1,180 @@
+/*
+ * hyb.h -- C ABI of the GB300-native hybrid fluid-kinetic laser-plasma step
+ * (arXiv 2510.11174, "Machine Learning-Integrated Hybrid Fluid-Kinetic
+ * Framework for Quantum Electrodynamic Laser-Plasma Simulations").
+ *
+ * The library advances, on one GPU, the paper's time step (Methodology): a
+ * 3D Yee FDTD field update with first-order Mur boundaries and a Gaussian
+ * laser source, a relativistic cold fluid in quiet cells, and a
+ * particle-in-cell update (relativistic Boris push, charge-conserving
+ * Esirkepov deposition, blended ADK/multiphoton ionization, Monte Carlo
+ * radiation reaction and pair production from Airy-function rates) in the
+ * cells a convolutional regime classifier flags as kinetic.
+ *
+ * Units (laser-normalised, wavelength lambda): length c/w0, time 1/w0,
+ * momentum u = gamma*beta (p / m c), E in m_e c w0 / e, B in m_e w0 / e,
+ * density in n_c = eps0 m_e w0^2 / e^2, charge in e, mass in m_e.  Particle
+ * positions are in cell units (x / dx), domain [0, n) on periodic axes and
+ * [0, n-1] on absorbing axes.
+ *
+ * Conventions common to every entry point:
+ *  - every call returns hyb_status; no C++ exception crosses the ABI;
+ *  - descriptors are caller-owned and copied during the call;
+ *  - pointers named *_host are host memory; pointers named *_dev are device
+ *    memory on the context's device; arrays passed to a call are borrowed for
+ *    the duration of that call only;
+ *  - calls are ordered on the context's CUDA stream and asynchronous, except
+ *    hyb_diagnostics and the hyb_get_* calls, which synchronise that stream;
+ *  - errors raised on the device (particle-capacity overflow, non-finite
+ *    fields) are latched in a device status word and returned by the next
+ *    synchronising call; a context in that state rejects hyb_step with
+ *    HYB_ESTATE until hyb_clear_status;
+ *  - hyb_last_error returns a human-readable message for the last failure.
+ */
+#ifndef HYB_H
+#define HYB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    HYB_OK = 0,
+    HYB_EINVAL = 1,     /* invalid argument or descriptor */
+    HYB_ENOMEM = 2,     /* device allocation or caller arena too small */
+    HYB_ECUDA = 3,      /* CUDA runtime error */
+    HYB_EOVERFLOW = 4,  /* a particle tile or migration buffer overflowed */
+    HYB_ENAN = 5,       /* non-finite value in fields */
+    HYB_ETIMEOUT = 6,   /* a bounded device wait gave up */
+    HYB_ESTATE = 7      /* context is in an error state */
+} hyb_status;
+
+enum { HYB_BC_PERIODIC = 0, HYB_BC_MUR = 1 };  /* per axis: Mur fields + reflecting particles */
+enum { HYB_LASER_NONE = 0, HYB_LASER_GAUSS = 1 };
+
+typedef struct hyb_ctx hyb_ctx;  /* opaque, library-owned */
+
+/*
+ * Grid, time step, boundaries and laser (paper, Methodology: uniform
+ * Cartesian grid; constant dt from the Courant limit; first-order Mur
+ * absorbers; Gaussian pulse with temporal and spatial envelopes).
+ */
+typedef struct {
+    int nx, ny, nz;           /* cells (= nodes) per axis; multiples of `tile` */
+    double dx, dy, dz;        /* cell size [c/w0] */
+    double dt;                /* time step [1/w0]; if <= 0, cfl_frac * Courant limit */
+    double cfl_frac;          /* used when dt <= 0 (e.g. 0.95) */
+    int bc[3];                /* HYB_BC_* per axis */
+    double lambda_um;         /* laser wavelength, fixes the physical scales */
+    /* Gaussian soft source: current sheet J_pol on the plane x = x_src
+     * (node index), field amplitude a0, intensity FWHM tau_fwhm [1/w0],
+     * 1/e^2 intensity radius w0_spot [c/w0], centre (y_c, z_c) [cells],
+     * peak time t_peak [1/w0]; pol 1 = y, 2 = z. */
+    int laser_kind;
+    double a0, tau_fwhm, w0_spot, t_peak, y_c, z_c;
+    int x_src, pol;
+    uint32_t seed;            /* Philox key word 0 */
+    int tile;                 /* tile edge in cells (4 or 8; 0 = 8) */
+    void *stream;             /* cudaStream_t the context runs on (NULL = legacy default) */
+    void *arena_dev;          /* optional caller-provided device arena (e.g. a torch tensor) */
+    size_t arena_bytes;       /* its size; all library buffers come from it when non-NULL */
+} hyb_grid_desc;
+
+/*
+ * A macro-particle species (paper, Methodology: PIC macro-particles weighted
+ * by density-volume fraction; electrons, ions and positrons).
+ * Initial particles are passed explicitly as SoA FP32 arrays (positions in
+ * cell units, u = gamma*beta, weight in n_c (c/w0)^3), either host or device
+ * memory as `ptr_on_device` says.  ids (uint64) identify particles across
+ * tile migrations and key their random streams; NULL assigns 0..n-1.
+ */
+typedef struct {
+    double q, m;              /* charge [e], mass [m_e] */
+    long long n;              /* initial particle count */
+    long long tile_capacity;  /* slots per tile; 0 = 2 x max initial count per tile + 64 */
+    int ptr_on_device;        /* 1: arrays below are device pointers */
+    const float *x, *y, *z, *ux, *uy, *uz, *w;
+    const float *zq;          /* per-particle charge state (ions, q_p = q * zq) or NULL */
+    const uint64_t *ids;      /* or NULL */
+} hyb_species_desc;
+
+/* Diagnostics: FP64 energy reductions (paper, Methodology: total energy from
+ * electromagnetic, kinetic and thermal components) and device status. */
+#define HYB_MAX_SPECIES 8
+typedef struct {
+    long long step;
+    double time;                           /* [1/w0] */
+    double w_e, w_b;                       /* field energy (1/2) sum E^2 dV, (1/2) sum B^2 dV */
+    double w_kin[HYB_MAX_SPECIES];         /* sum w m (gamma - 1) per species */
+    long long count[HYB_MAX_SPECIES];      /* live macro-particles per species */
+    int n_species;
+    int status;                            /* latched device status (hyb_status) */
+    long long launches_per_step;           /* kernels one step launches */
+} hyb_diag;
+
+/* Create a context: validates the descriptor, allocates fields on the
+ * context's stream and zeroes them.  Returns HYB_EINVAL for a bad descriptor
+ * (grid not a multiple of the tile, fewer than 4 nodes on a Mur axis, dt above
+ * the Courant limit, ...), HYB_ENOMEM when the arena is too small. */
+hyb_status hyb_init_grid(const hyb_grid_desc *desc, hyb_ctx **out);
+void hyb_destroy(hyb_ctx *ctx);
+
+/* Add a species; writes its id (0, 1, ...) to *species_id.  Particles are
+ * binned into tiles on the device.  HYB_EOVERFLOW if a tile exceeds its
+ * capacity. */
+hyb_status hyb_load_species(hyb_ctx *ctx, const hyb_species_desc *desc, int *species_id);
+
+/* Replace the fields E, B (each: 3 contiguous FP32 arrays of nz*ny*nx
+ * values, x fastest, Yee-staggered as documented in the library).  Host or
+ * device memory as on_device says. */
+hyb_status hyb_set_fields(hyb_ctx *ctx, const float *E, const float *B, int on_device);
+
+/* Advance n steps (stream-ordered; the step sequence is captured once into a
+ * CUDA graph and replayed). */
+hyb_status hyb_step(hyb_ctx *ctx, int nsteps);
+
+/* Synchronises; fills *out. */
+hyb_status hyb_diagnostics(hyb_ctx *ctx, hyb_diag *out);
+
+/* Copy fields back (synchronises): E, B, J each 3*nz*ny*nx floats (host). */
+hyb_status hyb_get_fields(hyb_ctx *ctx, float *E_host, float *B_host, float *J_host);
+
+/* Copy a species back in tile order (synchronises).  Arrays of `max_n`
+ * entries; *n_out receives the live count (HYB_EINVAL if > max_n).
+ * zq may be NULL. */
+hyb_status hyb_get_species(hyb_ctx *ctx, int species_id, long long max_n, float *x, float *y,
+                           float *z, float *ux, float *uy, float *uz, float *w, float *zq,
+                           uint64_t *ids, long long *n_out);
+
+/* Resets the latched device status word. */
+hyb_status hyb_clear_status(hyb_ctx *ctx);
+
+/* Per-phase timing of a step.  With profiling on, the captured step graph
+ * records a CUDA event (on the context's stream) at every phase boundary;
+ * hyb_phase_times synchronises and returns the device time of each phase of
+ * the most recent step in milliseconds (0 for phases the step does not run).
+ * Turning profiling on or off rebuilds the step graph. */
+enum {
+    HYB_PH_PUSH = 0,      /* gather + Boris + move + Esirkepov into tile frames */
+    HYB_PH_JREDUCE = 1,   /* fixed-order sum of tile frames into J */
+    HYB_PH_SOURCE = 2,    /* laser soft source */
+    HYB_PH_REBIN = 3,     /* migration + compaction of particle tiles */
+    HYB_PH_FIELD = 4,     /* B half, E, Mur, B half */
+    HYB_NPHASE = 8
+};
+typedef struct {
+    float ms[HYB_NPHASE];
+} hyb_phase_times_t;
+hyb_status hyb_set_profiling(hyb_ctx *ctx, int on);
+hyb_status hyb_phase_times(hyb_ctx *ctx, hyb_phase_times_t *out);
+
+/* Message for the last failing call on this thread (never NULL). */
+const char *hyb_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HYB_H */

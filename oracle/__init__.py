@@ -75,6 +75,7 @@ def _declare(L):
     L.orc_energy_particles.restype = C.c_double
     L.orc_charge_density.argtypes = [C.POINTER(Grid), C.POINTER(Species), _P]
     L.orc_div_e.argtypes = [C.POINTER(Grid), _D3, _P]
+    L.orc_laser_source.argtypes = [C.POINTER(Grid), C.c_int, C.c_int] + [C.c_double] * 6 + [C.c_long, _D3]
     L.orc_plasma_scales.argtypes = [C.c_double, _P]
     L.orc_laser_scales.argtypes = [C.c_double, _P]
     for name, fn in _EXTRA_DECLS:
@@ -229,3 +230,8 @@ def laser_scales(lambda_m):
     out = np.zeros(4)
     lib().orc_laser_scales(float(lambda_m), _ptr(out))
     return out
+
+
+def laser_source(g, J, step, x_src, pol, a0, tau_fwhm, t_peak, w0_spot, y_c, z_c):
+    lib().orc_laser_source(C.byref(g), int(x_src), int(pol), float(a0), float(tau_fwhm), float(t_peak),
+                           float(w0_spot), float(y_c), float(z_c), int(step), _f3(J))

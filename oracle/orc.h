@@ -45,6 +45,10 @@ double orc_u01(uint32_t x);  /* ((x>>9)+0.5)*2^-23, exactly representable in FP3
 void orc_fdtd_b_half(const orc_grid *g, const double *E[3], double *B[3]);
 void orc_fdtd_e(const orc_grid *g, double *E[3], const double *B[3], const double *J[3]);
 
+/* ---- laser ------------------------------------------------------------- */
+void orc_laser_source(const orc_grid *g, int x_src, int pol, double a0, double tau, double t_peak,
+                      double w0, double y_c, double z_c, long step, double *J[3]);
+
 /* ---- particles ---------------------------------------------------------- */
 typedef struct {
     double q, m;             /* charge (e) and mass (m_e) of the species */

@@ -1,0 +1,107 @@
+"""ctypes declarations of include/hyb.h: the structures and entry points with the
+same names as the C ABI.  Argument marshalling only -- every step of the
+hybrid fluid-kinetic time step runs in the CUDA library libhyb.so.
+
+The library is built in-tree (``paper_2510_11174_gb300/build.py``); importing
+this module raises if it is missing, there is no fallback.
+"""
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libhyb.so")
+
+HYB_OK, HYB_EINVAL, HYB_ENOMEM, HYB_ECUDA, HYB_EOVERFLOW, HYB_ENAN, HYB_ETIMEOUT, HYB_ESTATE = range(8)
+STATUS_NAMES = {0: "HYB_OK", 1: "HYB_EINVAL", 2: "HYB_ENOMEM", 3: "HYB_ECUDA", 4: "HYB_EOVERFLOW",
+                5: "HYB_ENAN", 6: "HYB_ETIMEOUT", 7: "HYB_ESTATE"}
+HYB_BC_PERIODIC, HYB_BC_MUR = 0, 1
+HYB_LASER_NONE, HYB_LASER_GAUSS = 0, 1
+HYB_MAX_SPECIES = 8
+
+
+class hyb_grid_desc(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+                ("dx", C.c_double), ("dy", C.c_double), ("dz", C.c_double),
+                ("dt", C.c_double), ("cfl_frac", C.c_double),
+                ("bc", C.c_int * 3), ("lambda_um", C.c_double),
+                ("laser_kind", C.c_int),
+                ("a0", C.c_double), ("tau_fwhm", C.c_double), ("w0_spot", C.c_double),
+                ("t_peak", C.c_double), ("y_c", C.c_double), ("z_c", C.c_double),
+                ("x_src", C.c_int), ("pol", C.c_int),
+                ("seed", C.c_uint32), ("tile", C.c_int),
+                ("stream", C.c_void_p), ("arena_dev", C.c_void_p), ("arena_bytes", C.c_size_t)]
+
+
+class hyb_species_desc(C.Structure):
+    _fields_ = [("q", C.c_double), ("m", C.c_double), ("n", C.c_longlong),
+                ("tile_capacity", C.c_longlong), ("ptr_on_device", C.c_int),
+                ("x", C.c_void_p), ("y", C.c_void_p), ("z", C.c_void_p),
+                ("ux", C.c_void_p), ("uy", C.c_void_p), ("uz", C.c_void_p), ("w", C.c_void_p),
+                ("zq", C.c_void_p), ("ids", C.c_void_p)]
+
+
+class hyb_diag(C.Structure):
+    _fields_ = [("step", C.c_longlong), ("time", C.c_double),
+                ("w_e", C.c_double), ("w_b", C.c_double),
+                ("w_kin", C.c_double * HYB_MAX_SPECIES),
+                ("count", C.c_longlong * HYB_MAX_SPECIES),
+                ("n_species", C.c_int), ("status", C.c_int),
+                ("launches_per_step", C.c_longlong)]
+
+
+HYB_NPHASE = 8
+PHASES = ["push", "j_reduce", "source", "rebin", "field", "ph5", "ph6", "ph7"]
+
+
+class hyb_phase_times_t(C.Structure):
+    _fields_ = [("ms", C.c_float * HYB_NPHASE)]
+
+
+_P = C.c_void_p
+_ctx = C.c_void_p
+
+# name -> (restype, argtypes)
+PROTOTYPES = {
+    "hyb_init_grid": (C.c_int, [C.POINTER(hyb_grid_desc), C.POINTER(C.c_void_p)]),
+    "hyb_destroy": (None, [_ctx]),
+    "hyb_load_species": (C.c_int, [_ctx, C.POINTER(hyb_species_desc), C.POINTER(C.c_int)]),
+    "hyb_set_fields": (C.c_int, [_ctx, _P, _P, C.c_int]),
+    "hyb_step": (C.c_int, [_ctx, C.c_int]),
+    "hyb_diagnostics": (C.c_int, [_ctx, C.POINTER(hyb_diag)]),
+    "hyb_get_fields": (C.c_int, [_ctx, _P, _P, _P]),
+    "hyb_get_species": (C.c_int, [_ctx, C.c_int, C.c_longlong] + [_P] * 9 + [C.POINTER(C.c_longlong)]),
+    "hyb_clear_status": (C.c_int, [_ctx]),
+    "hyb_last_error": (C.c_char_p, []),
+    "hyb_set_profiling": (C.c_int, [_ctx, C.c_int]),
+    "hyb_phase_times": (C.c_int, [_ctx, C.POINTER(hyb_phase_times_t)]),
+}
+
+_lib = None
+
+
+def load():
+    """Load libhyb.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libhyb.so is not built (run paper_2510_11174_gb300/build.py); "
+                               "there is no CPU fallback")
+        lib = C.CDLL(LIB_PATH)
+        for name, (res, args) in PROTOTYPES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+class HybError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(code, code), msg))
+        self.code = code
+
+
+def check(code):
+    if code != HYB_OK:
+        raise HybError(code, load().hyb_last_error().decode())
+    return code

@@ -1,0 +1,600 @@
+// C ABI of the hybrid fluid-kinetic step: context creation, species loading,
+// the step sequence (captured once into a CUDA graph and replayed), and the
+// synchronising read-back calls.  See include/hyb.h for the contract.
+//
+// Step order (arXiv 2510.11174, Methodology: time loop of laser excitation,
+// ionization, particle movement, fluid changes and field modification):
+//   1. push + gather + Esirkepov deposit of every species (J^{n+1/2})
+//   2. assemble J from the tile frames; add the laser source current
+//   3. re-insert particles that changed tile; compact vacated slots
+//   4. B half step, E full step with J, Mur faces, B half step
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "hyb_internal.cuh"
+
+namespace hyb {
+
+static thread_local std::string g_err = "no error";
+
+hyb_status set_error(hyb_status s, const std::string &msg) {
+    g_err = msg;
+    return s;
+}
+
+cudaError_t ctx_alloc(hyb_ctx *c, void **p, size_t bytes) {
+    bytes = (bytes + 255) & ~(size_t)255;
+    if (bytes == 0) bytes = 256;
+    if (c->arena.base) {
+        if (c->arena.used + bytes > c->arena.size) return cudaErrorMemoryAllocation;
+        *p = c->arena.base + c->arena.used;
+        c->arena.used += bytes;
+        return cudaSuccess;
+    }
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaSuccess) c->owned.push_back(*p);
+    return e;
+}
+
+static SpSet species_set(const hyb_ctx *c) {
+    SpSet s;
+    memset(&s, 0, sizeof(s));
+    s.n = (int)c->sp.size();
+    for (int i = 0; i < s.n; ++i) s.s[i] = c->sp[i].dev;
+    return s;
+}
+
+static hyb_status status_to_code(int st) {
+    if (st & ST_OVERFLOW) return HYB_EOVERFLOW;
+    if (st & ST_NAN) return HYB_ENAN;
+    if (st & ST_TIMEOUT) return HYB_ETIMEOUT;
+    if (st & ST_BADPOS) return HYB_EINVAL;
+    return HYB_OK;
+}
+
+// phase boundary markers (event records captured into the step graph)
+struct PhaseMark {
+    hyb_ctx *c;
+    void begin(int ph) {
+        c->phase_ran[ph] = true;
+        if (c->profiling) cudaEventRecord(c->ev_start[ph], c->stream);
+    }
+    void end(int ph) {
+        if (c->profiling) cudaEventRecord(c->ev_end[ph], c->stream);
+    }
+};
+
+// Enqueue one full step on the context stream.
+static void enqueue_step(hyb_ctx *c) {
+    const GridDev &g = c->g;
+    cudaStream_t st = c->stream;
+    const SpSet set = species_set(c);
+    PhaseMark pm{c};
+    for (int p = 0; p < HYB_NPHASE; ++p) c->phase_ran[p] = false;
+    cudaMemsetAsync(c->mig_counts, 0, sizeof(int) * HYB_MAX_SPECIES, st);
+    if (set.n > 0) {
+        pm.begin(HYB_PH_PUSH);
+        launch_push_deposit(g, c->E, c->B, set, c->jscratch, c->status, st);
+        pm.end(HYB_PH_PUSH);
+        pm.begin(HYB_PH_JREDUCE);
+        launch_j_reduce(g, c->jscratch, c->J, st);
+        pm.end(HYB_PH_JREDUCE);
+    } else {
+        cudaMemsetAsync(c->J, 0, sizeof(float) * 3 * g.N, st);
+    }
+    if (c->desc.laser_kind == HYB_LASER_GAUSS) {
+        pm.begin(HYB_PH_SOURCE);
+        launch_laser_source(g, c->desc, c->laser_profile, c->step_dev, c->J, st);
+        pm.end(HYB_PH_SOURCE);
+    }
+    if (set.n > 0) {
+        pm.begin(HYB_PH_REBIN);
+        for (int s = 0; s < set.n; ++s) {
+            launch_rebin(g, set.s[s], c->status, st);
+            launch_compact(g, set.s[s], st);
+        }
+        pm.end(HYB_PH_REBIN);
+    }
+    pm.begin(HYB_PH_FIELD);
+    launch_fdtd_b_half(g, c->E, c->B, st);
+    launch_fdtd_e(g, c->E, c->B, c->J, st);
+    launch_mur(g, c->E, c->mur_old, c->mur_plane, st);
+    launch_fdtd_b_half(g, c->E, c->B, st);
+    pm.end(HYB_PH_FIELD);
+    launch_step_inc(c->step_dev, st);
+
+    // kernels enqueued above (memsets and event records are not kernels)
+    long long k = 0;
+    if (set.n > 0) k += 2 + 2LL * set.n;
+    if (c->desc.laser_kind == HYB_LASER_GAUSS) k += 1;
+    k += 3 + ((g.bc[0] || g.bc[1] || g.bc[2]) ? 3 : 0) + 1;
+    c->launches_per_step = k;
+}
+
+}  // namespace hyb
+
+using namespace hyb;
+
+extern "C" {
+
+const char *hyb_last_error(void) { return g_err.c_str(); }
+
+hyb_status hyb_init_grid(const hyb_grid_desc *d, hyb_ctx **out) {
+    if (!d || !out) return set_error(HYB_EINVAL, "null descriptor or output");
+    *out = nullptr;
+    const int n[3] = {d->nx, d->ny, d->nz};
+    const double dd[3] = {d->dx, d->dy, d->dz};
+    const int T = d->tile == 0 ? 8 : d->tile;
+    if (T != 4 && T != 8) return set_error(HYB_EINVAL, "tile must be 4 or 8");
+    for (int a = 0; a < 3; ++a) {
+        if (n[a] <= 0 || n[a] % T != 0)
+            return set_error(HYB_EINVAL, "grid size must be a positive multiple of the tile edge");
+        if (!(dd[a] > 0.0)) return set_error(HYB_EINVAL, "cell size must be positive");
+        if (d->bc[a] != HYB_BC_PERIODIC && d->bc[a] != HYB_BC_MUR) return set_error(HYB_EINVAL, "bad boundary");
+        if (d->bc[a] == HYB_BC_MUR && n[a] < 4) return set_error(HYB_EINVAL, "Mur axis needs >= 4 nodes");
+    }
+    const double courant = 1.0 / std::sqrt(1.0 / (dd[0] * dd[0]) + 1.0 / (dd[1] * dd[1]) + 1.0 / (dd[2] * dd[2]));
+    double dt = d->dt;
+    if (!(dt > 0.0)) {
+        if (!(d->cfl_frac > 0.0 && d->cfl_frac < 1.0)) return set_error(HYB_EINVAL, "need dt or cfl_frac in (0,1)");
+        dt = d->cfl_frac * courant;
+    }
+    if (dt >= courant) return set_error(HYB_EINVAL, "dt at or above the Courant limit");
+    if (d->laser_kind == HYB_LASER_GAUSS) {
+        if (d->x_src < 0 || d->x_src >= n[0]) return set_error(HYB_EINVAL, "laser x_src outside the grid");
+        if (d->pol != 1 && d->pol != 2) return set_error(HYB_EINVAL, "laser pol must be 1 (y) or 2 (z)");
+        if (!(d->tau_fwhm > 0.0) || !(d->w0_spot > 0.0)) return set_error(HYB_EINVAL, "laser tau and w0 must be > 0");
+    } else if (d->laser_kind != HYB_LASER_NONE) {
+        return set_error(HYB_EINVAL, "bad laser kind");
+    }
+
+    hyb_ctx *c = new hyb_ctx();
+    c->desc = *d;
+    c->desc.dt = dt;
+    c->desc.tile = T;
+    GridDev &g = c->g;
+    for (int a = 0; a < 3; ++a) {
+        g.n[a] = n[a];
+        g.bc[a] = d->bc[a];
+        g.nt[a] = n[a] / T;
+        g.d[a] = (float)dd[a];
+        g.dd[a] = dd[a];
+    }
+    g.T = T;
+    g.ntiles = g.nt[0] * g.nt[1] * g.nt[2];
+    g.N = (long long)n[0] * n[1] * n[2];
+    g.dt = (float)dt;
+    g.dt_d = dt;
+
+    if (d->stream) {
+        c->stream = (cudaStream_t)d->stream;
+    } else {
+        cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            delete c;
+            return set_error(HYB_ECUDA, std::string("stream create: ") + cudaGetErrorString(e));
+        }
+        c->own_stream = true;
+    }
+    if (d->arena_dev) {
+        c->arena.base = (char *)d->arena_dev;
+        c->arena.size = d->arena_bytes;
+    }
+
+    auto fail = [&](hyb_status s, const std::string &m) {
+        hyb_destroy(c);
+        return set_error(s, m);
+    };
+    const size_t fbytes = sizeof(float) * 3 * (size_t)g.N;
+    c->mur_plane = std::max({(long long)n[1] * n[2], (long long)n[0] * n[2], (long long)n[0] * n[1]});
+    const int G = T + 3;
+    c->jframe = 3LL * G * G * G;
+    c->red_blocks = 152 * 2;
+    if (ctx_alloc(c, (void **)&c->E, fbytes) || ctx_alloc(c, (void **)&c->B, fbytes) ||
+        ctx_alloc(c, (void **)&c->J, fbytes) ||
+        ctx_alloc(c, (void **)&c->mur_old, sizeof(float) * 24 * (size_t)c->mur_plane) ||
+        ctx_alloc(c, (void **)&c->jscratch, sizeof(float) * (size_t)c->jframe * g.ntiles) ||
+        ctx_alloc(c, (void **)&c->red_partials, sizeof(double) * (2 + HYB_MAX_SPECIES) * c->red_blocks) ||
+        ctx_alloc(c, (void **)&c->red_out, sizeof(double) * (2 + HYB_MAX_SPECIES)) ||
+        ctx_alloc(c, (void **)&c->status, sizeof(int)) || ctx_alloc(c, (void **)&c->step_dev, sizeof(long long)) ||
+        ctx_alloc(c, (void **)&c->mig_counts, sizeof(int) * HYB_MAX_SPECIES))
+        return fail(HYB_ENOMEM, "device allocation for the grid failed (arena too small?)");
+    cudaStream_t st = c->stream;
+    cudaMemsetAsync(c->E, 0, fbytes, st);
+    cudaMemsetAsync(c->B, 0, fbytes, st);
+    cudaMemsetAsync(c->J, 0, fbytes, st);
+    cudaMemsetAsync(c->mur_old, 0, sizeof(float) * 24 * (size_t)c->mur_plane, st);
+    cudaMemsetAsync(c->status, 0, sizeof(int), st);
+    cudaMemsetAsync(c->step_dev, 0, sizeof(long long), st);
+
+    if (d->laser_kind == HYB_LASER_GAUSS) {
+        // transverse profile f = exp(-r^2 / w0^2) at the J_pol positions of the source plane, FP64
+        std::vector<float> prof((size_t)n[1] * n[2]);
+        for (int k = 0; k < n[2]; ++k)
+            for (int j = 0; j < n[1]; ++j) {
+                const double y = (j + (d->pol == 1 ? 0.5 : 0.0) - d->y_c) * dd[1];
+                const double z = (k + (d->pol == 2 ? 0.5 : 0.0) - d->z_c) * dd[2];
+                prof[(size_t)k * n[1] + j] = (float)std::exp(-(y * y + z * z) / (d->w0_spot * d->w0_spot));
+            }
+        if (ctx_alloc(c, (void **)&c->laser_profile, sizeof(float) * prof.size()))
+            return fail(HYB_ENOMEM, "laser profile allocation failed");
+        cudaError_t e = cudaMemcpyAsync(c->laser_profile, prof.data(), sizeof(float) * prof.size(),
+                                        cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return fail(HYB_ECUDA, std::string("laser profile upload: ") + cudaGetErrorString(e));
+    }
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail(HYB_ECUDA, std::string("init: ") + cudaGetErrorString(e));
+    *out = c;
+    return HYB_OK;
+}
+
+void hyb_destroy(hyb_ctx *c) {
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    for (int p = 0; p < HYB_NPHASE; ++p) {
+        if (c->ev_start[p]) cudaEventDestroy(c->ev_start[p]);
+        if (c->ev_end[p]) cudaEventDestroy(c->ev_end[p]);
+    }
+    for (void *p : c->owned) cudaFree(p);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+static hyb_status alloc_species(hyb_ctx *c, Species &sp, int cap, bool has_zq) {
+    const GridDev &g = c->g;
+    const size_t slots = (size_t)cap * g.ntiles;
+    SpDev &s = sp.dev;
+    memset(&s, 0, sizeof(s));
+    s.cap = cap;
+    s.q = (float)sp.q;
+    s.m = (float)sp.m;
+    float **fl[7] = {&s.x, &s.y, &s.z, &s.ux, &s.uy, &s.uz, &s.w};
+    for (auto f : fl)
+        if (ctx_alloc(c, (void **)f, sizeof(float) * slots)) return HYB_ENOMEM;
+    if (has_zq && ctx_alloc(c, (void **)&s.zq, sizeof(float) * slots)) return HYB_ENOMEM;
+    if (ctx_alloc(c, (void **)&s.id, sizeof(uint64_t) * slots)) return HYB_ENOMEM;
+    if (ctx_alloc(c, (void **)&s.count, sizeof(int) * g.ntiles) ||
+        ctx_alloc(c, (void **)&s.hole_count, sizeof(int) * g.ntiles) ||
+        ctx_alloc(c, (void **)&s.hole_used, sizeof(int) * g.ntiles) ||
+        ctx_alloc(c, (void **)&s.holes, sizeof(int) * slots))
+        return HYB_ENOMEM;
+    // a particle moves less than one cell per step, so only the shell of a tile can leave it
+    const long long mig = std::min<long long>((long long)slots, std::max<long long>(65536, (long long)slots * 3 / 4));
+    s.mig_cap = (int)std::min<long long>(mig, 0x7fffffffLL);
+    float **ml[7] = {&s.mx, &s.my, &s.mz, &s.mux, &s.muy, &s.muz, &s.mw};
+    for (auto f : ml)
+        if (ctx_alloc(c, (void **)f, sizeof(float) * s.mig_cap)) return HYB_ENOMEM;
+    if (has_zq && ctx_alloc(c, (void **)&s.mzq, sizeof(float) * s.mig_cap)) return HYB_ENOMEM;
+    if (ctx_alloc(c, (void **)&s.mid, sizeof(uint64_t) * s.mig_cap) ||
+        ctx_alloc(c, (void **)&s.mdest, sizeof(int) * s.mig_cap))
+        return HYB_ENOMEM;
+    s.mig_count = c->mig_counts + c->sp.size();
+    cudaMemsetAsync(s.count, 0, sizeof(int) * g.ntiles, c->stream);
+    cudaMemsetAsync(s.hole_count, 0, sizeof(int) * g.ntiles, c->stream);
+    cudaMemsetAsync(s.hole_used, 0, sizeof(int) * g.ntiles, c->stream);
+    return HYB_OK;
+}
+
+hyb_status hyb_load_species(hyb_ctx *c, const hyb_species_desc *d, int *species_id) {
+    if (!c || !d || !species_id) return set_error(HYB_EINVAL, "null argument");
+    if ((int)c->sp.size() >= HYB_MAX_SPECIES) return set_error(HYB_EINVAL, "too many species");
+    if (!(d->m > 0.0)) return set_error(HYB_EINVAL, "species mass must be > 0");
+    if (d->n < 0) return set_error(HYB_EINVAL, "negative particle count");
+    if (d->n > 0 && (!d->x || !d->y || !d->z || !d->ux || !d->uy || !d->uz || !d->w))
+        return set_error(HYB_EINVAL, "missing particle arrays");
+    const GridDev &g = c->g;
+    cudaStream_t st = c->stream;
+    const long long n = d->n;
+
+    // positions must lie inside the domain
+    // (checked on the device copy below through the tile counts: out-of-range positions are clamped
+    // into the edge tiles by tile_index, so validate on the host when the arrays are host memory)
+    if (!d->ptr_on_device) {
+        for (long long p = 0; p < n; ++p) {
+            const float v[3] = {d->x[p], d->y[p], d->z[p]};
+            for (int a = 0; a < 3; ++a) {
+                const float hi = g.bc[a] ? (float)(g.n[a] - 1) : (float)g.n[a];
+                if (!(v[a] >= 0.0f) || v[a] > hi || (g.bc[a] == 0 && v[a] >= hi))
+                    return set_error(HYB_EINVAL, "particle position outside the domain");
+            }
+        }
+    }
+
+    // stage arrays on the device (temporary)
+    size_t arena_mark = c->arena.used;
+    std::vector<void *> tmp;
+    auto talloc = [&](void **p, size_t b) -> bool {
+        if (c->arena.base) return ctx_alloc(c, p, b) == cudaSuccess;
+        if (cudaMalloc(p, b ? b : 256) != cudaSuccess) return false;
+        tmp.push_back(*p);
+        return true;
+    };
+    auto cleanup = [&]() {
+        cudaStreamSynchronize(st);
+        for (void *p : tmp) cudaFree(p);
+        if (c->arena.base) c->arena.used = arena_mark;
+    };
+    const float *src[8] = {d->x, d->y, d->z, d->ux, d->uy, d->uz, d->w, d->zq};
+    const float *dsrc[8] = {nullptr};
+    const uint64_t *dids = nullptr;
+    int *counts = nullptr;
+    bool ok = talloc((void **)&counts, sizeof(int) * g.ntiles);
+    for (int k = 0; ok && k < 8; ++k) {
+        if (!src[k]) continue;
+        if (d->ptr_on_device) {
+            dsrc[k] = src[k];
+        } else {
+            float *p = nullptr;
+            ok = talloc((void **)&p, sizeof(float) * n);
+            if (ok) ok = cudaMemcpyAsync(p, src[k], sizeof(float) * n, cudaMemcpyHostToDevice, st) == cudaSuccess;
+            dsrc[k] = p;
+        }
+    }
+    if (ok && d->ids) {
+        if (d->ptr_on_device) {
+            dids = d->ids;
+        } else {
+            uint64_t *p = nullptr;
+            ok = talloc((void **)&p, sizeof(uint64_t) * n);
+            if (ok) ok = cudaMemcpyAsync(p, d->ids, sizeof(uint64_t) * n, cudaMemcpyHostToDevice, st) == cudaSuccess;
+            dids = p;
+        }
+    }
+    if (!ok) {
+        cleanup();
+        return set_error(HYB_ENOMEM, "staging allocation/copy for species failed");
+    }
+    cudaMemsetAsync(counts, 0, sizeof(int) * g.ntiles, st);
+    launch_count_tiles(g, n, dsrc[0], dsrc[1], dsrc[2], counts, st);
+    std::vector<int> hcounts(g.ntiles);
+    cudaMemcpyAsync(hcounts.data(), counts, sizeof(int) * g.ntiles, cudaMemcpyDeviceToHost, st);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        cleanup();
+        return set_error(HYB_ECUDA, std::string("species count: ") + cudaGetErrorString(e));
+    }
+    int maxc = 0;
+    for (int v : hcounts) maxc = std::max(maxc, v);
+    long long cap = d->tile_capacity > 0 ? d->tile_capacity : 2LL * maxc + 64;
+    cap = (cap + 31) / 32 * 32;
+    if (cap < maxc) {
+        cleanup();
+        return set_error(HYB_EOVERFLOW, "tile_capacity below the initial count of a tile");
+    }
+    if (cap > 0x7fffffffLL / 2) {
+        cleanup();
+        return set_error(HYB_EINVAL, "tile capacity too large");
+    }
+
+    // the species buffers must outlive the staging area: allocate them after
+    // releasing it when an arena is used (the bump allocator is LIFO)
+    if (c->arena.base) {
+        // move staging out of the way: copy counts were read; re-stage after allocation
+    }
+    Species sp;
+    sp.q = d->q;
+    sp.m = d->m;
+    sp.has_zq = d->zq != nullptr;
+    sp.cap = (int)cap;
+    if (c->arena.base) {
+        // release staging, allocate species, then stage again on top
+        cleanup();
+        tmp.clear();
+        if (alloc_species(c, sp, (int)cap, sp.has_zq) != HYB_OK)
+            return set_error(HYB_ENOMEM, "species allocation failed (arena too small?)");
+        arena_mark = c->arena.used;
+        ok = true;
+        for (int k = 0; ok && k < 8; ++k) {
+            if (!src[k] || d->ptr_on_device) continue;
+            float *p = nullptr;
+            ok = talloc((void **)&p, sizeof(float) * n);
+            if (ok) ok = cudaMemcpyAsync(p, src[k], sizeof(float) * n, cudaMemcpyHostToDevice, st) == cudaSuccess;
+            dsrc[k] = p;
+        }
+        if (ok && d->ids && !d->ptr_on_device) {
+            uint64_t *p = nullptr;
+            ok = talloc((void **)&p, sizeof(uint64_t) * n);
+            if (ok) ok = cudaMemcpyAsync(p, d->ids, sizeof(uint64_t) * n, cudaMemcpyHostToDevice, st) == cudaSuccess;
+            dids = p;
+        }
+        if (!ok) {
+            cleanup();
+            return set_error(HYB_ENOMEM, "staging allocation for species failed (arena too small?)");
+        }
+    } else if (alloc_species(c, sp, (int)cap, sp.has_zq) != HYB_OK) {
+        cleanup();
+        return set_error(HYB_ENOMEM, "species allocation failed");
+    }
+    launch_bin_particles(g, sp.dev, n, dsrc[0], dsrc[1], dsrc[2], dsrc[3], dsrc[4], dsrc[5], dsrc[6], dsrc[7], dids,
+                         c->status, st);
+    int hstatus = 0;
+    cudaMemcpyAsync(&hstatus, c->status, sizeof(int), cudaMemcpyDeviceToHost, st);
+    e = cudaStreamSynchronize(st);
+    cleanup();
+    if (e != cudaSuccess) return set_error(HYB_ECUDA, std::string("species bin: ") + cudaGetErrorString(e));
+    if (hstatus) {
+        c->error_latched = true;
+        return set_error(status_to_code(hstatus), "particle binning overflowed a tile");
+    }
+    *species_id = (int)c->sp.size();
+    c->sp.push_back(sp);
+    c->graph_valid = false;
+    return HYB_OK;
+}
+
+hyb_status hyb_set_fields(hyb_ctx *c, const float *E, const float *B, int on_device) {
+    if (!c || !E || !B) return set_error(HYB_EINVAL, "null argument");
+    const size_t fbytes = sizeof(float) * 3 * (size_t)c->g.N;
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    HYB_CUDA_TRY(cudaMemcpyAsync(c->E, E, fbytes, kind, c->stream));
+    HYB_CUDA_TRY(cudaMemcpyAsync(c->B, B, fbytes, kind, c->stream));
+    launch_mur_save(c->g, c->E, c->mur_old, c->mur_plane, c->stream);
+    HYB_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return HYB_OK;
+}
+
+hyb_status hyb_step(hyb_ctx *c, int nsteps) {
+    if (!c || nsteps < 0) return set_error(HYB_EINVAL, "bad argument");
+    if (c->error_latched) return set_error(HYB_ESTATE, "context is in an error state (hyb_clear_status)");
+    if (nsteps == 0) return HYB_OK;
+    if (!c->graph_valid) {
+        if (c->graph) {
+            cudaGraphExecDestroy(c->graph);
+            c->graph = nullptr;
+        }
+        cudaGraph_t graph;
+        HYB_CUDA_TRY(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+        enqueue_step(c);
+        HYB_CUDA_TRY(cudaStreamEndCapture(c->stream, &graph));
+        cudaError_t e = cudaGraphInstantiate(&c->graph, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return set_error(HYB_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+        c->graph_valid = true;
+    }
+    for (int i = 0; i < nsteps; ++i) HYB_CUDA_TRY(cudaGraphLaunch(c->graph, c->stream));
+    c->step += nsteps;
+    return HYB_OK;
+}
+
+hyb_status hyb_set_profiling(hyb_ctx *c, int on) {
+    if (!c) return set_error(HYB_EINVAL, "null context");
+    if (on) {
+        for (int p = 0; p < HYB_NPHASE; ++p) {
+            if (!c->ev_start[p]) HYB_CUDA_TRY(cudaEventCreate(&c->ev_start[p]));
+            if (!c->ev_end[p]) HYB_CUDA_TRY(cudaEventCreate(&c->ev_end[p]));
+        }
+    }
+    if ((bool)on != c->profiling) {
+        c->profiling = on != 0;
+        c->graph_valid = false;
+    }
+    return HYB_OK;
+}
+
+hyb_status hyb_phase_times(hyb_ctx *c, hyb_phase_times_t *out) {
+    if (!c || !out) return set_error(HYB_EINVAL, "null argument");
+    if (!c->profiling) return set_error(HYB_ESTATE, "profiling is off");
+    HYB_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    for (int p = 0; p < HYB_NPHASE; ++p) {
+        out->ms[p] = 0.0f;
+        if (!c->phase_ran[p] || c->step == 0) continue;
+        HYB_CUDA_TRY(cudaEventElapsedTime(&out->ms[p], c->ev_start[p], c->ev_end[p]));
+    }
+    return HYB_OK;
+}
+
+hyb_status hyb_clear_status(hyb_ctx *c) {
+    if (!c) return set_error(HYB_EINVAL, "null context");
+    HYB_CUDA_TRY(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream));
+    HYB_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    c->error_latched = false;
+    return HYB_OK;
+}
+
+static hyb_status read_status(hyb_ctx *c) {
+    int h = 0;
+    HYB_CUDA_TRY(cudaMemcpyAsync(&h, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    HYB_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if (h) {
+        c->error_latched = true;
+        return set_error(status_to_code(h), "device status word set");
+    }
+    return HYB_OK;
+}
+
+hyb_status hyb_diagnostics(hyb_ctx *c, hyb_diag *out) {
+    if (!c || !out) return set_error(HYB_EINVAL, "null argument");
+    memset(out, 0, sizeof(*out));
+    const SpSet set = species_set(c);
+    launch_energy(c->g, c->E, c->B, set, c->red_partials, c->red_blocks, c->red_out, c->status, c->stream);
+    double r[2 + HYB_MAX_SPECIES];
+    HYB_CUDA_TRY(cudaMemcpyAsync(r, c->red_out, sizeof(double) * (2 + set.n), cudaMemcpyDeviceToHost, c->stream));
+    int h = 0;
+    HYB_CUDA_TRY(cudaMemcpyAsync(&h, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    std::vector<int> cnt((size_t)c->g.ntiles);
+    out->n_species = set.n;
+    for (int s = 0; s < set.n; ++s) {
+        HYB_CUDA_TRY(cudaMemcpyAsync(cnt.data(), set.s[s].count, sizeof(int) * cnt.size(), cudaMemcpyDeviceToHost,
+                                     c->stream));
+        HYB_CUDA_TRY(cudaStreamSynchronize(c->stream));
+        long long tot = 0;
+        for (int v : cnt) tot += std::min(v, set.s[s].cap);
+        out->count[s] = tot;
+    }
+    HYB_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    out->step = c->step;
+    out->time = c->step * c->g.dt_d;
+    out->w_e = r[0];
+    out->w_b = r[1];
+    for (int s = 0; s < set.n; ++s) out->w_kin[s] = r[2 + s];
+    out->status = status_to_code(h);
+    out->launches_per_step = c->launches_per_step;
+    if (h) {
+        c->error_latched = true;
+        return set_error(status_to_code(h), "device status word set");
+    }
+    return HYB_OK;
+}
+
+hyb_status hyb_get_fields(hyb_ctx *c, float *E, float *B, float *J) {
+    if (!c) return set_error(HYB_EINVAL, "null context");
+    const size_t fbytes = sizeof(float) * 3 * (size_t)c->g.N;
+    if (E) HYB_CUDA_TRY(cudaMemcpyAsync(E, c->E, fbytes, cudaMemcpyDeviceToHost, c->stream));
+    if (B) HYB_CUDA_TRY(cudaMemcpyAsync(B, c->B, fbytes, cudaMemcpyDeviceToHost, c->stream));
+    if (J) HYB_CUDA_TRY(cudaMemcpyAsync(J, c->J, fbytes, cudaMemcpyDeviceToHost, c->stream));
+    HYB_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return HYB_OK;
+}
+
+hyb_status hyb_get_species(hyb_ctx *c, int sid, long long max_n, float *x, float *y, float *z, float *ux, float *uy,
+                           float *uz, float *w, float *zq, uint64_t *ids, long long *n_out) {
+    if (!c || sid < 0 || sid >= (int)c->sp.size() || !n_out) return set_error(HYB_EINVAL, "bad argument");
+    const Species &sp = c->sp[sid];
+    const GridDev &g = c->g;
+    std::vector<int> cnt((size_t)g.ntiles);
+    HYB_CUDA_TRY(cudaMemcpyAsync(cnt.data(), sp.dev.count, sizeof(int) * cnt.size(), cudaMemcpyDeviceToHost,
+                                 c->stream));
+    HYB_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    long long tot = 0;
+    for (int &v : cnt) {
+        v = std::min(v, sp.cap);
+        tot += v;
+    }
+    *n_out = tot;
+    if (tot > max_n) return set_error(HYB_EINVAL, "output arrays too small");
+    // whole slabs are copied to the host and compacted there
+    const size_t slots = (size_t)sp.cap * g.ntiles;
+    std::vector<float> buf(slots);
+    std::vector<uint64_t> ibuf;
+    float *dst[8] = {x, y, z, ux, uy, uz, w, zq};
+    const float *srcs[8] = {sp.dev.x, sp.dev.y, sp.dev.z, sp.dev.ux, sp.dev.uy, sp.dev.uz, sp.dev.w, sp.dev.zq};
+    for (int k = 0; k < 8; ++k) {
+        if (!dst[k] || !srcs[k]) continue;
+        HYB_CUDA_TRY(cudaMemcpyAsync(buf.data(), srcs[k], sizeof(float) * slots, cudaMemcpyDeviceToHost, c->stream));
+        HYB_CUDA_TRY(cudaStreamSynchronize(c->stream));
+        long long o = 0;
+        for (int t = 0; t < g.ntiles; ++t) {
+            std::memcpy(dst[k] + o, buf.data() + (size_t)t * sp.cap, sizeof(float) * cnt[t]);
+            o += cnt[t];
+        }
+    }
+    if (ids) {
+        ibuf.resize(slots);
+        HYB_CUDA_TRY(cudaMemcpyAsync(ibuf.data(), sp.dev.id, sizeof(uint64_t) * slots, cudaMemcpyDeviceToHost,
+                                     c->stream));
+        HYB_CUDA_TRY(cudaStreamSynchronize(c->stream));
+        long long o = 0;
+        for (int t = 0; t < g.ntiles; ++t) {
+            std::memcpy(ids + o, ibuf.data() + (size_t)t * sp.cap, sizeof(uint64_t) * cnt[t]);
+            o += cnt[t];
+        }
+    }
+    return read_status(c);
+}
+
+}  // extern "C"

@@ -1,0 +1,88 @@
+// FP64 energy reductions (arXiv 2510.11174, Methodology: total energy from
+// electromagnetic, kinetic and thermal components; conservation checks during
+// steps).  Field energy (1/2) sum (E^2 + B^2) dV and particle kinetic energy
+// sum w m (gamma - 1), both in units m_e c^2 n_c (c/w0)^3.
+//
+// Deterministic two-pass reduction: a fixed grid of blocks accumulates FP64
+// per-thread sums in a fixed grid-stride order, reduces them with a fixed
+// shared-memory tree and writes one partial per block into a scratch array;
+// a single block then sums the partials of each quantity in block order.
+#include "hyb_internal.cuh"
+
+namespace hyb {
+
+static constexpr int RB = 256;  // threads per reduction block
+
+__device__ __forceinline__ double block_sum(double v, double *sh) {
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int s = RB / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+        __syncthreads();
+    }
+    const double r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(RB) k_energy_fields(GridDev g, const float *__restrict__ E,
+                                                      const float *__restrict__ B, double *__restrict__ partials,
+                                                      int nblocks, int *__restrict__ status) {
+    __shared__ double sh[RB];
+    double se = 0.0, sb = 0.0;
+    bool finite = true;
+    const long long n3 = 3 * g.N;
+    for (long long c = blockIdx.x * (long long)RB + threadIdx.x; c < n3; c += (long long)nblocks * RB) {
+        const double e = E[c], b = B[c];
+        finite = finite && isfinite(e) && isfinite(b);
+        se += e * e;
+        sb += b * b;
+    }
+    if (!finite) atomicOr(status, ST_NAN);
+    se = block_sum(se, sh);
+    sb = block_sum(sb, sh);
+    if (threadIdx.x == 0) {
+        partials[blockIdx.x] = se;
+        partials[nblocks + blockIdx.x] = sb;
+    }
+}
+
+// m (gamma - 1) written as m u^2 / (gamma + 1) (no cancellation for slow particles)
+__global__ void __launch_bounds__(RB) k_energy_species(GridDev g, SpDev sp, double *__restrict__ partials,
+                                                       int nblocks) {
+    __shared__ double sh[RB];
+    double acc = 0.0;
+    for (int t = blockIdx.x; t < g.ntiles; t += nblocks) {
+        const int n = min(sp.count[t], sp.cap);
+        const long long base = (long long)t * sp.cap;
+        for (int p = threadIdx.x; p < n; p += RB) {
+            const double ux = sp.ux[base + p], uy = sp.uy[base + p], uz = sp.uz[base + p];
+            const double u2 = ux * ux + uy * uy + uz * uz;
+            acc += (double)sp.w[base + p] * (double)sp.m * u2 / (sqrt(1.0 + u2) + 1.0);
+        }
+    }
+    acc = block_sum(acc, sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+}
+
+__global__ void __launch_bounds__(RB) k_final(const double *__restrict__ partials, int nq, int nblocks,
+                                              double dvol_half, double *__restrict__ out) {
+    __shared__ double sh[RB];
+    for (int q = 0; q < nq; ++q) {
+        double acc = 0.0;
+        for (int b = threadIdx.x; b < nblocks; b += RB) acc += partials[(long long)q * nblocks + b];
+        acc = block_sum(acc, sh);
+        if (threadIdx.x == 0) out[q] = q < 2 ? acc * dvol_half : acc;
+    }
+}
+
+void launch_energy(const GridDev &g, const float *E, const float *B, const SpSet &set, double *partials,
+                   int nblocks, double *out, int *status, cudaStream_t st) {
+    k_energy_fields<<<nblocks, RB, 0, st>>>(g, E, B, partials, nblocks, status);
+    for (int s = 0; s < set.n; ++s)
+        k_energy_species<<<nblocks, RB, 0, st>>>(g, set.s[s], partials + (long long)(2 + s) * nblocks, nblocks);
+    const double dvol_half = 0.5 * g.dd[0] * g.dd[1] * g.dd[2];
+    k_final<<<1, RB, 0, st>>>(partials, 2 + set.n, nblocks, dvol_half, out);
+}
+
+}  // namespace hyb

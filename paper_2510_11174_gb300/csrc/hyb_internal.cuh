@@ -1,0 +1,163 @@
+// Internal declarations of the hybrid fluid-kinetic step library (arXiv 2510.11174).
+// Shared by the CUDA translation units of libhyb; not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+
+#include "../../include/hyb.h"
+
+namespace hyb {
+
+// ---------------------------------------------------------------- grid view passed to kernels
+// Yee staggering: E_x (i+1/2, j, k), E_y (i, j+1/2, k), E_z (i, j, k+1/2),
+// B_x (i, j+1/2, k+1/2), B_y (i+1/2, j, k+1/2), B_z (i+1/2, j+1/2, k);
+// J with E; index i holds the value at i (integer) or i+1/2 (half-integer).
+// Arrays are component-major: F[c * N + i + nx * (j + ny * k)].
+struct GridDev {
+    int n[3];          // nx, ny, nz
+    int bc[3];         // 0 periodic, 1 Mur / reflecting
+    int T;             // tile edge (cells)
+    int nt[3];         // tiles per axis
+    int ntiles;
+    long long N;       // cells
+    float d[3];        // dx, dy, dz
+    float dt;
+    double dd[3];      // dx, dy, dz in FP64 (reductions)
+    double dt_d;       // the same step in FP64 (laser phase, time)
+};
+
+__host__ __device__ inline long long cidx(const GridDev &g, int i, int j, int k) {
+    return (long long)i + (long long)g.n[0] * ((long long)j + (long long)g.n[1] * (long long)k);
+}
+
+// ---------------------------------------------------------------- particle species on the device
+// SoA FP32 in fixed-capacity tiles: slot s of tile t lives at t * cap + s.
+// x, y, z are cell units; a dead slot (awaiting compaction) has x = -1.
+struct SpDev {
+    float *x, *y, *z, *ux, *uy, *uz, *w, *zq;  // zq may be null
+    uint64_t *id;
+    int *count;        // live slots per tile
+    int *holes;        // per tile: slots vacated by leavers this step
+    int *hole_count, *hole_used;
+    int cap;           // slots per tile
+    float q, m;
+    // migration buffer: particles that left their tile this step
+    float *mx, *my, *mz, *mux, *muy, *muz, *mw, *mzq;
+    uint64_t *mid;
+    int *mdest;
+    int *mig_count;
+    int mig_cap;
+};
+
+struct SpSet {
+    int n;
+    SpDev s[HYB_MAX_SPECIES];
+};
+
+// device status bits (latched; read by the synchronising calls)
+enum : int {
+    ST_OVERFLOW = 1,   // tile or migration capacity exceeded
+    ST_NAN = 2,        // non-finite field value
+    ST_TIMEOUT = 4,
+    ST_BADPOS = 8,     // particle outside its tile or non-finite position (skipped)
+};
+
+// ---------------------------------------------------------------- host-side context
+struct Species {
+    double q, m;
+    int has_zq;
+    int cap;
+    SpDev dev;
+    long long mig_cap;
+};
+
+struct Arena {
+    char *base = nullptr;
+    size_t size = 0, used = 0;
+};
+
+}  // namespace hyb
+
+struct hyb_ctx {
+    hyb_grid_desc desc;
+    hyb::GridDev g;
+    cudaStream_t stream;
+    bool own_stream = false;
+    bool error_latched = false;  // set when a synchronising call saw a device error
+    hyb::Arena arena;
+    std::vector<void *> owned;  // cudaMalloc'd buffers when no arena is given
+
+    float *E = nullptr, *B = nullptr, *J = nullptr;  // 3 * N each
+    float *mur_old = nullptr;                        // saved boundary planes for Mur
+    long long mur_plane = 0;                         // max plane size
+    float *jscratch = nullptr;                       // per-tile J frames
+    long long jframe = 0;                            // floats per tile frame (3 * G^3)
+    double *red_partials = nullptr;                  // FP64 block partials of reductions
+    int red_blocks = 0;
+    double *red_out = nullptr;                       // reduction results
+    int *status = nullptr;                           // device status word
+    long long *step_dev = nullptr;                   // device step counter (read by graph replays)
+    int *mig_counts = nullptr;                       // HYB_MAX_SPECIES migration counters
+
+    std::vector<hyb::Species> sp;
+    long long step = 0;
+
+    cudaGraphExec_t graph = nullptr;
+    bool graph_valid = false;
+
+    // phase profiling: events recorded at the start of every phase and at the end
+    bool profiling = false;
+    cudaEvent_t ev_start[HYB_NPHASE] = {};
+    cudaEvent_t ev_end[HYB_NPHASE] = {};
+    bool phase_ran[HYB_NPHASE] = {};
+    long long launches_per_step = 0;
+
+    // laser transverse profile (FP32, ny*nz) when a Gaussian source is set
+    float *laser_profile = nullptr;
+};
+
+namespace hyb {
+
+// allocation from the caller's arena (bump) or cudaMalloc
+cudaError_t ctx_alloc(hyb_ctx *c, void **p, size_t bytes);
+
+// error plumbing
+hyb_status set_error(hyb_status s, const std::string &msg);
+#define HYB_CUDA_TRY(expr)                                                                   \
+    do {                                                                                     \
+        cudaError_t _e = (expr);                                                             \
+        if (_e != cudaSuccess)                                                               \
+            return ::hyb::set_error(HYB_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(_e)); \
+    } while (0)
+
+// ---------------------------------------------------------------- launchers (one per kernel family)
+void launch_fdtd_b_half(const GridDev &g, const float *E, float *B, cudaStream_t st);
+void launch_fdtd_e(const GridDev &g, float *E, const float *B, const float *J, cudaStream_t st);
+void launch_mur(const GridDev &g, float *E, float *mur_old, long long plane, cudaStream_t st);
+void launch_mur_save(const GridDev &g, const float *E, float *mur_old, long long plane, cudaStream_t st);
+void launch_laser_source(const GridDev &g, const hyb_grid_desc &d, const float *profile,
+                         const long long *step_dev, float *J, cudaStream_t st);
+void launch_step_inc(long long *step_dev, cudaStream_t st);
+
+size_t push_smem_bytes(int T);
+void launch_push_deposit(const GridDev &g, const float *E, const float *B, const SpSet &set,
+                         float *jscratch, int *status, cudaStream_t st);
+void launch_j_reduce(const GridDev &g, const float *jscratch, float *J, cudaStream_t st);
+void launch_rebin(const GridDev &g, const SpDev &s, int *status, cudaStream_t st);
+void launch_compact(const GridDev &g, const SpDev &s, cudaStream_t st);
+void launch_bin_particles(const GridDev &g, const SpDev &s, long long n, const float *x, const float *y,
+                          const float *z, const float *ux, const float *uy, const float *uz,
+                          const float *w, const float *zq, const uint64_t *ids, int *status,
+                          cudaStream_t st);
+void launch_count_tiles(const GridDev &g, long long n, const float *x, const float *y, const float *z,
+                        int *counts, cudaStream_t st);
+
+// FP64 reductions; results written to out[]: [0] = sum E^2 dV / 2, [1] = sum B^2 dV / 2,
+// [2 + s] = kinetic energy of species s; also sets ST_NAN on non-finite fields.
+void launch_energy(const GridDev &g, const float *E, const float *B, const SpSet &set,
+                   double *partials, int nblocks, double *out, int *status, cudaStream_t st);
+
+}  // namespace hyb

@@ -1,0 +1,480 @@
+// Particle-in-cell kernels: CIC field gather on the Yee grid, relativistic Boris
+// push, move with reflecting walls, and charge-conserving Esirkepov current
+// deposition into shared-memory tiles (arXiv 2510.11174, Methodology: PIC
+// macro-particles weighted by density-volume fraction, advanced by the Boris
+// pusher; particles crossing a domain boundary have their velocity reversed;
+// charge conservation is checked at every step).
+//
+// Data layout: particles of a species live in fixed-capacity tiles of T^3
+// cells, SoA FP32 (x, y, z in cell units; u = gamma*beta; weight).  One CTA
+// owns one tile: it stages E and B of the tile plus a one-node halo in shared
+// memory, pushes every particle of every species in the tile, accumulates J in
+// a shared-memory frame of (T+3)^3 nodes (halo 1 below, 2 above, which holds
+// every node an Esirkepov stencil of a particle that started in the tile can
+// touch), and writes that frame to a per-tile scratch slab.  A second kernel
+// sums, for every node, the frames that cover it in a fixed order, so J is
+// assembled without global atomics and bit-reproducibly across tiles.
+// Particles that left their tile are copied to a migration buffer and
+// re-inserted by the rebin kernel; vacated slots are compacted afterwards.
+//
+// Boris (relativistic, Birdsall & Langdon):
+//   u- = u + (q dt/2m) E;  t = (q dt/2m gamma-) B;  s = 2t/(1+t.t)
+//   u' = u- + u- x t;  u+ = u- + u' x s;  u_new = u+ + (q dt/2m) E
+// Esirkepov, CIC shape, on the 3-node window that holds both shapes:
+//   W_x = DS_x (S0_y S0_z + DS_y S0_z/2 + S0_y DS_z/2 + DS_y DS_z/3) (cyclic),
+//   J_x(i+1/2) - J_x(i-1/2) = -q w W_x / (dt dy dz).
+#include "hyb_internal.cuh"
+
+namespace hyb {
+
+__host__ __device__ inline int frame_F(int T) { return T + 2; }  // field frame edge
+__host__ __device__ inline int frame_G(int T) { return T + 3; }  // current frame edge
+
+size_t push_smem_bytes(int T) {
+    const int F = frame_F(T), G = frame_G(T);
+    return sizeof(float) * (6 * (size_t)F * F * F + 3 * (size_t)G * G * G);
+}
+
+__device__ __forceinline__ int tile_of_cell(const GridDev &g, int a, float p) {
+    int c = (int)floorf(p);
+    c = c < 0 ? 0 : (c > g.n[a] - 1 ? g.n[a] - 1 : c);
+    return c / g.T;
+}
+
+__device__ __forceinline__ int tile_index(const GridDev &g, float x, float y, float z) {
+    return tile_of_cell(g, 0, x) + g.nt[0] * (tile_of_cell(g, 1, y) + g.nt[1] * tile_of_cell(g, 2, z));
+}
+
+// CIC weights of one axis for integer and half-integer staggering, relative to
+// the frame origin o (global node index of local 0)
+struct AxisW {
+    int li, lh;     // local base index (integer / half-integer grid)
+    float fi, fh;   // fractional offsets
+};
+
+__device__ __forceinline__ AxisW axis_weights(const GridDev &g, int a, float p, int o) {
+    AxisW r;
+    int i = (int)floorf(p);
+    if (g.bc[a] && i > g.n[a] - 2) i = g.n[a] - 2;  // particle on the top wall
+    r.li = i - o;
+    r.fi = p - (float)i;
+    const float s = p - 0.5f;
+    const int h = (int)floorf(s);
+    r.lh = h - o;
+    r.fh = s - (float)h;
+    return r;
+}
+
+__device__ __forceinline__ float interp8(const float *__restrict__ f, int F, int bx, int by, int bz, float fx,
+                                         float fy, float fz) {
+    float acc = 0.0f;
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        const float wz = c ? fz : 1.0f - fz;
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            const float wy = b ? fy : 1.0f - fy;
+            const float *row = f + ((bz + c) * F + (by + b)) * F + bx;
+            acc += (1.0f - fx) * wy * wz * row[0];
+            acc += fx * wy * wz * row[1];
+        }
+    }
+    return acc;
+}
+
+__device__ __forceinline__ void shape3(float p, int gbase, float S[3]) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float d = fabsf(p - (float)(gbase + k));
+        S[k] = d < 1.0f ? 1.0f - d : 0.0f;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_push_deposit(GridDev g, const float *__restrict__ E,
+                                                      const float *__restrict__ B, SpSet set,
+                                                      float *__restrict__ jscratch, int *__restrict__ status) {
+    extern __shared__ float sm[];
+    const int T = g.T, F = frame_F(T), G = frame_G(T);
+    const int F3 = F * F * F, G3 = G * G * G;
+    float *sf = sm;            // 6 field components, F^3 each
+    float *sj = sm + 6 * F3;   // 3 current components, G^3 each
+    __shared__ int s_holes;
+
+    const int t = blockIdx.x;
+    const int tx = t % g.nt[0], ty = (t / g.nt[0]) % g.nt[1], tz = t / (g.nt[0] * g.nt[1]);
+    const int o[3] = {tx * T - 1, ty * T - 1, tz * T - 1};
+    const long long N = g.N;
+
+    for (int l = threadIdx.x; l < F3; l += blockDim.x) {
+        const int lx = l % F, ly = (l / F) % F, lz = l / (F * F);
+        int gi[3] = {o[0] + lx, o[1] + ly, o[2] + lz};
+        bool in = true;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if (g.bc[a] == 0) {
+                gi[a] = gi[a] < 0 ? gi[a] + g.n[a] : (gi[a] >= g.n[a] ? gi[a] - g.n[a] : gi[a]);
+            } else if (gi[a] < 0 || gi[a] > g.n[a] - 1) {
+                in = false;
+            }
+        }
+        const long long c = in ? cidx(g, gi[0], gi[1], gi[2]) : 0;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            sf[q * F3 + l] = in ? E[q * N + c] : 0.0f;
+            sf[(3 + q) * F3 + l] = in ? B[q * N + c] : 0.0f;
+        }
+    }
+    for (int l = threadIdx.x; l < 3 * G3; l += blockDim.x) sj[l] = 0.0f;
+    if (threadIdx.x == 0) s_holes = 0;
+    __syncthreads();
+
+    const float dt = g.dt;
+    const float dvol[3] = {g.d[1] * g.d[2], g.d[0] * g.d[2], g.d[0] * g.d[1]};
+    const float *sEx = sf, *sEy = sf + F3, *sEz = sf + 2 * F3;
+    const float *sBx = sf + 3 * F3, *sBy = sf + 4 * F3, *sBz = sf + 5 * F3;
+
+    for (int si = 0; si < set.n; ++si) {
+        const SpDev sp = set.s[si];
+        const int n = min(sp.count[t], sp.cap);
+        const long long base = (long long)t * sp.cap;
+        const float qm_half = 0.5f * dt / sp.m;  // times q_p below
+        for (int p0 = 0; p0 < n; p0 += blockDim.x) {
+            const int p = p0 + threadIdx.x;
+            if (p < n) {
+                const long long s = base + p;
+                const float x0[3] = {sp.x[s], sp.y[s], sp.z[s]};
+                float u[3] = {sp.ux[s], sp.uy[s], sp.uz[s]};
+                const float wgt = sp.w[s];
+                const float q = sp.zq ? sp.q * sp.zq[s] : sp.q;
+
+                // every shared-memory index below derives from a cell inside this
+                // tile; anything else is flagged and left untouched
+                bool inside = true;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    int ci = (int)floorf(x0[a]);
+                    if (g.bc[a] && ci == g.n[a] - 1 && x0[a] == (float)(g.n[a] - 1)) ci = g.n[a] - 2;
+                    inside = inside && isfinite(x0[a]) && ci >= o[a] + 1 && ci <= o[a] + T &&
+                             (g.bc[a] == 0 || ci <= g.n[a] - 2);
+                }
+                if (!inside) {
+                    atomicOr(status, ST_BADPOS);
+                    continue;
+                }
+
+                // ---- gather E^n, B^n at x^n
+                const AxisW ax = axis_weights(g, 0, x0[0], o[0]);
+                const AxisW ay = axis_weights(g, 1, x0[1], o[1]);
+                const AxisW az = axis_weights(g, 2, x0[2], o[2]);
+                float e[3], b[3];
+                e[0] = interp8(sEx, F, ax.lh, ay.li, az.li, ax.fh, ay.fi, az.fi);
+                e[1] = interp8(sEy, F, ax.li, ay.lh, az.li, ax.fi, ay.fh, az.fi);
+                e[2] = interp8(sEz, F, ax.li, ay.li, az.lh, ax.fi, ay.fi, az.fh);
+                b[0] = interp8(sBx, F, ax.li, ay.lh, az.lh, ax.fi, ay.fh, az.fh);
+                b[1] = interp8(sBy, F, ax.lh, ay.li, az.lh, ax.fh, ay.fi, az.fh);
+                b[2] = interp8(sBz, F, ax.lh, ay.lh, az.li, ax.fh, ay.fh, az.fi);
+
+                // ---- Boris
+                const float h = q * qm_half;
+                float um[3], tt[3], ss[3], ud[3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) um[c] = u[c] + h * e[c];
+                const float gm = sqrtf(1.0f + um[0] * um[0] + um[1] * um[1] + um[2] * um[2]);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) tt[c] = h * b[c] / gm;
+                const float t2 = tt[0] * tt[0] + tt[1] * tt[1] + tt[2] * tt[2];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) ss[c] = 2.0f * tt[c] / (1.0f + t2);
+                ud[0] = um[0] + (um[1] * tt[2] - um[2] * tt[1]);
+                ud[1] = um[1] + (um[2] * tt[0] - um[0] * tt[2]);
+                ud[2] = um[2] + (um[0] * tt[1] - um[1] * tt[0]);
+                u[0] = um[0] + (ud[1] * ss[2] - ud[2] * ss[1]) + h * e[0];
+                u[1] = um[1] + (ud[2] * ss[0] - ud[0] * ss[2]) + h * e[1];
+                u[2] = um[2] + (ud[0] * ss[1] - ud[1] * ss[0]) + h * e[2];
+
+                // ---- move, reflect at absorbing walls
+                const float gam = sqrtf(1.0f + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+                float x1[3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    x1[a] = x0[a] + dt * u[a] / (gam * g.d[a]);
+                    if (g.bc[a]) {
+                        const float L = (float)(g.n[a] - 1);
+                        if (x1[a] < 0.0f) { x1[a] = -x1[a]; u[a] = -u[a]; }
+                        else if (x1[a] > L) { x1[a] = 2.0f * L - x1[a]; u[a] = -u[a]; }
+                    }
+                }
+
+                bool finite = true;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) finite = finite && isfinite(x1[a]) && fabsf(x1[a] - x0[a]) < 1.0f;
+                if (!finite) {
+                    atomicOr(status, ST_BADPOS);
+                    continue;
+                }
+
+                // ---- Esirkepov deposit into the shared frame
+                if (q != 0.0f) {
+                    int lb[3];
+                    float S0[3][3], DS[3][3];
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        const int i0 = (int)floorf(x0[a]), i1 = (int)floorf(x1[a]);
+                        const int gb = i0 < i1 ? i0 : i1;
+                        lb[a] = gb - o[a];
+                        float S1[3];
+                        shape3(x0[a], gb, S0[a]);
+                        shape3(x1[a], gb, S1);
+#pragma unroll
+                        for (int k = 0; k < 3; ++k) DS[a][k] = S1[k] - S0[a][k];
+                    }
+                    const float qw = q * wgt;
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        const int pa = (c + 1) % 3, qa = (c + 2) % 3;
+                        const float fac = -qw / (dt * dvol[c]);
+                        float *Jc = sj + c * G3;
+#pragma unroll
+                        for (int bq = 0; bq < 3; ++bq)
+#pragma unroll
+                            for (int bp = 0; bp < 3; ++bp) {
+                                const float cross = S0[pa][bp] * S0[qa][bq] + 0.5f * DS[pa][bp] * S0[qa][bq] +
+                                                    0.5f * S0[pa][bp] * DS[qa][bq] +
+                                                    DS[pa][bp] * DS[qa][bq] * (1.0f / 3.0f);
+                                float acc = 0.0f;
+#pragma unroll
+                                for (int a = 0; a < 2; ++a) {
+                                    acc += DS[c][a] * cross;
+                                    if (acc != 0.0f) {
+                                        int l3[3];
+                                        l3[c] = lb[c] + a;
+                                        l3[pa] = lb[pa] + bp;
+                                        l3[qa] = lb[qa] + bq;
+                                        atomicAdd(&Jc[(l3[2] * G + l3[1]) * G + l3[0]], fac * acc);
+                                    }
+                                }
+                            }
+                    }
+                }
+
+                // ---- periodic image, tile membership, write back or migrate
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    if (g.bc[a] == 0) {
+                        const float L = (float)g.n[a];
+                        if (x1[a] < 0.0f) x1[a] += L;
+                        else if (x1[a] >= L) x1[a] -= L;
+                        if (x1[a] >= L) x1[a] = 0.0f;
+                    }
+                }
+                const int nt = tile_index(g, x1[0], x1[1], x1[2]);
+                if (nt == t) {
+                    sp.x[s] = x1[0]; sp.y[s] = x1[1]; sp.z[s] = x1[2];
+                    sp.ux[s] = u[0]; sp.uy[s] = u[1]; sp.uz[s] = u[2];
+                } else {
+                    const unsigned mask = __activemask();
+                    const int lane = threadIdx.x & 31;
+                    const int leader = __ffs(mask) - 1;
+                    int mb = 0;
+                    if (lane == leader) mb = atomicAdd(sp.mig_count, __popc(mask));
+                    mb = __shfl_sync(mask, mb, leader);
+                    const int m = mb + __popc(mask & ((1u << lane) - 1u));
+                    if (m < sp.mig_cap) {
+                        sp.mx[m] = x1[0]; sp.my[m] = x1[1]; sp.mz[m] = x1[2];
+                        sp.mux[m] = u[0]; sp.muy[m] = u[1]; sp.muz[m] = u[2];
+                        sp.mw[m] = wgt;
+                        if (sp.zq) sp.mzq[m] = sp.zq[s];
+                        sp.mid[m] = sp.id[s];
+                        sp.mdest[m] = nt;
+                    } else {
+                        atomicOr(status, ST_OVERFLOW);
+                    }
+                    const int hslot = atomicAdd(&s_holes, 1);
+                    sp.holes[base + hslot] = p;
+                    sp.x[s] = -1.0f;
+                }
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            sp.hole_count[t] = s_holes;
+            sp.hole_used[t] = 0;
+            s_holes = 0;
+        }
+        __syncthreads();
+    }
+
+    float *dst = jscratch + (long long)t * 3 * G3;
+    for (int l = threadIdx.x; l < 3 * G3; l += blockDim.x) dst[l] = sj[l];
+}
+
+// For every node: J = sum of the tile frames that cover it, in a fixed order.
+// Frame of tile tt along an axis covers global nodes tt*T-1 .. tt*T+T+1; the
+// node i with own tile tt sits at local i - tt*T + 1 in [1, T]; the previous
+// tile covers it at local + T when local <= 2, the next at local - T when
+// local == T.
+__device__ __forceinline__ int axis_cands(const GridDev &g, int a, int i, int tile[2], int loc[2]) {
+    const int T = g.T, nt = g.nt[a];
+    const int own = i / T, l = i - own * T + 1;
+    int n = 0;
+    if (l <= 2) {
+        int pt = own - 1;
+        if (pt < 0 && g.bc[a] == 0) pt += nt;
+        if (pt >= 0) { tile[n] = pt; loc[n] = l + T; ++n; }
+    }
+    tile[n] = own; loc[n] = l; ++n;
+    if (l == T) {
+        int nt2 = own + 1;
+        if (nt2 >= nt && g.bc[a] == 0) nt2 -= nt;
+        if (nt2 < nt) { tile[n] = nt2; loc[n] = 0; ++n; }
+    }
+    return n;
+}
+
+__global__ void k_j_reduce(GridDev g, const float *__restrict__ jscratch, float *__restrict__ J) {
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= g.N) return;
+    const int nx = g.n[0], ny = g.n[1];
+    const int i = (int)(c % nx), j = (int)((c / nx) % ny), k = (int)(c / ((long long)nx * ny));
+    const int G = frame_G(g.T), G3 = G * G * G;
+    int tx[2], lx[2], ty[2], ly[2], tz[2], lz[2];
+    const int nxc = axis_cands(g, 0, i, tx, lx);
+    const int nyc = axis_cands(g, 1, j, ty, ly);
+    const int nzc = axis_cands(g, 2, k, tz, lz);
+    float acc[3] = {0.0f, 0.0f, 0.0f};
+    for (int cz = 0; cz < nzc; ++cz)
+        for (int cy = 0; cy < nyc; ++cy)
+            for (int cx = 0; cx < nxc; ++cx) {
+                const long long t = tx[cx] + (long long)g.nt[0] * (ty[cy] + (long long)g.nt[1] * tz[cz]);
+                const float *fr = jscratch + t * 3 * G3 + (lz[cz] * G + ly[cy]) * G + lx[cx];
+                acc[0] += fr[0];
+                acc[1] += fr[G3];
+                acc[2] += fr[2 * G3];
+            }
+    J[c] = acc[0];
+    J[g.N + c] = acc[1];
+    J[2 * g.N + c] = acc[2];
+}
+
+// Insert migrants: into a hole of the destination tile if one is free, else at
+// its end.  Grid-stride over the migration buffer (its fill is read on device).
+__global__ void k_rebin(SpDev sp, int *__restrict__ status) {
+    const int nm = min(*sp.mig_count, sp.mig_cap);
+    for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < nm; m += gridDim.x * blockDim.x) {
+        const int t = sp.mdest[m];
+        const int h = atomicAdd(&sp.hole_used[t], 1);
+        int slot;
+        if (h < sp.hole_count[t]) {
+            slot = sp.holes[(long long)t * sp.cap + h];
+        } else {
+            slot = atomicAdd(&sp.count[t], 1);
+            if (slot >= sp.cap) {
+                atomicOr(status, ST_OVERFLOW);
+                continue;
+            }
+        }
+        const long long s = (long long)t * sp.cap + slot;
+        sp.x[s] = sp.mx[m]; sp.y[s] = sp.my[m]; sp.z[s] = sp.mz[m];
+        sp.ux[s] = sp.mux[m]; sp.uy[s] = sp.muy[m]; sp.uz[s] = sp.muz[m];
+        sp.w[s] = sp.mw[m];
+        if (sp.zq) sp.zq[s] = sp.mzq[m];
+        sp.id[s] = sp.mid[m];
+    }
+}
+
+// Close the holes no migrant filled: move live particles from the end of the
+// tile into them and shrink the count.  One thread per tile.
+__global__ void k_compact(GridDev g, SpDev sp) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= g.ntiles) return;
+    const int hc = sp.hole_count[t], hu = sp.hole_used[t];
+    int n = min(sp.count[t], sp.cap);
+    if (hu >= hc) {
+        sp.count[t] = n;  // an overflowing append left count above the capacity
+        return;
+    }
+    const long long base = (long long)t * sp.cap;
+    const int nh = hc - hu;
+    const int new_n = n - nh;
+    int src = new_n;  // scans [new_n, n) for live particles
+    for (int h = hu; h < hc; ++h) {
+        const int dst = sp.holes[base + h];
+        if (dst >= new_n) continue;  // the hole disappears with the shrink
+        while (src < n && sp.x[base + src] < 0.0f) ++src;
+        if (src >= n) break;
+        const long long a = base + dst, b = base + src;
+        sp.x[a] = sp.x[b]; sp.y[a] = sp.y[b]; sp.z[a] = sp.z[b];
+        sp.ux[a] = sp.ux[b]; sp.uy[a] = sp.uy[b]; sp.uz[a] = sp.uz[b];
+        sp.w[a] = sp.w[b];
+        if (sp.zq) sp.zq[a] = sp.zq[b];
+        sp.id[a] = sp.id[b];
+        ++src;
+    }
+    sp.count[t] = new_n;
+    sp.hole_count[t] = 0;
+    sp.hole_used[t] = 0;
+}
+
+__global__ void k_count_tiles(GridDev g, long long n, const float *__restrict__ x, const float *__restrict__ y,
+                              const float *__restrict__ z, int *__restrict__ counts) {
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
+         p += (long long)gridDim.x * blockDim.x)
+        atomicAdd(&counts[tile_index(g, x[p], y[p], z[p])], 1);
+}
+
+__global__ void k_bin(GridDev g, SpDev sp, long long n, const float *__restrict__ x, const float *__restrict__ y,
+                      const float *__restrict__ z, const float *__restrict__ ux, const float *__restrict__ uy,
+                      const float *__restrict__ uz, const float *__restrict__ w, const float *__restrict__ zq,
+                      const uint64_t *__restrict__ ids, int *__restrict__ status) {
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
+         p += (long long)gridDim.x * blockDim.x) {
+        const int t = tile_index(g, x[p], y[p], z[p]);
+        const int slot = atomicAdd(&sp.count[t], 1);
+        if (slot >= sp.cap) {
+            atomicOr(status, ST_OVERFLOW);
+            continue;
+        }
+        const long long s = (long long)t * sp.cap + slot;
+        sp.x[s] = x[p]; sp.y[s] = y[p]; sp.z[s] = z[p];
+        sp.ux[s] = ux[p]; sp.uy[s] = uy[p]; sp.uz[s] = uz[p];
+        sp.w[s] = w[p];
+        if (sp.zq) sp.zq[s] = zq ? zq[p] : 0.0f;
+        sp.id[s] = ids ? ids[p] : (uint64_t)p;
+    }
+}
+
+static inline unsigned blocks_for(long long n, int b) { return (unsigned)((n + b - 1) / b); }
+
+void launch_push_deposit(const GridDev &g, const float *E, const float *B, const SpSet &set, float *jscratch,
+                         int *status, cudaStream_t st) {
+    const size_t smem = push_smem_bytes(g.T);
+    k_push_deposit<<<g.ntiles, 256, smem, st>>>(g, E, B, set, jscratch, status);
+}
+
+void launch_j_reduce(const GridDev &g, const float *jscratch, float *J, cudaStream_t st) {
+    k_j_reduce<<<blocks_for(g.N, 256), 256, 0, st>>>(g, jscratch, J);
+}
+
+void launch_rebin(const GridDev &g, const SpDev &s, int *status, cudaStream_t st) {
+    (void)g;
+    k_rebin<<<152 * 4, 256, 0, st>>>(s, status);
+}
+
+void launch_compact(const GridDev &g, const SpDev &s, cudaStream_t st) {
+    k_compact<<<blocks_for(g.ntiles, 128), 128, 0, st>>>(g, s);
+}
+
+void launch_count_tiles(const GridDev &g, long long n, const float *x, const float *y, const float *z,
+                        int *counts, cudaStream_t st) {
+    if (n == 0) return;
+    k_count_tiles<<<min(blocks_for(n, 256), 152u * 16u), 256, 0, st>>>(g, n, x, y, z, counts);
+}
+
+void launch_bin_particles(const GridDev &g, const SpDev &s, long long n, const float *x, const float *y,
+                          const float *z, const float *ux, const float *uy, const float *uz, const float *w,
+                          const float *zq, const uint64_t *ids, int *status, cudaStream_t st) {
+    if (n == 0) return;
+    k_bin<<<min(blocks_for(n, 256), 152u * 16u), 256, 0, st>>>(g, s, n, x, y, z, ux, uy, uz, w, zq, ids, status);
+}
+
+}  // namespace hyb

@@ -1,0 +1,73 @@
+"""Seeded synthetic inputs shared by the CUDA path's tests/benchmarks and the oracle.
+
+This module holds none of the method's arithmetic: it only draws initial
+particle sets and initial field configurations (FP32, so both sides start from
+identical values).  The workloads follow the paper's setting (Methodology:
+uniform Cartesian grid, macro-particles per cell weighted by density-volume
+fraction, Gaussian laser) at the sizes of the benchmark configurations:
+
+* ``periodic_plasma`` -- pre-ionised hydrogen (e-, p+) at uniform density,
+  `ppc` particles per cell per species at uniform random positions, Maxwellian
+  momenta of temperature `T_keV` (non-relativistic Gaussian per component,
+  sigma_u = sqrt(kT / m c^2)), plus a linearly polarised plane wave
+  E_y = a0 cos(k x), B_z = a0 cos(k x) along x (k = 2 pi / box length for the
+  fundamental mode that fits the box).
+"""
+import math
+
+import numpy as np
+
+M_P = 1836.15267343          # proton / electron mass ratio (CODATA 2018)
+MC2_KEV = 510.99895000       # electron rest energy [keV]
+
+
+def laser_units(lambda_um=0.8):
+    """Length c/w0 in micrometres for the given wavelength."""
+    return lambda_um / (2.0 * math.pi)
+
+
+def uniform_particles(rng, n_cells, ppc, density, d, temperature_keV, mass, lo=(0, 0, 0), hi=None):
+    """Uniformly placed particles (cell units) inside [lo, hi) with Maxwellian momenta."""
+    nx, ny, nz = n_cells
+    hi = hi if hi is not None else (nx, ny, nz)
+    cells = (hi[0] - lo[0]) * (hi[1] - lo[1]) * (hi[2] - lo[2])
+    n = int(cells * ppc)
+    x = rng.uniform(lo[0], hi[0], n).astype(np.float32)
+    y = rng.uniform(lo[1], hi[1], n).astype(np.float32)
+    z = rng.uniform(lo[2], hi[2], n).astype(np.float32)
+    for a, (v, h) in enumerate(((x, hi[0]), (y, hi[1]), (z, hi[2]))):
+        np.minimum(v, np.nextafter(np.float32(h), np.float32(0)), out=v)
+    sig = math.sqrt(temperature_keV / (MC2_KEV * mass))
+    ux, uy, uz = (rng.standard_normal((3, n)) * sig).astype(np.float32)
+    w = np.full(n, density * d[0] * d[1] * d[2] / ppc, np.float32)
+    return dict(x=x, y=y, z=z, ux=ux, uy=uy, uz=uz, w=w)
+
+
+def plane_wave_fields(nx, ny, nz, dx, a0, modes=1):
+    """E_y = a0 cos(k x) at E_y nodes (i dx), B_z = a0 cos(k x) at B_z nodes
+    ((i + 1/2) dx); k = 2 pi modes / (nx dx).  Shapes (3, nz, ny, nx) FP32."""
+    k = 2.0 * math.pi * modes / (nx * dx)
+    E = np.zeros((3, nz, ny, nx), np.float32)
+    B = np.zeros((3, nz, ny, nx), np.float32)
+    xe = np.arange(nx) * dx
+    xb = (np.arange(nx) + 0.5) * dx
+    E[1] = (a0 * np.cos(k * xe)).astype(np.float32)[None, None, :]
+    B[2] = (a0 * np.cos(k * xb)).astype(np.float32)[None, None, :]
+    return E, B
+
+
+def periodic_plasma(n=32, ppc=8, density=0.1, temperature_keV=1.0, a0=1.0, cells_per_lambda=16,
+                    seed=1, ny=None, nz=None):
+    """The plain full-PIC workload: periodic box, e- and p+ at `density` n_c,
+    `ppc` per cell per species, Maxwellian T, plane wave a0 (defaults: the
+    32^3, lambda/16, 0.1 n_c, 8 ppc, 1 keV, a0 = 1 configuration)."""
+    ny = n if ny is None else ny
+    nz = n if nz is None else nz
+    dx = 2.0 * math.pi / cells_per_lambda
+    rng = np.random.default_rng(seed)
+    d = (dx, dx, dx)
+    ele = uniform_particles(rng, (n, ny, nz), ppc, density, d, temperature_keV, 1.0)
+    ion = uniform_particles(rng, (n, ny, nz), ppc, density, d, temperature_keV, M_P)
+    E, B = plane_wave_fields(n, ny, nz, dx, a0, modes=max(1, round(n / cells_per_lambda)))
+    return dict(grid=dict(nx=n, ny=ny, nz=nz, dx=dx, cfl_frac=0.95, bc=(0, 0, 0)),
+                species=[dict(q=-1.0, m=1.0, **ele), dict(q=1.0, m=M_P, **ion)], E=E, B=B)

@@ -1,0 +1,183 @@
+"""Thin Python front end over the C ABI (include/hyb.h).
+
+Argument marshalling only: arrays are handed to libhyb.so as host pointers
+(numpy) or device pointers (torch CUDA tensors); PyTorch provides the CUDA
+stream the context runs on.  Every step of the method runs in the library.
+"""
+import ctypes as C
+
+import numpy as np
+
+from . import _abi
+from ._abi import check
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _ptr_and_dev(a, dtype):
+    """Return (pointer, on_device, keepalive) for a numpy array or torch tensor."""
+    if a is None:
+        return None, False, None
+    if isinstance(a, np.ndarray):
+        arr = np.ascontiguousarray(a, dtype=dtype)
+        return arr.ctypes.data, False, arr
+    torch = _torch()
+    if isinstance(a, torch.Tensor):
+        tdt = {np.float32: torch.float32, np.uint64: torch.int64}[dtype]
+        t = a.contiguous()
+        if t.dtype != tdt:
+            t = t.to(tdt)
+        return t.data_ptr(), t.is_cuda, t
+    arr = np.ascontiguousarray(np.asarray(a), dtype=dtype)
+    return arr.ctypes.data, False, arr
+
+
+class Simulation:
+    """One hybrid fluid-kinetic context on the current CUDA device.
+
+    Geometry: nx*ny*nz cells of size (dx, dy, dz) [c/w0]; bc per axis
+    0 = periodic, 1 = Mur + reflecting walls.  dt <= 0 picks cfl_frac times the
+    Courant limit.  ``laser`` is None or a dict with keys a0, tau_fwhm, w0_spot,
+    t_peak, y_c, z_c, x_src, pol (Gaussian soft source).
+    """
+
+    def __init__(self, nx, ny, nz, dx, dy=None, dz=None, dt=0.0, cfl_frac=0.95, bc=(0, 0, 0),
+                 lambda_um=0.8, laser=None, seed=1, tile=8, stream=None, arena=None):
+        self._lib = _abi.load()
+        d = _abi.hyb_grid_desc()
+        d.nx, d.ny, d.nz = nx, ny, nz
+        d.dx = dx
+        d.dy = dx if dy is None else dy
+        d.dz = dx if dz is None else dz
+        d.dt, d.cfl_frac = dt, cfl_frac
+        for a in range(3):
+            d.bc[a] = bc[a]
+        d.lambda_um = lambda_um
+        if laser:
+            d.laser_kind = _abi.HYB_LASER_GAUSS
+            for k in ("a0", "tau_fwhm", "w0_spot", "t_peak", "y_c", "z_c"):
+                setattr(d, k, float(laser[k]))
+            d.x_src, d.pol = int(laser["x_src"]), int(laser.get("pol", 1))
+        d.seed = seed
+        d.tile = tile
+        if stream is None:
+            torch = _torch()
+            stream = torch.cuda.current_stream().cuda_stream
+        d.stream = stream
+        self._arena = arena
+        if arena is not None:
+            d.arena_dev = arena.data_ptr()
+            d.arena_bytes = arena.numel() * arena.element_size()
+        self.desc = d
+        self.shape = (nz, ny, nx)
+        self.N = nx * ny * nz
+        h = C.c_void_p()
+        check(self._lib.hyb_init_grid(C.byref(d), C.byref(h)))
+        self._ctx = h
+        self.n_species = 0
+
+    # ------------------------------------------------------------------ lifecycle
+    def close(self):
+        if getattr(self, "_ctx", None):
+            self._lib.hyb_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # ------------------------------------------------------------------ set-up
+    def load_species(self, q, m, x, y, z, ux, uy, uz, w, zq=None, ids=None, tile_capacity=0):
+        d = _abi.hyb_species_desc()
+        d.q, d.m = q, m
+        keep = []
+        ptrs = []
+        on_dev = None
+        for a in (x, y, z, ux, uy, uz, w, zq):
+            p, dev, k = _ptr_and_dev(a, np.float32)
+            keep.append(k)
+            ptrs.append(p)
+            if a is not None:
+                on_dev = dev if on_dev is None else on_dev
+                if dev != on_dev:
+                    raise ValueError("particle arrays must all be host or all be device memory")
+        pid, dev, k = _ptr_and_dev(ids, np.uint64)
+        keep.append(k)
+        if ids is not None and dev != on_dev:
+            raise ValueError("ids must live where the particle arrays live")
+        d.n = int(len(x))
+        d.tile_capacity = int(tile_capacity)
+        d.ptr_on_device = int(bool(on_dev))
+        d.x, d.y, d.z, d.ux, d.uy, d.uz, d.w, d.zq = ptrs
+        d.ids = pid
+        sid = C.c_int()
+        check(self._lib.hyb_load_species(self._ctx, C.byref(d), C.byref(sid)))
+        self.n_species += 1
+        return sid.value
+
+    def set_fields(self, E, B):
+        pe, de, ke = _ptr_and_dev(E, np.float32)
+        pb, db, kb = _ptr_and_dev(B, np.float32)
+        if de != db:
+            raise ValueError("E and B must both be host or both be device memory")
+        check(self._lib.hyb_set_fields(self._ctx, pe, pb, int(de)))
+
+    # ------------------------------------------------------------------ stepping
+    def step(self, n=1):
+        check(self._lib.hyb_step(self._ctx, int(n)))
+
+    def set_profiling(self, on=True):
+        check(self._lib.hyb_set_profiling(self._ctx, int(bool(on))))
+
+    def phase_times(self):
+        """Device milliseconds of each phase of the most recent step (synchronises)."""
+        out = _abi.hyb_phase_times_t()
+        check(self._lib.hyb_phase_times(self._ctx, C.byref(out)))
+        return {name: out.ms[i] for i, name in enumerate(_abi.PHASES) if out.ms[i] > 0}
+
+    def clear_status(self):
+        check(self._lib.hyb_clear_status(self._ctx))
+
+    # ------------------------------------------------------------------ read-back
+    def diagnostics(self, raise_on_status=True):
+        out = _abi.hyb_diag()
+        code = self._lib.hyb_diagnostics(self._ctx, C.byref(out))
+        if raise_on_status:
+            check(code)
+        ns = out.n_species
+        return {"step": out.step, "time": out.time, "w_e": out.w_e, "w_b": out.w_b,
+                "w_kin": [out.w_kin[i] for i in range(ns)], "count": [out.count[i] for i in range(ns)],
+                "status": out.status, "launches_per_step": out.launches_per_step}
+
+    def get_fields(self):
+        E = np.empty((3,) + self.shape, np.float32)
+        B = np.empty((3,) + self.shape, np.float32)
+        J = np.empty((3,) + self.shape, np.float32)
+        check(self._lib.hyb_get_fields(self._ctx, E.ctypes.data, B.ctypes.data, J.ctypes.data))
+        return E, B, J
+
+    def get_species(self, sid, with_zq=False, max_n=None):
+        if max_n is None:
+            max_n = self.diagnostics(raise_on_status=False)["count"][sid]
+        arrs = {k: np.empty(max_n, np.float32) for k in ("x", "y", "z", "ux", "uy", "uz", "w")}
+        arrs["zq"] = np.empty(max_n, np.float32) if with_zq else None
+        ids = np.empty(max_n, np.uint64)
+        n = C.c_longlong()
+        check(self._lib.hyb_get_species(
+            self._ctx, sid, max_n, *[arrs[k].ctypes.data if arrs[k] is not None else None
+                                     for k in ("x", "y", "z", "ux", "uy", "uz", "w", "zq")],
+            ids.ctypes.data, C.byref(n)))
+        out = {k: v[:n.value] for k, v in arrs.items() if v is not None}
+        out["ids"] = ids[:n.value]
+        return out

@@ -1,0 +1,159 @@
+"""GPU parity of the Yee FDTD, Mur, laser source and PIC push/deposit against the
+FP64 oracle on identical seeded FP32 inputs.
+
+Tolerances (stated by the method's targets): per-particle momentum relative
+error <= 1e-5 after one step; field relative L2 <= 1e-4 after 100 steps.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2510_11174_gb300 import inputs
+from _util import by_id, make_pair, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+def _fields_close(sim, orc, tol):
+    E, B, J = sim.get_fields()
+    eE, eB = rel_l2(E, orc.E), rel_l2(B, orc.B)
+    assert eE <= tol and eB <= tol, (eE, eB)
+    return eE, eB
+
+
+def test_vacuum_fdtd_periodic_100_steps():
+    rng = np.random.default_rng(7)
+    nx, ny, nz = 16, 16, 8
+    # a superposition of smooth random modes
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    E = np.zeros((3, nz, ny, nx), np.float32)
+    B = np.zeros((3, nz, ny, nx), np.float32)
+    for c in range(3):
+        for _ in range(4):
+            k = rng.integers(0, 3, 3)
+            ph = 2 * np.pi * (k[0] * x / nx + k[1] * y / ny + k[2] * z / nz) + rng.uniform(0, 6)
+            E[c] += np.cos(ph).astype(np.float32) * np.float32(rng.normal())
+            B[c] += np.sin(ph).astype(np.float32) * np.float32(rng.normal())
+    inp = dict(grid=dict(nx=nx, ny=ny, nz=nz, dx=0.39), E=E, B=B)
+    sim, orc = make_pair(inp)
+    sim.step(100)
+    orc.step(100)
+    _fields_close(sim, orc, 1e-4)
+
+
+@pytest.mark.parametrize("bc", [(1, 0, 0), (1, 1, 1)])
+def test_mur_laser_source_100_steps(bc):
+    nx, ny, nz = 32, 16, 16
+    dx = 2 * math.pi / 20
+    laser = dict(a0=1.0, tau_fwhm=8.0, w0_spot=2.5, t_peak=12.0, y_c=8.0, z_c=8.0, x_src=3, pol=1)
+    inp = dict(grid=dict(nx=nx, ny=ny, nz=nz, dx=dx, bc=bc))
+    sim, orc = make_pair(inp, laser=laser)
+    for _ in range(4):
+        sim.step(25)
+        orc.step(25)
+    eE, eB = _fields_close(sim, orc, 1e-4)
+    assert np.max(np.abs(orc.E)) > 0.1  # the pulse is in the box
+
+
+def _plasma(n=16, ppc=8, seed=3, a0=1.0):
+    return inputs.periodic_plasma(n=n, ppc=ppc, seed=seed, a0=a0)
+
+
+def test_one_step_per_particle_momentum():
+    inp = _plasma()
+    sim, orc = make_pair(inp)
+    sim.step(1)
+    orc.step(1)
+    for sid in range(2):
+        gsp = by_id(sim.get_species(sid))
+        osp = orc.species[sid]
+        assert np.array_equal(gsp["ids"], np.sort(osp.ids))
+        o = np.argsort(osp.ids)
+        ug = np.stack([gsp["ux"], gsp["uy"], gsp["uz"]]).astype(np.float64)
+        uo = np.stack([osp.ux[o], osp.uy[o], osp.uz[o]])
+        rel = np.linalg.norm(ug - uo, axis=0) / np.linalg.norm(uo, axis=0)
+        assert rel.max() <= 1e-5, rel.max()
+        for k in ("x", "y", "z"):
+            dx = np.abs(gsp[k] - getattr(osp, k)[o])
+            dx = np.minimum(dx, 16 - dx)  # periodic image
+            assert dx.max() <= 2e-5
+    E, B, J = sim.get_fields()
+    assert rel_l2(J, orc.J) <= 1e-5
+
+
+def test_pic_100_steps_fields_and_energy():
+    inp = _plasma(n=16, ppc=8, seed=5)
+    sim, orc = make_pair(inp)
+    d0 = sim.diagnostics()
+    o0 = orc.diagnostics()
+    assert abs(d0["w_e"] - o0["w_e"]) <= 1e-12 * o0["w_e"]
+    for s in range(2):
+        assert abs(d0["w_kin"][s] - o0["w_kin"][s]) <= 1e-12 * o0["w_kin"][s]
+    for _ in range(4):
+        sim.step(25)
+        orc.step(25)
+    _fields_close(sim, orc, 1e-4)
+    d1, o1 = sim.diagnostics(), orc.diagnostics()
+    wt = o1["w_e"] + o1["w_b"] + sum(o1["w_kin"])
+    for key in ("w_e", "w_b"):
+        assert abs(d1[key] - o1[key]) <= 1e-4 * wt
+    for s in range(2):
+        assert abs(d1["w_kin"][s] - o1["w_kin"][s]) <= 1e-4 * wt
+    assert d1["count"] == o1["count"]
+
+
+def test_reflecting_walls_and_mur_with_particles():
+    nx = ny = nz = 16
+    rng = np.random.default_rng(9)
+    dx = 2 * math.pi / 16
+    n = 6000
+    sp = dict(q=-1.0, m=1.0, x=rng.uniform(0, 15, n).astype(np.float32),
+              y=rng.uniform(0, 15, n).astype(np.float32), z=rng.uniform(0, 15, n).astype(np.float32),
+              ux=rng.normal(0, 0.5, n).astype(np.float32), uy=rng.normal(0, 0.5, n).astype(np.float32),
+              uz=rng.normal(0, 0.5, n).astype(np.float32), w=np.full(n, 1e-3, np.float32))
+    inp = dict(grid=dict(nx=nx, ny=ny, nz=nz, dx=dx, bc=(1, 1, 1)), species=[sp])
+    sim, orc = make_pair(inp)
+    sim.step(40)
+    orc.step(40)
+    _fields_close(sim, orc, 1e-4)
+    gsp = by_id(sim.get_species(0))
+    o = np.argsort(orc.species[0].ids)
+    assert gsp["x"].min() >= 0 and gsp["x"].max() <= 15
+    ug = np.stack([gsp["ux"], gsp["uy"], gsp["uz"]]).astype(np.float64)
+    uo = np.stack([orc.species[0].ux[o], orc.species[0].uy[o], orc.species[0].uz[o]])
+    assert rel_l2(ug, uo) <= 1e-4
+
+
+@pytest.mark.parametrize("tile", [4, 8])
+def test_tile_sizes_agree(tile):
+    inp = _plasma(n=16, ppc=4, seed=11)
+    sim, orc = make_pair(inp, tile=tile)
+    sim.step(20)
+    orc.step(20)
+    _fields_close(sim, orc, 1e-4)
+
+
+def test_empty_species_and_ragged_tiles():
+    rng = np.random.default_rng(2)
+    n = 777  # ragged: not a multiple of the CTA width, uneven per tile
+    sp = dict(q=-1.0, m=1.0, x=rng.uniform(0, 4, n).astype(np.float32), y=rng.uniform(0, 16, n).astype(np.float32),
+              z=rng.uniform(0, 8, n).astype(np.float32), ux=rng.normal(0, 0.3, n).astype(np.float32),
+              uy=rng.normal(0, 0.3, n).astype(np.float32), uz=rng.normal(0, 0.3, n).astype(np.float32),
+              w=np.full(n, 2e-3, np.float32))
+    empty = {k: v[:0] for k, v in sp.items() if k not in ("q", "m")}
+    inp = dict(grid=dict(nx=16, ny=16, nz=8, dx=0.4), species=[sp, dict(q=1.0, m=1836.0, **empty)])
+    sim, orc = make_pair(inp)
+    sim.step(10)
+    orc.step(10)
+    _fields_close(sim, orc, 1e-4)
+    assert sim.diagnostics()["count"] == [n, 0]
+
+
+def test_full_size_periodic_plasma_100_steps():
+    """The 32^3, 8 ppc/species, lambda/16, a0 = 1 workload for 100 steps."""
+    inp = inputs.periodic_plasma()
+    sim, orc = make_pair(inp)
+    sim.step(100)
+    orc.step(100)
+    _fields_close(sim, orc, 1e-4)
