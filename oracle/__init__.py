@@ -53,7 +53,7 @@ class Species(C.Structure):
     _fields_ = [("q", C.c_double), ("m", C.c_double), ("n", C.c_long),
                 ("x", C.c_void_p), ("y", C.c_void_p), ("z", C.c_void_p),
                 ("ux", C.c_void_p), ("uy", C.c_void_p), ("uz", C.c_void_p),
-                ("w", C.c_void_p), ("zq", C.c_void_p)]
+                ("w", C.c_void_p), ("zq", C.c_void_p), ("id", C.c_void_p), ("eb", C.c_void_p)]
 
 
 _P = C.c_void_p
@@ -78,6 +78,19 @@ def _declare(L):
     L.orc_laser_source.argtypes = [C.POINTER(Grid), C.c_int, C.c_int] + [C.c_double] * 6 + [C.c_long, _D3]
     L.orc_plasma_scales.argtypes = [C.c_double, _P]
     L.orc_laser_scales.argtypes = [C.c_double, _P]
+    L.orc_adk_rate.argtypes = [C.c_double, C.c_double, C.c_double, C.c_int, C.c_int]
+    L.orc_adk_rate.restype = C.c_double
+    L.orc_keldysh.argtypes = [C.c_double] * 3
+    L.orc_keldysh.restype = C.c_double
+    L.orc_mpi_rate.argtypes = [C.c_double, C.c_double, C.c_double, C.c_int, C.c_double]
+    L.orc_mpi_rate.restype = C.c_double
+    L.orc_blend_weight.argtypes = [C.c_double]
+    L.orc_blend_weight.restype = C.c_double
+    L.orc_ionization_rate.argtypes = [C.c_double, C.c_double, C.c_double, C.c_int, C.c_double]
+    L.orc_ionization_rate.restype = C.c_double
+    L.orc_ionize.argtypes = [C.POINTER(Species), _P, C.c_int, _P, _P, C.c_double, C.c_double, C.c_double,
+                             C.c_uint32, C.c_uint32, C.c_long, C.POINTER(Species), C.c_long, _P]
+    L.orc_ionize.restype = C.c_long
     for name, fn in _EXTRA_DECLS:
         fn(L)
 
@@ -148,6 +161,7 @@ class Particles:
         self.tau = None if tau is None else np.ascontiguousarray(tau, dtype=np.float64).copy()
         self.ids = (np.arange(len(self.x), dtype=np.uint64) if ids is None
                     else np.ascontiguousarray(ids, dtype=np.uint64).copy())
+        self.eb = None  # set to a (n, 6) array to record E^n, B^n at x^n during the push
 
     @property
     def n(self):
@@ -159,6 +173,8 @@ class Particles:
         for name in self.FIELDS:
             setattr(s, name, _ptr(getattr(self, name)).value)
         s.zq = None if self.zq is None else _ptr(self.zq).value
+        s.id = _ptr(self.ids).value
+        s.eb = None if self.eb is None else _ptr(self.eb).value
         return s
 
     def append(self, other):
@@ -235,3 +251,54 @@ def laser_scales(lambda_m):
 def laser_source(g, J, step, x_src, pol, a0, tau_fwhm, t_peak, w0_spot, y_c, z_c):
     lib().orc_laser_source(C.byref(g), int(x_src), int(pol), float(a0), float(tau_fwhm), float(t_peak),
                            float(w0_spot), float(y_c), float(z_c), int(step), _f3(J))
+
+
+# --------------------------------------------------------------------------- ionization
+HARTREE_EV = 27.211386245988      # CODATA 2018
+T_ATOMIC = 2.4188843265857e-17    # atomic unit of time [s]
+E_ATOMIC = 5.14220674763e11       # atomic unit of field [V/m]
+
+
+def adk_rate(F, Ip, Z, l=0, m=0):
+    return lib().orc_adk_rate(float(F), float(Ip), float(Z), int(l), int(m))
+
+
+def keldysh(F, Ip, w0):
+    return lib().orc_keldysh(float(F), float(Ip), float(w0))
+
+
+def mpi_rate(F, Ip, Z, l, w0):
+    return lib().orc_mpi_rate(float(F), float(Ip), float(Z), int(l), float(w0))
+
+
+def blend_weight(gamma):
+    return lib().orc_blend_weight(float(gamma))
+
+
+def ionization_rate(F, Ip, Z, l, w0):
+    """Blended ADK/MPI rate [1/atomic time] at field F [atomic units]."""
+    return lib().orc_ionization_rate(float(F), float(Ip), float(Z), int(l), float(w0))
+
+
+def atomic_units(lambda_m, dt_norm):
+    """(w0 in a.u., E_ref/E_atomic, dt in a.u.) for wavelength lambda and dt in 1/w0."""
+    w0, nc, Eref, L = laser_scales(lambda_m)
+    return w0 * T_ATOMIC, Eref / E_ATOMIC, dt_norm / w0 / T_ATOMIC
+
+
+def ionize(ions, zmax, Ip_eV, lq, lambda_m, dt_norm, seed, sp_index, step):
+    """One Monte Carlo ionization pass over `ions` (uses ions.eb from the push).
+    Returns (new electron Particles, ionization energy in units m_e c^2 * n_c (c/w0)^3)."""
+    w0_au, eratio, dt_au = atomic_units(lambda_m, dt_norm)
+    Ip = np.ascontiguousarray(np.asarray(Ip_eV, dtype=np.float64) / HARTREE_EV)
+    lqa = np.ascontiguousarray(np.asarray(lq, dtype=np.int32))
+    cap = ions.n
+    out = Particles(-1.0, 1.0, *([np.zeros(cap)] * 7))
+    out.ids = np.zeros(cap, dtype=np.uint64)
+    si, so = ions.cstruct(), out.cstruct()
+    en = np.zeros(1)
+    n = lib().orc_ionize(C.byref(si), _ptr(ions.eb), int(zmax), _ptr(Ip), _ptr(lqa), w0_au, eratio, dt_au,
+                         int(seed) & 0xFFFFFFFF, int(sp_index), int(step), C.byref(so), cap, _ptr(en))
+    out.select(np.arange(n))
+    # Hartree -> m_e c^2
+    return out, en[0] * HARTREE_EV / 510998.95

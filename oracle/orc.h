@@ -56,7 +56,9 @@ typedef struct {
     double *x, *y, *z;       /* cell units */
     double *ux, *uy, *uz;    /* gamma*beta */
     double *w;               /* weight: real particles per macro particle, units n_c (c/w0)^3 */
-    double *zq;              /* per-particle charge state (ions) or NULL: q_p = zq[p] when set */
+    double *zq;              /* per-particle charge state (ions) or NULL: q_p = q * zq[p] when set */
+    uint64_t *id;            /* particle ids (keys of the random streams) */
+    double *eb;              /* optional output of the push: E^n, B^n at x^n, 6 per particle */
 } orc_species;
 
 void orc_gather(const orc_grid *g, const double *E[3], const double *B[3],
@@ -66,6 +68,16 @@ void orc_esirkepov(const orc_grid *g, double qw, double x0, double y0, double z0
                    double x1, double y1, double z1, double *J[3]);
 void orc_push_deposit(const orc_grid *g, const double *E[3], const double *B[3],
                       double *J[3], orc_species *s);
+
+/* ---- ionization ----------------------------------------------------------- */
+double orc_adk_rate(double F, double Ip, double Z, int l, int m);
+double orc_keldysh(double F, double Ip, double w0);
+double orc_mpi_rate(double F, double Ip, double Z, int l, double w0);
+double orc_blend_weight(double gamma);
+double orc_ionization_rate(double F, double Ip, double Z, int l, double w0);
+long orc_ionize(orc_species *ions, const double *eb, int zmax, const double *Ip_au, const int *lq,
+                double w0_au, double Eref_over_Ea, double dt_au, uint32_t seed, uint32_t sp_index, long step,
+                orc_species *out, long cap, double *energy_au);
 
 /* ---- diagnostics --------------------------------------------------------- */
 void orc_energy_fields(const orc_grid *g, const double *E[3], const double *B[3], double out[2]);

@@ -152,6 +152,9 @@ void orc_push_deposit(const orc_grid *g, const double *E[3], const double *B[3],
         double x0[3] = {s->x[p], s->y[p], s->z[p]};
         double e[3], b[3], u[3] = {s->ux[p], s->uy[p], s->uz[p]};
         orc_gather(g, E, B, x0[0], x0[1], x0[2], e, b);
+        if (s->eb) {
+            for (int c = 0; c < 3; ++c) { s->eb[6 * p + c] = e[c]; s->eb[6 * p + 3 + c] = b[c]; }
+        }
         orc_boris(q * dt / (2.0 * s->m), e, b, u);
         const double gam = sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
         double x1[3];

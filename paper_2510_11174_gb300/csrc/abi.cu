@@ -253,6 +253,7 @@ static hyb_status alloc_species(hyb_ctx *c, Species &sp, int cap, bool has_zq) {
     s.cap = cap;
     s.q = (float)sp.q;
     s.m = (float)sp.m;
+    s.m_d = sp.m;
     float **fl[7] = {&s.x, &s.y, &s.z, &s.ux, &s.uy, &s.uz, &s.w};
     for (auto f : fl)
         if (ctx_alloc(c, (void **)f, sizeof(float) * slots)) return HYB_ENOMEM;

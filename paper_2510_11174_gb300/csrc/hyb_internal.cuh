@@ -44,6 +44,7 @@ struct SpDev {
     int *hole_count, *hole_used;
     int cap;           // slots per tile
     float q, m;
+    double m_d;        // mass in FP64 for the energy reductions
     // migration buffer: particles that left their tile this step
     float *mx, *my, *mz, *mux, *muy, *muz, *mw, *mzq;
     uint64_t *mid;
