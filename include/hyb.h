@@ -99,6 +99,18 @@ typedef struct {
     const float *x, *y, *z, *ux, *uy, *uz, *w;
     const float *zq;          /* per-particle charge state (ions, q_p = q * zq) or NULL */
     const uint64_t *ids;      /* or NULL */
+    /* Field ionization (paper, Methodology: ADK tunnelling and multiphoton
+     * rates blended by a sigmoid at Keldysh parameter ~1.5).  zmax > 0 makes
+     * the species ionizable up to charge state zmax (zq required); ip_eV[Z]
+     * and l_qn[Z] are the ionization potential and orbital quantum number of
+     * the electron removed in Z -> Z+1; new electrons join species
+     * ionize_into (already loaded, charge -1, mass 1).  Rates come from an
+     * FP64-built table on the device; events use Philox with key (seed,
+     * species id) and counter (id, step, 1). */
+    int zmax;
+    double ip_eV[8];
+    int l_qn[8];
+    int ionize_into;
 } hyb_species_desc;
 
 /* Diagnostics: FP64 energy reductions (paper, Methodology: total energy from
@@ -113,6 +125,8 @@ typedef struct {
     int n_species;
     int status;                            /* latched device status (hyb_status) */
     long long launches_per_step;           /* kernels one step launches */
+    double w_ionize;                       /* energy spent on ionization so far, sum w Ip */
+    long long n_ionize;                    /* ionization events so far */
 } hyb_diag;
 
 /* Create a context: validates the descriptor, allocates fields on the
@@ -170,6 +184,14 @@ typedef struct {
 } hyb_phase_times_t;
 hyb_status hyb_set_profiling(hyb_ctx *ctx, int on);
 hyb_status hyb_phase_times(hyb_ctx *ctx, hyb_phase_times_t *out);
+
+/* Evaluate a device rate table the way the step does, for n field values.
+ * table = HYB_LUT_IONIZE: the ionization rate w [1/atomic time] of species
+ * `species_id`, charge state `level`, at field strengths x_host[i] given in
+ * atomic units.  Host arrays of n values; synchronises. */
+enum { HYB_LUT_IONIZE = 0 };
+hyb_status hyb_eval_rate_table(hyb_ctx *ctx, int table, int species_id, int level, const float *x_host, int n,
+                               float *out_host);
 
 /* Message for the last failing call on this thread (never NULL). */
 const char *hyb_last_error(void);

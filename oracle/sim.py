@@ -16,7 +16,7 @@ import math
 
 import numpy as np
 
-from . import (Grid, Particles, energy_fields, energy_particles, fdtd_b_half, fdtd_e, laser_source,
+from . import (Grid, Particles, energy_fields, energy_particles, fdtd_b_half, fdtd_e, ionize, laser_source,
                push_deposit, zeros_field)
 
 
@@ -26,7 +26,8 @@ def courant_dt(d, cfl_frac):
 
 
 class OracleSim:
-    def __init__(self, nx, ny, nz, dx, dy=None, dz=None, dt=0.0, cfl_frac=0.95, bc=(0, 0, 0), laser=None):
+    def __init__(self, nx, ny, nz, dx, dy=None, dz=None, dt=0.0, cfl_frac=0.95, bc=(0, 0, 0), laser=None,
+                 lambda_um=0.8, seed=1):
         dy = dx if dy is None else dy
         dz = dx if dz is None else dz
         if not dt > 0:
@@ -36,11 +37,17 @@ class OracleSim:
         self.B = zeros_field(self.g)
         self.J = zeros_field(self.g)
         self.laser = laser
+        self.lambda_m = lambda_um * 1e-6
+        self.seed = seed
         self.species = []
+        self.ionize_cfg = []
+        self.w_ionize = 0.0
+        self.n_ionize = 0
         self.nstep = 0
 
-    def load_species(self, q, m, x, y, z, ux, uy, uz, w, zq=None, ids=None):
+    def load_species(self, q, m, x, y, z, ux, uy, uz, w, zq=None, ids=None, ionize=None, **_):
         self.species.append(Particles(q, m, x, y, z, ux, uy, uz, w, zq=zq, ids=ids))
+        self.ionize_cfg.append(ionize)
         return len(self.species) - 1
 
     def set_fields(self, E, B):
@@ -51,8 +58,20 @@ class OracleSim:
         g = self.g
         for _ in range(n):
             self.J[:] = 0.0
-            for sp in self.species:
+            for sp, ion in zip(self.species, self.ionize_cfg):
+                sp.eb = np.zeros((sp.n, 6)) if ion else None
                 push_deposit(g, self.E, self.B, self.J, sp)
+            # field ionization with E^n at x^n (recorded by the push); new electrons
+            # start at x^{n+1} and are not pushed before the next step
+            for si, (sp, ion) in enumerate(zip(self.species, self.ionize_cfg)):
+                if not ion:
+                    continue
+                new, en = ionize(sp, ion["zmax"], ion["ip_eV"], ion["l"], self.lambda_m, g.dt, self.seed, si,
+                                 self.nstep)
+                self.species[ion["into"]].append(new)
+                self.w_ionize += en
+                self.n_ionize += new.n
+                sp.eb = None
             if self.laser:
                 L = self.laser
                 laser_source(g, self.J, self.nstep, L["x_src"], L.get("pol", 1), L["a0"], L["tau_fwhm"],
@@ -66,4 +85,4 @@ class OracleSim:
         we, wb = energy_fields(self.g, self.E, self.B)
         return {"step": self.nstep, "w_e": we, "w_b": wb,
                 "w_kin": [energy_particles(sp) for sp in self.species],
-                "count": [sp.n for sp in self.species]}
+                "count": [sp.n for sp in self.species], "w_ionize": self.w_ionize, "n_ionize": self.n_ionize}

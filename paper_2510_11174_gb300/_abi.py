@@ -16,6 +16,7 @@ STATUS_NAMES = {0: "HYB_OK", 1: "HYB_EINVAL", 2: "HYB_ENOMEM", 3: "HYB_ECUDA", 4
                 5: "HYB_ENAN", 6: "HYB_ETIMEOUT", 7: "HYB_ESTATE"}
 HYB_BC_PERIODIC, HYB_BC_MUR = 0, 1
 HYB_LASER_NONE, HYB_LASER_GAUSS = 0, 1
+HYB_LUT_IONIZE = 0
 HYB_MAX_SPECIES = 8
 
 
@@ -37,7 +38,9 @@ class hyb_species_desc(C.Structure):
                 ("tile_capacity", C.c_longlong), ("ptr_on_device", C.c_int),
                 ("x", C.c_void_p), ("y", C.c_void_p), ("z", C.c_void_p),
                 ("ux", C.c_void_p), ("uy", C.c_void_p), ("uz", C.c_void_p), ("w", C.c_void_p),
-                ("zq", C.c_void_p), ("ids", C.c_void_p)]
+                ("zq", C.c_void_p), ("ids", C.c_void_p),
+                ("zmax", C.c_int), ("ip_eV", C.c_double * 8), ("l_qn", C.c_int * 8),
+                ("ionize_into", C.c_int)]
 
 
 class hyb_diag(C.Structure):
@@ -46,7 +49,8 @@ class hyb_diag(C.Structure):
                 ("w_kin", C.c_double * HYB_MAX_SPECIES),
                 ("count", C.c_longlong * HYB_MAX_SPECIES),
                 ("n_species", C.c_int), ("status", C.c_int),
-                ("launches_per_step", C.c_longlong)]
+                ("launches_per_step", C.c_longlong),
+                ("w_ionize", C.c_double), ("n_ionize", C.c_longlong)]
 
 
 HYB_NPHASE = 8
@@ -74,6 +78,7 @@ PROTOTYPES = {
     "hyb_last_error": (C.c_char_p, []),
     "hyb_set_profiling": (C.c_int, [_ctx, C.c_int]),
     "hyb_phase_times": (C.c_int, [_ctx, C.POINTER(hyb_phase_times_t)]),
+    "hyb_eval_rate_table": (C.c_int, [_ctx, C.c_int, C.c_int, C.c_int, _P, C.c_int, _P]),
 }
 
 _lib = None

@@ -60,10 +60,12 @@ struct PhaseMark {
     hyb_ctx *c;
     void begin(int ph) {
         c->phase_ran[ph] = true;
-        if (c->profiling) cudaEventRecord(c->ev_start[ph], c->stream);
+        // External: during stream capture this becomes an event-record node that
+        // records at every replay (a plain record would only order the capture)
+        if (c->profiling) cudaEventRecordWithFlags(c->ev_start[ph], c->stream, cudaEventRecordExternal);
     }
     void end(int ph) {
-        if (c->profiling) cudaEventRecord(c->ev_end[ph], c->stream);
+        if (c->profiling) cudaEventRecordWithFlags(c->ev_end[ph], c->stream, cudaEventRecordExternal);
     }
 };
 
@@ -77,7 +79,7 @@ static void enqueue_step(hyb_ctx *c) {
     cudaMemsetAsync(c->mig_counts, 0, sizeof(int) * HYB_MAX_SPECIES, st);
     if (set.n > 0) {
         pm.begin(HYB_PH_PUSH);
-        launch_push_deposit(g, c->E, c->B, set, c->jscratch, c->status, st);
+        launch_push_deposit(g, c->E, c->B, c->sp_dev, set.n, c->jscratch, c->status, c->step_dev, st);
         pm.end(HYB_PH_PUSH);
         pm.begin(HYB_PH_JREDUCE);
         launch_j_reduce(g, c->jscratch, c->J, st);
@@ -168,6 +170,7 @@ hyb_status hyb_init_grid(const hyb_grid_desc *d, hyb_ctx **out) {
     g.N = (long long)n[0] * n[1] * n[2];
     g.dt = (float)dt;
     g.dt_d = dt;
+    g.seed = d->seed;
 
     if (d->stream) {
         c->stream = (cudaStream_t)d->stream;
@@ -200,7 +203,8 @@ hyb_status hyb_init_grid(const hyb_grid_desc *d, hyb_ctx **out) {
         ctx_alloc(c, (void **)&c->red_partials, sizeof(double) * (2 + HYB_MAX_SPECIES) * c->red_blocks) ||
         ctx_alloc(c, (void **)&c->red_out, sizeof(double) * (2 + HYB_MAX_SPECIES)) ||
         ctx_alloc(c, (void **)&c->status, sizeof(int)) || ctx_alloc(c, (void **)&c->step_dev, sizeof(long long)) ||
-        ctx_alloc(c, (void **)&c->mig_counts, sizeof(int) * HYB_MAX_SPECIES))
+        ctx_alloc(c, (void **)&c->mig_counts, sizeof(int) * HYB_MAX_SPECIES) ||
+        ctx_alloc(c, (void **)&c->sp_dev, sizeof(SpDev) * HYB_MAX_SPECIES))
         return fail(HYB_ENOMEM, "device allocation for the grid failed (arena too small?)");
     cudaStream_t st = c->stream;
     cudaMemsetAsync(c->E, 0, fbytes, st);
@@ -288,6 +292,18 @@ hyb_status hyb_load_species(hyb_ctx *c, const hyb_species_desc *d, int *species_
     if (d->n < 0) return set_error(HYB_EINVAL, "negative particle count");
     if (d->n > 0 && (!d->x || !d->y || !d->z || !d->ux || !d->uy || !d->uz || !d->w))
         return set_error(HYB_EINVAL, "missing particle arrays");
+    if (d->zmax < 0 || d->zmax > 8) return set_error(HYB_EINVAL, "zmax must be in 0..8");
+    if (d->zmax > 0) {
+        if (!d->zq) return set_error(HYB_EINVAL, "an ionizable species needs per-particle charge states (zq)");
+        if (d->ionize_into < 0 || d->ionize_into >= (int)c->sp.size())
+            return set_error(HYB_EINVAL, "ionize_into must name an already loaded species");
+        if (c->sp[d->ionize_into].has_zq || c->sp[d->ionize_into].q != -1.0 || c->sp[d->ionize_into].m != 1.0)
+            return set_error(HYB_EINVAL, "ionize_into must be an electron species (q = -1, m = 1, no zq)");
+        for (int z = 0; z < d->zmax; ++z)
+            if (!(d->ip_eV[z] > 0.0) || d->l_qn[z] < 0 || d->l_qn[z] > 3)
+                return set_error(HYB_EINVAL, "bad ionization potential or quantum number");
+        if (!(c->desc.lambda_um > 0.0)) return set_error(HYB_EINVAL, "ionization needs lambda_um > 0");
+    }
     const GridDev &g = c->g;
     cudaStream_t st = c->stream;
     const long long n = d->n;
@@ -388,6 +404,8 @@ hyb_status hyb_load_species(hyb_ctx *c, const hyb_species_desc *d, int *species_
         tmp.clear();
         if (alloc_species(c, sp, (int)cap, sp.has_zq) != HYB_OK)
             return set_error(HYB_ENOMEM, "species allocation failed (arena too small?)");
+        hyb_status is = setup_ionization(c, sp.dev, d);
+        if (is != HYB_OK) return is;
         arena_mark = c->arena.used;
         ok = true;
         for (int k = 0; ok && k < 8; ++k) {
@@ -407,9 +425,16 @@ hyb_status hyb_load_species(hyb_ctx *c, const hyb_species_desc *d, int *species_
             cleanup();
             return set_error(HYB_ENOMEM, "staging allocation for species failed (arena too small?)");
         }
-    } else if (alloc_species(c, sp, (int)cap, sp.has_zq) != HYB_OK) {
-        cleanup();
-        return set_error(HYB_ENOMEM, "species allocation failed");
+    } else {
+        if (alloc_species(c, sp, (int)cap, sp.has_zq) != HYB_OK) {
+            cleanup();
+            return set_error(HYB_ENOMEM, "species allocation failed");
+        }
+        hyb_status is = setup_ionization(c, sp.dev, d);
+        if (is != HYB_OK) {
+            cleanup();
+            return is;
+        }
     }
     launch_bin_particles(g, sp.dev, n, dsrc[0], dsrc[1], dsrc[2], dsrc[3], dsrc[4], dsrc[5], dsrc[6], dsrc[7], dids,
                          c->status, st);
@@ -424,6 +449,15 @@ hyb_status hyb_load_species(hyb_ctx *c, const hyb_species_desc *d, int *species_
     }
     *species_id = (int)c->sp.size();
     c->sp.push_back(sp);
+    {
+        const SpSet all = species_set(c);
+        e = cudaMemcpyAsync(c->sp_dev, all.s, sizeof(SpDev) * all.n, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) {
+            c->sp.pop_back();
+            return set_error(HYB_ECUDA, std::string("species table upload: ") + cudaGetErrorString(e));
+        }
+    }
     c->graph_valid = false;
     return HYB_OK;
 }
@@ -489,6 +523,16 @@ hyb_status hyb_phase_times(hyb_ctx *c, hyb_phase_times_t *out) {
     return HYB_OK;
 }
 
+hyb_status hyb_eval_rate_table(hyb_ctx *c, int table, int sid, int level, const float *x, int n, float *out) {
+    if (!c || !x || !out || n < 0) return set_error(HYB_EINVAL, "bad argument");
+    if (n == 0) return HYB_OK;
+    if (table == HYB_LUT_IONIZE) {
+        if (sid < 0 || sid >= (int)c->sp.size()) return set_error(HYB_EINVAL, "bad species id");
+        return eval_ion_table(c, c->sp[sid].dev, level, x, n, out);
+    }
+    return set_error(HYB_EINVAL, "unknown table");
+}
+
 hyb_status hyb_clear_status(hyb_ctx *c) {
     if (!c) return set_error(HYB_EINVAL, "null context");
     HYB_CUDA_TRY(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream));
@@ -535,6 +579,21 @@ hyb_status hyb_diagnostics(hyb_ctx *c, hyb_diag *out) {
     for (int s = 0; s < set.n; ++s) out->w_kin[s] = r[2 + s];
     out->status = status_to_code(h);
     out->launches_per_step = c->launches_per_step;
+    // ionization tallies: per-tile FP64 accumulators summed here in tile order
+    std::vector<double> te((size_t)c->g.ntiles);
+    std::vector<unsigned long long> tn((size_t)c->g.ntiles);
+    for (int s = 0; s < set.n; ++s) {
+        if (set.s[s].zmax <= 0) continue;
+        HYB_CUDA_TRY(cudaMemcpyAsync(te.data(), set.s[s].ion_energy, sizeof(double) * te.size(),
+                                     cudaMemcpyDeviceToHost, c->stream));
+        HYB_CUDA_TRY(cudaMemcpyAsync(tn.data(), set.s[s].ion_events, sizeof(unsigned long long) * tn.size(),
+                                     cudaMemcpyDeviceToHost, c->stream));
+        HYB_CUDA_TRY(cudaStreamSynchronize(c->stream));
+        for (size_t t = 0; t < te.size(); ++t) {
+            out->w_ionize += te[t];
+            out->n_ionize += (long long)tn[t];
+        }
+    }
     if (h) {
         c->error_latched = true;
         return set_error(status_to_code(h), "device status word set");

@@ -27,6 +27,7 @@ struct GridDev {
     float dt;
     double dd[3];      // dx, dy, dz in FP64 (reductions)
     double dt_d;       // the same step in FP64 (laser phase, time)
+    uint32_t seed;     // Philox key word 0
 };
 
 __host__ __device__ inline long long cidx(const GridDev &g, int i, int j, int k) {
@@ -51,7 +52,22 @@ struct SpDev {
     int *mdest;
     int *mig_count;
     int mig_cap;
+    // field ionization (zmax = 0: none)
+    int zmax;
+    int ion_into;          // species index of the electrons
+    uint32_t sp_index;     // Philox key word 1
+    const float *lnw;      // [zmax][ION_NL] ln of the rate [1/atomic time] on the ln F grid
+    float lnF0, inv_h;     // grid: ln F = lnF0 + i / inv_h
+    float e_ratio;         // |E| (normalised) -> F (atomic units)
+    float dt_au;           // dt in atomic units
+    double ip_mc2[8];      // Ip of state Z in m_e c^2 (energy tally)
+    double *ion_energy;    // per tile: accumulated sum w Ip
+    unsigned long long *ion_events;  // per tile: accumulated events
 };
+
+static constexpr int ION_NL = 8192;       // table points per charge state
+static constexpr double ION_FMIN = 1e-4;  // atomic units
+static constexpr double ION_FMAX = 1e3;
 
 struct SpSet {
     int n;
@@ -104,6 +120,7 @@ struct hyb_ctx {
     int *mig_counts = nullptr;                       // HYB_MAX_SPECIES migration counters
 
     std::vector<hyb::Species> sp;
+    hyb::SpDev *sp_dev = nullptr;  // device copy of the species descriptors (HYB_MAX_SPECIES)
     long long step = 0;
 
     cudaGraphExec_t graph = nullptr;
@@ -144,8 +161,10 @@ void launch_laser_source(const GridDev &g, const hyb_grid_desc &d, const float *
 void launch_step_inc(long long *step_dev, cudaStream_t st);
 
 size_t push_smem_bytes(int T);
-void launch_push_deposit(const GridDev &g, const float *E, const float *B, const SpSet &set,
-                         float *jscratch, int *status, cudaStream_t st);
+void launch_push_deposit(const GridDev &g, const float *E, const float *B, const SpDev *sps_dev, int nsp,
+                         float *jscratch, int *status, const long long *step_dev, cudaStream_t st);
+hyb_status setup_ionization(hyb_ctx *c, SpDev &s, const hyb_species_desc *d);
+hyb_status eval_ion_table(hyb_ctx *c, const SpDev &s, int Z, const float *x_host, int n, float *out_host);
 void launch_j_reduce(const GridDev &g, const float *jscratch, float *J, cudaStream_t st);
 void launch_rebin(const GridDev &g, const SpDev &s, int *status, cudaStream_t st);
 void launch_compact(const GridDev &g, const SpDev &s, cudaStream_t st);

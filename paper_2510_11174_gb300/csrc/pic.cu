@@ -24,8 +24,22 @@
 //   W_x = DS_x (S0_y S0_z + DS_y S0_z/2 + S0_y DS_z/2 + DS_y DS_z/3) (cyclic),
 //   J_x(i+1/2) - J_x(i-1/2) = -q w W_x / (dt dy dz).
 #include "hyb_internal.cuh"
+#include "ionize.cuh"
+#include "philox.cuh"
 
 namespace hyb {
+
+// warp-aggregated slot allocation from a global counter (the active lanes of
+// the calling warp get consecutive slots)
+__device__ __forceinline__ int warp_append(int *counter) {
+    const unsigned mask = __activemask();
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(mask) - 1;
+    int b = 0;
+    if (lane == leader) b = atomicAdd(counter, __popc(mask));
+    b = __shfl_sync(mask, b, leader);
+    return b + __popc(mask & ((1u << lane) - 1u));
+}
 
 __host__ __device__ inline int frame_F(int T) { return T + 2; }  // field frame edge
 __host__ __device__ inline int frame_G(int T) { return T + 3; }  // current frame edge
@@ -91,14 +105,21 @@ __device__ __forceinline__ void shape3(float p, int gbase, float S[3]) {
 }
 
 __global__ void __launch_bounds__(256) k_push_deposit(GridDev g, const float *__restrict__ E,
-                                                      const float *__restrict__ B, SpSet set,
-                                                      float *__restrict__ jscratch, int *__restrict__ status) {
+                                                      const float *__restrict__ B,
+                                                      const SpDev *__restrict__ sps, int nsp,
+                                                      float *__restrict__ jscratch, int *__restrict__ status,
+                                                      const long long *__restrict__ step_dev) {
     extern __shared__ float sm[];
     const int T = g.T, F = frame_F(T), G = frame_G(T);
     const int F3 = F * F * F, G3 = G * G * G;
     float *sf = sm;            // 6 field components, F^3 each
     float *sj = sm + 6 * F3;   // 3 current components, G^3 each
     __shared__ int s_holes;
+    __shared__ double s_ion_e;
+    __shared__ unsigned long long s_ion_n;
+    const long long step = *step_dev;
+    double ion_e = 0.0;
+    int ion_n = 0;
 
     const int t = blockIdx.x;
     const int tx = t % g.nt[0], ty = (t / g.nt[0]) % g.nt[1], tz = t / (g.nt[0] * g.nt[1]);
@@ -125,7 +146,11 @@ __global__ void __launch_bounds__(256) k_push_deposit(GridDev g, const float *__
         }
     }
     for (int l = threadIdx.x; l < 3 * G3; l += blockDim.x) sj[l] = 0.0f;
-    if (threadIdx.x == 0) s_holes = 0;
+    if (threadIdx.x == 0) {
+        s_holes = 0;
+        s_ion_e = 0.0;
+        s_ion_n = 0;
+    }
     __syncthreads();
 
     const float dt = g.dt;
@@ -133,8 +158,8 @@ __global__ void __launch_bounds__(256) k_push_deposit(GridDev g, const float *__
     const float *sEx = sf, *sEy = sf + F3, *sEz = sf + 2 * F3;
     const float *sBx = sf + 3 * F3, *sBy = sf + 4 * F3, *sBz = sf + 5 * F3;
 
-    for (int si = 0; si < set.n; ++si) {
-        const SpDev sp = set.s[si];
+    for (int si = 0; si < nsp; ++si) {
+        const SpDev &sp = sps[si];
         const int n = min(sp.count[t], sp.cap);
         const long long base = (long long)t * sp.cap;
         const float qm_half = 0.5f * dt / sp.m;  // times q_p below
@@ -268,22 +293,47 @@ __global__ void __launch_bounds__(256) k_push_deposit(GridDev g, const float *__
                     }
                 }
                 const int nt = tile_index(g, x1[0], x1[1], x1[2]);
+
+                // ---- field ionization: after the deposit (this step's current
+                // carries the old charge); at most one level per step; the new
+                // electron starts at x^{n+1} with the ion's u and weight
+                float zq_new = sp.zq ? sp.zq[s] : 0.0f;
+                if (sp.zmax > 0 && zq_new < (float)sp.zmax) {
+                    const int Z = (int)zq_new;
+                    const float P = ion_probability(sp, Z, sqrtf(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]));
+                    const uint64_t pid = sp.id[s];
+                    const u32x4 r = philox4x32_10((uint32_t)pid, (uint32_t)(pid >> 32), (uint32_t)step, RNG_IONIZE,
+                                                  g.seed, sp.sp_index);
+                    if (u01f(r.v[0]) < P) {
+                        zq_new = (float)(Z + 1);
+                        ion_e += (double)wgt * sp.ip_mc2[Z];
+                        ion_n += 1;
+                        const SpDev &el = sps[sp.ion_into];
+                        const int m = warp_append(el.mig_count);
+                        if (m < el.mig_cap) {
+                            el.mx[m] = x1[0]; el.my[m] = x1[1]; el.mz[m] = x1[2];
+                            el.mux[m] = u[0]; el.muy[m] = u[1]; el.muz[m] = u[2];
+                            el.mw[m] = wgt;
+                            if (el.zq) el.mzq[m] = 0.0f;
+                            el.mid[m] = (1ULL << 63) | (pid << 3) | (uint64_t)(Z + 1);
+                            el.mdest[m] = nt;
+                        } else {
+                            atomicOr(status, ST_OVERFLOW);
+                        }
+                    }
+                }
+
                 if (nt == t) {
                     sp.x[s] = x1[0]; sp.y[s] = x1[1]; sp.z[s] = x1[2];
                     sp.ux[s] = u[0]; sp.uy[s] = u[1]; sp.uz[s] = u[2];
+                    if (sp.zmax > 0) sp.zq[s] = zq_new;
                 } else {
-                    const unsigned mask = __activemask();
-                    const int lane = threadIdx.x & 31;
-                    const int leader = __ffs(mask) - 1;
-                    int mb = 0;
-                    if (lane == leader) mb = atomicAdd(sp.mig_count, __popc(mask));
-                    mb = __shfl_sync(mask, mb, leader);
-                    const int m = mb + __popc(mask & ((1u << lane) - 1u));
+                    const int m = warp_append(sp.mig_count);
                     if (m < sp.mig_cap) {
                         sp.mx[m] = x1[0]; sp.my[m] = x1[1]; sp.mz[m] = x1[2];
                         sp.mux[m] = u[0]; sp.muy[m] = u[1]; sp.muz[m] = u[2];
                         sp.mw[m] = wgt;
-                        if (sp.zq) sp.mzq[m] = sp.zq[s];
+                        if (sp.zq) sp.mzq[m] = zq_new;
                         sp.mid[m] = sp.id[s];
                         sp.mdest[m] = nt;
                     } else {
@@ -295,11 +345,31 @@ __global__ void __launch_bounds__(256) k_push_deposit(GridDev g, const float *__
                 }
             }
         }
+        if (sp.zmax > 0) {
+            // per-tile ionization tallies: warp sums, then one shared accumulator
+#pragma unroll
+            for (int o2 = 16; o2 > 0; o2 >>= 1) {
+                ion_e += __shfl_down_sync(0xffffffffu, ion_e, o2);
+                ion_n += __shfl_down_sync(0xffffffffu, ion_n, o2);
+            }
+            if ((threadIdx.x & 31) == 0 && ion_n > 0) {
+                atomicAdd(&s_ion_e, ion_e);
+                atomicAdd(&s_ion_n, (unsigned long long)ion_n);
+            }
+            ion_e = 0.0;
+            ion_n = 0;
+        }
         __syncthreads();
         if (threadIdx.x == 0) {
             sp.hole_count[t] = s_holes;
             sp.hole_used[t] = 0;
             s_holes = 0;
+            if (sp.zmax > 0 && s_ion_n > 0) {
+                sp.ion_energy[t] += s_ion_e;
+                sp.ion_events[t] += s_ion_n;
+            }
+            s_ion_e = 0.0;
+            s_ion_n = 0;
         }
         __syncthreads();
     }
@@ -445,10 +515,10 @@ __global__ void k_bin(GridDev g, SpDev sp, long long n, const float *__restrict_
 
 static inline unsigned blocks_for(long long n, int b) { return (unsigned)((n + b - 1) / b); }
 
-void launch_push_deposit(const GridDev &g, const float *E, const float *B, const SpSet &set, float *jscratch,
-                         int *status, cudaStream_t st) {
+void launch_push_deposit(const GridDev &g, const float *E, const float *B, const SpDev *sps_dev, int nsp,
+                         float *jscratch, int *status, const long long *step_dev, cudaStream_t st) {
     const size_t smem = push_smem_bytes(g.T);
-    k_push_deposit<<<g.ntiles, 256, smem, st>>>(g, E, B, set, jscratch, status);
+    k_push_deposit<<<g.ntiles, 256, smem, st>>>(g, E, B, sps_dev, nsp, jscratch, status, step_dev);
 }
 
 void launch_j_reduce(const GridDev &g, const float *jscratch, float *J, cudaStream_t st) {

@@ -30,6 +30,9 @@ def _ptr_and_dev(a, dtype):
         t = a.contiguous()
         if t.dtype != tdt:
             t = t.to(tdt)
+        if t.is_cuda:
+            # the context runs on its own stream: make the producer's work visible
+            torch.cuda.current_stream(t.device).synchronize()
         return t.data_ptr(), t.is_cuda, t
     arr = np.ascontiguousarray(np.asarray(a), dtype=dtype)
     return arr.ctypes.data, False, arr
@@ -63,9 +66,16 @@ class Simulation:
             d.x_src, d.pol = int(laser["x_src"]), int(laser.get("pol", 1))
         d.seed = seed
         d.tile = tile
+        self.torch_stream = None
         if stream is None:
+            # the legacy default stream cannot be captured into a CUDA graph:
+            # run on torch's current stream unless that is the default one
             torch = _torch()
-            stream = torch.cuda.current_stream().cuda_stream
+            cur = torch.cuda.current_stream()
+            if cur.cuda_stream == 0:
+                cur = torch.cuda.Stream()
+            self.torch_stream = cur
+            stream = cur.cuda_stream
         d.stream = stream
         self._arena = arena
         if arena is not None:
@@ -98,9 +108,17 @@ class Simulation:
         self.close()
 
     # ------------------------------------------------------------------ set-up
-    def load_species(self, q, m, x, y, z, ux, uy, uz, w, zq=None, ids=None, tile_capacity=0):
+    def load_species(self, q, m, x, y, z, ux, uy, uz, w, zq=None, ids=None, tile_capacity=0, ionize=None):
+        """Add a species; returns its id.  ``ionize`` = dict(zmax, ip_eV, l, into)
+        makes it field-ionizable (zq = charge states required)."""
         d = _abi.hyb_species_desc()
         d.q, d.m = q, m
+        if ionize:
+            d.zmax = int(ionize["zmax"])
+            for z in range(d.zmax):
+                d.ip_eV[z] = float(ionize["ip_eV"][z])
+                d.l_qn[z] = int(ionize["l"][z])
+            d.ionize_into = int(ionize["into"])
         keep = []
         ptrs = []
         on_dev = None
@@ -158,7 +176,16 @@ class Simulation:
         ns = out.n_species
         return {"step": out.step, "time": out.time, "w_e": out.w_e, "w_b": out.w_b,
                 "w_kin": [out.w_kin[i] for i in range(ns)], "count": [out.count[i] for i in range(ns)],
-                "status": out.status, "launches_per_step": out.launches_per_step}
+                "status": out.status, "launches_per_step": out.launches_per_step,
+                "w_ionize": out.w_ionize, "n_ionize": out.n_ionize}
+
+    def eval_rate_table(self, table, species_id, level, x):
+        """Evaluate a device rate table at the points x (see hyb_eval_rate_table)."""
+        xa = np.ascontiguousarray(x, dtype=np.float32)
+        out = np.empty_like(xa)
+        check(self._lib.hyb_eval_rate_table(self._ctx, int(table), int(species_id), int(level),
+                                            xa.ctypes.data, len(xa), out.ctypes.data))
+        return out
 
     def get_fields(self):
         E = np.empty((3,) + self.shape, np.float32)
