@@ -12,6 +12,7 @@ The arithmetic lives in the C files next to this module (compiled with gcc
 into ``liboracle.so``); this module only marshals numpy arrays.
 """
 import ctypes as C
+import math
 import os
 
 import numpy as np
@@ -91,6 +92,33 @@ def _declare(L):
     L.orc_ionize.argtypes = [C.POINTER(Species), _P, C.c_int, _P, _P, C.c_double, C.c_double, C.c_double,
                              C.c_uint32, C.c_uint32, C.c_long, C.POINTER(Species), C.c_long, _P]
     L.orc_ionize.restype = C.c_long
+    for nm in ("orc_bessel_k", "orc_bessel_k_int"):
+        getattr(L, nm).argtypes = [C.c_double, C.c_double]
+        getattr(L, nm).restype = C.c_double
+    for nm in ("orc_airy_ai", "orc_airy_aip", "orc_airy_int"):
+        getattr(L, nm).argtypes = [C.c_double]
+        getattr(L, nm).restype = C.c_double
+    for nm in ("orc_qed_h", "orc_qed_power", "orc_qed_T"):
+        getattr(L, nm).argtypes = [C.c_double]
+        getattr(L, nm).restype = C.c_double
+    for nm in ("orc_qed_em_density", "orc_qed_pair_density", "orc_qed_em_sample", "orc_qed_pair_sample"):
+        getattr(L, nm).argtypes = [C.c_double, C.c_double]
+        getattr(L, nm).restype = C.c_double
+    L.orc_chi.argtypes = [C.c_double, _P, _P, _P, C.c_int]
+    L.orc_chi.restype = C.c_double
+    L.orc_splitmix64.argtypes = [C.c_uint64]
+    L.orc_splitmix64.restype = C.c_uint64
+    L.orc_derived_id.argtypes = [C.c_uint64, C.c_long, C.c_uint]
+    L.orc_derived_id.restype = C.c_uint64
+    L.orc_qed_tau0.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32]
+    L.orc_qed_tau0.restype = C.c_double
+    L.orc_qed_emit.argtypes = [C.POINTER(Species), _P, C.c_double, C.c_double, C.c_double, C.c_uint32, C.c_uint32,
+                               C.c_long, C.POINTER(Species), _P, C.c_long, _P]
+    L.orc_qed_emit.restype = C.c_long
+    L.orc_photon_move.argtypes = [C.POINTER(Grid), C.POINTER(Species)]
+    L.orc_qed_pairs.argtypes = [C.POINTER(Species), _P, _P, C.c_double, C.c_double, C.c_uint32, C.c_uint32, C.c_long,
+                                C.POINTER(Species), _P, C.POINTER(Species), _P, C.c_long, _P]
+    L.orc_qed_pairs.restype = C.c_long
     for name, fn in _EXTRA_DECLS:
         fn(L)
 
@@ -302,3 +330,123 @@ def ionize(ions, zmax, Ip_eV, lq, lambda_m, dt_norm, seed, sp_index, step):
     out.select(np.arange(n))
     # Hartree -> m_e c^2
     return out, en[0] * HARTREE_EV / 510998.95
+
+
+# --------------------------------------------------------------------------- Airy
+def bessel_k(nu, x):
+    return lib().orc_bessel_k(float(nu), float(x))
+
+
+def bessel_k_int(nu, x):
+    return lib().orc_bessel_k_int(float(nu), float(x))
+
+
+def airy_ai(z):
+    return lib().orc_airy_ai(float(z))
+
+
+def airy_aip(z):
+    return lib().orc_airy_aip(float(z))
+
+
+def airy_int(z):
+    """int_z^inf Ai(t) dt, z >= 0."""
+    return lib().orc_airy_int(float(z))
+
+
+# --------------------------------------------------------------------------- QED (LCFA)
+ALPHA = 7.2973525693e-3
+
+
+def qed_kappa(lambda_m):
+    """hbar w0 / (m c^2) = E_ref / E_s for the laser wavelength."""
+    hbar, me, c = 1.054571817e-34, 9.1093837015e-31, 299792458.0
+    return hbar * 2 * math.pi * c / lambda_m / (me * c * c)
+
+
+def qed_h(chi):
+    return lib().orc_qed_h(float(chi))
+
+
+def qed_power(chi):
+    return lib().orc_qed_power(float(chi))
+
+
+def qed_T(chi):
+    return lib().orc_qed_T(float(chi))
+
+
+def qed_em_density(chi, xi):
+    return lib().orc_qed_em_density(float(chi), float(xi))
+
+
+def qed_pair_density(chi, xi):
+    return lib().orc_qed_pair_density(float(chi), float(xi))
+
+
+def qed_em_sample(chi, r):
+    return lib().orc_qed_em_sample(float(chi), float(r))
+
+
+def qed_pair_sample(chi, r):
+    return lib().orc_qed_pair_sample(float(chi), float(r))
+
+
+def chi_param(kappa, e, b, u, photon=False):
+    e = np.ascontiguousarray(e, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    return lib().orc_chi(float(kappa), _ptr(e), _ptr(b), _ptr(u), int(photon))
+
+
+def derived_id(pid, step, tag):
+    return lib().orc_derived_id(int(pid), int(step), int(tag))
+
+
+def qed_tau0(ids, seed, sp_index):
+    return np.array([lib().orc_qed_tau0(int(i), int(seed) & 0xFFFFFFFF, int(sp_index)) for i in ids])
+
+
+def _empty(n, q, m):
+    out = Particles(q, m, *([np.zeros(n)] * 7))
+    out.ids = np.zeros(n, dtype=np.uint64)
+    return out
+
+
+def qed_emit(sp, kappa, dt, eps_min, seed, sp_index, step):
+    """Emission pass over `sp` (uses sp.eb and sp.tau).  Returns
+    (photon Particles with .tau, energy of photons not kept, number of events)."""
+    cap = sp.n
+    ph = _empty(cap, 0.0, 0.0)
+    ph_tau = np.zeros(cap)
+    tal = np.zeros(2)
+    s, so = sp.cstruct(), ph.cstruct()
+    n = lib().orc_qed_emit(C.byref(s), _ptr(sp.tau), float(kappa), float(dt), float(eps_min),
+                           int(seed) & 0xFFFFFFFF, int(sp_index), int(step), C.byref(so), _ptr(ph_tau), cap, _ptr(tal))
+    ph.select(np.arange(n))
+    ph.tau = np.ascontiguousarray(ph_tau[:n])
+    return ph, tal[0], int(tal[1])
+
+
+def photon_move(g, sp):
+    s = sp.cstruct()
+    lib().orc_photon_move(C.byref(g), C.byref(s))
+
+
+def qed_pairs(ph, kappa, dt, seed, sp_index, step):
+    """Pair pass over photons (uses ph.eb, ph.tau); removes converted photons.
+    Returns (electrons, positrons, energy deficit, events)."""
+    cap = ph.n
+    el, po = _empty(cap, -1.0, 1.0), _empty(cap, 1.0, 1.0)
+    el_tau, po_tau = np.zeros(cap), np.zeros(cap)
+    alive = np.ones(cap, dtype=np.uint8)
+    tal = np.zeros(2)
+    s, se, sq = ph.cstruct(), el.cstruct(), po.cstruct()
+    n = lib().orc_qed_pairs(C.byref(s), _ptr(ph.tau), _ptr(alive), float(kappa), float(dt), int(seed) & 0xFFFFFFFF,
+                            int(sp_index), int(step), C.byref(se), _ptr(el_tau), C.byref(sq), _ptr(po_tau), cap,
+                            _ptr(tal))
+    for o, t in ((el, el_tau), (po, po_tau)):
+        o.select(np.arange(n))
+        o.tau = np.ascontiguousarray(t[:n])
+    ph.select(alive.astype(bool))
+    return el, po, tal[0], int(tal[1])

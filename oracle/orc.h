@@ -79,6 +79,30 @@ long orc_ionize(orc_species *ions, const double *eb, int zmax, const double *Ip_
                 double w0_au, double Eref_over_Ea, double dt_au, uint32_t seed, uint32_t sp_index, long step,
                 orc_species *out, long cap, double *energy_au);
 
+/* ---- Airy functions (z >= 0) and LCFA QED rates ---------------------------- */
+double orc_bessel_k(double nu, double x);
+double orc_bessel_k_int(double nu, double x);
+double orc_airy_ai(double z);
+double orc_airy_aip(double z);
+double orc_airy_int(double z);
+double orc_qed_em_density(double chi, double xi);
+double orc_qed_pair_density(double chi, double xi);
+double orc_qed_h(double chi);
+double orc_qed_power(double chi);
+double orc_qed_T(double chi);
+double orc_qed_em_sample(double chi, double r);
+double orc_qed_pair_sample(double chi, double r);
+double orc_chi(double kappa, const double e[3], const double b[3], const double u[3], int photon);
+uint64_t orc_splitmix64(uint64_t x);
+uint64_t orc_derived_id(uint64_t id, long step, unsigned tag);
+double orc_qed_tau0(uint64_t id, uint32_t seed, uint32_t sp_index);
+long orc_qed_emit(orc_species *s, double *tau, double kappa, double dt, double eps_min, uint32_t seed,
+                  uint32_t sp_index, long step, orc_species *ph, double *ph_tau, long cap, double *tallies);
+void orc_photon_move(const orc_grid *g, orc_species *s);
+long orc_qed_pairs(orc_species *s, double *tau, unsigned char *alive, double kappa, double dt, uint32_t seed,
+                   uint32_t sp_index, long step, orc_species *el, double *el_tau, orc_species *po, double *po_tau,
+                   long cap, double *tallies);
+
 /* ---- diagnostics --------------------------------------------------------- */
 void orc_energy_fields(const orc_grid *g, const double *E[3], const double *B[3], double out[2]);
 double orc_energy_particles(const orc_species *s);
