@@ -123,7 +123,9 @@ def run_ours(args, rank, world):
     build.build()
     dev = int(os.environ.get("LOCAL_RANK", 0))
     torch.cuda.set_device(dev)
-    stream = torch.cuda.current_stream()
+    # a capturable (non-default) stream shared by the library, the L2 flush and the events
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
     inp = workloads()[args.workload](1 + rank)
     g = inp["grid"]
     cells = g["nx"] * g["ny"] * g["nz"]

@@ -111,7 +111,25 @@ typedef struct {
     double ip_eV[8];
     int l_qn[8];
     int ionize_into;
+    /* Strong-field QED (paper, Methodology: radiation reaction and pair
+     * production from Airy-function rates with the local field).  kind =
+     * HYB_KIND_PHOTON makes a photon species (q = 0, u holds the momentum k
+     * in m c, moves at c).  qed = 1 on a lepton species turns on photon
+     * emission with recoil (optical-depth Monte Carlo, LCFA spectrum);
+     * photons of energy >= photon_eps_min [m c^2] (0 = 2) join species
+     * photon_species (-1: their energy is only tallied).  On a photon
+     * species, pair_electron / pair_positron (-1: none) receive Breit-Wheeler
+     * pairs.  Rates and spectra come from FP64-built tables on the device;
+     * events use Philox counters (id, step, 2) for emission and (id, step, 3)
+     * for pairs. */
+    int kind;
+    int qed;
+    int photon_species;
+    double photon_eps_min;
+    int pair_electron, pair_positron;
 } hyb_species_desc;
+
+enum { HYB_KIND_MASSIVE = 0, HYB_KIND_PHOTON = 1 };
 
 /* Diagnostics: FP64 energy reductions (paper, Methodology: total energy from
  * electromagnetic, kinetic and thermal components) and device status. */
@@ -127,6 +145,10 @@ typedef struct {
     long long launches_per_step;           /* kernels one step launches */
     double w_ionize;                       /* energy spent on ionization so far, sum w Ip */
     long long n_ionize;                    /* ionization events so far */
+    double w_photon_untracked;             /* energy of emitted photons below the tracking threshold */
+    double w_pair_deficit;                 /* pair energy below m c^2 that could not become momentum */
+    long long n_emit;                      /* photon emission events so far */
+    long long n_pair;                      /* pair creation events so far */
 } hyb_diag;
 
 /* Create a context: validates the descriptor, allocates fields on the
@@ -192,6 +214,16 @@ hyb_status hyb_phase_times(hyb_ctx *ctx, hyb_phase_times_t *out);
 enum { HYB_LUT_IONIZE = 0 };
 hyb_status hyb_eval_rate_table(hyb_ctx *ctx, int table, int species_id, int level, const float *x_host, int n,
                                float *out_host);
+
+/* Evaluate the device QED tables the way the step does, for n points:
+ * what = HYB_QED_H: h(chi) (photon emission rate = alpha/kappa * h / gamma);
+ * HYB_QED_T: T(chi) (pair rate = alpha/kappa * T / eps); HYB_QED_EM_SAMPLE:
+ * the photon energy fraction xi drawn for (chi, r); HYB_QED_PAIR_SAMPLE: the
+ * electron energy fraction for (chi, r).  chi_host, r_host (r only for the
+ * samplers) and out_host hold n values; synchronises.  The tables are built
+ * on first use (or by a QED species load). */
+enum { HYB_QED_H = 0, HYB_QED_T = 1, HYB_QED_EM_SAMPLE = 2, HYB_QED_PAIR_SAMPLE = 3 };
+hyb_status hyb_eval_qed(hyb_ctx *ctx, int what, const float *chi_host, const float *r_host, int n, float *out_host);
 
 /* Message for the last failing call on this thread (never NULL). */
 const char *hyb_last_error(void);

@@ -116,6 +116,7 @@ def _declare(L):
                                C.c_long, C.POINTER(Species), _P, C.c_long, _P]
     L.orc_qed_emit.restype = C.c_long
     L.orc_photon_move.argtypes = [C.POINTER(Grid), C.POINTER(Species)]
+    L.orc_gather_species.argtypes = [C.POINTER(Grid), _D3, _D3, C.POINTER(Species)]
     L.orc_qed_pairs.argtypes = [C.POINTER(Species), _P, _P, C.c_double, C.c_double, C.c_uint32, C.c_uint32, C.c_long,
                                 C.POINTER(Species), _P, C.POINTER(Species), _P, C.c_long, _P]
     L.orc_qed_pairs.restype = C.c_long
@@ -426,6 +427,13 @@ def qed_emit(sp, kappa, dt, eps_min, seed, sp_index, step):
     ph.select(np.arange(n))
     ph.tau = np.ascontiguousarray(ph_tau[:n])
     return ph, tal[0], int(tal[1])
+
+
+def gather_species(g, E, B, sp):
+    """Fill sp.eb with E, B at the particle positions."""
+    sp.eb = np.zeros((sp.n, 6))
+    s = sp.cstruct()
+    lib().orc_gather_species(C.byref(g), _f3(E), _f3(B), C.byref(s))
 
 
 def photon_move(g, sp):

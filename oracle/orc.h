@@ -68,6 +68,7 @@ void orc_esirkepov(const orc_grid *g, double qw, double x0, double y0, double z0
                    double x1, double y1, double z1, double *J[3]);
 void orc_push_deposit(const orc_grid *g, const double *E[3], const double *B[3],
                       double *J[3], orc_species *s);
+void orc_gather_species(const orc_grid *g, const double *E[3], const double *B[3], orc_species *s);
 
 /* ---- ionization ----------------------------------------------------------- */
 double orc_adk_rate(double F, double Ip, double Z, int l, int m);

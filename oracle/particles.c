@@ -179,3 +179,13 @@ void orc_push_deposit(const orc_grid *g, const double *E[3], const double *B[3],
         s->ux[p] = u[0]; s->uy[p] = u[1]; s->uz[p] = u[2];
     }
 }
+
+/* Record E^n, B^n at the particles' positions into s->eb (photons: the
+ * fields that drive pair creation, gathered before the photon moves). */
+void orc_gather_species(const orc_grid *g, const double *E[3], const double *B[3], orc_species *s) {
+    for (long p = 0; p < s->n; ++p) {
+        double e[3], b[3];
+        orc_gather(g, E, B, s->x[p], s->y[p], s->z[p], e, b);
+        for (int c = 0; c < 3; ++c) { s->eb[6 * p + c] = e[c]; s->eb[6 * p + 3 + c] = b[c]; }
+    }
+}

@@ -25,8 +25,9 @@
  * z = exp(2 mu / 3) exactly and the spectrum lives in mu in [-30, 5] for
  * every chi; below mu = -30 the integrand is 2 |Ai'(0)| / z (the small-xi
  * limit) and is integrated in closed form.  Composite 8-point Gauss-Legendre
- * panels of width 1/4.  Pair integrals: xi in (0, 1/2] (the spectrum is
- * symmetric), panels of width 1/200.
+ * panels of width 1/4.  Pair integrals: over t = ln(xi/(1 - xi)) in
+ * [-30, 0] (xi in (0, 1/2], the spectrum is symmetric; for chi >> 1 it
+ * extends down to xi ~ 1/chi), panels of width 1/8.
  *
  * Monte Carlo (one event per particle per step at most):
  *   lepton: tau -= W_em dt; when tau <= 0, a Philox draw (counter
@@ -102,18 +103,26 @@ static double em_integral(double chi, int p) {
 double orc_qed_h(double chi) { return chi > 0.0 ? em_integral(chi, 0) : 0.0; }
 double orc_qed_power(double chi) { return chi > 0.0 ? em_integral(chi, 1) : 0.0; }
 
+/* pair integrand in t = ln(xi/(1-xi)): F_pair(xi) dxi/dt */
+static double pair_t(double chi, double t) {
+    const double xi = 1.0 / (1.0 + exp(-t));
+    return orc_qed_pair_density(chi, xi) * xi * (1.0 - xi);
+}
+
 static double pair_panel(double chi, double a, double b) {
     const double hm = 0.5 * (b - a), cm = 0.5 * (b + a);
     double s = 0.0;
-    for (int k = 0; k < 8; ++k) s += GL_W[k] * orc_qed_pair_density(chi, cm + hm * GL_X[k]);
+    for (int k = 0; k < 8; ++k) s += GL_W[k] * pair_t(chi, cm + hm * GL_X[k]);
     return s * hm;
 }
 
-#define PAIR_PANELS 100
+#define PAIR_T0 (-30.0)
+#define PAIR_PANELS 240  /* width 1/8 over [-30, 0] */
 double orc_qed_T(double chi) {
     if (!(chi > 0.0)) return 0.0;
+    const double w = -PAIR_T0 / PAIR_PANELS;
     double s = 0.0;
-    for (int i = 0; i < PAIR_PANELS; ++i) s += pair_panel(chi, 0.5 * i / PAIR_PANELS, 0.5 * (i + 1) / PAIR_PANELS);
+    for (int i = 0; i < PAIR_PANELS; ++i) s += pair_panel(chi, PAIR_T0 + i * w, PAIR_T0 + (i + 1) * w);
     return 2.0 * s;
 }
 
@@ -144,13 +153,14 @@ double orc_qed_em_sample(double chi, double r) {
     return e / (1.0 + e);
 }
 
-/* invert the cumulative pair spectrum over (0, 1) */
+/* invert the cumulative pair spectrum over (0, 1) (t from -30 to 30) */
 double orc_qed_pair_sample(double chi, double r) {
     const double total = orc_qed_T(chi);
     const double target = r * total;
+    const double w = -PAIR_T0 / PAIR_PANELS;
     double acc = 0.0;
     for (int i = 0; i < 2 * PAIR_PANELS; ++i) {
-        const double a = 0.5 * i / PAIR_PANELS, b = 0.5 * (i + 1) / PAIR_PANELS;
+        const double a = PAIR_T0 + i * w, b = a + w;
         const double pv = pair_panel(chi, a, b);
         if (acc + pv >= target || i == 2 * PAIR_PANELS - 1) {
             double lo = a, hi = b;
@@ -158,7 +168,7 @@ double orc_qed_pair_sample(double chi, double r) {
                 const double mid = 0.5 * (lo + hi);
                 if (acc + pair_panel(chi, a, mid) < target) lo = mid; else hi = mid;
             }
-            return 0.5 * (lo + hi);
+            return 1.0 / (1.0 + exp(-0.5 * (lo + hi)));
         }
         acc += pv;
     }

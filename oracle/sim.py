@@ -16,8 +16,8 @@ import math
 
 import numpy as np
 
-from . import (Grid, Particles, energy_fields, energy_particles, fdtd_b_half, fdtd_e, ionize, laser_source,
-               push_deposit, zeros_field)
+from . import (Grid, Particles, energy_fields, energy_particles, fdtd_b_half, fdtd_e, gather_species, ionize,
+               laser_source, photon_move, push_deposit, qed_emit, qed_kappa, qed_pairs, qed_tau0, zeros_field)
 
 
 def courant_dt(d, cfl_frac):
@@ -41,14 +41,29 @@ class OracleSim:
         self.seed = seed
         self.species = []
         self.ionize_cfg = []
+        self.kind = []
+        self.qed_cfg = []
+        self.pair_cfg = []
         self.w_ionize = 0.0
         self.n_ionize = 0
+        self.w_photon_untracked = 0.0
+        self.w_pair_deficit = 0.0
+        self.n_emit = 0
+        self.n_pair = 0
         self.nstep = 0
 
-    def load_species(self, q, m, x, y, z, ux, uy, uz, w, zq=None, ids=None, ionize=None, **_):
-        self.species.append(Particles(q, m, x, y, z, ux, uy, uz, w, zq=zq, ids=ids))
+    def load_species(self, q, m, x, y, z, ux, uy, uz, w, zq=None, ids=None, ionize=None, kind=0, qed=None,
+                     pairs=None, **_):
+        sid = len(self.species)
+        sp = Particles(q, m, x, y, z, ux, uy, uz, w, zq=zq, ids=ids)
+        if qed or pairs:
+            sp.tau = qed_tau0(sp.ids, self.seed, sid)
+        self.species.append(sp)
         self.ionize_cfg.append(ionize)
-        return len(self.species) - 1
+        self.kind.append(int(kind))
+        self.qed_cfg.append(qed)
+        self.pair_cfg.append(pairs)
+        return sid
 
     def set_fields(self, E, B):
         self.E[:] = np.asarray(E, dtype=np.float64)
@@ -58,20 +73,57 @@ class OracleSim:
         g = self.g
         for _ in range(n):
             self.J[:] = 0.0
-            for sp, ion in zip(self.species, self.ionize_cfg):
-                sp.eb = np.zeros((sp.n, 6)) if ion else None
-                push_deposit(g, self.E, self.B, self.J, sp)
-            # field ionization with E^n at x^n (recorded by the push); new electrons
-            # start at x^{n+1} and are not pushed before the next step
-            for si, (sp, ion) in enumerate(zip(self.species, self.ionize_cfg)):
-                if not ion:
+            for si, sp in enumerate(self.species):
+                if self.kind[si] == 1:
+                    # photons: fields at x^n for pair creation, then a straight move at c
+                    if self.pair_cfg[si]:
+                        gather_species(g, self.E, self.B, sp)
+                    photon_move(g, sp)
                     continue
-                new, en = ionize(sp, ion["zmax"], ion["ip_eV"], ion["l"], self.lambda_m, g.dt, self.seed, si,
-                                 self.nstep)
-                self.species[ion["into"]].append(new)
-                self.w_ionize += en
-                self.n_ionize += new.n
+                sp.eb = np.zeros((sp.n, 6)) if (self.ionize_cfg[si] or self.qed_cfg[si]) else None
+                push_deposit(g, self.E, self.B, self.J, sp)
+            # stochastic events on the pushed particles (E^n, B^n at x^n, u^{n+1/2});
+            # every new particle starts at x^{n+1} and joins its species after all
+            # events of the step, so none of them is pushed or converted this step
+            spawned = [[] for _ in self.species]
+            kappa = qed_kappa(self.lambda_m)
+            for si, sp in enumerate(self.species):
+                ion = self.ionize_cfg[si]
+                if ion:
+                    new, en = ionize(sp, ion["zmax"], ion["ip_eV"], ion["l"], self.lambda_m, g.dt, self.seed, si,
+                                     self.nstep)
+                    if self.qed_cfg[ion["into"]] or self.pair_cfg[ion["into"]]:
+                        new.tau = qed_tau0(new.ids, self.seed, ion["into"])
+                    spawned[ion["into"]].append(new)
+                    self.w_ionize += en
+                    self.n_ionize += new.n
+                qc = self.qed_cfg[si]
+                if qc:
+                    eps_min = qc.get("eps_min", 0.0) or 2.0
+                    ph, lost, ev = qed_emit(sp, kappa, g.dt, eps_min, self.seed, si, self.nstep)
+                    self.n_emit += ev
+                    target = qc.get("photon_species", -1)
+                    if target is not None and target >= 0:
+                        spawned[target].append(ph)
+                        self.w_photon_untracked += lost
+                    else:
+                        self.w_photon_untracked += lost + float(np.sum(ph.w * np.sqrt(ph.ux ** 2 + ph.uy ** 2 +
+                                                                                       ph.uz ** 2)))
+                pc = self.pair_cfg[si]
+                if pc:
+                    el, po, deficit, ev = qed_pairs(sp, kappa, g.dt, self.seed, si, self.nstep)
+                    spawned[pc["electron"]].append(el)
+                    spawned[pc["positron"]].append(po)
+                    self.w_pair_deficit += deficit
+                    self.n_pair += ev
                 sp.eb = None
+            for si, lst in enumerate(spawned):
+                for new in lst:
+                    if self.species[si].tau is not None and new.tau is None:
+                        new.tau = qed_tau0(new.ids, self.seed, si)
+                    if self.species[si].tau is None:
+                        new.tau = None
+                    self.species[si].append(new)
             if self.laser:
                 L = self.laser
                 laser_source(g, self.J, self.nstep, L["x_src"], L.get("pol", 1), L["a0"], L["tau_fwhm"],
@@ -83,6 +135,9 @@ class OracleSim:
 
     def diagnostics(self):
         we, wb = energy_fields(self.g, self.E, self.B)
-        return {"step": self.nstep, "w_e": we, "w_b": wb,
-                "w_kin": [energy_particles(sp) for sp in self.species],
-                "count": [sp.n for sp in self.species], "w_ionize": self.w_ionize, "n_ionize": self.n_ionize}
+        w_kin = [float(np.sum(sp.w * np.sqrt(sp.ux ** 2 + sp.uy ** 2 + sp.uz ** 2))) if k == 1
+                 else energy_particles(sp) for sp, k in zip(self.species, self.kind)]
+        return {"step": self.nstep, "w_e": we, "w_b": wb, "w_kin": w_kin,
+                "count": [sp.n for sp in self.species], "w_ionize": self.w_ionize, "n_ionize": self.n_ionize,
+                "w_photon_untracked": self.w_photon_untracked, "w_pair_deficit": self.w_pair_deficit,
+                "n_emit": self.n_emit, "n_pair": self.n_pair}

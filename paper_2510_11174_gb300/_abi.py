@@ -17,6 +17,8 @@ STATUS_NAMES = {0: "HYB_OK", 1: "HYB_EINVAL", 2: "HYB_ENOMEM", 3: "HYB_ECUDA", 4
 HYB_BC_PERIODIC, HYB_BC_MUR = 0, 1
 HYB_LASER_NONE, HYB_LASER_GAUSS = 0, 1
 HYB_LUT_IONIZE = 0
+HYB_KIND_MASSIVE, HYB_KIND_PHOTON = 0, 1
+HYB_QED_H, HYB_QED_T, HYB_QED_EM_SAMPLE, HYB_QED_PAIR_SAMPLE = 0, 1, 2, 3
 HYB_MAX_SPECIES = 8
 
 
@@ -40,7 +42,9 @@ class hyb_species_desc(C.Structure):
                 ("ux", C.c_void_p), ("uy", C.c_void_p), ("uz", C.c_void_p), ("w", C.c_void_p),
                 ("zq", C.c_void_p), ("ids", C.c_void_p),
                 ("zmax", C.c_int), ("ip_eV", C.c_double * 8), ("l_qn", C.c_int * 8),
-                ("ionize_into", C.c_int)]
+                ("ionize_into", C.c_int),
+                ("kind", C.c_int), ("qed", C.c_int), ("photon_species", C.c_int),
+                ("photon_eps_min", C.c_double), ("pair_electron", C.c_int), ("pair_positron", C.c_int)]
 
 
 class hyb_diag(C.Structure):
@@ -50,7 +54,9 @@ class hyb_diag(C.Structure):
                 ("count", C.c_longlong * HYB_MAX_SPECIES),
                 ("n_species", C.c_int), ("status", C.c_int),
                 ("launches_per_step", C.c_longlong),
-                ("w_ionize", C.c_double), ("n_ionize", C.c_longlong)]
+                ("w_ionize", C.c_double), ("n_ionize", C.c_longlong),
+                ("w_photon_untracked", C.c_double), ("w_pair_deficit", C.c_double),
+                ("n_emit", C.c_longlong), ("n_pair", C.c_longlong)]
 
 
 HYB_NPHASE = 8
@@ -79,6 +85,7 @@ PROTOTYPES = {
     "hyb_set_profiling": (C.c_int, [_ctx, C.c_int]),
     "hyb_phase_times": (C.c_int, [_ctx, C.POINTER(hyb_phase_times_t)]),
     "hyb_eval_rate_table": (C.c_int, [_ctx, C.c_int, C.c_int, C.c_int, _P, C.c_int, _P]),
+    "hyb_eval_qed": (C.c_int, [_ctx, C.c_int, _P, _P, C.c_int, _P]),
 }
 
 _lib = None

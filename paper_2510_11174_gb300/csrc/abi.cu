@@ -79,7 +79,7 @@ static void enqueue_step(hyb_ctx *c) {
     cudaMemsetAsync(c->mig_counts, 0, sizeof(int) * HYB_MAX_SPECIES, st);
     if (set.n > 0) {
         pm.begin(HYB_PH_PUSH);
-        launch_push_deposit(g, c->E, c->B, c->sp_dev, set.n, c->jscratch, c->status, c->step_dev, st);
+        launch_push_deposit(g, c->E, c->B, c->sp_dev, set.n, c->qed, c->jscratch, c->status, c->step_dev, st);
         pm.end(HYB_PH_PUSH);
         pm.begin(HYB_PH_JREDUCE);
         launch_j_reduce(g, c->jscratch, c->J, st);
@@ -249,7 +249,7 @@ void hyb_destroy(hyb_ctx *c) {
     delete c;
 }
 
-static hyb_status alloc_species(hyb_ctx *c, Species &sp, int cap, bool has_zq) {
+static hyb_status alloc_species(hyb_ctx *c, Species &sp, int cap, bool has_zq, bool has_tau) {
     const GridDev &g = c->g;
     const size_t slots = (size_t)cap * g.ntiles;
     SpDev &s = sp.dev;
@@ -262,19 +262,24 @@ static hyb_status alloc_species(hyb_ctx *c, Species &sp, int cap, bool has_zq) {
     for (auto f : fl)
         if (ctx_alloc(c, (void **)f, sizeof(float) * slots)) return HYB_ENOMEM;
     if (has_zq && ctx_alloc(c, (void **)&s.zq, sizeof(float) * slots)) return HYB_ENOMEM;
+    if (has_tau && ctx_alloc(c, (void **)&s.tau, sizeof(float) * slots)) return HYB_ENOMEM;
     if (ctx_alloc(c, (void **)&s.id, sizeof(uint64_t) * slots)) return HYB_ENOMEM;
+    if (ctx_alloc(c, (void **)&s.tal_e, sizeof(double) * NTALLY * g.ntiles) ||
+        ctx_alloc(c, (void **)&s.tal_n, sizeof(unsigned long long) * NTALLY * g.ntiles))
+        return HYB_ENOMEM;
     if (ctx_alloc(c, (void **)&s.count, sizeof(int) * g.ntiles) ||
         ctx_alloc(c, (void **)&s.hole_count, sizeof(int) * g.ntiles) ||
         ctx_alloc(c, (void **)&s.hole_used, sizeof(int) * g.ntiles) ||
         ctx_alloc(c, (void **)&s.holes, sizeof(int) * slots))
         return HYB_ENOMEM;
     // a particle moves less than one cell per step, so only the shell of a tile can leave it
-    const long long mig = std::min<long long>((long long)slots, std::max<long long>(65536, (long long)slots * 3 / 4));
+    const long long mig = std::min<long long>((long long)slots, std::max<long long>(65536, (long long)slots / 2));
     s.mig_cap = (int)std::min<long long>(mig, 0x7fffffffLL);
     float **ml[7] = {&s.mx, &s.my, &s.mz, &s.mux, &s.muy, &s.muz, &s.mw};
     for (auto f : ml)
         if (ctx_alloc(c, (void **)f, sizeof(float) * s.mig_cap)) return HYB_ENOMEM;
     if (has_zq && ctx_alloc(c, (void **)&s.mzq, sizeof(float) * s.mig_cap)) return HYB_ENOMEM;
+    if (has_tau && ctx_alloc(c, (void **)&s.mtau, sizeof(float) * s.mig_cap)) return HYB_ENOMEM;
     if (ctx_alloc(c, (void **)&s.mid, sizeof(uint64_t) * s.mig_cap) ||
         ctx_alloc(c, (void **)&s.mdest, sizeof(int) * s.mig_cap))
         return HYB_ENOMEM;
@@ -282,23 +287,71 @@ static hyb_status alloc_species(hyb_ctx *c, Species &sp, int cap, bool has_zq) {
     cudaMemsetAsync(s.count, 0, sizeof(int) * g.ntiles, c->stream);
     cudaMemsetAsync(s.hole_count, 0, sizeof(int) * g.ntiles, c->stream);
     cudaMemsetAsync(s.hole_used, 0, sizeof(int) * g.ntiles, c->stream);
+    cudaMemsetAsync(s.tal_e, 0, sizeof(double) * NTALLY * g.ntiles, c->stream);
+    cudaMemsetAsync(s.tal_n, 0, sizeof(unsigned long long) * NTALLY * g.ntiles, c->stream);
+    return HYB_OK;
+}
+
+// fill the species' kind / QED fields from its descriptor
+static void species_flags(SpDev &s, const hyb_species_desc *d, int sid) {
+    s.kind = d->kind;
+    s.qed = d->qed;
+    s.ph_species = d->qed ? d->photon_species : -1;
+    s.eps_min = d->photon_eps_min > 0.0 ? (float)d->photon_eps_min : 2.0f;
+    s.pair_e = d->kind == HYB_KIND_PHOTON ? d->pair_electron : -1;
+    s.pair_p = d->kind == HYB_KIND_PHOTON ? d->pair_positron : -1;
+    s.tau_index = (uint32_t)sid;
+    s.sp_index = (uint32_t)sid;
+}
+
+static bool needs_tau(const hyb_species_desc *d) {
+    return d->qed || (d->kind == HYB_KIND_PHOTON && d->pair_electron >= 0);
+}
+
+// cross-species references must name loaded species of the right kind
+static hyb_status validate_links(const hyb_ctx *c) {
+    const int ns = (int)c->sp.size();
+    auto lepton = [&](int i, double q) {
+        return i >= 0 && i < ns && c->sp[i].dev.kind == HYB_KIND_MASSIVE && c->sp[i].q == q && c->sp[i].m == 1.0 &&
+               !c->sp[i].has_zq;
+    };
+    for (int i = 0; i < ns; ++i) {
+        const SpDev &s = c->sp[i].dev;
+        if (s.zmax > 0 && !lepton(s.ion_into, -1.0))
+            return set_error(HYB_EINVAL, "ionize_into must be an electron species");
+        if (s.qed && s.ph_species >= 0 &&
+            !(s.ph_species < ns && c->sp[s.ph_species].dev.kind == HYB_KIND_PHOTON))
+            return set_error(HYB_EINVAL, "photon_species must be a photon species");
+        if (s.kind == HYB_KIND_PHOTON && s.pair_e >= 0 && !(lepton(s.pair_e, -1.0) && lepton(s.pair_p, 1.0)))
+            return set_error(HYB_EINVAL, "pair_electron / pair_positron must be electron / positron species");
+    }
     return HYB_OK;
 }
 
 hyb_status hyb_load_species(hyb_ctx *c, const hyb_species_desc *d, int *species_id) {
     if (!c || !d || !species_id) return set_error(HYB_EINVAL, "null argument");
     if ((int)c->sp.size() >= HYB_MAX_SPECIES) return set_error(HYB_EINVAL, "too many species");
-    if (!(d->m > 0.0)) return set_error(HYB_EINVAL, "species mass must be > 0");
+    if (d->kind != HYB_KIND_MASSIVE && d->kind != HYB_KIND_PHOTON) return set_error(HYB_EINVAL, "bad species kind");
+    if (d->kind == HYB_KIND_PHOTON) {
+        if (d->q != 0.0 || d->zmax != 0 || d->qed || d->zq)
+            return set_error(HYB_EINVAL, "a photon species has q = 0 and no ionization, emission or zq");
+        if ((d->pair_electron >= 0) != (d->pair_positron >= 0))
+            return set_error(HYB_EINVAL, "pair creation needs both an electron and a positron species");
+    } else if (!(d->m > 0.0)) {
+        return set_error(HYB_EINVAL, "species mass must be > 0");
+    }
+    if (d->qed && !(std::fabs(d->q) == 1.0 && d->m == 1.0))
+        return set_error(HYB_EINVAL, "photon emission is for electrons and positrons (|q| = 1, m = 1)");
+    if ((d->qed || (d->kind == HYB_KIND_PHOTON && d->pair_electron >= 0)) && !(c->desc.lambda_um > 0.0))
+        return set_error(HYB_EINVAL, "QED needs lambda_um > 0");
     if (d->n < 0) return set_error(HYB_EINVAL, "negative particle count");
     if (d->n > 0 && (!d->x || !d->y || !d->z || !d->ux || !d->uy || !d->uz || !d->w))
         return set_error(HYB_EINVAL, "missing particle arrays");
     if (d->zmax < 0 || d->zmax > 8) return set_error(HYB_EINVAL, "zmax must be in 0..8");
     if (d->zmax > 0) {
         if (!d->zq) return set_error(HYB_EINVAL, "an ionizable species needs per-particle charge states (zq)");
-        if (d->ionize_into < 0 || d->ionize_into >= (int)c->sp.size())
-            return set_error(HYB_EINVAL, "ionize_into must name an already loaded species");
-        if (c->sp[d->ionize_into].has_zq || c->sp[d->ionize_into].q != -1.0 || c->sp[d->ionize_into].m != 1.0)
-            return set_error(HYB_EINVAL, "ionize_into must be an electron species (q = -1, m = 1, no zq)");
+        if (d->ionize_into < 0 || d->ionize_into >= HYB_MAX_SPECIES)
+            return set_error(HYB_EINVAL, "ionize_into must be a species id");
         for (int z = 0; z < d->zmax; ++z)
             if (!(d->ip_eV[z] > 0.0) || d->l_qn[z] < 0 || d->l_qn[z] > 3)
                 return set_error(HYB_EINVAL, "bad ionization potential or quantum number");
@@ -317,7 +370,9 @@ hyb_status hyb_load_species(hyb_ctx *c, const hyb_species_desc *d, int *species_
             for (int a = 0; a < 3; ++a) {
                 const float hi = g.bc[a] ? (float)(g.n[a] - 1) : (float)g.n[a];
                 if (!(v[a] >= 0.0f) || v[a] > hi || (g.bc[a] == 0 && v[a] >= hi))
-                    return set_error(HYB_EINVAL, "particle position outside the domain");
+                    return set_error(HYB_EINVAL, "particle " + std::to_string(p) + " position " +
+                                                     std::to_string(v[a]) + " on axis " + std::to_string(a) +
+                                                     " outside the domain");
             }
         }
     }
@@ -402,8 +457,9 @@ hyb_status hyb_load_species(hyb_ctx *c, const hyb_species_desc *d, int *species_
         // release staging, allocate species, then stage again on top
         cleanup();
         tmp.clear();
-        if (alloc_species(c, sp, (int)cap, sp.has_zq) != HYB_OK)
+        if (alloc_species(c, sp, (int)cap, sp.has_zq, needs_tau(d)) != HYB_OK)
             return set_error(HYB_ENOMEM, "species allocation failed (arena too small?)");
+        species_flags(sp.dev, d, (int)c->sp.size());
         hyb_status is = setup_ionization(c, sp.dev, d);
         if (is != HYB_OK) return is;
         arena_mark = c->arena.used;
@@ -426,10 +482,11 @@ hyb_status hyb_load_species(hyb_ctx *c, const hyb_species_desc *d, int *species_
             return set_error(HYB_ENOMEM, "staging allocation for species failed (arena too small?)");
         }
     } else {
-        if (alloc_species(c, sp, (int)cap, sp.has_zq) != HYB_OK) {
+        if (alloc_species(c, sp, (int)cap, sp.has_zq, needs_tau(d)) != HYB_OK) {
             cleanup();
             return set_error(HYB_ENOMEM, "species allocation failed");
         }
+        species_flags(sp.dev, d, (int)c->sp.size());
         hyb_status is = setup_ionization(c, sp.dev, d);
         if (is != HYB_OK) {
             cleanup();
@@ -446,6 +503,10 @@ hyb_status hyb_load_species(hyb_ctx *c, const hyb_species_desc *d, int *species_
     if (hstatus) {
         c->error_latched = true;
         return set_error(status_to_code(hstatus), "particle binning overflowed a tile");
+    }
+    if (needs_tau(d)) {
+        hyb_status qs = setup_qed(c);
+        if (qs != HYB_OK) return qs;
     }
     *species_id = (int)c->sp.size();
     c->sp.push_back(sp);
@@ -478,6 +539,8 @@ hyb_status hyb_step(hyb_ctx *c, int nsteps) {
     if (c->error_latched) return set_error(HYB_ESTATE, "context is in an error state (hyb_clear_status)");
     if (nsteps == 0) return HYB_OK;
     if (!c->graph_valid) {
+        hyb_status lv = validate_links(c);
+        if (lv != HYB_OK) return lv;
         if (c->graph) {
             cudaGraphExecDestroy(c->graph);
             c->graph = nullptr;
@@ -533,6 +596,12 @@ hyb_status hyb_eval_rate_table(hyb_ctx *c, int table, int sid, int level, const 
     return set_error(HYB_EINVAL, "unknown table");
 }
 
+hyb_status hyb_eval_qed(hyb_ctx *c, int what, const float *chi, const float *r, int n, float *out) {
+    if (!c || !chi || !out || n < 0) return set_error(HYB_EINVAL, "bad argument");
+    if (n == 0) return HYB_OK;
+    return eval_qed(c, what, chi, r, n, out);
+}
+
 hyb_status hyb_clear_status(hyb_ctx *c) {
     if (!c) return set_error(HYB_EINVAL, "null context");
     HYB_CUDA_TRY(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream));
@@ -579,19 +648,24 @@ hyb_status hyb_diagnostics(hyb_ctx *c, hyb_diag *out) {
     for (int s = 0; s < set.n; ++s) out->w_kin[s] = r[2 + s];
     out->status = status_to_code(h);
     out->launches_per_step = c->launches_per_step;
-    // ionization tallies: per-tile FP64 accumulators summed here in tile order
-    std::vector<double> te((size_t)c->g.ntiles);
-    std::vector<unsigned long long> tn((size_t)c->g.ntiles);
+    // event tallies: per-tile FP64 accumulators summed here in tile order
+    std::vector<double> te((size_t)c->g.ntiles * NTALLY);
+    std::vector<unsigned long long> tn((size_t)c->g.ntiles * NTALLY);
     for (int s = 0; s < set.n; ++s) {
-        if (set.s[s].zmax <= 0) continue;
-        HYB_CUDA_TRY(cudaMemcpyAsync(te.data(), set.s[s].ion_energy, sizeof(double) * te.size(),
-                                     cudaMemcpyDeviceToHost, c->stream));
-        HYB_CUDA_TRY(cudaMemcpyAsync(tn.data(), set.s[s].ion_events, sizeof(unsigned long long) * tn.size(),
+        HYB_CUDA_TRY(cudaMemcpyAsync(te.data(), set.s[s].tal_e, sizeof(double) * te.size(), cudaMemcpyDeviceToHost,
+                                     c->stream));
+        HYB_CUDA_TRY(cudaMemcpyAsync(tn.data(), set.s[s].tal_n, sizeof(unsigned long long) * tn.size(),
                                      cudaMemcpyDeviceToHost, c->stream));
         HYB_CUDA_TRY(cudaStreamSynchronize(c->stream));
-        for (size_t t = 0; t < te.size(); ++t) {
-            out->w_ionize += te[t];
-            out->n_ionize += (long long)tn[t];
+        for (int t = 0; t < c->g.ntiles; ++t) {
+            const double *e = &te[(size_t)t * NTALLY];
+            const unsigned long long *k = &tn[(size_t)t * NTALLY];
+            out->w_ionize += e[TALLY_IONIZE];
+            out->n_ionize += (long long)k[TALLY_IONIZE];
+            out->w_photon_untracked += e[TALLY_EMIT];
+            out->n_emit += (long long)k[TALLY_EMIT];
+            out->w_pair_deficit += e[TALLY_PAIR];
+            out->n_pair += (long long)k[TALLY_PAIR];
         }
     }
     if (h) {

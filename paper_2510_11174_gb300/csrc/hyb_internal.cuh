@@ -34,6 +34,21 @@ __host__ __device__ inline long long cidx(const GridDev &g, int i, int j, int k)
     return (long long)i + (long long)g.n[0] * ((long long)j + (long long)g.n[1] * (long long)k);
 }
 
+#ifdef __CUDACC__
+// Position of v on a grid uniform in log2 v with npo points per octave that
+// starts at 2^e0.  The octave comes from the binary exponent (exact) and the
+// in-octave position from log2 of the mantissa, so the coordinate keeps the
+// mantissa's precision however many octaves the grid spans.
+__device__ __forceinline__ void log2_grid(float v, int e0, int npo, int &i, float &f) {
+    int e;
+    const float m = frexpf(v, &e);           // v = m 2^e, m in [0.5, 1)
+    const float lm = log2f(m) * (float)npo;  // in [-npo, 0)
+    const float fl = floorf(lm);
+    i = (e - e0) * npo + (int)fl;
+    f = lm - fl;
+}
+#endif
+
 // ---------------------------------------------------------------- particle species on the device
 // SoA FP32 in fixed-capacity tiles: slot s of tile t lives at t * cap + s.
 // x, y, z are cell units; a dead slot (awaiting compaction) has x = -1.
@@ -56,18 +71,39 @@ struct SpDev {
     int zmax;
     int ion_into;          // species index of the electrons
     uint32_t sp_index;     // Philox key word 1
-    const float *lnw;      // [zmax][ION_NL] ln of the rate [1/atomic time] on the ln F grid
-    float lnF0, inv_h;     // grid: ln F = lnF0 + i / inv_h
+    const float *lnw;      // [zmax][ION_NL] ln of the rate [1/atomic time] on the log2 F grid
     float e_ratio;         // |E| (normalised) -> F (atomic units)
     float dt_au;           // dt in atomic units
     double ip_mc2[8];      // Ip of state Z in m_e c^2 (energy tally)
-    double *ion_energy;    // per tile: accumulated sum w Ip
-    unsigned long long *ion_events;  // per tile: accumulated events
+    // strong-field QED
+    int kind;              // 0 massive, 1 photon (moves at c, no charge)
+    int qed;               // lepton emits photons
+    int ph_species;        // receiving photon species (-1: tally only)
+    float eps_min;         // tracking threshold of emitted photons [m c^2]
+    int pair_e, pair_p;    // photon species: receiving electron / positron species (-1: none)
+    float *tau, *mtau;     // optical depth per slot / per migrant (QED leptons, photons)
+    uint32_t tau_index;    // Philox key word 1 for the initial optical depth
+    // per-tile accumulated tallies, TALLY_* entries per tile
+    double *tal_e;
+    unsigned long long *tal_n;
 };
 
-static constexpr int ION_NL = 8192;       // table points per charge state
-static constexpr double ION_FMIN = 1e-4;  // atomic units
-static constexpr double ION_FMAX = 1e3;
+// tallies per tile: energies (FP64) and event counts
+enum { TALLY_IONIZE = 0, TALLY_EMIT = 1, TALLY_PAIR = 2, NTALLY = 3 };
+
+// device QED tables (see qed.cuh)
+struct QedDev {
+    const float *em_lnh;    // ln h(chi) on the emission chi grid
+    const float *em_cdf;    // cumulative emission spectrum rows over mu
+    const float *pair_lnT;  // ln T(chi) on the pair chi grid
+    const float *pair_cdf;  // cumulative pair spectrum rows over xi
+    float kappa;            // hbar w0 / m c^2
+    float pref;             // alpha / kappa
+};
+
+// ionization table grid: uniform in log2 F over F = 2^-14 .. 2^10 atomic units
+static constexpr int ION_E0 = -14, ION_E1 = 10, ION_NPO = 2048;
+static constexpr int ION_NL = (ION_E1 - ION_E0) * ION_NPO + 1;
 
 struct SpSet {
     int n;
@@ -121,6 +157,11 @@ struct hyb_ctx {
 
     std::vector<hyb::Species> sp;
     hyb::SpDev *sp_dev = nullptr;  // device copy of the species descriptors (HYB_MAX_SPECIES)
+
+    // LCFA QED tables (built on first use)
+    bool qed_ready = false;
+    hyb::QedDev qed = {};
+    double *airy_ai = nullptr, *airy_aip = nullptr, *airy_aint = nullptr;
     long long step = 0;
 
     cudaGraphExec_t graph = nullptr;
@@ -162,7 +203,10 @@ void launch_step_inc(long long *step_dev, cudaStream_t st);
 
 size_t push_smem_bytes(int T);
 void launch_push_deposit(const GridDev &g, const float *E, const float *B, const SpDev *sps_dev, int nsp,
-                         float *jscratch, int *status, const long long *step_dev, cudaStream_t st);
+                         const QedDev &qd, float *jscratch, int *status, const long long *step_dev,
+                         cudaStream_t st);
+hyb_status setup_qed(hyb_ctx *c);  // builds the QED tables once per context
+hyb_status eval_qed(hyb_ctx *c, int what, const float *chi, const float *r, int n, float *out);
 hyb_status setup_ionization(hyb_ctx *c, SpDev &s, const hyb_species_desc *d);
 hyb_status eval_ion_table(hyb_ctx *c, const SpDev &s, int Z, const float *x_host, int n, float *out_host);
 void launch_j_reduce(const GridDev &g, const float *jscratch, float *J, cudaStream_t st);

@@ -29,12 +29,12 @@ __device__ double adk_ln_rate(double F, double Ip, double Zc, int l) {
     return lnC2 + log((2.0 * l + 1.0) * Ip) + (2.0 * ns - 1.0) * log(2.0 * k / F) - 2.0 * k / (3.0 * F);
 }
 
-__global__ void k_build_ion_lut(float *__restrict__ lnw, int zmax, double lnF0, double h,
-                                const double *__restrict__ ip_au, const int *__restrict__ lq, double w0) {
+__global__ void k_build_ion_lut(float *__restrict__ lnw, int zmax, const double *__restrict__ ip_au,
+                                const int *__restrict__ lq, double w0) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= zmax * ION_NL) return;
     const int Z = t / ION_NL, i = t % ION_NL;
-    const double F = exp(lnF0 + h * i);
+    const double F = exp2((double)ION_E0 + (double)i / ION_NPO);
     const double Ip = ip_au[Z], Zc = Z + 1.0;
     const int l = lq[Z];
     const double lnadk = adk_ln_rate(F, Ip, Zc, l);
@@ -72,9 +72,6 @@ hyb_status setup_ionization(hyb_ctx *c, SpDev &s, const hyb_species_desc *d) {
     s.zmax = d->zmax;
     s.ion_into = d->ionize_into;
     s.sp_index = (uint32_t)c->sp.size();
-    const double lnF0 = std::log(ION_FMIN), h = (std::log(ION_FMAX) - lnF0) / (ION_NL - 1);
-    s.lnF0 = (float)lnF0;
-    s.inv_h = (float)(1.0 / h);
     s.e_ratio = (float)(Eref / E_AU);
     s.dt_au = (float)(c->g.dt_d / w0 / T_AU);
     std::vector<double> ip(d->zmax);
@@ -87,9 +84,7 @@ hyb_status setup_ionization(hyb_ctx *c, SpDev &s, const hyb_species_desc *d) {
     float *lnw = nullptr;
     double *dip = nullptr;
     int *dlq = nullptr;
-    if (ctx_alloc(c, (void **)&lnw, sizeof(float) * d->zmax * ION_NL) ||
-        ctx_alloc(c, (void **)&s.ion_energy, sizeof(double) * c->g.ntiles) ||
-        ctx_alloc(c, (void **)&s.ion_events, sizeof(unsigned long long) * c->g.ntiles))
+    if (ctx_alloc(c, (void **)&lnw, sizeof(float) * d->zmax * ION_NL))
         return set_error(HYB_ENOMEM, "ionization table allocation failed");
     // the small parameter arrays are staged in temporary device buffers
     if (cudaMalloc(&dip, sizeof(double) * 8) != cudaSuccess || cudaMalloc(&dlq, sizeof(int) * 8) != cudaSuccess) {
@@ -100,9 +95,7 @@ hyb_status setup_ionization(hyb_ctx *c, SpDev &s, const hyb_species_desc *d) {
     cudaMemcpyAsync(dip, ip.data(), sizeof(double) * d->zmax, cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(dlq, lq.data(), sizeof(int) * d->zmax, cudaMemcpyHostToDevice, st);
     const int tot = d->zmax * ION_NL;
-    k_build_ion_lut<<<(tot + 255) / 256, 256, 0, st>>>(lnw, d->zmax, lnF0, h, dip, dlq, w0 * T_AU);
-    cudaMemsetAsync(s.ion_energy, 0, sizeof(double) * c->g.ntiles, st);
-    cudaMemsetAsync(s.ion_events, 0, sizeof(unsigned long long) * c->g.ntiles, st);
+    k_build_ion_lut<<<(tot + 255) / 256, 256, 0, st>>>(lnw, d->zmax, dip, dlq, w0 * T_AU);
     cudaError_t e = cudaStreamSynchronize(st);
     cudaFree(dip);
     cudaFree(dlq);

@@ -26,6 +26,7 @@
 #include "hyb_internal.cuh"
 #include "ionize.cuh"
 #include "philox.cuh"
+#include "qed.cuh"
 
 namespace hyb {
 
@@ -39,6 +40,31 @@ __device__ __forceinline__ int warp_append(int *counter) {
     if (lane == leader) b = atomicAdd(counter, __popc(mask));
     b = __shfl_sync(mask, b, leader);
     return b + __popc(mask & ((1u << lane) - 1u));
+}
+
+// initial optical depth of a particle: -ln u, u from counter (id_lo, id_hi, 2^32-1, 4)
+__device__ __forceinline__ float tau_initial(uint64_t id, uint32_t seed, uint32_t key1) {
+    const u32x4 r = philox4x32_10((uint32_t)id, (uint32_t)(id >> 32), 0xFFFFFFFFu, RNG_QED_TAU, seed, key1);
+    return -logf(u01f(r.v[0]));
+}
+
+// a particle created by an event joins species d through its migration buffer
+// (tau < 0: draw the initial optical depth from the particle's own stream)
+__device__ __forceinline__ void spawn(const SpDev &d, const float x[3], const float u[3], float w, uint64_t id,
+                                      int dest, long long step, uint32_t seed, float tau, int *status) {
+    (void)step;
+    const int m = warp_append(d.mig_count);
+    if (m >= d.mig_cap) {
+        atomicOr(status, ST_OVERFLOW);
+        return;
+    }
+    d.mx[m] = x[0]; d.my[m] = x[1]; d.mz[m] = x[2];
+    d.mux[m] = u[0]; d.muy[m] = u[1]; d.muz[m] = u[2];
+    d.mw[m] = w;
+    if (d.zq) d.mzq[m] = 0.0f;
+    if (d.tau) d.mtau[m] = tau >= 0.0f ? tau : tau_initial(id, seed, d.tau_index);
+    d.mid[m] = id;
+    d.mdest[m] = dest;
 }
 
 __host__ __device__ inline int frame_F(int T) { return T + 2; }  // field frame edge
@@ -108,18 +134,18 @@ __global__ void __launch_bounds__(256) k_push_deposit(GridDev g, const float *__
                                                       const float *__restrict__ B,
                                                       const SpDev *__restrict__ sps, int nsp,
                                                       float *__restrict__ jscratch, int *__restrict__ status,
-                                                      const long long *__restrict__ step_dev) {
+                                                      const long long *__restrict__ step_dev, QedDev qd) {
     extern __shared__ float sm[];
     const int T = g.T, F = frame_F(T), G = frame_G(T);
     const int F3 = F * F * F, G3 = G * G * G;
     float *sf = sm;            // 6 field components, F^3 each
     float *sj = sm + 6 * F3;   // 3 current components, G^3 each
     __shared__ int s_holes;
-    __shared__ double s_ion_e;
-    __shared__ unsigned long long s_ion_n;
+    __shared__ double s_tal_e[NTALLY];
+    __shared__ unsigned long long s_tal_n[NTALLY];
     const long long step = *step_dev;
-    double ion_e = 0.0;
-    int ion_n = 0;
+    double tal_e[NTALLY] = {0.0, 0.0, 0.0};
+    int tal_n[NTALLY] = {0, 0, 0};
 
     const int t = blockIdx.x;
     const int tx = t % g.nt[0], ty = (t / g.nt[0]) % g.nt[1], tz = t / (g.nt[0] * g.nt[1]);
@@ -148,8 +174,10 @@ __global__ void __launch_bounds__(256) k_push_deposit(GridDev g, const float *__
     for (int l = threadIdx.x; l < 3 * G3; l += blockDim.x) sj[l] = 0.0f;
     if (threadIdx.x == 0) {
         s_holes = 0;
-        s_ion_e = 0.0;
-        s_ion_n = 0;
+        for (int k = 0; k < NTALLY; ++k) {
+            s_tal_e[k] = 0.0;
+            s_tal_n[k] = 0;
+        }
     }
     __syncthreads();
 
@@ -162,7 +190,8 @@ __global__ void __launch_bounds__(256) k_push_deposit(GridDev g, const float *__
         const SpDev &sp = sps[si];
         const int n = min(sp.count[t], sp.cap);
         const long long base = (long long)t * sp.cap;
-        const float qm_half = 0.5f * dt / sp.m;  // times q_p below
+        // times q_p below; photons (m = 0, q = 0) get no Lorentz force
+        const float qm_half = sp.kind == 1 ? 0.0f : 0.5f * dt / sp.m;
         for (int p0 = 0; p0 < n; p0 += blockDim.x) {
             const int p = p0 + threadIdx.x;
             if (p < n) {
@@ -217,8 +246,9 @@ __global__ void __launch_bounds__(256) k_push_deposit(GridDev g, const float *__
                 u[1] = um[1] + (ud[2] * ss[0] - ud[0] * ss[2]) + h * e[1];
                 u[2] = um[2] + (ud[0] * ss[1] - ud[1] * ss[0]) + h * e[2];
 
-                // ---- move, reflect at absorbing walls
-                const float gam = sqrtf(1.0f + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+                // ---- move (photons at c: velocity k / |k|), reflect at absorbing walls
+                const float gam = sp.kind == 1 ? fmaxf(sqrtf(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]), 1e-30f)
+                                               : sqrtf(1.0f + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
                 float x1[3];
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
@@ -294,50 +324,109 @@ __global__ void __launch_bounds__(256) k_push_deposit(GridDev g, const float *__
                 }
                 const int nt = tile_index(g, x1[0], x1[1], x1[2]);
 
-                // ---- field ionization: after the deposit (this step's current
-                // carries the old charge); at most one level per step; the new
-                // electron starts at x^{n+1} with the ion's u and weight
+                // ---- stochastic events, after the deposit (this step's current
+                // used the pre-event charge and momentum); new particles start at
+                // x^{n+1} and enter their species through its migration buffer
                 float zq_new = sp.zq ? sp.zq[s] : 0.0f;
+                float tau = sp.tau ? sp.tau[s] : 0.0f;
+                bool dead = false;
+                const uint64_t pid = sp.id[s];
                 if (sp.zmax > 0 && zq_new < (float)sp.zmax) {
+                    // field ionization: at most one level per step; the electron
+                    // takes the ion's u and weight
                     const int Z = (int)zq_new;
                     const float P = ion_probability(sp, Z, sqrtf(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]));
-                    const uint64_t pid = sp.id[s];
                     const u32x4 r = philox4x32_10((uint32_t)pid, (uint32_t)(pid >> 32), (uint32_t)step, RNG_IONIZE,
                                                   g.seed, sp.sp_index);
                     if (u01f(r.v[0]) < P) {
                         zq_new = (float)(Z + 1);
-                        ion_e += (double)wgt * sp.ip_mc2[Z];
-                        ion_n += 1;
+                        tal_e[TALLY_IONIZE] += (double)wgt * sp.ip_mc2[Z];
+                        tal_n[TALLY_IONIZE] += 1;
                         const SpDev &el = sps[sp.ion_into];
-                        const int m = warp_append(el.mig_count);
-                        if (m < el.mig_cap) {
-                            el.mx[m] = x1[0]; el.my[m] = x1[1]; el.mz[m] = x1[2];
-                            el.mux[m] = u[0]; el.muy[m] = u[1]; el.muz[m] = u[2];
-                            el.mw[m] = wgt;
-                            if (el.zq) el.mzq[m] = 0.0f;
-                            el.mid[m] = (1ULL << 63) | (pid << 3) | (uint64_t)(Z + 1);
-                            el.mdest[m] = nt;
+                        const uint64_t eid = (1ULL << 63) | (pid << 3) | (uint64_t)(Z + 1);
+                        spawn(el, x1, u, wgt, eid, nt, step, g.seed, -1.0f, status);
+                    }
+                }
+                if (sp.qed) {
+                    // photon emission (radiation reaction), optical-depth method
+                    const float gl = sqrtf(1.0f + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+                    const float chi = qed_chi(qd.kappa, e, b, u, gl);
+                    tau -= qd.pref * qed_h(qd, chi) / gl * dt;
+                    if (tau <= 0.0f) {
+                        const u32x4 r = philox4x32_10((uint32_t)pid, (uint32_t)(pid >> 32), (uint32_t)step,
+                                                      RNG_QED_EMIT, g.seed, sp.sp_index);
+                        const float xi = qed_em_sample(qd, chi, u01f(r.v[0]));
+                        tau = -logf(u01f(r.v[1]));
+                        const float eps = fminf(xi * gl, gl - 1.0f);
+                        const float g1 = gl - eps;
+                        const float un = sqrtf(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+                        const float u1 = sqrtf(fmaxf(g1 * g1 - 1.0f, 0.0f));
+                        const float sc = un > 0.0f ? u1 / un : 0.0f;
+                        float k[3];
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            k[c] = un > 0.0f ? eps * u[c] / un : 0.0f;
+                            u[c] *= sc;
+                        }
+                        tal_n[TALLY_EMIT] += 1;
+                        if (eps >= sp.eps_min && sp.ph_species >= 0 && un > 0.0f) {
+                            spawn(sps[sp.ph_species], x1, k, wgt, derived_id(pid, step, 2u), nt, step, g.seed,
+                                  -logf(u01f(r.v[2])), status);
                         } else {
-                            atomicOr(status, ST_OVERFLOW);
+                            tal_e[TALLY_EMIT] += (double)wgt * eps;
+                        }
+                    }
+                }
+                if (sp.kind == 1 && sp.pair_e >= 0) {
+                    // Breit-Wheeler pair creation by a photon (energy >= 2 m c^2)
+                    const float eps = sqrtf(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+                    if (eps >= 2.0f) {
+                        const float chi = qed_chi(qd.kappa, e, b, u, eps);
+                        tau -= qd.pref * qed_T(qd, chi) / eps * dt;
+                        if (tau <= 0.0f) {
+                            const u32x4 r = philox4x32_10((uint32_t)pid, (uint32_t)(pid >> 32), (uint32_t)step,
+                                                          RNG_QED_PAIR, g.seed, sp.sp_index);
+                            const float xi = qed_pair_sample(qd, chi, u01f(r.v[0]));
+                            const float ee = xi * eps, ep = (1.0f - xi) * eps;
+                            const float ue = ee > 1.0f ? sqrtf(ee * ee - 1.0f) : 0.0f;
+                            const float up = ep > 1.0f ? sqrtf(ep * ep - 1.0f) : 0.0f;
+                            if (ee < 1.0f) tal_e[TALLY_PAIR] += (double)wgt * (1.0f - ee);
+                            if (ep < 1.0f) tal_e[TALLY_PAIR] += (double)wgt * (1.0f - ep);
+                            tal_n[TALLY_PAIR] += 1;
+                            float ve[3], vp[3];
+#pragma unroll
+                            for (int c = 0; c < 3; ++c) {
+                                ve[c] = ue * u[c] / eps;
+                                vp[c] = up * u[c] / eps;
+                            }
+                            spawn(sps[sp.pair_e], x1, ve, wgt, derived_id(pid, step, 3u), nt, step, g.seed,
+                                  -logf(u01f(r.v[1])), status);
+                            spawn(sps[sp.pair_p], x1, vp, wgt, derived_id(pid, step, 5u), nt, step, g.seed,
+                                  -logf(u01f(r.v[2])), status);
+                            dead = true;
                         }
                     }
                 }
 
-                if (nt == t) {
+                if (nt == t && !dead) {
                     sp.x[s] = x1[0]; sp.y[s] = x1[1]; sp.z[s] = x1[2];
                     sp.ux[s] = u[0]; sp.uy[s] = u[1]; sp.uz[s] = u[2];
                     if (sp.zmax > 0) sp.zq[s] = zq_new;
+                    if (sp.tau) sp.tau[s] = tau;
                 } else {
-                    const int m = warp_append(sp.mig_count);
-                    if (m < sp.mig_cap) {
-                        sp.mx[m] = x1[0]; sp.my[m] = x1[1]; sp.mz[m] = x1[2];
-                        sp.mux[m] = u[0]; sp.muy[m] = u[1]; sp.muz[m] = u[2];
-                        sp.mw[m] = wgt;
-                        if (sp.zq) sp.mzq[m] = zq_new;
-                        sp.mid[m] = sp.id[s];
-                        sp.mdest[m] = nt;
-                    } else {
-                        atomicOr(status, ST_OVERFLOW);
+                    if (!dead) {
+                        const int m = warp_append(sp.mig_count);
+                        if (m < sp.mig_cap) {
+                            sp.mx[m] = x1[0]; sp.my[m] = x1[1]; sp.mz[m] = x1[2];
+                            sp.mux[m] = u[0]; sp.muy[m] = u[1]; sp.muz[m] = u[2];
+                            sp.mw[m] = wgt;
+                            if (sp.zq) sp.mzq[m] = zq_new;
+                            if (sp.tau) sp.mtau[m] = tau;
+                            sp.mid[m] = pid;
+                            sp.mdest[m] = nt;
+                        } else {
+                            atomicOr(status, ST_OVERFLOW);
+                        }
                     }
                     const int hslot = atomicAdd(&s_holes, 1);
                     sp.holes[base + hslot] = p;
@@ -345,31 +434,35 @@ __global__ void __launch_bounds__(256) k_push_deposit(GridDev g, const float *__
                 }
             }
         }
-        if (sp.zmax > 0) {
-            // per-tile ionization tallies: warp sums, then one shared accumulator
+        // per-tile tallies: warp sums, then shared accumulators, then one add per tile
+#pragma unroll
+        for (int k = 0; k < NTALLY; ++k) {
 #pragma unroll
             for (int o2 = 16; o2 > 0; o2 >>= 1) {
-                ion_e += __shfl_down_sync(0xffffffffu, ion_e, o2);
-                ion_n += __shfl_down_sync(0xffffffffu, ion_n, o2);
+                tal_e[k] += __shfl_down_sync(0xffffffffu, tal_e[k], o2);
+                tal_n[k] += __shfl_down_sync(0xffffffffu, tal_n[k], o2);
             }
-            if ((threadIdx.x & 31) == 0 && ion_n > 0) {
-                atomicAdd(&s_ion_e, ion_e);
-                atomicAdd(&s_ion_n, (unsigned long long)ion_n);
+            if ((threadIdx.x & 31) == 0 && tal_n[k] > 0) {
+                atomicAdd(&s_tal_e[k], tal_e[k]);
+                atomicAdd(&s_tal_n[k], (unsigned long long)tal_n[k]);
             }
-            ion_e = 0.0;
-            ion_n = 0;
+            tal_e[k] = 0.0;
+            tal_n[k] = 0;
         }
         __syncthreads();
         if (threadIdx.x == 0) {
             sp.hole_count[t] = s_holes;
             sp.hole_used[t] = 0;
             s_holes = 0;
-            if (sp.zmax > 0 && s_ion_n > 0) {
-                sp.ion_energy[t] += s_ion_e;
-                sp.ion_events[t] += s_ion_n;
+#pragma unroll
+            for (int k = 0; k < NTALLY; ++k) {
+                if (s_tal_n[k] > 0) {
+                    sp.tal_e[(long long)t * NTALLY + k] += s_tal_e[k];
+                    sp.tal_n[(long long)t * NTALLY + k] += s_tal_n[k];
+                }
+                s_tal_e[k] = 0.0;
+                s_tal_n[k] = 0;
             }
-            s_ion_e = 0.0;
-            s_ion_n = 0;
         }
         __syncthreads();
     }
@@ -449,6 +542,7 @@ __global__ void k_rebin(SpDev sp, int *__restrict__ status) {
         sp.w[s] = sp.mw[m];
         if (sp.zq) sp.zq[s] = sp.mzq[m];
         sp.id[s] = sp.mid[m];
+        if (sp.tau) sp.tau[s] = sp.mtau[m];
     }
 }
 
@@ -478,6 +572,7 @@ __global__ void k_compact(GridDev g, SpDev sp) {
         sp.w[a] = sp.w[b];
         if (sp.zq) sp.zq[a] = sp.zq[b];
         sp.id[a] = sp.id[b];
+        if (sp.tau) sp.tau[a] = sp.tau[b];
         ++src;
     }
     sp.count[t] = new_n;
@@ -510,15 +605,17 @@ __global__ void k_bin(GridDev g, SpDev sp, long long n, const float *__restrict_
         sp.w[s] = w[p];
         if (sp.zq) sp.zq[s] = zq ? zq[p] : 0.0f;
         sp.id[s] = ids ? ids[p] : (uint64_t)p;
+        if (sp.tau) sp.tau[s] = tau_initial(sp.id[s], g.seed, sp.tau_index);
     }
 }
 
 static inline unsigned blocks_for(long long n, int b) { return (unsigned)((n + b - 1) / b); }
 
 void launch_push_deposit(const GridDev &g, const float *E, const float *B, const SpDev *sps_dev, int nsp,
-                         float *jscratch, int *status, const long long *step_dev, cudaStream_t st) {
+                         const QedDev &qd, float *jscratch, int *status, const long long *step_dev,
+                         cudaStream_t st) {
     const size_t smem = push_smem_bytes(g.T);
-    k_push_deposit<<<g.ntiles, 256, smem, st>>>(g, E, B, sps_dev, nsp, jscratch, status, step_dev);
+    k_push_deposit<<<g.ntiles, 256, smem, st>>>(g, E, B, sps_dev, nsp, jscratch, status, step_dev, qd);
 }
 
 void launch_j_reduce(const GridDev &g, const float *jscratch, float *J, cudaStream_t st) {

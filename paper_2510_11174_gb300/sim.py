@@ -108,21 +108,37 @@ class Simulation:
         self.close()
 
     # ------------------------------------------------------------------ set-up
-    def load_species(self, q, m, x, y, z, ux, uy, uz, w, zq=None, ids=None, tile_capacity=0, ionize=None):
+    def load_species(self, q, m, x, y, z, ux, uy, uz, w, zq=None, ids=None, tile_capacity=0, ionize=None,
+                     kind=0, qed=None, pairs=None):
         """Add a species; returns its id.  ``ionize`` = dict(zmax, ip_eV, l, into)
-        makes it field-ionizable (zq = charge states required)."""
+        makes it field-ionizable (zq = charge states required); kind = 1 makes
+        a photon species; ``qed`` = dict(photon_species, eps_min) turns on
+        photon emission by a lepton species; ``pairs`` = dict(electron,
+        positron) turns on pair creation by a photon species."""
         d = _abi.hyb_species_desc()
         d.q, d.m = q, m
+        d.kind = int(kind)
+        d.photon_species = d.pair_electron = d.pair_positron = -1
+        if qed:
+            d.qed = 1
+            d.photon_species = int(qed.get("photon_species", -1))
+            d.photon_eps_min = float(qed.get("eps_min", 0.0))
+        if pairs:
+            d.pair_electron = int(pairs["electron"])
+            d.pair_positron = int(pairs["positron"])
         if ionize:
             d.zmax = int(ionize["zmax"])
-            for z in range(d.zmax):
-                d.ip_eV[z] = float(ionize["ip_eV"][z])
-                d.l_qn[z] = int(ionize["l"][z])
+            for lev in range(d.zmax):
+                d.ip_eV[lev] = float(ionize["ip_eV"][lev])
+                d.l_qn[lev] = int(ionize["l"][lev])
             d.ionize_into = int(ionize["into"])
         keep = []
         ptrs = []
         on_dev = None
+        n = len(x)
         for a in (x, y, z, ux, uy, uz, w, zq):
+            if a is not None and (np.ndim(a) != 1 or len(a) != n):
+                raise ValueError("particle arrays must be 1-D and of equal length")
             p, dev, k = _ptr_and_dev(a, np.float32)
             keep.append(k)
             ptrs.append(p)
@@ -177,7 +193,18 @@ class Simulation:
         return {"step": out.step, "time": out.time, "w_e": out.w_e, "w_b": out.w_b,
                 "w_kin": [out.w_kin[i] for i in range(ns)], "count": [out.count[i] for i in range(ns)],
                 "status": out.status, "launches_per_step": out.launches_per_step,
-                "w_ionize": out.w_ionize, "n_ionize": out.n_ionize}
+                "w_ionize": out.w_ionize, "n_ionize": out.n_ionize,
+                "w_photon_untracked": out.w_photon_untracked, "w_pair_deficit": out.w_pair_deficit,
+                "n_emit": out.n_emit, "n_pair": out.n_pair}
+
+    def eval_qed(self, what, chi, r=None):
+        """Evaluate the device QED tables (see hyb_eval_qed)."""
+        ca = np.ascontiguousarray(chi, dtype=np.float32)
+        ra = None if r is None else np.ascontiguousarray(r, dtype=np.float32)
+        out = np.empty_like(ca)
+        check(self._lib.hyb_eval_qed(self._ctx, int(what), ca.ctypes.data, None if ra is None else ra.ctypes.data,
+                                     len(ca), out.ctypes.data))
+        return out
 
     def eval_rate_table(self, table, species_id, level, x):
         """Evaluate a device rate table at the points x (see hyb_eval_rate_table)."""

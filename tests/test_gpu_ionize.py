@@ -19,8 +19,8 @@ M_C = 12 * 1836.15267343
 def _carbon_case(n_ions=20000, Ey=0.0085, seed=3, n=16, zq0=0.0):
     rng = np.random.default_rng(seed)
     f32 = lambda v: np.asarray(v, np.float32)
-    ions = dict(q=1.0, m=M_C, x=f32(rng.uniform(0, n, n_ions)), y=f32(rng.uniform(0, n, n_ions)),
-                z=f32(rng.uniform(0, n, n_ions)), ux=f32(np.zeros(n_ions)), uy=f32(np.zeros(n_ions)),
+    pos = lambda: np.minimum(rng.uniform(0, n, n_ions).astype(np.float32), np.float32(n - 1e-3))
+    ions = dict(q=1.0, m=M_C, x=pos(), y=pos(), z=pos(), ux=f32(np.zeros(n_ions)), uy=f32(np.zeros(n_ions)),
                 uz=f32(np.zeros(n_ions)), w=f32(np.full(n_ions, 1e-3)), zq=f32(np.full(n_ions, zq0)),
                 ionize=dict(zmax=6, ip_eV=CARBON_IP, l=CARBON_L, into=0), tile_capacity=4096)
     e0 = {k: np.zeros(0, np.float32) for k in ("x", "y", "z", "ux", "uy", "uz", "w")}
