@@ -120,6 +120,11 @@ def _declare(L):
     L.orc_qed_pairs.argtypes = [C.POINTER(Species), _P, _P, C.c_double, C.c_double, C.c_uint32, C.c_uint32, C.c_long,
                                 C.POINTER(Species), _P, C.POINTER(Species), _P, C.c_long, _P]
     L.orc_qed_pairs.restype = C.c_long
+    L.orc_node_fields.argtypes = [C.POINTER(Grid), _D3, _D3, C.c_int, C.c_int, C.c_int, _P, _P]
+    L.orc_fluid_step.argtypes = [C.POINTER(Grid), _D3, _D3, _D3, C.c_double, C.c_double, _P, _D3, C.c_double]
+    L.orc_fluid_step.restype = C.c_long
+    L.orc_fluid_energy.argtypes = [C.POINTER(Grid), C.c_double, _P, _D3]
+    L.orc_fluid_energy.restype = C.c_double
     for name, fn in _EXTRA_DECLS:
         fn(L)
 
@@ -458,3 +463,31 @@ def qed_pairs(ph, kappa, dt, seed, sp_index, step):
         o.tau = np.ascontiguousarray(t[:n])
     ph.select(alive.astype(bool))
     return el, po, tal[0], int(tal[1])
+
+
+# --------------------------------------------------------------------------- cold fluid
+class Fluid:
+    """A cold fluid species on the nodes: density n [n_c] and u = gamma beta."""
+
+    def __init__(self, q, m, n, u=None, n_floor=1e-10):
+        self.q, self.m, self.n_floor = float(q), float(m), float(n_floor)
+        self.n = np.ascontiguousarray(n, dtype=np.float64).copy()
+        self.u = (np.zeros((3,) + self.n.shape) if u is None
+                  else np.ascontiguousarray(u, dtype=np.float64).copy())
+
+
+def node_fields(g, E, B, i, j, k):
+    e = np.zeros(3)
+    b = np.zeros(3)
+    lib().orc_node_fields(C.byref(g), _f3(E), _f3(B), int(i), int(j), int(k), _ptr(e), _ptr(b))
+    return e, b
+
+
+def fluid_step(g, E, B, J, fl):
+    """One cold-fluid step; adds the face currents to J.  Returns the number of clamped nodes."""
+    return lib().orc_fluid_step(C.byref(g), _f3(E), _f3(B), _f3(J), fl.q, fl.m, _ptr(fl.n), _f3(fl.u),
+                                fl.n_floor)
+
+
+def fluid_energy(g, fl):
+    return lib().orc_fluid_energy(C.byref(g), fl.m, _ptr(fl.n), _f3(fl.u))

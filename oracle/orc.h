@@ -104,6 +104,13 @@ long orc_qed_pairs(orc_species *s, double *tau, unsigned char *alive, double kap
                    uint32_t sp_index, long step, orc_species *el, double *el_tau, orc_species *po, double *po_tau,
                    long cap, double *tallies);
 
+/* ---- cold relativistic fluid ----------------------------------------------- */
+void orc_node_fields(const orc_grid *g, const double *E[3], const double *B[3], int i, int j, int k,
+                     double e[3], double b[3]);
+long orc_fluid_step(const orc_grid *g, const double *E[3], const double *B[3], double *J[3], double q, double m,
+                    double *n, double *u[3], double n_floor);
+double orc_fluid_energy(const orc_grid *g, double m, const double *n, const double *u[3]);
+
 /* ---- diagnostics --------------------------------------------------------- */
 void orc_energy_fields(const orc_grid *g, const double *E[3], const double *B[3], double out[2]);
 double orc_energy_particles(const orc_species *s);

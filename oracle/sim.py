@@ -16,8 +16,9 @@ import math
 
 import numpy as np
 
-from . import (Grid, Particles, energy_fields, energy_particles, fdtd_b_half, fdtd_e, gather_species, ionize,
-               laser_source, photon_move, push_deposit, qed_emit, qed_kappa, qed_pairs, qed_tau0, zeros_field)
+from . import (Fluid, Grid, Particles, energy_fields, energy_particles, fdtd_b_half, fdtd_e, fluid_energy, fluid_step,
+               gather_species, ionize, laser_source, photon_move, push_deposit, qed_emit, qed_kappa, qed_pairs,
+               qed_tau0, zeros_field)
 
 
 def courant_dt(d, cfl_frac):
@@ -50,6 +51,8 @@ class OracleSim:
         self.w_pair_deficit = 0.0
         self.n_emit = 0
         self.n_pair = 0
+        self.fluids = []
+        self.n_clamped = 0
         self.nstep = 0
 
     def load_species(self, q, m, x, y, z, ux, uy, uz, w, zq=None, ids=None, ionize=None, kind=0, qed=None,
@@ -64,6 +67,16 @@ class OracleSim:
         self.qed_cfg.append(qed)
         self.pair_cfg.append(pairs)
         return sid
+
+    def load_fluid(self, q, m, n, ux=None, uy=None, uz=None, n_floor=1e-10, **_):
+        """A cold fluid species on the nodes (arrays shaped (nz, ny, nx))."""
+        n = np.asarray(n, dtype=np.float64)
+        u = np.zeros((3,) + n.shape)
+        for a, v in enumerate((ux, uy, uz)):
+            if v is not None:
+                u[a] = np.asarray(v, dtype=np.float64)
+        self.fluids.append(Fluid(q, m, n, u, n_floor=n_floor))
+        return len(self.fluids) - 1
 
     def set_fields(self, E, B):
         self.E[:] = np.asarray(E, dtype=np.float64)
@@ -124,6 +137,9 @@ class OracleSim:
                     if self.species[si].tau is None:
                         new.tau = None
                     self.species[si].append(new)
+            # cold fluids: Lorentz force, donor-cell transport, face currents into J
+            for fl in self.fluids:
+                self.n_clamped += fluid_step(g, self.E, self.B, self.J, fl)
             if self.laser:
                 L = self.laser
                 laser_source(g, self.J, self.nstep, L["x_src"], L.get("pol", 1), L["a0"], L["tau_fwhm"],
@@ -140,4 +156,5 @@ class OracleSim:
         return {"step": self.nstep, "w_e": we, "w_b": wb, "w_kin": w_kin,
                 "count": [sp.n for sp in self.species], "w_ionize": self.w_ionize, "n_ionize": self.n_ionize,
                 "w_photon_untracked": self.w_photon_untracked, "w_pair_deficit": self.w_pair_deficit,
-                "n_emit": self.n_emit, "n_pair": self.n_pair}
+                "n_emit": self.n_emit, "n_pair": self.n_pair,
+                "w_fluid": [fluid_energy(self.g, fl) for fl in self.fluids], "n_clamped": self.n_clamped}
