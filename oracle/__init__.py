@@ -125,6 +125,12 @@ def _declare(L):
     L.orc_fluid_step.restype = C.c_long
     L.orc_fluid_energy.argtypes = [C.POINTER(Grid), C.c_double, _P, _D3]
     L.orc_fluid_energy.restype = C.c_double
+    L.orc_regime_criterion.argtypes = [C.POINTER(Grid), _D3, _D3, _P, C.c_void_p] + [C.c_double] * 5 + [C.c_int, _P]
+    L.orc_fluid_to_particles.argtypes = [C.POINTER(Grid), _P, C.c_double, _P, _D3, C.c_double, C.c_int, C.c_uint32,
+                                         C.c_uint32, C.c_uint32, C.POINTER(Species), C.c_long, _P]
+    L.orc_fluid_to_particles.restype = C.c_long
+    L.orc_particles_to_fluid.argtypes = [C.POINTER(Grid), _P, C.POINTER(Species), _P, _D3, C.c_double, _P]
+    L.orc_particles_to_fluid.restype = C.c_long
     for name, fn in _EXTRA_DECLS:
         fn(L)
 
@@ -491,3 +497,43 @@ def fluid_step(g, E, B, J, fl):
 
 def fluid_energy(g, fl):
     return lib().orc_fluid_energy(C.byref(g), fl.m, _ptr(fl.n), _f3(fl.u))
+
+
+# --------------------------------------------------------------------------- regime switching
+REGIME_DEFAULTS = dict(a_thr=1.0, n_thr=1.0, c_thr=0.1, chi_thr=1e-3, dilate=2)
+
+
+def regime_criterion(g, E, B, ne, fluid_u=None, kappa=None, lambda_m=0.8e-6, **thr):
+    """Physics criterion mask (1 = kinetic) at the nodes, dilated."""
+    t = dict(REGIME_DEFAULTS)
+    t.update(thr)
+    kappa = qed_kappa(lambda_m) if kappa is None else kappa
+    ne = np.ascontiguousarray(ne, dtype=np.float64)
+    mask = np.zeros(g.shape, dtype=np.uint8)
+    fu = None if fluid_u is None else _f3(np.ascontiguousarray(fluid_u, dtype=np.float64))
+    lib().orc_regime_criterion(C.byref(g), _f3(E), _f3(B), _ptr(ne), fu, float(kappa), float(t["a_thr"]),
+                               float(t["n_thr"]), float(t["c_thr"]), float(t["chi_thr"]), int(t["dilate"]),
+                               _ptr(mask))
+    return mask
+
+
+def fluid_to_particles(g, mask, fl, ppc, seed, sp_index, epoch, rho_bg):
+    """Convert the fluid at kinetic nodes into particles (returns Particles)."""
+    mask = np.ascontiguousarray(mask, dtype=np.uint8)
+    cap = int(np.count_nonzero(mask)) * ppc
+    out = _empty(max(cap, 1), fl.q, fl.m)
+    n = lib().orc_fluid_to_particles(C.byref(g), _ptr(mask), fl.q, _ptr(fl.n), _f3(fl.u), fl.n_floor, int(ppc),
+                                     int(seed) & 0xFFFFFFFF, int(sp_index), int(epoch), C.byref(out.cstruct()),
+                                     max(cap, 1), _ptr(rho_bg))
+    out.select(np.arange(n))
+    return out
+
+
+def particles_to_fluid(g, mask, sp, fl):
+    """Move the particles whose nearest node is fluid into the fluid; returns the count."""
+    mask = np.ascontiguousarray(mask, dtype=np.uint8)
+    alive = np.ones(max(sp.n, 1), dtype=np.uint8)
+    n = lib().orc_particles_to_fluid(C.byref(g), _ptr(mask), C.byref(sp.cstruct()), _ptr(fl.n), _f3(fl.u),
+                                     fl.n_floor, _ptr(alive))
+    sp.select(alive[:sp.n].astype(bool))
+    return n

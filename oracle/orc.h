@@ -111,6 +111,16 @@ long orc_fluid_step(const orc_grid *g, const double *E[3], const double *B[3], d
                     double *n, double *u[3], double n_floor);
 double orc_fluid_energy(const orc_grid *g, double m, const double *n, const double *u[3]);
 
+/* ---- regime criterion and conversions ---------------------------------------- */
+void orc_regime_criterion(const orc_grid *g, const double *E[3], const double *B[3], const double *ne,
+                          const double *fu[3], double kappa, double a_thr, double n_thr, double c_thr,
+                          double chi_thr, int dilate, unsigned char *mask);
+long orc_fluid_to_particles(const orc_grid *g, const unsigned char *mask, double q, double *n, double *u[3],
+                            double n_floor, int ppc, uint32_t seed, uint32_t sp_index, uint32_t epoch,
+                            orc_species *out, long cap, double *rho_bg);
+long orc_particles_to_fluid(const orc_grid *g, const unsigned char *mask, orc_species *s, double *n,
+                            double *u[3], double n_floor, unsigned char *alive);
+
 /* ---- diagnostics --------------------------------------------------------- */
 void orc_energy_fields(const orc_grid *g, const double *E[3], const double *B[3], double out[2]);
 double orc_energy_particles(const orc_species *s);

@@ -1,0 +1,104 @@
+"""Pins of the oracle's regime switching: the criterion marks what its
+thresholds say and dilates by the stated distance; conversions keep the
+discrete Gauss law (with the residual background charge), the number of
+real particles, the momentum and, for fluid -> particles, the kinetic energy
+exactly."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+
+
+def _grid(bc=(0, 0, 0)):
+    return oracle.Grid.make(16, 12, 8, 0.3, 0.3, 0.3, 0.15, bc=bc)
+
+
+def test_criterion_marks_strong_field_region_dilated():
+    g = _grid()
+    E = oracle.zeros_field(g)
+    B = oracle.zeros_field(g)
+    E[1][4, 6, 8] = 3.0          # E_y at (8, 6.5, 4): node fields |E| >= 1 at (8,6,4) and (8,7,4)
+    ne = np.zeros(g.shape)
+    m = oracle.regime_criterion(g, E, B, ne, dilate=2, chi_thr=1e9)
+    z, y, x = np.nonzero(m)
+    assert (x.min(), x.max()) == (6, 10) and (y.min(), y.max()) == (4, 9) and (z.min(), z.max()) == (2, 6)
+    m0 = oracle.regime_criterion(g, E, B, ne, dilate=0, chi_thr=1e9)
+    assert np.count_nonzero(m0) == 2
+
+
+def test_criterion_density_and_compression():
+    g = _grid()
+    E = oracle.zeros_field(g)
+    B = oracle.zeros_field(g)
+    ne = np.full(g.shape, 0.1)
+    ne[3, 3, 3] = 1.5
+    m = oracle.regime_criterion(g, E, B, ne, dilate=0)
+    assert np.count_nonzero(m) == 1 and m[3, 3, 3] == 1
+    # converging flow along x: v = -0.5 tanh(x - x0) -> dt div v strongly negative at x0
+    u = np.zeros((3,) + g.shape)
+    x = np.arange(16) * g.dx
+    u[0] = (-3.0 * np.tanh((x - x[8]) / g.dx))[None, None, :]
+    m = oracle.regime_criterion(g, E, B, np.full(g.shape, 0.1), fluid_u=u, dilate=0)
+    assert np.all(m[:, :, 8] == 1) and np.count_nonzero(m[:, :, 2]) == 0
+
+
+def _rho_total(g, species, fluids, rho_bg):
+    rho = np.zeros(g.shape)
+    for sp in species:
+        oracle.charge_density(g, sp, rho)
+    for fl in fluids:
+        rho += fl.q * fl.n
+    return rho + rho_bg
+
+
+@pytest.mark.parametrize("bc", [(0, 0, 0), (1, 1, 1)])
+def test_fluid_to_particles_keeps_gauss_law_number_momentum_energy(bc):
+    g = _grid(bc)
+    rng = np.random.default_rng(2)
+    fl = oracle.Fluid(-1.0, 1.0, 0.2 + rng.random(g.shape), 0.3 * rng.standard_normal((3,) + g.shape))
+    mask = (rng.random(g.shape) < 0.3).astype(np.uint8)
+    rho_bg = np.zeros(g.shape)
+    before = _rho_total(g, [], [fl], rho_bg)
+    dV = g.dx * g.dy * g.dz
+    num0 = fl.n[mask == 1].sum() * dV
+    mom0 = (fl.n * fl.u)[:, mask == 1].sum(axis=1) * dV
+    en0 = oracle.fluid_energy(g, oracle.Fluid(-1.0, 1.0, fl.n * mask, fl.u))
+    sp = oracle.fluid_to_particles(g, mask, fl, 8, 5, 0, 1, rho_bg)
+    assert sp.n == 8 * np.count_nonzero(mask)
+    after = _rho_total(g, [oracle.Particles(-1.0, 1.0, sp.x, sp.y, sp.z, sp.ux, sp.uy, sp.uz, sp.w)], [fl], rho_bg)
+    assert np.max(np.abs(after - before)) < 1e-12 * np.max(np.abs(before))
+    assert sp.w.sum() == pytest.approx(num0, rel=1e-13)
+    assert np.allclose(np.stack([(sp.w * sp.ux).sum(), (sp.w * sp.uy).sum(), (sp.w * sp.uz).sum()]), mom0,
+                       rtol=1e-12, atol=1e-14)
+    assert oracle.energy_particles(sp) == pytest.approx(en0, rel=1e-12)
+    assert np.all(fl.n[mask == 1] == 0)
+    # positions lie in the nodes' dual cells and inside the domain
+    hi = [16, 12, 8] if bc[0] == 0 else [15, 11, 7]
+    for v, h in zip((sp.x, sp.y, sp.z), hi):
+        assert v.min() >= 0 and v.max() <= h
+
+
+def test_particles_to_fluid_keeps_node_charge_number_momentum():
+    g = _grid()
+    rng = np.random.default_rng(3)
+    n = 3000
+    sp = oracle.Particles(-1.0, 1.0, rng.uniform(0, 16, n), rng.uniform(0, 12, n), rng.uniform(0, 8, n),
+                          *(0.2 * rng.standard_normal((3, n))), rng.uniform(0.5, 1.5, n) * 1e-3)
+    fl = oracle.Fluid(-1.0, 1.0, np.full(g.shape, 0.05), 0.1 * rng.standard_normal((3,) + g.shape))
+    mask = (rng.random(g.shape) < 0.5).astype(np.uint8)
+    rho_bg = np.zeros(g.shape)
+    before = _rho_total(g, [sp], [fl], rho_bg)
+    dV = g.dx * g.dy * g.dz
+    num0 = sp.w.sum() + fl.n.sum() * dV
+    mom0 = np.array([(sp.w * sp.ux).sum(), (sp.w * sp.uy).sum(), (sp.w * sp.uz).sum()]) + \
+        (fl.n * fl.u).sum(axis=(1, 2, 3)) * dV
+    k = oracle.particles_to_fluid(g, mask, sp, fl)
+    assert 0 < k < n
+    after = _rho_total(g, [sp], [fl], rho_bg)
+    assert np.max(np.abs(after - before)) < 1e-12 * np.max(np.abs(before))
+    assert sp.w.sum() + fl.n.sum() * dV == pytest.approx(num0, rel=1e-13)
+    mom1 = np.array([(sp.w * sp.ux).sum(), (sp.w * sp.uy).sum(), (sp.w * sp.uz).sum()]) + \
+        (fl.n * fl.u).sum(axis=(1, 2, 3)) * dV
+    assert np.allclose(mom1, mom0, rtol=1e-12, atol=1e-15)
