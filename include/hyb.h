@@ -225,6 +225,29 @@ hyb_status hyb_eval_rate_table(hyb_ctx *ctx, int table, int species_id, int leve
 enum { HYB_QED_H = 0, HYB_QED_T = 1, HYB_QED_EM_SAMPLE = 2, HYB_QED_PAIR_SAMPLE = 3 };
 hyb_status hyb_eval_qed(hyb_ctx *ctx, int what, const float *chi_host, const float *r_host, int n, float *out_host);
 
+/* Field energy without any device allocation.  The paper has no counterpart:
+ * this is a service for callers that cannot call cudaMalloc -- code that must
+ * not synchronise the device mid-loop (cudaMalloc/cudaFree can), code whose
+ * device memory is all owned by another allocator, code with a memory budget
+ * fixed at start-up.  It computes what hyb_diagnostics reports as w_e and w_b,
+ * out_dev[0] = (1/2) sum E^2 dV and out_dev[1] = (1/2) sum B^2 dV (FP64,
+ * deterministic), for E_dev, B_dev laid out like the context's fields (3
+ * component-major FP32 arrays of n_cells values each) and out_dev pointing to 2
+ * doubles, all device memory of the current device; the work is enqueued on
+ * `stream` (cudaStream_t, NULL = legacy default) and the call returns without
+ * waiting.  Block partial sums live in a fixed file-scope device array of
+ * 64 KiB that every GPU loading the library holds until exit, so n_cells is
+ * limited to HYB_NOALLOC_MAX_CELLS (HYB_EINVAL beyond it).  The first call on a
+ * device looks up that array's device address (make it before any stream
+ * capture).  Every call overwrites the partial sums it reads, so nothing needs
+ * clearing, but all calls share the array: calls that overlap on the GPU (on
+ * different streams, or from different threads) race and must be serialised
+ * by the caller.  No cudaMalloc, cudaFree or allocating library routine is
+ * called. */
+#define HYB_NOALLOC_MAX_CELLS 22369621LL
+hyb_status hyb_field_energy_noalloc(const float *E_dev, const float *B_dev, long long n_cells, double dx, double dy,
+                                    double dz, double *out_dev, void *stream);
+
 /* Message for the last failing call on this thread (never NULL). */
 const char *hyb_last_error(void);
 

@@ -86,6 +86,7 @@ PROTOTYPES = {
     "hyb_phase_times": (C.c_int, [_ctx, C.POINTER(hyb_phase_times_t)]),
     "hyb_eval_rate_table": (C.c_int, [_ctx, C.c_int, C.c_int, C.c_int, _P, C.c_int, _P]),
     "hyb_eval_qed": (C.c_int, [_ctx, C.c_int, _P, _P, C.c_int, _P]),
+    "hyb_field_energy_noalloc": (C.c_int, [_P, _P, C.c_longlong, C.c_double, C.c_double, C.c_double, _P, _P]),
 }
 
 _lib = None
