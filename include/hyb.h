@@ -131,9 +131,28 @@ typedef struct {
 
 enum { HYB_KIND_MASSIVE = 0, HYB_KIND_PHOTON = 1 };
 
+/*
+ * A cold relativistic fluid species on the nodes (paper, Methodology: fluid
+ * continuity and momentum equations with relativistic gamma factors for the
+ * bulk plasma in stable regions; clamping against instability).  n is the
+ * density [n_c] and u = gamma beta, each an array of nz*ny*nx values at the
+ * nodes (x fastest); ux/uy/uz may be NULL (u = 0).  Host or device memory as
+ * ptr_on_device says.  Transport is first-order donor cell on the node
+ * control volumes; the face fluxes times q are added to J on the Yee edges,
+ * so charge is conserved exactly.  Where the new density is below n_floor
+ * (0 = 1e-10) u is set to 0; negative densities are clamped to 0 and counted.
+ */
+typedef struct {
+    double q, m;
+    int ptr_on_device;
+    const float *n, *ux, *uy, *uz;
+    double n_floor;
+} hyb_fluid_desc;
+
 /* Diagnostics: FP64 energy reductions (paper, Methodology: total energy from
  * electromagnetic, kinetic and thermal components) and device status. */
 #define HYB_MAX_SPECIES 8
+#define HYB_MAX_FLUIDS 4
 typedef struct {
     long long step;
     double time;                           /* [1/w0] */
@@ -149,6 +168,10 @@ typedef struct {
     double w_pair_deficit;                 /* pair energy below m c^2 that could not become momentum */
     long long n_emit;                      /* photon emission events so far */
     long long n_pair;                      /* pair creation events so far */
+    int n_fluids;
+    double w_fluid[HYB_MAX_FLUIDS];        /* sum n m (gamma - 1) dV per fluid */
+    double n_fluid[HYB_MAX_FLUIDS];        /* sum n dV per fluid */
+    long long n_clamped;                   /* fluid nodes clamped from negative density so far */
 } hyb_diag;
 
 /* Create a context: validates the descriptor, allocates fields on the
@@ -162,6 +185,90 @@ void hyb_destroy(hyb_ctx *ctx);
  * binned into tiles on the device.  HYB_EOVERFLOW if a tile exceeds its
  * capacity. */
 hyb_status hyb_load_species(hyb_ctx *ctx, const hyb_species_desc *desc, int *species_id);
+
+/*
+ * Regime switching (paper, Methodology: fluid in stable regions, PIC where
+ * SwitchNet flags instability; charge and energy checked at switches).  The
+ * paper does not define the instability criterion; the physics criterion
+ * marks a node kinetic when |E| >= a_thr, or the electron density (fluid +
+ * CIC of electron macro-particles) >= n_thr [n_c], or dt div v_e <= -c_thr
+ * (electron fluid), or kappa gamma |E| >= chi_thr; the mask is then dilated by
+ * `dilate` nodes.  With a classifier, a node is kinetic when
+ * p_mean + k_sigma p_std >= 0.5 (same dilation).  Conversions: fluid f at
+ * kinetic nodes becomes ppc macro-particles of species to_species[f]
+ * (Philox-uniform in the node's dual cell, the fluid's u, weight n dV / ppc);
+ * particles of species to_species[f] whose nearest node is fluid are
+ * deposited (CIC) into fluid f.  A residual background charge keeps
+ * div E - rho - rho_bg unchanged across conversions.  to_species[f] = -1:
+ * fluid f is not converted.
+ */
+typedef struct {
+    double a_thr, n_thr, c_thr, chi_thr;  /* 0 = defaults 1, 1, 0.1, 1e-3 */
+    int dilate;                           /* nodes (e.g. 2) */
+    double k_sigma;                       /* classifier decision: p_mean + k_sigma p_std >= 0.5 */
+    int ppc;                              /* macro-particles per node created from fluid */
+    int to_species[HYB_MAX_FLUIDS];
+} hyb_regime_desc;
+hyb_status hyb_set_regime(hyb_ctx *ctx, const hyb_regime_desc *desc);
+
+/* Recompute the regime mask and convert (stream-ordered).  model = NULL uses
+ * the physics criterion; otherwise the classifier runs mc_passes MC-dropout
+ * passes (see hyb_model_*).  Optional device outputs of nz*ny*nx values:
+ * p_mean_dev, p_std_dev (NULL with the physics criterion) and mask_dev
+ * (1 = kinetic). */
+typedef struct hyb_model hyb_model;
+hyb_status hyb_classify(hyb_ctx *ctx, const hyb_model *model, float *p_mean_dev, float *p_std_dev,
+                        uint8_t *mask_dev);
+
+/*
+ * Regime classifier (paper, Methodology and Results: a convolutional network
+ * on per-channel normalised fields decides fluid vs PIC; Monte Carlo dropout
+ * gives its uncertainty; training uses a physics-informed energy term).  The
+ * network is a 3D CNN 6 -> 32 -> 32 -> 16 -> 1 with 3x3x3 kernels, zero
+ * "same" padding, ReLU and dropout(p) after each hidden layer and a sigmoid
+ * output; input channels are E_x, E_y, E_z, B_x, B_y, B_z at the nodes,
+ * normalised per channel as (x - mean_c) / std_c.  Weights are kept in FP32
+ * (Adam master copy) and used in BF16 with FP32 accumulation; activations
+ * between layers are BF16.  Dropout masks come from Philox (key (seed,
+ * 0xD0), counter (cell, batch, layer << 16 | channel / 4, pass)).
+ */
+typedef struct {
+    double dropout;            /* p (e.g. 0.2) */
+    int mc_passes;             /* MC-dropout passes at classification (e.g. 16) */
+    uint32_t seed;             /* initialisation and dropout streams */
+    float mean[6], std[6];     /* per-channel normalisation of the input */
+    double lr, beta1, beta2, eps;  /* Adam (0 = 1e-3, 0.9, 0.999, 1e-8) */
+    double energy_weight;      /* lambda of the energy-weighted BCE (e.g. 0.1) */
+    void *stream;              /* cudaStream_t (NULL: own stream) */
+} hyb_model_desc;
+hyb_status hyb_model_create(const hyb_model_desc *desc, hyb_model **out);
+void hyb_model_destroy(hyb_model *model);
+
+/* Weights as FP32 host arrays in the layout [c_out][c_in][kz][ky][kx] (x
+ * fastest), biases [c_out]; layers 0..3 have (c_in, c_out) = (6, 32),
+ * (32, 32), (32, 16), (16, 1).  hyb_model_create initialises them
+ * He-uniform from the seed. */
+hyb_status hyb_model_set_layer(hyb_model *model, int layer, const float *w_host, const float *b_host);
+hyb_status hyb_model_get_layer(hyb_model *model, int layer, float *w_host, float *b_host);
+
+/* One forward pass over patches x_dev (device FP32, [batch][6][D][H][W]):
+ * writes the logits (device FP32, [batch][D][H][W]).  pass >= 0 applies the
+ * dropout masks of that pass; pass < 0 disables dropout.  W % 8 == 0 and
+ * H % 16 == 0.  Stream-ordered. */
+hyb_status hyb_model_forward(hyb_model *model, const float *x_dev, int batch, int D, int H, int W, int pass,
+                             float *logits_dev);
+
+/* Copy the current mask (uint8, 1 = kinetic) and the residual background
+ * charge rho_bg (FP32) to host arrays of nz*ny*nx values (either may be NULL;
+ * synchronises). */
+hyb_status hyb_get_regime(hyb_ctx *ctx, uint8_t *mask_host, float *rho_bg_host);
+
+/* Add a cold fluid species; writes its id (0, 1, ...) to *fluid_id. */
+hyb_status hyb_load_fluid(hyb_ctx *ctx, const hyb_fluid_desc *desc, int *fluid_id);
+
+/* Copy a fluid back (synchronises): n, ux, uy, uz host arrays of nz*ny*nx
+ * values (any may be NULL). */
+hyb_status hyb_get_fluid(hyb_ctx *ctx, int fluid_id, float *n, float *ux, float *uy, float *uz);
 
 /* Replace the fields E, B (each: 3 contiguous FP32 arrays of nz*ny*nx
  * values, x fastest, Yee-staggered as documented in the library).  Host or
@@ -199,6 +306,7 @@ enum {
     HYB_PH_SOURCE = 2,    /* laser soft source */
     HYB_PH_REBIN = 3,     /* migration + compaction of particle tiles */
     HYB_PH_FIELD = 4,     /* B half, E, Mur, B half */
+    HYB_PH_FLUID = 5,     /* cold fluid Lorentz step, transport, face currents */
     HYB_NPHASE = 8
 };
 typedef struct {

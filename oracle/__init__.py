@@ -131,6 +131,7 @@ def _declare(L):
     L.orc_fluid_to_particles.restype = C.c_long
     L.orc_particles_to_fluid.argtypes = [C.POINTER(Grid), _P, C.POINTER(Species), _P, _D3, C.c_double, _P]
     L.orc_particles_to_fluid.restype = C.c_long
+    L.orc_dropout_mask.argtypes = [_P, C.c_int, C.c_int, C.c_long, C.c_uint32, C.c_uint32, C.c_uint32, C.c_double]
     for name, fn in _EXTRA_DECLS:
         fn(L)
 
@@ -537,3 +538,11 @@ def particles_to_fluid(g, mask, sp, fl):
                                      fl.n_floor, _ptr(alive))
     sp.select(alive[:sp.n].astype(bool))
     return n
+
+
+def dropout_mask(B, C_, V, seed, pass_index, layer, p):
+    """uint8 keep mask [B][C][V] of the classifier's dropout."""
+    keep = np.zeros((B, C_, V), dtype=np.uint8)
+    lib().orc_dropout_mask(_ptr(keep), int(B), int(C_), int(V), int(seed) & 0xFFFFFFFF, int(pass_index),
+                           int(layer), float(p))
+    return keep

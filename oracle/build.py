@@ -9,7 +9,7 @@ import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 SOURCES = ["philox.c", "fdtd.c", "particles.c", "diag.c", "laser.c", "ionize.c",
-           "airy.c", "qed.c", "fluid.c", "regime.c"]
+           "airy.c", "qed.c", "fluid.c", "regime.c", "nn.c"]
 LIB = os.path.join(HERE, "liboracle.so")
 
 

@@ -121,6 +121,10 @@ long orc_fluid_to_particles(const orc_grid *g, const unsigned char *mask, double
 long orc_particles_to_fluid(const orc_grid *g, const unsigned char *mask, orc_species *s, double *n,
                             double *u[3], double n_floor, unsigned char *alive);
 
+/* ---- classifier dropout masks ----------------------------------------------- */
+void orc_dropout_mask(unsigned char *keep, int B, int C, long V, uint32_t seed, uint32_t pass, uint32_t layer,
+                      double p);
+
 /* ---- diagnostics --------------------------------------------------------- */
 void orc_energy_fields(const orc_grid *g, const double *E[3], const double *B[3], double out[2]);
 double orc_energy_particles(const orc_species *s);

@@ -56,15 +56,37 @@ class hyb_diag(C.Structure):
                 ("launches_per_step", C.c_longlong),
                 ("w_ionize", C.c_double), ("n_ionize", C.c_longlong),
                 ("w_photon_untracked", C.c_double), ("w_pair_deficit", C.c_double),
-                ("n_emit", C.c_longlong), ("n_pair", C.c_longlong)]
+                ("n_emit", C.c_longlong), ("n_pair", C.c_longlong),
+                ("n_fluids", C.c_int), ("w_fluid", C.c_double * 4), ("n_fluid", C.c_double * 4),
+                ("n_clamped", C.c_longlong)]
 
 
 HYB_NPHASE = 8
-PHASES = ["push", "j_reduce", "source", "rebin", "field", "ph5", "ph6", "ph7"]
+PHASES = ["push", "j_reduce", "source", "rebin", "field", "fluid", "ph6", "ph7"]
+HYB_MAX_FLUIDS = 4
+
+
+class hyb_fluid_desc(C.Structure):
+    _fields_ = [("q", C.c_double), ("m", C.c_double), ("ptr_on_device", C.c_int),
+                ("n", C.c_void_p), ("ux", C.c_void_p), ("uy", C.c_void_p), ("uz", C.c_void_p),
+                ("n_floor", C.c_double)]
 
 
 class hyb_phase_times_t(C.Structure):
     _fields_ = [("ms", C.c_float * HYB_NPHASE)]
+
+
+class hyb_regime_desc(C.Structure):
+    _fields_ = [("a_thr", C.c_double), ("n_thr", C.c_double), ("c_thr", C.c_double), ("chi_thr", C.c_double),
+                ("dilate", C.c_int), ("k_sigma", C.c_double), ("ppc", C.c_int),
+                ("to_species", C.c_int * 4)]
+
+
+class hyb_model_desc(C.Structure):
+    _fields_ = [("dropout", C.c_double), ("mc_passes", C.c_int), ("seed", C.c_uint32),
+                ("mean", C.c_float * 6), ("std", C.c_float * 6),
+                ("lr", C.c_double), ("beta1", C.c_double), ("beta2", C.c_double), ("eps", C.c_double),
+                ("energy_weight", C.c_double), ("stream", C.c_void_p)]
 
 
 _P = C.c_void_p
@@ -86,7 +108,17 @@ PROTOTYPES = {
     "hyb_phase_times": (C.c_int, [_ctx, C.POINTER(hyb_phase_times_t)]),
     "hyb_eval_rate_table": (C.c_int, [_ctx, C.c_int, C.c_int, C.c_int, _P, C.c_int, _P]),
     "hyb_eval_qed": (C.c_int, [_ctx, C.c_int, _P, _P, C.c_int, _P]),
-    "hyb_field_energy_noalloc": (C.c_int, [_P, _P, C.c_longlong, C.c_double, C.c_double, C.c_double, _P, _P]),
+    "hyb_load_fluid": (C.c_int, [_ctx, C.c_void_p, C.POINTER(C.c_int)]),
+    "hyb_set_regime": (C.c_int, [_ctx, C.POINTER(hyb_regime_desc)]),
+    "hyb_classify": (C.c_int, [_ctx, _P, _P, _P, _P]),
+    "hyb_get_regime": (C.c_int, [_ctx, _P, _P]),
+    "hyb_model_create": (C.c_int, [C.POINTER(hyb_model_desc), C.POINTER(C.c_void_p)]),
+    "hyb_model_destroy": (None, [_P]),
+    "hyb_model_set_layer": (C.c_int, [_P, C.c_int, _P, _P]),
+    "hyb_model_get_layer": (C.c_int, [_P, C.c_int, _P, _P]),
+    "hyb_model_forward": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _P]),
+    "hyb_get_fluid": (C.c_int, [_ctx, C.c_int, _P, _P, _P, _P]),
+    "hyb_field_energy_noalloc":(C.c_int, [_P, _P, C.c_longlong, C.c_double, C.c_double, C.c_double, _P, _P]),
 }
 
 _lib = None

@@ -87,6 +87,11 @@ static void enqueue_step(hyb_ctx *c) {
     } else {
         cudaMemsetAsync(c->J, 0, sizeof(float) * 3 * g.N, st);
     }
+    if (!c->fluids.empty()) {
+        pm.begin(HYB_PH_FLUID);
+        for (const FluidDev &f : c->fluids) launch_fluid(g, c->E, c->B, f, c->J, st);
+        pm.end(HYB_PH_FLUID);
+    }
     if (c->desc.laser_kind == HYB_LASER_GAUSS) {
         pm.begin(HYB_PH_SOURCE);
         launch_laser_source(g, c->desc, c->laser_profile, c->step_dev, c->J, st);
@@ -111,6 +116,7 @@ static void enqueue_step(hyb_ctx *c) {
     // kernels enqueued above (memsets and event records are not kernels)
     long long k = 0;
     if (set.n > 0) k += 2 + 2LL * set.n;
+    k += 2LL * (long long)c->fluids.size();
     if (c->desc.laser_kind == HYB_LASER_GAUSS) k += 1;
     k += 3 + ((g.bc[0] || g.bc[1] || g.bc[2]) ? 3 : 0) + 1;
     c->launches_per_step = k;
@@ -121,6 +127,8 @@ static void enqueue_step(hyb_ctx *c) {
 using namespace hyb;
 
 extern "C" {
+
+static hyb_status read_status(hyb_ctx *c);
 
 const char *hyb_last_error(void) { return g_err.c_str(); }
 
@@ -200,11 +208,14 @@ hyb_status hyb_init_grid(const hyb_grid_desc *d, hyb_ctx **out) {
         ctx_alloc(c, (void **)&c->J, fbytes) ||
         ctx_alloc(c, (void **)&c->mur_old, sizeof(float) * 24 * (size_t)c->mur_plane) ||
         ctx_alloc(c, (void **)&c->jscratch, sizeof(float) * (size_t)c->jframe * g.ntiles) ||
-        ctx_alloc(c, (void **)&c->red_partials, sizeof(double) * (2 + HYB_MAX_SPECIES) * c->red_blocks) ||
-        ctx_alloc(c, (void **)&c->red_out, sizeof(double) * (2 + HYB_MAX_SPECIES)) ||
+        ctx_alloc(c, (void **)&c->red_partials, sizeof(double) * (2 + HYB_MAX_SPECIES + 2 * HYB_MAX_FLUIDS) * c->red_blocks) ||
+        ctx_alloc(c, (void **)&c->red_out, sizeof(double) * (2 + HYB_MAX_SPECIES + 2 * HYB_MAX_FLUIDS)) ||
         ctx_alloc(c, (void **)&c->status, sizeof(int)) || ctx_alloc(c, (void **)&c->step_dev, sizeof(long long)) ||
         ctx_alloc(c, (void **)&c->mig_counts, sizeof(int) * HYB_MAX_SPECIES) ||
-        ctx_alloc(c, (void **)&c->sp_dev, sizeof(SpDev) * HYB_MAX_SPECIES))
+        ctx_alloc(c, (void **)&c->sp_dev, sizeof(SpDev) * HYB_MAX_SPECIES) ||
+        ctx_alloc(c, (void **)&c->mask, (size_t)g.N) || ctx_alloc(c, (void **)&c->mask_tmp, (size_t)g.N) ||
+        ctx_alloc(c, (void **)&c->rho_bg, sizeof(float) * (size_t)g.N) ||
+        ctx_alloc(c, (void **)&c->ne, sizeof(float) * (size_t)g.N))
         return fail(HYB_ENOMEM, "device allocation for the grid failed (arena too small?)");
     cudaStream_t st = c->stream;
     cudaMemsetAsync(c->E, 0, fbytes, st);
@@ -213,6 +224,16 @@ hyb_status hyb_init_grid(const hyb_grid_desc *d, hyb_ctx **out) {
     cudaMemsetAsync(c->mur_old, 0, sizeof(float) * 24 * (size_t)c->mur_plane, st);
     cudaMemsetAsync(c->status, 0, sizeof(int), st);
     cudaMemsetAsync(c->step_dev, 0, sizeof(long long), st);
+    cudaMemsetAsync(c->mask, 1, (size_t)g.N, st);  // everything kinetic until a classification
+    cudaMemsetAsync(c->rho_bg, 0, sizeof(float) * (size_t)g.N, st);
+    c->regime.a_thr = 1.0;
+    c->regime.n_thr = 1.0;
+    c->regime.c_thr = 0.1;
+    c->regime.chi_thr = 1e-3;
+    c->regime.dilate = 2;
+    c->regime.k_sigma = 1.0;
+    c->regime.ppc = 8;
+    for (int f = 0; f < HYB_MAX_FLUIDS; ++f) c->regime.to_species[f] = -1;
 
     if (d->laser_kind == HYB_LASER_GAUSS) {
         // transverse profile f = exp(-r^2 / w0^2) at the J_pol positions of the source plane, FP64
@@ -523,6 +544,98 @@ hyb_status hyb_load_species(hyb_ctx *c, const hyb_species_desc *d, int *species_
     return HYB_OK;
 }
 
+hyb_status hyb_load_fluid(hyb_ctx *c, const hyb_fluid_desc *d, int *fluid_id) {
+    if (!c || !d || !fluid_id || !d->n) return set_error(HYB_EINVAL, "null argument");
+    if ((int)c->fluids.size() >= HYB_MAX_FLUIDS) return set_error(HYB_EINVAL, "too many fluids");
+    if (!(d->m > 0.0)) return set_error(HYB_EINVAL, "fluid mass must be > 0");
+    const size_t N = (size_t)c->g.N;
+    FluidDev f;
+    memset(&f, 0, sizeof(f));
+    float **bufs[8] = {&f.n, &f.ux, &f.uy, &f.uz, &f.ns, &f.usx, &f.usy, &f.usz};
+    for (auto b : bufs)
+        if (ctx_alloc(c, (void **)b, sizeof(float) * N)) return set_error(HYB_ENOMEM, "fluid allocation failed");
+    if (ctx_alloc(c, (void **)&f.clamped, sizeof(unsigned long long)))
+        return set_error(HYB_ENOMEM, "fluid allocation failed");
+    f.q = (float)d->q;
+    f.m = (float)d->m;
+    f.m_d = d->m;
+    f.n_floor = d->n_floor > 0.0 ? (float)d->n_floor : 1e-10f;
+    const cudaMemcpyKind kind = d->ptr_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    const float *src[4] = {d->n, d->ux, d->uy, d->uz};
+    float *dst[4] = {f.n, f.ux, f.uy, f.uz};
+    for (int k = 0; k < 4; ++k) {
+        if (src[k]) HYB_CUDA_TRY(cudaMemcpyAsync(dst[k], src[k], sizeof(float) * N, kind, c->stream));
+        else HYB_CUDA_TRY(cudaMemsetAsync(dst[k], 0, sizeof(float) * N, c->stream));
+    }
+    HYB_CUDA_TRY(cudaMemsetAsync(f.clamped, 0, sizeof(unsigned long long), c->stream));
+    HYB_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    *fluid_id = (int)c->fluids.size();
+    c->fluids.push_back(f);
+    c->graph_valid = false;
+    return HYB_OK;
+}
+
+hyb_status hyb_set_regime(hyb_ctx *c, const hyb_regime_desc *d) {
+    if (!c || !d) return set_error(HYB_EINVAL, "null argument");
+    if (d->dilate < 0 || d->dilate > 8) return set_error(HYB_EINVAL, "dilate must be in 0..8");
+    if (d->ppc < 0 || d->ppc > 64) return set_error(HYB_EINVAL, "ppc must be in 0..64");
+    for (int f = 0; f < HYB_MAX_FLUIDS; ++f)
+        if (d->to_species[f] >= (int)c->sp.size() ||
+            (d->to_species[f] >= 0 && c->sp[d->to_species[f]].dev.kind != HYB_KIND_MASSIVE))
+            return set_error(HYB_EINVAL, "to_species must name a loaded massive species or -1");
+    hyb_regime_desc r = *d;
+    if (!(r.a_thr > 0.0)) r.a_thr = 1.0;
+    if (!(r.n_thr > 0.0)) r.n_thr = 1.0;
+    if (!(r.c_thr > 0.0)) r.c_thr = 0.1;
+    if (!(r.chi_thr > 0.0)) r.chi_thr = 1e-3;
+    if (r.ppc == 0) r.ppc = 8;
+    c->regime = r;
+    return HYB_OK;
+}
+
+hyb_status hyb_classify(hyb_ctx *c, const hyb_model *model, float *p_mean_dev, float *p_std_dev, uint8_t *mask_dev) {
+    if (!c) return set_error(HYB_EINVAL, "null context");
+    if (c->error_latched) return set_error(HYB_ESTATE, "context is in an error state (hyb_clear_status)");
+    for (size_t f = 0; f < c->fluids.size(); ++f) {
+        const int sid = c->regime.to_species[f];
+        if (sid >= 0 && (c->sp[sid].q != (double)c->fluids[f].q || c->sp[sid].m != c->fluids[f].m_d))
+            return set_error(HYB_EINVAL, "a fluid converts into a species of the same charge and mass");
+    }
+    hyb_status s;
+    if (model) {
+        s = classifier_forward(c, model, p_mean_dev, p_std_dev);
+        if (s != HYB_OK) return s;
+        s = regime_update(c, model_p_mean(model), model_p_std(model));
+    } else {
+        s = regime_update(c, nullptr, nullptr);
+    }
+    if (s != HYB_OK) return s;
+    if (mask_dev) HYB_CUDA_TRY(cudaMemcpyAsync(mask_dev, c->mask, (size_t)c->g.N, cudaMemcpyDeviceToDevice, c->stream));
+    return HYB_OK;
+}
+
+hyb_status hyb_get_regime(hyb_ctx *c, uint8_t *mask, float *rho_bg) {
+    if (!c) return set_error(HYB_EINVAL, "null context");
+    if (mask) HYB_CUDA_TRY(cudaMemcpyAsync(mask, c->mask, (size_t)c->g.N, cudaMemcpyDeviceToHost, c->stream));
+    if (rho_bg)
+        HYB_CUDA_TRY(cudaMemcpyAsync(rho_bg, c->rho_bg, sizeof(float) * (size_t)c->g.N, cudaMemcpyDeviceToHost,
+                                     c->stream));
+    HYB_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return read_status(c);
+}
+
+hyb_status hyb_get_fluid(hyb_ctx *c, int id, float *n, float *ux, float *uy, float *uz) {
+    if (!c || id < 0 || id >= (int)c->fluids.size()) return set_error(HYB_EINVAL, "bad fluid id");
+    const FluidDev &f = c->fluids[id];
+    const size_t bytes = sizeof(float) * (size_t)c->g.N;
+    float *dst[4] = {n, ux, uy, uz};
+    const float *src[4] = {f.n, f.ux, f.uy, f.uz};
+    for (int k = 0; k < 4; ++k)
+        if (dst[k]) HYB_CUDA_TRY(cudaMemcpyAsync(dst[k], src[k], bytes, cudaMemcpyDeviceToHost, c->stream));
+    HYB_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return HYB_OK;
+}
+
 hyb_status hyb_set_fields(hyb_ctx *c, const float *E, const float *B, int on_device) {
     if (!c || !E || !B) return set_error(HYB_EINVAL, "null argument");
     const size_t fbytes = sizeof(float) * 3 * (size_t)c->g.N;
@@ -625,9 +738,15 @@ hyb_status hyb_diagnostics(hyb_ctx *c, hyb_diag *out) {
     if (!c || !out) return set_error(HYB_EINVAL, "null argument");
     memset(out, 0, sizeof(*out));
     const SpSet set = species_set(c);
-    launch_energy(c->g, c->E, c->B, set, c->red_partials, c->red_blocks, c->red_out, c->status, c->stream);
-    double r[2 + HYB_MAX_SPECIES];
-    HYB_CUDA_TRY(cudaMemcpyAsync(r, c->red_out, sizeof(double) * (2 + set.n), cudaMemcpyDeviceToHost, c->stream));
+    const int nfl = (int)c->fluids.size();
+    for (int f = 0; f < nfl; ++f) {
+        double *pw = c->red_partials + (long long)(2 + set.n + 2 * f) * c->red_blocks;
+        launch_fluid_energy(c->g, c->fluids[f], pw, pw + c->red_blocks, c->red_blocks, c->stream);
+    }
+    launch_energy(c->g, c->E, c->B, set, c->red_partials, c->red_blocks, c->red_out, c->status, c->stream, 2 * nfl);
+    double r[2 + HYB_MAX_SPECIES + 2 * HYB_MAX_FLUIDS];
+    HYB_CUDA_TRY(cudaMemcpyAsync(r, c->red_out, sizeof(double) * (2 + set.n + 2 * nfl), cudaMemcpyDeviceToHost,
+                                 c->stream));
     int h = 0;
     HYB_CUDA_TRY(cudaMemcpyAsync(&h, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     std::vector<int> cnt((size_t)c->g.ntiles);
@@ -648,6 +767,15 @@ hyb_status hyb_diagnostics(hyb_ctx *c, hyb_diag *out) {
     for (int s = 0; s < set.n; ++s) out->w_kin[s] = r[2 + s];
     out->status = status_to_code(h);
     out->launches_per_step = c->launches_per_step;
+    out->n_fluids = nfl;
+    for (int f = 0; f < nfl; ++f) {
+        out->w_fluid[f] = r[2 + set.n + 2 * f];
+        out->n_fluid[f] = r[2 + set.n + 2 * f + 1];
+        unsigned long long cl = 0;
+        HYB_CUDA_TRY(cudaMemcpyAsync(&cl, c->fluids[f].clamped, sizeof(cl), cudaMemcpyDeviceToHost, c->stream));
+        HYB_CUDA_TRY(cudaStreamSynchronize(c->stream));
+        out->n_clamped += (long long)cl;
+    }
     // event tallies: per-tile FP64 accumulators summed here in tile order
     std::vector<double> te((size_t)c->g.ntiles * NTALLY);
     std::vector<unsigned long long> tn((size_t)c->g.ntiles * NTALLY);

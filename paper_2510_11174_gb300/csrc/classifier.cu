@@ -1,0 +1,401 @@
+// The regime classifier around the tensor-core convolution (arXiv 2510.11174,
+// Methodology and Results: convolutional network on per-channel normalised
+// fields; Monte Carlo dropout for the uncertainty of the switch).
+//
+// Network: conv3(6->32) ReLU drop, conv3(32->32) ReLU drop, conv3(32->16) ReLU
+// drop, conv3(16->1), sigmoid.  Layers 0-2 run on the tensor cores
+// (k_conv3_tc, BF16 operands, FP32 accumulation, BF16 channels-last
+// activations); the 16->1 layer is a 432-MAC dot product per cell on the CUDA
+// cores with BF16-rounded weights.  Classification runs mc_passes passes with
+// independent dropout masks and keeps the running mean and variance of the
+// sigmoid per node (Welford).
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include <cuda_bf16.h>
+
+#include "conv_tc.cuh"
+#include "hyb_internal.cuh"
+#include "philox.cuh"
+
+
+static constexpr int NL = 4;
+static constexpr int CIN[NL] = {6, 32, 32, 16}, COUT[NL] = {32, 32, 16, 1};
+static constexpr int CINP[NL] = {16, 32, 32, 16};  // input channels padded for the tensor-core layout
+
+struct hyb_model {
+    hyb_model_desc d;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    float *w[NL] = {}, *b[NL] = {};      // FP32 master weights [co][ci][27], biases
+    float *mw[NL] = {}, *vw[NL] = {}, *mb[NL] = {}, *vb[NL] = {};  // Adam moments
+    __nv_bfloat16 *wt[3] = {};           // packed forward weights, layers 0..2
+    __nv_bfloat16 *wtT[3] = {};          // packed transposed + flipped (data gradient)
+    float *w4r = nullptr;                // layer 3 weights rounded to BF16 (as FP32), [16][27]
+    float *mean = nullptr, *std_ = nullptr;
+    // activation buffers (capacity in cells)
+    long long cap = 0;
+    __nv_bfloat16 *x0 = nullptr, *a1 = nullptr, *a2 = nullptr, *a3 = nullptr;
+    float *logit = nullptr, *pm = nullptr, *ps = nullptr;
+    int *status = nullptr;
+    long long adam_t = 0;
+    std::vector<void *> owned;
+};
+
+namespace hyb {
+
+static cudaError_t m_alloc(hyb_model *m, void **p, size_t bytes) {
+    cudaError_t e = cudaMalloc(p, bytes ? bytes : 256);
+    if (e == cudaSuccess) m->owned.push_back(*p);
+    return e;
+}
+
+// forward pack: wt[tap][kc][n][8] = W[n][kc*8+j][tap] (zero for padded channels)
+// transposed: the data gradient is the convolution of dY with W^T flipped:
+// wtT[tap'][kc][ci][8] = W[kc*8+j][ci][26 - tap']
+__global__ void k_pack(const float *__restrict__ W, int cin, int cinp, int cout, int transpose,
+                       __nv_bfloat16 *__restrict__ out) {
+    const int ci_n = transpose ? cout : cinp;  // input channels of the packed conv
+    const int n_n = transpose ? cin : cout;    // output channels of the packed conv
+    const int KC = ci_n / 8;
+    const int total = 27 * KC * n_n * 8;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= total) return;
+    const int j = t % 8, n = (t / 8) % n_n, kc = (t / (8 * n_n)) % KC, tap = t / (8 * n_n * KC);
+    const int c = kc * 8 + j;
+    float v = 0.0f;
+    if (!transpose) {
+        if (c < cin) v = W[((long long)n * cin + c) * 27 + tap];
+    } else {
+        if (c < cout && n < cin) v = W[((long long)c * cin + n) * 27 + (26 - tap)];
+    }
+    out[t] = __float2bfloat16_rn(v);
+}
+
+__global__ void k_round_bf16(const float *__restrict__ in, float *__restrict__ out, int n) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) out[t] = __bfloat162float(__float2bfloat16_rn(in[t]));
+}
+
+// patches [B][6][D][H][W] FP32 -> normalised BF16 channels-last [B][D][H][W][16]
+__global__ void k_prep_patches_cl(const float *__restrict__ x, int B, long long V, const float *__restrict__ mean,
+                                  const float *__restrict__ sd, __nv_bfloat16 *__restrict__ out) {
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= (long long)B * V) return;
+    const long long b = t / V, v = t % V;
+    __align__(16) __nv_bfloat16 o[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+        float s = 0.0f;
+        if (c < 6) s = (x[(b * 6 + c) * V + v] - mean[c]) / sd[c];
+        o[c] = __float2bfloat16_rn(s);
+    }
+    uint4 *dst = reinterpret_cast<uint4 *>(out + t * 16);
+    dst[0] = reinterpret_cast<const uint4 *>(o)[0];
+    dst[1] = reinterpret_cast<const uint4 *>(o)[1];
+}
+
+// context fields at the nodes (E averaged from the Yee edges, B from the four
+// faces around the node) -> normalised BF16 channels-last [D=nz][H=ny][W=nx][16]
+__global__ void k_prep_fields(GridDev g, const float *__restrict__ E, const float *__restrict__ Bf,
+                              const float *__restrict__ mean, const float *__restrict__ sd,
+                              __nv_bfloat16 *__restrict__ out) {
+    const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (c >= g.N) return;
+    const int nx = g.n[0], ny = g.n[1];
+    const int i = (int)(c % nx), j = (int)((c / nx) % ny), k = (int)(c / ((long long)nx * ny));
+    auto fv = [&](const float *F, int a, int bb, int cc) -> float {
+        int idx[3] = {a, bb, cc};
+        for (int ax = 0; ax < 3; ++ax) {
+            if (g.bc[ax] == 0) idx[ax] = idx[ax] < 0 ? idx[ax] + g.n[ax] : (idx[ax] >= g.n[ax] ? idx[ax] - g.n[ax] : idx[ax]);
+            else if (idx[ax] < 0 || idx[ax] > g.n[ax] - 1) return 0.0f;
+        }
+        return F[cidx(g, idx[0], idx[1], idx[2])];
+    };
+    const long long N = g.N;
+    float f[6];
+    f[0] = 0.5f * (fv(E, i - 1, j, k) + fv(E, i, j, k));
+    f[1] = 0.5f * (fv(E + N, i, j - 1, k) + fv(E + N, i, j, k));
+    f[2] = 0.5f * (fv(E + 2 * N, i, j, k - 1) + fv(E + 2 * N, i, j, k));
+    f[3] = 0.25f * (fv(Bf, i, j - 1, k - 1) + fv(Bf, i, j, k - 1) + fv(Bf, i, j - 1, k) + fv(Bf, i, j, k));
+    f[4] = 0.25f * (fv(Bf + N, i - 1, j, k - 1) + fv(Bf + N, i, j, k - 1) + fv(Bf + N, i - 1, j, k) +
+                    fv(Bf + N, i, j, k));
+    f[5] = 0.25f * (fv(Bf + 2 * N, i - 1, j - 1, k) + fv(Bf + 2 * N, i, j - 1, k) + fv(Bf + 2 * N, i - 1, j, k) +
+                    fv(Bf + 2 * N, i, j, k));
+    __align__(16) __nv_bfloat16 o[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) o[q] = __float2bfloat16_rn(q < 6 ? (f[q] - mean[q]) / sd[q] : 0.0f);
+    uint4 *dst = reinterpret_cast<uint4 *>(out + c * 16);
+    dst[0] = reinterpret_cast<const uint4 *>(o)[0];
+    dst[1] = reinterpret_cast<const uint4 *>(o)[1];
+}
+
+// the 16 -> 1 layer on CUDA cores: logit = b + sum_tap sum_ci W[ci][tap] a3[cell + tap - 1][ci]
+__global__ void k_conv_last(const __nv_bfloat16 *__restrict__ a3, int B, int D, int H, int W,
+                            const float *__restrict__ w4r, const float *__restrict__ b4, float *__restrict__ logit) {
+    __shared__ float ws[16 * 27];
+    for (int i = threadIdx.x; i < 16 * 27; i += blockDim.x) ws[i] = w4r[i];
+    __syncthreads();
+    const long long V = (long long)D * H * W;
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= (long long)B * V) return;
+    const long long b = t / V, v = t % V;
+    const int x = (int)(v % W), y = (int)((v / W) % H), z = (int)(v / ((long long)W * H));
+    float acc = b4[0];
+    for (int tap = 0; tap < 27; ++tap) {
+        const int zz = z + tap / 9 - 1, yy = y + (tap / 3) % 3 - 1, xx = x + tap % 3 - 1;
+        if (zz < 0 || zz >= D || yy < 0 || yy >= H || xx < 0 || xx >= W) continue;
+        const __nv_bfloat16 *src = a3 + ((b * V) + ((long long)zz * H + yy) * W + xx) * 16;
+        __align__(16) __nv_bfloat16 h[16];
+        reinterpret_cast<uint4 *>(h)[0] = reinterpret_cast<const uint4 *>(src)[0];
+        reinterpret_cast<uint4 *>(h)[1] = reinterpret_cast<const uint4 *>(src)[1];
+#pragma unroll
+        for (int ci = 0; ci < 16; ++ci) acc += ws[ci * 27 + tap] * __bfloat162float(h[ci]);
+    }
+    logit[t] = acc;
+}
+
+// Welford update of the per-node mean / M2 of sigmoid(logit) for pass k (1-based)
+__global__ void k_mc_update(long long n, const float *__restrict__ logit, int k, float *__restrict__ pm,
+                            float *__restrict__ m2) {
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const float p = 1.0f / (1.0f + expf(-logit[t]));
+    if (k == 1) {
+        pm[t] = p;
+        m2[t] = 0.0f;
+        return;
+    }
+    const float d = p - pm[t];
+    pm[t] += d / (float)k;
+    m2[t] += d * (p - pm[t]);
+}
+
+__global__ void k_mc_final(long long n, int k, const float *__restrict__ m2, float *__restrict__ ps) {
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t < n) ps[t] = sqrtf(fmaxf(m2[t], 0.0f) / (float)k);  // population standard deviation over the passes
+}
+
+static inline unsigned nb(long long n, int b = 256) { return (unsigned)((n + b - 1) / b); }
+
+hyb_status model_repack(hyb_model *m) {
+    for (int l = 0; l < 3; ++l) {
+        const int tot = 27 * (CINP[l] / 8) * COUT[l] * 8;
+        k_pack<<<nb(tot), 256, 0, m->stream>>>(m->w[l], CIN[l], CINP[l], COUT[l], 0, m->wt[l]);
+        const int totT = 27 * (COUT[l] / 8) * CIN[l] * 8;
+        if (l > 0) k_pack<<<nb(totT), 256, 0, m->stream>>>(m->w[l], CIN[l], CINP[l], COUT[l], 1, m->wtT[l]);
+    }
+    k_round_bf16<<<nb(16 * 27), 256, 0, m->stream>>>(m->w[3], m->w4r, 16 * 27);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return set_error(HYB_ECUDA, std::string("weight packing: ") + cudaGetErrorString(e));
+    return HYB_OK;
+}
+
+static hyb_status model_reserve(hyb_model *m, long long cells) {
+    if (cells <= m->cap) return HYB_OK;
+    // buffers are replaced only between stream-ordered uses
+    cudaStreamSynchronize(m->stream);
+    void *bufs[7] = {m->x0, m->a1, m->a2, m->a3, m->logit, m->pm, m->ps};
+    for (void *p : bufs) {
+        if (!p) continue;
+        for (auto it = m->owned.begin(); it != m->owned.end(); ++it)
+            if (*it == p) {
+                m->owned.erase(it);
+                break;
+            }
+        cudaFree(p);
+    }
+    if (m_alloc(m, (void **)&m->x0, sizeof(__nv_bfloat16) * 16 * cells) ||
+        m_alloc(m, (void **)&m->a1, sizeof(__nv_bfloat16) * 32 * cells) ||
+        m_alloc(m, (void **)&m->a2, sizeof(__nv_bfloat16) * 32 * cells) ||
+        m_alloc(m, (void **)&m->a3, sizeof(__nv_bfloat16) * 16 * cells) ||
+        m_alloc(m, (void **)&m->logit, sizeof(float) * cells) || m_alloc(m, (void **)&m->pm, sizeof(float) * cells) ||
+        m_alloc(m, (void **)&m->ps, sizeof(float) * cells))
+        return set_error(HYB_ENOMEM, "classifier activation buffers");
+    m->cap = cells;
+    return HYB_OK;
+}
+
+// layers 0..3 on the prepared input m->x0 (B x D x H x W cells) -> m->logit
+static hyb_status model_run(hyb_model *m, int B, int D, int H, int W, int pass) {
+    const float p = pass >= 0 ? (float)m->d.dropout : 0.0f;
+    __nv_bfloat16 *ins[3] = {m->x0, m->a1, m->a2}, *outs[3] = {m->a1, m->a2, m->a3};
+    for (int l = 0; l < 3; ++l) {
+        ConvArgs a;
+        a.x = ins[l];
+        a.wt = m->wt[l];
+        a.bias = m->b[l];
+        a.y = outs[l];
+        a.B = B;
+        a.D = D;
+        a.H = H;
+        a.W = W;
+        a.cin = CINP[l];
+        a.N = COUT[l];
+        a.relu = 1;
+        a.drop_p = p;
+        a.seed = m->d.seed;
+        a.pass = (uint32_t)(pass >= 0 ? pass : 0);
+        a.layer = (uint32_t)l;
+        a.status = m->status;
+        hyb_status s = launch_conv3_tc(a, m->stream);
+        if (s != HYB_OK) return s;
+    }
+    const long long cells = (long long)B * D * H * W;
+    k_conv_last<<<nb(cells), 256, 0, m->stream>>>(m->a3, B, D, H, W, m->w4r, m->b[3], m->logit);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return set_error(HYB_ECUDA, std::string("classifier: ") + cudaGetErrorString(e));
+    return HYB_OK;
+}
+
+hyb_status classifier_forward(hyb_ctx *c, const hyb_model *mc, float *p_mean_dev, float *p_std_dev) {
+    hyb_model *m = const_cast<hyb_model *>(mc);
+    const GridDev &g = c->g;
+    const int D = g.n[2], H = g.n[1], W = g.n[0];
+    if (W % 8 != 0 || H % 16 != 0) return set_error(HYB_EINVAL, "classifier needs nx % 8 == 0 and ny % 16 == 0");
+    hyb_status s = model_reserve(m, g.N);
+    if (s != HYB_OK) return s;
+    // the model runs on the context's stream for the classification
+    cudaStream_t saved = m->stream;
+    m->stream = c->stream;
+    k_prep_fields<<<nb(g.N), 256, 0, c->stream>>>(g, c->E, c->B, m->mean, m->std_, m->x0);
+    const int K = m->d.mc_passes > 0 ? m->d.mc_passes : 1;
+    for (int k = 1; k <= K && s == HYB_OK; ++k) {
+        s = model_run(m, 1, D, H, W, K > 1 ? k - 1 : -1);
+        if (s == HYB_OK) k_mc_update<<<nb(g.N), 256, 0, c->stream>>>(g.N, m->logit, k, m->pm, m->ps);
+    }
+    if (s == HYB_OK) {
+        // ps held M2; turn it into the standard deviation in place
+        k_mc_final<<<nb(g.N), 256, 0, c->stream>>>(g.N, K, m->ps, m->ps);
+        if (p_mean_dev) cudaMemcpyAsync(p_mean_dev, m->pm, sizeof(float) * g.N, cudaMemcpyDeviceToDevice, c->stream);
+        if (p_std_dev) cudaMemcpyAsync(p_std_dev, m->ps, sizeof(float) * g.N, cudaMemcpyDeviceToDevice, c->stream);
+    }
+    m->stream = saved;
+    return s;
+}
+
+const float *model_p_mean(const hyb_model *m) { return m->pm; }
+const float *model_p_std(const hyb_model *m) { return m->ps; }
+
+}  // namespace hyb
+
+using namespace hyb;
+
+extern "C" {
+
+hyb_status hyb_model_create(const hyb_model_desc *d, hyb_model **out) {
+    if (!d || !out) return set_error(HYB_EINVAL, "null argument");
+    *out = nullptr;
+    if (!(d->dropout >= 0.0 && d->dropout < 1.0)) return set_error(HYB_EINVAL, "dropout must be in [0, 1)");
+    for (int c = 0; c < 6; ++c)
+        if (!(d->std[c] > 0.0f)) return set_error(HYB_EINVAL, "normalisation std must be > 0");
+    hyb_model *m = new hyb_model();
+    m->d = *d;
+    if (!(m->d.lr > 0)) m->d.lr = 1e-3;
+    if (!(m->d.beta1 > 0)) m->d.beta1 = 0.9;
+    if (!(m->d.beta2 > 0)) m->d.beta2 = 0.999;
+    if (!(m->d.eps > 0)) m->d.eps = 1e-8;
+    if (d->stream) {
+        m->stream = (cudaStream_t)d->stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&m->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete m;
+            return set_error(HYB_ECUDA, "stream create");
+        }
+        m->own_stream = true;
+    }
+    auto fail = [&](const char *msg) {
+        hyb_model_destroy(m);
+        return set_error(HYB_ENOMEM, msg);
+    };
+    for (int l = 0; l < NL; ++l) {
+        const size_t nw = (size_t)COUT[l] * CIN[l] * 27;
+        if (m_alloc(m, (void **)&m->w[l], sizeof(float) * nw) || m_alloc(m, (void **)&m->b[l], sizeof(float) * COUT[l]) ||
+            m_alloc(m, (void **)&m->mw[l], sizeof(float) * nw) || m_alloc(m, (void **)&m->vw[l], sizeof(float) * nw) ||
+            m_alloc(m, (void **)&m->mb[l], sizeof(float) * COUT[l]) ||
+            m_alloc(m, (void **)&m->vb[l], sizeof(float) * COUT[l]))
+            return fail("model allocation");
+        cudaMemsetAsync(m->mw[l], 0, sizeof(float) * nw, m->stream);
+        cudaMemsetAsync(m->vw[l], 0, sizeof(float) * nw, m->stream);
+        cudaMemsetAsync(m->mb[l], 0, sizeof(float) * COUT[l], m->stream);
+        cudaMemsetAsync(m->vb[l], 0, sizeof(float) * COUT[l], m->stream);
+    }
+    for (int l = 0; l < 3; ++l) {
+        if (m_alloc(m, (void **)&m->wt[l], sizeof(__nv_bfloat16) * 27 * CINP[l] * COUT[l]) ||
+            m_alloc(m, (void **)&m->wtT[l], sizeof(__nv_bfloat16) * 27 * COUT[l] * CIN[l] + 256))
+            return fail("model allocation");
+    }
+    if (m_alloc(m, (void **)&m->w4r, sizeof(float) * 16 * 27) || m_alloc(m, (void **)&m->mean, sizeof(float) * 6) ||
+        m_alloc(m, (void **)&m->std_, sizeof(float) * 6) || m_alloc(m, (void **)&m->status, sizeof(int)))
+        return fail("model allocation");
+    cudaMemcpyAsync(m->mean, d->mean, sizeof(float) * 6, cudaMemcpyHostToDevice, m->stream);
+    cudaMemcpyAsync(m->std_, d->std, sizeof(float) * 6, cudaMemcpyHostToDevice, m->stream);
+    cudaMemsetAsync(m->status, 0, sizeof(int), m->stream);
+    // He-uniform initialisation from the seed (Philox on the host):
+    // w ~ U(-sqrt(6/fan_in), sqrt(6/fan_in)), b = 0
+    for (int l = 0; l < NL; ++l) {
+        const size_t nw = (size_t)COUT[l] * CIN[l] * 27;
+        std::vector<float> w(nw), b(COUT[l], 0.0f);
+        const float lim = std::sqrt(6.0f / (float)(CIN[l] * 27));
+        for (size_t i = 0; i < nw; ++i) {
+            const u32x4 r = philox4x32_10((uint32_t)i, (uint32_t)l, 0x1417u, 0u, d->seed, 0xA1u);
+            w[i] = (2.0f * u01f(r.v[0]) - 1.0f) * lim;
+        }
+        cudaMemcpy(m->w[l], w.data(), sizeof(float) * nw, cudaMemcpyHostToDevice);
+        cudaMemcpy(m->b[l], b.data(), sizeof(float) * COUT[l], cudaMemcpyHostToDevice);
+    }
+    hyb_status s = model_repack(m);
+    if (s == HYB_OK && cudaStreamSynchronize(m->stream) != cudaSuccess) s = set_error(HYB_ECUDA, "model init");
+    if (s != HYB_OK) {
+        hyb_model_destroy(m);
+        return s;
+    }
+    *out = m;
+    return HYB_OK;
+}
+
+void hyb_model_destroy(hyb_model *m) {
+    if (!m) return;
+    if (m->stream) cudaStreamSynchronize(m->stream);
+    for (void *p : m->owned) cudaFree(p);
+    if (m->own_stream && m->stream) cudaStreamDestroy(m->stream);
+    delete m;
+}
+
+hyb_status hyb_model_set_layer(hyb_model *m, int l, const float *w, const float *b) {
+    if (!m || l < 0 || l >= NL || !w || !b) return set_error(HYB_EINVAL, "bad argument");
+    HYB_CUDA_TRY(cudaMemcpyAsync(m->w[l], w, sizeof(float) * COUT[l] * CIN[l] * 27, cudaMemcpyHostToDevice, m->stream));
+    HYB_CUDA_TRY(cudaMemcpyAsync(m->b[l], b, sizeof(float) * COUT[l], cudaMemcpyHostToDevice, m->stream));
+    hyb_status s = model_repack(m);
+    if (s != HYB_OK) return s;
+    HYB_CUDA_TRY(cudaStreamSynchronize(m->stream));
+    return HYB_OK;
+}
+
+hyb_status hyb_model_get_layer(hyb_model *m, int l, float *w, float *b) {
+    if (!m || l < 0 || l >= NL) return set_error(HYB_EINVAL, "bad argument");
+    if (w) HYB_CUDA_TRY(cudaMemcpyAsync(w, m->w[l], sizeof(float) * COUT[l] * CIN[l] * 27, cudaMemcpyDeviceToHost, m->stream));
+    if (b) HYB_CUDA_TRY(cudaMemcpyAsync(b, m->b[l], sizeof(float) * COUT[l], cudaMemcpyDeviceToHost, m->stream));
+    HYB_CUDA_TRY(cudaStreamSynchronize(m->stream));
+    return HYB_OK;
+}
+
+hyb_status hyb_model_forward(hyb_model *m, const float *x, int B, int D, int H, int W, int pass, float *logits) {
+    if (!m || !x || !logits || B <= 0 || D <= 0 || H <= 0 || W <= 0) return set_error(HYB_EINVAL, "bad argument");
+    if (W % 8 != 0 || H % 16 != 0) return set_error(HYB_EINVAL, "forward needs W % 8 == 0 and H % 16 == 0");
+    const long long V = (long long)D * H * W, cells = (long long)B * V;
+    hyb_status s = model_reserve(m, cells);
+    if (s != HYB_OK) return s;
+    k_prep_patches_cl<<<nb(cells), 256, 0, m->stream>>>(x, B, V, m->mean, m->std_, m->x0);
+    s = model_run(m, B, D, H, W, pass);
+    if (s != HYB_OK) return s;
+    HYB_CUDA_TRY(cudaMemcpyAsync(logits, m->logit, sizeof(float) * cells, cudaMemcpyDeviceToDevice, m->stream));
+    int st = 0;
+    HYB_CUDA_TRY(cudaMemcpyAsync(&st, m->status, sizeof(int), cudaMemcpyDeviceToHost, m->stream));
+    HYB_CUDA_TRY(cudaStreamSynchronize(m->stream));
+    if (st) return set_error(HYB_ETIMEOUT, "a tensor-core wait gave up");
+    return HYB_OK;
+}
+
+}  // extern "C"

@@ -79,12 +79,13 @@ __global__ void __launch_bounds__(RB) k_final(const double *__restrict__ partial
 }
 
 void launch_energy(const GridDev &g, const float *E, const float *B, const SpSet &set, double *partials,
-                   int nblocks, double *out, int *status, cudaStream_t st) {
+                   int nblocks, double *out, int *status, cudaStream_t st, int n_extra) {
     k_energy_fields<<<nblocks, RB, 0, st>>>(g, E, B, partials, nblocks, status);
     for (int s = 0; s < set.n; ++s)
         k_energy_species<<<nblocks, RB, 0, st>>>(g, set.s[s], partials + (long long)(2 + s) * nblocks, nblocks);
     const double dvol_half = 0.5 * g.dd[0] * g.dd[1] * g.dd[2];
-    k_final<<<1, RB, 0, st>>>(partials, 2 + set.n, nblocks, dvol_half, out);
+    // quantities 2 + set.n .. are partials the caller filled before (already in final units)
+    k_final<<<1, RB, 0, st>>>(partials, 2 + set.n + n_extra, nblocks, dvol_half, out);
 }
 
 }  // namespace hyb

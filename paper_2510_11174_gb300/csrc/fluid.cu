@@ -1,0 +1,164 @@
+// Cold relativistic fluid on the nodes (arXiv 2510.11174, Methodology: fluid
+// continuity and momentum equations with relativistic gamma factors for the
+// bulk plasma in stable regions; clamping against numerical instability).
+//
+//   dn/dt + div(n v) = 0,   d(n u)/dt + div(n u v) = (q/m) n (E + v x B)
+//
+// Two kernels per fluid and step:
+//  1. k_fluid_lorentz: at every node, E and B averaged from their Yee
+//     positions, u* = Boris(u; E, B); u* and a copy of n go to scratch.
+//  2. k_fluid_update: donor-cell transport on the node control volumes; the
+//     flux through the face between nodes i and i+1 along axis a uses the
+//     mean face velocity s = (v*_a(i) + v*_a(i+1))/2 and the upwind node:
+//       F = max(s,0) n_i + min(s,0) n_{i+1},  G = the same with n u*,
+//     n^{n+1} = n - dt sum (F+ - F-)/d,  (n u)^{n+1} = n u* - dt sum (G+ - G-)/d;
+//     each node adds q F of its upper faces to J (the face of the node control
+//     volume is the Yee edge of E_a, so continuity holds exactly with rho = q n);
+//     negative densities are clamped to 0 and counted, u = 0 below n_floor.
+// Outer faces of absorbing axes carry no flux.
+#include "hyb_internal.cuh"
+
+namespace hyb {
+
+__device__ __forceinline__ float fval(const GridDev &g, const float *__restrict__ F, int i, int j, int k) {
+    int idx[3] = {i, j, k};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (g.bc[a] == 0) {
+            idx[a] = idx[a] < 0 ? idx[a] + g.n[a] : (idx[a] >= g.n[a] ? idx[a] - g.n[a] : idx[a]);
+        } else if (idx[a] < 0 || idx[a] > g.n[a] - 1) {
+            return 0.0f;
+        }
+    }
+    return F[cidx(g, idx[0], idx[1], idx[2])];
+}
+
+__global__ void k_fluid_lorentz(GridDev g, const float *__restrict__ E, const float *__restrict__ B, FluidDev f) {
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= g.N) return;
+    const int nx = g.n[0], ny = g.n[1];
+    const int i = (int)(c % nx), j = (int)((c / nx) % ny), k = (int)(c / ((long long)nx * ny));
+    const long long N = g.N;
+    const float *Ex = E, *Ey = E + N, *Ez = E + 2 * N, *Bx = B, *By = B + N, *Bz = B + 2 * N;
+    float e[3], b[3];
+    e[0] = 0.5f * (fval(g, Ex, i - 1, j, k) + fval(g, Ex, i, j, k));
+    e[1] = 0.5f * (fval(g, Ey, i, j - 1, k) + fval(g, Ey, i, j, k));
+    e[2] = 0.5f * (fval(g, Ez, i, j, k - 1) + fval(g, Ez, i, j, k));
+    b[0] = 0.25f * (fval(g, Bx, i, j - 1, k - 1) + fval(g, Bx, i, j, k - 1) + fval(g, Bx, i, j - 1, k) +
+                    fval(g, Bx, i, j, k));
+    b[1] = 0.25f * (fval(g, By, i - 1, j, k - 1) + fval(g, By, i, j, k - 1) + fval(g, By, i - 1, j, k) +
+                    fval(g, By, i, j, k));
+    b[2] = 0.25f * (fval(g, Bz, i - 1, j - 1, k) + fval(g, Bz, i, j - 1, k) + fval(g, Bz, i - 1, j, k) +
+                    fval(g, Bz, i, j, k));
+    const float h = f.q * 0.5f * g.dt / f.m;
+    float um[3], tt[3], ss[3], ud[3];
+    const float u0[3] = {f.ux[c], f.uy[c], f.uz[c]};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) um[a] = u0[a] + h * e[a];
+    const float gm = sqrtf(1.0f + um[0] * um[0] + um[1] * um[1] + um[2] * um[2]);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) tt[a] = h * b[a] / gm;
+    const float t2 = tt[0] * tt[0] + tt[1] * tt[1] + tt[2] * tt[2];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) ss[a] = 2.0f * tt[a] / (1.0f + t2);
+    ud[0] = um[0] + (um[1] * tt[2] - um[2] * tt[1]);
+    ud[1] = um[1] + (um[2] * tt[0] - um[0] * tt[2]);
+    ud[2] = um[2] + (um[0] * tt[1] - um[1] * tt[0]);
+    f.usx[c] = um[0] + (ud[1] * ss[2] - ud[2] * ss[1]) + h * e[0];
+    f.usy[c] = um[1] + (ud[2] * ss[0] - ud[0] * ss[2]) + h * e[1];
+    f.usz[c] = um[2] + (ud[0] * ss[1] - ud[1] * ss[0]) + h * e[2];
+    f.ns[c] = f.n[c];
+}
+
+__global__ void k_fluid_update(GridDev g, FluidDev f, float *__restrict__ J) {
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= g.N) return;
+    const int nx = g.n[0], ny = g.n[1];
+    const int idx[3] = {(int)(c % nx), (int)((c / nx) % ny), (int)(c / ((long long)nx * ny))};
+    const float n0 = f.ns[c];
+    const float u0[3] = {f.usx[c], f.usy[c], f.usz[c]};
+    const float g0 = sqrtf(1.0f + u0[0] * u0[0] + u0[1] * u0[1] + u0[2] * u0[2]);
+    float dn = 0.0f, dm[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float ida = 1.0f / g.d[a];
+        // upper face (c, c+1) and lower face (c-1, c)
+#pragma unroll
+        for (int side = 0; side < 2; ++side) {
+            int nb[3] = {idx[0], idx[1], idx[2]};
+            const int o = side == 0 ? 1 : -1;
+            nb[a] += o;
+            if (g.bc[a]) {
+                if (nb[a] < 0 || nb[a] > g.n[a] - 1) continue;  // closed outer face
+            } else {
+                nb[a] = nb[a] < 0 ? nb[a] + g.n[a] : (nb[a] >= g.n[a] ? nb[a] - g.n[a] : nb[a]);
+            }
+            const long long c1 = cidx(g, nb[0], nb[1], nb[2]);
+            const float n1 = f.ns[c1];
+            const float u1[3] = {f.usx[c1], f.usy[c1], f.usz[c1]};
+            const float g1 = sqrtf(1.0f + u1[0] * u1[0] + u1[1] * u1[1] + u1[2] * u1[2]);
+            // nodes (lo, hi) of the face, in increasing index order
+            const float nlo = side == 0 ? n0 : n1, nhi = side == 0 ? n1 : n0;
+            const float vlo = side == 0 ? u0[a] / g0 : u1[a] / g1, vhi = side == 0 ? u1[a] / g1 : u0[a] / g0;
+            const float s = 0.5f * (vlo + vhi);
+            const float sp = fmaxf(s, 0.0f), sm = fminf(s, 0.0f);
+            const float F = sp * nlo + sm * nhi;
+            const float sgn = side == 0 ? -1.0f : 1.0f;  // out through the upper face, in through the lower
+            dn += sgn * F * ida;
+#pragma unroll
+            for (int b2 = 0; b2 < 3; ++b2) {
+                const float ulo = side == 0 ? u0[b2] : u1[b2], uhi = side == 0 ? u1[b2] : u0[b2];
+                dm[b2] += sgn * (sp * nlo * ulo + sm * nhi * uhi) * ida;
+            }
+            if (side == 0) J[(long long)a * g.N + c] += f.q * F;
+        }
+    }
+    const float n1 = n0 + g.dt * dn;
+    float mom[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) mom[a] = n0 * u0[a] + g.dt * dm[a];
+    if (n1 < 0.0f) atomicAdd(f.clamped, 1ULL);
+    f.n[c] = fmaxf(n1, 0.0f);
+    const bool keep = n1 > f.n_floor;
+    f.ux[c] = keep ? mom[0] / n1 : 0.0f;
+    f.uy[c] = keep ? mom[1] / n1 : 0.0f;
+    f.uz[c] = keep ? mom[2] / n1 : 0.0f;
+}
+
+static constexpr int FB = 256;
+
+__global__ void __launch_bounds__(FB) k_fluid_energy(GridDev g, FluidDev f, double *__restrict__ p_w,
+                                                     double *__restrict__ p_n, int nblocks) {
+    __shared__ double sh[FB];
+    double aw = 0.0, an = 0.0;
+    for (long long c = blockIdx.x * (long long)FB + threadIdx.x; c < g.N; c += (long long)nblocks * FB) {
+        const double n = f.n[c], ux = f.ux[c], uy = f.uy[c], uz = f.uz[c];
+        const double u2 = ux * ux + uy * uy + uz * uz;
+        aw += n * f.m_d * u2 / (sqrt(1.0 + u2) + 1.0);
+        an += n;
+    }
+    const double dV = g.dd[0] * g.dd[1] * g.dd[2];
+    for (int q = 0; q < 2; ++q) {
+        sh[threadIdx.x] = q == 0 ? aw : an;
+        __syncthreads();
+        for (int s = FB / 2; s > 0; s >>= 1) {
+            if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) (q == 0 ? p_w : p_n)[blockIdx.x] = sh[0] * dV;
+        __syncthreads();
+    }
+}
+
+void launch_fluid(const GridDev &g, const float *E, const float *B, const FluidDev &f, float *J, cudaStream_t st) {
+    const unsigned nb = (unsigned)((g.N + 255) / 256);
+    k_fluid_lorentz<<<nb, 256, 0, st>>>(g, E, B, f);
+    k_fluid_update<<<nb, 256, 0, st>>>(g, f, J);
+}
+
+void launch_fluid_energy(const GridDev &g, const FluidDev &f, double *p_w, double *p_n, int nblocks,
+                         cudaStream_t st) {
+    k_fluid_energy<<<nblocks, FB, 0, st>>>(g, f, p_w, p_n, nblocks);
+}
+
+}  // namespace hyb

@@ -91,6 +91,15 @@ struct SpDev {
 // tallies per tile: energies (FP64) and event counts
 enum { TALLY_IONIZE = 0, TALLY_EMIT = 1, TALLY_PAIR = 2, NTALLY = 3 };
 
+// cold fluid species on the nodes (state + per-step scratch)
+struct FluidDev {
+    float *n, *ux, *uy, *uz;       // state: density, u = gamma beta
+    float *ns, *usx, *usy, *usz;   // scratch: density and u* after the Lorentz step
+    float q, m, n_floor;
+    double m_d;
+    unsigned long long *clamped;   // accumulated clamp count
+};
+
 // device QED tables (see qed.cuh)
 struct QedDev {
     const float *em_lnh;    // ln h(chi) on the emission chi grid
@@ -158,6 +167,15 @@ struct hyb_ctx {
     std::vector<hyb::Species> sp;
     hyb::SpDev *sp_dev = nullptr;  // device copy of the species descriptors (HYB_MAX_SPECIES)
 
+    std::vector<hyb::FluidDev> fluids;
+
+    // regime switching
+    hyb_regime_desc regime = {};
+    uint8_t *mask = nullptr, *mask_tmp = nullptr;  // 1 = kinetic
+    float *rho_bg = nullptr;                       // residual background charge
+    float *ne = nullptr;                           // electron density scratch
+    uint32_t epoch = 0;                            // conversion counter (Philox counter word)
+
     // LCFA QED tables (built on first use)
     bool qed_ready = false;
     hyb::QedDev qed = {};
@@ -206,6 +224,14 @@ void launch_push_deposit(const GridDev &g, const float *E, const float *B, const
                          const QedDev &qd, float *jscratch, int *status, const long long *step_dev,
                          cudaStream_t st);
 hyb_status setup_qed(hyb_ctx *c);  // builds the QED tables once per context
+hyb_status regime_update(hyb_ctx *c, const float *p_mean, const float *p_std);
+hyb_status classifier_forward(hyb_ctx *c, const hyb_model *m, float *p_mean_dev, float *p_std_dev);
+const float *model_p_mean(const hyb_model *m);
+const float *model_p_std(const hyb_model *m);
+void launch_fluid(const GridDev &g, const float *E, const float *B, const FluidDev &f, float *J, cudaStream_t st);
+// FP64 partials of sum n m (gamma-1) (into p_w) and sum n (into p_n), nblocks each
+void launch_fluid_energy(const GridDev &g, const FluidDev &f, double *p_w, double *p_n, int nblocks,
+                         cudaStream_t st);
 hyb_status eval_qed(hyb_ctx *c, int what, const float *chi, const float *r, int n, float *out);
 hyb_status setup_ionization(hyb_ctx *c, SpDev &s, const hyb_species_desc *d);
 hyb_status eval_ion_table(hyb_ctx *c, const SpDev &s, int Z, const float *x_host, int n, float *out_host);
@@ -222,6 +248,6 @@ void launch_count_tiles(const GridDev &g, long long n, const float *x, const flo
 // FP64 reductions; results written to out[]: [0] = sum E^2 dV / 2, [1] = sum B^2 dV / 2,
 // [2 + s] = kinetic energy of species s; also sets ST_NAN on non-finite fields.
 void launch_energy(const GridDev &g, const float *E, const float *B, const SpSet &set,
-                   double *partials, int nblocks, double *out, int *status, cudaStream_t st);
+                   double *partials, int nblocks, double *out, int *status, cudaStream_t st, int n_extra);
 
 }  // namespace hyb

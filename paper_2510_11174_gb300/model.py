@@ -1,0 +1,79 @@
+"""Thin Python front end of the regime classifier (hyb_model_* in include/hyb.h).
+
+Argument marshalling only: weights and patches are handed to libhyb.so,
+which runs every layer on the GPU.
+"""
+import ctypes as C
+
+import numpy as np
+
+from . import _abi
+from ._abi import check
+
+LAYERS = [(6, 32), (32, 32), (32, 16), (16, 1)]
+
+
+class Classifier:
+    """3D CNN 6->32->32->16->1 (3x3x3, ReLU, dropout, sigmoid) on the GPU."""
+
+    def __init__(self, dropout=0.2, mc_passes=16, seed=7, mean=None, std=None, lr=1e-3, energy_weight=0.1,
+                 stream=None):
+        self._lib = _abi.load()
+        d = _abi.hyb_model_desc()
+        d.dropout, d.mc_passes, d.seed = dropout, mc_passes, seed
+        mean = [0.0] * 6 if mean is None else mean
+        std = [1.0] * 6 if std is None else std
+        for c in range(6):
+            d.mean[c] = float(mean[c])
+            d.std[c] = float(std[c])
+        d.lr, d.energy_weight = lr, energy_weight
+        if stream is None:
+            import torch
+            cur = torch.cuda.current_stream()
+            if cur.cuda_stream == 0:
+                cur = torch.cuda.Stream()
+            self.torch_stream = cur
+            stream = cur.cuda_stream
+        d.stream = stream
+        self.desc = d
+        h = C.c_void_p()
+        check(self._lib.hyb_model_create(C.byref(d), C.byref(h)))
+        self._m = h
+
+    @property
+    def handle(self):
+        return self._m
+
+    def close(self):
+        if getattr(self, "_m", None):
+            self._lib.hyb_model_destroy(self._m)
+            self._m = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_layer(self, layer, w, b):
+        ci, co = LAYERS[layer]
+        w = np.ascontiguousarray(w, dtype=np.float32).reshape(co, ci, 3, 3, 3)
+        b = np.ascontiguousarray(b, dtype=np.float32).reshape(co)
+        check(self._lib.hyb_model_set_layer(self._m, layer, w.ctypes.data, b.ctypes.data))
+
+    def get_layer(self, layer):
+        ci, co = LAYERS[layer]
+        w = np.empty((co, ci, 3, 3, 3), np.float32)
+        b = np.empty(co, np.float32)
+        check(self._lib.hyb_model_get_layer(self._m, layer, w.ctypes.data, b.ctypes.data))
+        return w, b
+
+    def forward(self, x, pass_index=-1):
+        """x: torch CUDA tensor [B, 6, D, H, W] FP32 -> logits [B, D, H, W] (torch CUDA)."""
+        import torch
+        x = x.contiguous().float()
+        B, _, D, H, W = x.shape
+        out = torch.empty((B, D, H, W), dtype=torch.float32, device=x.device)
+        torch.cuda.current_stream().synchronize()
+        check(self._lib.hyb_model_forward(self._m, x.data_ptr(), B, D, H, W, int(pass_index), out.data_ptr()))
+        return out

@@ -160,6 +160,58 @@ class Simulation:
         self.n_species += 1
         return sid.value
 
+    def load_fluid(self, q, m, n, ux=None, uy=None, uz=None, n_floor=0.0):
+        """Add a cold fluid species (node arrays shaped (nz, ny, nx)); returns its id."""
+        d = _abi.hyb_fluid_desc()
+        d.q, d.m, d.n_floor = q, m, n_floor
+        keep = []
+        ptrs = []
+        on_dev = None
+        for a in (n, ux, uy, uz):
+            if a is not None and np.size(a) != self.N:
+                raise ValueError("fluid arrays must hold nz*ny*nx values")
+            p, dev, k = _ptr_and_dev(a, np.float32)
+            keep.append(k)
+            ptrs.append(p)
+            if a is not None:
+                on_dev = dev if on_dev is None else on_dev
+                if dev != on_dev:
+                    raise ValueError("fluid arrays must all be host or all be device memory")
+        d.ptr_on_device = int(bool(on_dev))
+        d.n, d.ux, d.uy, d.uz = ptrs
+        fid = C.c_int()
+        check(self._lib.hyb_load_fluid(self._ctx, C.byref(d), C.byref(fid)))
+        return fid.value
+
+    def set_regime(self, a_thr=1.0, n_thr=1.0, c_thr=0.1, chi_thr=1e-3, dilate=2, k_sigma=1.0, ppc=8,
+                   to_species=None):
+        d = _abi.hyb_regime_desc()
+        d.a_thr, d.n_thr, d.c_thr, d.chi_thr = a_thr, n_thr, c_thr, chi_thr
+        d.dilate, d.k_sigma, d.ppc = dilate, k_sigma, ppc
+        ts = list(to_species or [])
+        for f in range(_abi.HYB_MAX_FLUIDS):
+            d.to_species[f] = int(ts[f]) if f < len(ts) else -1
+        check(self._lib.hyb_set_regime(self._ctx, C.byref(d)))
+
+    def classify(self, model=None, p_mean=None, p_std=None):
+        """Recompute the regime mask (physics criterion, or the classifier
+        `model`) and convert fluid <-> particles.  p_mean / p_std: optional
+        torch CUDA tensors of nz*ny*nx FP32 values receiving the MC statistics."""
+        ptr = lambda t: None if t is None else t.data_ptr()
+        check(self._lib.hyb_classify(self._ctx, None if model is None else model.handle, ptr(p_mean), ptr(p_std),
+                                     None))
+
+    def get_regime(self):
+        mask = np.empty(self.shape, np.uint8)
+        rho_bg = np.empty(self.shape, np.float32)
+        check(self._lib.hyb_get_regime(self._ctx, mask.ctypes.data, rho_bg.ctypes.data))
+        return mask, rho_bg
+
+    def get_fluid(self, fid):
+        out = {k: np.empty(self.shape, np.float32) for k in ("n", "ux", "uy", "uz")}
+        check(self._lib.hyb_get_fluid(self._ctx, int(fid), *[out[k].ctypes.data for k in ("n", "ux", "uy", "uz")]))
+        return out
+
     def set_fields(self, E, B):
         pe, de, ke = _ptr_and_dev(E, np.float32)
         pb, db, kb = _ptr_and_dev(B, np.float32)
@@ -195,7 +247,9 @@ class Simulation:
                 "status": out.status, "launches_per_step": out.launches_per_step,
                 "w_ionize": out.w_ionize, "n_ionize": out.n_ionize,
                 "w_photon_untracked": out.w_photon_untracked, "w_pair_deficit": out.w_pair_deficit,
-                "n_emit": out.n_emit, "n_pair": out.n_pair}
+                "n_emit": out.n_emit, "n_pair": out.n_pair,
+                "w_fluid": [out.w_fluid[i] for i in range(out.n_fluids)],
+                "n_fluid": [out.n_fluid[i] for i in range(out.n_fluids)], "n_clamped": out.n_clamped}
 
     def eval_qed(self, what, chi, r=None):
         """Evaluate the device QED tables (see hyb_eval_qed)."""

@@ -1,0 +1,54 @@
+"""Pins of the oracle's classifier: the orientation of the 3x3x3 taps (a
+one-hot kernel is a shift), BF16 rounding points, the dropout mask law and
+the MC statistics definitions."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle.classifier import LAYERS, OracleCNN, bf16
+
+
+def _weights(seed=0, scale=1.0):
+    rng = np.random.default_rng(seed)
+    return [(scale * rng.standard_normal((co, ci, 3, 3, 3)).astype(np.float32) / np.sqrt(ci * 27),
+             (0.1 * rng.standard_normal(co)).astype(np.float32)) for ci, co in LAYERS]
+
+
+def test_one_hot_kernel_is_a_shift():
+    x = torch.arange(2 * 1 * 4 * 5 * 6, dtype=torch.float64).reshape(2, 1, 4, 5, 6)
+    w = torch.zeros(1, 1, 3, 3, 3, dtype=torch.float64)
+    w[0, 0, 2, 1, 0] = 1.0  # (kz, ky, kx): output(z, y, x) = input(z + 1, y, x - 1)
+    y = torch.nn.functional.conv3d(x, w, padding=1)
+    assert torch.equal(y[:, 0, :3, :, 1:], x[:, 0, 1:, :, :5])
+    assert torch.all(y[:, 0, 3] == 0) and torch.all(y[:, 0, :, :, 0] == 0)
+
+
+def test_bf16_rounding_is_round_to_nearest_even():
+    v = torch.tensor([1.0 + 2 ** -8, 1.0 + 3 * 2 ** -8, 1.0 + 2 ** -9], dtype=torch.float64)
+    # BF16 keeps 8 significant bits: ties go to even, below-half rounds down
+    assert bf16(v).tolist() == [1.0, 1.0 + 2 ** -6, 1.0]
+
+
+def test_dropout_mask_law_and_pass_dependence():
+    p = 0.2
+    m0 = oracle.dropout_mask(2, 32, 4096, 7, 0, 1, p)
+    m1 = oracle.dropout_mask(2, 32, 4096, 7, 1, 1, p)
+    n = m0.size
+    assert abs(m0.mean() - (1 - p)) < 3 * np.sqrt(p * (1 - p) / n)
+    assert 0.25 < np.mean(m0 != m1) < 0.4          # independent passes: 2 p (1 - p) = 0.32
+    # the documented Philox stream
+    r = oracle.philox([17, 1, (1 << 16) | (9 >> 2), 0], [7, 0xD0])
+    assert m0[1, 9, 17] == (not (oracle.u01(r[9 & 3]) < p))
+
+
+def test_mc_statistics_are_mean_and_population_std():
+    net = OracleCNN(_weights(1), dropout=0.3, seed=11)
+    x = np.random.default_rng(2).standard_normal((1, 6, 2, 16, 8)).astype(np.float32)
+    m, s = net.mc_statistics(x, 5)
+    ps = torch.stack([torch.sigmoid(net.forward(x, k)) for k in range(5)])
+    assert torch.allclose(m, ps.mean(0)) and torch.allclose(s, torch.sqrt(((ps - ps.mean(0)) ** 2).mean(0)))
+    # without dropout every pass is the same network
+    net0 = OracleCNN(_weights(1), dropout=0.0, seed=11)
+    m0, s0 = net0.mc_statistics(x, 3)
+    assert torch.all(s0 == 0)
