@@ -258,6 +258,34 @@ hyb_status hyb_model_get_layer(hyb_model *model, int layer, float *w_host, float
 hyb_status hyb_model_forward(hyb_model *model, const float *x_dev, int batch, int D, int H, int W, int pass,
                              float *logits_dev);
 
+/*
+ * One training step (paper, Methodology: the network is trained on data the
+ * simulation generates, with a physics-informed energy-conservation term in
+ * the loss).  patches_dev: device FP32 [batch][6][D][H][W] (E, B);
+ * labels_dev: device FP32 [batch][D][H][W] in {0, 1} (1 = kinetic).  The loss
+ * is the energy-weighted binary cross-entropy
+ *   L = (1/N) sum_c w_c BCE(sigmoid(logit_c), y_c),
+ *   w_c = 1 + energy_weight * e_c / mean(e),  e_c = (|E|^2 + |B|^2)/2 at c,
+ * so cells holding more field energy weigh more (the reading of the paper's
+ * energy term for a regime label).  Dropout is on with the masks of pass =
+ * the step index; gradients flow through the same BF16 tensor-core
+ * convolutions (data gradient = convolution with the transposed, flipped
+ * kernel), weight gradients are FP32 reductions in a fixed order, and Adam
+ * updates the FP32 master weights.  Synchronises; fills *out.
+ */
+typedef struct {
+    double loss;       /* L above */
+    double bce;        /* unweighted mean BCE */
+    double accuracy;   /* fraction of cells with (p >= 0.5) == y */
+    long long step;    /* Adam step count after this update */
+} hyb_train_stats;
+hyb_status hyb_train_step(hyb_model *model, const float *patches_dev, const float *labels_dev, int batch, int D,
+                          int H, int W, hyb_train_stats *out);
+
+/* Gradients of the last training step (FP32 host arrays in the layout of
+ * hyb_model_get_layer). */
+hyb_status hyb_model_get_grad(hyb_model *model, int layer, float *gw_host, float *gb_host);
+
 /* Copy the current mask (uint8, 1 = kinetic) and the residual background
  * charge rho_bg (FP32) to host arrays of nz*ny*nx values (either may be NULL;
  * synchronises). */

@@ -63,3 +63,65 @@ class OracleCNN:
         """Mean and population standard deviation of sigmoid(logit) over the passes."""
         ps = torch.stack([torch.sigmoid(self.forward(x, pass_index=k)) for k in range(passes)])
         return ps.mean(0), ps.std(0, unbiased=False)
+
+
+def _wgrad(a, dz):
+    """dW[co][ci][kz][ky][kx] = sum_{b,z,y,x} dz[b,co,z,y,x] a_pad[b,ci,z+kz,y+ky,x+kx]."""
+    B, ci, D, H, W = a.shape
+    ap = F.pad(a, (1, 1, 1, 1, 1, 1))
+    out = torch.zeros(dz.shape[1], ci, 3, 3, 3, dtype=torch.float64)
+    for kz in range(3):
+        for ky in range(3):
+            for kx in range(3):
+                sh = ap[:, :, kz:kz + D, ky:ky + H, kx:kx + W]
+                out[:, :, kz, ky, kx] = torch.einsum("bozyx,bizyx->oi", dz, sh)
+    return out
+
+
+def train_grads(net, x, y, pass_index, energy_weight, exact=False):
+    """Loss and gradients of one training step (see hyb_train_step):
+    L = (1/N) sum_c w_c BCE(sigmoid(logit_c), y_c), w_c = 1 + lambda e_c / mean(e),
+    e_c = (|E|^2 + |B|^2)/2 of the raw input.  exact=True drops every BF16
+    rounding (for the finite-difference check)."""
+    rnd = (lambda t: t) if exact else bf16
+    W = [w if exact else bf16(w) for w in net.W]
+    xr = torch.as_tensor(np.asarray(x, dtype=np.float32))
+    a = ((xr - net.mean.view(1, 6, 1, 1, 1)) / net.std.view(1, 6, 1, 1, 1)).to(torch.float64)
+    a = rnd(a)
+    acts = [a]
+    B, _, D, H, Wd = a.shape
+    V = D * H * Wd
+    keeps = []
+    for l in range(3):
+        h = torch.relu(F.conv3d(a, W[l], net.b[l], padding=1))
+        keep = torch.ones_like(h)
+        if pass_index >= 0 and net.p > 0:
+            keep = torch.from_numpy(dropout_mask(B, h.shape[1], V, net.seed, pass_index, l, net.p)
+                                    .reshape(h.shape).astype(np.float64)) / (1.0 - net.p)
+        a = rnd(h * keep)
+        keeps.append(keep)
+        acts.append(a)
+    logit = F.conv3d(a, W[3], net.b[3], padding=1)[:, 0]
+    yt = torch.as_tensor(np.asarray(y, dtype=np.float64))
+    e = 0.5 * (xr.to(torch.float64) ** 2).sum(1)
+    w = 1.0 + energy_weight * e / e.mean()
+    bce = torch.clamp(logit, min=0) - logit * yt + torch.log1p(torch.exp(-logit.abs()))
+    N = logit.numel()
+    loss = (w * bce).sum() / N
+    p = torch.sigmoid(logit)
+    dlogit = w * (p - yt) / N
+    grads = [None] * 4
+    grads[3] = (_wgrad(acts[3], dlogit[:, None]), dlogit.sum().reshape(1))
+    dA = F.conv_transpose3d(dlogit[:, None], W[3], padding=1)
+    inv = 1.0 / (1.0 - net.p) if (pass_index >= 0 and net.p > 0) else 1.0
+    for l in (2, 1, 0):
+        dz = rnd(dA * (acts[l + 1] > 0) * inv)
+        grads[l] = (_wgrad(acts[l][:, :W[l].shape[1]], dz), dz.sum(dim=(0, 2, 3, 4)))
+        if l > 0:
+            dA = rnd(F.conv_transpose3d(dz, W[l], padding=1))
+    acc = ((p >= 0.5) == (yt >= 0.5)).double().mean()
+    return dict(loss=float(loss), bce=float(bce.mean()), accuracy=float(acc), grads=grads, logit=logit)
+
+
+def loss_only(net, x, y, pass_index, energy_weight):
+    return train_grads(net, x, y, pass_index, energy_weight, exact=True)["loss"]

@@ -89,6 +89,10 @@ class hyb_model_desc(C.Structure):
                 ("energy_weight", C.c_double), ("stream", C.c_void_p)]
 
 
+class hyb_train_stats(C.Structure):
+    _fields_ = [("loss", C.c_double), ("bce", C.c_double), ("accuracy", C.c_double), ("step", C.c_longlong)]
+
+
 _P = C.c_void_p
 _ctx = C.c_void_p
 
@@ -117,6 +121,8 @@ PROTOTYPES = {
     "hyb_model_set_layer": (C.c_int, [_P, C.c_int, _P, _P]),
     "hyb_model_get_layer": (C.c_int, [_P, C.c_int, _P, _P]),
     "hyb_model_forward": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _P]),
+    "hyb_train_step": (C.c_int, [_P, _P, _P, C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(hyb_train_stats)]),
+    "hyb_model_get_grad": (C.c_int, [_P, C.c_int, _P, _P]),
     "hyb_get_fluid": (C.c_int, [_ctx, C.c_int, _P, _P, _P, _P]),
     "hyb_field_energy_noalloc":(C.c_int, [_P, _P, C.c_longlong, C.c_double, C.c_double, C.c_double, _P, _P]),
 }

@@ -40,6 +40,7 @@ struct hyb_model {
     float *logit = nullptr, *pm = nullptr, *ps = nullptr;
     int *status = nullptr;
     long long adam_t = 0;
+    void *train = nullptr;  // training buffers (allocated by the first training step)
     std::vector<void *> owned;
 };
 
@@ -172,7 +173,7 @@ __global__ void k_mc_update(long long n, const float *__restrict__ logit, int k,
     m2[t] += d * (p - pm[t]);
 }
 
-__global__ void k_mc_final(long long n, int k, const float *__restrict__ m2, float *__restrict__ ps) {
+__global__ void k_mc_final(long long n, int k, const float *m2, float *ps) {  // may run in place
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (t < n) ps[t] = sqrtf(fmaxf(m2[t], 0.0f) / (float)k);  // population standard deviation over the passes
 }
@@ -280,6 +281,10 @@ const float *model_p_std(const hyb_model *m) { return m->ps; }
 
 }  // namespace hyb
 
+namespace hyb {
+void train_free(hyb_model *m);
+}
+
 using namespace hyb;
 
 extern "C" {
@@ -359,6 +364,7 @@ void hyb_model_destroy(hyb_model *m) {
     if (!m) return;
     if (m->stream) cudaStreamSynchronize(m->stream);
     for (void *p : m->owned) cudaFree(p);
+    train_free(m);
     if (m->own_stream && m->stream) cudaStreamDestroy(m->stream);
     delete m;
 }
@@ -395,6 +401,377 @@ hyb_status hyb_model_forward(hyb_model *m, const float *x, int B, int D, int H, 
     HYB_CUDA_TRY(cudaMemcpyAsync(&st, m->status, sizeof(int), cudaMemcpyDeviceToHost, m->stream));
     HYB_CUDA_TRY(cudaStreamSynchronize(m->stream));
     if (st) return set_error(HYB_ETIMEOUT, "a tensor-core wait gave up");
+    return HYB_OK;
+}
+
+}  // extern "C"
+
+// ============================================================================ training
+// Loss, backward and Adam (see hyb_train_step in include/hyb.h).
+namespace hyb {
+
+static constexpr int WG_CHUNK = 8192;  // cells per weight-gradient partial
+static constexpr int WG_SUB = 64;      // cells staged in shared memory at a time
+static constexpr int RBT = 256;
+
+struct TrainBufs {
+    float *gw[NL] = {}, *gb[NL] = {};
+    float *dlogit = nullptr, *edens = nullptr;
+    __nv_bfloat16 *dz3 = nullptr, *dz2 = nullptr, *dz1 = nullptr;  // data gradients (BF16, channels-last)
+    float *wpart = nullptr;   // weight-gradient partials
+    float *wsum = nullptr;    // summed weight gradient in [tap][ci][co] order
+    double *lpart = nullptr;  // loss partials
+    long long cap = 0, wcap = 0;
+    int lblocks = 0;
+};
+
+__device__ __forceinline__ double block_sum_d(double v, double *sh) {
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int s = RBT / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+        __syncthreads();
+    }
+    const double r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+// field energy density per cell (|E|^2 + |B|^2)/2 of the raw patches; FP64 partial sums
+__global__ void __launch_bounds__(RBT) k_energy_density(const float *__restrict__ x, int B, long long V,
+                                                        float *__restrict__ e, double *__restrict__ part) {
+    __shared__ double sh[RBT];
+    double acc = 0.0;
+    for (long long t = blockIdx.x * (long long)RBT + threadIdx.x; t < (long long)B * V; t += (long long)gridDim.x * RBT) {
+        const long long b = t / V, v = t % V;
+        float s = 0.0f;
+        for (int c = 0; c < 6; ++c) {
+            const float q = x[(b * 6 + c) * V + v];
+            s += q * q;
+        }
+        e[t] = 0.5f * s;
+        acc += 0.5 * (double)s;
+    }
+    acc = block_sum_d(acc, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = acc;
+}
+
+// weighted BCE with logits, its gradient, and FP64 partial sums (loss, bce, correct)
+__global__ void __launch_bounds__(RBT) k_loss(const float *__restrict__ logit, const float *__restrict__ y,
+                                              const float *__restrict__ e, float inv_emean, float lam, long long n,
+                                              float *__restrict__ dlogit, double *__restrict__ part) {
+    __shared__ double sh[RBT];
+    double al = 0.0, ab = 0.0, ac = 0.0;
+    const float invn = 1.0f / (float)n;
+    for (long long t = blockIdx.x * (long long)RBT + threadIdx.x; t < n; t += (long long)gridDim.x * RBT) {
+        const float l = logit[t], yy = y[t];
+        const float w = 1.0f + lam * e[t] * inv_emean;
+        // BCE(sigmoid(l), y) = max(l, 0) - l y + log(1 + exp(-|l|))
+        const float bce = fmaxf(l, 0.0f) - l * yy + log1pf(expf(-fabsf(l)));
+        const float p = 1.0f / (1.0f + expf(-l));
+        dlogit[t] = w * (p - yy) * invn;
+        al += (double)w * bce;
+        ab += bce;
+        ac += ((p >= 0.5f) == (yy >= 0.5f)) ? 1.0 : 0.0;
+    }
+    al = block_sum_d(al, sh);
+    ab = block_sum_d(ab, sh);
+    ac = block_sum_d(ac, sh);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x * 3 + 0] = al;
+        part[blockIdx.x * 3 + 1] = ab;
+        part[blockIdx.x * 3 + 2] = ac;
+    }
+}
+
+// layer 3 data gradient: dA3[c][ci] = sum_tap W[ci][tap] dlogit[c - s(tap)], then
+// dz3 = bf16(dA3 [a3 > 0] / (1 - p)) (ReLU and dropout of layer 2's output)
+__global__ void k_dgrad_last(const float *__restrict__ dlogit, const float *__restrict__ w4r,
+                             const __nv_bfloat16 *__restrict__ a3, int B, int D, int H, int W, float inv_keep,
+                             __nv_bfloat16 *__restrict__ dz3) {
+    __shared__ float ws[16 * 27];
+    for (int i = threadIdx.x; i < 16 * 27; i += blockDim.x) ws[i] = w4r[i];
+    __syncthreads();
+    const long long V = (long long)D * H * W;
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= (long long)B * V) return;
+    const long long b = t / V, v = t % V;
+    const int x = (int)(v % W), y = (int)((v / W) % H), z = (int)(v / ((long long)W * H));
+    float acc[16];
+#pragma unroll
+    for (int ci = 0; ci < 16; ++ci) acc[ci] = 0.0f;
+    for (int tap = 0; tap < 27; ++tap) {
+        const int zz = z - (tap / 9 - 1), yy = y - ((tap / 3) % 3 - 1), xx = x - (tap % 3 - 1);
+        if (zz < 0 || zz >= D || yy < 0 || yy >= H || xx < 0 || xx >= W) continue;
+        const float g = dlogit[b * V + ((long long)zz * H + yy) * W + xx];
+#pragma unroll
+        for (int ci = 0; ci < 16; ++ci) acc[ci] += ws[ci * 27 + tap] * g;
+    }
+    __align__(16) __nv_bfloat16 h[16], o[16];
+    reinterpret_cast<uint4 *>(h)[0] = reinterpret_cast<const uint4 *>(a3 + t * 16)[0];
+    reinterpret_cast<uint4 *>(h)[1] = reinterpret_cast<const uint4 *>(a3 + t * 16)[1];
+#pragma unroll
+    for (int ci = 0; ci < 16; ++ci)
+        o[ci] = __float2bfloat16_rn(__bfloat162float(h[ci]) > 0.0f ? acc[ci] * inv_keep : 0.0f);
+    reinterpret_cast<uint4 *>(dz3 + t * 16)[0] = reinterpret_cast<const uint4 *>(o)[0];
+    reinterpret_cast<uint4 *>(dz3 + t * 16)[1] = reinterpret_cast<const uint4 *>(o)[1];
+}
+
+// layer 3 weight gradient partials per chunk: [16 * 27] weights then 1 bias
+__global__ void k_wgrad_last(const __nv_bfloat16 *__restrict__ a3, const float *__restrict__ dlogit, int B, int D,
+                             int H, int W, float *__restrict__ part) {
+    const long long V = (long long)D * H * W, n = (long long)B * V;
+    const long long c0 = (long long)blockIdx.x * WG_CHUNK, c1 = min(c0 + WG_CHUNK, n);
+    for (int o = threadIdx.x; o < 16 * 27 + 1; o += blockDim.x) {
+        float acc = 0.0f;
+        if (o == 16 * 27) {
+            for (long long t = c0; t < c1; ++t) acc += dlogit[t];
+        } else {
+            const int ci = o / 27, tap = o % 27;
+            const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+            for (long long t = c0; t < c1; ++t) {
+                const long long b = t / V, v = t % V;
+                const int x = (int)(v % W) + dx, y = (int)((v / W) % H) + dy, z = (int)(v / ((long long)W * H)) + dz;
+                if (z < 0 || z >= D || y < 0 || y >= H || x < 0 || x >= W) continue;
+                acc += __bfloat162float(a3[(b * V + ((long long)z * H + y) * W + x) * 16 + ci]) * dlogit[t];
+            }
+        }
+        part[(long long)blockIdx.x * (16 * 27 + 1) + o] = acc;
+    }
+}
+
+// dz = bf16(dA [a > 0] / (1 - p)) in place (dA from the tensor-core data gradient)
+__global__ void k_mask_grad(__nv_bfloat16 *__restrict__ d, const __nv_bfloat16 *__restrict__ a, long long n,
+                            float inv_keep) {
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    d[t] = __float2bfloat16_rn(__bfloat162float(a[t]) > 0.0f ? __bfloat162float(d[t]) * inv_keep : 0.0f);
+}
+
+// weight (and bias) gradient partials of a 3x3x3 layer:
+//   dW[co][ci][tap] = sum_cells A[cell + s(tap)][ci] dZ[cell][co]   (zero outside the volume)
+// grid (chunk, tap); part[chunk][tap][ci][co]; the tap-0 blocks also write db[co] to bpart[chunk][co]
+__global__ void __launch_bounds__(256) k_wgrad(const __nv_bfloat16 *__restrict__ A, int ca, int ci_n,
+                                               const __nv_bfloat16 *__restrict__ dZ, int co_n, int B, int D, int H,
+                                               int W, float *__restrict__ part, float *__restrict__ bpart) {
+    __shared__ float sa[WG_SUB][33], sz[WG_SUB][33];
+    const long long V = (long long)D * H * W, n = (long long)B * V;
+    const int tap = blockIdx.y;
+    const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+    const long long c0 = (long long)blockIdx.x * WG_CHUNK, c1 = min(c0 + WG_CHUNK, n);
+    const int nout = ci_n * co_n;
+    float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    float bacc = 0.0f;
+    for (long long s0 = c0; s0 < c1; s0 += WG_SUB) {
+        for (int i = threadIdx.x; i < WG_SUB * 32; i += blockDim.x) {
+            const int r = i / 32, ch = i % 32;
+            const long long t = s0 + r;
+            float av = 0.0f, zv = 0.0f;
+            if (t < c1) {
+                const long long b = t / V, v = t % V;
+                const int x = (int)(v % W) + dx, y = (int)((v / W) % H) + dy, z = (int)(v / ((long long)W * H)) + dz;
+                if (ch < ci_n && z >= 0 && z < D && y >= 0 && y < H && x >= 0 && x < W)
+                    av = __bfloat162float(A[(b * V + ((long long)z * H + y) * W + x) * ca + ch]);
+                if (ch < co_n) zv = __bfloat162float(dZ[t * co_n + ch]);
+            }
+            sa[r][ch] = av;
+            sz[r][ch] = zv;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int o = threadIdx.x + k * 256;
+            if (o < nout) {
+                const int ci = o / co_n, co = o % co_n;
+                float s = 0.0f;
+                for (int r = 0; r < WG_SUB; ++r) s += sa[r][ci] * sz[r][co];
+                acc[k] += s;
+            }
+        }
+        if (tap == 0 && threadIdx.x < co_n)
+            for (int r = 0; r < WG_SUB; ++r) bacc += sz[r][threadIdx.x];
+        __syncthreads();
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int o = threadIdx.x + k * 256;
+        if (o < nout) part[((long long)blockIdx.x * 27 + tap) * nout + o] = acc[k];
+    }
+    if (tap == 0 && threadIdx.x < co_n) bpart[(long long)blockIdx.x * co_n + threadIdx.x] = bacc;
+}
+
+// sum the chunk partials in chunk order: out[o] = sum_k part[k][o]
+__global__ void k_sum_parts(const float *__restrict__ part, int nchunks, int nout, float *__restrict__ out) {
+    const int o = blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= nout) return;
+    float s = 0.0f;
+    for (int k = 0; k < nchunks; ++k) s += part[(long long)k * nout + o];
+    out[o] = s;
+}
+
+// reorder [tap][ci][co] -> [co][ci][tap] (the master-weight layout)
+__global__ void k_reorder_wg(const float *__restrict__ in, int ci_n, int co_n, float *__restrict__ out) {
+    const int o = blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= 27 * ci_n * co_n) return;
+    const int co = o % co_n, ci = (o / co_n) % ci_n, tap = o / (co_n * ci_n);
+    out[((long long)co * ci_n + ci) * 27 + tap] = in[o];
+}
+
+__global__ void k_adam(float *__restrict__ w, const float *__restrict__ g, float *__restrict__ m, float *__restrict__ v,
+                       int n, float lr, float b1, float b2, float eps, float c1, float c2) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.0f - b1) * gi;
+    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+static inline unsigned nbl(long long n, int b = 256) { return (unsigned)((n + b - 1) / b); }
+
+// training buffers, allocated on the first step and grown with the batch
+static hyb_status train_reserve(hyb_model *m, long long cells) {
+    if (!m->train) m->train = new TrainBufs();
+    TrainBufs &t = *static_cast<TrainBufs *>(m->train);
+    if (!t.gw[0]) {
+        for (int l = 0; l < NL; ++l)
+            if (m_alloc(m, (void **)&t.gw[l], sizeof(float) * COUT[l] * CIN[l] * 27) ||
+                m_alloc(m, (void **)&t.gb[l], sizeof(float) * COUT[l]))
+                return set_error(HYB_ENOMEM, "gradient buffers");
+        t.lblocks = 152 * 2;
+        if (m_alloc(m, (void **)&t.lpart, sizeof(double) * 3 * t.lblocks) ||
+            m_alloc(m, (void **)&t.wsum, sizeof(float) * 27 * 32 * 32))
+            return set_error(HYB_ENOMEM, "loss partials");
+    }
+    if (cells > t.cap) {
+        cudaStreamSynchronize(m->stream);
+        // old buffers stay owned by the model until it is destroyed
+        const long long nch = (cells + WG_CHUNK - 1) / WG_CHUNK;
+        if (m_alloc(m, (void **)&t.dlogit, sizeof(float) * cells) || m_alloc(m, (void **)&t.edens, sizeof(float) * cells) ||
+            m_alloc(m, (void **)&t.dz3, sizeof(__nv_bfloat16) * 16 * cells) ||
+            m_alloc(m, (void **)&t.dz2, sizeof(__nv_bfloat16) * 32 * cells) ||
+            m_alloc(m, (void **)&t.dz1, sizeof(__nv_bfloat16) * 32 * cells) ||
+            m_alloc(m, (void **)&t.wpart, sizeof(float) * nch * (27 * 32 * 32 + 32)))
+            return set_error(HYB_ENOMEM, "training buffers");
+        t.cap = cells;
+    }
+    return HYB_OK;
+}
+
+// weight and bias gradient of layer l from its input A (channels ca, ci_n real) and dZ (co_n channels)
+static void layer_wgrad(hyb_model *m, TrainBufs &t, int l, const __nv_bfloat16 *A, int ca, const __nv_bfloat16 *dZ,
+                        int B, int D, int H, int W) {
+    const long long cells = (long long)B * D * H * W;
+    const int nch = (int)((cells + WG_CHUNK - 1) / WG_CHUNK);
+    const int ci_n = CIN[l], co_n = COUT[l], nout = ci_n * co_n;
+    float *part = t.wpart, *bpart = t.wpart + (long long)nch * 27 * nout;
+    dim3 grid(nch, 27);
+    k_wgrad<<<grid, 256, 0, m->stream>>>(A, ca, ci_n, dZ, co_n, B, D, H, W, part, bpart);
+    float *wsum = t.wsum;
+    k_sum_parts<<<nbl(27 * nout), 256, 0, m->stream>>>(part, nch, 27 * nout, wsum);
+    k_reorder_wg<<<nbl(27 * nout), 256, 0, m->stream>>>(wsum, ci_n, co_n, t.gw[l]);
+    k_sum_parts<<<nbl(co_n), 256, 0, m->stream>>>(bpart, nch, co_n, t.gb[l]);
+}
+
+}  // namespace hyb
+
+namespace hyb {
+void train_free(hyb_model *m) {
+    delete static_cast<TrainBufs *>(m->train);
+    m->train = nullptr;
+}
+}  // namespace hyb
+
+extern "C" {
+
+hyb_status hyb_train_step(hyb_model *m, const float *x, const float *y, int B, int D, int H, int W,
+                          hyb_train_stats *out) {
+    if (!m || !x || !y || !out || B <= 0 || D <= 0 || H <= 0 || W <= 0) return set_error(HYB_EINVAL, "bad argument");
+    if (W % 8 != 0 || H % 16 != 0) return set_error(HYB_EINVAL, "training needs W % 8 == 0 and H % 16 == 0");
+    const long long V = (long long)D * H * W, cells = (long long)B * V;
+    hyb_status s = model_reserve(m, cells);
+    if (s == HYB_OK) s = train_reserve(m, cells);
+    if (s != HYB_OK) return s;
+    TrainBufs &t = *static_cast<TrainBufs *>(m->train);
+    cudaStream_t st = m->stream;
+    const float p = (float)m->d.dropout, inv_keep = 1.0f / (1.0f - p);
+    // forward, dropout masks of pass = the step index
+    k_prep_patches_cl<<<nbl(cells), 256, 0, st>>>(x, B, V, m->mean, m->std_, m->x0);
+    s = model_run(m, B, D, H, W, (int)(m->adam_t & 0x7fffffff));
+    if (s != HYB_OK) return s;
+    // energy weights: mean field energy density of the batch
+    k_energy_density<<<t.lblocks, RBT, 0, st>>>(x, B, V, t.edens, t.lpart);
+    std::vector<double> hp((size_t)3 * t.lblocks);
+    HYB_CUDA_TRY(cudaMemcpyAsync(hp.data(), t.lpart, sizeof(double) * t.lblocks, cudaMemcpyDeviceToHost, st));
+    HYB_CUDA_TRY(cudaStreamSynchronize(st));
+    double esum = 0.0;
+    for (int k = 0; k < t.lblocks; ++k) esum += hp[k];
+    const double emean = esum / (double)cells;
+    const float inv_emean = emean > 0.0 ? (float)(1.0 / emean) : 0.0f;
+    k_loss<<<t.lblocks, RBT, 0, st>>>(m->logit, y, t.edens, inv_emean, (float)m->d.energy_weight, cells, t.dlogit,
+                                      t.lpart);
+    // layer 3 (16 -> 1) on the CUDA cores
+    const int nch = (int)((cells + WG_CHUNK - 1) / WG_CHUNK);
+    k_wgrad_last<<<nch, 256, 0, st>>>(m->a3, t.dlogit, B, D, H, W, t.wpart);
+    k_sum_parts<<<nbl(16 * 27 + 1), 256, 0, st>>>(t.wpart, nch, 16 * 27 + 1, t.wsum);
+    HYB_CUDA_TRY(cudaMemcpyAsync(t.gw[3], t.wsum, sizeof(float) * 16 * 27, cudaMemcpyDeviceToDevice, st));
+    HYB_CUDA_TRY(cudaMemcpyAsync(t.gb[3], t.wsum + 16 * 27, sizeof(float), cudaMemcpyDeviceToDevice, st));
+    k_dgrad_last<<<nbl(cells), 256, 0, st>>>(t.dlogit, m->w4r, m->a3, B, D, H, W, inv_keep, t.dz3);
+    // layer 2 (32 -> 16): weight gradient, then the data gradient on the tensor cores
+    layer_wgrad(m, t, 2, m->a2, 32, t.dz3, B, D, H, W);
+    ConvArgs a;
+    memset(&a, 0, sizeof(a));
+    a.B = B; a.D = D; a.H = H; a.W = W;
+    a.status = m->status;
+    a.x = t.dz3; a.wt = m->wtT[2]; a.cin = 16; a.N = 32; a.y = t.dz2;
+    if ((s = launch_conv3_tc(a, st)) != HYB_OK) return s;
+    k_mask_grad<<<nbl(cells * 32), 256, 0, st>>>(t.dz2, m->a2, cells * 32, inv_keep);
+    // layer 1 (32 -> 32)
+    layer_wgrad(m, t, 1, m->a1, 32, t.dz2, B, D, H, W);
+    a.x = t.dz2; a.wt = m->wtT[1]; a.cin = 32; a.N = 32; a.y = t.dz1;
+    if ((s = launch_conv3_tc(a, st)) != HYB_OK) return s;
+    k_mask_grad<<<nbl(cells * 32), 256, 0, st>>>(t.dz1, m->a1, cells * 32, inv_keep);
+    // layer 0 (6 -> 32): weight gradient only
+    layer_wgrad(m, t, 0, m->x0, 16, t.dz1, B, D, H, W);
+    // Adam on the FP32 master weights, then the BF16 copies
+    m->adam_t += 1;
+    const float b1 = (float)m->d.beta1, b2 = (float)m->d.beta2;
+    const float c1 = (float)(1.0 - std::pow(m->d.beta1, (double)m->adam_t));
+    const float c2 = (float)(1.0 - std::pow(m->d.beta2, (double)m->adam_t));
+    for (int l = 0; l < NL; ++l) {
+        const int nw = COUT[l] * CIN[l] * 27;
+        k_adam<<<nbl(nw), 256, 0, st>>>(m->w[l], t.gw[l], m->mw[l], m->vw[l], nw, (float)m->d.lr, b1, b2,
+                                        (float)m->d.eps, c1, c2);
+        k_adam<<<nbl(COUT[l]), 256, 0, st>>>(m->b[l], t.gb[l], m->mb[l], m->vb[l], COUT[l], (float)m->d.lr, b1, b2,
+                                             (float)m->d.eps, c1, c2);
+    }
+    if ((s = model_repack(m)) != HYB_OK) return s;
+    HYB_CUDA_TRY(cudaMemcpyAsync(hp.data(), t.lpart, sizeof(double) * 3 * t.lblocks, cudaMemcpyDeviceToHost, st));
+    int stw = 0;
+    HYB_CUDA_TRY(cudaMemcpyAsync(&stw, m->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    HYB_CUDA_TRY(cudaStreamSynchronize(st));
+    if (stw) return set_error(HYB_ETIMEOUT, "a tensor-core wait gave up");
+    double L = 0, bce = 0, acc = 0;
+    for (int k = 0; k < t.lblocks; ++k) {
+        L += hp[3 * k];
+        bce += hp[3 * k + 1];
+        acc += hp[3 * k + 2];
+    }
+    out->loss = L / (double)cells;
+    out->bce = bce / (double)cells;
+    out->accuracy = acc / (double)cells;
+    out->step = m->adam_t;
+    return HYB_OK;
+}
+
+hyb_status hyb_model_get_grad(hyb_model *m, int l, float *gw, float *gb) {
+    if (!m || l < 0 || l >= NL || !m->train) return set_error(HYB_EINVAL, "no gradients (no training step yet)");
+    TrainBufs &t = *static_cast<TrainBufs *>(m->train);
+    if (gw) HYB_CUDA_TRY(cudaMemcpyAsync(gw, t.gw[l], sizeof(float) * COUT[l] * CIN[l] * 27, cudaMemcpyDeviceToHost, m->stream));
+    if (gb) HYB_CUDA_TRY(cudaMemcpyAsync(gb, t.gb[l], sizeof(float) * COUT[l], cudaMemcpyDeviceToHost, m->stream));
+    HYB_CUDA_TRY(cudaStreamSynchronize(m->stream));
     return HYB_OK;
 }
 

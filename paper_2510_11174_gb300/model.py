@@ -77,3 +77,22 @@ class Classifier:
         torch.cuda.current_stream().synchronize()
         check(self._lib.hyb_model_forward(self._m, x.data_ptr(), B, D, H, W, int(pass_index), out.data_ptr()))
         return out
+
+    def train_step(self, x, y):
+        """One Adam step on patches x [B, 6, D, H, W] and labels y [B, D, H, W]
+        (torch CUDA tensors).  Returns the step statistics."""
+        import torch
+        x = x.contiguous().float()
+        y = y.contiguous().float()
+        B, _, D, H, W = x.shape
+        st = _abi.hyb_train_stats()
+        torch.cuda.current_stream().synchronize()
+        check(self._lib.hyb_train_step(self._m, x.data_ptr(), y.data_ptr(), B, D, H, W, C.byref(st)))
+        return {"loss": st.loss, "bce": st.bce, "accuracy": st.accuracy, "step": st.step}
+
+    def get_grad(self, layer):
+        ci, co = LAYERS[layer]
+        w = np.empty((co, ci, 3, 3, 3), np.float32)
+        b = np.empty(co, np.float32)
+        check(self._lib.hyb_model_get_grad(self._m, layer, w.ctypes.data, b.ctypes.data))
+        return w, b

@@ -52,3 +52,32 @@ def test_mc_statistics_are_mean_and_population_std():
     net0 = OracleCNN(_weights(1), dropout=0.0, seed=11)
     m0, s0 = net0.mc_statistics(x, 3)
     assert torch.all(s0 == 0)
+
+
+def test_oracle_backward_matches_central_differences():
+    """Exact FP64 backward of the energy-weighted BCE against central differences."""
+    from oracle.classifier import train_grads
+    rng = np.random.default_rng(4)
+    net = OracleCNN(_weights(3, scale=2.0), dropout=0.2, seed=5)
+    x = rng.standard_normal((1, 6, 2, 16, 8)).astype(np.float32)
+    y = (rng.random((1, 2, 16, 8)) < 0.4).astype(np.float32)
+    out = train_grads(net, x, y, pass_index=2, energy_weight=0.1, exact=True)
+    h = 1e-6
+    for l in range(4):
+        gw, gb = out["grads"][l]
+        for idx in [(0, 0, 1, 1, 1), (gw.shape[0] - 1, gw.shape[1] - 1, 0, 2, 1), (0, gw.shape[1] // 2, 2, 0, 0)]:
+            w0 = net.W[l][idx].item()
+            net.W[l][idx] = w0 + h
+            lp = train_grads(net, x, y, 2, 0.1, exact=True)["loss"]
+            net.W[l][idx] = w0 - h
+            lm = train_grads(net, x, y, 2, 0.1, exact=True)["loss"]
+            net.W[l][idx] = w0
+            fd = (lp - lm) / (2 * h)
+            assert gw[idx].item() == pytest.approx(fd, rel=1e-6, abs=1e-11), (l, idx)
+        b0 = net.b[l][0].item()
+        net.b[l][0] = b0 + h
+        lp = train_grads(net, x, y, 2, 0.1, exact=True)["loss"]
+        net.b[l][0] = b0 - h
+        lm = train_grads(net, x, y, 2, 0.1, exact=True)["loss"]
+        net.b[l][0] = b0
+        assert gb[0].item() == pytest.approx((lp - lm) / (2 * h), rel=1e-6, abs=1e-11), l
