@@ -36,12 +36,26 @@ PUSH_BYTES_PER_PARTICLE = 52
 PUSH_BYTES_PER_CELL = 36
 
 
+N_CLS = 10          # classification interval of the hybrid step [steps]
+MC_PASSES = 16      # MC-dropout passes per classification
+
+
 def workloads():
+    """name -> (kind, generator(seed)).  "pic": particles only (plain full
+    PIC); "hybrid": fluids everywhere, particles in the cells the classifier
+    and the physics criterion flag, reclassified every N_CLS steps."""
     from paper_2510_11174_gb300 import inputs
     return {
         # plain full PIC: periodic 32^3, lambda/16, e-/p+ 0.1 n_c, 8 ppc, 1 keV, a0 = 1
-        "periodic_plasma_32": lambda seed: inputs.periodic_plasma(n=32, ppc=8, seed=seed),
+        "periodic_plasma_32": ("pic", lambda seed: inputs.periodic_plasma(n=32, ppc=8, seed=seed)),
+        # hybrid: 256 x 256 x 128, lambda/16, ramp 0.01 -> 1 n_c + 5 n_c slab, a0 log-uniform [10, 300]
+        "ramp_slab_256x256x128": ("hybrid", lambda seed: inputs.ramp_slab(seed=seed + 2)),
+        # the same recipe at 1/8 of the cells (quick checks)
+        "ramp_slab_128x128x64": ("hybrid", lambda seed: inputs.ramp_slab(nx=128, ny=128, nz=64, seed=seed + 2)),
     }
+
+
+DEFAULT_WORKLOAD = "ramp_slab_256x256x128"
 
 
 def measured_peaks():
@@ -101,19 +115,119 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def make_sim(P, inp, stream=None):
+# classifier: 2 * 27 * (6*32 + 32*32 + 32*16 + 16*1) FLOP per cell per MC pass
+CLS_FLOP_PER_CELL_PASS = 94176
+# split FDTD (B half, E, B half): read E,B (24) + write B (12); read E,B,J (36) + write E (12); B half again
+FDTD_BYTES_PER_CELL = 120
+# cold fluid: read n, n u (16 B) + write (16 B) per node and fluid, + E, B read (24 B) per node
+FLUID_BYTES_PER_NODE = 32
+FLUID_FIELD_BYTES_PER_NODE = 24
+
+
+def make_model(P, stream):
+    """Classifier of the hybrid step: He-uniform weights from the seed, the
+    output bias set so quiet fields read as fluid (p ~ 0.02)."""
+    m = P.Classifier(dropout=0.2, mc_passes=MC_PASSES, seed=11, stream=stream)
+    w, b = m.get_layer(3)
+    m.set_layer(3, w, np.full_like(b, -4.0))
+    return m
+
+
+def make_sim(P, inp, stream, policy="union"):
+    """Context for a workload.  Hybrid workloads get their fluids, the regime
+    settings and one classification (which creates the particles of the
+    kinetic cells; policy "all_kinetic" turns every fluid node into
+    particles: the full-PIC run)."""
     g = inp["grid"]
     sim = P.Simulation(g["nx"], g["ny"], g["nz"], g["dx"], cfl_frac=g["cfl_frac"], bc=g["bc"],
                        laser=inp.get("laser"), stream=stream)
     for sp in inp["species"]:
         sim.load_species(**sp)
+    for fl in inp.get("fluids", []):
+        sim.load_fluid(**fl)
     if "E" in inp:
         sim.set_fields(inp["E"], inp["B"])
-    return sim
+    model = None
+    if inp.get("fluids"):
+        sim.set_regime(dilate=2, ppc=inp["ppc"], to_species=list(range(len(inp["fluids"]))), policy=policy)
+        if policy != "all_kinetic":
+            model = make_model(P, stream)
+        sim.classify(model)
+    return sim, model
 
 
 def count_particles(inp):
     return sum(len(sp["x"]) for sp in inp["species"])
+
+
+def advance(sim, model, n, step0):
+    """n steps from global step step0; with a classifier the regime is
+    recomputed after every N_CLS-th step."""
+    cls = 0
+    for k in range(n):
+        sim.step(1)
+        if model is not None and (step0 + k + 1) % N_CLS == 0:
+            sim.classify(model)
+            cls += 1
+    return cls
+
+
+def state_bytes(diag, cells):
+    """Bytes of the resident state a step streams (fields E, B, J; fluids;
+    particle SoA)."""
+    return 36 * cells + 16 * cells * len(diag["n_fluid"]) + 36 * sum(diag["count"])
+
+
+def timed_run(torch, sim, model, steps, warmup, stream, barrier, flush_l2):
+    """Warm-up, then exactly `steps` steps between CUDA events on the
+    library's stream.  flush_l2: write 2 x L2 between steps (outside the
+    events) and sum per-step times; else one event pair around all steps."""
+    advance(sim, model, warmup, 0)
+    before = sim.diagnostics()
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda") if flush_l2 else None
+    barrier()
+    torch.cuda.synchronize()
+    ncls = 0
+    if flush_l2:
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for k in range(steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            ncls += advance(sim, model, 1, warmup + k)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        total = sum(a.elapsed_time(b) for a, b in ev)
+    else:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ncls = advance(sim, model, steps, warmup)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        total = e0.elapsed_time(e1)
+    barrier()
+    after = sim.diagnostics()
+    return total, ncls, before, after
+
+
+def profile_phases(sim, model, step0):
+    """N_CLS further steps with per-phase CUDA events (captured in the step
+    graph; hyb_classify's phases around the classification at their end).
+    Returns the mean per-step ms of each step phase and the ms of one
+    classification."""
+    sim.set_profiling(True)
+    per = []
+    cls = {}
+    for k in range(N_CLS):
+        sim.step(1)
+        per.append(sim.phase_times())
+        if model is not None and (step0 + k + 1) % N_CLS == 0:
+            sim.classify(model)
+            pt = sim.phase_times()
+            cls = {"classify": pt["classify"], "regime": pt["regime"]}
+    sim.set_profiling(False)
+    step_phases = ["push", "j_reduce", "source", "rebin", "field", "fluid"]
+    mean = {k: statistics.mean(p[k] for p in per) for k in step_phases}
+    return mean, cls
 
 
 def run_ours(args, rank, world):
@@ -123,73 +237,105 @@ def run_ours(args, rank, world):
     build.build()
     dev = int(os.environ.get("LOCAL_RANK", 0))
     torch.cuda.set_device(dev)
-    # a capturable (non-default) stream shared by the library, the L2 flush and the events
+    # a capturable (non-default) stream shared by the library and the events
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    inp = workloads()[args.workload](1 + rank)
+    kind, gen = workloads()[args.workload]
+    inp = gen(1 + rank)
     g = inp["grid"]
     cells = g["nx"] * g["ny"] * g["nz"]
-    npart = count_particles(inp)
-    sim = make_sim(P, inp, stream.cuda_stream)
-    sim.set_profiling(True)
-    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
-    sim.step(args.warmup)
-    torch.cuda.synchronize()
 
     def barrier():
         if world > 1:
             torch.distributed.barrier()
 
-    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    push_ms, phases = [], []
-    barrier()
-    torch.cuda.synchronize()
+    def allmax(v):
+        if world > 1:
+            t = torch.tensor([v], device="cuda", dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            return float(t.item())
+        return v
+
+    sim, model = make_sim(P, inp, stream.cuda_stream, policy="union")
+    probe = sim.diagnostics()
+    flush_l2 = state_bytes(probe, cells) < 2 * L2_BYTES
     clocks = ClockSampler(dev)
-    for k in range(args.steps):
-        flush.zero_()  # evict L2 between timed steps (outside the event pair)
-        ev0[k].record(stream)
-        sim.step(1)
-        ev1[k].record(stream)
-        pt = sim.phase_times()  # synchronises
-        phases.append(pt)
-        push_ms.append(pt.get("push", 0.0))
-    torch.cuda.synchronize()
-    barrier()
+    total_ms, ncls, before, after = timed_run(torch, sim, model, args.steps, args.warmup, stream.cuda_stream,
+                                              barrier, flush_l2)
     clk = clocks.stop()
-    step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
-    total_ms = sum(step_ms)
-    diag = sim.diagnostics()
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    ms_per_step = total_ms / args.steps
-    steps_per_s = world * args.steps / (total_ms * 1e-3)
-    mean_push_ms = statistics.mean(push_ms)
-    peak, peak_kind = measured_peaks()
-    push_bytes = PUSH_BYTES_PER_PARTICLE * npart + PUSH_BYTES_PER_CELL * cells
-    achieved = push_bytes / (mean_push_ms * 1e-3) / 1e9
-    phase_mean = {k: statistics.mean(p.get(k, 0.0) for p in phases) for k in phases[-1]}
-    launches = diag["launches_per_step"] * args.steps
+    total_ms = allmax(total_ms)
+    parts = 0.5 * (sum(before["count"]) + sum(after["count"]))
+    kin_frac = float(sim.get_regime()[0].mean()) if kind == "hybrid" else 1.0
+    phases, cls = profile_phases(sim, model, args.warmup + args.steps)
+    launches = after["launches_per_step"] * args.steps + ncls * after["launches_classify"]
     sim.close()
+    if model is not None:
+        model.close()
+
+    ms_per_step = total_ms / args.steps
+    peak_hbm, peak_kind = measured_peaks()
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    kin_cells = kin_frac * cells
+    nfl = len(inp.get("fluids", []))
+    roofs = {}
+    if phases["push"] > 0:
+        b = PUSH_BYTES_PER_PARTICLE * parts + PUSH_BYTES_PER_CELL * kin_cells
+        roofs["push"] = dict(kernel="k_push_deposit", bound="hbm", achieved=b / (phases["push"] * 1e-3) / 1e9,
+                             peak=peak_hbm, unit="GB/s", algorithmic_bytes_per_launch=b,
+                             mean_launch_ms=phases["push"], share=phases["push"] / ms_per_step)
+    b = FDTD_BYTES_PER_CELL * cells
+    roofs["field"] = dict(kernel="k_b_half + k_e_yee + k_mur (split Yee step)", bound="hbm",
+                          achieved=b / (phases["field"] * 1e-3) / 1e9, peak=peak_hbm, unit="GB/s",
+                          algorithmic_bytes_per_launch=b, mean_launch_ms=phases["field"],
+                          share=phases["field"] / ms_per_step)
+    if nfl and phases["fluid"] > 0:
+        b = (FLUID_BYTES_PER_NODE + FLUID_FIELD_BYTES_PER_NODE) * cells * nfl
+        roofs["fluid"] = dict(kernel="k_fluid_*", bound="hbm", achieved=b / (phases["fluid"] * 1e-3) / 1e9,
+                              peak=peak_hbm, unit="GB/s", algorithmic_bytes_per_launch=b,
+                              mean_launch_ms=phases["fluid"], share=phases["fluid"] / ms_per_step)
+    if cls:
+        f = CLS_FLOP_PER_CELL_PASS * cells * MC_PASSES
+        pk = peaks.get("bf16_tflops_sustained", 1700.0)
+        roofs["classify"] = dict(kernel="k_conv3_tc (+ prep, last layer, MC statistics)", bound="tensor",
+                                 achieved=f / (cls["classify"] * 1e-3) / 1e12, peak=pk, unit="TFLOP/s",
+                                 algorithmic_flop_per_launch=f, mean_launch_ms=cls["classify"],
+                                 share=cls["classify"] / N_CLS / ms_per_step)
+    for r in roofs.values():
+        r["frac"] = r["achieved"] / r["peak"]
+        r["peak_kind"] = "measured" if peaks else "fallback"
+        r["traffic"] = None
+    dom = max(roofs, key=lambda k: roofs[k]["share"])
+
+    full = None
+    if kind == "hybrid" and not args.no_full_pic:
+        fsim, _ = make_sim(P, inp, stream.cuda_stream, policy="all_kinetic")
+        fms, _, fb, fa = timed_run(torch, fsim, None, args.steps, args.warmup, stream.cuda_stream, barrier, False)
+        fms = allmax(fms)
+        fparts = 0.5 * (sum(fb["count"]) + sum(fa["count"]))
+        fsim.close()
+        full = {"steps_per_s": world * args.steps / (fms * 1e-3), "ms_per_step": fms / args.steps,
+                "particles": fparts, "particle_pushes_per_s": world * fparts * args.steps / (fms * 1e-3),
+                "hybrid_speedup": fms / total_ms}
 
     e2e = run_e2e(P, inp, args.steps, stream) if rank == 0 else None
     out = {
-        "metric": METRIC, "value": steps_per_s, "unit": "steps/s", "n_gpus": world,
+        "metric": METRIC, "value": world * args.steps / (total_ms * 1e-3), "unit": "steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded)",
-        "config": {"workload": args.workload, "grid": [g["nx"], g["ny"], g["nz"]], "particles": npart,
-                   "species": len(inp["species"]), "parallelism": "replicas" if world > 1 else "single",
-                   "l2": "flushed between timed steps (256 MiB write outside the events)"},
-        "particle_pushes_per_s": world * npart * args.steps / (total_ms * 1e-3),
+        "config": {"workload": args.workload, "kind": kind, "grid": [g["nx"], g["ny"], g["nz"]],
+                   "particles_mean": parts, "kinetic_fraction": kin_frac,
+                   "classify_every": N_CLS if kind == "hybrid" else None,
+                   "mc_passes": MC_PASSES if kind == "hybrid" else None,
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "l2": ("flushed between timed steps (2 x L2 write outside the events)" if flush_l2 else
+                          "resident state larger than L2 (%.0f MB); no flush" % (state_bytes(after, cells) / 1e6))},
+        "particle_pushes_per_s": world * parts * args.steps / (total_ms * 1e-3),
         "cell_updates_per_s": world * cells * args.steps / (total_ms * 1e-3),
-        "phase_ms": phase_mean,
-        "roofline": {"kernel": "k_push_deposit", "bound": "hbm", "achieved": achieved, "peak": peak,
-                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": None, "algorithmic_bytes_per_launch": push_bytes,
-                     "mean_launch_ms": mean_push_ms},
+        "full_pic": full,
+        "phase_ms": phases, "classification_ms": cls,
+        "roofline": roofs[dom], "roofline_all": roofs,
         "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clk,
@@ -198,8 +344,9 @@ def run_ours(args, rank, world):
 
 
 def run_e2e(P, inp, steps, stream):
-    """Whole job through the C ABI from pinned host buffers: create the context,
-    upload particles and fields, then per step advance and read the FP64
+    """Whole job through the public API from pinned host buffers: create the
+    context, upload the initial state (particles or fluids, fields), classify,
+    then per step advance (reclassifying every N_CLS steps) and read the FP64
     diagnostics back to the host."""
     import torch
 
@@ -208,59 +355,123 @@ def run_e2e(P, inp, steps, stream):
         return t.numpy(), t
 
     keep = []
-    pin = {"grid": inp["grid"], "species": []}
+    pin = {k: v for k, v in inp.items() if k not in ("species", "fluids", "E", "B")}
+    pin["species"], pin["fluids"] = [], []
     h2d = 0
     for sp in inp["species"]:
-        d = {"q": sp["q"], "m": sp["m"]}
+        d = dict(sp)
         for k in ("x", "y", "z", "ux", "uy", "uz", "w"):
             arr, t = pinned(sp[k])
             keep.append(t)
             d[k] = arr
             h2d += arr.nbytes
         pin["species"].append(d)
+    for fl in inp.get("fluids", []):
+        d = dict(fl)
+        arr, t = pinned(fl["n"])
+        keep.append(t)
+        d["n"] = arr
+        h2d += arr.nbytes
+        pin["fluids"].append(d)
     if "E" in inp:
         for k in ("E", "B"):
             arr, t = pinned(inp[k])
             keep.append(t)
             pin[k] = arr
             h2d += arr.nbytes
+    if not pin["fluids"]:
+        del pin["fluids"]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    sim = make_sim(P, pin, stream.cuda_stream)
+    sim, model = make_sim(P, pin, stream.cuda_stream, policy="union")
     d2h = 0
-    for _ in range(steps):
-        sim.step(1)
-        sim.diagnostics()
-        d2h += 8 * (3 + 2 * len(inp["species"]))
+    for k in range(steps):
+        advance(sim, model, 1, k)
+        diag = sim.diagnostics()
+        d2h += 8 * (3 + 2 * len(diag["count"]) + 2 * len(diag["n_fluid"]))
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     sim.close()
+    if model is not None:
+        model.close()
     return {"value": steps / dt, "unit": "steps/s", "h2d_bytes_per_step": h2d / steps,
             "d2h_bytes_per_step": d2h / steps,
-            "note": "context creation + host upload amortised over the steps; per-step FP64 diagnostics read"}
+            "note": "context creation, host upload and the first classification amortised over the steps; "
+                    "FP64 diagnostics read back every step"}
+
+
+def oracle_sample(workload):
+    """The FP64 oracle (as it stands) set up on a bounded sample of the
+    workload: the full workload for "pic" ones; for "hybrid" ones the same
+    recipe on a 16 x 16 transverse cross-section (full length along x, so the
+    ramp, slab and pulse are the same), with an oracle classifier of the same
+    architecture (He-uniform weights from numpy's generator, output bias -4)
+    united with the physics criterion.  Returns (sim, net, cells ratio,
+    description)."""
+    import oracle.sim as S
+    kind, gen = workloads()[workload]
+    if kind == "pic":
+        inp = gen(1)
+        ratio, what = 1.0, "the full %s workload" % workload
+    else:
+        full = gen(1)["grid"]
+        from paper_2510_11174_gb300 import inputs
+        inp = inputs.ramp_slab(nx=full["nx"], ny=16, nz=16, seed=3, a0=gen(1)["a0"])
+        ratio = full["nx"] * full["ny"] * full["nz"] / float(inp["grid"]["nx"] * 16 * 16)
+        what = "a %dx16x16 cross-section of %s (1/%d of its cells)" % (full["nx"], workload, round(ratio))
+    g = inp["grid"]
+    o = S.OracleSim(g["nx"], g["ny"], g["nz"], g["dx"], cfl_frac=g["cfl_frac"], bc=g["bc"], laser=inp.get("laser"))
+    for sp in inp["species"]:
+        o.load_species(**sp)
+    for fl in inp.get("fluids", []):
+        o.load_fluid(**fl, n_floor=0.0)
+    if "E" in inp:
+        o.set_fields(inp["E"], inp["B"])
+    net = None
+    if inp.get("fluids"):
+        from oracle.classifier import OracleCNN, LAYERS
+        rng = np.random.default_rng(11)
+        ws = []
+        for ci, co in LAYERS:
+            lim = math.sqrt(6.0 / (27 * ci))
+            ws.append((rng.uniform(-lim, lim, (co, ci, 3, 3, 3)).astype(np.float32), np.zeros(co, np.float32)))
+        ws[-1] = (ws[-1][0], np.full(1, -4.0, np.float32))
+        net = OracleCNN(ws, dropout=0.2, seed=11)
+        o.set_regime(dilate=2, ppc=inp["ppc"], to_species=list(range(len(inp["fluids"]))), policy="union")
+        o.classify(net, passes=MC_PASSES)
+    return o, net, ratio, what
+
+
+def oracle_advance(o, net, n, step0):
+    for k in range(n):
+        o.step(1)
+        if net is not None and (step0 + k + 1) % N_CLS == 0:
+            o.classify(net, passes=MC_PASSES)
+
+
+def oracle_threads():
+    import torch
+    return torch.get_num_threads()
 
 
 def run_oracle_sample(workload, budget_s=15.0, max_steps=None):
-    """Time the FP64 oracle (as it stands) on the workload for about budget_s."""
-    import oracle.sim as S
-    inp = workloads()[workload](1)
-    g = inp["grid"]
-    o = S.OracleSim(g["nx"], g["ny"], g["nz"], g["dx"], cfl_frac=g["cfl_frac"], bc=g["bc"],
-                    laser=inp.get("laser"))
-    for sp in inp["species"]:
-        o.load_species(**sp)
-    if "E" in inp:
-        o.set_fields(inp["E"], inp["B"])
-    npart = count_particles(inp)
+    """Time the oracle on its bounded sample for about budget_s; the value is
+    scaled to the whole workload by the cell ratio (its work is linear in
+    cells and particles, both proportional to the cross-section)."""
+    o, net, ratio, what = oracle_sample(workload)
     t0 = time.perf_counter()
     n = 0
+    parts = sum(sp.n for sp in o.species)
     while time.perf_counter() - t0 < budget_s and (max_steps is None or n < max_steps):
-        o.step(1)
+        oracle_advance(o, net, 1, n)
         n += 1
     dt = time.perf_counter() - t0
-    return {"value": n / dt, "unit": "steps/s", "cores": 1, "kind": "oracle",
-            "sample": "%d full steps of the %s workload (%d particles), single-threaded FP64 C" % (n, workload, npart),
-            "particle_pushes_per_s": n * npart / dt}
+    cores = 1 if net is None else oracle_threads()
+    return {"value": n / dt / ratio, "unit": "steps/s", "cores": cores, "kind": "oracle",
+            "sample": "%d steps of %s (%d particles at the start), FP64 C single-threaded; classifier convolutions "
+                      "in PyTorch CPU on %d threads; steps/s divided by %g" % (n, what, parts, oracle_threads(),
+                                                                             ratio),
+            "particle_pushes_per_s": n * parts / dt}
 
 
 def run_reference(args, rank, world):
@@ -268,36 +479,37 @@ def run_reference(args, rank, world):
         return None
     from oracle import build as OB
     OB.build()
-    for _ in range(args.warmup):
-        pass
-    samples = []
-    per = max(5.0, 60.0 / max(1, args.steps))
-    for _ in range(max(1, args.steps)):
-        samples.append(run_oracle_sample(args.workload, budget_s=min(per, 20.0))["value"])
-        if sum(1.0 / s for s in samples) > 150:
-            break
-    cb = run_oracle_sample(args.workload, budget_s=5.0)
-    v = statistics.mean(samples)
-    inp = workloads()[args.workload](1)
-    g = inp["grid"]
+    o, net, ratio, what = oracle_sample(args.workload)
+    oracle_advance(o, net, args.warmup, 0)
+    parts0 = sum(sp.n for sp in o.species)
+    t0 = time.perf_counter()
+    oracle_advance(o, net, args.steps, args.warmup)
+    dt = time.perf_counter() - t0
+    parts = 0.5 * (parts0 + sum(sp.n for sp in o.species))
+    v = args.steps / dt / ratio
+    g = workloads()[args.workload][1](1)["grid"]
+    cores = 1 if net is None else oracle_threads()
+    sample = ("%d timed steps (after %d warm-up) of %s; FP64 C single-threaded, classifier convolutions in PyTorch "
+              "CPU on %d threads; value = sample steps/s / %g" % (args.steps, args.warmup, what, oracle_threads(),
+                                                                   ratio))
     return {"metric": METRIC, "value": v, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 / v, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)", "impl": "reference",
-            "config": {"workload": args.workload, "grid": [g["nx"], g["ny"], g["nz"]],
-                       "particles": count_particles(inp)},
-            "cpu_baseline": {"value": v, "unit": "steps/s", "cores": 1, "kind": "oracle",
-                             "sample": cb["sample"]},
+            "config": {"workload": args.workload, "grid": [g["nx"], g["ny"], g["nz"]]},
+            "particle_pushes_per_s_sample": parts * args.steps / dt,
+            "cpu_baseline": {"value": v, "unit": "steps/s", "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="periodic_plasma_32")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-full-pic", action="store_true", help="skip the full-PIC comparison run")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         ap.error("--warmup must be >= 3")
@@ -312,8 +524,7 @@ def main():
     else:
         out = run_ours(args, rank, world)
         if rank == 0 and world == 1 and not args.no_cpu_baseline:
-            cb = run_oracle_sample(args.workload, budget_s=15.0)
-            out["cpu_baseline"] = cb
+            out["cpu_baseline"] = run_oracle_sample(args.workload, budget_s=15.0)
     if rank == 0 and out is not None:
         print(json.dumps(out))
     if world > 1 and args.impl == "ours":

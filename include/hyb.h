@@ -172,6 +172,7 @@ typedef struct {
     double w_fluid[HYB_MAX_FLUIDS];        /* sum n m (gamma - 1) dV per fluid */
     double n_fluid[HYB_MAX_FLUIDS];        /* sum n dV per fluid */
     long long n_clamped;                   /* fluid nodes clamped from negative density so far */
+    long long launches_classify;           /* kernels the most recent hyb_classify launched */
 } hyb_diag;
 
 /* Create a context: validates the descriptor, allocates fields on the
@@ -208,7 +209,17 @@ typedef struct {
     double k_sigma;                       /* classifier decision: p_mean + k_sigma p_std >= 0.5 */
     int ppc;                              /* macro-particles per node created from fluid */
     int to_species[HYB_MAX_FLUIDS];
+    int policy;                           /* HYB_REGIME_* below */
 } hyb_regime_desc;
+/* Which decision hyb_classify takes.  DEFAULT: the classifier when a model is
+ * given, else the physics criterion.  UNION: a node is kinetic when the
+ * classifier or the physics criterion says so (the thresholds act as prior
+ * knowledge the network can only add to).  ALL_KINETIC: every node is
+ * kinetic, i.e. all fluid becomes macro-particles (the full-PIC run that
+ * judges the hybrid's error). */
+#define HYB_REGIME_DEFAULT 0
+#define HYB_REGIME_UNION 1
+#define HYB_REGIME_ALL_KINETIC 2
 hyb_status hyb_set_regime(hyb_ctx *ctx, const hyb_regime_desc *desc);
 
 /* Recompute the regime mask and convert (stream-ordered).  model = NULL uses
@@ -326,7 +337,8 @@ hyb_status hyb_clear_status(hyb_ctx *ctx);
 /* Per-phase timing of a step.  With profiling on, the captured step graph
  * records a CUDA event (on the context's stream) at every phase boundary;
  * hyb_phase_times synchronises and returns the device time of each phase of
- * the most recent step in milliseconds (0 for phases the step does not run).
+ * the most recent step in milliseconds (0 for phases the step does not run);
+ * the two hyb_classify phases report the most recent classification.
  * Turning profiling on or off rebuilds the step graph. */
 enum {
     HYB_PH_PUSH = 0,      /* gather + Boris + move + Esirkepov into tile frames */
@@ -335,6 +347,8 @@ enum {
     HYB_PH_REBIN = 3,     /* migration + compaction of particle tiles */
     HYB_PH_FIELD = 4,     /* B half, E, Mur, B half */
     HYB_PH_FLUID = 5,     /* cold fluid Lorentz step, transport, face currents */
+    HYB_PH_CLASSIFY = 6,  /* hyb_classify: classifier forward over the MC-dropout passes */
+    HYB_PH_REGIME = 7,    /* hyb_classify: decision, dilation, conversions */
     HYB_NPHASE = 8
 };
 typedef struct {

@@ -16,9 +16,53 @@ import math
 
 import numpy as np
 
-from . import (Fluid, Grid, Particles, energy_fields, energy_particles, fdtd_b_half, fdtd_e, fluid_energy, fluid_step,
-               gather_species, ionize, laser_source, photon_move, push_deposit, qed_emit, qed_kappa, qed_pairs,
-               qed_tau0, zeros_field)
+from . import (Fluid, Grid, Particles, charge_density, energy_fields, energy_particles, fdtd_b_half, fdtd_e,
+               fluid_energy, fluid_step, fluid_to_particles, gather_species, ionize, laser_source, particles_to_fluid,
+               photon_move, push_deposit, qed_emit, qed_kappa, qed_pairs, qed_tau0, regime_criterion, zeros_field)
+
+
+def node_fields(g, E, B):
+    """The six field components at the nodes (the classifier's input): each E
+    component averaged over the two edges that meet at the node along its
+    axis, each B component over the four faces around it; a neighbour outside
+    a non-periodic axis counts as zero.  Returns [6, nz, ny, nx]."""
+    def at(F, shifts):
+        out = np.asarray(F, dtype=np.float64)
+        for axis, sh in shifts:
+            nd = 2 - axis                     # array axis of grid axis `axis` (x fastest)
+            out = np.roll(out, 1, axis=nd) if sh else out
+            if sh and g.bc[axis]:
+                sl = [slice(None)] * 3
+                sl[nd] = 0
+                out = out.copy()
+                out[tuple(sl)] = 0.0
+        return out
+    f = np.zeros((6,) + tuple(g.shape))
+    for a in range(3):
+        f[a] = 0.5 * (at(E[a], [(a, 1)]) + at(E[a], []))
+    for a in range(3):
+        p, q = [b for b in range(3) if b != a]
+        f[3 + a] = 0.25 * (at(B[a], [(p, 1), (q, 1)]) + at(B[a], [(q, 1)]) + at(B[a], [(p, 1)]) + at(B[a], []))
+    return f
+
+
+def dilate(g, raw, r):
+    """Chebyshev dilation by r nodes: a node is set when any node within r
+    along every axis is (periodic axes wrap, others stop at the edge)."""
+    m = np.asarray(raw, dtype=bool)
+    for a in range(3):
+        nd = 2 - a
+        out = m.copy()
+        for d in range(1, r + 1):
+            for sgn in (1, -1):
+                sh = np.roll(m, sgn * d, axis=nd)
+                if g.bc[a]:
+                    sl = [slice(None)] * 3
+                    sl[nd] = slice(0, d) if sgn > 0 else slice(-d, None)
+                    sh[tuple(sl)] = False
+                out |= sh
+        m = out
+    return m.astype(np.uint8)
 
 
 def courant_dt(d, cfl_frac):
@@ -54,6 +98,11 @@ class OracleSim:
         self.fluids = []
         self.n_clamped = 0
         self.nstep = 0
+        self.regime = dict(a_thr=1.0, n_thr=1.0, c_thr=0.1, chi_thr=1e-3, dilate=2, k_sigma=1.0, ppc=8,
+                           to_species=[], policy="default")
+        self.epoch = 0
+        self.mask = np.ones(self.g.shape, dtype=np.uint8)
+        self.rho_bg = np.zeros(self.g.shape)
 
     def load_species(self, q, m, x, y, z, ux, uy, uz, w, zq=None, ids=None, ionize=None, kind=0, qed=None,
                      pairs=None, **_):
@@ -77,6 +126,70 @@ class OracleSim:
                 u[a] = np.asarray(v, dtype=np.float64)
         self.fluids.append(Fluid(q, m, n, u, n_floor=n_floor))
         return len(self.fluids) - 1
+
+    def set_regime(self, a_thr=1.0, n_thr=1.0, c_thr=0.1, chi_thr=1e-3, dilate=2, k_sigma=1.0, ppc=8,
+                   to_species=None, policy="default"):
+        self.regime = dict(a_thr=a_thr, n_thr=n_thr, c_thr=c_thr, chi_thr=chi_thr, dilate=dilate,
+                           k_sigma=k_sigma, ppc=ppc, to_species=list(to_species or []), policy=policy)
+
+    def classify(self, net=None, passes=16, mask=None):
+        """Regime decision and conversions (Methodology: fluid where the flow
+        is stable, PIC where the classifier or the physics flags it):
+        physics criterion on the electron density (fluid + CIC of the
+        electron macro-particles) and the first electron fluid's velocity,
+        and/or the classifier's MC-dropout decision p_mean + k_sigma p_std >=
+        0.5 on the node fields, each dilated; then per fluid f the fluid at
+        kinetic nodes becomes macro-particles of species to_species[f] and
+        that species' particles whose nearest node is fluid go back into f.
+        Returns (p_mean, p_std) of the classifier, or (None, None).  A given
+        `mask` (1 = kinetic) replaces the decision: the conversions alone."""
+        r, g = self.regime, self.g
+        if mask is not None:
+            return self._convert(np.ascontiguousarray(mask, dtype=np.uint8)) or (None, None)
+        all_k = r["policy"] == "all_kinetic"
+        physics = not all_k and (net is None or r["policy"] == "union")
+        mask = np.full(g.shape, 1 if all_k else 0, dtype=np.uint8)
+        pm = ps = None
+        if physics:
+            ne = np.zeros(g.shape)
+            for sp, k in zip(self.species, self.kind):
+                if k == 0 and sp.q < 0 and sp.zq is None:
+                    ne -= charge_density(g, sp) / (-sp.q)
+            fe = next((fl for fl in self.fluids if fl.q < 0), None)
+            if fe is not None:
+                ne += fe.n
+            mask |= regime_criterion(g, self.E, self.B, ne, fluid_u=None if fe is None else fe.u,
+                                     lambda_m=self.lambda_m, a_thr=r["a_thr"], n_thr=r["n_thr"], c_thr=r["c_thr"],
+                                     chi_thr=r["chi_thr"], dilate=r["dilate"])
+        if net is not None and not all_k:
+            x = node_fields(g, self.E, self.B)[None]
+            if passes > 1:
+                pm, ps = net.mc_statistics(x, passes)
+                pm, ps = pm[0].numpy(), ps[0].numpy()
+            else:
+                import torch
+                pm, ps = torch.sigmoid(net.forward(x, pass_index=-1))[0].numpy(), np.zeros(g.shape)
+            mask |= dilate(g, pm + r["k_sigma"] * ps >= 0.5, r["dilate"])
+        self._convert(mask)
+        return pm, ps
+
+    def _convert(self, mask):
+        r, g = self.regime, self.g
+        for f, fl in enumerate(self.fluids):
+            ts = r["to_species"]
+            sid = ts[f] if f < len(ts) else -1
+            if sid is None or sid < 0:
+                continue
+            new = fluid_to_particles(g, mask, fl, r["ppc"], self.seed, sid, self.epoch, self.rho_bg)
+            dst = self.species[sid]
+            if dst.tau is not None:
+                new.tau = qed_tau0(new.ids, self.seed, sid)
+            if dst.zq is not None:
+                new.zq = np.zeros(new.n)
+            dst.append(new)
+            particles_to_fluid(g, mask, dst, fl)
+        self.epoch += 1
+        self.mask = mask
 
     def set_fields(self, E, B):
         self.E[:] = np.asarray(E, dtype=np.float64)

@@ -58,11 +58,11 @@ class hyb_diag(C.Structure):
                 ("w_photon_untracked", C.c_double), ("w_pair_deficit", C.c_double),
                 ("n_emit", C.c_longlong), ("n_pair", C.c_longlong),
                 ("n_fluids", C.c_int), ("w_fluid", C.c_double * 4), ("n_fluid", C.c_double * 4),
-                ("n_clamped", C.c_longlong)]
+                ("n_clamped", C.c_longlong), ("launches_classify", C.c_longlong)]
 
 
 HYB_NPHASE = 8
-PHASES = ["push", "j_reduce", "source", "rebin", "field", "fluid", "ph6", "ph7"]
+PHASES = ["push", "j_reduce", "source", "rebin", "field", "fluid", "classify", "regime"]
 HYB_MAX_FLUIDS = 4
 
 
@@ -79,7 +79,10 @@ class hyb_phase_times_t(C.Structure):
 class hyb_regime_desc(C.Structure):
     _fields_ = [("a_thr", C.c_double), ("n_thr", C.c_double), ("c_thr", C.c_double), ("chi_thr", C.c_double),
                 ("dilate", C.c_int), ("k_sigma", C.c_double), ("ppc", C.c_int),
-                ("to_species", C.c_int * 4)]
+                ("to_species", C.c_int * 4), ("policy", C.c_int)]
+
+
+HYB_REGIME_DEFAULT, HYB_REGIME_UNION, HYB_REGIME_ALL_KINETIC = 0, 1, 2
 
 
 class hyb_model_desc(C.Structure):

@@ -75,7 +75,7 @@ static void enqueue_step(hyb_ctx *c) {
     cudaStream_t st = c->stream;
     const SpSet set = species_set(c);
     PhaseMark pm{c};
-    for (int p = 0; p < HYB_NPHASE; ++p) c->phase_ran[p] = false;
+    for (int p = 0; p < HYB_PH_CLASSIFY; ++p) c->phase_ran[p] = false;
     cudaMemsetAsync(c->mig_counts, 0, sizeof(int) * HYB_MAX_SPECIES, st);
     if (set.n > 0) {
         pm.begin(HYB_PH_PUSH);
@@ -87,7 +87,8 @@ static void enqueue_step(hyb_ctx *c) {
     } else {
         cudaMemsetAsync(c->J, 0, sizeof(float) * 3 * g.N, st);
     }
-    if (!c->fluids.empty()) {
+    const bool fluid_phase = !c->fluids.empty() && !c->fluids_idle;
+    if (fluid_phase) {
         pm.begin(HYB_PH_FLUID);
         for (const FluidDev &f : c->fluids) launch_fluid(g, c->E, c->B, f, c->J, st);
         pm.end(HYB_PH_FLUID);
@@ -116,7 +117,7 @@ static void enqueue_step(hyb_ctx *c) {
     // kernels enqueued above (memsets and event records are not kernels)
     long long k = 0;
     if (set.n > 0) k += 2 + 2LL * set.n;
-    k += 2LL * (long long)c->fluids.size();
+    if (fluid_phase) k += 2LL * (long long)c->fluids.size();
     if (c->desc.laser_kind == HYB_LASER_GAUSS) k += 1;
     k += 3 + ((g.bc[0] || g.bc[1] || g.bc[2]) ? 3 : 0) + 1;
     c->launches_per_step = k;
@@ -569,6 +570,7 @@ hyb_status hyb_load_fluid(hyb_ctx *c, const hyb_fluid_desc *d, int *fluid_id) {
     }
     HYB_CUDA_TRY(cudaMemsetAsync(f.clamped, 0, sizeof(unsigned long long), c->stream));
     HYB_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    c->fluids_idle = false;
     *fluid_id = (int)c->fluids.size();
     c->fluids.push_back(f);
     c->graph_valid = false;
@@ -579,6 +581,8 @@ hyb_status hyb_set_regime(hyb_ctx *c, const hyb_regime_desc *d) {
     if (!c || !d) return set_error(HYB_EINVAL, "null argument");
     if (d->dilate < 0 || d->dilate > 8) return set_error(HYB_EINVAL, "dilate must be in 0..8");
     if (d->ppc < 0 || d->ppc > 64) return set_error(HYB_EINVAL, "ppc must be in 0..64");
+    if (d->policy < HYB_REGIME_DEFAULT || d->policy > HYB_REGIME_ALL_KINETIC)
+        return set_error(HYB_EINVAL, "policy must be one of HYB_REGIME_*");
     for (int f = 0; f < HYB_MAX_FLUIDS; ++f)
         if (d->to_species[f] >= (int)c->sp.size() ||
             (d->to_species[f] >= 0 && c->sp[d->to_species[f]].dev.kind != HYB_KIND_MASSIVE))
@@ -602,13 +606,21 @@ hyb_status hyb_classify(hyb_ctx *c, const hyb_model *model, float *p_mean_dev, f
             return set_error(HYB_EINVAL, "a fluid converts into a species of the same charge and mass");
     }
     hyb_status s;
+    c->launches_classify = 0;
+    auto mark = [c](cudaEvent_t e) {
+        if (c->profiling) cudaEventRecord(e, c->stream);
+    };
     if (model) {
+        c->phase_ran[HYB_PH_CLASSIFY] = true;
+        mark(c->ev_start[HYB_PH_CLASSIFY]);
         s = classifier_forward(c, model, p_mean_dev, p_std_dev);
+        mark(c->ev_end[HYB_PH_CLASSIFY]);
         if (s != HYB_OK) return s;
-        s = regime_update(c, model_p_mean(model), model_p_std(model));
-    } else {
-        s = regime_update(c, nullptr, nullptr);
     }
+    c->phase_ran[HYB_PH_REGIME] = true;
+    mark(c->ev_start[HYB_PH_REGIME]);
+    s = model ? regime_update(c, model_p_mean(model), model_p_std(model)) : regime_update(c, nullptr, nullptr);
+    mark(c->ev_end[HYB_PH_REGIME]);
     if (s != HYB_OK) return s;
     if (mask_dev) HYB_CUDA_TRY(cudaMemcpyAsync(mask_dev, c->mask, (size_t)c->g.N, cudaMemcpyDeviceToDevice, c->stream));
     return HYB_OK;
@@ -693,7 +705,7 @@ hyb_status hyb_phase_times(hyb_ctx *c, hyb_phase_times_t *out) {
     HYB_CUDA_TRY(cudaStreamSynchronize(c->stream));
     for (int p = 0; p < HYB_NPHASE; ++p) {
         out->ms[p] = 0.0f;
-        if (!c->phase_ran[p] || c->step == 0) continue;
+        if (!c->phase_ran[p] || (c->step == 0 && p < HYB_PH_CLASSIFY)) continue;
         HYB_CUDA_TRY(cudaEventElapsedTime(&out->ms[p], c->ev_start[p], c->ev_end[p]));
     }
     return HYB_OK;
@@ -767,6 +779,7 @@ hyb_status hyb_diagnostics(hyb_ctx *c, hyb_diag *out) {
     for (int s = 0; s < set.n; ++s) out->w_kin[s] = r[2 + s];
     out->status = status_to_code(h);
     out->launches_per_step = c->launches_per_step;
+    out->launches_classify = c->launches_classify;
     out->n_fluids = nfl;
     for (int f = 0; f < nfl; ++f) {
         out->w_fluid[f] = r[2 + set.n + 2 * f];

@@ -269,6 +269,7 @@ hyb_status classifier_forward(hyb_ctx *c, const hyb_model *mc, float *p_mean_dev
     if (s == HYB_OK) {
         // ps held M2; turn it into the standard deviation in place
         k_mc_final<<<nb(g.N), 256, 0, c->stream>>>(g.N, K, m->ps, m->ps);
+        c->launches_classify += 2 + 5LL * K;  // prep, K x (3 conv + last layer + MC update), final
         if (p_mean_dev) cudaMemcpyAsync(p_mean_dev, m->pm, sizeof(float) * g.N, cudaMemcpyDeviceToDevice, c->stream);
         if (p_std_dev) cudaMemcpyAsync(p_std_dev, m->ps, sizeof(float) * g.N, cudaMemcpyDeviceToDevice, c->stream);
     }

@@ -175,6 +175,7 @@ struct hyb_ctx {
     float *rho_bg = nullptr;                       // residual background charge
     float *ne = nullptr;                           // electron density scratch
     uint32_t epoch = 0;                            // conversion counter (Philox counter word)
+    bool fluids_idle = false;                      // every fluid was converted by an all-kinetic classification
 
     // LCFA QED tables (built on first use)
     bool qed_ready = false;
@@ -191,6 +192,7 @@ struct hyb_ctx {
     cudaEvent_t ev_end[HYB_NPHASE] = {};
     bool phase_ran[HYB_NPHASE] = {};
     long long launches_per_step = 0;
+    long long launches_classify = 0;               // kernels the most recent hyb_classify launched
 
     // laser transverse profile (FP32, ny*nz) when a Gaussian source is set
     float *laser_profile = nullptr;

@@ -29,6 +29,33 @@ __device__ __forceinline__ int warp_append(int *counter) {
     return b + __popc(mask & ((1u << lane) - 1u));
 }
 
+// a particle placed straight into tile t, which must hold no holes (a compacted
+// tile); the lanes of a warp that target the same tile share one atomic.  A
+// full tile latches ST_OVERFLOW and drops the particle (the count is clamped
+// back to the capacity by launch_clamp_counts).
+__device__ __forceinline__ void tile_put(const SpDev &d, int t, const float x[3], const float u[3], float w,
+                                         uint64_t id, float tau, int *status) {
+    const unsigned act = __activemask();
+    const unsigned peers = __match_any_sync(act, t);
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(peers) - 1;
+    int b = 0;
+    if (lane == leader) b = atomicAdd(&d.count[t], __popc(peers));
+    b = __shfl_sync(peers, b, leader);
+    const int slot = b + __popc(peers & ((1u << lane) - 1u));
+    if (slot >= d.cap) {
+        atomicOr(status, ST_OVERFLOW);
+        return;
+    }
+    const long long s = (long long)t * d.cap + slot;
+    d.x[s] = x[0]; d.y[s] = x[1]; d.z[s] = x[2];
+    d.ux[s] = u[0]; d.uy[s] = u[1]; d.uz[s] = u[2];
+    d.w[s] = w;
+    if (d.zq) d.zq[s] = 0.0f;
+    if (d.tau) d.tau[s] = tau;
+    d.id[s] = id;
+}
+
 // initial optical depth of a particle: -ln u, u from counter (id_lo, id_hi, 2^32-1, 4)
 __device__ __forceinline__ float tau_initial(uint64_t id, uint32_t seed, uint32_t key1) {
     const u32x4 r = philox4x32_10((uint32_t)id, (uint32_t)(id >> 32), 0xFFFFFFFFu, RNG_QED_TAU, seed, key1);

@@ -96,10 +96,19 @@ __global__ void k_criterion(GridDev g, const float *__restrict__ E, const float 
     raw[c] = kin ? 1 : 0;
 }
 
+// classifier decision; with `merge` the node also stays kinetic where the
+// physics criterion already marked it
 __global__ void k_decide(long long N, const float *__restrict__ pm, const float *__restrict__ ps, float k_sigma,
-                         uint8_t *__restrict__ raw) {
+                         int merge, uint8_t *__restrict__ raw) {
     const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c < N) raw[c] = pm[c] + k_sigma * ps[c] >= 0.5f ? 1 : 0;
+    if (c >= N) return;
+    const bool kin = pm[c] + k_sigma * ps[c] >= 0.5f;
+    raw[c] = (kin || (merge && raw[c])) ? 1 : 0;
+}
+
+__global__ void k_clamp_counts(int ntiles, SpDev sp) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < ntiles && sp.count[t] > sp.cap) sp.count[t] = sp.cap;
 }
 
 // max filter of radius r along axis a (Chebyshev dilation is three of these)
@@ -172,7 +181,8 @@ __global__ void k_fluid_to_particles(GridDev g, const uint8_t *__restrict__ mask
             atomicAdd(&rho_bg[cidx(g, q[0], q[1], q[2])], -dst.q * w / dV * wgt);
         }
         const uint64_t id = (1ULL << 62) | (derived_id((uint64_t)c | ((uint64_t)epoch << 40), p, 6u) >> 2);
-        spawn(dst, pos, u, w, id, tile_index(g, pos[0], pos[1], pos[2]), 0, g.seed, -1.0f, status);
+        const float tau = dst.tau ? tau_initial(id, g.seed, dst.tau_index) : 0.0f;
+        tile_put(dst, tile_index(g, pos[0], pos[1], pos[2]), pos, u, w, id, tau, status);
     }
     f.n[c] = 0.0f;
     f.ux[c] = f.uy[c] = f.uz[c] = 0.0f;
@@ -261,10 +271,14 @@ hyb_status regime_update(hyb_ctx *c, const float *pm, const float *ps) {
     cudaStream_t st = c->stream;
     const hyb_regime_desc &rd = c->regime;
     uint8_t *raw = c->mask_tmp, *mask = c->mask;
-    if (!pm) {
+    const bool all = rd.policy == HYB_REGIME_ALL_KINETIC;
+    const bool physics = !all && (!pm || rd.policy == HYB_REGIME_UNION);
+    long long launches = 0;
+    if (all) cudaMemsetAsync(raw, 1, (size_t)g.N, st);
+    if (physics) {
         cudaMemsetAsync(c->ne, 0, sizeof(float) * g.N, st);
         for (const Species &s : c->sp)
-            if (s.dev.kind == 0 && s.q < 0.0 && !s.has_zq)
+            if (s.dev.kind == 0 && s.q < 0.0 && !s.has_zq && ++launches)
                 k_density<<<g.ntiles, 256, 0, st>>>(g, s.dev, (float)(-s.q / (g.dd[0] * g.dd[1] * g.dd[2])), c->ne);
         int fe = -1;
         for (size_t f = 0; f < c->fluids.size(); ++f)
@@ -279,29 +293,41 @@ hyb_status regime_update(hyb_ctx *c, const float *pm, const float *ps) {
         const float kappa = lambda > 0.0 ? (float)(1.054571817e-34 * 2.0 * M_PI * 299792458.0 / lambda /
                                                    (9.1093837015e-31 * 299792458.0 * 299792458.0))
                                          : 0.0f;
+        ++launches;
         k_criterion<<<nblk(g.N), 256, 0, st>>>(g, c->E, c->ne, fd, fe >= 0, kappa, (float)rd.a_thr, (float)rd.n_thr,
                                                (float)rd.c_thr, (float)rd.chi_thr, raw);
-    } else {
-        k_decide<<<nblk(g.N), 256, 0, st>>>(g.N, pm, ps, (float)rd.k_sigma, raw);
     }
+    if (pm && !all && ++launches) k_decide<<<nblk(g.N), 256, 0, st>>>(g.N, pm, ps, (float)rd.k_sigma, physics ? 1 : 0, raw);
     // Chebyshev dilation: max filters along x, y, z (raw -> mask -> raw -> mask)
     k_dilate<<<nblk(g.N), 256, 0, st>>>(g, 0, rd.dilate, raw, mask);
     k_dilate<<<nblk(g.N), 256, 0, st>>>(g, 1, rd.dilate, mask, raw);
     k_dilate<<<nblk(g.N), 256, 0, st>>>(g, 2, rd.dilate, raw, mask);
+    launches += 3;
     // conversions
     for (size_t f = 0; f < c->fluids.size(); ++f) {
         const int sid = rd.to_species[f];
         if (sid < 0 || sid >= (int)c->sp.size()) continue;
         const SpDev &dst = c->sp[sid].dev;
-        cudaMemsetAsync(dst.mig_count, 0, sizeof(int), st);
+        // the tiles are compact between steps: new particles go straight into them
         k_fluid_to_particles<<<nblk(g.N), 256, 0, st>>>(g, mask, c->fluids[f], dst, rd.ppc > 0 ? rd.ppc : 8,
                                                         c->epoch, c->rho_bg, c->status);
-        launch_rebin(g, dst, c->status, st);
-        launch_compact(g, dst, st);
+        k_clamp_counts<<<(g.ntiles + 255) / 256, 256, 0, st>>>(g.ntiles, dst);
         k_mom_init<<<nblk(g.N), 256, 0, st>>>(g.N, c->fluids[f]);
         k_particles_to_fluid<<<g.ntiles, 256, 0, st>>>(g, mask, dst, c->fluids[f]);
         k_mom_final<<<nblk(g.N), 256, 0, st>>>(g.N, c->fluids[f]);
         launch_compact(g, dst, st);
+        launches += 6;
+    }
+    c->launches_classify += launches;
+    // after an all-kinetic classification that converted every fluid the
+    // fluids hold no density and the step leaves their update out (a full-PIC
+    // run); any other classification brings it back
+    bool idle = all;
+    for (size_t f = 0; f < c->fluids.size(); ++f)
+        if (rd.to_species[f] < 0 || rd.to_species[f] >= (int)c->sp.size()) idle = false;
+    if (idle != c->fluids_idle) {
+        c->fluids_idle = idle;
+        c->graph_valid = false;
     }
     c->epoch += 1;
     cudaError_t e = cudaGetLastError();

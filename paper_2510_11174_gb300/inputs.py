@@ -6,6 +6,12 @@ identical values).  The workloads follow the paper's setting (Methodology:
 uniform Cartesian grid, macro-particles per cell weighted by density-volume
 fraction, Gaussian laser) at the sizes of the benchmark configurations:
 
+* ``ramp_slab`` -- the hybrid workload: pre-ionised hydrogen as cold electron
+  and proton fluids on a linear underdense ramp (n_lo -> n_hi n_c over the
+  first half of the box along x, after a vacuum gap) followed by an
+  overdense slab, absorbing (Mur) faces, and a Gaussian pulse launched from
+  the x_min side with a0 drawn log-uniformly from [10, 300]; the kinetic
+  cells receive `ppc` macro-particles per species when they are classified.
 * ``periodic_plasma`` -- pre-ionised hydrogen (e-, p+) at uniform density,
   `ppc` particles per cell per species at uniform random positions, Maxwellian
   momenta of temperature `T_keV` (non-relativistic Gaussian per component,
@@ -71,3 +77,38 @@ def periodic_plasma(n=32, ppc=8, density=0.1, temperature_keV=1.0, a0=1.0, cells
     E, B = plane_wave_fields(n, ny, nz, dx, a0, modes=max(1, round(n / cells_per_lambda)))
     return dict(grid=dict(nx=n, ny=ny, nz=nz, dx=dx, cfl_frac=0.95, bc=(0, 0, 0)),
                 species=[dict(q=-1.0, m=1.0, **ele), dict(q=1.0, m=M_P, **ion)], E=E, B=B)
+
+
+OMEGA0_PER_FS = 2.0 * math.pi * 299792458.0 / 0.8e-6 * 1e-15   # w0 [1/fs] at 0.8 um
+
+
+def ramp_slab(nx=256, ny=256, nz=128, cells_per_lambda=16, n_lo=0.01, n_hi=1.0, n_slab=5.0,
+              slab_lambda=2.0, vacuum_lambda=1.0, a0=None, tau_fs=30.0, w0_lambda=2.0, seed=3, ppc=8,
+              tile_capacity=6144):
+    """The hybrid workload (defaults: 256 x 256 x 128, lambda/16).  Node
+    densities n(x): 0 in the first `vacuum_lambda`, linear n_lo -> n_hi up to
+    nx/2, n_slab over the next `slab_lambda`, 0 beyond; uniform in y and z.
+    Fluids are at rest.  Returns grid, laser, fluids (electron, proton) and
+    two empty particle species that receive the conversions."""
+    dx = 2.0 * math.pi / cells_per_lambda
+    rng = np.random.default_rng(seed)
+    if a0 is None:
+        a0 = float(np.exp(rng.uniform(math.log(10.0), math.log(300.0))))
+    i = np.arange(nx, dtype=np.float64)
+    x0 = int(round(vacuum_lambda * cells_per_lambda))
+    x1 = nx // 2
+    x2 = x1 + int(round(slab_lambda * cells_per_lambda))
+    prof = np.zeros(nx)
+    ramp = (i >= x0) & (i < x1)
+    prof[ramp] = n_lo + (n_hi - n_lo) * (i[ramp] - x0) / max(1, x1 - 1 - x0)
+    prof[(i >= x1) & (i < x2)] = n_slab
+    n = np.broadcast_to(prof.astype(np.float32)[None, None, :], (nz, ny, nx)).copy()
+    tau = tau_fs * OMEGA0_PER_FS
+    laser = dict(a0=a0, tau_fwhm=tau, w0_spot=w0_lambda * 2.0 * math.pi, t_peak=1.5 * tau,
+                 y_c=0.5 * (ny - 1), z_c=0.5 * (nz - 1), x_src=max(2, x0 // 2), pol=1)
+    empty = np.zeros(0, np.float32)
+    sp = lambda q, m: dict(q=q, m=m, x=empty, y=empty, z=empty, ux=empty, uy=empty, uz=empty, w=empty,
+                           tile_capacity=tile_capacity)
+    return dict(grid=dict(nx=nx, ny=ny, nz=nz, dx=dx, cfl_frac=0.95, bc=(1, 1, 1)), laser=laser,
+                fluids=[dict(q=-1.0, m=1.0, n=n), dict(q=1.0, m=M_P, n=n)],
+                species=[sp(-1.0, 1.0), sp(1.0, M_P)], ppc=ppc, a0=a0)

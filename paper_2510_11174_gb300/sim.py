@@ -183,9 +183,16 @@ class Simulation:
         check(self._lib.hyb_load_fluid(self._ctx, C.byref(d), C.byref(fid)))
         return fid.value
 
+    POLICIES = {"default": _abi.HYB_REGIME_DEFAULT, "union": _abi.HYB_REGIME_UNION,
+                "all_kinetic": _abi.HYB_REGIME_ALL_KINETIC}
+
     def set_regime(self, a_thr=1.0, n_thr=1.0, c_thr=0.1, chi_thr=1e-3, dilate=2, k_sigma=1.0, ppc=8,
-                   to_species=None):
+                   to_species=None, policy="default"):
+        """Thresholds and conversion targets of hyb_classify; policy is
+        "default" (classifier if given, else physics criterion), "union"
+        (classifier or criterion) or "all_kinetic" (full PIC)."""
         d = _abi.hyb_regime_desc()
+        d.policy = self.POLICIES[policy]
         d.a_thr, d.n_thr, d.c_thr, d.chi_thr = a_thr, n_thr, c_thr, chi_thr
         d.dilate, d.k_sigma, d.ppc = dilate, k_sigma, ppc
         ts = list(to_species or [])
@@ -249,7 +256,8 @@ class Simulation:
                 "w_photon_untracked": out.w_photon_untracked, "w_pair_deficit": out.w_pair_deficit,
                 "n_emit": out.n_emit, "n_pair": out.n_pair,
                 "w_fluid": [out.w_fluid[i] for i in range(out.n_fluids)],
-                "n_fluid": [out.n_fluid[i] for i in range(out.n_fluids)], "n_clamped": out.n_clamped}
+                "n_fluid": [out.n_fluid[i] for i in range(out.n_fluids)], "n_clamped": out.n_clamped,
+                "launches_classify": out.launches_classify}
 
     def eval_qed(self, what, chi, r=None):
         """Evaluate the device QED tables (see hyb_eval_qed)."""

@@ -1,0 +1,119 @@
+"""The whole hybrid step on the GPU against the oracle: a small ramp + slab
+box with a Gaussian pulse, cold electron and proton fluids, the classifier
+(MC dropout) united with the physics criterion, conversions every 10 steps;
+and the hybrid's field error against the full-PIC run of the same state."""
+import numpy as np
+import pytest
+
+from _util import by_id, rel_l2, require_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+def _workload(nx=32, ny=16, nz=16, **kw):
+    from paper_2510_11174_gb300 import inputs
+    inp = inputs.ramp_slab(nx=nx, ny=ny, nz=nz, vacuum_lambda=0.25, slab_lambda=0.5, a0=kw.pop("a0", 8.0),
+                           tile_capacity=4096, **kw)
+    inp["laser"]["t_peak"] = 6.0
+    inp["laser"]["tau_fwhm"] = 6.0
+    inp["laser"]["w0_spot"] = 6.0
+    return inp
+
+
+def _gpu(P, inp, policy, model=None):
+    g = inp["grid"]
+    sim = P.Simulation(g["nx"], g["ny"], g["nz"], g["dx"], cfl_frac=g["cfl_frac"], bc=g["bc"], laser=inp["laser"])
+    for sp in inp["species"]:
+        sim.load_species(**sp)
+    for fl in inp["fluids"]:
+        sim.load_fluid(**fl)
+    sim.set_regime(dilate=1, ppc=inp["ppc"], to_species=[0, 1], policy=policy)
+    return sim
+
+
+def test_hybrid_step_matches_oracle():
+    P = require_gpu()
+    import oracle.sim as S
+    from oracle.classifier import OracleCNN
+    from paper_2510_11174_gb300.model import Classifier
+    inp = _workload(ppc=2)
+    g = inp["grid"]
+    model = Classifier(dropout=0.2, mc_passes=4, seed=9)
+    w, b = model.get_layer(3)
+    model.set_layer(3, w, np.full_like(b, -2.0))
+    net = OracleCNN([model.get_layer(l) for l in range(4)], dropout=0.2, seed=9)
+    sim = _gpu(P, inp, "union")
+    orc = S.OracleSim(g["nx"], g["ny"], g["nz"], g["dx"], cfl_frac=g["cfl_frac"], bc=g["bc"], laser=inp["laser"])
+    for sp in inp["species"]:
+        orc.load_species(**sp)
+    for fl in inp["fluids"]:
+        orc.load_fluid(**fl, n_floor=0.0)
+    orc.set_regime(dilate=1, ppc=inp["ppc"], to_species=[0, 1], policy="union")
+    for cycle in range(3):
+        sim.classify(model)
+        mask, rho_bg = sim.get_regime()
+        # the oracle's own decision on its own state (FP64 vs BF16 convolutions:
+        # only nodes within rounding of the threshold may differ) ...
+        om = _decide_only(orc, net, passes=4)
+        assert np.count_nonzero(om != mask) <= max(2, mask.size // 2000), (cycle, np.count_nonzero(om != mask))
+        # ... and the conversions with the GPU's mask
+        orc.classify(mask=mask)
+        assert 0.0 < mask.mean() < 1.0
+        assert np.max(np.abs(rho_bg - orc.rho_bg)) <= 1e-5 * 5.0
+        d = sim.diagnostics()
+        assert d["count"] == [orc.species[0].n, orc.species[1].n], cycle
+        sim.step(10)
+        orc.step(10)
+    E, B, _ = sim.get_fields()
+    assert rel_l2(E, orc.E) <= 1e-4, rel_l2(E, orc.E)
+    assert rel_l2(B, orc.B) <= 1e-4, rel_l2(B, orc.B)
+    for f in range(2):
+        assert rel_l2(sim.get_fluid(f)["n"], orc.fluids[f].n) <= 1e-4
+    for s in range(2):
+        gs = by_id(sim.get_species(s))
+        o = np.argsort(orc.species[s].ids)
+        assert np.array_equal(gs["ids"], orc.species[s].ids[o])
+        for k in ("ux", "uy", "uz"):
+            ref = getattr(orc.species[s], k)[o]
+            assert np.max(np.abs(gs[k] - ref)) <= 1e-4 * max(1.0, np.abs(ref).max()), (s, k)
+
+
+def _decide_only(orc, net, passes):
+    """The oracle's mask for its current state without converting anything."""
+    import oracle
+    from oracle.sim import dilate, node_fields
+    r, g = orc.regime, orc.g
+    ne = np.zeros(g.shape)
+    for sp, k in zip(orc.species, orc.kind):
+        if k == 0 and sp.q < 0 and sp.zq is None:
+            ne -= oracle.charge_density(g, sp) / (-sp.q)
+    fe = orc.fluids[0]
+    ne += fe.n
+    mask = oracle.regime_criterion(g, orc.E, orc.B, ne, fluid_u=fe.u, a_thr=r["a_thr"], n_thr=r["n_thr"],
+                                   c_thr=r["c_thr"], chi_thr=r["chi_thr"], dilate=r["dilate"])
+    pm, ps = net.mc_statistics(node_fields(g, orc.E, orc.B)[None], passes)
+    mask |= dilate(g, pm[0].numpy() + r["k_sigma"] * ps[0].numpy() >= 0.5, r["dilate"])
+    return mask
+
+
+def test_hybrid_field_error_against_full_pic():
+    """The full-PIC run (every node kinetic) judges the hybrid: same initial
+    state, same pulse; after 60 steps the hybrid's fields stay within 1e-3
+    relative L2 of the full-PIC fields."""
+    P = require_gpu()
+    inp = _workload(nx=64, ny=32, nz=32, ppc=8, a0=4.0)
+    hyb = _gpu(P, inp, "default")
+    full = _gpu(P, inp, "all_kinetic")
+    hyb.classify()
+    full.classify()
+    frac = hyb.get_regime()[0].mean()
+    for k in range(6):
+        hyb.step(10)
+        full.step(10)
+        hyb.classify()
+    Eh, Bh, _ = hyb.get_fields()
+    Ef, Bf, _ = full.get_fields()
+    err = rel_l2(np.concatenate([Eh.ravel(), Bh.ravel()]), np.concatenate([Ef.ravel(), Bf.ravel()]))
+    print("kinetic fraction %.3f -> %.3f, field rel-L2 vs full PIC %.3e" % (frac, hyb.get_regime()[0].mean(), err))
+    assert 0.0 < frac < 1.0
+    assert err <= 1e-3, err

@@ -102,3 +102,62 @@ def test_hybrid_steps_after_classification_keep_gauss_law():
         sim.step(5)
         sim.classify()
     assert np.max(np.abs(gauss() - r0)) <= 2e-5 * np.max(np.abs(fl["n"]))
+
+
+def _mask_with(policy, model_seed=None, seed=3):
+    from paper_2510_11174_gb300.model import Classifier
+    inp, fl = _setup(seed=seed)
+    sim, _ = make_pair(inp, with_oracle=False)
+    sim.load_fluid(**fl)
+    sim.set_regime(dilate=1, ppc=2, to_species=[0], policy=policy)
+    model = None
+    if model_seed is not None:
+        model = Classifier(dropout=0.2, mc_passes=4, seed=model_seed)
+        w, b = model.get_layer(3)
+        model.set_layer(3, w, np.full_like(b, -1.0))
+    sim.classify(model)
+    mask, _ = sim.get_regime()
+    return mask
+
+
+def test_union_policy_is_the_union_of_classifier_and_criterion():
+    # dilation commutes with the union, so the three masks of the same state obey
+    # union = criterion | classifier exactly
+    phys = _mask_with("default")
+    cls = _mask_with("default", model_seed=5)
+    uni = _mask_with("union", model_seed=5)
+    assert 0 < cls.mean() < 1 and 0 < phys.mean() < 1
+    assert np.array_equal(uni, phys | cls)
+
+
+def test_all_kinetic_policy_converts_every_fluid_node_and_drops_the_fluid_phase():
+    inp, fl = _setup(seed=4)
+    sim, _ = make_pair(inp, with_oracle=False)
+    sim.load_fluid(**fl)
+    sim.step(1)
+    launches_hybrid = sim.diagnostics()["launches_per_step"]
+    n0 = sim.diagnostics()["count"][0]
+    sim.set_regime(dilate=0, ppc=3, to_species=[0], policy="all_kinetic")
+    g = oracle.Grid.make(NX, NY, NZ, DX, DX, DX, 0.1)
+    sp0 = sim.get_species(0)
+    E0, _, _ = sim.get_fields()
+    fl0 = sim.get_fluid(0)["n"]
+    before = _gauss(g, E0, [oracle.Particles(-1, 1, sp0["x"], sp0["y"], sp0["z"], sp0["ux"], sp0["uy"], sp0["uz"],
+                                             sp0["w"])], [(-1.0, fl0)], np.zeros(g.shape))
+    sim.classify()
+    mask, rho_bg = sim.get_regime()
+    assert mask.all()
+    assert np.all(sim.get_fluid(0)["n"] == 0.0)
+    d = sim.diagnostics()
+    assert d["count"][0] == n0 + 3 * np.count_nonzero(fl0 > 0)
+    sp1 = sim.get_species(0)
+    after = _gauss(g, E0, [oracle.Particles(-1, 1, sp1["x"], sp1["y"], sp1["z"], sp1["ux"], sp1["uy"], sp1["uz"],
+                                            sp1["w"])], [(-1.0, sim.get_fluid(0)["n"])], rho_bg)
+    assert np.max(np.abs(after - before)) <= 1e-5 * np.max(np.abs(fl["n"]))
+    sim.step(2)
+    d = sim.diagnostics()
+    assert d["status"] == 0
+    assert d["launches_per_step"] == launches_hybrid - 2
+    # every node still holds particles of its own dual cell only: ids unique
+    ids = sim.get_species(0)["ids"]
+    assert len(np.unique(ids)) == len(ids)

@@ -102,3 +102,69 @@ def test_particles_to_fluid_keeps_node_charge_number_momentum():
     mom1 = np.array([(sp.w * sp.ux).sum(), (sp.w * sp.uy).sum(), (sp.w * sp.uz).sum()]) + \
         (fl.n * fl.u).sum(axis=(1, 2, 3)) * dV
     assert np.allclose(mom1, mom0, rtol=1e-12, atol=1e-15)
+
+
+@pytest.mark.parametrize("bc", [(0, 0, 0), (1, 0, 1)])
+def test_dilate_matches_brute_force(bc):
+    from oracle.sim import dilate
+    g = oracle.Grid.make(9, 7, 5, 0.3, 0.3, 0.3, 0.15, bc=bc)
+    raw = (np.random.default_rng(1).random(g.shape) > 0.93).astype(np.uint8)
+    r = 2
+    ref = np.zeros_like(raw)
+    nz, ny, nx = g.shape
+    for k in range(nz):
+        for j in range(ny):
+            for i in range(nx):
+                hit = 0
+                for dk in range(-r, r + 1):
+                    for dj in range(-r, r + 1):
+                        for di in range(-r, r + 1):
+                            q = [i + di, j + dj, k + dk]
+                            n = [nx, ny, nz]
+                            ok = True
+                            for a in range(3):
+                                if bc[a] == 0:
+                                    q[a] %= n[a]
+                                elif not 0 <= q[a] < n[a]:
+                                    ok = False
+                            if ok and raw[q[2], q[1], q[0]]:
+                                hit = 1
+                ref[k, j, i] = hit
+    assert np.array_equal(dilate(g, raw, r), ref)
+
+
+def test_node_fields_of_linear_fields_are_exact():
+    # E_a sampled at its edge positions (i + 1/2 along a) and B_a at its face
+    # centres (half-integer along the two other axes): averaging a linear
+    # function over symmetric neighbours returns its value at the node
+    from oracle.sim import node_fields
+    g = oracle.Grid.make(8, 6, 5, 0.3, 0.3, 0.3, 0.15, bc=(1, 1, 1))
+    nz, ny, nx = g.shape
+    k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    lin = lambda x, y, z, c: c + 0.3 * x - 0.2 * y + 0.7 * z
+    E = np.stack([lin(i + 0.5, j, k, 1.0), lin(i, j + 0.5, k, 2.0), lin(i, j, k + 0.5, 3.0)])
+    B = np.stack([lin(i, j + 0.5, k + 0.5, 4.0), lin(i + 0.5, j, k + 0.5, 5.0), lin(i + 0.5, j + 0.5, k, 6.0)])
+    f = node_fields(g, E, B)
+    inner = (slice(1, None), slice(1, None), slice(1, None))
+    for c in range(6):
+        assert np.allclose(f[c][inner], lin(i, j, k, c + 1.0)[inner], atol=1e-12), c
+    # at the lower faces of non-periodic axes the missing neighbour counts as zero
+    assert np.allclose(f[0][:, :, 0], 0.5 * E[0][:, :, 0])
+
+
+def test_oracle_all_kinetic_classification():
+    from oracle.sim import OracleSim
+    o = OracleSim(8, 8, 8, 0.3, bc=(1, 1, 1))
+    o.load_species(-1.0, 1.0, *[np.zeros(0, np.float32)] * 7)
+    n = np.full((8, 8, 8), 0.2)
+    n[:, :, :2] = 0.0
+    o.load_fluid(-1.0, 1.0, n, n_floor=0.0)
+    o.set_regime(ppc=3, to_species=[0], policy="all_kinetic", dilate=0)
+    rho0 = -n.copy()
+    o.classify()
+    assert o.mask.all()
+    assert o.species[0].n == 3 * np.count_nonzero(n > 0)
+    assert np.all(o.fluids[0].n == 0.0)
+    rho = oracle.charge_density(o.g, o.species[0]) + o.rho_bg
+    assert np.max(np.abs(rho - rho0)) <= 1e-12
+    assert math.isclose(float(np.sum(o.species[0].w)), float(np.sum(n)) * 0.3 ** 3, rel_tol=1e-12)
