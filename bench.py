@@ -260,8 +260,7 @@ def run_ours(args, rank, world):
     probe = sim.diagnostics()
     flush_l2 = state_bytes(probe, cells) < 2 * L2_BYTES
     clocks = ClockSampler(dev)
-    total_ms, ncls, before, after = timed_run(torch, sim, model, args.steps, args.warmup, stream.cuda_stream,
-                                              barrier, flush_l2)
+    total_ms, ncls, before, after = timed_run(torch, sim, model, args.steps, args.warmup, stream, barrier, flush_l2)
     clk = clocks.stop()
     total_ms = allmax(total_ms)
     parts = 0.5 * (sum(before["count"]) + sum(after["count"]))
@@ -310,7 +309,7 @@ def run_ours(args, rank, world):
     full = None
     if kind == "hybrid" and not args.no_full_pic:
         fsim, _ = make_sim(P, inp, stream.cuda_stream, policy="all_kinetic")
-        fms, _, fb, fa = timed_run(torch, fsim, None, args.steps, args.warmup, stream.cuda_stream, barrier, False)
+        fms, _, fb, fa = timed_run(torch, fsim, None, args.steps, args.warmup, stream, barrier, False)
         fms = allmax(fms)
         fparts = 0.5 * (sum(fb["count"]) + sum(fa["count"]))
         fsim.close()
@@ -424,7 +423,7 @@ def oracle_sample(workload):
     for sp in inp["species"]:
         o.load_species(**sp)
     for fl in inp.get("fluids", []):
-        o.load_fluid(**fl, n_floor=0.0)
+        o.load_fluid(**fl)
     if "E" in inp:
         o.set_fields(inp["E"], inp["B"])
     net = None

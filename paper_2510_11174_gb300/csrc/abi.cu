@@ -611,13 +611,13 @@ hyb_status hyb_classify(hyb_ctx *c, const hyb_model *model, float *p_mean_dev, f
         if (c->profiling) cudaEventRecord(e, c->stream);
     };
     if (model) {
-        c->phase_ran[HYB_PH_CLASSIFY] = true;
+        c->phase_ran[HYB_PH_CLASSIFY] = c->profiling;
         mark(c->ev_start[HYB_PH_CLASSIFY]);
         s = classifier_forward(c, model, p_mean_dev, p_std_dev);
         mark(c->ev_end[HYB_PH_CLASSIFY]);
         if (s != HYB_OK) return s;
     }
-    c->phase_ran[HYB_PH_REGIME] = true;
+    c->phase_ran[HYB_PH_REGIME] = c->profiling;
     mark(c->ev_start[HYB_PH_REGIME]);
     s = model ? regime_update(c, model_p_mean(model), model_p_std(model)) : regime_update(c, nullptr, nullptr);
     mark(c->ev_end[HYB_PH_REGIME]);
@@ -695,6 +695,7 @@ hyb_status hyb_set_profiling(hyb_ctx *c, int on) {
     if ((bool)on != c->profiling) {
         c->profiling = on != 0;
         c->graph_valid = false;
+        for (int p = 0; p < HYB_NPHASE; ++p) c->phase_ran[p] = false;
     }
     return HYB_OK;
 }

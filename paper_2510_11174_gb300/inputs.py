@@ -84,12 +84,15 @@ OMEGA0_PER_FS = 2.0 * math.pi * 299792458.0 / 0.8e-6 * 1e-15   # w0 [1/fs] at 0.
 
 def ramp_slab(nx=256, ny=256, nz=128, cells_per_lambda=16, n_lo=0.01, n_hi=1.0, n_slab=5.0,
               slab_lambda=2.0, vacuum_lambda=1.0, a0=None, tau_fs=30.0, w0_lambda=2.0, seed=3, ppc=8,
-              tile_capacity=6144):
+              tile_capacity=6144, n_floor=1e-10):
     """The hybrid workload (defaults: 256 x 256 x 128, lambda/16).  Node
     densities n(x): 0 in the first `vacuum_lambda`, linear n_lo -> n_hi up to
     nx/2, n_slab over the next `slab_lambda`, 0 beyond; uniform in y and z.
-    Fluids are at rest.  Returns grid, laser, fluids (electron, proton) and
-    two empty particle species that receive the conversions."""
+    Fluids are at rest; densities below n_floor [n_c] count as vacuum (the
+    donor-cell scheme spreads trace densities one node per step, which
+    conversions must not turn into particles).  Returns grid, laser, fluids
+    (electron, proton) and two empty particle species that receive the
+    conversions."""
     dx = 2.0 * math.pi / cells_per_lambda
     rng = np.random.default_rng(seed)
     if a0 is None:
@@ -110,5 +113,5 @@ def ramp_slab(nx=256, ny=256, nz=128, cells_per_lambda=16, n_lo=0.01, n_hi=1.0, 
     sp = lambda q, m: dict(q=q, m=m, x=empty, y=empty, z=empty, ux=empty, uy=empty, uz=empty, w=empty,
                            tile_capacity=tile_capacity)
     return dict(grid=dict(nx=nx, ny=ny, nz=nz, dx=dx, cfl_frac=0.95, bc=(1, 1, 1)), laser=laser,
-                fluids=[dict(q=-1.0, m=1.0, n=n), dict(q=1.0, m=M_P, n=n)],
+                fluids=[dict(q=-1.0, m=1.0, n=n, n_floor=n_floor), dict(q=1.0, m=M_P, n=n, n_floor=n_floor)],
                 species=[sp(-1.0, 1.0), sp(1.0, M_P)], ppc=ppc, a0=a0)

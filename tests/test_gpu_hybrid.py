@@ -11,9 +11,10 @@ pytestmark = pytest.mark.gpu
 
 
 def _workload(nx=32, ny=16, nz=16, **kw):
+    # tiles hold 4x the initial 8 ppc: the pulse piles electrons up at the slab
     from paper_2510_11174_gb300 import inputs
     inp = inputs.ramp_slab(nx=nx, ny=ny, nz=nz, vacuum_lambda=0.25, slab_lambda=0.5, a0=kw.pop("a0", 8.0),
-                           tile_capacity=4096, **kw)
+                           tile_capacity=16384, **kw)
     inp["laser"]["t_peak"] = 6.0
     inp["laser"]["tau_fwhm"] = 6.0
     inp["laser"]["w0_spot"] = 6.0
@@ -47,7 +48,7 @@ def test_hybrid_step_matches_oracle():
     for sp in inp["species"]:
         orc.load_species(**sp)
     for fl in inp["fluids"]:
-        orc.load_fluid(**fl, n_floor=0.0)
+        orc.load_fluid(**fl)
     orc.set_regime(dilate=1, ppc=inp["ppc"], to_species=[0, 1], policy="union")
     for cycle in range(3):
         sim.classify(model)
@@ -106,6 +107,7 @@ def test_hybrid_field_error_against_full_pic():
     full = _gpu(P, inp, "all_kinetic")
     hyb.classify()
     full.classify()
+    assert hyb.diagnostics()["status"] == 0 and full.diagnostics()["status"] == 0
     frac = hyb.get_regime()[0].mean()
     for k in range(6):
         hyb.step(10)
