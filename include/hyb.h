@@ -241,7 +241,9 @@ hyb_status hyb_classify(hyb_ctx *ctx, const hyb_model *model, float *p_mean_dev,
  * normalised per channel as (x - mean_c) / std_c.  Weights are kept in FP32
  * (Adam master copy) and used in BF16 with FP32 accumulation; activations
  * between layers are BF16.  Dropout masks come from Philox (key (seed,
- * 0xD0), counter (cell, batch, layer << 16 | channel / 4, pass)).
+ * 0xD0), counter (cell, batch, layer << 16 | channel / 8, pass)): channel c
+ * is kept when 16-bit field c % 8 of the output (word (c % 8) / 2, low half
+ * for even c) is >= round(p 2^16); p is used as round(p 2^16) / 2^16.
  */
 typedef struct {
     double dropout;            /* p (e.g. 0.2) */

@@ -32,7 +32,8 @@ class OracleCNN:
         """weights: list of (W [co][ci][3][3][3], b [co]) FP32 arrays."""
         self.W = [torch.from_numpy(np.asarray(w, dtype=np.float32)).to(torch.float64) for w, _ in weights]
         self.b = [torch.from_numpy(np.asarray(b, dtype=np.float32)).to(torch.float64) for _, b in weights]
-        self.p = float(dropout)
+        # p as the mask realises it: round(p 2^16) / 2^16
+        self.p = round(float(dropout) * 65536.0) / 65536.0
         self.seed = int(seed)
         self.mean = torch.tensor(np.zeros(6) if mean is None else np.asarray(mean, np.float32), dtype=torch.float32)
         self.std = torch.tensor(np.ones(6) if std is None else np.asarray(std, np.float32), dtype=torch.float32)

@@ -79,10 +79,11 @@ static void enqueue_step(hyb_ctx *c) {
     cudaMemsetAsync(c->mig_counts, 0, sizeof(int) * HYB_MAX_SPECIES, st);
     if (set.n > 0) {
         pm.begin(HYB_PH_PUSH);
-        launch_push_deposit(g, c->E, c->B, c->sp_dev, set.n, c->qed, c->jscratch, c->status, c->step_dev, st);
+        launch_push_deposit(g, c->E, c->B, c->sp_dev, set.n, c->qed, c->jscratch, c->jvalid, c->status, c->step_dev,
+                            st);
         pm.end(HYB_PH_PUSH);
         pm.begin(HYB_PH_JREDUCE);
-        launch_j_reduce(g, c->jscratch, c->J, st);
+        launch_j_reduce(g, c->jscratch, c->jvalid, c->J, st);
         pm.end(HYB_PH_JREDUCE);
     } else {
         cudaMemsetAsync(c->J, 0, sizeof(float) * 3 * g.N, st);
@@ -209,6 +210,7 @@ hyb_status hyb_init_grid(const hyb_grid_desc *d, hyb_ctx **out) {
         ctx_alloc(c, (void **)&c->J, fbytes) ||
         ctx_alloc(c, (void **)&c->mur_old, sizeof(float) * 24 * (size_t)c->mur_plane) ||
         ctx_alloc(c, (void **)&c->jscratch, sizeof(float) * (size_t)c->jframe * g.ntiles) ||
+        ctx_alloc(c, (void **)&c->jvalid, sizeof(int) * (size_t)g.ntiles) ||
         ctx_alloc(c, (void **)&c->red_partials, sizeof(double) * (2 + HYB_MAX_SPECIES + 2 * HYB_MAX_FLUIDS) * c->red_blocks) ||
         ctx_alloc(c, (void **)&c->red_out, sizeof(double) * (2 + HYB_MAX_SPECIES + 2 * HYB_MAX_FLUIDS)) ||
         ctx_alloc(c, (void **)&c->status, sizeof(int)) || ctx_alloc(c, (void **)&c->step_dev, sizeof(long long)) ||

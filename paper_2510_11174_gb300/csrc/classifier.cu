@@ -33,10 +33,13 @@ struct hyb_model {
     __nv_bfloat16 *wt[3] = {};           // packed forward weights, layers 0..2
     __nv_bfloat16 *wtT[3] = {};          // packed transposed + flipped (data gradient)
     float *w4r = nullptr;                // layer 3 weights rounded to BF16 (as FP32), [16][27]
+    float w4h[27 * 16] = {};             // host copy of w4r as [tap][ci] (kernel parameter of the last layer)
+    float b4h = 0.0f;
     float *mean = nullptr, *std_ = nullptr;
     // activation buffers (capacity in cells)
     long long cap = 0;
     __nv_bfloat16 *x0 = nullptr, *a1 = nullptr, *a2 = nullptr, *a3 = nullptr;
+    float *h0 = nullptr;                 // layer-0 output before dropout (FP32), shared by the MC passes
     float *logit = nullptr, *pm = nullptr, *ps = nullptr;
     int *status = nullptr;
     long long adam_t = 0;
@@ -133,46 +136,120 @@ __global__ void k_prep_fields(GridDev g, const float *__restrict__ E, const floa
 }
 
 // the 16 -> 1 layer on CUDA cores: logit = b + sum_tap sum_ci W[ci][tap] a3[cell + tap - 1][ci]
-__global__ void k_conv_last(const __nv_bfloat16 *__restrict__ a3, int B, int D, int H, int W,
-                            const float *__restrict__ w4r, const float *__restrict__ b4, float *__restrict__ logit) {
-    __shared__ float ws[16 * 27];
-    for (int i = threadIdx.x; i < 16 * 27; i += blockDim.x) ws[i] = w4r[i];
-    __syncthreads();
+// the 16 -> 1 layer on CUDA cores: logit = b + sum_tap sum_ci W[ci][tap] a3[cell + tap - 1][ci].
+// Weights travel as a kernel parameter (constant bank, used directly by the
+// FMAs).  A block of 128 threads owns 8 (x) x 16 (y) x 4 (z) cells; the BF16
+// input halo (10 x 18 x 6 cells x 16 channels) is staged in shared memory by
+// asynchronous copies (zero outside the volume) and each thread sums the taps
+// of its 4-cell column.  mc_k = 0 writes the logit; mc_k = k >= 1 folds
+// sigmoid(logit) into the running mean / M2 of the MC passes instead (k = 1
+// starts them).
+struct LastW {
+    float w[27 * 16];  // [tap][ci]
+    float b;
+};
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, bool in) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(in ? 16 : 0) : "memory");
+}
+
+__global__ void __launch_bounds__(128) k_conv_last(const __grid_constant__ LastW lw,
+                                                   const __nv_bfloat16 *__restrict__ a3, int B, int D, int H, int W,
+                                                   float *__restrict__ logit, int mc_k, float *__restrict__ pm,
+                                                   float *__restrict__ m2) {
+    __shared__ __align__(16) uint4 halo[6 * 18 * 10 * 2];  // [z][y][x][2 x 8 channels]
+    const int tiles_x = W / 8, tiles_y = H / 16, tiles_z = (D + 3) / 4;
+    const long long tile = blockIdx.x;
+    const int tx = (int)(tile % tiles_x), ty = (int)((tile / tiles_x) % tiles_y);
+    const int tz = (int)((tile / ((long long)tiles_x * tiles_y)) % tiles_z);
+    const int b = (int)(tile / ((long long)tiles_x * tiles_y * tiles_z));
+    const int x0 = tx * 8, y0 = ty * 16, z0 = tz * 4;
     const long long V = (long long)D * H * W;
-    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (t >= (long long)B * V) return;
-    const long long b = t / V, v = t % V;
-    const int x = (int)(v % W), y = (int)((v / W) % H), z = (int)(v / ((long long)W * H));
-    float acc = b4[0];
-    for (int tap = 0; tap < 27; ++tap) {
-        const int zz = z + tap / 9 - 1, yy = y + (tap / 3) % 3 - 1, xx = x + tap % 3 - 1;
-        if (zz < 0 || zz >= D || yy < 0 || yy >= H || xx < 0 || xx >= W) continue;
-        const __nv_bfloat16 *src = a3 + ((b * V) + ((long long)zz * H + yy) * W + xx) * 16;
-        __align__(16) __nv_bfloat16 h[16];
-        reinterpret_cast<uint4 *>(h)[0] = reinterpret_cast<const uint4 *>(src)[0];
-        reinterpret_cast<uint4 *>(h)[1] = reinterpret_cast<const uint4 *>(src)[1];
+    const __nv_bfloat16 *src = a3 + (long long)b * V * 16;
+    for (int i = threadIdx.x; i < 6 * 18 * 10 * 2; i += 128) {
+        const int h = i & 1, c = i >> 1;
+        const int lx = c % 10, ly = (c / 10) % 18, lz = c / 180;
+        const int gx = x0 - 1 + lx, gy = y0 - 1 + ly, gz = z0 - 1 + lz;
+        const bool in = gx >= 0 && gx < W && gy >= 0 && gy < H && gz >= 0 && gz < D;
+        const __nv_bfloat16 *p = in ? src + (((long long)gz * H + gy) * W + gx) * 16 + h * 8 : src;
+        cp_async16((uint32_t)__cvta_generic_to_shared(&halo[i]), p, in);
+    }
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+    __syncthreads();
+    const int lx = threadIdx.x & 7, ly = threadIdx.x >> 3;
+    float acc[4] = {lw.b, lw.b, lw.b, lw.b};
 #pragma unroll
-        for (int ci = 0; ci < 16; ++ci) acc += ws[ci * 27 + tap] * __bfloat162float(h[ci]);
+    for (int zi = 0; zi < 6; ++zi) {
+#pragma unroll
+        for (int dy = 0; dy < 3; ++dy) {
+#pragma unroll
+            for (int dx = 0; dx < 3; ++dx) {
+                const int cell = (zi * 18 + ly + dy) * 10 + lx + dx;
+                const uint4 v0 = halo[2 * cell], v1 = halo[2 * cell + 1];
+                const uint32_t u[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+                float f[16];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    f[2 * q] = __uint_as_float(u[q] << 16);
+                    f[2 * q + 1] = __uint_as_float(u[q] & 0xFFFF0000u);
+                }
+#pragma unroll
+                for (int o = 0; o < 4; ++o) {
+                    const int dz = zi - o;
+                    if (dz < 0 || dz > 2) continue;
+                    const int tap = (dz * 3 + dy) * 3 + dx;
+#pragma unroll
+                    for (int ci = 0; ci < 16; ++ci) acc[o] = fmaf(lw.w[tap * 16 + ci], f[ci], acc[o]);
+                }
+            }
+        }
     }
-    logit[t] = acc;
+#pragma unroll
+    for (int o = 0; o < 4; ++o) {
+        const int z = z0 + o;
+        if (z >= D) break;
+        const long long t = (long long)b * V + ((long long)z * H + y0 + ly) * W + x0 + lx;
+        if (mc_k == 0) {
+            logit[t] = acc[o];
+        } else {
+            const float p = 1.0f / (1.0f + expf(-acc[o]));
+            if (mc_k == 1) {
+                pm[t] = p;
+                m2[t] = 0.0f;
+            } else {
+                const float mo = pm[t];
+                const float d = p - mo;
+                const float mn = mo + d / (float)mc_k;
+                pm[t] = mn;
+                m2[t] += d * (p - mn);
+            }
+        }
+    }
 }
 
-// Welford update of the per-node mean / M2 of sigmoid(logit) for pass k (1-based)
-__global__ void k_mc_update(long long n, const float *__restrict__ logit, int k, float *__restrict__ pm,
-                            float *__restrict__ m2) {
+// a1 = bf16(h0 kept / (1 - p)) with the layer-0 dropout mask of `pass`
+// (the MC passes share layer 0 up to its dropout)
+__global__ void k_dropout_apply(const float *__restrict__ h0, long long cells, long long V, uint32_t seed,
+                                uint32_t pass, uint32_t thr, float scale, __nv_bfloat16 *__restrict__ a1) {
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (t >= n) return;
-    const float p = 1.0f / (1.0f + expf(-logit[t]));
-    if (k == 1) {
-        pm[t] = p;
-        m2[t] = 0.0f;
-        return;
+    if (t >= cells) return;
+    const uint32_t b = (uint32_t)(t / V), lin = (uint32_t)(t % V);
+    const float4 *src = reinterpret_cast<const float4 *>(h0 + t * 32);
+    uint4 *dst = reinterpret_cast<uint4 *>(a1 + t * 32);
+#pragma unroll
+    for (int g8 = 0; g8 < 4; ++g8) {
+        const u32x4 r = philox4x32_10(lin, b, (0u << 16) | (uint32_t)g8, pass, seed, 0xD0u);
+        const float4 lo = src[2 * g8], hi = src[2 * g8 + 1];
+        const float v[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+        __align__(16) __nv_bfloat16 o[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const uint32_t f = (r.v[j >> 1] >> (16 * (j & 1))) & 0xFFFFu;
+            o[j] = __float2bfloat16_rn(f >= thr ? v[j] * scale : 0.0f);
+        }
+        dst[g8] = *reinterpret_cast<const uint4 *>(o);
     }
-    const float d = p - pm[t];
-    pm[t] += d / (float)k;
-    m2[t] += d * (p - pm[t]);
 }
-
 __global__ void k_mc_final(long long n, int k, const float *m2, float *ps) {  // may run in place
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (t < n) ps[t] = sqrtf(fmaxf(m2[t], 0.0f) / (float)k);  // population standard deviation over the passes
@@ -190,6 +267,14 @@ hyb_status model_repack(hyb_model *m) {
     k_round_bf16<<<nb(16 * 27), 256, 0, m->stream>>>(m->w[3], m->w4r, 16 * 27);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return set_error(HYB_ECUDA, std::string("weight packing: ") + cudaGetErrorString(e));
+    // the last layer takes its weights as a kernel parameter: keep a host copy
+    float w4[16 * 27];
+    e = cudaMemcpyAsync(w4, m->w4r, sizeof(w4), cudaMemcpyDeviceToHost, m->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&m->b4h, m->b[3], sizeof(float), cudaMemcpyDeviceToHost, m->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+    if (e != cudaSuccess) return set_error(HYB_ECUDA, std::string("weight copy: ") + cudaGetErrorString(e));
+    for (int ci = 0; ci < 16; ++ci)
+        for (int tap = 0; tap < 27; ++tap) m->w4h[tap * 16 + ci] = w4[ci * 27 + tap];
     return HYB_OK;
 }
 
@@ -197,7 +282,7 @@ static hyb_status model_reserve(hyb_model *m, long long cells) {
     if (cells <= m->cap) return HYB_OK;
     // buffers are replaced only between stream-ordered uses
     cudaStreamSynchronize(m->stream);
-    void *bufs[7] = {m->x0, m->a1, m->a2, m->a3, m->logit, m->pm, m->ps};
+    void *bufs[8] = {m->x0, m->a1, m->a2, m->a3, m->logit, m->pm, m->ps, m->h0};
     for (void *p : bufs) {
         if (!p) continue;
         for (auto it = m->owned.begin(); it != m->owned.end(); ++it)
@@ -211,6 +296,7 @@ static hyb_status model_reserve(hyb_model *m, long long cells) {
         m_alloc(m, (void **)&m->a1, sizeof(__nv_bfloat16) * 32 * cells) ||
         m_alloc(m, (void **)&m->a2, sizeof(__nv_bfloat16) * 32 * cells) ||
         m_alloc(m, (void **)&m->a3, sizeof(__nv_bfloat16) * 16 * cells) ||
+        m_alloc(m, (void **)&m->h0, sizeof(float) * 32 * cells) ||
         m_alloc(m, (void **)&m->logit, sizeof(float) * cells) || m_alloc(m, (void **)&m->pm, sizeof(float) * cells) ||
         m_alloc(m, (void **)&m->ps, sizeof(float) * cells))
         return set_error(HYB_ENOMEM, "classifier activation buffers");
@@ -218,38 +304,66 @@ static hyb_status model_reserve(hyb_model *m, long long cells) {
     return HYB_OK;
 }
 
+// dropout p as the threshold on 16-bit Philox fields (p is used as
+// round(p 2^16) / 2^16) and the inverted-dropout scale of kept values
+static inline uint32_t dropout_threshold(double p) {
+    const long t = std::lround(p * 65536.0);
+    return (uint32_t)(t < 0 ? 0 : (t > 65535 ? 65535 : t));
+}
+static inline float dropout_scale(uint32_t thr) { return (float)(65536.0 / (65536.0 - (double)thr)); }
+
 // layers 0..3 on the prepared input m->x0 (B x D x H x W cells) -> m->logit
-static hyb_status model_run(hyb_model *m, int B, int D, int H, int W, int pass) {
-    const float p = pass >= 0 ? (float)m->d.dropout : 0.0f;
+static ConvArgs conv_args(hyb_model *m, int l, int B, int D, int H, int W, int pass) {
+    const uint32_t thr = pass >= 0 ? dropout_threshold(m->d.dropout) : 0u;
     __nv_bfloat16 *ins[3] = {m->x0, m->a1, m->a2}, *outs[3] = {m->a1, m->a2, m->a3};
-    for (int l = 0; l < 3; ++l) {
-        ConvArgs a;
-        a.x = ins[l];
-        a.wt = m->wt[l];
-        a.bias = m->b[l];
-        a.y = outs[l];
-        a.B = B;
-        a.D = D;
-        a.H = H;
-        a.W = W;
-        a.cin = CINP[l];
-        a.N = COUT[l];
-        a.relu = 1;
-        a.drop_p = p;
-        a.seed = m->d.seed;
-        a.pass = (uint32_t)(pass >= 0 ? pass : 0);
-        a.layer = (uint32_t)l;
-        a.status = m->status;
-        hyb_status s = launch_conv3_tc(a, m->stream);
+    ConvArgs a;
+    memset(&a, 0, sizeof(a));
+    a.x = ins[l];
+    a.wt = m->wt[l];
+    a.bias = m->b[l];
+    a.y = outs[l];
+    a.B = B;
+    a.D = D;
+    a.H = H;
+    a.W = W;
+    a.cin = CINP[l];
+    a.N = COUT[l];
+    a.relu = 1;
+    a.drop_thr = thr;
+    a.drop_scale = dropout_scale(thr);
+    a.seed = m->d.seed;
+    a.pass = (uint32_t)(pass >= 0 ? pass : 0);
+    a.layer = (uint32_t)l;
+    a.status = m->status;
+    return a;
+}
+
+static void launch_last(hyb_model *m, int B, int D, int H, int W, int mc_k) {
+    LastW lw;
+    memcpy(lw.w, m->w4h, sizeof(lw.w));
+    lw.b = m->b4h;
+    const long long tiles = (long long)B * ((D + 3) / 4) * (H / 16) * (W / 8);
+    k_conv_last<<<(unsigned)tiles, 128, 0, m->stream>>>(lw, m->a3, B, D, H, W, m->logit, mc_k, m->pm, m->ps);
+}
+
+// layers first_layer..3 on m->x0 (or on m->a1 when first_layer = 1) for
+// B x D x H x W cells; mc_k = 0 writes m->logit, mc_k >= 1 folds the pass
+// into the MC statistics (see k_conv_last)
+static hyb_status model_run(hyb_model *m, int B, int D, int H, int W, int pass, int mc_k = 0, int first_layer = 0) {
+    for (int l = first_layer; l < 3; ++l) {
+        hyb_status s = launch_conv3_tc(conv_args(m, l, B, D, H, W, pass), m->stream);
         if (s != HYB_OK) return s;
     }
-    const long long cells = (long long)B * D * H * W;
-    k_conv_last<<<nb(cells), 256, 0, m->stream>>>(m->a3, B, D, H, W, m->w4r, m->b[3], m->logit);
+    launch_last(m, B, D, H, W, mc_k);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return set_error(HYB_ECUDA, std::string("classifier: ") + cudaGetErrorString(e));
     return HYB_OK;
 }
 
+// Classification of the context's fields: K = mc_passes MC-dropout passes.
+// Layer 0 is the same in every pass up to its dropout, so it runs once (FP32
+// output before dropout) and each pass applies its own layer-0 mask before
+// layers 1..3; the last layer folds each pass into the running mean and M2.
 hyb_status classifier_forward(hyb_ctx *c, const hyb_model *mc, float *p_mean_dev, float *p_std_dev) {
     hyb_model *m = const_cast<hyb_model *>(mc);
     const GridDev &g = c->g;
@@ -262,14 +376,30 @@ hyb_status classifier_forward(hyb_ctx *c, const hyb_model *mc, float *p_mean_dev
     m->stream = c->stream;
     k_prep_fields<<<nb(g.N), 256, 0, c->stream>>>(g, c->E, c->B, m->mean, m->std_, m->x0);
     const int K = m->d.mc_passes > 0 ? m->d.mc_passes : 1;
-    for (int k = 1; k <= K && s == HYB_OK; ++k) {
-        s = model_run(m, 1, D, H, W, K > 1 ? k - 1 : -1);
-        if (s == HYB_OK) k_mc_update<<<nb(g.N), 256, 0, c->stream>>>(g.N, m->logit, k, m->pm, m->ps);
+    const uint32_t thr = dropout_threshold(m->d.dropout);
+    long long launches = 1;
+    if (K > 1 && thr > 0) {
+        ConvArgs a0 = conv_args(m, 0, 1, D, H, W, -1);
+        a0.y = nullptr;
+        a0.y_f32 = m->h0;
+        s = launch_conv3_tc(a0, c->stream);
+        ++launches;
+        for (int k = 1; k <= K && s == HYB_OK; ++k) {
+            k_dropout_apply<<<nb(g.N), 256, 0, c->stream>>>(m->h0, g.N, g.N, m->d.seed, (uint32_t)(k - 1), thr,
+                                                            dropout_scale(thr), m->a1);
+            s = model_run(m, 1, D, H, W, k - 1, k, 1);
+            launches += 4;
+        }
+    } else {
+        for (int k = 1; k <= K && s == HYB_OK; ++k) {
+            s = model_run(m, 1, D, H, W, K > 1 ? k - 1 : -1, k, 0);
+            launches += 4;
+        }
     }
     if (s == HYB_OK) {
         // ps held M2; turn it into the standard deviation in place
         k_mc_final<<<nb(g.N), 256, 0, c->stream>>>(g.N, K, m->ps, m->ps);
-        c->launches_classify += 2 + 5LL * K;  // prep, K x (3 conv + last layer + MC update), final
+        c->launches_classify += launches + 1;
         if (p_mean_dev) cudaMemcpyAsync(p_mean_dev, m->pm, sizeof(float) * g.N, cudaMemcpyDeviceToDevice, c->stream);
         if (p_std_dev) cudaMemcpyAsync(p_std_dev, m->ps, sizeof(float) * g.N, cudaMemcpyDeviceToDevice, c->stream);
     }
@@ -298,6 +428,7 @@ hyb_status hyb_model_create(const hyb_model_desc *d, hyb_model **out) {
         if (!(d->std[c] > 0.0f)) return set_error(HYB_EINVAL, "normalisation std must be > 0");
     hyb_model *m = new hyb_model();
     m->d = *d;
+    m->d.dropout = dropout_threshold(d->dropout) / 65536.0;
     if (!(m->d.lr > 0)) m->d.lr = 1e-3;
     if (!(m->d.beta1 > 0)) m->d.beta1 = 0.9;
     if (!(m->d.beta2 > 0)) m->d.beta2 = 0.999;
@@ -697,7 +828,7 @@ hyb_status hyb_train_step(hyb_model *m, const float *x, const float *y, int B, i
     if (s != HYB_OK) return s;
     TrainBufs &t = *static_cast<TrainBufs *>(m->train);
     cudaStream_t st = m->stream;
-    const float p = (float)m->d.dropout, inv_keep = 1.0f / (1.0f - p);
+    const float inv_keep = dropout_scale(dropout_threshold(m->d.dropout));
     // forward, dropout masks of pass = the step index
     k_prep_patches_cl<<<nbl(cells), 256, 0, st>>>(x, B, V, m->mean, m->std_, m->x0);
     s = model_run(m, B, D, H, W, (int)(m->adam_t & 0x7fffffff));

@@ -3,22 +3,33 @@
 // Monte Carlo dropout for uncertainty; here the 3D CNN 6->32->32->16->1 with
 // BF16 weights and FP32 accumulation).
 //
-// k_conv3_tc: implicit GEMM on the 5th-generation tensor cores.  A CTA owns
-// an output tile of 128 cells = 8 (x) x 16 (y) x 1 (z).  It stages the input
-// halo (10 x 18 x 3 cells, channels in 8-wide chunks) and all 27 x C_in x
-// C_out weights in shared memory, and one thread issues, for each of the 27
-// taps and each 16-channel slice of the input, one tcgen05.mma of shape
-// M = 128 (cells) x N = C_out x K = 16 that accumulates into TMEM.  The
-// operand of tap (dz, dy, dx) is the halo shifted by that tap: with the
-// chunk-major halo layout [chunk][z][y][x][8 channels], the 8 cells of one
-// output row are 8 consecutive 16-byte rows (one core matrix) and the 16
-// rows of the tile are 160 bytes apart, so every tap is a plain matrix
-// descriptor (start shifted by the tap; leading byte offset = one chunk block,
-// stride byte offset = 160 B) -- no im2col copy.  The epilogue reads the
-// accumulator from TMEM (tcgen05.ld), adds the bias, applies ReLU and the
-// Philox dropout mask (inverted scaling 1/(1-p)), converts to BF16 and stores
-// channels-last.  Each CTA loops over tiles (persistent grid).
+// k_conv3_tc: implicit GEMM on the 5th-generation tensor cores, persistent
+// and warp-specialised.  A CTA owns output tiles of 128 cells = 8 (x) x 16
+// (y) x 1 (z), taken round-robin.  Its input halo (10 x 18 x 3 cells) is
+// fetched by TMA, one 8-channel chunk per copy, into a ring of STAGES
+// shared-memory buffers laid out [chunk][z][y][x][8 channels]; all
+// 27 x C_in x C_out weights stay resident in shared memory.
+//   warp 0      TMA producer: waits for a free stage, posts the expected bytes
+//               on the stage's "full" barrier and issues the chunk copies
+//               (zero fill outside the volume comes from the tensor map);
+//   warp 1      MMA issuer: per tile 27 taps x C_in/16 tcgen05.mma of shape
+//               M = 128 cells x N = C_out x K = 16 into one of two TMEM
+//               accumulators; commits free the stage and hand the
+//               accumulator to the epilogue;
+//   warps 2..5  epilogue: tcgen05.ld of the accumulator rows (warp w reads
+//               TMEM lanes 32 (w % 4) ..), bias, ReLU, Philox dropout with
+//               inverted scaling, BF16 channels-last stores.
+// The operand of tap (dz, dy, dx) is the halo shifted by that tap: the 8
+// cells of one output row are 8 consecutive 16-byte rows (one core matrix),
+// the 16 rows of the tile are 160 bytes apart, the chunks one chunk block
+// apart, so every tap is a plain matrix descriptor -- no im2col copy.
+// Every wait is bounded: a wait that gives up sets ST_TIMEOUT, the roles stop
+// issuing work, copies and MMAs in flight are waited for (bounded) and TMEM
+// is released.
+#include <cuda.h>
 #include <cuda_bf16.h>
+
+#include <mutex>
 
 #include "conv_tc.cuh"
 #include "hyb_internal.cuh"
@@ -29,149 +40,304 @@ namespace hyb {
 static constexpr int TX = 8, TY = 16;                 // output tile (cells)
 static constexpr int HX = TX + 2, HY = TY + 2, HZ = 3; // halo
 static constexpr int HCELLS = HX * HY * HZ;            // 540
-static constexpr int CHB = HCELLS * 16;                // bytes of one 8-channel chunk block
+static constexpr int CHB = HCELLS * 16;                // bytes one chunk copy writes (8640)
+static constexpr int CHBP = (CHB + 127) / 128 * 128;   // chunk block pitch in shared memory (8704)
+static constexpr int STAGES = 3;
+static constexpr int NTHREADS = 192;
 static constexpr long long MBAR_LIMIT = 1LL << 26;     // polls before a wait gives up
 
 // dropout keep decision of channel ch at cell (b, lin): Philox counter
-// (lin, b, (layer << 16) | (ch >> 2), pass), key (seed, 0xD0); word ch & 3
+// (lin, b, (layer << 16) | (ch >> 3), pass), key (seed, 0xD0); 16-bit field
+// ch & 7 of the output (word (ch & 7) >> 1, low half for even ch); kept when
+// the field is >= thr = round(p 2^16)
 __host__ __device__ inline bool dropout_keep(uint32_t seed, uint32_t pass, uint32_t layer, uint32_t b, uint32_t lin,
-                                             int ch, float p) {
-    const u32x4 r = philox4x32_10(lin, b, (layer << 16) | ((uint32_t)ch >> 2), pass, seed, 0xD0u);
-    return !(u01f(r.v[ch & 3]) < p);
+                                             int ch, uint32_t thr) {
+    const u32x4 r = philox4x32_10(lin, b, (layer << 16) | ((uint32_t)ch >> 3), pass, seed, 0xD0u);
+    const uint32_t f = (r.v[(ch & 7) >> 1] >> (16 * (ch & 1))) & 0xFFFFu;
+    return f >= thr;
 }
 
-size_t conv_smem_bytes(int cin, int N) {
-    const size_t halo = (size_t)(cin / 8) * CHB;
-    const size_t w = (size_t)27 * (cin / 8) * N * 16;
-    // the operand descriptors of every tap stay inside this allocation for
-    // either reading of the leading/stride offsets (halo first)
-    const size_t need = halo + w;
-    const size_t worst = (size_t)(cin / 8 - 2) * CHB + (2 * HY + 2) * HX * 16 + 32 + 15 * (size_t)CHB + 288;
-    return need > worst ? need : worst;
-}
+template <int KC, int N>
+struct ConvCfg {
+    static constexpr int WBYTES = 27 * KC * N * 16;    // weights, core layout [27][KC][N][8]
+    static constexpr int STAGE = KC * CHBP;            // one halo buffer
+    static constexpr int SMEM = WBYTES + STAGES * STAGE + 1024;  // + alignment slack
+    static constexpr int TCOLS = 2 * N < 32 ? 32 : 2 * N;        // two accumulators
+};
 
-__global__ void __launch_bounds__(128) k_conv3_tc(ConvArgs a) {
-    extern __shared__ __align__(1024) uint8_t smem[];
-    __shared__ __align__(8) uint64_t mbar;
+template <int KC, int N>
+__global__ void __launch_bounds__(NTHREADS, 1) k_conv3_tc(const __grid_constant__ CUtensorMap tmap, ConvArgs a) {
+    using Cfg = ConvCfg<KC, N>;
+    extern __shared__ uint8_t smem_raw[];
+    // 1024-byte aligned base: weights first, then the halo ring
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t *wsm = smem;
+    uint8_t *ring = smem + Cfg::WBYTES;
+    __shared__ __align__(8) uint64_t full_b[STAGES], empty_b[STAGES], tfull_b[2], tempty_b[2], done_b;
     __shared__ uint32_t taddr_s;
-    const int KC = a.cin / 8;
-    uint8_t *halo = smem;
-    uint8_t *wsm = smem + (size_t)KC * CHB;
+    __shared__ int abort_s;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-    if (warp == 0) {
-        tmem_alloc(smem_u32(&taddr_s), 32);
+    if (warp == 1) {
+        tmem_alloc(smem_u32(&taddr_s), Cfg::TCOLS);
         tmem_relinquish();
     }
     if (tid == 0) {
-        mbar_init(smem_u32(&mbar), 1);
-        fence_proxy_async_smem();
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(smem_u32(&full_b[s]), 1);
+            mbar_init(smem_u32(&empty_b[s]), 1);
+        }
+        for (int k = 0; k < 2; ++k) {
+            mbar_init(smem_u32(&tfull_b[k]), 1);
+            mbar_init(smem_u32(&tempty_b[k]), 4);
+        }
+        mbar_init(smem_u32(&done_b), 1);
+        abort_s = 0;
+        fence_mbar_init();
+        prefetch_tmap(&tmap);
     }
     // weights: straight 16-byte copies (already in core layout)
     {
-        const int nv = 27 * KC * a.N;
         const uint4 *src = reinterpret_cast<const uint4 *>(a.wt);
         uint4 *dst = reinterpret_cast<uint4 *>(wsm);
-        for (int i = tid; i < nv; i += blockDim.x) dst[i] = src[i];
+        for (int i = tid; i < Cfg::WBYTES / 16; i += NTHREADS) dst[i] = src[i];
     }
+    fence_proxy_async_smem();
     fence_before_sync();
     __syncthreads();
     fence_after_sync();
     const uint32_t taddr = taddr_s;
-    const uint32_t halo_s = smem_u32(halo), w_s = smem_u32(wsm);
-    const uint32_t idesc = idesc_bf16(128, a.N);
     const int tiles_x = a.W / TX, tiles_y = a.H / TY;
     const long long ntiles = (long long)a.B * a.D * tiles_y * tiles_x;
-    uint32_t phase = 0;
+    const uint32_t ring_s = smem_u32(ring), w_s = smem_u32(wsm);
 
-    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int tx = (int)(tile % tiles_x);
-        const int ty = (int)((tile / tiles_x) % tiles_y);
-        const int z0 = (int)((tile / ((long long)tiles_x * tiles_y)) % a.D);
-        const int b = (int)(tile / ((long long)tiles_x * tiles_y * a.D));
-        const int x0 = tx * TX, y0 = ty * TY;
-        // ---- halo [chunk][lz][ly][lx][8], zero outside the volume
-        for (int i = tid; i < KC * HCELLS; i += blockDim.x) {
-            const int ch = i / HCELLS, cell = i % HCELLS;
-            const int lz = cell / (HY * HX), ly = (cell / HX) % HY, lx = cell % HX;
-            const int gz = z0 - 1 + lz, gy = y0 - 1 + ly, gx = x0 - 1 + lx;
-            uint4 v = make_uint4(0, 0, 0, 0);
-            if (gz >= 0 && gz < a.D && gy >= 0 && gy < a.H && gx >= 0 && gx < a.W) {
-                const long long off = ((((long long)b * a.D + gz) * a.H + gy) * a.W + gx) * a.cin + ch * 8;
-                v = *reinterpret_cast<const uint4 *>(a.x + off);
-            }
-            reinterpret_cast<uint4 *>(halo)[i] = v;
-        }
-        fence_proxy_async_smem();
-        fence_before_sync();
-        __syncthreads();
-        fence_after_sync();
-        if (tid == 0) {
-            for (int tap = 0; tap < 27; ++tap) {
-                const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
-                for (int kk = 0; kk < KC / 2; ++kk) {
-                    const uint32_t aa = halo_s + (uint32_t)(2 * kk) * CHB + (uint32_t)(((dz * HY + dy) * HX + dx) * 16);
-                    const uint32_t bb = w_s + (uint32_t)((tap * KC + 2 * kk) * a.N) * 16;
-                    umma_bf16(taddr, smem_desc(aa, CHB, HX * 16), smem_desc(bb, a.N * 16, 128), idesc,
-                              (tap | kk) != 0);
+    if (warp == 0) {
+        // ------------------------------------------------------------ producer
+        if (lane == 0) {
+            int s = 0;
+            uint32_t ph = 0;
+            long long issued = 0;
+            for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+                if (!mbar_wait(smem_u32(&empty_b[s]), ph ^ 1, MBAR_LIMIT) || *(volatile int *)&abort_s) {
+                    atomicOr(a.status, ST_TIMEOUT);
+                    *(volatile int *)&abort_s = 1;
+                    break;
+                }
+                const int tx = (int)(tile % tiles_x);
+                const int ty = (int)((tile / tiles_x) % tiles_y);
+                const int z0 = (int)((tile / ((long long)tiles_x * tiles_y)) % a.D);
+                const int b = (int)(tile / ((long long)tiles_x * tiles_y * a.D));
+                const uint32_t fb = smem_u32(&full_b[s]);
+                mbar_arrive_expect_tx(fb, KC * CHB);
+                const uint32_t dst = ring_s + (uint32_t)(s * Cfg::STAGE);
+#pragma unroll
+                for (int c = 0; c < KC; ++c)
+                    tma_load_5d(dst + (uint32_t)(c * CHBP), &tmap, 8 * c, tx * TX - 1, ty * TY - 1, z0 - 1, b, fb);
+                ++issued;
+                if (++s == STAGES) {
+                    s = 0;
+                    ph ^= 1;
                 }
             }
-            umma_commit(smem_u32(&mbar));
-        }
-        const bool ok = mbar_wait(smem_u32(&mbar), phase, MBAR_LIMIT);
-        phase ^= 1;
-        if (__syncthreads_or(!ok)) {
-            if (tid == 0) atomicOr(a.status, ST_TIMEOUT);
-            break;
-        }
-        fence_after_sync();
-        // ---- epilogue: row m = 32 warp + lane -> cell (x0 + m % 8, y0 + m / 8, z0)
-        const int m = warp * 32 + lane;
-        const int cx = x0 + (m & 7), cy = y0 + (m >> 3);
-        const uint32_t lin = (uint32_t)(((long long)z0 * a.H + cy) * a.W + cx);
-        __nv_bfloat16 *out = a.y + ((((long long)b * a.D + z0) * a.H + cy) * a.W + cx) * a.N;
-        for (int h = 0; h < a.N / 16; ++h) {
-            float v[16];
-            tmem_ld16(taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)(h * 16), v);
-            __align__(16) __nv_bfloat16 o[16];
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const int ch = h * 16 + j;
-                float s = v[j] + (a.bias ? a.bias[ch] : 0.0f);
-                if (a.relu) s = fmaxf(s, 0.0f);
-                if (a.drop_p > 0.0f)
-                    s = dropout_keep(a.seed, a.pass, a.layer, (uint32_t)b, lin, ch, a.drop_p) ? s / (1.0f - a.drop_p)
-                                                                                              : 0.0f;
-                o[j] = __float2bfloat16_rn(s);
+            // copies still in flight when the loop stopped early complete before exit
+            if (*(volatile int *)&abort_s) {
+                for (int k = 0; k < STAGES && issued > 0; ++k, --issued) {
+                    if (--s < 0) {
+                        s = STAGES - 1;
+                        ph ^= 1;
+                    }
+                    mbar_wait(smem_u32(&full_b[s]), ph, MBAR_LIMIT);
+                }
             }
-            reinterpret_cast<uint4 *>(out + h * 16)[0] = reinterpret_cast<const uint4 *>(o)[0];
-            reinterpret_cast<uint4 *>(out + h * 16)[1] = reinterpret_cast<const uint4 *>(o)[1];
         }
-        fence_before_sync();
-        __syncthreads();
+    } else if (warp == 1) {
+        // ------------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            constexpr uint32_t idesc = idesc_bf16(128, N);
+            const uint64_t a0 = smem_desc(ring_s, CHBP, HX * 16);
+            const uint64_t b0 = smem_desc(w_s, N * 16, 128);
+            int s = 0;
+            uint32_t ph = 0;
+            long long it = 0;
+            for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+                const int acc = (int)(it & 1);
+                const uint32_t aph = (uint32_t)((it >> 1) & 1);
+                if (!mbar_wait(smem_u32(&tempty_b[acc]), aph ^ 1, MBAR_LIMIT) ||
+                    !mbar_wait(smem_u32(&full_b[s]), ph, MBAR_LIMIT) || *(volatile int *)&abort_s) {
+                    atomicOr(a.status, ST_TIMEOUT);
+                    *(volatile int *)&abort_s = 1;
+                    break;
+                }
+                fence_after_sync();
+                const uint32_t d = taddr + (uint32_t)(acc * N);
+                const uint64_t as = a0 + (uint64_t)((s * Cfg::STAGE) >> 4);
+#pragma unroll
+                for (int tap = 0; tap < 27; ++tap) {
+                    const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
+                    const uint32_t toff = (uint32_t)(((dz * HY + dy) * HX + dx) * 16);
+#pragma unroll
+                    for (int kk = 0; kk < KC / 2; ++kk) {
+                        const uint64_t ad = as + (uint64_t)((toff + (uint32_t)(2 * kk * CHBP)) >> 4);
+                        const uint64_t bd = b0 + (uint64_t)(((tap * KC + 2 * kk) * N * 16) >> 4);
+                        umma_bf16(d, ad, bd, idesc, (tap | kk) != 0);
+                    }
+                }
+                umma_commit(smem_u32(&empty_b[s]));    // the stage may be refilled
+                umma_commit(smem_u32(&tfull_b[acc]));  // the accumulator is ready
+                if (++s == STAGES) {
+                    s = 0;
+                    ph ^= 1;
+                }
+            }
+            // every MMA issued has finished reading shared memory before exit
+            umma_commit(smem_u32(&done_b));
+            mbar_wait(smem_u32(&done_b), 0, MBAR_LIMIT);
+        }
+    } else {
+        // ------------------------------------------------------------ epilogue
+        const int q = warp & 3;              // TMEM lane quarter this warp may access
+        const int m = q * 32 + lane;         // accumulator row = cell of the tile
+        const float scale = a.drop_scale;
+        long long it = 0;
+        for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+            const int acc = (int)(it & 1);
+            const uint32_t aph = (uint32_t)((it >> 1) & 1);
+            const bool ok = mbar_wait(smem_u32(&tfull_b[acc]), aph, MBAR_LIMIT);
+            if (!__all_sync(0xffffffffu, ok) || *(volatile int *)&abort_s) {
+                if (lane == 0) {
+                    atomicOr(a.status, ST_TIMEOUT);
+                    *(volatile int *)&abort_s = 1;
+                }
+                break;
+            }
+            fence_after_sync();
+            float v[N];
+#pragma unroll
+            for (int h = 0; h < N / 16; ++h)
+                tmem_ld16(taddr + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * N + h * 16), v + 16 * h);
+            fence_before_sync();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&tempty_b[acc]));
+
+            const int tx = (int)(tile % tiles_x);
+            const int ty = (int)((tile / tiles_x) % tiles_y);
+            const int z0 = (int)((tile / ((long long)tiles_x * tiles_y)) % a.D);
+            const int b = (int)(tile / ((long long)tiles_x * tiles_y * a.D));
+            const int cx = tx * TX + (m & 7), cy = ty * TY + (m >> 3);
+            const uint32_t lin = (uint32_t)(((long long)z0 * a.H + cy) * a.W + cx);
+            const long long obase = ((((long long)b * a.D + z0) * a.H + cy) * a.W + cx) * N;
+            __nv_bfloat16 *out = a.y ? a.y + obase : nullptr;
+            float *outf = a.y_f32 ? a.y_f32 + obase : nullptr;
+#pragma unroll
+            for (int g8 = 0; g8 < N / 8; ++g8) {
+                uint32_t keep16[4] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu};
+                if (a.drop_thr) {
+                    const u32x4 r = philox4x32_10(lin, (uint32_t)b, (a.layer << 16) | (uint32_t)g8, a.pass, a.seed,
+                                                  0xD0u);
+#pragma unroll
+                    for (int w = 0; w < 4; ++w) keep16[w] = r.v[w];
+                }
+                float r8[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int ch = g8 * 8 + j;
+                    float s = v[ch] + (a.bias ? __ldg(a.bias + ch) : 0.0f);
+                    if (a.relu) s = fmaxf(s, 0.0f);
+                    if (a.drop_thr) {
+                        const uint32_t f = (keep16[j >> 1] >> (16 * (j & 1))) & 0xFFFFu;
+                        s = f >= a.drop_thr ? s * scale : 0.0f;
+                    }
+                    r8[j] = s;
+                }
+                if (outf) {
+                    reinterpret_cast<float4 *>(outf)[2 * g8] = make_float4(r8[0], r8[1], r8[2], r8[3]);
+                    reinterpret_cast<float4 *>(outf)[2 * g8 + 1] = make_float4(r8[4], r8[5], r8[6], r8[7]);
+                } else {
+                    __align__(16) __nv_bfloat16 o[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) o[j] = __float2bfloat16_rn(r8[j]);
+                    reinterpret_cast<uint4 *>(out)[g8] = *reinterpret_cast<const uint4 *>(o);
+                }
+            }
+        }
     }
-    fence_after_sync();
+    fence_before_sync();
     __syncthreads();
-    if (warp == 0) tmem_dealloc(taddr, 32);
+    fence_after_sync();
+    if (warp == 1) tmem_dealloc(taddr, Cfg::TCOLS);
 }
 
-hyb_status launch_conv3_tc(const ConvArgs &a, cudaStream_t st) {
-    if (a.cin % 16 != 0 || (a.N != 16 && a.N != 32) || a.W % TX != 0 || a.H % TY != 0)
-        return set_error(HYB_EINVAL, "conv shape: cin % 16, N in {16, 32}, W % 8, H % 16 required");
-    const size_t smem = conv_smem_bytes(a.cin, a.N);
-    cudaError_t e = cudaFuncSetAttribute(k_conv3_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+// ---------------------------------------------------------------- host side
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+    });
+    return fn;
+}
+
+// tensor map of a channels-last BF16 activation [B][D][H][W][C]: dims
+// (C, W, H, D, B), box (8 channels, halo x, halo y, halo z, 1)
+static hyb_status make_tmap(CUtensorMap *tm, const ConvArgs &a) {
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return set_error(HYB_ECUDA, "cuTensorMapEncodeTiled is not available");
+    const cuuint64_t dims[5] = {(cuuint64_t)a.cin, (cuuint64_t)a.W, (cuuint64_t)a.H, (cuuint64_t)a.D,
+                                (cuuint64_t)a.B};
+    const cuuint64_t es = 2;
+    const cuuint64_t strides[4] = {es * a.cin, es * a.cin * a.W, es * a.cin * a.W * a.H,
+                                   es * a.cin * a.W * a.H * a.D};
+    const cuuint32_t box[5] = {8, (cuuint32_t)HX, (cuuint32_t)HY, (cuuint32_t)HZ, 1};
+    const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    CUresult r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, (void *)a.x, dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return set_error(HYB_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+    return HYB_OK;
+}
+
+template <int KC, int N>
+static hyb_status launch_cfg(const ConvArgs &a, cudaStream_t st) {
+    using Cfg = ConvCfg<KC, N>;
+    CUtensorMap tm;
+    hyb_status s = make_tmap(&tm, a);
+    if (s != HYB_OK) return s;
+    cudaError_t e = cudaFuncSetAttribute(k_conv3_tc<KC, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
     if (e != cudaSuccess) return set_error(HYB_ECUDA, std::string("conv smem attribute: ") + cudaGetErrorString(e));
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_conv3_tc, 128, smem);
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_conv3_tc<KC, N>, NTHREADS, Cfg::SMEM);
     const long long ntiles = (long long)a.B * a.D * (a.H / TY) * (a.W / TX);
     const long long grid = std::min<long long>(ntiles, (long long)nsm * std::max(per_sm, 1));
-    k_conv3_tc<<<(unsigned)grid, 128, smem, st>>>(a);
+    k_conv3_tc<KC, N><<<(unsigned)grid, NTHREADS, Cfg::SMEM, st>>>(tm, a);
     e = cudaGetLastError();
     if (e != cudaSuccess) return set_error(HYB_ECUDA, std::string("conv launch: ") + cudaGetErrorString(e));
     return HYB_OK;
+}
+
+hyb_status launch_conv3_tc(const ConvArgs &a, cudaStream_t st) {
+    if (a.W % TX != 0 || a.H % TY != 0 || a.B < 1 || a.D < 1)
+        return set_error(HYB_EINVAL, "conv shape: W % 8 == 0 and H % 16 == 0 required");
+    if (((uintptr_t)a.x & 15) || ((uintptr_t)a.y & 15) || ((uintptr_t)a.y_f32 & 15) || ((uintptr_t)a.wt & 15) ||
+        (!a.y && !a.y_f32))
+        return set_error(HYB_EINVAL, "conv operands must be present and 16-byte aligned");
+    if (a.cin == 16 && a.N == 32) return launch_cfg<2, 32>(a, st);
+    if (a.cin == 32 && a.N == 32) return launch_cfg<4, 32>(a, st);
+    if (a.cin == 32 && a.N == 16) return launch_cfg<4, 16>(a, st);
+    if (a.cin == 16 && a.N == 16) return launch_cfg<2, 16>(a, st);
+    return set_error(HYB_EINVAL, "conv channels: (C_in, C_out) in {16, 32} x {16, 32}");
 }
 
 }  // namespace hyb

@@ -84,6 +84,34 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, long l
     return false;
 }
 
+// plain arrival (count 1) on an mbarrier
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
+}
+
+// arrival that also announces `bytes` of asynchronous (TMA) transactions
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t mbar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// tiled TMA load of a 5-D box into shared memory, completion counted on mbar
+__device__ __forceinline__ void tma_load_5d(uint32_t dst, const void *tmap, int c0, int c1, int c2, int c3, int c4,
+                                            uint32_t mbar) {
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+        "%5, %6}], [%7];" ::"r"(dst),
+        "l"(tmap), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(mbar)
+        : "memory");
+}
+
+__device__ __forceinline__ void prefetch_tmap(const void *tmap) {
+    asm volatile("prefetch.tensormap [%0];" ::"l"(tmap) : "memory");
+}
+
 // 32 lanes x 32 bits, 16 consecutive columns: thread i of the warp gets lane (32w + i)
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
     uint32_t r[16];
@@ -109,9 +137,11 @@ struct ConvArgs {
     const __nv_bfloat16 *wt;  // [27][cin/8][N][8] core layout
     const float *bias;        // [N] or null
     __nv_bfloat16 *y;         // [B][D][H][W][N]
+    float *y_f32;             // when set: FP32 output [B][D][H][W][N] instead of y
     int B, D, H, W, cin, N;
     int relu;
-    float drop_p;             // 0: no dropout
+    uint32_t drop_thr;        // dropout threshold round(p 2^16) on 16-bit Philox fields; 0: no dropout
+    float drop_scale;         // 1 / (1 - drop_thr 2^-16)
     uint32_t seed, pass, layer;
     int *status;
 };

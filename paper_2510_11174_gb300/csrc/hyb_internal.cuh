@@ -156,6 +156,7 @@ struct hyb_ctx {
     float *mur_old = nullptr;                        // saved boundary planes for Mur
     long long mur_plane = 0;                         // max plane size
     float *jscratch = nullptr;                       // per-tile J frames
+    int *jvalid = nullptr;                           // per tile: 1 when its frame was written this step
     long long jframe = 0;                            // floats per tile frame (3 * G^3)
     double *red_partials = nullptr;                  // FP64 block partials of reductions
     int red_blocks = 0;
@@ -223,7 +224,7 @@ void launch_step_inc(long long *step_dev, cudaStream_t st);
 
 size_t push_smem_bytes(int T);
 void launch_push_deposit(const GridDev &g, const float *E, const float *B, const SpDev *sps_dev, int nsp,
-                         const QedDev &qd, float *jscratch, int *status, const long long *step_dev,
+                         const QedDev &qd, float *jscratch, int *jvalid, int *status, const long long *step_dev,
                          cudaStream_t st);
 hyb_status setup_qed(hyb_ctx *c);  // builds the QED tables once per context
 hyb_status regime_update(hyb_ctx *c, const float *p_mean, const float *p_std);
@@ -237,7 +238,7 @@ void launch_fluid_energy(const GridDev &g, const FluidDev &f, double *p_w, doubl
 hyb_status eval_qed(hyb_ctx *c, int what, const float *chi, const float *r, int n, float *out);
 hyb_status setup_ionization(hyb_ctx *c, SpDev &s, const hyb_species_desc *d);
 hyb_status eval_ion_table(hyb_ctx *c, const SpDev &s, int Z, const float *x_host, int n, float *out_host);
-void launch_j_reduce(const GridDev &g, const float *jscratch, float *J, cudaStream_t st);
+void launch_j_reduce(const GridDev &g, const float *jscratch, const int *jvalid, float *J, cudaStream_t st);
 void launch_rebin(const GridDev &g, const SpDev &s, int *status, cudaStream_t st);
 void launch_compact(const GridDev &g, const SpDev &s, cudaStream_t st);
 void launch_bin_particles(const GridDev &g, const SpDev &s, long long n, const float *x, const float *y,

@@ -84,10 +84,11 @@ __device__ __forceinline__ void shape3(float p, int gbase, float S[3]) {
     }
 }
 
-__global__ void __launch_bounds__(256) k_push_deposit(GridDev g, const float *__restrict__ E,
+__global__ void __launch_bounds__(256, 3) k_push_deposit(GridDev g, const float *__restrict__ E,
                                                       const float *__restrict__ B,
                                                       const SpDev *__restrict__ sps, int nsp,
-                                                      float *__restrict__ jscratch, int *__restrict__ status,
+                                                      float *__restrict__ jscratch, int *__restrict__ jvalid,
+                                                      int *__restrict__ status,
                                                       const long long *__restrict__ step_dev, QedDev qd) {
     extern __shared__ float sm[];
     const int T = g.T, F = frame_F(T), G = frame_G(T);
@@ -102,6 +103,19 @@ __global__ void __launch_bounds__(256) k_push_deposit(GridDev g, const float *__
     int tal_n[NTALLY] = {0, 0, 0};
 
     const int t = blockIdx.x;
+    // a tile without particles writes no frame: the reduction skips it
+    {
+        int total = 0;
+        for (int si = 0; si < nsp; ++si) total += min(sps[si].count[t], sps[si].cap);
+        if (total == 0) {
+            if (threadIdx.x < nsp) {
+                sps[threadIdx.x].hole_count[t] = 0;
+                sps[threadIdx.x].hole_used[t] = 0;
+            }
+            if (threadIdx.x == 0) jvalid[t] = 0;
+            return;
+        }
+    }
     const int tx = t % g.nt[0], ty = (t / g.nt[0]) % g.nt[1], tz = t / (g.nt[0] * g.nt[1]);
     const int o[3] = {tx * T - 1, ty * T - 1, tz * T - 1};
     const long long N = g.N;
@@ -223,7 +237,51 @@ __global__ void __launch_bounds__(256) k_push_deposit(GridDev g, const float *__
                 }
 
                 // ---- Esirkepov deposit into the shared frame
-                if (q != 0.0f) {
+                bool same_cell = true;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) same_cell = same_cell && floorf(x0[a]) == floorf(x1[a]);
+                if (q != 0.0f && same_cell) {
+                    // no cell boundary crossed: per axis S0 = (1 - f0, f0), DS = (-d, d);
+                    // W_c is nonzero only at the cell's lower c-face, at the 2 x 2
+                    // transverse nodes (the general form below with its zero terms dropped)
+                    int lb[3];
+                    float s0[3][2], ds[3][2];
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        const float c0 = floorf(x0[a]);
+                        lb[a] = (int)c0 - o[a];
+                        float S0f[3], S1f[3];
+                        shape3(x0[a], (int)c0, S0f);
+                        shape3(x1[a], (int)c0, S1f);
+                        s0[a][0] = S0f[0];
+                        s0[a][1] = S0f[1];
+                        ds[a][0] = S1f[0] - S0f[0];
+                        ds[a][1] = S1f[1] - S0f[1];
+                    }
+                    const float qw = q * wgt;
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        const int pa = (c + 1) % 3, qa = (c + 2) % 3;
+                        const float fac = -qw / (dt * dvol[c]);
+                        float *Jc = sj + c * G3;
+#pragma unroll
+                        for (int bq = 0; bq < 2; ++bq)
+#pragma unroll
+                            for (int bp = 0; bp < 2; ++bp) {
+                                const float cross = s0[pa][bp] * s0[qa][bq] + 0.5f * ds[pa][bp] * s0[qa][bq] +
+                                                    0.5f * s0[pa][bp] * ds[qa][bq] +
+                                                    ds[pa][bp] * ds[qa][bq] * (1.0f / 3.0f);
+                                const float acc = 0.0f + ds[c][0] * cross;
+                                if (acc != 0.0f) {
+                                    int l3[3];
+                                    l3[c] = lb[c];
+                                    l3[pa] = lb[pa] + bp;
+                                    l3[qa] = lb[qa] + bq;
+                                    atomicAdd(&Jc[(l3[2] * G + l3[1]) * G + l3[0]], fac * acc);
+                                }
+                            }
+                    }
+                } else if (q != 0.0f) {
                     int lb[3];
                     float S0[3][3], DS[3][3];
 #pragma unroll
@@ -423,6 +481,7 @@ __global__ void __launch_bounds__(256) k_push_deposit(GridDev g, const float *__
 
     float *dst = jscratch + (long long)t * 3 * G3;
     for (int l = threadIdx.x; l < 3 * G3; l += blockDim.x) dst[l] = sj[l];
+    if (threadIdx.x == 0) jvalid[t] = 1;
 }
 
 // For every node: J = sum of the tile frames that cover it, in a fixed order.
@@ -448,7 +507,8 @@ __device__ __forceinline__ int axis_cands(const GridDev &g, int a, int i, int ti
     return n;
 }
 
-__global__ void k_j_reduce(GridDev g, const float *__restrict__ jscratch, float *__restrict__ J) {
+__global__ void k_j_reduce(GridDev g, const float *__restrict__ jscratch, const int *__restrict__ jvalid,
+                           float *__restrict__ J) {
     const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= g.N) return;
     const int nx = g.n[0], ny = g.n[1];
@@ -463,6 +523,7 @@ __global__ void k_j_reduce(GridDev g, const float *__restrict__ jscratch, float 
         for (int cy = 0; cy < nyc; ++cy)
             for (int cx = 0; cx < nxc; ++cx) {
                 const long long t = tx[cx] + (long long)g.nt[0] * (ty[cy] + (long long)g.nt[1] * tz[cz]);
+                if (!jvalid[t]) continue;
                 const float *fr = jscratch + t * 3 * G3 + (lz[cz] * G + ly[cy]) * G + lx[cx];
                 acc[0] += fr[0];
                 acc[1] += fr[G3];
@@ -566,14 +627,14 @@ __global__ void k_bin(GridDev g, SpDev sp, long long n, const float *__restrict_
 static inline unsigned blocks_for(long long n, int b) { return (unsigned)((n + b - 1) / b); }
 
 void launch_push_deposit(const GridDev &g, const float *E, const float *B, const SpDev *sps_dev, int nsp,
-                         const QedDev &qd, float *jscratch, int *status, const long long *step_dev,
+                         const QedDev &qd, float *jscratch, int *jvalid, int *status, const long long *step_dev,
                          cudaStream_t st) {
     const size_t smem = push_smem_bytes(g.T);
-    k_push_deposit<<<g.ntiles, 256, smem, st>>>(g, E, B, sps_dev, nsp, jscratch, status, step_dev, qd);
+    k_push_deposit<<<g.ntiles, 256, smem, st>>>(g, E, B, sps_dev, nsp, jscratch, jvalid, status, step_dev, qd);
 }
 
-void launch_j_reduce(const GridDev &g, const float *jscratch, float *J, cudaStream_t st) {
-    k_j_reduce<<<blocks_for(g.N, 256), 256, 0, st>>>(g, jscratch, J);
+void launch_j_reduce(const GridDev &g, const float *jscratch, const int *jvalid, float *J, cudaStream_t st) {
+    k_j_reduce<<<blocks_for(g.N, 256), 256, 0, st>>>(g, jscratch, jvalid, J);
 }
 
 void launch_rebin(const GridDev &g, const SpDev &s, int *status, cudaStream_t st) {

@@ -37,9 +37,12 @@ def test_dropout_mask_law_and_pass_dependence():
     n = m0.size
     assert abs(m0.mean() - (1 - p)) < 3 * np.sqrt(p * (1 - p) / n)
     assert 0.25 < np.mean(m0 != m1) < 0.4          # independent passes: 2 p (1 - p) = 0.32
-    # the documented Philox stream
-    r = oracle.philox([17, 1, (1 << 16) | (9 >> 2), 0], [7, 0xD0])
-    assert m0[1, 9, 17] == (not (oracle.u01(r[9 & 3]) < p))
+    # the documented Philox stream: channel 9 -> counter word (1 << 16) | 1,
+    # field 9 % 8 = 1 = high half of word 0
+    r = oracle.philox([17, 1, (1 << 16) | (9 // 8), 0], [7, 0xD0])
+    assert m0[1, 9, 17] == (((int(r[0]) >> 16) & 0xFFFF) >= round(p * 65536))
+    r = oracle.philox([17, 1, (1 << 16) | (30 // 8), 0], [7, 0xD0])
+    assert m0[1, 30, 17] == ((int(r[3]) & 0xFFFF) >= round(p * 65536))
 
 
 def test_mc_statistics_are_mean_and_population_std():
