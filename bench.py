@@ -226,7 +226,7 @@ def profile_phases(sim, model, step0):
             cls = {"classify": pt["classify"], "regime": pt["regime"]}
     sim.set_profiling(False)
     step_phases = ["push", "j_reduce", "source", "rebin", "field", "fluid"]
-    mean = {k: statistics.mean(p[k] for p in per) for k in step_phases}
+    mean = {k: statistics.mean(p.get(k, 0.0) for p in per) for k in step_phases}
     return mean, cls
 
 
@@ -312,10 +312,18 @@ def run_ours(args, rank, world):
         fms, _, fb, fa = timed_run(torch, fsim, None, args.steps, args.warmup, stream, barrier, False)
         fms = allmax(fms)
         fparts = 0.5 * (sum(fb["count"]) + sum(fa["count"]))
+        fphases, _ = profile_phases(fsim, None, args.warmup + args.steps)
         fsim.close()
-        full = {"steps_per_s": world * args.steps / (fms * 1e-3), "ms_per_step": fms / args.steps,
+        full_step = fms / args.steps
+        # the hybrid step without its classification, and the classification
+        # interval at which the hybrid would match full PIC
+        plain = ms_per_step - (cls["classify"] + cls["regime"]) / N_CLS if cls else ms_per_step
+        full = {"steps_per_s": world * args.steps / (fms * 1e-3), "ms_per_step": full_step,
                 "particles": fparts, "particle_pushes_per_s": world * fparts * args.steps / (fms * 1e-3),
-                "hybrid_speedup": fms / total_ms}
+                "phase_ms": fphases, "hybrid_speedup": fms / total_ms,
+                "hybrid_ms_per_step_without_classification": plain,
+                "break_even_classify_every": ((cls["classify"] + cls["regime"]) / (full_step - plain)
+                                              if cls and full_step > plain else None)}
 
     e2e = run_e2e(P, inp, args.steps, stream) if rank == 0 else None
     out = {

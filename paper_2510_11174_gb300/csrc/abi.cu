@@ -91,7 +91,7 @@ static void enqueue_step(hyb_ctx *c) {
     const bool fluid_phase = !c->fluids.empty() && !c->fluids_idle;
     if (fluid_phase) {
         pm.begin(HYB_PH_FLUID);
-        for (const FluidDev &f : c->fluids) launch_fluid(g, c->E, c->B, f, c->J, st);
+        launch_fluids(g, c->E, c->B, c->fluids.data(), (int)c->fluids.size(), c->J, st);
         pm.end(HYB_PH_FLUID);
     }
     if (c->desc.laser_kind == HYB_LASER_GAUSS) {
@@ -118,7 +118,7 @@ static void enqueue_step(hyb_ctx *c) {
     // kernels enqueued above (memsets and event records are not kernels)
     long long k = 0;
     if (set.n > 0) k += 2 + 2LL * set.n;
-    if (fluid_phase) k += 2LL * (long long)c->fluids.size();
+    if (fluid_phase) k += 2;
     if (c->desc.laser_kind == HYB_LASER_GAUSS) k += 1;
     k += 3 + ((g.bc[0] || g.bc[1] || g.bc[2]) ? 3 : 0) + 1;
     c->launches_per_step = k;
@@ -176,6 +176,7 @@ hyb_status hyb_init_grid(const hyb_grid_desc *d, hyb_ctx **out) {
         g.dd[a] = dd[a];
     }
     g.T = T;
+    g.tshift = T == 8 ? 3 : 2;
     g.ntiles = g.nt[0] * g.nt[1] * g.nt[2];
     g.N = (long long)n[0] * n[1] * n[2];
     g.dt = (float)dt;

@@ -20,109 +20,130 @@
 
 namespace hyb {
 
-__device__ __forceinline__ float fval(const GridDev &g, const float *__restrict__ F, int i, int j, int k) {
-    int idx[3] = {i, j, k};
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        if (g.bc[a] == 0) {
-            idx[a] = idx[a] < 0 ? idx[a] + g.n[a] : (idx[a] >= g.n[a] ? idx[a] - g.n[a] : idx[a]);
-        } else if (idx[a] < 0 || idx[a] > g.n[a] - 1) {
-            return 0.0f;
-        }
-    }
-    return F[cidx(g, idx[0], idx[1], idx[2])];
-}
+// all fluids of a context in one launch (they share E, B and J)
+struct FluidSet {
+    FluidDev f[HYB_MAX_FLUIDS];
+    int n;
+};
 
-__global__ void k_fluid_lorentz(GridDev g, const float *__restrict__ E, const float *__restrict__ B, FluidDev f) {
-    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= g.N) return;
-    const int nx = g.n[0], ny = g.n[1];
-    const int i = (int)(c % nx), j = (int)((c / nx) % ny), k = (int)(c / ((long long)nx * ny));
+// index of the lower neighbour along an axis: wrapped on periodic axes, -1
+// (outside: zero field, closed face) on absorbing ones
+__device__ __forceinline__ int lower_nb(int i, int n, int periodic) { return i > 0 ? i - 1 : (periodic ? n - 1 : -1); }
+__device__ __forceinline__ int upper_nb(int i, int n, int periodic) { return i < n - 1 ? i + 1 : (periodic ? 0 : -1); }
+
+// grid: (ceil(nx / blockDim.x), ny, nz); one thread per node
+__global__ void __launch_bounds__(128) k_fluid_lorentz(GridDev g, const float *__restrict__ E,
+                                                       const float *__restrict__ B, FluidSet fs) {
+    const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
+    if (i >= nx) return;
+    const int im = lower_nb(i, nx, g.bc[0] == 0), jm = lower_nb(j, ny, g.bc[1] == 0),
+              km = lower_nb(k, nz, g.bc[2] == 0);
     const long long N = g.N;
+    auto at = [&](const float *F, int a, int b, int c) -> float {
+        return (a < 0 || b < 0 || c < 0) ? 0.0f : __ldg(F + ((long long)c * ny + b) * nx + a);
+    };
     const float *Ex = E, *Ey = E + N, *Ez = E + 2 * N, *Bx = B, *By = B + N, *Bz = B + 2 * N;
     float e[3], b[3];
-    e[0] = 0.5f * (fval(g, Ex, i - 1, j, k) + fval(g, Ex, i, j, k));
-    e[1] = 0.5f * (fval(g, Ey, i, j - 1, k) + fval(g, Ey, i, j, k));
-    e[2] = 0.5f * (fval(g, Ez, i, j, k - 1) + fval(g, Ez, i, j, k));
-    b[0] = 0.25f * (fval(g, Bx, i, j - 1, k - 1) + fval(g, Bx, i, j, k - 1) + fval(g, Bx, i, j - 1, k) +
-                    fval(g, Bx, i, j, k));
-    b[1] = 0.25f * (fval(g, By, i - 1, j, k - 1) + fval(g, By, i, j, k - 1) + fval(g, By, i - 1, j, k) +
-                    fval(g, By, i, j, k));
-    b[2] = 0.25f * (fval(g, Bz, i - 1, j - 1, k) + fval(g, Bz, i, j - 1, k) + fval(g, Bz, i - 1, j, k) +
-                    fval(g, Bz, i, j, k));
-    const float h = f.q * 0.5f * g.dt / f.m;
-    float um[3], tt[3], ss[3], ud[3];
-    const float u0[3] = {f.ux[c], f.uy[c], f.uz[c]};
+    e[0] = 0.5f * (at(Ex, im, j, k) + at(Ex, i, j, k));
+    e[1] = 0.5f * (at(Ey, i, jm, k) + at(Ey, i, j, k));
+    e[2] = 0.5f * (at(Ez, i, j, km) + at(Ez, i, j, k));
+    b[0] = 0.25f * (at(Bx, i, jm, km) + at(Bx, i, j, km) + at(Bx, i, jm, k) + at(Bx, i, j, k));
+    b[1] = 0.25f * (at(By, im, j, km) + at(By, i, j, km) + at(By, im, j, k) + at(By, i, j, k));
+    b[2] = 0.25f * (at(Bz, im, jm, k) + at(Bz, i, jm, k) + at(Bz, im, j, k) + at(Bz, i, j, k));
+    const long long c = ((long long)k * ny + j) * nx + i;
+    for (int q = 0; q < fs.n; ++q) {
+        const FluidDev &f = fs.f[q];
+        const float h = f.q * 0.5f * g.dt / f.m;
+        float um[3], tt[3], ss[3], ud[3];
+        const float u0[3] = {f.ux[c], f.uy[c], f.uz[c]};
 #pragma unroll
-    for (int a = 0; a < 3; ++a) um[a] = u0[a] + h * e[a];
-    const float gm = sqrtf(1.0f + um[0] * um[0] + um[1] * um[1] + um[2] * um[2]);
+        for (int a = 0; a < 3; ++a) um[a] = u0[a] + h * e[a];
+        const float gm = sqrtf(1.0f + um[0] * um[0] + um[1] * um[1] + um[2] * um[2]);
 #pragma unroll
-    for (int a = 0; a < 3; ++a) tt[a] = h * b[a] / gm;
-    const float t2 = tt[0] * tt[0] + tt[1] * tt[1] + tt[2] * tt[2];
+        for (int a = 0; a < 3; ++a) tt[a] = h * b[a] * (1.0f / gm);
+        const float t2 = tt[0] * tt[0] + tt[1] * tt[1] + tt[2] * tt[2];
+        const float s2 = 2.0f / (1.0f + t2);
 #pragma unroll
-    for (int a = 0; a < 3; ++a) ss[a] = 2.0f * tt[a] / (1.0f + t2);
-    ud[0] = um[0] + (um[1] * tt[2] - um[2] * tt[1]);
-    ud[1] = um[1] + (um[2] * tt[0] - um[0] * tt[2]);
-    ud[2] = um[2] + (um[0] * tt[1] - um[1] * tt[0]);
-    f.usx[c] = um[0] + (ud[1] * ss[2] - ud[2] * ss[1]) + h * e[0];
-    f.usy[c] = um[1] + (ud[2] * ss[0] - ud[0] * ss[2]) + h * e[1];
-    f.usz[c] = um[2] + (ud[0] * ss[1] - ud[1] * ss[0]) + h * e[2];
-    f.ns[c] = f.n[c];
+        for (int a = 0; a < 3; ++a) ss[a] = tt[a] * s2;
+        ud[0] = um[0] + (um[1] * tt[2] - um[2] * tt[1]);
+        ud[1] = um[1] + (um[2] * tt[0] - um[0] * tt[2]);
+        ud[2] = um[2] + (um[0] * tt[1] - um[1] * tt[0]);
+        f.usx[c] = um[0] + (ud[1] * ss[2] - ud[2] * ss[1]) + h * e[0];
+        f.usy[c] = um[1] + (ud[2] * ss[0] - ud[0] * ss[2]) + h * e[1];
+        f.usz[c] = um[2] + (ud[0] * ss[1] - ud[1] * ss[0]) + h * e[2];
+        f.ns[c] = f.n[c];
+    }
 }
 
-__global__ void k_fluid_update(GridDev g, FluidDev f, float *__restrict__ J) {
-    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= g.N) return;
-    const int nx = g.n[0], ny = g.n[1];
-    const int idx[3] = {(int)(c % nx), (int)((c / nx) % ny), (int)(c / ((long long)nx * ny))};
-    const float n0 = f.ns[c];
-    const float u0[3] = {f.usx[c], f.usy[c], f.usz[c]};
-    const float g0 = sqrtf(1.0f + u0[0] * u0[0] + u0[1] * u0[1] + u0[2] * u0[2]);
-    float dn = 0.0f, dm[3] = {0.0f, 0.0f, 0.0f};
+__global__ void __launch_bounds__(128) k_fluid_update(GridDev g, FluidSet fs, float *__restrict__ J) {
+    const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
+    if (i >= nx) return;
+    const int idx[3] = {i, j, k};
+    // neighbour nodes (lower, upper) per axis; -1 = closed outer face
+    int nbi[3][2];
+    nbi[0][0] = lower_nb(i, nx, g.bc[0] == 0);
+    nbi[0][1] = upper_nb(i, nx, g.bc[0] == 0);
+    nbi[1][0] = lower_nb(j, ny, g.bc[1] == 0);
+    nbi[1][1] = upper_nb(j, ny, g.bc[1] == 0);
+    nbi[2][0] = lower_nb(k, nz, g.bc[2] == 0);
+    nbi[2][1] = upper_nb(k, nz, g.bc[2] == 0);
+    const long long c = ((long long)k * ny + j) * nx + i;
+    const float inv_d[3] = {1.0f / g.d[0], 1.0f / g.d[1], 1.0f / g.d[2]};
+    float jf[3] = {0.0f, 0.0f, 0.0f};
+    for (int q = 0; q < fs.n; ++q) {
+        const FluidDev &f = fs.f[q];
+        const float n0 = f.ns[c];
+        const float u0[3] = {f.usx[c], f.usy[c], f.usz[c]};
+        const float ig0 = rsqrtf(1.0f + u0[0] * u0[0] + u0[1] * u0[1] + u0[2] * u0[2]);  // 1 / gamma
+        float dn = 0.0f, dm[3] = {0.0f, 0.0f, 0.0f};
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        const float ida = 1.0f / g.d[a];
-        // upper face (c, c+1) and lower face (c-1, c)
+        for (int a = 0; a < 3; ++a) {
+            const float ida = inv_d[a];
+            // upper face (c, c+1) and lower face (c-1, c)
 #pragma unroll
-        for (int side = 0; side < 2; ++side) {
-            int nb[3] = {idx[0], idx[1], idx[2]};
-            const int o = side == 0 ? 1 : -1;
-            nb[a] += o;
-            if (g.bc[a]) {
-                if (nb[a] < 0 || nb[a] > g.n[a] - 1) continue;  // closed outer face
-            } else {
-                nb[a] = nb[a] < 0 ? nb[a] + g.n[a] : (nb[a] >= g.n[a] ? nb[a] - g.n[a] : nb[a]);
+            for (int side = 0; side < 2; ++side) {
+                const int nbv = nbi[a][side == 0 ? 1 : 0];
+                if (nbv < 0) continue;  // closed outer face
+                int nb[3] = {idx[0], idx[1], idx[2]};
+                nb[a] = nbv;
+                const long long c1 = ((long long)nb[2] * ny + nb[1]) * nx + nb[0];
+                const float n1 = f.ns[c1];
+                const float u1[3] = {f.usx[c1], f.usy[c1], f.usz[c1]};
+                const float ig1 = rsqrtf(1.0f + u1[0] * u1[0] + u1[1] * u1[1] + u1[2] * u1[2]);
+                // nodes (lo, hi) of the face, in increasing index order
+                const float nlo = side == 0 ? n0 : n1, nhi = side == 0 ? n1 : n0;
+                const float v0 = u0[a] * ig0, v1 = u1[a] * ig1;
+                const float vlo = side == 0 ? v0 : v1, vhi = side == 0 ? v1 : v0;
+                const float s = 0.5f * (vlo + vhi);
+                const float sp = fmaxf(s, 0.0f), sm = fminf(s, 0.0f);
+                const float F = sp * nlo + sm * nhi;
+                const float sgn = side == 0 ? -1.0f : 1.0f;  // out through the upper face, in through the lower
+                dn += sgn * F * ida;
+#pragma unroll
+                for (int b2 = 0; b2 < 3; ++b2) {
+                    const float ulo = side == 0 ? u0[b2] : u1[b2], uhi = side == 0 ? u1[b2] : u0[b2];
+                    dm[b2] += sgn * (sp * nlo * ulo + sm * nhi * uhi) * ida;
+                }
+                if (side == 0) jf[a] += f.q * F;
             }
-            const long long c1 = cidx(g, nb[0], nb[1], nb[2]);
-            const float n1 = f.ns[c1];
-            const float u1[3] = {f.usx[c1], f.usy[c1], f.usz[c1]};
-            const float g1 = sqrtf(1.0f + u1[0] * u1[0] + u1[1] * u1[1] + u1[2] * u1[2]);
-            // nodes (lo, hi) of the face, in increasing index order
-            const float nlo = side == 0 ? n0 : n1, nhi = side == 0 ? n1 : n0;
-            const float vlo = side == 0 ? u0[a] / g0 : u1[a] / g1, vhi = side == 0 ? u1[a] / g1 : u0[a] / g0;
-            const float s = 0.5f * (vlo + vhi);
-            const float sp = fmaxf(s, 0.0f), sm = fminf(s, 0.0f);
-            const float F = sp * nlo + sm * nhi;
-            const float sgn = side == 0 ? -1.0f : 1.0f;  // out through the upper face, in through the lower
-            dn += sgn * F * ida;
-#pragma unroll
-            for (int b2 = 0; b2 < 3; ++b2) {
-                const float ulo = side == 0 ? u0[b2] : u1[b2], uhi = side == 0 ? u1[b2] : u0[b2];
-                dm[b2] += sgn * (sp * nlo * ulo + sm * nhi * uhi) * ida;
-            }
-            if (side == 0) J[(long long)a * g.N + c] += f.q * F;
         }
-    }
-    const float n1 = n0 + g.dt * dn;
-    float mom[3];
+        const float n1 = n0 + g.dt * dn;
+        float mom[3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) mom[a] = n0 * u0[a] + g.dt * dm[a];
-    if (n1 < 0.0f) atomicAdd(f.clamped, 1ULL);
-    f.n[c] = fmaxf(n1, 0.0f);
-    const bool keep = n1 > f.n_floor;
-    f.ux[c] = keep ? mom[0] / n1 : 0.0f;
-    f.uy[c] = keep ? mom[1] / n1 : 0.0f;
-    f.uz[c] = keep ? mom[2] / n1 : 0.0f;
+        for (int a = 0; a < 3; ++a) mom[a] = n0 * u0[a] + g.dt * dm[a];
+        if (n1 < 0.0f) atomicAdd(f.clamped, 1ULL);
+        f.n[c] = fmaxf(n1, 0.0f);
+        const bool keep = n1 > f.n_floor;
+        const float in1 = keep ? 1.0f / n1 : 0.0f;
+        f.ux[c] = mom[0] * in1;
+        f.uy[c] = mom[1] * in1;
+        f.uz[c] = mom[2] * in1;
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+        if (fs.n > 0) J[(long long)a * g.N + c] += jf[a];
 }
 
 static constexpr int FB = 256;
@@ -150,10 +171,16 @@ __global__ void __launch_bounds__(FB) k_fluid_energy(GridDev g, FluidDev f, doub
     }
 }
 
-void launch_fluid(const GridDev &g, const float *E, const float *B, const FluidDev &f, float *J, cudaStream_t st) {
-    const unsigned nb = (unsigned)((g.N + 255) / 256);
-    k_fluid_lorentz<<<nb, 256, 0, st>>>(g, E, B, f);
-    k_fluid_update<<<nb, 256, 0, st>>>(g, f, J);
+void launch_fluids(const GridDev &g, const float *E, const float *B, const FluidDev *f, int nf, float *J,
+                   cudaStream_t st) {
+    FluidSet fs;
+    memset(&fs, 0, sizeof(fs));
+    fs.n = nf < HYB_MAX_FLUIDS ? nf : HYB_MAX_FLUIDS;
+    for (int q = 0; q < fs.n; ++q) fs.f[q] = f[q];
+    const int bx = g.n[0] >= 128 ? 128 : 32 * ((g.n[0] + 31) / 32);
+    const dim3 grid((unsigned)((g.n[0] + bx - 1) / bx), (unsigned)g.n[1], (unsigned)g.n[2]);
+    k_fluid_lorentz<<<grid, bx, 0, st>>>(g, E, B, fs);
+    k_fluid_update<<<grid, bx, 0, st>>>(g, fs, J);
 }
 
 void launch_fluid_energy(const GridDev &g, const FluidDev &f, double *p_w, double *p_n, int nblocks,

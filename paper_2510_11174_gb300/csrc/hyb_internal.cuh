@@ -19,7 +19,8 @@ namespace hyb {
 struct GridDev {
     int n[3];          // nx, ny, nz
     int bc[3];         // 0 periodic, 1 Mur / reflecting
-    int T;             // tile edge (cells)
+    int T;             // tile edge (cells), a power of two
+    int tshift;        // log2 T
     int nt[3];         // tiles per axis
     int ntiles;
     long long N;       // cells
@@ -231,7 +232,8 @@ hyb_status regime_update(hyb_ctx *c, const float *p_mean, const float *p_std);
 hyb_status classifier_forward(hyb_ctx *c, const hyb_model *m, float *p_mean_dev, float *p_std_dev);
 const float *model_p_mean(const hyb_model *m);
 const float *model_p_std(const hyb_model *m);
-void launch_fluid(const GridDev &g, const float *E, const float *B, const FluidDev &f, float *J, cudaStream_t st);
+void launch_fluids(const GridDev &g, const float *E, const float *B, const FluidDev *f, int nf, float *J,
+                   cudaStream_t st);
 // FP64 partials of sum n m (gamma-1) (into p_w) and sum n (into p_n), nblocks each
 void launch_fluid_energy(const GridDev &g, const FluidDev &f, double *p_w, double *p_n, int nblocks,
                          cudaStream_t st);

@@ -10,7 +10,7 @@ namespace hyb {
 __device__ __forceinline__ int tile_of_cell(const GridDev &g, int a, float p) {
     int c = (int)floorf(p);
     c = c < 0 ? 0 : (c > g.n[a] - 1 ? g.n[a] - 1 : c);
-    return c / g.T;
+    return c >> g.tshift;
 }
 
 __device__ __forceinline__ int tile_index(const GridDev &g, float x, float y, float z) {

@@ -150,7 +150,10 @@ __global__ void __launch_bounds__(256, 3) k_push_deposit(GridDev g, const float 
     __syncthreads();
 
     const float dt = g.dt;
-    const float dvol[3] = {g.d[1] * g.d[2], g.d[0] * g.d[2], g.d[0] * g.d[1]};
+    const float inv_d[3] = {1.0f / g.d[0], 1.0f / g.d[1], 1.0f / g.d[2]};
+    // current per unit q w of a face crossing: -1 / (dt dA_c)
+    const float jfac[3] = {-1.0f / (dt * g.d[1] * g.d[2]), -1.0f / (dt * g.d[0] * g.d[2]),
+                           -1.0f / (dt * g.d[0] * g.d[1])};
     const float *sEx = sf, *sEy = sf + F3, *sEz = sf + 2 * F3;
     const float *sBx = sf + 3 * F3, *sBy = sf + 4 * F3, *sBz = sf + 5 * F3;
 
@@ -203,10 +206,11 @@ __global__ void __launch_bounds__(256, 3) k_push_deposit(GridDev g, const float 
                 for (int c = 0; c < 3; ++c) um[c] = u[c] + h * e[c];
                 const float gm = sqrtf(1.0f + um[0] * um[0] + um[1] * um[1] + um[2] * um[2]);
 #pragma unroll
-                for (int c = 0; c < 3; ++c) tt[c] = h * b[c] / gm;
+                for (int c = 0; c < 3; ++c) tt[c] = h * b[c] * (1.0f / gm);
                 const float t2 = tt[0] * tt[0] + tt[1] * tt[1] + tt[2] * tt[2];
+                const float s2 = 2.0f / (1.0f + t2);
 #pragma unroll
-                for (int c = 0; c < 3; ++c) ss[c] = 2.0f * tt[c] / (1.0f + t2);
+                for (int c = 0; c < 3; ++c) ss[c] = tt[c] * s2;
                 ud[0] = um[0] + (um[1] * tt[2] - um[2] * tt[1]);
                 ud[1] = um[1] + (um[2] * tt[0] - um[0] * tt[2]);
                 ud[2] = um[2] + (um[0] * tt[1] - um[1] * tt[0]);
@@ -220,7 +224,7 @@ __global__ void __launch_bounds__(256, 3) k_push_deposit(GridDev g, const float 
                 float x1[3];
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
-                    x1[a] = x0[a] + dt * u[a] / (gam * g.d[a]);
+                    x1[a] = x0[a] + u[a] * (dt / gam) * inv_d[a];
                     if (g.bc[a]) {
                         const float L = (float)(g.n[a] - 1);
                         if (x1[a] < 0.0f) { x1[a] = -x1[a]; u[a] = -u[a]; }
@@ -262,7 +266,7 @@ __global__ void __launch_bounds__(256, 3) k_push_deposit(GridDev g, const float 
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
                         const int pa = (c + 1) % 3, qa = (c + 2) % 3;
-                        const float fac = -qw / (dt * dvol[c]);
+                        const float fac = qw * jfac[c];
                         float *Jc = sj + c * G3;
 #pragma unroll
                         for (int bq = 0; bq < 2; ++bq)
@@ -299,7 +303,7 @@ __global__ void __launch_bounds__(256, 3) k_push_deposit(GridDev g, const float 
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
                         const int pa = (c + 1) % 3, qa = (c + 2) % 3;
-                        const float fac = -qw / (dt * dvol[c]);
+                        const float fac = qw * jfac[c];
                         float *Jc = sj + c * G3;
 #pragma unroll
                         for (int bq = 0; bq < 3; ++bq)
@@ -491,7 +495,7 @@ __global__ void __launch_bounds__(256, 3) k_push_deposit(GridDev g, const float 
 // local == T.
 __device__ __forceinline__ int axis_cands(const GridDev &g, int a, int i, int tile[2], int loc[2]) {
     const int T = g.T, nt = g.nt[a];
-    const int own = i / T, l = i - own * T + 1;
+    const int own = i >> g.tshift, l = i - own * T + 1;
     int n = 0;
     if (l <= 2) {
         int pt = own - 1;
@@ -509,10 +513,11 @@ __device__ __forceinline__ int axis_cands(const GridDev &g, int a, int i, int ti
 
 __global__ void k_j_reduce(GridDev g, const float *__restrict__ jscratch, const int *__restrict__ jvalid,
                            float *__restrict__ J) {
-    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= g.N) return;
+    // grid (ceil(nx / blockDim.x), ny, nz)
     const int nx = g.n[0], ny = g.n[1];
-    const int i = (int)(c % nx), j = (int)((c / nx) % ny), k = (int)(c / ((long long)nx * ny));
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
+    if (i >= nx) return;
+    const long long c = ((long long)k * ny + j) * nx + i;
     const int G = frame_G(g.T), G3 = G * G * G;
     int tx[2], lx[2], ty[2], ly[2], tz[2], lz[2];
     const int nxc = axis_cands(g, 0, i, tx, lx);
@@ -634,7 +639,9 @@ void launch_push_deposit(const GridDev &g, const float *E, const float *B, const
 }
 
 void launch_j_reduce(const GridDev &g, const float *jscratch, const int *jvalid, float *J, cudaStream_t st) {
-    k_j_reduce<<<blocks_for(g.N, 256), 256, 0, st>>>(g, jscratch, jvalid, J);
+    const int bx = g.n[0] >= 128 ? 128 : 32 * ((g.n[0] + 31) / 32);
+    const dim3 grid((unsigned)((g.n[0] + bx - 1) / bx), (unsigned)g.n[1], (unsigned)g.n[2]);
+    k_j_reduce<<<grid, bx, 0, st>>>(g, jscratch, jvalid, J);
 }
 
 void launch_rebin(const GridDev &g, const SpDev &s, int *status, cudaStream_t st) {
