@@ -351,7 +351,9 @@ enum {
     HYB_PH_FLUID = 5,     /* cold fluid Lorentz step, transport, face currents */
     HYB_PH_CLASSIFY = 6,  /* hyb_classify: classifier forward over the MC-dropout passes */
     HYB_PH_REGIME = 7,    /* hyb_classify: decision, dilation, conversions */
-    HYB_NPHASE = 8
+    HYB_PH_CONV1 = 8,     /* hyb_classify: the 32 -> 32 convolutions, summed over the MC passes */
+    HYB_PH_CONV2 = 9,     /* hyb_classify: the 32 -> 16 convolutions, summed over the MC passes */
+    HYB_NPHASE = 10
 };
 typedef struct {
     float ms[HYB_NPHASE];

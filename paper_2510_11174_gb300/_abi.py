@@ -61,8 +61,8 @@ class hyb_diag(C.Structure):
                 ("n_clamped", C.c_longlong), ("launches_classify", C.c_longlong)]
 
 
-HYB_NPHASE = 8
-PHASES = ["push", "j_reduce", "source", "rebin", "field", "fluid", "classify", "regime"]
+HYB_NPHASE = 10
+PHASES = ["push", "j_reduce", "source", "rebin", "field", "fluid", "classify", "regime", "conv_l1", "conv_l2"]
 HYB_MAX_FLUIDS = 4
 
 

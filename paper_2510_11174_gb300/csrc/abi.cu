@@ -265,6 +265,7 @@ void hyb_destroy(hyb_ctx *c) {
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
     if (c->graph) cudaGraphExecDestroy(c->graph);
+    for (cudaEvent_t e : c->conv_ev) cudaEventDestroy(e);
     for (int p = 0; p < HYB_NPHASE; ++p) {
         if (c->ev_start[p]) cudaEventDestroy(c->ev_start[p]);
         if (c->ev_end[p]) cudaEventDestroy(c->ev_end[p]);
@@ -710,6 +711,15 @@ hyb_status hyb_phase_times(hyb_ctx *c, hyb_phase_times_t *out) {
     for (int p = 0; p < HYB_NPHASE; ++p) {
         out->ms[p] = 0.0f;
         if (!c->phase_ran[p] || (c->step == 0 && p < HYB_PH_CLASSIFY)) continue;
+        if (p == HYB_PH_CONV1 || p == HYB_PH_CONV2) {
+            const int l = p - HYB_PH_CONV1, K = c->conv_ev_passes;
+            for (int k = 0; k < K; ++k) {
+                float ms = 0.0f;
+                HYB_CUDA_TRY(cudaEventElapsedTime(&ms, c->conv_ev[(l * K + k) * 2], c->conv_ev[(l * K + k) * 2 + 1]));
+                out->ms[p] += ms;
+            }
+            continue;
+        }
         HYB_CUDA_TRY(cudaEventElapsedTime(&out->ms[p], c->ev_start[p], c->ev_end[p]));
     }
     return HYB_OK;

@@ -384,10 +384,30 @@ hyb_status classifier_forward(hyb_ctx *c, const hyb_model *mc, float *p_mean_dev
         a0.y_f32 = m->h0;
         s = launch_conv3_tc(a0, c->stream);
         ++launches;
+        // profiling: events around the layer-1 and layer-2 convolutions of every pass
+        const bool prof = c->profiling;
+        if (prof) {
+            const size_t need = (size_t)2 * K * 2;
+            while (c->conv_ev.size() < need) {
+                cudaEvent_t e;
+                if (cudaEventCreate(&e) != cudaSuccess) {
+                    m->stream = saved;
+                    return set_error(HYB_ECUDA, "profiling event creation");
+                }
+                c->conv_ev.push_back(e);
+            }
+            c->conv_ev_passes = K;
+            c->phase_ran[HYB_PH_CONV1] = c->phase_ran[HYB_PH_CONV2] = true;
+        }
         for (int k = 1; k <= K && s == HYB_OK; ++k) {
             k_dropout_apply<<<nb(g.N), 256, 0, c->stream>>>(m->h0, g.N, g.N, m->d.seed, (uint32_t)(k - 1), thr,
                                                             dropout_scale(thr), m->a1);
-            s = model_run(m, 1, D, H, W, k - 1, k, 1);
+            for (int l = 1; l < 3 && s == HYB_OK; ++l) {
+                if (prof) cudaEventRecord(c->conv_ev[((l - 1) * K + (k - 1)) * 2], c->stream);
+                s = launch_conv3_tc(conv_args(m, l, 1, D, H, W, k - 1), c->stream);
+                if (prof) cudaEventRecord(c->conv_ev[((l - 1) * K + (k - 1)) * 2 + 1], c->stream);
+            }
+            if (s == HYB_OK) launch_last(m, 1, D, H, W, k);
             launches += 4;
         }
     } else {

@@ -59,8 +59,8 @@ __global__ void __launch_bounds__(RB) k_energy_species(GridDev g, SpDev sp, doub
             const double ux = sp.ux[base + p], uy = sp.uy[base + p], uz = sp.uz[base + p];
             const double u2 = ux * ux + uy * uy + uz * uz;
             // photons carry w |k| (m c^2 units); massive particles w m (gamma - 1)
-            acc += sp.kind == 1 ? (double)sp.w[base + p] * sqrt(u2)
-                                : (double)sp.w[base + p] * sp.m_d * u2 / (sqrt(1.0 + u2) + 1.0);
+            acc += sp.kind == 1 ? (double)sp.w[base + p] * norm_from_sq(u2)
+                                : (double)sp.w[base + p] * sp.m_d * gamma_minus_one(u2);
         }
     }
     acc = block_sum(acc, sh);

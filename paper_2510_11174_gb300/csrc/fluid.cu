@@ -155,7 +155,7 @@ __global__ void __launch_bounds__(FB) k_fluid_energy(GridDev g, FluidDev f, doub
     for (long long c = blockIdx.x * (long long)FB + threadIdx.x; c < g.N; c += (long long)nblocks * FB) {
         const double n = f.n[c], ux = f.ux[c], uy = f.uy[c], uz = f.uz[c];
         const double u2 = ux * ux + uy * uy + uz * uz;
-        aw += n * f.m_d * u2 / (sqrt(1.0 + u2) + 1.0);
+        aw += n * f.m_d * gamma_minus_one(u2);
         an += n;
     }
     const double dV = g.dd[0] * g.dd[1] * g.dd[2];

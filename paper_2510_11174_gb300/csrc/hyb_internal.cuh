@@ -36,6 +36,31 @@ __host__ __device__ inline long long cidx(const GridDev &g, int i, int j, int k)
 }
 
 #ifdef __CUDACC__
+// FP64 kinetic-energy helpers of the reductions.  FP64 square roots and
+// divisions are slow on this part, so 1/sqrt(x) and 1/x start from the FP32
+// hardware estimates and take two Newton-Raphson steps in FP64
+// (y <- y (3 - x y^2) / 2 and r <- r (2 - x r)); each step squares the
+// relative error, so the FP32 estimate's ~1e-7 ends below FP64 rounding.
+__device__ __forceinline__ double rsqrt_f64(double x) {
+    double y = (double)rsqrtf((float)x);
+    y = y * (1.5 - 0.5 * x * y * y);
+    return y * (1.5 - 0.5 * x * y * y);
+}
+__device__ __forceinline__ double rcp_f64(double x) {
+    double r = (double)(1.0f / (float)x);
+    r = r * (2.0 - x * r);
+    return r * (2.0 - x * r);
+}
+// gamma - 1 = u^2 / (gamma + 1) (no cancellation for slow particles)
+__device__ __forceinline__ double gamma_minus_one(double u2) {
+    const double x = 1.0 + u2;
+    return u2 * rcp_f64(x * rsqrt_f64(x) + 1.0);
+}
+// |u| for photons (0 at u = 0)
+__device__ __forceinline__ double norm_from_sq(double u2) {
+    return u2 > 1e-30 ? u2 * rsqrt_f64(u2) : sqrt(u2);  // FP32 estimates need a normal FP32 argument
+}
+
 // Position of v on a grid uniform in log2 v with npo points per octave that
 // starts at 2^e0.  The octave comes from the binary exponent (exact) and the
 // in-octave position from log2 of the mantissa, so the coordinate keeps the
@@ -193,6 +218,8 @@ struct hyb_ctx {
     cudaEvent_t ev_start[HYB_NPHASE] = {};
     cudaEvent_t ev_end[HYB_NPHASE] = {};
     bool phase_ran[HYB_NPHASE] = {};
+    std::vector<cudaEvent_t> conv_ev;               // profiling: [layer 1, 2][pass][start, end]
+    int conv_ev_passes = 0;                         // passes recorded by the most recent classification
     long long launches_per_step = 0;
     long long launches_classify = 0;               // kernels the most recent hyb_classify launched
 

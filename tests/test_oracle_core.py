@@ -282,3 +282,53 @@ def test_reflecting_wall_reverses_normal_momentum():
     assert abs(sp.x[0] - x_exp) < 1e-14 and sp.ux[0] == 2.0
     assert abs(sp.y[0] - y_exp) < 1e-14 and sp.uy[0] == -3.0
     assert abs(oracle.energy_particles(sp) - (gam - 1)) < 1e-14
+
+
+def test_boris_reproduces_the_exb_drift():
+    """Crossed uniform fields, |E| << |B|: the guiding centre drifts at E x B / B^2
+    (here +x at E0 / B0); averaged over whole gyrations the Boris velocity matches."""
+    E0, B0, h = 0.01, 1.0, 0.05          # h = q dt / (2 m) with q = -1 below
+    e, b = np.array([0.0, E0, 0.0]), np.array([0.0, 0.0, B0])
+    u = np.zeros(3)
+    theta = 2 * math.atan(h * B0)        # rotation per step at gamma ~ 1
+    n = int(round(40 * 2 * math.pi / theta))
+    vs = []
+    for _ in range(n):
+        u = oracle.boris(-h, e, b, u)
+        vs.append(u / math.sqrt(1 + u @ u))
+    v = np.mean(vs, axis=0)
+    assert abs(v[0] - E0 / B0) < 2e-3 * (E0 / B0)
+    assert abs(v[1]) < 2e-2 * (E0 / B0) and abs(v[2]) < 1e-15
+
+
+def test_laser_sheet_radiates_the_prescribed_pulse():
+    """A current sheet J_y = -2 A(t) / dx on one plane radiates E_y = A(t - L/c)
+    to either side (surface current K = J dx, E = -K / 2).  With a transverse
+    spot much wider than the box the wave is plane; at lambda/32 the Yee phase
+    error over L is ~1e-3, so the field seen downstream must be the envelope
+    and carrier of A up to a time shift of at most one step."""
+    n = 256
+    dx = 2 * math.pi / 32
+    dt = 0.95 * dx / math.sqrt(3)
+    g = oracle.Grid.make(n, 4, 4, dx, dx, dx, dt, bc=(1, 0, 0))
+    E, B, J = oracle.zeros_field(g), oracle.zeros_field(g), oracle.zeros_field(g)
+    a0, tau, tp, xs, xo = 0.7, 20.0, 40.0, 20, 80
+    L = (xo - xs) * dx
+    steps = int((tp + L + 2.5 * tau) / dt)
+    t, ey = [], []
+    for s in range(steps):
+        J[:] = 0.0
+        oracle.laser_source(g, J, s, xs, 1, a0, tau, tp, 1e6, 1.5, 1.5)
+        oracle.fdtd_b_half(g, E, B)
+        oracle.fdtd_e(g, E, B, J)
+        oracle.fdtd_b_half(g, E, B)
+        t.append((s + 1) * dt)
+        ey.append(E[1][2, 2, xo])
+    t, ey = np.array(t), np.array(ey)
+    A = lambda tt: a0 * np.exp(-2 * math.log(2) * (tt - tp) ** 2 / tau ** 2) * np.sin(tt - tp)
+    shifts = np.linspace(-2 * dt, 2 * dt, 81)
+    errs = [np.sqrt(np.mean((ey - A(t - L - sh)) ** 2)) for sh in shifts]
+    k = int(np.argmin(errs))
+    assert abs(shifts[k]) <= dt
+    assert errs[k] <= 0.005 * a0, errs[k]
+    assert abs(np.max(np.abs(ey)) - a0) <= 0.01 * a0
