@@ -173,6 +173,7 @@ typedef struct {
     double n_fluid[HYB_MAX_FLUIDS];        /* sum n dV per fluid */
     long long n_clamped;                   /* fluid nodes clamped from negative density so far */
     long long launches_classify;           /* kernels the most recent hyb_classify launched */
+    long long tile_capacity[HYB_MAX_SPECIES];  /* current slots per tile of each species */
 } hyb_diag;
 
 /* Create a context: validates the descriptor, allocates fields on the
@@ -317,7 +318,13 @@ hyb_status hyb_get_fluid(hyb_ctx *ctx, int fluid_id, float *n, float *ux, float 
 hyb_status hyb_set_fields(hyb_ctx *ctx, const float *E, const float *B, int on_device);
 
 /* Advance n steps (stream-ordered; the step sequence is captured once into a
- * CUDA graph and replayed). */
+ * CUDA graph and replayed).  Tiles have a fixed number of slots per species;
+ * every 4 steps the compaction's fill flags travel to the host behind the
+ * steps (the host never runs more than 8 steps ahead of the last flags it
+ * read), and once a species' tiles have passed 3/4 of their slots hyb_step
+ * synchronises and doubles that species' slots per tile (its particles are
+ * copied tile by tile) before the next steps.  A tile that overflows before
+ * that drops particles and latches HYB_EOVERFLOW. */
 hyb_status hyb_step(hyb_ctx *ctx, int nsteps);
 
 /* Synchronises; fills *out. */

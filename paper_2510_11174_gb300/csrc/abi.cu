@@ -18,6 +18,8 @@
 
 namespace hyb {
 
+static constexpr int GROW_CHECK_STEPS = 4;  // steps between checks of the tile fill
+
 static thread_local std::string g_err = "no error";
 
 hyb_status set_error(hyb_status s, const std::string &msg) {
@@ -216,6 +218,7 @@ hyb_status hyb_init_grid(const hyb_grid_desc *d, hyb_ctx **out) {
         ctx_alloc(c, (void **)&c->red_out, sizeof(double) * (2 + HYB_MAX_SPECIES + 2 * HYB_MAX_FLUIDS)) ||
         ctx_alloc(c, (void **)&c->status, sizeof(int)) || ctx_alloc(c, (void **)&c->step_dev, sizeof(long long)) ||
         ctx_alloc(c, (void **)&c->mig_counts, sizeof(int) * HYB_MAX_SPECIES) ||
+        ctx_alloc(c, (void **)&c->fill_flags, sizeof(int)) ||
         ctx_alloc(c, (void **)&c->sp_dev, sizeof(SpDev) * HYB_MAX_SPECIES) ||
         ctx_alloc(c, (void **)&c->mask, (size_t)g.N) || ctx_alloc(c, (void **)&c->mask_tmp, (size_t)g.N) ||
         ctx_alloc(c, (void **)&c->rho_bg, sizeof(float) * (size_t)g.N) ||
@@ -229,6 +232,11 @@ hyb_status hyb_init_grid(const hyb_grid_desc *d, hyb_ctx **out) {
     cudaMemsetAsync(c->status, 0, sizeof(int), st);
     cudaMemsetAsync(c->step_dev, 0, sizeof(long long), st);
     cudaMemsetAsync(c->mask, 1, (size_t)g.N, st);  // everything kinetic until a classification
+    cudaMemsetAsync(c->fill_flags, 0, sizeof(int), st);
+    if (cudaMallocHost((void **)&c->fill_host, sizeof(int)) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->fill_ev, cudaEventDisableTiming) != cudaSuccess)
+        return fail(HYB_ENOMEM, "pinned fill flag");
+    *c->fill_host = 0;
     cudaMemsetAsync(c->rho_bg, 0, sizeof(float) * (size_t)g.N, st);
     c->regime.a_thr = 1.0;
     c->regime.n_thr = 1.0;
@@ -271,32 +279,24 @@ void hyb_destroy(hyb_ctx *c) {
         if (c->ev_end[p]) cudaEventDestroy(c->ev_end[p]);
     }
     for (void *p : c->owned) cudaFree(p);
+    if (c->fill_host) cudaFreeHost(c->fill_host);
+    if (c->fill_ev) cudaEventDestroy(c->fill_ev);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
 }
 
-static hyb_status alloc_species(hyb_ctx *c, Species &sp, int cap, bool has_zq, bool has_tau) {
-    const GridDev &g = c->g;
-    const size_t slots = (size_t)cap * g.ntiles;
-    SpDev &s = sp.dev;
-    memset(&s, 0, sizeof(s));
+// the per-slot arrays (particles, hole list) and the migration buffer of a
+// species with `cap` slots per tile
+static hyb_status alloc_slots(hyb_ctx *c, SpDev &s, int cap, bool has_zq, bool has_tau) {
+    const size_t slots = (size_t)cap * c->g.ntiles;
     s.cap = cap;
-    s.q = (float)sp.q;
-    s.m = (float)sp.m;
-    s.m_d = sp.m;
+    s.zq = s.tau = s.mzq = s.mtau = nullptr;
     float **fl[7] = {&s.x, &s.y, &s.z, &s.ux, &s.uy, &s.uz, &s.w};
     for (auto f : fl)
         if (ctx_alloc(c, (void **)f, sizeof(float) * slots)) return HYB_ENOMEM;
     if (has_zq && ctx_alloc(c, (void **)&s.zq, sizeof(float) * slots)) return HYB_ENOMEM;
     if (has_tau && ctx_alloc(c, (void **)&s.tau, sizeof(float) * slots)) return HYB_ENOMEM;
-    if (ctx_alloc(c, (void **)&s.id, sizeof(uint64_t) * slots)) return HYB_ENOMEM;
-    if (ctx_alloc(c, (void **)&s.tal_e, sizeof(double) * NTALLY * g.ntiles) ||
-        ctx_alloc(c, (void **)&s.tal_n, sizeof(unsigned long long) * NTALLY * g.ntiles))
-        return HYB_ENOMEM;
-    if (ctx_alloc(c, (void **)&s.count, sizeof(int) * g.ntiles) ||
-        ctx_alloc(c, (void **)&s.hole_count, sizeof(int) * g.ntiles) ||
-        ctx_alloc(c, (void **)&s.hole_used, sizeof(int) * g.ntiles) ||
-        ctx_alloc(c, (void **)&s.holes, sizeof(int) * slots))
+    if (ctx_alloc(c, (void **)&s.id, sizeof(uint64_t) * slots) || ctx_alloc(c, (void **)&s.holes, sizeof(int) * slots))
         return HYB_ENOMEM;
     // a particle moves less than one cell per step, so only the shell of a tile can leave it
     const long long mig = std::min<long long>((long long)slots, std::max<long long>(65536, (long long)slots / 2));
@@ -309,6 +309,43 @@ static hyb_status alloc_species(hyb_ctx *c, Species &sp, int cap, bool has_zq, b
     if (ctx_alloc(c, (void **)&s.mid, sizeof(uint64_t) * s.mig_cap) ||
         ctx_alloc(c, (void **)&s.mdest, sizeof(int) * s.mig_cap))
         return HYB_ENOMEM;
+    return HYB_OK;
+}
+
+// release a buffer of the context (buffers carved from a caller's arena stay
+// until the context is destroyed)
+static void ctx_free(hyb_ctx *c, void *p) {
+    if (!p || c->arena.base) return;
+    for (auto it = c->owned.begin(); it != c->owned.end(); ++it)
+        if (*it == p) {
+            c->owned.erase(it);
+            cudaFree(p);
+            return;
+        }
+}
+
+static void free_slots(hyb_ctx *c, const SpDev &s) {
+    void *ps[] = {s.x, s.y, s.z, s.ux, s.uy, s.uz, s.w, s.zq, s.tau, s.id, s.holes,
+                  s.mx, s.my, s.mz, s.mux, s.muy, s.muz, s.mw, s.mzq, s.mtau, s.mid, s.mdest};
+    for (void *p : ps) ctx_free(c, p);
+}
+
+static hyb_status alloc_species(hyb_ctx *c, Species &sp, int cap, bool has_zq, bool has_tau) {
+    const GridDev &g = c->g;
+    SpDev &s = sp.dev;
+    memset(&s, 0, sizeof(s));
+    s.q = (float)sp.q;
+    s.m = (float)sp.m;
+    s.m_d = sp.m;
+    if (alloc_slots(c, s, cap, has_zq, has_tau) != HYB_OK) return HYB_ENOMEM;
+    if (ctx_alloc(c, (void **)&s.tal_e, sizeof(double) * NTALLY * g.ntiles) ||
+        ctx_alloc(c, (void **)&s.tal_n, sizeof(unsigned long long) * NTALLY * g.ntiles))
+        return HYB_ENOMEM;
+    if (ctx_alloc(c, (void **)&s.count, sizeof(int) * g.ntiles) ||
+        ctx_alloc(c, (void **)&s.hole_count, sizeof(int) * g.ntiles) ||
+        ctx_alloc(c, (void **)&s.hole_used, sizeof(int) * g.ntiles))
+        return HYB_ENOMEM;
+    s.fill_flags = c->fill_flags;
     s.mig_count = c->mig_counts + c->sp.size();
     cudaMemsetAsync(s.count, 0, sizeof(int) * g.ntiles, c->stream);
     cudaMemsetAsync(s.hole_count, 0, sizeof(int) * g.ntiles, c->stream);
@@ -663,6 +700,58 @@ hyb_status hyb_set_fields(hyb_ctx *c, const float *E, const float *B, int on_dev
     return HYB_OK;
 }
 
+static hyb_status capture_step(hyb_ctx *c) {
+    if (c->graph) {
+        cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
+    }
+    cudaGraph_t graph;
+    HYB_CUDA_TRY(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    enqueue_step(c);
+    HYB_CUDA_TRY(cudaStreamEndCapture(c->stream, &graph));
+    cudaError_t e = cudaGraphInstantiate(&c->graph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return set_error(HYB_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    c->graph_valid = true;
+    return HYB_OK;
+}
+
+// Capacity growth: a species whose tiles passed 3/4 of their capacity (flag
+// set by the compaction or a conversion) gets twice the slots per tile before
+// the next steps; its live particles are copied tile by tile.
+static hyb_status grow_full_species(hyb_ctx *c, bool wait) {
+    if (!c->fill_pending) return HYB_OK;
+    const cudaError_t q = wait ? cudaEventSynchronize(c->fill_ev) : cudaEventQuery(c->fill_ev);
+    if (q == cudaErrorNotReady) return HYB_OK;
+    if (q != cudaSuccess) return set_error(HYB_ECUDA, std::string("fill check: ") + cudaGetErrorString(q));
+    c->fill_pending = false;
+    const int flags = *c->fill_host;
+    if (!flags) return HYB_OK;
+    HYB_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    for (size_t sid = 0; sid < c->sp.size(); ++sid) {
+        if (!(flags & (1 << sid))) continue;
+        Species &sp = c->sp[sid];
+        const long long ncap = std::min<long long>(2LL * sp.dev.cap, 0x3fffffffLL);
+        if (ncap <= sp.dev.cap || ncap * (long long)c->g.ntiles > (1LL << 40))
+            return set_error(HYB_EOVERFLOW, "species tiles are full and cannot grow");
+        SpDev ns = sp.dev;
+        if (alloc_slots(c, ns, (int)ncap, sp.dev.zq != nullptr, sp.dev.tau != nullptr) != HYB_OK)
+            return set_error(HYB_ENOMEM, "growing a species' tiles");
+        launch_regrid(c->g, sp.dev, ns, c->stream);
+        HYB_CUDA_TRY(cudaStreamSynchronize(c->stream));
+        free_slots(c, sp.dev);
+        sp.dev = ns;
+        sp.cap = (int)ncap;
+        sp.mig_cap = ns.mig_cap;
+    }
+    const SpSet all = species_set(c);
+    HYB_CUDA_TRY(cudaMemcpyAsync(c->sp_dev, all.s, sizeof(SpDev) * all.n, cudaMemcpyHostToDevice, c->stream));
+    HYB_CUDA_TRY(cudaMemsetAsync(c->fill_flags, 0, sizeof(int), c->stream));
+    HYB_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    c->graph_valid = false;
+    return HYB_OK;
+}
+
 hyb_status hyb_step(hyb_ctx *c, int nsteps) {
     if (!c || nsteps < 0) return set_error(HYB_EINVAL, "bad argument");
     if (c->error_latched) return set_error(HYB_ESTATE, "context is in an error state (hyb_clear_status)");
@@ -670,21 +759,31 @@ hyb_status hyb_step(hyb_ctx *c, int nsteps) {
     if (!c->graph_valid) {
         hyb_status lv = validate_links(c);
         if (lv != HYB_OK) return lv;
-        if (c->graph) {
-            cudaGraphExecDestroy(c->graph);
-            c->graph = nullptr;
-        }
-        cudaGraph_t graph;
-        HYB_CUDA_TRY(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-        enqueue_step(c);
-        HYB_CUDA_TRY(cudaStreamEndCapture(c->stream, &graph));
-        cudaError_t e = cudaGraphInstantiate(&c->graph, graph, 0);
-        cudaGraphDestroy(graph);
-        if (e != cudaSuccess) return set_error(HYB_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
-        c->graph_valid = true;
     }
-    for (int i = 0; i < nsteps; ++i) HYB_CUDA_TRY(cudaGraphLaunch(c->graph, c->stream));
-    c->step += nsteps;
+    for (int done = 0; done < nsteps;) {
+        if (c->auto_grow) {
+            // the host may run ahead of the flags by at most two check intervals
+            hyb_status gs = grow_full_species(c, c->steps_since_copy >= 2 * GROW_CHECK_STEPS);
+            if (gs != HYB_OK) return gs;
+        }
+        if (!c->graph_valid) {
+            hyb_status cs = capture_step(c);
+            if (cs != HYB_OK) return cs;
+        }
+        const int chunk = std::min(nsteps - done, GROW_CHECK_STEPS);
+        for (int i = 0; i < chunk; ++i) HYB_CUDA_TRY(cudaGraphLaunch(c->graph, c->stream));
+        done += chunk;
+        c->step += chunk;
+        c->steps_since_copy += chunk;
+        if (c->auto_grow && !c->fill_pending && c->steps_since_copy >= GROW_CHECK_STEPS) {
+            // the fill flags travel to pinned memory behind the steps; the next
+            // check reads them once the copy is done, without waiting for it
+            HYB_CUDA_TRY(cudaMemcpyAsync(c->fill_host, c->fill_flags, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+            HYB_CUDA_TRY(cudaEventRecord(c->fill_ev, c->stream));
+            c->fill_pending = true;
+            c->steps_since_copy = 0;
+        }
+    }
     return HYB_OK;
 }
 
@@ -794,6 +893,7 @@ hyb_status hyb_diagnostics(hyb_ctx *c, hyb_diag *out) {
     out->status = status_to_code(h);
     out->launches_per_step = c->launches_per_step;
     out->launches_classify = c->launches_classify;
+    for (size_t i = 0; i < c->sp.size() && i < HYB_MAX_SPECIES; ++i) out->tile_capacity[i] = c->sp[i].dev.cap;
     out->n_fluids = nfl;
     for (int f = 0; f < nfl; ++f) {
         out->w_fluid[f] = r[2 + set.n + 2 * f];

@@ -112,6 +112,8 @@ struct SpDev {
     // per-tile accumulated tallies, TALLY_* entries per tile
     double *tal_e;
     unsigned long long *tal_n;
+    // bit sp_index is set when a tile of this species passed 3/4 of its capacity
+    int *fill_flags;
 };
 
 // tallies per tile: energies (FP64) and event counts
@@ -190,6 +192,12 @@ struct hyb_ctx {
     int *status = nullptr;                           // device status word
     long long *step_dev = nullptr;                   // device step counter (read by graph replays)
     int *mig_counts = nullptr;                       // HYB_MAX_SPECIES migration counters
+    int *fill_flags = nullptr;                       // device: species whose tiles passed 3/4 of their capacity
+    int *fill_host = nullptr;                        // pinned copy of fill_flags (read without a sync)
+    cudaEvent_t fill_ev = nullptr;                   // marks the copy into fill_host
+    bool fill_pending = false;                       // a copy into fill_host was enqueued
+    long long steps_since_copy = 0;                  // steps enqueued since that copy
+    bool auto_grow = true;                           // hyb_step grows full species
 
     std::vector<hyb::Species> sp;
     hyb::SpDev *sp_dev = nullptr;  // device copy of the species descriptors (HYB_MAX_SPECIES)
@@ -270,6 +278,7 @@ hyb_status eval_ion_table(hyb_ctx *c, const SpDev &s, int Z, const float *x_host
 void launch_j_reduce(const GridDev &g, const float *jscratch, const int *jvalid, float *J, cudaStream_t st);
 void launch_rebin(const GridDev &g, const SpDev &s, int *status, cudaStream_t st);
 void launch_compact(const GridDev &g, const SpDev &s, cudaStream_t st);
+void launch_regrid(const GridDev &g, const SpDev &from, const SpDev &to, cudaStream_t st);
 void launch_bin_particles(const GridDev &g, const SpDev &s, long long n, const float *x, const float *y,
                           const float *z, const float *ux, const float *uy, const float *uz,
                           const float *w, const float *zq, const uint64_t *ids, int *status,

@@ -575,6 +575,7 @@ __global__ void k_compact(GridDev g, SpDev sp) {
     int n = min(sp.count[t], sp.cap);
     if (hu >= hc) {
         sp.count[t] = n;  // an overflowing append left count above the capacity
+        if (4 * n > 3 * sp.cap) atomicOr(sp.fill_flags, 1 << sp.sp_index);
         return;
     }
     const long long base = (long long)t * sp.cap;
@@ -598,6 +599,22 @@ __global__ void k_compact(GridDev g, SpDev sp) {
     sp.count[t] = new_n;
     sp.hole_count[t] = 0;
     sp.hole_used[t] = 0;
+    if (4 * new_n > 3 * sp.cap) atomicOr(sp.fill_flags, 1 << sp.sp_index);
+}
+
+// copy every tile's live slots into a species layout with a larger capacity
+__global__ void k_regrid(SpDev from, SpDev to) {
+    const int t = blockIdx.x;
+    const int n = min(from.count[t], from.cap);
+    const long long a = (long long)t * from.cap, b = (long long)t * to.cap;
+    for (int p = threadIdx.x; p < n; p += blockDim.x) {
+        to.x[b + p] = from.x[a + p]; to.y[b + p] = from.y[a + p]; to.z[b + p] = from.z[a + p];
+        to.ux[b + p] = from.ux[a + p]; to.uy[b + p] = from.uy[a + p]; to.uz[b + p] = from.uz[a + p];
+        to.w[b + p] = from.w[a + p];
+        if (from.zq) to.zq[b + p] = from.zq[a + p];
+        if (from.tau) to.tau[b + p] = from.tau[a + p];
+        to.id[b + p] = from.id[a + p];
+    }
 }
 
 __global__ void k_count_tiles(GridDev g, long long n, const float *__restrict__ x, const float *__restrict__ y,
@@ -647,6 +664,10 @@ void launch_j_reduce(const GridDev &g, const float *jscratch, const int *jvalid,
 void launch_rebin(const GridDev &g, const SpDev &s, int *status, cudaStream_t st) {
     (void)g;
     k_rebin<<<152 * 4, 256, 0, st>>>(s, status);
+}
+
+void launch_regrid(const GridDev &g, const SpDev &from, const SpDev &to, cudaStream_t st) {
+    k_regrid<<<g.ntiles, 256, 0, st>>>(from, to);
 }
 
 void launch_compact(const GridDev &g, const SpDev &s, cudaStream_t st) {

@@ -108,7 +108,9 @@ __global__ void k_decide(long long N, const float *__restrict__ pm, const float 
 
 __global__ void k_clamp_counts(int ntiles, SpDev sp) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < ntiles && sp.count[t] > sp.cap) sp.count[t] = sp.cap;
+    if (t >= ntiles) return;
+    if (sp.count[t] > sp.cap) sp.count[t] = sp.cap;
+    if (4 * sp.count[t] > 3 * sp.cap) atomicOr(sp.fill_flags, 1 << sp.sp_index);
 }
 
 // max filter of radius r along axis a (Chebyshev dilation is three of these)

@@ -12,6 +12,11 @@ fraction, Gaussian laser) at the sizes of the benchmark configurations:
   overdense slab, absorbing (Mur) faces, and a Gaussian pulse launched from
   the x_min side with a0 drawn log-uniformly from [10, 300]; the kinetic
   cells receive `ppc` macro-particles per species when they are classified.
+* ``carbon_slab`` -- full PIC with ionization and QED: neutral carbon atoms
+  (16 per cell) in a slab of atom density n_e,max / 6 (fully ionized it
+  holds n_e,max electrons) with a flat top and Gaussian edges, a Gaussian
+  pulse from the x_min side, and empty electron, photon and positron
+  species that receive the ionization electrons, emitted photons and pairs.
 * ``periodic_plasma`` -- pre-ionised hydrogen (e-, p+) at uniform density,
   `ppc` particles per cell per species at uniform random positions, Maxwellian
   momenta of temperature `T_keV` (non-relativistic Gaussian per component,
@@ -84,7 +89,7 @@ OMEGA0_PER_FS = 2.0 * math.pi * 299792458.0 / 0.8e-6 * 1e-15   # w0 [1/fs] at 0.
 
 def ramp_slab(nx=256, ny=256, nz=128, cells_per_lambda=16, n_lo=0.01, n_hi=1.0, n_slab=5.0,
               slab_lambda=2.0, vacuum_lambda=1.0, a0=None, tau_fs=30.0, w0_lambda=2.0, seed=3, ppc=8,
-              tile_capacity=6144, n_floor=1e-10):
+              tile_capacity=8192, n_floor=1e-10):
     """The hybrid workload (defaults: 256 x 256 x 128, lambda/16).  Node
     densities n(x): 0 in the first `vacuum_lambda`, linear n_lo -> n_hi up to
     nx/2, n_slab over the next `slab_lambda`, 0 beyond; uniform in y and z.
@@ -115,3 +120,51 @@ def ramp_slab(nx=256, ny=256, nz=128, cells_per_lambda=16, n_lo=0.01, n_hi=1.0, 
     return dict(grid=dict(nx=nx, ny=ny, nz=nz, dx=dx, cfl_frac=0.95, bc=(1, 1, 1)), laser=laser,
                 fluids=[dict(q=-1.0, m=1.0, n=n, n_floor=n_floor), dict(q=1.0, m=M_P, n=n, n_floor=n_floor)],
                 species=[sp(-1.0, 1.0), sp(1.0, M_P)], ppc=ppc, a0=a0)
+
+
+CARBON_IP_EV = [11.260, 24.383, 47.888, 64.494, 392.09, 489.99]   # NIST ASD
+CARBON_L = [1, 1, 0, 0, 0, 0]                                      # 2p, 2p, 2s, 2s, 1s, 1s
+M_C = 12.0 * M_P
+
+
+def carbon_slab(n=128, cells_per_lambda=20, ppc=16, ne_max=10.0, plateau_lambda=2.0, edge_lambda=0.5,
+                a0=100.0, tau_fs=30.0, w0_lambda=2.0, seed=2, caps=(163840, 12288, 32768, 8192)):
+    """Full PIC with ionization and QED (defaults: 128^3, lambda/20).  Atom
+    density n_a(x) = (ne_max / 6) on a plateau of `plateau_lambda` centred in
+    x, with Gaussian edges of width `edge_lambda` cut at 3 sigma; `ppc` atoms
+    per cell at uniform random positions, weight n_a(x) dV / ppc, at rest.
+    Species: 0 electrons (emit photons into 2), 1 carbon (Z = 0, ionizes into
+    0), 2 photons (pairs into 0 and 3), 3 positrons (emit into 2).  `caps`
+    are their initial slots per 8^3 tile: the electron tiles hold 6 electrons
+    per atom slot with room for the pulse's snowplow (a front ionizes up to
+    one level per ion and step, faster than the tiles can grow)."""
+    dx = 2.0 * math.pi / cells_per_lambda
+    rng = np.random.default_rng(seed)
+    c0 = 0.5 * n
+    half = 0.5 * plateau_lambda * cells_per_lambda
+    sig = edge_lambda * cells_per_lambda
+    lo, hi = int(math.floor(c0 - half - 3 * sig)), int(math.ceil(c0 + half + 3 * sig))
+    lo, hi = max(lo, 1), min(hi, n - 2)
+
+    def profile(x):
+        d = np.maximum(np.abs(x - c0) - half, 0.0)
+        return (ne_max / 6.0) * np.exp(-0.5 * (d / sig) ** 2)
+
+    cells = (hi - lo) * n * n
+    m = cells * ppc
+    x = rng.uniform(lo, hi, m).astype(np.float32)
+    y = rng.uniform(0, n - 1, m).astype(np.float32)
+    z = rng.uniform(0, n - 1, m).astype(np.float32)
+    w = (profile(x.astype(np.float64)) * dx ** 3 / ppc).astype(np.float32)
+    zero = np.zeros(m, np.float32)
+    ions = dict(q=1.0, m=M_C, x=x, y=y, z=z, ux=zero, uy=zero.copy(), uz=zero.copy(), w=w, zq=zero.copy(),
+                ionize=dict(zmax=6, ip_eV=CARBON_IP_EV, l=CARBON_L, into=0), tile_capacity=caps[1])
+    empty = {k: np.zeros(0, np.float32) for k in ("x", "y", "z", "ux", "uy", "uz", "w")}
+    electrons = dict(q=-1.0, m=1.0, qed=dict(photon_species=2, eps_min=2.0), tile_capacity=caps[0], **empty)
+    photons = dict(q=0.0, m=0.0, kind=1, pairs=dict(electron=0, positron=3), tile_capacity=caps[2], **empty)
+    positrons = dict(q=1.0, m=1.0, qed=dict(photon_species=2, eps_min=2.0), tile_capacity=caps[3], **empty)
+    tau = tau_fs * OMEGA0_PER_FS
+    laser = dict(a0=a0, tau_fwhm=tau, w0_spot=w0_lambda * 2.0 * math.pi, t_peak=1.5 * tau,
+                 y_c=0.5 * (n - 1), z_c=0.5 * (n - 1), x_src=4, pol=1)
+    return dict(grid=dict(nx=n, ny=n, nz=n, dx=dx, cfl_frac=0.95, bc=(1, 1, 1)), laser=laser,
+                species=[electrons, ions, photons, positrons])

@@ -257,7 +257,8 @@ class Simulation:
                 "n_emit": out.n_emit, "n_pair": out.n_pair,
                 "w_fluid": [out.w_fluid[i] for i in range(out.n_fluids)],
                 "n_fluid": [out.n_fluid[i] for i in range(out.n_fluids)], "n_clamped": out.n_clamped,
-                "launches_classify": out.launches_classify}
+                "launches_classify": out.launches_classify,
+                "tile_capacity": [out.tile_capacity[i] for i in range(ns)]}
 
     def eval_qed(self, what, chi, r=None):
         """Evaluate the device QED tables (see hyb_eval_qed)."""

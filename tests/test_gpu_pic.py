@@ -157,3 +157,31 @@ def test_full_size_periodic_plasma_100_steps():
     sim.step(100)
     orc.step(100)
     _fields_close(sim, orc, 1e-4)
+
+
+def test_tiles_grow_when_they_fill_up():
+    """Species loaded at ~80 % of their tile capacity: after the first check the
+    library doubles the slots per tile, keeps every particle and the run stays
+    on the oracle's trajectory."""
+    inp = _plasma(n=16, ppc=8, seed=9, a0=0.5)
+    counts = []
+    for sp in inp["species"]:
+        t = (np.floor(sp["x"]).astype(int) // 8) + 2 * ((np.floor(sp["y"]).astype(int) // 8) +
+                                                         2 * (np.floor(sp["z"]).astype(int) // 8))
+        counts.append(np.bincount(t, minlength=8).max())
+        sp["tile_capacity"] = int(np.ceil(counts[-1] / 0.8 / 32) * 32)
+    sim, orc = make_pair(inp)
+    caps0 = sim.diagnostics()["tile_capacity"]
+    n0 = sim.diagnostics()["count"]
+    for _ in range(6):
+        sim.step(4)
+        orc.step(4)
+    d = sim.diagnostics()
+    assert d["status"] == 0
+    assert d["count"] == n0
+    assert all(c1 >= 2 * c0 for c0, c1 in zip(caps0, d["tile_capacity"]))
+    E, B, _ = sim.get_fields()
+    assert rel_l2(E, orc.E) <= 1e-4 and rel_l2(B, orc.B) <= 1e-4
+    for s in range(2):
+        g = by_id(sim.get_species(s))
+        assert np.array_equal(np.sort(g["ids"]), np.sort(orc.species[s].ids))
