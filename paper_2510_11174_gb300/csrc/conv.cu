@@ -6,8 +6,10 @@
 // k_conv3_tc: implicit GEMM on the 5th-generation tensor cores, persistent
 // and warp-specialised.  A CTA owns output tiles of 128 cells = 8 (x) x 16
 // (y) x 1 (z), taken round-robin.  Its input halo (10 x 18 x 3 cells) is
-// fetched by TMA, one 8-channel chunk per copy, into a ring of STAGES
-// shared-memory buffers laid out [chunk][z][y][x][8 channels]; all
+// fetched by TMA, one 16-channel block per copy, into a ring of STAGES
+// shared-memory buffers laid out [block][z][y][x][16 channels] with the
+// 32-byte swizzle (the TMA and the tensor core both apply it to the absolute
+// shared address, so an operand may start at any cell of the halo); all
 // 27 x C_in x C_out weights stay resident in shared memory.
 //   warp 0      TMA producer: waits for a free stage, posts the expected bytes
 //               on the stage's "full" barrier and issues the chunk copies
@@ -20,9 +22,9 @@
 //               TMEM lanes 32 (w % 4) ..), bias, ReLU, Philox dropout with
 //               inverted scaling, BF16 channels-last stores.
 // The operand of tap (dz, dy, dx) is the halo shifted by that tap: the 8
-// cells of one output row are 8 consecutive 16-byte rows (one core matrix),
-// the 16 rows of the tile are 160 bytes apart, the chunks one chunk block
-// apart, so every tap is a plain matrix descriptor -- no im2col copy.
+// cells of one output row are 8 consecutive 32-byte rows (one swizzle atom
+// wide in K), the 16 rows of the tile are 320 bytes apart, so every tap and
+// 16-channel block is a plain K-major SW32 matrix descriptor -- no im2col.
 // Every wait is bounded: a wait that gives up sets ST_TIMEOUT, the roles stop
 // issuing work, copies and MMAs in flight are waited for (bounded) and TMEM
 // is released.
@@ -40,8 +42,8 @@ namespace hyb {
 static constexpr int TX = 8, TY = 16;                 // output tile (cells)
 static constexpr int HX = TX + 2, HY = TY + 2, HZ = 3; // halo
 static constexpr int HCELLS = HX * HY * HZ;            // 540
-static constexpr int CHB = HCELLS * 16;                // bytes one chunk copy writes (8640)
-static constexpr int CHBP = (CHB + 127) / 128 * 128;   // chunk block pitch in shared memory (8704)
+static constexpr int CHB = HCELLS * 32;                // bytes one 16-channel copy writes (17280)
+static constexpr int CHBP = (CHB + 1023) / 1024 * 1024; // block pitch in shared memory (17408)
 static constexpr int STAGES = 3;
 static constexpr int NTHREADS = 192;
 static constexpr long long MBAR_LIMIT = 1LL << 26;     // polls before a wait gives up
@@ -60,8 +62,9 @@ __host__ __device__ inline bool dropout_keep(uint32_t seed, uint32_t pass, uint3
 template <int KC, int N>
 struct ConvCfg {
     static constexpr int WBYTES = 27 * KC * N * 16;    // weights, core layout [27][KC][N][8]
-    static constexpr int STAGE = KC * CHBP;            // one halo buffer
-    static constexpr int SMEM = WBYTES + STAGES * STAGE + 1024;  // + alignment slack
+    static constexpr int RING = (WBYTES + 1023) / 1024 * 1024;  // halo ring offset (swizzle-aligned)
+    static constexpr int STAGE = (KC / 2) * CHBP;      // one halo buffer (16-channel blocks)
+    static constexpr int SMEM = RING + STAGES * STAGE + 1024;  // + alignment slack
     static constexpr int TCOLS = 2 * N < 32 ? 32 : 2 * N;        // two accumulators
 };
 
@@ -72,7 +75,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv3_tc(const __grid_constant_
     // 1024-byte aligned base: weights first, then the halo ring
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t *wsm = smem;
-    uint8_t *ring = smem + Cfg::WBYTES;
+    uint8_t *ring = smem + Cfg::RING;
     __shared__ __align__(8) uint64_t full_b[STAGES], empty_b[STAGES], tfull_b[2], tempty_b[2], done_b;
     __shared__ uint32_t taddr_s;
     __shared__ int abort_s;
@@ -128,11 +131,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv3_tc(const __grid_constant_
                 const int z0 = (int)((tile / ((long long)tiles_x * tiles_y)) % a.D);
                 const int b = (int)(tile / ((long long)tiles_x * tiles_y * a.D));
                 const uint32_t fb = smem_u32(&full_b[s]);
-                mbar_arrive_expect_tx(fb, KC * CHB);
+                mbar_arrive_expect_tx(fb, (KC / 2) * CHB);
                 const uint32_t dst = ring_s + (uint32_t)(s * Cfg::STAGE);
 #pragma unroll
-                for (int c = 0; c < KC; ++c)
-                    tma_load_5d(dst + (uint32_t)(c * CHBP), &tmap, 8 * c, tx * TX - 1, ty * TY - 1, z0 - 1, b, fb);
+                for (int c = 0; c < KC / 2; ++c)
+                    tma_load_5d(dst + (uint32_t)(c * CHBP), &tmap, 16 * c, tx * TX - 1, ty * TY - 1, z0 - 1, b, fb);
                 ++issued;
                 if (++s == STAGES) {
                     s = 0;
@@ -154,7 +157,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv3_tc(const __grid_constant_
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
             constexpr uint32_t idesc = idesc_bf16(128, N);
-            const uint64_t a0 = smem_desc(ring_s, CHBP, HX * 16);
+            const uint64_t a0 = smem_desc_sw32(ring_s, HX * 32);
             const uint64_t b0 = smem_desc(w_s, N * 16, 128);
             int s = 0;
             uint32_t ph = 0;
@@ -174,10 +177,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv3_tc(const __grid_constant_
 #pragma unroll
                 for (int tap = 0; tap < 27; ++tap) {
                     const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
-                    const uint32_t toff = (uint32_t)(((dz * HY + dy) * HX + dx) * 16);
+                    const uint32_t toff = (uint32_t)(((dz * HY + dy) * HX + dx) * 32);
 #pragma unroll
                     for (int kk = 0; kk < KC / 2; ++kk) {
-                        const uint64_t ad = as + (uint64_t)((toff + (uint32_t)(2 * kk * CHBP)) >> 4);
+                        const uint64_t ad = as + (uint64_t)((toff + (uint32_t)(kk * CHBP)) >> 4);
                         const uint64_t bd = b0 + (uint64_t)(((tap * KC + 2 * kk) * N * 16) >> 4);
                         umma_bf16(d, ad, bd, idesc, (tap | kk) != 0);
                     }
@@ -297,10 +300,10 @@ static hyb_status make_tmap(CUtensorMap *tm, const ConvArgs &a) {
     const cuuint64_t es = 2;
     const cuuint64_t strides[4] = {es * a.cin, es * a.cin * a.W, es * a.cin * a.W * a.H,
                                    es * a.cin * a.W * a.H * a.D};
-    const cuuint32_t box[5] = {8, (cuuint32_t)HX, (cuuint32_t)HY, (cuuint32_t)HZ, 1};
+    const cuuint32_t box[5] = {16, (cuuint32_t)HX, (cuuint32_t)HY, (cuuint32_t)HZ, 1};
     const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
     CUresult r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, (void *)a.x, dims, strides, box, estr,
-                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return set_error(HYB_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
     return HYB_OK;

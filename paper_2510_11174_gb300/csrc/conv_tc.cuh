@@ -28,6 +28,20 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
     return d;
 }
 
+// K-major operand with the 32-byte swizzle (layout type 6 in [61,64)): rows
+// of 32 bytes (16 BF16 along K), 8-row groups `sbo` bytes apart; the swizzle
+// is taken from the absolute shared address (base offset 0), so the start may
+// be any 32-byte row, not only a swizzle-pattern boundary
+__device__ __forceinline__ uint64_t smem_desc_sw32(uint32_t addr, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr >> 4) & 0x3FFFu);
+    d |= (uint64_t)1 << 16;  // leading byte offset: unused when K fits the swizzle width
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)6 << 61;
+    return d;
+}
+
 // instruction descriptor for kind::f16: FP32 accumulator (bits [4,6) = 1),
 // BF16 A and B (bits [7,10) = 1, [10,13) = 1), both K-major, N>>3 in
 // [17,23), M>>4 in [24,29)
