@@ -137,6 +137,10 @@ FDTD_BYTES_PER_CELL = 120
 # cold fluid: read n, n u (16 B) + write (16 B) per node and fluid, + E, B read (24 B) per node
 FLUID_BYTES_PER_NODE = 32
 FLUID_FIELD_BYTES_PER_NODE = 24
+# DRAM read + write per cell of one launch of the 32 -> 32 convolution, from
+# the ncu capture on the 128 x 128 x 64 ramp + slab (67.2 + 22.4 MB for
+# 1,048,576 cells); scaled to a full launch by the cell count
+NCU_CONV_L1_BYTES_PER_CELL = 89.6e6 / 1048576
 
 
 def make_model(P, stream):
@@ -324,6 +328,9 @@ def run_ours(args, rank, world):
         r["frac"] = r["achieved"] / r["peak"]
         r["peak_kind"] = "measured" if peaks else "fallback"
         r["traffic"] = None
+    if "conv_l1" in roofs:
+        roofs["conv_l1"]["traffic"] = NCU_CONV_L1_BYTES_PER_CELL * cells
+        roofs["conv_l1"]["traffic_note"] = "ncu dram bytes of a 128x128x64 launch scaled by cells"
     # the dominant single kernel (the classification as a whole is reported beside it)
     dom = max((k for k in roofs if k != "classify"), key=lambda k: roofs[k]["share"])
 
