@@ -52,6 +52,8 @@ def workloads():
         "ramp_slab_256x256x128": ("hybrid", lambda seed: inputs.ramp_slab(seed=seed + 2)),
         # the same recipe at 1/8 of the cells (quick checks)
         "ramp_slab_128x128x64": ("hybrid", lambda seed: inputs.ramp_slab(nx=128, ny=128, nz=64, seed=seed + 2)),
+        # laser-parameter scan: 32 independent hybrid runs of uneven grids 64..128 per axis
+        "scan_32": ("scan", lambda seed: inputs.scan_runs(32, seed=seed + 4)),
     }
 
 
@@ -152,11 +154,12 @@ def make_model(P, stream):
     return m
 
 
-def make_sim(P, inp, stream, policy="union"):
+def make_sim(P, inp, stream, policy="union", model=None):
     """Context for a workload.  Hybrid workloads get their fluids, the regime
     settings and one classification (which creates the particles of the
     kinetic cells; policy "all_kinetic" turns every fluid node into
-    particles: the full-PIC run)."""
+    particles: the full-PIC run).  `model`: a classifier to share (else a
+    new one)."""
     g = inp["grid"]
     sim = P.Simulation(g["nx"], g["ny"], g["nz"], g["dx"], cfl_frac=g["cfl_frac"], bc=g["bc"],
                        laser=inp.get("laser"), stream=stream)
@@ -169,10 +172,10 @@ def make_sim(P, inp, stream, policy="union"):
     model = None
     if inp.get("fluids"):
         sim.set_regime(dilate=2, ppc=inp["ppc"], to_species=list(range(len(inp["fluids"]))), policy=policy)
-        if policy != "all_kinetic":
+        if policy != "all_kinetic" and model is None:
             model = make_model(P, stream)
-        sim.classify(model)
-    return sim, model
+        sim.classify(model if policy != "all_kinetic" else None)
+    return sim, (model if policy != "all_kinetic" else None)
 
 
 def count_particles(inp):
@@ -261,6 +264,8 @@ def run_ours(args, rank, world):
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     kind, gen = workloads()[args.workload]
+    if kind == "scan":
+        return run_scan(args, P, torch)
     inp = gen(1 + rank)
     g = inp["grid"]
     cells = g["nx"] * g["ny"] * g["nz"]
@@ -378,6 +383,67 @@ def run_ours(args, rank, world):
     return out
 
 
+def run_scan(args, P, torch):
+    """Batched scan: every run advanced by one graph per step (hyb_batch)
+    against the same runs advanced one after another on the same stream.
+    One cycle = N_CLS steps of every run + one classification of every run;
+    also timed without the classifications."""
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    runs = workloads()[args.workload][1](1)
+    model = make_model(P, stream.cuda_stream)
+    sims = [make_sim(P, inp, stream.cuda_stream, "union", model)[0] for inp in runs]
+    cells = sum(s.N for s in sims)
+    batch = P.Batch(sims, stream)
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+
+    def cycle(batched, classify):
+        if batched:
+            batch.step(N_CLS)
+        else:
+            for s in sims:
+                s.step(N_CLS)
+        if classify:
+            for s in sims:
+                s.classify(model)
+
+    out = {}
+    for classify in (False, True):
+        for batched in (False, True):
+            cycle(batched, classify)           # warm-up (captures, batch graph)
+            torch.cuda.synchronize()
+            e0, e1 = ev(), ev()
+            e0.record(stream)
+            ncyc = max(1, args.steps // N_CLS)
+            for _ in range(ncyc):
+                cycle(batched, classify)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            key = ("batched" if batched else "sequential") + ("_with_classification" if classify else "_steps_only")
+            out[key] = {"ms_per_step": ms / (ncyc * N_CLS), "cell_steps_per_s": cells * ncyc * N_CLS / (ms * 1e-3)}
+    bad = [(i, runs[i]["a0"], s.diagnostics(raise_on_status=False)["tile_capacity"])
+           for i, s in enumerate(sims) if s.diagnostics(raise_on_status=False)["status"] != 0]
+    if bad:
+        raise RuntimeError("scan runs in an error state (run, a0, tile capacity): %s" % bad)
+    batch.close()
+    for s in sims:
+        s.close()
+    model.close()
+    res = {"metric": METRIC, "value": out["batched_with_classification"]["cell_steps_per_s"],
+           "unit": "cell-steps/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": out["batched_with_classification"]["ms_per_step"], "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded)",
+           "config": {"workload": args.workload, "runs": len(runs), "cells": cells,
+                      "grids": [[r["grid"]["nx"], r["grid"]["ny"], r["grid"]["nz"]] for r in runs]},
+           "scan": out,
+           "batch_speedup_steps_only": out["sequential_steps_only"]["ms_per_step"] /
+                                       out["batched_steps_only"]["ms_per_step"],
+           "batch_speedup_with_classification": out["sequential_with_classification"]["ms_per_step"] /
+                                                out["batched_with_classification"]["ms_per_step"]}
+    return res
+
+
 def run_e2e(P, inp, steps, stream):
     """Whole job through the public API from pinned host buffers: create the
     context, upload the initial state (particles or fluids, fields), classify,
@@ -449,11 +515,13 @@ def oracle_sample(workload):
         inp = gen(1)
         ratio, what = 1.0, "the full %s workload" % workload
     else:
-        full = gen(1)["grid"]
+        first = gen(1) if kind == "hybrid" else gen(1)[0]   # a scan is sampled through its first run
+        full = first["grid"]
         from paper_2510_11174_gb300 import inputs
-        inp = inputs.ramp_slab(nx=full["nx"], ny=16, nz=16, seed=3, a0=gen(1)["a0"])
+        inp = inputs.ramp_slab(nx=full["nx"], ny=16, nz=16, seed=3, a0=first["a0"])
         ratio = full["nx"] * full["ny"] * full["nz"] / float(inp["grid"]["nx"] * 16 * 16)
-        what = "a %dx16x16 cross-section of %s (1/%d of its cells)" % (full["nx"], workload, round(ratio))
+        what = "a %dx16x16 cross-section of %s%s (1/%d of its cells)" % (
+            full["nx"], "the first run of " if kind == "scan" else "", workload, round(ratio))
     g = inp["grid"]
     o = S.OracleSim(g["nx"], g["ny"], g["nz"], g["dx"], cfl_frac=g["cfl_frac"], bc=g["bc"], laser=inp.get("laser"))
     for sp in inp["species"]:
@@ -502,6 +570,11 @@ def run_oracle_sample(workload, budget_s=15.0, max_steps=None):
         n += 1
     dt = time.perf_counter() - t0
     cores = 1 if net is None else oracle_threads()
+    if workloads()[workload][0] == "scan":
+        # the scan's metric is cell-steps/s, the same per cell for the sample
+        return {"value": n / dt * o.g.nx * o.g.ny * o.g.nz, "unit": "cell-steps/s", "cores": cores,
+                "kind": "oracle", "sample": "%d steps of %s (%d particles at the start)" % (n, what, parts),
+                "particle_pushes_per_s": n * parts / dt}
     return {"value": n / dt / ratio, "unit": "steps/s", "cores": cores, "kind": "oracle",
             "sample": "%d steps of %s (%d particles at the start), FP64 C single-threaded; classifier convolutions "
                       "in PyTorch CPU on %d threads; steps/s divided by %g" % (n, what, parts, oracle_threads(),
@@ -521,19 +594,24 @@ def run_reference(args, rank, world):
     oracle_advance(o, net, args.steps, args.warmup)
     dt = time.perf_counter() - t0
     parts = 0.5 * (parts0 + sum(sp.n for sp in o.species))
+    unit = "steps/s"
     v = args.steps / dt / ratio
-    g = workloads()[args.workload][1](1)["grid"]
+    if workloads()[args.workload][0] == "scan":
+        unit, v = "cell-steps/s", args.steps / dt * o.g.nx * o.g.ny * o.g.nz
+    wl = workloads()[args.workload][1](1)
+    g = (wl[0] if isinstance(wl, list) else wl)["grid"]
     cores = 1 if net is None else oracle_threads()
     sample = ("%d timed steps (after %d warm-up) of %s; FP64 C single-threaded, classifier convolutions in PyTorch "
               "CPU on %d threads; value = sample steps/s / %g" % (args.steps, args.warmup, what, oracle_threads(),
                                                                    ratio))
-    return {"metric": METRIC, "value": v, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 / v, "higher_is_better": True, "scaling": "weak",
+    return {"metric": METRIC, "value": v, "unit": unit, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 / v if unit == "steps/s" else 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)", "impl": "reference",
             "config": {"workload": args.workload, "grid": [g["nx"], g["ny"], g["nz"]]},
             "particle_pushes_per_s_sample": parts * args.steps / dt,
-            "cpu_baseline": {"value": v, "unit": "steps/s", "cores": cores, "kind": "oracle", "sample": sample},
-            "e2e": {"value": v, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "cpu_baseline": {"value": v, "unit": unit, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
 def main():

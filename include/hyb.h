@@ -197,7 +197,9 @@ hyb_status hyb_load_species(hyb_ctx *ctx, const hyb_species_desc *desc, int *spe
  * (electron fluid), or kappa gamma |E| >= chi_thr; the mask is then dilated by
  * `dilate` nodes.  With a classifier, a node is kinetic when
  * p_mean + k_sigma p_std >= 0.5 (same dilation).  Conversions: fluid f at
- * kinetic nodes becomes ppc macro-particles of species to_species[f]
+ * nodes that switch to kinetic (kinetic now, fluid at the previous
+ * classification; every node counts as fluid before the first one) becomes
+ * ppc macro-particles of species to_species[f]
  * (Philox-uniform in the node's dual cell, the fluid's u, weight n dV / ppc);
  * particles of species to_species[f] whose nearest node is fluid are
  * deposited (CIC) into fluid f.  A residual background charge keeps
@@ -320,12 +322,28 @@ hyb_status hyb_set_fields(hyb_ctx *ctx, const float *E, const float *B, int on_d
 /* Advance n steps (stream-ordered; the step sequence is captured once into a
  * CUDA graph and replayed).  Tiles have a fixed number of slots per species;
  * every 4 steps the compaction's fill flags travel to the host behind the
- * steps (the host never runs more than 8 steps ahead of the last flags it
- * read), and once a species' tiles have passed 3/4 of their slots hyb_step
+ * steps (the host never runs more than 4 steps ahead of the last flags it
+ * read), and once a species' tiles have passed half of their slots hyb_step
  * synchronises and doubles that species' slots per tile (its particles are
  * copied tile by tile) before the next steps.  A tile that overflows before
  * that drops particles and latches HYB_EOVERFLOW. */
 hyb_status hyb_step(hyb_ctx *ctx, int nsteps);
+
+/* Batches of independent runs (many laser and plasma parameters, uneven grids,
+ * advanced together).  A batch replays the captured step of each of its
+ * contexts as one CUDA graph whose branches do not depend on each other, so
+ * the GPU runs small grids side by side.  hyb_batch_step(b, n) advances every
+ * context by n steps on the batch's stream (`stream`, or a stream of its own
+ * when NULL): it first waits for the work already queued on each context's
+ * stream and leaves each context's stream waiting for the batch, so calls on
+ * a context before and after stay ordered.  Capacity growth works as in
+ * hyb_step.  Contexts must be distinct and on the current device; a context
+ * may belong to several batches but must not be stepped by two at once.  The
+ * batch does not own its contexts: destroy it before them. */
+typedef struct hyb_batch hyb_batch;
+hyb_status hyb_batch_create(hyb_ctx *const *ctxs, int n, void *stream, hyb_batch **out);
+hyb_status hyb_batch_step(hyb_batch *batch, int nsteps);
+void hyb_batch_destroy(hyb_batch *batch);
 
 /* Synchronises; fills *out. */
 hyb_status hyb_diagnostics(hyb_ctx *ctx, hyb_diag *out);

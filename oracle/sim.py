@@ -101,7 +101,7 @@ class OracleSim:
         self.regime = dict(a_thr=1.0, n_thr=1.0, c_thr=0.1, chi_thr=1e-3, dilate=2, k_sigma=1.0, ppc=8,
                            to_species=[], policy="default")
         self.epoch = 0
-        self.mask = np.ones(self.g.shape, dtype=np.uint8)
+        self.mask = np.zeros(self.g.shape, dtype=np.uint8)   # every node fluid before a classification
         self.rho_bg = np.zeros(self.g.shape)
 
     def load_species(self, q, m, x, y, z, ux, uy, uz, w, zq=None, ids=None, ionize=None, kind=0, qed=None,
@@ -139,7 +139,8 @@ class OracleSim:
         electron macro-particles) and the first electron fluid's velocity,
         and/or the classifier's MC-dropout decision p_mean + k_sigma p_std >=
         0.5 on the node fields, each dilated; then per fluid f the fluid at
-        kinetic nodes becomes macro-particles of species to_species[f] and
+        nodes that switch to kinetic (kinetic now, fluid at the previous
+        classification) becomes macro-particles of species to_species[f] and
         that species' particles whose nearest node is fluid go back into f.
         Returns (p_mean, p_std) of the classifier, or (None, None).  A given
         `mask` (1 = kinetic) replaces the decision: the conversions alone."""
@@ -180,7 +181,9 @@ class OracleSim:
             sid = ts[f] if f < len(ts) else -1
             if sid is None or sid < 0:
                 continue
-            new = fluid_to_particles(g, mask, fl, r["ppc"], self.seed, sid, self.epoch, self.rho_bg)
+            switched = (mask != 0) & (self.mask == 0)
+            new = fluid_to_particles(g, switched.astype(np.uint8), fl, r["ppc"], self.seed, sid, self.epoch,
+                                     self.rho_bg)
             dst = self.species[sid]
             if dst.tau is not None:
                 new.tau = qed_tau0(new.ids, self.seed, sid)

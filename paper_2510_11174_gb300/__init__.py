@@ -5,5 +5,5 @@ include/hyb.h); this package is its thin Python binding plus seeded input
 generators.
 """
 from ._abi import HybError, load  # noqa: F401
-from .sim import Simulation  # noqa: F401
+from .sim import Batch, Simulation  # noqa: F401
 from .model import Classifier  # noqa: F401

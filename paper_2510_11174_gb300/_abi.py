@@ -128,6 +128,9 @@ PROTOTYPES = {
     "hyb_train_step": (C.c_int, [_P, _P, _P, C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(hyb_train_stats)]),
     "hyb_model_get_grad": (C.c_int, [_P, C.c_int, _P, _P]),
     "hyb_get_fluid": (C.c_int, [_ctx, C.c_int, _P, _P, _P, _P]),
+    "hyb_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, _P, C.POINTER(C.c_void_p)]),
+    "hyb_batch_step": (C.c_int, [_P, C.c_int]),
+    "hyb_batch_destroy": (None, [_P]),
     "hyb_field_energy_noalloc":(C.c_int, [_P, _P, C.c_longlong, C.c_double, C.c_double, C.c_double, _P, _P]),
 }
 

@@ -221,6 +221,7 @@ hyb_status hyb_init_grid(const hyb_grid_desc *d, hyb_ctx **out) {
         ctx_alloc(c, (void **)&c->fill_flags, sizeof(int)) ||
         ctx_alloc(c, (void **)&c->sp_dev, sizeof(SpDev) * HYB_MAX_SPECIES) ||
         ctx_alloc(c, (void **)&c->mask, (size_t)g.N) || ctx_alloc(c, (void **)&c->mask_tmp, (size_t)g.N) ||
+        ctx_alloc(c, (void **)&c->mask_prev, (size_t)g.N) ||
         ctx_alloc(c, (void **)&c->rho_bg, sizeof(float) * (size_t)g.N) ||
         ctx_alloc(c, (void **)&c->ne, sizeof(float) * (size_t)g.N))
         return fail(HYB_ENOMEM, "device allocation for the grid failed (arena too small?)");
@@ -231,7 +232,7 @@ hyb_status hyb_init_grid(const hyb_grid_desc *d, hyb_ctx **out) {
     cudaMemsetAsync(c->mur_old, 0, sizeof(float) * 24 * (size_t)c->mur_plane, st);
     cudaMemsetAsync(c->status, 0, sizeof(int), st);
     cudaMemsetAsync(c->step_dev, 0, sizeof(long long), st);
-    cudaMemsetAsync(c->mask, 1, (size_t)g.N, st);  // everything kinetic until a classification
+    cudaMemsetAsync(c->mask, 0, (size_t)g.N, st);  // no node has switched to kinetic before a classification
     cudaMemsetAsync(c->fill_flags, 0, sizeof(int), st);
     if (cudaMallocHost((void **)&c->fill_host, sizeof(int)) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->fill_ev, cudaEventDisableTiming) != cudaSuccess)
@@ -273,6 +274,7 @@ void hyb_destroy(hyb_ctx *c) {
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
     if (c->graph) cudaGraphExecDestroy(c->graph);
+    if (c->graph_tmpl) cudaGraphDestroy(c->graph_tmpl);
     for (cudaEvent_t e : c->conv_ev) cudaEventDestroy(e);
     for (int p = 0; p < HYB_NPHASE; ++p) {
         if (c->ev_start[p]) cudaEventDestroy(c->ev_start[p]);
@@ -705,21 +707,29 @@ static hyb_status capture_step(hyb_ctx *c) {
         cudaGraphExecDestroy(c->graph);
         c->graph = nullptr;
     }
+    if (c->graph_tmpl) {
+        cudaGraphDestroy(c->graph_tmpl);
+        c->graph_tmpl = nullptr;
+    }
     cudaGraph_t graph;
     HYB_CUDA_TRY(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
     enqueue_step(c);
     HYB_CUDA_TRY(cudaStreamEndCapture(c->stream, &graph));
     cudaError_t e = cudaGraphInstantiate(&c->graph, graph, 0);
-    cudaGraphDestroy(graph);
-    if (e != cudaSuccess) return set_error(HYB_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        return set_error(HYB_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    }
+    c->graph_tmpl = graph;
+    c->graph_version += 1;
     c->graph_valid = true;
     return HYB_OK;
 }
 
-// Capacity growth: a species whose tiles passed 3/4 of their capacity (flag
+// Capacity growth: a species whose tiles passed half of their capacity (flag
 // set by the compaction or a conversion) gets twice the slots per tile before
 // the next steps; its live particles are copied tile by tile.
-static hyb_status grow_full_species(hyb_ctx *c, bool wait) {
+static hyb_status grow_full_species(hyb_ctx *c, bool wait, cudaStream_t steps_stream = nullptr) {
     if (!c->fill_pending) return HYB_OK;
     const cudaError_t q = wait ? cudaEventSynchronize(c->fill_ev) : cudaEventQuery(c->fill_ev);
     if (q == cudaErrorNotReady) return HYB_OK;
@@ -727,6 +737,7 @@ static hyb_status grow_full_species(hyb_ctx *c, bool wait) {
     c->fill_pending = false;
     const int flags = *c->fill_host;
     if (!flags) return HYB_OK;
+    if (steps_stream) HYB_CUDA_TRY(cudaStreamSynchronize(steps_stream));
     HYB_CUDA_TRY(cudaStreamSynchronize(c->stream));
     for (size_t sid = 0; sid < c->sp.size(); ++sid) {
         if (!(flags & (1 << sid))) continue;
@@ -763,7 +774,7 @@ hyb_status hyb_step(hyb_ctx *c, int nsteps) {
     for (int done = 0; done < nsteps;) {
         if (c->auto_grow) {
             // the host may run ahead of the flags by at most two check intervals
-            hyb_status gs = grow_full_species(c, c->steps_since_copy >= 2 * GROW_CHECK_STEPS);
+            hyb_status gs = grow_full_species(c, c->steps_since_copy >= GROW_CHECK_STEPS);
             if (gs != HYB_OK) return gs;
         }
         if (!c->graph_valid) {
@@ -784,6 +795,137 @@ hyb_status hyb_step(hyb_ctx *c, int nsteps) {
             c->steps_since_copy = 0;
         }
     }
+    return HYB_OK;
+}
+
+}  // extern "C"
+
+// A batch replays the captured steps of several contexts as one CUDA graph
+// whose branches (one child graph per context) have no dependencies between
+// them, so small runs share the GPU instead of queueing behind each other.
+struct hyb_batch {
+    std::vector<hyb_ctx *> ctx;
+    std::vector<unsigned> version;      // graph_version of each context when the batch graph was built
+    std::vector<cudaEvent_t> ctx_ev;    // orders the batch after each context's earlier work
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cudaEvent_t done = nullptr;         // orders each context's later work after the batch
+};
+
+static hyb_status batch_build(hyb_batch *b) {
+    if (b->exec) {
+        cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+    }
+    cudaGraph_t parent;
+    HYB_CUDA_TRY(cudaGraphCreate(&parent, 0));
+    for (size_t i = 0; i < b->ctx.size(); ++i) {
+        cudaGraphNode_t node;
+        const cudaError_t e = cudaGraphAddChildGraphNode(&node, parent, nullptr, 0, b->ctx[i]->graph_tmpl);
+        if (e != cudaSuccess) {
+            cudaGraphDestroy(parent);
+            return set_error(HYB_ECUDA, std::string("batch graph: ") + cudaGetErrorString(e));
+        }
+        b->version[i] = b->ctx[i]->graph_version;
+    }
+    const cudaError_t e = cudaGraphInstantiate(&b->exec, parent, 0);
+    cudaGraphDestroy(parent);
+    if (e != cudaSuccess) return set_error(HYB_ECUDA, std::string("batch instantiate: ") + cudaGetErrorString(e));
+    return HYB_OK;
+}
+
+extern "C" {
+
+hyb_status hyb_batch_create(hyb_ctx *const *ctxs, int n, void *stream, hyb_batch **out) {
+    if (!ctxs || n <= 0 || !out) return set_error(HYB_EINVAL, "bad argument");
+    *out = nullptr;
+    for (int i = 0; i < n; ++i) {
+        if (!ctxs[i]) return set_error(HYB_EINVAL, "null context in a batch");
+        for (int j = 0; j < i; ++j)
+            if (ctxs[j] == ctxs[i]) return set_error(HYB_EINVAL, "a context appears twice in a batch");
+    }
+    hyb_batch *b = new hyb_batch();
+    b->ctx.assign(ctxs, ctxs + n);
+    b->version.assign(n, 0);
+    b->ctx_ev.assign(n, nullptr);
+    bool ok = true;
+    if (stream) {
+        b->stream = (cudaStream_t)stream;
+    } else {
+        ok = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) == cudaSuccess;
+        b->own_stream = ok;
+    }
+    for (int i = 0; ok && i < n; ++i) ok = cudaEventCreateWithFlags(&b->ctx_ev[i], cudaEventDisableTiming) == cudaSuccess;
+    if (ok) ok = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        hyb_batch_destroy(b);
+        return set_error(HYB_ECUDA, "batch stream or events");
+    }
+    *out = b;
+    return HYB_OK;
+}
+
+void hyb_batch_destroy(hyb_batch *b) {
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    for (cudaEvent_t e : b->ctx_ev)
+        if (e) cudaEventDestroy(e);
+    if (b->done) cudaEventDestroy(b->done);
+    if (b->own_stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+hyb_status hyb_batch_step(hyb_batch *b, int nsteps) {
+    if (!b || nsteps < 0) return set_error(HYB_EINVAL, "bad argument");
+    if (nsteps == 0) return HYB_OK;
+    const size_t n = b->ctx.size();
+    for (hyb_ctx *c : b->ctx) {
+        if (c->error_latched) return set_error(HYB_ESTATE, "a context of the batch is in an error state");
+        if (!c->graph_valid) {
+            hyb_status lv = validate_links(c);
+            if (lv != HYB_OK) return lv;
+        }
+    }
+    for (size_t i = 0; i < n; ++i) {
+        HYB_CUDA_TRY(cudaEventRecord(b->ctx_ev[i], b->ctx[i]->stream));
+        HYB_CUDA_TRY(cudaStreamWaitEvent(b->stream, b->ctx_ev[i], 0));
+    }
+    for (int done = 0; done < nsteps;) {
+        bool rebuild = b->exec == nullptr;
+        for (size_t i = 0; i < n; ++i) {
+            hyb_ctx *c = b->ctx[i];
+            if (c->auto_grow) {
+                hyb_status gs = grow_full_species(c, c->steps_since_copy >= GROW_CHECK_STEPS, b->stream);
+                if (gs != HYB_OK) return gs;
+            }
+            if (!c->graph_valid) {
+                hyb_status cs = capture_step(c);
+                if (cs != HYB_OK) return cs;
+            }
+            rebuild = rebuild || b->version[i] != c->graph_version;
+        }
+        if (rebuild) {
+            hyb_status bs = batch_build(b);
+            if (bs != HYB_OK) return bs;
+        }
+        const int chunk = std::min(nsteps - done, GROW_CHECK_STEPS);
+        for (int k = 0; k < chunk; ++k) HYB_CUDA_TRY(cudaGraphLaunch(b->exec, b->stream));
+        done += chunk;
+        for (hyb_ctx *c : b->ctx) {
+            c->step += chunk;
+            c->steps_since_copy += chunk;
+            if (c->auto_grow && !c->fill_pending && c->steps_since_copy >= GROW_CHECK_STEPS) {
+                HYB_CUDA_TRY(cudaMemcpyAsync(c->fill_host, c->fill_flags, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+                HYB_CUDA_TRY(cudaEventRecord(c->fill_ev, b->stream));
+                c->fill_pending = true;
+                c->steps_since_copy = 0;
+            }
+        }
+    }
+    HYB_CUDA_TRY(cudaEventRecord(b->done, b->stream));
+    for (hyb_ctx *c : b->ctx) HYB_CUDA_TRY(cudaStreamWaitEvent(c->stream, b->done, 0));
     return HYB_OK;
 }
 

@@ -112,7 +112,7 @@ struct SpDev {
     // per-tile accumulated tallies, TALLY_* entries per tile
     double *tal_e;
     unsigned long long *tal_n;
-    // bit sp_index is set when a tile of this species passed 3/4 of its capacity
+    // bit sp_index is set when a tile of this species passed half of its capacity
     int *fill_flags;
 };
 
@@ -192,7 +192,7 @@ struct hyb_ctx {
     int *status = nullptr;                           // device status word
     long long *step_dev = nullptr;                   // device step counter (read by graph replays)
     int *mig_counts = nullptr;                       // HYB_MAX_SPECIES migration counters
-    int *fill_flags = nullptr;                       // device: species whose tiles passed 3/4 of their capacity
+    int *fill_flags = nullptr;                       // device: species whose tiles passed half of their capacity
     int *fill_host = nullptr;                        // pinned copy of fill_flags (read without a sync)
     cudaEvent_t fill_ev = nullptr;                   // marks the copy into fill_host
     bool fill_pending = false;                       // a copy into fill_host was enqueued
@@ -207,6 +207,7 @@ struct hyb_ctx {
     // regime switching
     hyb_regime_desc regime = {};
     uint8_t *mask = nullptr, *mask_tmp = nullptr;  // 1 = kinetic
+    uint8_t *mask_prev = nullptr;                  // the mask before the current classification
     float *rho_bg = nullptr;                       // residual background charge
     float *ne = nullptr;                           // electron density scratch
     uint32_t epoch = 0;                            // conversion counter (Philox counter word)
@@ -219,6 +220,8 @@ struct hyb_ctx {
     long long step = 0;
 
     cudaGraphExec_t graph = nullptr;
+    cudaGraph_t graph_tmpl = nullptr;               // the captured step (kept for batches)
+    unsigned graph_version = 0;                     // bumped at every capture
     bool graph_valid = false;
 
     // phase profiling: events recorded at the start of every phase and at the end

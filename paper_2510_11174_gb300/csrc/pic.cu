@@ -575,7 +575,7 @@ __global__ void k_compact(GridDev g, SpDev sp) {
     int n = min(sp.count[t], sp.cap);
     if (hu >= hc) {
         sp.count[t] = n;  // an overflowing append left count above the capacity
-        if (4 * n > 3 * sp.cap) atomicOr(sp.fill_flags, 1 << sp.sp_index);
+        if (2 * n > sp.cap) atomicOr(sp.fill_flags, 1 << sp.sp_index);
         return;
     }
     const long long base = (long long)t * sp.cap;
@@ -599,7 +599,7 @@ __global__ void k_compact(GridDev g, SpDev sp) {
     sp.count[t] = new_n;
     sp.hole_count[t] = 0;
     sp.hole_used[t] = 0;
-    if (4 * new_n > 3 * sp.cap) atomicOr(sp.fill_flags, 1 << sp.sp_index);
+    if (2 * new_n > sp.cap) atomicOr(sp.fill_flags, 1 << sp.sp_index);
 }
 
 // copy every tile's live slots into a species layout with a larger capacity

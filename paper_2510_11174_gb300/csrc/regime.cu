@@ -110,7 +110,7 @@ __global__ void k_clamp_counts(int ntiles, SpDev sp) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= ntiles) return;
     if (sp.count[t] > sp.cap) sp.count[t] = sp.cap;
-    if (4 * sp.count[t] > 3 * sp.cap) atomicOr(sp.fill_flags, 1 << sp.sp_index);
+    if (2 * sp.count[t] > sp.cap) atomicOr(sp.fill_flags, 1 << sp.sp_index);
 }
 
 // max filter of radius r along axis a (Chebyshev dilation is three of these)
@@ -133,11 +133,14 @@ __global__ void k_dilate(GridDev g, int a, int r, const uint8_t *__restrict__ in
 
 // fluid -> particles at kinetic nodes; rho_bg takes (removed fluid charge) -
 // (CIC charge of the new particles)
-__global__ void k_fluid_to_particles(GridDev g, const uint8_t *__restrict__ mask, FluidDev f, SpDev dst, int ppc,
-                                     uint32_t epoch, float *__restrict__ rho_bg, int *__restrict__ status) {
+__global__ void k_fluid_to_particles(GridDev g, const uint8_t *__restrict__ mask, const uint8_t *__restrict__ prev,
+                                     FluidDev f, SpDev dst, int ppc, uint32_t epoch, float *__restrict__ rho_bg,
+                                     int *__restrict__ status) {
     const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= g.N) return;
-    if (!mask[c] || !(f.n[c] > f.n_floor)) return;
+    // only nodes that switch to kinetic now: fluid that flows into a node
+    // that was kinetic already stays fluid there
+    if (!mask[c] || prev[c] || !(f.n[c] > f.n_floor)) return;
     const int nx = g.n[0], ny = g.n[1];
     const int idx[3] = {(int)(c % nx), (int)((c / nx) % ny), (int)(c / ((long long)nx * ny))};
     const float dV = g.d[0] * g.d[1] * g.d[2];
@@ -273,6 +276,7 @@ hyb_status regime_update(hyb_ctx *c, const float *pm, const float *ps) {
     cudaStream_t st = c->stream;
     const hyb_regime_desc &rd = c->regime;
     uint8_t *raw = c->mask_tmp, *mask = c->mask;
+    cudaMemcpyAsync(c->mask_prev, mask, (size_t)g.N, cudaMemcpyDeviceToDevice, st);
     const bool all = rd.policy == HYB_REGIME_ALL_KINETIC;
     const bool physics = !all && (!pm || rd.policy == HYB_REGIME_UNION);
     long long launches = 0;
@@ -311,8 +315,8 @@ hyb_status regime_update(hyb_ctx *c, const float *pm, const float *ps) {
         if (sid < 0 || sid >= (int)c->sp.size()) continue;
         const SpDev &dst = c->sp[sid].dev;
         // the tiles are compact between steps: new particles go straight into them
-        k_fluid_to_particles<<<nblk(g.N), 256, 0, st>>>(g, mask, c->fluids[f], dst, rd.ppc > 0 ? rd.ppc : 8,
-                                                        c->epoch, c->rho_bg, c->status);
+        k_fluid_to_particles<<<nblk(g.N), 256, 0, st>>>(g, mask, c->mask_prev, c->fluids[f], dst,
+                                                        rd.ppc > 0 ? rd.ppc : 8, c->epoch, c->rho_bg, c->status);
         k_clamp_counts<<<(g.ntiles + 255) / 256, 256, 0, st>>>(g.ntiles, dst);
         k_mom_init<<<nblk(g.N), 256, 0, st>>>(g.N, c->fluids[f]);
         k_particles_to_fluid<<<g.ntiles, 256, 0, st>>>(g, mask, dst, c->fluids[f]);

@@ -12,6 +12,8 @@ fraction, Gaussian laser) at the sizes of the benchmark configurations:
   overdense slab, absorbing (Mur) faces, and a Gaussian pulse launched from
   the x_min side with a0 drawn log-uniformly from [10, 300]; the kinetic
   cells receive `ppc` macro-particles per species when they are classified.
+* ``scan_runs`` -- a laser-parameter scan: independent ``ramp_slab`` runs of
+  uneven grids with seeded pulse amplitudes, densities and particle counts.
 * ``carbon_slab`` -- full PIC with ionization and QED: neutral carbon atoms
   (16 per cell) in a slab of atom density n_e,max / 6 (fully ionized it
   holds n_e,max electrons) with a flat top and Gaussian edges, a Gaussian
@@ -168,3 +170,23 @@ def carbon_slab(n=128, cells_per_lambda=20, ppc=16, ne_max=10.0, plateau_lambda=
                  y_c=0.5 * (n - 1), z_c=0.5 * (n - 1), x_src=4, pol=1)
     return dict(grid=dict(nx=n, ny=n, nz=n, dx=dx, cfl_frac=0.95, bc=(1, 1, 1)), laser=laser,
                 species=[electrons, ions, photons, positrons])
+
+
+def scan_runs(n_runs=64, sizes=(64, 80, 96, 112), a0_range=(1.0, 300.0), density_range=(0.01, 2.0),
+              ppc_choices=(8, 12, 16), seed=5):
+    """Independent hybrid runs for a parameter scan: per run nx, ny, nz drawn
+    from `sizes` (multiples of 16), a0 log-uniform in `a0_range`, the ramp +
+    slab profile scaled by a density factor d log-uniform in `density_range`
+    (ramp 0.01 d -> d n_c, slab 5 d n_c), `ppc` from `ppc_choices`; tiles hold
+    three times the particles of a fully kinetic tile (the strongest pulses
+    pile electrons up faster than the tiles grow)."""
+    rng = np.random.default_rng(seed)
+    runs = []
+    for r in range(n_runs):
+        nx, ny, nz = (int(v) for v in rng.choice(sizes, 3))
+        a0 = float(np.exp(rng.uniform(math.log(a0_range[0]), math.log(a0_range[1]))))
+        d = float(np.exp(rng.uniform(math.log(density_range[0]), math.log(density_range[1]))))
+        ppc = int(rng.choice(ppc_choices))
+        runs.append(ramp_slab(nx=nx, ny=ny, nz=nz, n_lo=0.01 * d, n_hi=d, n_slab=5.0 * d, a0=a0, seed=seed + r,
+                              ppc=ppc, tile_capacity=3 * 512 * ppc, vacuum_lambda=1.0, slab_lambda=1.0))
+    return runs

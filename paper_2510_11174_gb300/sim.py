@@ -298,3 +298,35 @@ class Simulation:
         out = {k: v[:n.value] for k, v in arrs.items() if v is not None}
         out["ids"] = ids[:n.value]
         return out
+
+
+class Batch:
+    """Independent Simulations advanced together (hyb_batch_*): one CUDA graph
+    per step with one branch per simulation.  ``stream``: a torch CUDA stream
+    or raw stream handle for the batch (default: the first simulation's)."""
+
+    def __init__(self, sims, stream=None):
+        self._lib = _abi.load()
+        self.sims = list(sims)
+        arr = (C.c_void_p * len(self.sims))(*[s._ctx for s in self.sims])
+        if stream is None:
+            stream = self.sims[0].desc.stream
+        elif not isinstance(stream, int):
+            stream = stream.cuda_stream
+        h = C.c_void_p()
+        check(self._lib.hyb_batch_create(arr, len(self.sims), stream, C.byref(h)))
+        self._b = h
+
+    def step(self, n=1):
+        check(self._lib.hyb_batch_step(self._b, int(n)))
+
+    def close(self):
+        if getattr(self, "_b", None):
+            self._lib.hyb_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -168,3 +168,25 @@ def test_oracle_all_kinetic_classification():
     rho = oracle.charge_density(o.g, o.species[0]) + o.rho_bg
     assert np.max(np.abs(rho - rho0)) <= 1e-12
     assert math.isclose(float(np.sum(o.species[0].w)), float(np.sum(n)) * 0.3 ** 3, rel_tol=1e-12)
+
+
+def test_oracle_converts_only_nodes_that_switch_to_kinetic():
+    """Fluid that flows into a node already kinetic stays fluid: a second
+    classification with the same mask creates no particles, one that adds
+    nodes creates ppc particles at each new node only."""
+    from oracle.sim import OracleSim
+    o = OracleSim(8, 8, 8, 0.3, bc=(1, 1, 1))
+    o.load_species(-1.0, 1.0, *[np.zeros(0, np.float32)] * 7)
+    o.load_fluid(-1.0, 1.0, np.full((8, 8, 8), 0.2), n_floor=0.0)
+    o.set_regime(ppc=2, to_species=[0], dilate=0)
+    m1 = np.zeros((8, 8, 8), np.uint8)
+    m1[2:4, 2:4, 2:4] = 1
+    o.classify(mask=m1)
+    assert o.species[0].n == 2 * 8
+    o.fluids[0].n[m1 == 1] = 0.05             # fluid flowed back into the kinetic nodes
+    o.classify(mask=m1)
+    assert o.species[0].n == 2 * 8 and np.all(o.fluids[0].n[m1 == 1] == 0.05)
+    m2 = m1.copy()
+    m2[5, 5, 5] = 1
+    o.classify(mask=m2)
+    assert o.species[0].n == 2 * 9
