@@ -407,10 +407,14 @@ def run_scan(args, P, torch):
             for s in sims:
                 s.classify(model)
 
+    # warm-up cycles first, so tile growth and graph captures settle before any arm is timed
+    for _ in range(max(1, args.warmup)):
+        cycle(True, True)
+    torch.cuda.synchronize()
     out = {}
     for classify in (False, True):
         for batched in (False, True):
-            cycle(batched, classify)           # warm-up (captures, batch graph)
+            cycle(batched, classify)
             torch.cuda.synchronize()
             e0, e1 = ev(), ev()
             e0.record(stream)

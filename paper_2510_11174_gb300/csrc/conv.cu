@@ -315,13 +315,28 @@ static hyb_status launch_cfg(const ConvArgs &a, cudaStream_t st) {
     CUtensorMap tm;
     hyb_status s = make_tmap(&tm, a);
     if (s != HYB_OK) return s;
-    cudaError_t e = cudaFuncSetAttribute(k_conv3_tc<KC, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
-    if (e != cudaSuccess) return set_error(HYB_ECUDA, std::string("conv smem attribute: ") + cudaGetErrorString(e));
-    int dev = 0, nsm = 0;
+    // per-device launch set-up, done once (its host cost shows on small grids)
+    static std::mutex mu;
+    static int ready_dev[64] = {0}, nsm_dev[64] = {0}, per_sm_dev[64] = {0};
+    int dev = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_conv3_tc<KC, N>, NTHREADS, Cfg::SMEM);
+    if (dev < 0 || dev >= 64) return set_error(HYB_EINVAL, "device index out of range");
+    int nsm, per_sm;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (!ready_dev[dev]) {
+            cudaError_t e = cudaFuncSetAttribute(k_conv3_tc<KC, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 Cfg::SMEM);
+            if (e != cudaSuccess)
+                return set_error(HYB_ECUDA, std::string("conv smem attribute: ") + cudaGetErrorString(e));
+            cudaDeviceGetAttribute(&nsm_dev[dev], cudaDevAttrMultiProcessorCount, dev);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_dev[dev], k_conv3_tc<KC, N>, NTHREADS, Cfg::SMEM);
+            ready_dev[dev] = 1;
+        }
+        nsm = nsm_dev[dev];
+        per_sm = per_sm_dev[dev];
+    }
+    cudaError_t e;
     const long long ntiles = (long long)a.B * a.D * (a.H / TY) * (a.W / TX);
     const long long grid = std::min<long long>(ntiles, (long long)nsm * std::max(per_sm, 1));
     k_conv3_tc<KC, N><<<(unsigned)grid, NTHREADS, Cfg::SMEM, st>>>(tm, a);
