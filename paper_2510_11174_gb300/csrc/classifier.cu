@@ -55,9 +55,9 @@ static cudaError_t m_alloc(hyb_model *m, void **p, size_t bytes) {
     return e;
 }
 
-// forward pack: wt[tap][kc][n][8] = W[n][kc*8+j][tap] (zero for padded channels)
-// transposed: the data gradient is the convolution of dY with W^T flipped:
-// wtT[tap'][kc][ci][8] = W[kc*8+j][ci][26 - tap']
+// forward pack: wt[(dz, dy)][kc][dx n + o][8] = W[o][kc*8+j][tap (dz, dy, dx)]
+// (zero for padded channels); transposed: the data gradient is the
+// convolution of dY with W^T flipped, wtT[...][dx ci + i][8] = W[kc*8+j][i][26 - tap]
 __global__ void k_pack(const float *__restrict__ W, int cin, int cinp, int cout, int transpose,
                        __nv_bfloat16 *__restrict__ out) {
     const int ci_n = transpose ? cout : cinp;  // input channels of the packed conv
@@ -66,7 +66,9 @@ __global__ void k_pack(const float *__restrict__ W, int cin, int cinp, int cout,
     const int total = 27 * KC * n_n * 8;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= total) return;
-    const int j = t % 8, n = (t / 8) % n_n, kc = (t / (8 * n_n)) % KC, tap = t / (8 * n_n * KC);
+    // layout [9 (dz, dy)][KC][3 (dx) x n_n][8]: the three x-taps side by side in N
+    const int j = t % 8, nn = (t / 8) % (3 * n_n), kc = (t / (8 * 3 * n_n)) % KC, tap9 = t / (8 * 3 * n_n * KC);
+    const int dx = nn / n_n, n = nn % n_n, tap = tap9 * 3 + dx;
     const int c = kc * 8 + j;
     float v = 0.0f;
     if (!transpose) {

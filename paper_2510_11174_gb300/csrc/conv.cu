@@ -4,8 +4,15 @@
 // BF16 weights and FP32 accumulation).
 //
 // k_conv3_tc: implicit GEMM on the 5th-generation tensor cores, persistent
-// and warp-specialised.  A CTA owns output tiles of 128 cells = 8 (x) x 16
-// (y) x 1 (z), taken round-robin.  Its input halo (10 x 18 x 3 cells) is
+// and warp-specialised.  The three x-taps of the stencil go into the N
+// dimension: for each of the 9 (dz, dy) taps one tcgen05.mma multiplies the
+// 128 input cells of a 16 (x) x 8 (y) x 1 (z) block, shifted by (dz, dy), by
+// the weights of all three x-taps side by side (N = 3 C_out), so every A tile
+// read from shared memory feeds three times the math (the A-operand fetch,
+// not the math, limits narrow layers).  The epilogue adds the three partial
+// sums of neighbouring x cells (lanes m - 1, m, m + 1, one warp shuffle each
+// way), so a tile yields the 14 (x) x 8 (y) interior outputs of its block;
+// tiles step by 14 cells in x.  The block halo (16 x 10 x 3 cells) is
 // fetched by TMA, one 16-channel block per copy, into a ring of STAGES
 // shared-memory buffers laid out [block][z][y][x][16 channels] with the
 // 32-byte swizzle (the TMA and the tensor core both apply it to the absolute
@@ -14,17 +21,19 @@
 //   warp 0      TMA producer: waits for a free stage, posts the expected bytes
 //               on the stage's "full" barrier and issues the chunk copies
 //               (zero fill outside the volume comes from the tensor map);
-//   warp 1      MMA issuer: per tile 27 taps x C_in/16 tcgen05.mma of shape
-//               M = 128 cells x N = C_out x K = 16 into one of two TMEM
+//   warp 1      MMA issuer: per tile 9 taps x C_in/16 tcgen05.mma of shape
+//               M = 128 cells x N = 3 C_out x K = 16 into one of two TMEM
 //               accumulators; commits free the stage and hand the
 //               accumulator to the epilogue;
-//   warps 2..5  epilogue: tcgen05.ld of the accumulator rows (warp w reads
-//               TMEM lanes 32 (w % 4) ..), bias, ReLU, Philox dropout with
-//               inverted scaling, BF16 channels-last stores.
-// The operand of tap (dz, dy, dx) is the halo shifted by that tap: the 8
-// cells of one output row are 8 consecutive 32-byte rows (one swizzle atom
-// wide in K), the 16 rows of the tile are 320 bytes apart, so every tap and
-// 16-channel block is a plain K-major SW32 matrix descriptor -- no im2col.
+//   warps 2..9  epilogue: tcgen05.ld of the accumulator rows (warp w reads
+//               TMEM lanes 32 (w % 4) .., and half of the output channels:
+//               two warps per lane quarter), the x-tap sum across lanes, bias,
+//               ReLU, Philox dropout with inverted scaling, channels-last
+//               stores.
+// The operand of tap (dz, dy) is the halo shifted by that tap: its 128 cells
+// are 128 consecutive 32-byte rows (one swizzle atom wide in K, 8-row groups
+// 256 bytes apart), so every tap and 16-channel block is a plain K-major SW32
+// matrix descriptor -- no im2col.
 // Every wait is bounded: a wait that gives up sets ST_TIMEOUT, the roles stop
 // issuing work, copies and MMAs in flight are waited for (bounded) and TMEM
 // is released.
@@ -39,13 +48,14 @@
 
 namespace hyb {
 
-static constexpr int TX = 8, TY = 16;                 // output tile (cells)
-static constexpr int HX = TX + 2, HY = TY + 2, HZ = 3; // halo
-static constexpr int HCELLS = HX * HY * HZ;            // 540
-static constexpr int CHB = HCELLS * 32;                // bytes one 16-channel copy writes (17280)
-static constexpr int CHBP = (CHB + 1023) / 1024 * 1024; // block pitch in shared memory (17408)
+static constexpr int TX = 16, TY = 8;                 // A block (cells): M = 128 rows
+static constexpr int TXO = TX - 2;                     // output cells per block row (the interior)
+static constexpr int HY = TY + 2, HZ = 3;              // halo (x needs none: the x-taps live in N)
+static constexpr int HCELLS = TX * HY * HZ;            // 480
+static constexpr int CHB = HCELLS * 32;                // bytes one 16-channel copy writes (15360)
+static constexpr int CHBP = (CHB + 1023) / 1024 * 1024; // block pitch in shared memory (15360)
 static constexpr int STAGES = 3;
-static constexpr int NTHREADS = 192;
+static constexpr int NTHREADS = 320;                   // producer, MMA issuer, 8 epilogue warps
 static constexpr long long MBAR_LIMIT = 1LL << 26;     // polls before a wait gives up
 
 // dropout keep decision of channel ch at cell (b, lin): Philox counter
@@ -61,11 +71,12 @@ __host__ __device__ inline bool dropout_keep(uint32_t seed, uint32_t pass, uint3
 
 template <int KC, int N>
 struct ConvCfg {
-    static constexpr int WBYTES = 27 * KC * N * 16;    // weights, core layout [27][KC][N][8]
+    static constexpr int NP = 3 * N;                   // MMA N: the three x-taps side by side
+    static constexpr int WBYTES = 27 * KC * N * 16;    // weights, core layout [9][KC][3 N][8]
     static constexpr int RING = (WBYTES + 1023) / 1024 * 1024;  // halo ring offset (swizzle-aligned)
     static constexpr int STAGE = (KC / 2) * CHBP;      // one halo buffer (16-channel blocks)
     static constexpr int SMEM = RING + STAGES * STAGE + 1024;  // + alignment slack
-    static constexpr int TCOLS = 2 * N < 32 ? 32 : 2 * N;        // two accumulators
+    static constexpr int TCOLS = 2 * NP <= 32 ? 32 : (2 * NP <= 64 ? 64 : (2 * NP <= 128 ? 128 : 256));
 };
 
 template <int KC, int N>
@@ -92,7 +103,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv3_tc(const __grid_constant_
         }
         for (int k = 0; k < 2; ++k) {
             mbar_init(smem_u32(&tfull_b[k]), 1);
-            mbar_init(smem_u32(&tempty_b[k]), 4);
+            mbar_init(smem_u32(&tempty_b[k]), 8);
         }
         mbar_init(smem_u32(&done_b), 1);
         abort_s = 0;
@@ -110,7 +121,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv3_tc(const __grid_constant_
     __syncthreads();
     fence_after_sync();
     const uint32_t taddr = taddr_s;
-    const int tiles_x = a.W / TX, tiles_y = a.H / TY;
+    const int tiles_x = (a.W + TXO - 1) / TXO, tiles_y = a.H / TY;
     const long long ntiles = (long long)a.B * a.D * tiles_y * tiles_x;
     const uint32_t ring_s = smem_u32(ring), w_s = smem_u32(wsm);
 
@@ -135,7 +146,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv3_tc(const __grid_constant_
                 const uint32_t dst = ring_s + (uint32_t)(s * Cfg::STAGE);
 #pragma unroll
                 for (int c = 0; c < KC / 2; ++c)
-                    tma_load_5d(dst + (uint32_t)(c * CHBP), &tmap, 16 * c, tx * TX - 1, ty * TY - 1, z0 - 1, b, fb);
+                    tma_load_5d(dst + (uint32_t)(c * CHBP), &tmap, 16 * c, tx * TXO - 1, ty * TY - 1, z0 - 1, b, fb);
                 ++issued;
                 if (++s == STAGES) {
                     s = 0;
@@ -156,9 +167,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv3_tc(const __grid_constant_
     } else if (warp == 1) {
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
-            constexpr uint32_t idesc = idesc_bf16(128, N);
-            const uint64_t a0 = smem_desc_sw32(ring_s, HX * 32);
-            const uint64_t b0 = smem_desc(w_s, N * 16, 128);
+            constexpr uint32_t idesc = idesc_bf16(128, Cfg::NP);
+            const uint64_t a0 = smem_desc_sw32(ring_s, 8 * 32);
+            const uint64_t b0 = smem_desc(w_s, Cfg::NP * 16, 128);
             int s = 0;
             uint32_t ph = 0;
             long long it = 0;
@@ -172,16 +183,16 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv3_tc(const __grid_constant_
                     break;
                 }
                 fence_after_sync();
-                const uint32_t d = taddr + (uint32_t)(acc * N);
+                const uint32_t d = taddr + (uint32_t)(acc * Cfg::NP);
                 const uint64_t as = a0 + (uint64_t)((s * Cfg::STAGE) >> 4);
 #pragma unroll
-                for (int tap = 0; tap < 27; ++tap) {
-                    const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
-                    const uint32_t toff = (uint32_t)(((dz * HY + dy) * HX + dx) * 32);
+                for (int tap = 0; tap < 9; ++tap) {
+                    const int dz = tap / 3, dy = tap % 3;
+                    const uint32_t toff = (uint32_t)((dz * HY + dy) * TX * 32);
 #pragma unroll
                     for (int kk = 0; kk < KC / 2; ++kk) {
                         const uint64_t ad = as + (uint64_t)((toff + (uint32_t)(kk * CHBP)) >> 4);
-                        const uint64_t bd = b0 + (uint64_t)(((tap * KC + 2 * kk) * N * 16) >> 4);
+                        const uint64_t bd = b0 + (uint64_t)(((tap * KC + 2 * kk) * Cfg::NP * 16) >> 4);
                         umma_bf16(d, ad, bd, idesc, (tap | kk) != 0);
                     }
                 }
@@ -199,6 +210,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv3_tc(const __grid_constant_
     } else {
         // ------------------------------------------------------------ epilogue
         const int q = warp & 3;              // TMEM lane quarter this warp may access
+        const int half = (warp - 2) >> 2;    // two warps per lane quarter: each takes half the channels
+        constexpr int NH = N / 2;
         const int m = q * 32 + lane;         // accumulator row = cell of the tile
         const float scale = a.drop_scale;
         long long it = 0;
@@ -214,28 +227,54 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv3_tc(const __grid_constant_
                 break;
             }
             fence_after_sync();
-            float v[N];
+            // row m holds, per x-tap dx, the partial sum of the outputs at cell
+            // x - dx + 1; the output at x is D_0[x - 1] + D_1[x] + D_2[x + 1]
+            float v[NH];
+            {
+                float p0[NH], p2[NH];
+                const uint32_t rowa =
+                    taddr + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * Cfg::NP + half * NH);
+                if constexpr (NH == 16) {
+                    tmem_ld16(rowa, p0);
+                    tmem_ld16(rowa + (uint32_t)N, v);
+                    tmem_ld16(rowa + (uint32_t)(2 * N), p2);
+                } else {
+                    tmem_ld8(rowa, p0);
+                    tmem_ld8(rowa + (uint32_t)N, v);
+                    tmem_ld8(rowa + (uint32_t)(2 * N), p2);
+                }
+                fence_before_sync();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&tempty_b[acc]));
+                // lanes m - 1 and m + 1 are the x-neighbours (same block row for
+                // the interior cells that produce output)
 #pragma unroll
-            for (int h = 0; h < N / 16; ++h)
-                tmem_ld16(taddr + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * N + h * 16), v + 16 * h);
-            fence_before_sync();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(smem_u32(&tempty_b[acc]));
+                for (int o = 0; o < NH; ++o) {
+                    const float left = __shfl_up_sync(0xffffffffu, p0[o], 1);
+                    const float right = __shfl_down_sync(0xffffffffu, p2[o], 1);
+                    v[o] = left + v[o] + right;
+                }
+            }
 
             const int tx = (int)(tile % tiles_x);
             const int ty = (int)((tile / tiles_x) % tiles_y);
             const int z0 = (int)((tile / ((long long)tiles_x * tiles_y)) % a.D);
             const int b = (int)(tile / ((long long)tiles_x * tiles_y * a.D));
-            const int cx = tx * TX + (m & 7), cy = ty * TY + (m >> 3);
-            const uint32_t lin = (uint32_t)(((long long)z0 * a.H + cy) * a.W + cx);
-            const long long obase = ((((long long)b * a.D + z0) * a.H + cy) * a.W + cx) * N;
+            const int bx = m & (TX - 1);                 // cell of the block row (0 and TX - 1 are halo)
+            const int cx = tx * TXO + bx - 1, cy = ty * TY + (m >> 4);
+            // the halo cells of the block row, and cells past the volume, write nothing
+            const bool valid = bx != 0 && bx != TX - 1 && cx < a.W;
+            const uint32_t lin = (uint32_t)(((long long)z0 * a.H + cy) * a.W + (valid ? cx : 0));
+            const long long obase = ((((long long)b * a.D + z0) * a.H + cy) * a.W + (valid ? cx : 0)) * N + half * NH;
             __nv_bfloat16 *out = a.y ? a.y + obase : nullptr;
             float *outf = a.y_f32 ? a.y_f32 + obase : nullptr;
+            if (valid) {
 #pragma unroll
-            for (int g8 = 0; g8 < N / 8; ++g8) {
+            for (int g8 = 0; g8 < NH / 8; ++g8) {
+                const int g8c = half * (NH / 8) + g8;      // 8-channel group of the layer
                 uint32_t keep16[4] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu};
                 if (a.drop_thr) {
-                    const u32x4 r = philox4x32_10(lin, (uint32_t)b, (a.layer << 16) | (uint32_t)g8, a.pass, a.seed,
+                    const u32x4 r = philox4x32_10(lin, (uint32_t)b, (a.layer << 16) | (uint32_t)g8c, a.pass, a.seed,
                                                   0xD0u);
 #pragma unroll
                     for (int w = 0; w < 4; ++w) keep16[w] = r.v[w];
@@ -244,7 +283,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv3_tc(const __grid_constant_
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
                     const int ch = g8 * 8 + j;
-                    float s = v[ch] + (a.bias ? __ldg(a.bias + ch) : 0.0f);
+                    float s = v[ch] + (a.bias ? __ldg(a.bias + half * NH + ch) : 0.0f);
                     if (a.relu) s = fmaxf(s, 0.0f);
                     if (a.drop_thr) {
                         const uint32_t f = (keep16[j >> 1] >> (16 * (j & 1))) & 0xFFFFu;
@@ -261,6 +300,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv3_tc(const __grid_constant_
                     for (int j = 0; j < 8; ++j) o[j] = __float2bfloat16_rn(r8[j]);
                     reinterpret_cast<uint4 *>(out)[g8] = *reinterpret_cast<const uint4 *>(o);
                 }
+            }
             }
         }
     }
@@ -300,7 +340,7 @@ static hyb_status make_tmap(CUtensorMap *tm, const ConvArgs &a) {
     const cuuint64_t es = 2;
     const cuuint64_t strides[4] = {es * a.cin, es * a.cin * a.W, es * a.cin * a.W * a.H,
                                    es * a.cin * a.W * a.H * a.D};
-    const cuuint32_t box[5] = {16, (cuuint32_t)HX, (cuuint32_t)HY, (cuuint32_t)HZ, 1};
+    const cuuint32_t box[5] = {16, (cuuint32_t)TX, (cuuint32_t)HY, (cuuint32_t)HZ, 1};
     const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
     CUresult r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, (void *)a.x, dims, strides, box, estr,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -337,7 +377,7 @@ static hyb_status launch_cfg(const ConvArgs &a, cudaStream_t st) {
         per_sm = per_sm_dev[dev];
     }
     cudaError_t e;
-    const long long ntiles = (long long)a.B * a.D * (a.H / TY) * (a.W / TX);
+    const long long ntiles = (long long)a.B * a.D * (a.H / TY) * ((a.W + TXO - 1) / TXO);
     const long long grid = std::min<long long>(ntiles, (long long)nsm * std::max(per_sm, 1));
     k_conv3_tc<KC, N><<<(unsigned)grid, NTHREADS, Cfg::SMEM, st>>>(tm, a);
     e = cudaGetLastError();
@@ -346,8 +386,8 @@ static hyb_status launch_cfg(const ConvArgs &a, cudaStream_t st) {
 }
 
 hyb_status launch_conv3_tc(const ConvArgs &a, cudaStream_t st) {
-    if (a.W % TX != 0 || a.H % TY != 0 || a.B < 1 || a.D < 1)
-        return set_error(HYB_EINVAL, "conv shape: W % 8 == 0 and H % 16 == 0 required");
+    if (a.W < 1 || a.H % TY != 0 || a.B < 1 || a.D < 1)
+        return set_error(HYB_EINVAL, "conv shape: H % 8 == 0 required");
     if (((uintptr_t)a.x & 15) || ((uintptr_t)a.y & 15) || ((uintptr_t)a.y_f32 & 15) || ((uintptr_t)a.wt & 15) ||
         (!a.y && !a.y_f32))
         return set_error(HYB_EINVAL, "conv operands must be present and 16-byte aligned");
