@@ -13,7 +13,7 @@
 // sums of neighbouring x cells (lanes m - 1, m, m + 1, one warp shuffle each
 // way), so a tile yields the 14 (x) x 8 (y) interior outputs of its block;
 // tiles step by 14 cells in x.  The block halo (16 x 10 x 3 cells) is
-// fetched by TMA, one 16-channel block per copy, into a ring of STAGES
+// fetched by TMA, one 16-channel block per copy, into a ring of 5 to 8
 // shared-memory buffers laid out [block][z][y][x][16 channels] with the
 // 32-byte swizzle (the TMA and the tensor core both apply it to the absolute
 // shared address, so an operand may start at any cell of the halo); all
@@ -25,11 +25,13 @@
 //               M = 128 cells x N = 3 C_out x K = 16 into one of two TMEM
 //               accumulators; commits free the stage and hand the
 //               accumulator to the epilogue;
-//   warps 2..9  epilogue: tcgen05.ld of the accumulator rows (warp w reads
-//               TMEM lanes 32 (w % 4) .., and half of the output channels:
-//               two warps per lane quarter), the x-tap sum across lanes, bias,
-//               ReLU, Philox dropout with inverted scaling, channels-last
-//               stores.
+//   warps 2..   epilogue, one warp per TMEM lane quarter and 8-channel
+//               output group (4 C_out / 8 warps; warp w reads TMEM lanes
+//               32 (w % 4) .. and channels 8 ((w - 2) / 4) ..): tcgen05.ld of
+//               the accumulator rows, the x-tap sum across lanes, bias, ReLU,
+//               Philox dropout with inverted scaling, channels-last stores.
+//               Many epilogue warps hide the latency of its dependent chains
+//               (the Philox rounds above all).
 // The operand of tap (dz, dy) is the halo shifted by that tap: its 128 cells
 // are 128 consecutive 32-byte rows (one swizzle atom wide in K, 8-row groups
 // 256 bytes apart), so every tap and 16-channel block is a plain K-major SW32
@@ -54,8 +56,6 @@ static constexpr int HY = TY + 2, HZ = 3;              // halo (x needs none: th
 static constexpr int HCELLS = TX * HY * HZ;            // 480
 static constexpr int CHB = HCELLS * 32;                // bytes one 16-channel copy writes (15360)
 static constexpr int CHBP = (CHB + 1023) / 1024 * 1024; // block pitch in shared memory (15360)
-static constexpr int STAGES = 3;
-static constexpr int NTHREADS = 320;                   // producer, MMA issuer, 8 epilogue warps
 static constexpr long long MBAR_LIMIT = 1LL << 26;     // polls before a wait gives up
 
 // dropout keep decision of channel ch at cell (b, lin): Philox counter
@@ -69,24 +69,71 @@ __host__ __device__ inline bool dropout_keep(uint32_t seed, uint32_t pass, uint3
     return f >= thr;
 }
 
+// position of a persistent CTA's tile in (x tile, y tile, z, batch) digits,
+// stepped by the grid size with carries instead of divisions
+struct TileCursor {
+    int tx, ty, z, b;        // the current tile
+    int sx, sy, sz, sb;      // the step (grid size) in the same digits
+    int nx, ny, nz;
+    __device__ void init(uint32_t t, uint32_t step, int nx_, int ny_, int nz_) {
+        nx = nx_;
+        ny = ny_;
+        nz = nz_;
+        tx = (int)(t % (uint32_t)nx);
+        t /= (uint32_t)nx;
+        ty = (int)(t % (uint32_t)ny);
+        t /= (uint32_t)ny;
+        z = (int)(t % (uint32_t)nz);
+        b = (int)(t / (uint32_t)nz);
+        sx = (int)(step % (uint32_t)nx);
+        step /= (uint32_t)nx;
+        sy = (int)(step % (uint32_t)ny);
+        step /= (uint32_t)ny;
+        sz = (int)(step % (uint32_t)nz);
+        sb = (int)(step / (uint32_t)nz);
+    }
+    __device__ void next() {
+        tx += sx;
+        int c = tx >= nx;
+        tx -= c ? nx : 0;
+        ty += sy + c;
+        c = ty >= ny;
+        ty -= c ? ny : 0;
+        z += sz + c;
+        c = z >= nz;
+        z -= c ? nz : 0;
+        b += sb + c;
+    }
+};
+
 template <int KC, int N>
 struct ConvCfg {
     static constexpr int NP = 3 * N;                   // MMA N: the three x-taps side by side
     static constexpr int WBYTES = 27 * KC * N * 16;    // weights, core layout [9][KC][3 N][8]
     static constexpr int RING = (WBYTES + 1023) / 1024 * 1024;  // halo ring offset (swizzle-aligned)
     static constexpr int STAGE = (KC / 2) * CHBP;      // one halo buffer (16-channel blocks)
+    // as many halo buffers as shared memory holds (up to 8): the copies in
+    // flight must cover the L2 latency of a stage
+    static constexpr int SMEM_MAX = 227 * 1024 - 512;  // dynamic share (static barriers take the rest)
+    static constexpr int STAGES = (SMEM_MAX - 1024 - RING) / STAGE > 8 ? 8 : (SMEM_MAX - 1024 - RING) / STAGE;
     static constexpr int SMEM = RING + STAGES * STAGE + 1024;  // + alignment slack
     static constexpr int TCOLS = 2 * NP <= 32 ? 32 : (2 * NP <= 64 ? 64 : (2 * NP <= 128 ? 128 : 256));
+    static constexpr int NG = N / 8;                   // 8-channel output groups
+    static constexpr int NEPI = 4 * NG;                // epilogue warps: one per lane quarter and group
+    static constexpr int NTHREADS = 64 + 32 * NEPI;    // + producer and MMA issuer
 };
 
 template <int KC, int N>
-__global__ void __launch_bounds__(NTHREADS, 1) k_conv3_tc(const __grid_constant__ CUtensorMap tmap, ConvArgs a) {
+__global__ void __launch_bounds__(ConvCfg<KC, N>::NTHREADS, 1)
+    k_conv3_tc(const __grid_constant__ CUtensorMap tmap, ConvArgs a) {
     using Cfg = ConvCfg<KC, N>;
     extern __shared__ uint8_t smem_raw[];
     // 1024-byte aligned base: weights first, then the halo ring
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t *wsm = smem;
     uint8_t *ring = smem + Cfg::RING;
+    constexpr int STAGES = Cfg::STAGES;
+    static_assert(STAGES >= 2, "shared memory holds fewer than two halo buffers");
     __shared__ __align__(8) uint64_t full_b[STAGES], empty_b[STAGES], tfull_b[2], tempty_b[2], done_b;
     __shared__ uint32_t taddr_s;
     __shared__ int abort_s;
@@ -103,7 +150,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv3_tc(const __grid_constant_
         }
         for (int k = 0; k < 2; ++k) {
             mbar_init(smem_u32(&tfull_b[k]), 1);
-            mbar_init(smem_u32(&tempty_b[k]), 8);
+            mbar_init(smem_u32(&tempty_b[k]), Cfg::NEPI);
         }
         mbar_init(smem_u32(&done_b), 1);
         abort_s = 0;
@@ -114,7 +161,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv3_tc(const __grid_constant_
     {
         const uint4 *src = reinterpret_cast<const uint4 *>(a.wt);
         uint4 *dst = reinterpret_cast<uint4 *>(wsm);
-        for (int i = tid; i < Cfg::WBYTES / 16; i += NTHREADS) dst[i] = src[i];
+        for (int i = tid; i < Cfg::WBYTES / 16; i += Cfg::NTHREADS) dst[i] = src[i];
     }
     fence_proxy_async_smem();
     fence_before_sync();
@@ -131,16 +178,15 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv3_tc(const __grid_constant_
             int s = 0;
             uint32_t ph = 0;
             long long issued = 0;
-            for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+            TileCursor cur;
+            cur.init(blockIdx.x, gridDim.x, tiles_x, tiles_y, a.D);
+            for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, cur.next()) {
                 if (!mbar_wait(smem_u32(&empty_b[s]), ph ^ 1, MBAR_LIMIT) || *(volatile int *)&abort_s) {
                     atomicOr(a.status, ST_TIMEOUT);
                     *(volatile int *)&abort_s = 1;
                     break;
                 }
-                const int tx = (int)(tile % tiles_x);
-                const int ty = (int)((tile / tiles_x) % tiles_y);
-                const int z0 = (int)((tile / ((long long)tiles_x * tiles_y)) % a.D);
-                const int b = (int)(tile / ((long long)tiles_x * tiles_y * a.D));
+                const int tx = cur.tx, ty = cur.ty, z0 = cur.z, b = cur.b;
                 const uint32_t fb = smem_u32(&full_b[s]);
                 mbar_arrive_expect_tx(fb, (KC / 2) * CHB);
                 const uint32_t dst = ring_s + (uint32_t)(s * Cfg::STAGE);
@@ -210,12 +256,32 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv3_tc(const __grid_constant_
     } else {
         // ------------------------------------------------------------ epilogue
         const int q = warp & 3;              // TMEM lane quarter this warp may access
-        const int half = (warp - 2) >> 2;    // two warps per lane quarter: each takes half the channels
-        constexpr int NH = N / 2;
+        const int grp = (warp - 2) >> 2;     // the 8 output channels 8 grp .. 8 grp + 7 of this warp
         const int m = q * 32 + lane;         // accumulator row = cell of the tile
         const float scale = a.drop_scale;
+        const int bx = m & (TX - 1);         // cell of the block row (0 and TX - 1 are halo)
+        float bias8[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) bias8[j] = a.bias ? __ldg(a.bias + grp * 8 + j) : 0.0f;
+        TileCursor cur;                      // tile counts fit in 32 bits (checked at launch)
+        cur.init(blockIdx.x, gridDim.x, tiles_x, tiles_y, a.D);
         long long it = 0;
-        for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+        for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it, cur.next()) {
+            // first what does not need the accumulator (it overlaps the MMAs):
+            // the cell, its validity and its dropout bits
+            const int tx = cur.tx, ty = cur.ty, z0 = cur.z, b = cur.b;
+            const int cx = tx * TXO + bx - 1, cy = ty * TY + (m >> 4);
+            // the halo cells of the block row, and cells past the volume, write nothing
+            const bool valid = bx != 0 && bx != TX - 1 && cx < a.W;
+            const uint32_t lin = (uint32_t)(((long long)z0 * a.H + cy) * a.W + (valid ? cx : 0));
+            const long long obase = ((((long long)b * a.D + z0) * a.H + cy) * a.W + (valid ? cx : 0)) * N + grp * 8;
+            uint32_t keep16[4] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu};
+            if (a.drop_thr) {
+                const u32x4 r = philox4x32_10(lin, (uint32_t)b, (a.layer << 16) | (uint32_t)grp, a.pass, a.seed, 0xD0u);
+#pragma unroll
+                for (int w = 0; w < 4; ++w) keep16[w] = r.v[w];
+            }
+
             const int acc = (int)(it & 1);
             const uint32_t aph = (uint32_t)((it >> 1) & 1);
             const bool ok = mbar_wait(smem_u32(&tfull_b[acc]), aph, MBAR_LIMIT);
@@ -229,61 +295,30 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv3_tc(const __grid_constant_
             fence_after_sync();
             // row m holds, per x-tap dx, the partial sum of the outputs at cell
             // x - dx + 1; the output at x is D_0[x - 1] + D_1[x] + D_2[x + 1]
-            float v[NH];
+            float v[8];
             {
-                float p0[NH], p2[NH];
-                const uint32_t rowa =
-                    taddr + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * Cfg::NP + half * NH);
-                if constexpr (NH == 16) {
-                    tmem_ld16(rowa, p0);
-                    tmem_ld16(rowa + (uint32_t)N, v);
-                    tmem_ld16(rowa + (uint32_t)(2 * N), p2);
-                } else {
-                    tmem_ld8(rowa, p0);
-                    tmem_ld8(rowa + (uint32_t)N, v);
-                    tmem_ld8(rowa + (uint32_t)(2 * N), p2);
-                }
+                float p[24];
+                const uint32_t rowa = taddr + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * Cfg::NP + grp * 8);
+                tmem_ld8x3(rowa, rowa + (uint32_t)N, rowa + (uint32_t)(2 * N), p);
                 fence_before_sync();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(smem_u32(&tempty_b[acc]));
                 // lanes m - 1 and m + 1 are the x-neighbours (same block row for
                 // the interior cells that produce output)
 #pragma unroll
-                for (int o = 0; o < NH; ++o) {
-                    const float left = __shfl_up_sync(0xffffffffu, p0[o], 1);
-                    const float right = __shfl_down_sync(0xffffffffu, p2[o], 1);
-                    v[o] = left + v[o] + right;
+                for (int o = 0; o < 8; ++o) {
+                    const float left = __shfl_up_sync(0xffffffffu, p[o], 1);
+                    const float right = __shfl_down_sync(0xffffffffu, p[16 + o], 1);
+                    v[o] = left + p[8 + o] + right;
                 }
             }
-
-            const int tx = (int)(tile % tiles_x);
-            const int ty = (int)((tile / tiles_x) % tiles_y);
-            const int z0 = (int)((tile / ((long long)tiles_x * tiles_y)) % a.D);
-            const int b = (int)(tile / ((long long)tiles_x * tiles_y * a.D));
-            const int bx = m & (TX - 1);                 // cell of the block row (0 and TX - 1 are halo)
-            const int cx = tx * TXO + bx - 1, cy = ty * TY + (m >> 4);
-            // the halo cells of the block row, and cells past the volume, write nothing
-            const bool valid = bx != 0 && bx != TX - 1 && cx < a.W;
-            const uint32_t lin = (uint32_t)(((long long)z0 * a.H + cy) * a.W + (valid ? cx : 0));
-            const long long obase = ((((long long)b * a.D + z0) * a.H + cy) * a.W + (valid ? cx : 0)) * N + half * NH;
             __nv_bfloat16 *out = a.y ? a.y + obase : nullptr;
             float *outf = a.y_f32 ? a.y_f32 + obase : nullptr;
             if (valid) {
-#pragma unroll
-            for (int g8 = 0; g8 < NH / 8; ++g8) {
-                const int g8c = half * (NH / 8) + g8;      // 8-channel group of the layer
-                uint32_t keep16[4] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu};
-                if (a.drop_thr) {
-                    const u32x4 r = philox4x32_10(lin, (uint32_t)b, (a.layer << 16) | (uint32_t)g8c, a.pass, a.seed,
-                                                  0xD0u);
-#pragma unroll
-                    for (int w = 0; w < 4; ++w) keep16[w] = r.v[w];
-                }
                 float r8[8];
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
-                    const int ch = g8 * 8 + j;
-                    float s = v[ch] + (a.bias ? __ldg(a.bias + half * NH + ch) : 0.0f);
+                    float s = v[j] + bias8[j];
                     if (a.relu) s = fmaxf(s, 0.0f);
                     if (a.drop_thr) {
                         const uint32_t f = (keep16[j >> 1] >> (16 * (j & 1))) & 0xFFFFu;
@@ -292,15 +327,14 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_conv3_tc(const __grid_constant_
                     r8[j] = s;
                 }
                 if (outf) {
-                    reinterpret_cast<float4 *>(outf)[2 * g8] = make_float4(r8[0], r8[1], r8[2], r8[3]);
-                    reinterpret_cast<float4 *>(outf)[2 * g8 + 1] = make_float4(r8[4], r8[5], r8[6], r8[7]);
+                    reinterpret_cast<float4 *>(outf)[0] = make_float4(r8[0], r8[1], r8[2], r8[3]);
+                    reinterpret_cast<float4 *>(outf)[1] = make_float4(r8[4], r8[5], r8[6], r8[7]);
                 } else {
                     __align__(16) __nv_bfloat16 o[8];
 #pragma unroll
                     for (int j = 0; j < 8; ++j) o[j] = __float2bfloat16_rn(r8[j]);
-                    reinterpret_cast<uint4 *>(out)[g8] = *reinterpret_cast<const uint4 *>(o);
+                    *reinterpret_cast<uint4 *>(out) = *reinterpret_cast<const uint4 *>(o);
                 }
-            }
             }
         }
     }
@@ -370,7 +404,8 @@ static hyb_status launch_cfg(const ConvArgs &a, cudaStream_t st) {
             if (e != cudaSuccess)
                 return set_error(HYB_ECUDA, std::string("conv smem attribute: ") + cudaGetErrorString(e));
             cudaDeviceGetAttribute(&nsm_dev[dev], cudaDevAttrMultiProcessorCount, dev);
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_dev[dev], k_conv3_tc<KC, N>, NTHREADS, Cfg::SMEM);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_dev[dev], k_conv3_tc<KC, N>, Cfg::NTHREADS,
+                                                          Cfg::SMEM);
             ready_dev[dev] = 1;
         }
         nsm = nsm_dev[dev];
@@ -379,7 +414,7 @@ static hyb_status launch_cfg(const ConvArgs &a, cudaStream_t st) {
     cudaError_t e;
     const long long ntiles = (long long)a.B * a.D * (a.H / TY) * ((a.W + TXO - 1) / TXO);
     const long long grid = std::min<long long>(ntiles, (long long)nsm * std::max(per_sm, 1));
-    k_conv3_tc<KC, N><<<(unsigned)grid, NTHREADS, Cfg::SMEM, st>>>(tm, a);
+    k_conv3_tc<KC, N><<<(unsigned)grid, Cfg::NTHREADS, Cfg::SMEM, st>>>(tm, a);
     e = cudaGetLastError();
     if (e != cudaSuccess) return set_error(HYB_ECUDA, std::string("conv launch: ") + cudaGetErrorString(e));
     return HYB_OK;
@@ -388,6 +423,8 @@ static hyb_status launch_cfg(const ConvArgs &a, cudaStream_t st) {
 hyb_status launch_conv3_tc(const ConvArgs &a, cudaStream_t st) {
     if (a.W < 1 || a.H % TY != 0 || a.B < 1 || a.D < 1)
         return set_error(HYB_EINVAL, "conv shape: H % 8 == 0 required");
+    if ((long long)a.B * a.D * (a.H / TY) * ((a.W + TXO - 1) / TXO) >= (1LL << 31))
+        return set_error(HYB_EINVAL, "conv shape: more than 2^31 tiles");
     if (((uintptr_t)a.x & 15) || ((uintptr_t)a.y & 15) || ((uintptr_t)a.y_f32 & 15) || ((uintptr_t)a.wt & 15) ||
         (!a.y && !a.y_f32))
         return set_error(HYB_EINVAL, "conv operands must be present and 16-byte aligned");
