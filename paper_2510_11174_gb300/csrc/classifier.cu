@@ -23,6 +23,7 @@
 static constexpr int NL = 4;
 static constexpr int CIN[NL] = {6, 32, 32, 16}, COUT[NL] = {32, 32, 16, 1};
 static constexpr int CINP[NL] = {16, 32, 32, 16};  // input channels padded for the tensor-core layout
+static constexpr int MC_GROUP = 4;                  // MC passes whose layer-1 inputs one dropout launch writes
 
 struct hyb_model {
     hyb_model_desc d;
@@ -33,13 +34,13 @@ struct hyb_model {
     __nv_bfloat16 *wt[3] = {};           // packed forward weights, layers 0..2
     __nv_bfloat16 *wtT[3] = {};          // packed transposed + flipped (data gradient)
     float *w4r = nullptr;                // layer 3 weights rounded to BF16 (as FP32), [16][27]
-    float w4h[27 * 16] = {};             // host copy of w4r as [tap][ci] (kernel parameter of the last layer)
+    uint32_t w4pk[256] = {};             // w4r as BF16 B operand [ci / 8][tap (32)][ci % 8] (kernel parameter)
     float b4h = 0.0f;
     float *mean = nullptr, *std_ = nullptr;
     // activation buffers (capacity in cells)
     long long cap = 0;
     __nv_bfloat16 *x0 = nullptr, *a1 = nullptr, *a2 = nullptr, *a3 = nullptr;
-    float *h0 = nullptr;                 // layer-0 output before dropout (FP32), shared by the MC passes
+    __nv_bfloat16 *h0s = nullptr;        // layer-0 output scaled by 1 / (1 - p), shared by the MC passes
     float *logit = nullptr, *pm = nullptr, *ps = nullptr;
     int *status = nullptr;
     long long adam_t = 0;
@@ -137,119 +138,35 @@ __global__ void k_prep_fields(GridDev g, const float *__restrict__ E, const floa
     dst[1] = reinterpret_cast<const uint4 *>(o)[1];
 }
 
-// the 16 -> 1 layer on CUDA cores: logit = b + sum_tap sum_ci W[ci][tap] a3[cell + tap - 1][ci]
-// the 16 -> 1 layer on CUDA cores: logit = b + sum_tap sum_ci W[ci][tap] a3[cell + tap - 1][ci].
-// Weights travel as a kernel parameter (constant bank, used directly by the
-// FMAs).  A block of 128 threads owns 8 (x) x 16 (y) x 4 (z) cells; the BF16
-// input halo (10 x 18 x 6 cells x 16 channels) is staged in shared memory by
-// asynchronous copies (zero outside the volume) and each thread sums the taps
-// of its 4-cell column.  mc_k = 0 writes the logit; mc_k = k >= 1 folds
-// sigmoid(logit) into the running mean / M2 of the MC passes instead (k = 1
-// starts them).
-struct LastW {
-    float w[27 * 16];  // [tap][ci]
-    float b;
-};
-
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, bool in) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(in ? 16 : 0) : "memory");
-}
-
-__global__ void __launch_bounds__(128) k_conv_last(const __grid_constant__ LastW lw,
-                                                   const __nv_bfloat16 *__restrict__ a3, int B, int D, int H, int W,
-                                                   float *__restrict__ logit, int mc_k, float *__restrict__ pm,
-                                                   float *__restrict__ m2) {
-    __shared__ __align__(16) uint4 halo[6 * 18 * 10 * 2];  // [z][y][x][2 x 8 channels]
-    const int tiles_x = W / 8, tiles_y = H / 16, tiles_z = (D + 3) / 4;
-    const long long tile = blockIdx.x;
-    const int tx = (int)(tile % tiles_x), ty = (int)((tile / tiles_x) % tiles_y);
-    const int tz = (int)((tile / ((long long)tiles_x * tiles_y)) % tiles_z);
-    const int b = (int)(tile / ((long long)tiles_x * tiles_y * tiles_z));
-    const int x0 = tx * 8, y0 = ty * 16, z0 = tz * 4;
-    const long long V = (long long)D * H * W;
-    const __nv_bfloat16 *src = a3 + (long long)b * V * 16;
-    for (int i = threadIdx.x; i < 6 * 18 * 10 * 2; i += 128) {
-        const int h = i & 1, c = i >> 1;
-        const int lx = c % 10, ly = (c / 10) % 18, lz = c / 180;
-        const int gx = x0 - 1 + lx, gy = y0 - 1 + ly, gz = z0 - 1 + lz;
-        const bool in = gx >= 0 && gx < W && gy >= 0 && gy < H && gz >= 0 && gz < D;
-        const __nv_bfloat16 *p = in ? src + (((long long)gz * H + gy) * W + gx) * 16 + h * 8 : src;
-        cp_async16((uint32_t)__cvta_generic_to_shared(&halo[i]), p, in);
-    }
-    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
-    __syncthreads();
-    const int lx = threadIdx.x & 7, ly = threadIdx.x >> 3;
-    float acc[4] = {lw.b, lw.b, lw.b, lw.b};
-#pragma unroll
-    for (int zi = 0; zi < 6; ++zi) {
-#pragma unroll
-        for (int dy = 0; dy < 3; ++dy) {
-#pragma unroll
-            for (int dx = 0; dx < 3; ++dx) {
-                const int cell = (zi * 18 + ly + dy) * 10 + lx + dx;
-                const uint4 v0 = halo[2 * cell], v1 = halo[2 * cell + 1];
-                const uint32_t u[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
-                float f[16];
-#pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    f[2 * q] = __uint_as_float(u[q] << 16);
-                    f[2 * q + 1] = __uint_as_float(u[q] & 0xFFFF0000u);
-                }
-#pragma unroll
-                for (int o = 0; o < 4; ++o) {
-                    const int dz = zi - o;
-                    if (dz < 0 || dz > 2) continue;
-                    const int tap = (dz * 3 + dy) * 3 + dx;
-#pragma unroll
-                    for (int ci = 0; ci < 16; ++ci) acc[o] = fmaf(lw.w[tap * 16 + ci], f[ci], acc[o]);
-                }
-            }
-        }
-    }
-#pragma unroll
-    for (int o = 0; o < 4; ++o) {
-        const int z = z0 + o;
-        if (z >= D) break;
-        const long long t = (long long)b * V + ((long long)z * H + y0 + ly) * W + x0 + lx;
-        if (mc_k == 0) {
-            logit[t] = acc[o];
-        } else {
-            const float p = 1.0f / (1.0f + expf(-acc[o]));
-            if (mc_k == 1) {
-                pm[t] = p;
-                m2[t] = 0.0f;
-            } else {
-                const float mo = pm[t];
-                const float d = p - mo;
-                const float mn = mo + d / (float)mc_k;
-                pm[t] = mn;
-                m2[t] += d * (p - mn);
-            }
-        }
-    }
-}
-
-// a1 = bf16(h0 kept / (1 - p)) with the layer-0 dropout mask of `pass`
-// (the MC passes share layer 0 up to its dropout)
-__global__ void k_dropout_apply(const float *__restrict__ h0, long long cells, long long V, uint32_t seed,
-                                uint32_t pass, uint32_t thr, float scale, __nv_bfloat16 *__restrict__ a1) {
+// layer-1 inputs of the passes pass0 .. pass0 + G - 1: a1[g] = h0s where the
+// layer-0 dropout mask of pass pass0 + g keeps the channel, else 0 (h0s holds
+// bf16(relu(layer 0) / (1 - p)), the kept value of every pass).  The 16-bit
+// Philox field of channel j is the low (even j) or high (odd j) half of word
+// j / 2, the same half that holds channel j in a word of two BF16 values, so
+// one SIMD compare per word gives the mask.
+__global__ void k_dropout_select(const __nv_bfloat16 *__restrict__ h0s, long long cells, long long V, uint32_t seed,
+                                 uint32_t pass0, int G, uint32_t thr, __nv_bfloat16 *__restrict__ a1,
+                                 long long pitch) {
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (t >= cells) return;
     const uint32_t b = (uint32_t)(t / V), lin = (uint32_t)(t % V);
-    const float4 *src = reinterpret_cast<const float4 *>(h0 + t * 32);
-    uint4 *dst = reinterpret_cast<uint4 *>(a1 + t * 32);
+    const uint4 *src = reinterpret_cast<const uint4 *>(h0s + t * 32);
+    uint4 h[4];
 #pragma unroll
-    for (int g8 = 0; g8 < 4; ++g8) {
-        const u32x4 r = philox4x32_10(lin, b, (0u << 16) | (uint32_t)g8, pass, seed, 0xD0u);
-        const float4 lo = src[2 * g8], hi = src[2 * g8 + 1];
-        const float v[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
-        __align__(16) __nv_bfloat16 o[8];
+    for (int g8 = 0; g8 < 4; ++g8) h[g8] = src[g8];
+    const uint32_t thr2 = thr | (thr << 16);
+    for (int g = 0; g < G; ++g) {
+        uint4 *dst = reinterpret_cast<uint4 *>(a1 + g * pitch + t * 32);
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const uint32_t f = (r.v[j >> 1] >> (16 * (j & 1))) & 0xFFFFu;
-            o[j] = __float2bfloat16_rn(f >= thr ? v[j] * scale : 0.0f);
+        for (int g8 = 0; g8 < 4; ++g8) {
+            const u32x4 r = philox4x32_10(lin, b, (0u << 16) | (uint32_t)g8, pass0 + (uint32_t)g, seed, 0xD0u);
+            uint4 o;
+            o.x = h[g8].x & __vcmpgeu2(r.v[0], thr2);
+            o.y = h[g8].y & __vcmpgeu2(r.v[1], thr2);
+            o.z = h[g8].z & __vcmpgeu2(r.v[2], thr2);
+            o.w = h[g8].w & __vcmpgeu2(r.v[3], thr2);
+            dst[g8] = o;
         }
-        dst[g8] = *reinterpret_cast<const uint4 *>(o);
     }
 }
 __global__ void k_mc_final(long long n, int k, const float *m2, float *ps) {  // may run in place
@@ -275,8 +192,15 @@ hyb_status model_repack(hyb_model *m) {
     if (e == cudaSuccess) e = cudaMemcpyAsync(&m->b4h, m->b[3], sizeof(float), cudaMemcpyDeviceToHost, m->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
     if (e != cudaSuccess) return set_error(HYB_ECUDA, std::string("weight copy: ") + cudaGetErrorString(e));
-    for (int ci = 0; ci < 16; ++ci)
-        for (int tap = 0; tap < 27; ++tap) m->w4h[tap * 16 + ci] = w4[ci * 27 + tap];
+    // the values are BF16-rounded already: their BF16 code is the upper half
+    uint16_t pk[512];
+    for (int e = 0; e < 512; ++e) {
+        const int j = e % 8, tap = (e / 8) % 32, kc = e / 256, ci = kc * 8 + j;
+        uint32_t bits = 0;
+        if (tap < 27) memcpy(&bits, &w4[ci * 27 + tap], 4);
+        pk[e] = (uint16_t)(bits >> 16);
+    }
+    for (int i = 0; i < 256; ++i) m->w4pk[i] = (uint32_t)pk[2 * i] | ((uint32_t)pk[2 * i + 1] << 16);
     return HYB_OK;
 }
 
@@ -284,7 +208,7 @@ static hyb_status model_reserve(hyb_model *m, long long cells) {
     if (cells <= m->cap) return HYB_OK;
     // buffers are replaced only between stream-ordered uses
     cudaStreamSynchronize(m->stream);
-    void *bufs[8] = {m->x0, m->a1, m->a2, m->a3, m->logit, m->pm, m->ps, m->h0};
+    void *bufs[8] = {m->x0, m->a1, m->a2, m->a3, m->logit, m->pm, m->ps, m->h0s};
     for (void *p : bufs) {
         if (!p) continue;
         for (auto it = m->owned.begin(); it != m->owned.end(); ++it)
@@ -295,10 +219,10 @@ static hyb_status model_reserve(hyb_model *m, long long cells) {
         cudaFree(p);
     }
     if (m_alloc(m, (void **)&m->x0, sizeof(__nv_bfloat16) * 16 * cells) ||
-        m_alloc(m, (void **)&m->a1, sizeof(__nv_bfloat16) * 32 * cells) ||
+        m_alloc(m, (void **)&m->a1, sizeof(__nv_bfloat16) * 32 * cells * MC_GROUP) ||
         m_alloc(m, (void **)&m->a2, sizeof(__nv_bfloat16) * 32 * cells) ||
         m_alloc(m, (void **)&m->a3, sizeof(__nv_bfloat16) * 16 * cells) ||
-        m_alloc(m, (void **)&m->h0, sizeof(float) * 32 * cells) ||
+        m_alloc(m, (void **)&m->h0s, sizeof(__nv_bfloat16) * 32 * cells) ||
         m_alloc(m, (void **)&m->logit, sizeof(float) * cells) || m_alloc(m, (void **)&m->pm, sizeof(float) * cells) ||
         m_alloc(m, (void **)&m->ps, sizeof(float) * cells))
         return set_error(HYB_ENOMEM, "classifier activation buffers");
@@ -333,6 +257,7 @@ static ConvArgs conv_args(hyb_model *m, int l, int B, int D, int H, int W, int p
     a.relu = 1;
     a.drop_thr = thr;
     a.drop_scale = dropout_scale(thr);
+    a.scale_out = thr != 0;
     a.seed = m->d.seed;
     a.pass = (uint32_t)(pass >= 0 ? pass : 0);
     a.layer = (uint32_t)l;
@@ -340,23 +265,33 @@ static ConvArgs conv_args(hyb_model *m, int l, int B, int D, int H, int W, int p
     return a;
 }
 
-static void launch_last(hyb_model *m, int B, int D, int H, int W, int mc_k) {
-    LastW lw;
-    memcpy(lw.w, m->w4h, sizeof(lw.w));
-    lw.b = m->b4h;
-    const long long tiles = (long long)B * ((D + 3) / 4) * (H / 16) * (W / 8);
-    k_conv_last<<<(unsigned)tiles, 128, 0, m->stream>>>(lw, m->a3, B, D, H, W, m->logit, mc_k, m->pm, m->ps);
+static hyb_status launch_last(hyb_model *m, int B, int D, int H, int W, int mc_k, cudaStream_t st) {
+    LastArgs a;
+    a.x = m->a3;
+    memcpy(a.w, m->w4pk, sizeof(a.w));
+    a.bias = m->b4h;
+    a.B = B;
+    a.D = D;
+    a.H = H;
+    a.W = W;
+    a.logit = m->logit;
+    a.mc_k = mc_k;
+    a.pm = m->pm;
+    a.m2 = m->ps;
+    a.status = m->status;
+    return launch_conv_last_tc(a, st);
 }
 
 // layers first_layer..3 on m->x0 (or on m->a1 when first_layer = 1) for
 // B x D x H x W cells; mc_k = 0 writes m->logit, mc_k >= 1 folds the pass
-// into the MC statistics (see k_conv_last)
+// into the MC statistics (see k_conv_last_tc)
 static hyb_status model_run(hyb_model *m, int B, int D, int H, int W, int pass, int mc_k = 0, int first_layer = 0) {
     for (int l = first_layer; l < 3; ++l) {
         hyb_status s = launch_conv3_tc(conv_args(m, l, B, D, H, W, pass), m->stream);
         if (s != HYB_OK) return s;
     }
-    launch_last(m, B, D, H, W, mc_k);
+    hyb_status s = launch_last(m, B, D, H, W, mc_k, m->stream);
+    if (s != HYB_OK) return s;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return set_error(HYB_ECUDA, std::string("classifier: ") + cudaGetErrorString(e));
     return HYB_OK;
@@ -381,9 +316,11 @@ hyb_status classifier_forward(hyb_ctx *c, const hyb_model *mc, float *p_mean_dev
     const uint32_t thr = dropout_threshold(m->d.dropout);
     long long launches = 1;
     if (K > 1 && thr > 0) {
+        // layer 0 once, its outputs scaled as kept values: bf16(relu(.) / (1 - p))
         ConvArgs a0 = conv_args(m, 0, 1, D, H, W, -1);
-        a0.y = nullptr;
-        a0.y_f32 = m->h0;
+        a0.y = m->h0s;
+        a0.drop_scale = dropout_scale(thr);
+        a0.scale_out = 1;
         s = launch_conv3_tc(a0, c->stream);
         ++launches;
         // profiling: events around the layer-1 and layer-2 convolutions of every pass
@@ -402,15 +339,23 @@ hyb_status classifier_forward(hyb_ctx *c, const hyb_model *mc, float *p_mean_dev
             c->phase_ran[HYB_PH_CONV1] = c->phase_ran[HYB_PH_CONV2] = true;
         }
         for (int k = 1; k <= K && s == HYB_OK; ++k) {
-            k_dropout_apply<<<nb(g.N), 256, 0, c->stream>>>(m->h0, g.N, g.N, m->d.seed, (uint32_t)(k - 1), thr,
-                                                            dropout_scale(thr), m->a1);
+            const int slot = (k - 1) % MC_GROUP;
+            if (slot == 0) {
+                // the layer-0 dropout of the next MC_GROUP passes, one read of h0s
+                const int G = std::min(MC_GROUP, K - (k - 1));
+                k_dropout_select<<<nb(g.N), 256, 0, c->stream>>>(m->h0s, g.N, g.N, m->d.seed, (uint32_t)(k - 1), G,
+                                                                 thr, m->a1, g.N * 32);
+                ++launches;
+            }
             for (int l = 1; l < 3 && s == HYB_OK; ++l) {
+                ConvArgs a = conv_args(m, l, 1, D, H, W, k - 1);
+                if (l == 1) a.x = m->a1 + (size_t)slot * g.N * 32;
                 if (prof) cudaEventRecord(c->conv_ev[((l - 1) * K + (k - 1)) * 2], c->stream);
-                s = launch_conv3_tc(conv_args(m, l, 1, D, H, W, k - 1), c->stream);
+                s = launch_conv3_tc(a, c->stream);
                 if (prof) cudaEventRecord(c->conv_ev[((l - 1) * K + (k - 1)) * 2 + 1], c->stream);
             }
-            if (s == HYB_OK) launch_last(m, 1, D, H, W, k);
-            launches += 4;
+            if (s == HYB_OK) s = launch_last(m, 1, D, H, W, k, c->stream);
+            launches += 3;
         }
     } else {
         for (int k = 1; k <= K && s == HYB_OK; ++k) {

@@ -22,7 +22,7 @@
 //               on the stage's "full" barrier and issues the chunk copies
 //               (zero fill outside the volume comes from the tensor map);
 //   warp 1      MMA issuer: per tile 9 taps x C_in/16 tcgen05.mma of shape
-//               M = 128 cells x N = 3 C_out x K = 16 into one of two TMEM
+//               M = 128 cells x N = 3 C_out x K = 16 into one of 2 or 4 TMEM
 //               accumulators; commits free the stage and hand the
 //               accumulator to the epilogue;
 //   warps 2..   epilogue, one warp per TMEM lane quarter and 8-channel
@@ -117,7 +117,11 @@ struct ConvCfg {
     static constexpr int SMEM_MAX = 227 * 1024 - 512;  // dynamic share (static barriers take the rest)
     static constexpr int STAGES = (SMEM_MAX - 1024 - RING) / STAGE > 8 ? 8 : (SMEM_MAX - 1024 - RING) / STAGE;
     static constexpr int SMEM = RING + STAGES * STAGE + 1024;  // + alignment slack
-    static constexpr int TCOLS = 2 * NP <= 32 ? 32 : (2 * NP <= 64 ? 64 : (2 * NP <= 128 ? 128 : 256));
+    // TMEM accumulators: four when they fit the 512 columns (the MMAs may run
+    // three tiles ahead of the slowest epilogue warp), else two
+    static constexpr int NACC = 4 * NP <= 512 ? 4 : 2;
+    static constexpr int TCOLS = NACC * NP <= 32 ? 32 : (NACC * NP <= 64 ? 64 : (NACC * NP <= 128 ? 128 :
+                                 (NACC * NP <= 256 ? 256 : 512)));
     static constexpr int NG = N / 8;                   // 8-channel output groups
     static constexpr int NEPI = 4 * NG;                // epilogue warps: one per lane quarter and group
     static constexpr int NTHREADS = 64 + 32 * NEPI;    // + producer and MMA issuer
@@ -134,7 +138,7 @@ __global__ void __launch_bounds__(ConvCfg<KC, N>::NTHREADS, 1)
     uint8_t *ring = smem + Cfg::RING;
     constexpr int STAGES = Cfg::STAGES;
     static_assert(STAGES >= 2, "shared memory holds fewer than two halo buffers");
-    __shared__ __align__(8) uint64_t full_b[STAGES], empty_b[STAGES], tfull_b[2], tempty_b[2], done_b;
+    __shared__ __align__(8) uint64_t full_b[STAGES], empty_b[STAGES], tfull_b[Cfg::NACC], tempty_b[Cfg::NACC], done_b;
     __shared__ uint32_t taddr_s;
     __shared__ int abort_s;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -148,7 +152,7 @@ __global__ void __launch_bounds__(ConvCfg<KC, N>::NTHREADS, 1)
             mbar_init(smem_u32(&full_b[s]), 1);
             mbar_init(smem_u32(&empty_b[s]), 1);
         }
-        for (int k = 0; k < 2; ++k) {
+        for (int k = 0; k < Cfg::NACC; ++k) {
             mbar_init(smem_u32(&tfull_b[k]), 1);
             mbar_init(smem_u32(&tempty_b[k]), Cfg::NEPI);
         }
@@ -220,8 +224,8 @@ __global__ void __launch_bounds__(ConvCfg<KC, N>::NTHREADS, 1)
             uint32_t ph = 0;
             long long it = 0;
             for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
-                const int acc = (int)(it & 1);
-                const uint32_t aph = (uint32_t)((it >> 1) & 1);
+                const int acc = (int)(it % Cfg::NACC);
+                const uint32_t aph = (uint32_t)((it / Cfg::NACC) & 1);
                 if (!mbar_wait(smem_u32(&tempty_b[acc]), aph ^ 1, MBAR_LIMIT) ||
                     !mbar_wait(smem_u32(&full_b[s]), ph, MBAR_LIMIT) || *(volatile int *)&abort_s) {
                     atomicOr(a.status, ST_TIMEOUT);
@@ -282,8 +286,8 @@ __global__ void __launch_bounds__(ConvCfg<KC, N>::NTHREADS, 1)
                 for (int w = 0; w < 4; ++w) keep16[w] = r.v[w];
             }
 
-            const int acc = (int)(it & 1);
-            const uint32_t aph = (uint32_t)((it >> 1) & 1);
+            const int acc = (int)(it % Cfg::NACC);
+            const uint32_t aph = (uint32_t)((it / Cfg::NACC) & 1);
             const bool ok = mbar_wait(smem_u32(&tfull_b[acc]), aph, MBAR_LIMIT);
             if (!__all_sync(0xffffffffu, ok) || *(volatile int *)&abort_s) {
                 if (lane == 0) {
@@ -320,7 +324,7 @@ __global__ void __launch_bounds__(ConvCfg<KC, N>::NTHREADS, 1)
                 for (int j = 0; j < 8; ++j) {
                     float s = v[j] + bias8[j];
                     if (a.relu) s = fmaxf(s, 0.0f);
-                    if (a.drop_thr) {
+                    if (a.scale_out) {
                         const uint32_t f = (keep16[j >> 1] >> (16 * (j & 1))) & 0xFFFFu;
                         s = f >= a.drop_thr ? s * scale : 0.0f;
                     }
@@ -433,6 +437,343 @@ hyb_status launch_conv3_tc(const ConvArgs &a, cudaStream_t st) {
     if (a.cin == 32 && a.N == 16) return launch_cfg<4, 16>(a, st);
     if (a.cin == 16 && a.N == 16) return launch_cfg<2, 16>(a, st);
     return set_error(HYB_EINVAL, "conv channels: (C_in, C_out) in {16, 32} x {16, 32}");
+}
+
+
+// ---------------------------------------------------------------- last layer
+// k_conv_last_tc: the 16 -> 1 channel layer with all 27 taps in the MMA N
+// dimension.  A plane block of 16 (x) x 8 (y) cells (M = 128 rows, K = the 16
+// channels) times the weights of the 27 taps (N = 32, padded) gives, per cell
+// c and tap t, the partial product P[c][t] = sum_ci x[c][ci] w[t][ci] -- one
+// MMA per plane.  The output at cell c is y[c] = b + sum_t P[c + offset(t)][t]:
+// the z part of the sum runs in registers (a cell's own partials of three
+// consecutive planes), the in-plane 3 x 3 part through shared memory; the
+// 14 x 6 interior cells of the block have all their neighbours in it.  A CTA walks a column of such blocks through z
+// (chunks of LZC output planes plus one plane of halo on either side), so
+// every plane is multiplied once and used by three output planes.
+//   warp 0      TMA producer: one 16 x 8 x 1 x 16-channel box per plane
+//               (zero fill outside the volume) into a ring of LSTAGES;
+//   warp 1      MMA issuer: one tcgen05.mma (128 x 32 x 16) per plane into
+//               one of two TMEM accumulators;
+//   warps 2..5  epilogue: tcgen05.ld of the 32 columns, the z sums in
+//               registers, the 9 in-plane partials of the completed output
+//               plane into shared memory, a named barrier of the four warps,
+//               the 3 x 3 gather, bias, and the logit or the sigmoid folded
+//               into the MC mean / M2 (Welford).
+// Waits are bounded; a warp whose wait gives up records ST_TIMEOUT and stops
+// waiting, but the epilogue warps keep meeting at their barrier until the
+// end, so no warp is left behind at it.
+static constexpr int LTX = 16, LTY = 8;            // block (cells) = 128 MMA rows
+static constexpr int LOX = LTX - 2, LOY = LTY - 2; // interior outputs per block row / column
+static constexpr int LZC = 32;                     // output planes per work unit
+static constexpr int LSTAGES = 4;
+static constexpr int LCTAS = 4;                    // CTAs per SM (64 TMEM columns each)
+static constexpr int LPF = 3;                      // planes of MC statistics read ahead
+static constexpr int LSTAGE = LTX * LTY * 32;      // bytes of one plane block (4096)
+static constexpr int LSMEM = LSTAGES * LSTAGE + 2 * 9 * 128 * 4 + 1024 + 1024;  // ring, 2 x Q, weights, slack
+
+struct LastTiles {
+    int tx_n, ty_n, zc_n;
+    long long units;
+};
+
+__host__ __device__ inline LastTiles last_tiles(int B, int D, int H, int W) {
+    LastTiles t;
+    t.tx_n = (W + LOX - 1) / LOX;
+    t.ty_n = (H + LOY - 1) / LOY;
+    t.zc_n = (D + LZC - 1) / LZC;
+    t.units = (long long)B * t.zc_n * t.ty_n * t.tx_n;
+    return t;
+}
+
+// unit u -> block position and z range; planes z = zlo - 1 .. zhi
+__device__ inline void last_unit(long long u, const LastTiles &t, int D, int &tx, int &ty, int &zlo, int &zhi,
+                                 int &b) {
+    tx = (int)(u % t.tx_n);
+    u /= t.tx_n;
+    ty = (int)(u % t.ty_n);
+    u /= t.ty_n;
+    const int zc = (int)(u % t.zc_n);
+    b = (int)(u / t.zc_n);
+    zlo = zc * LZC;
+    zhi = min(zlo + LZC, D);
+}
+
+__global__ void __launch_bounds__(192, LCTAS) k_conv_last_tc(const __grid_constant__ CUtensorMap tmap,
+                                                      const __grid_constant__ LastArgs a) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t *ring = smem;                                          // LSTAGES x 4 KB (1 KB aligned)
+    uint8_t *wsm = smem + LSTAGES * LSTAGE;                        // 1 KB of weights
+    float *qs = reinterpret_cast<float *>(wsm + 1024);             // [2][9][128] in-plane partials Q
+    __shared__ __align__(8) uint64_t full_b[LSTAGES], empty_b[LSTAGES], tfull_b[2], tempty_b[2], done_b;
+    __shared__ uint32_t taddr_s;
+    __shared__ int abort_s;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    if (warp == 1) {
+        tmem_alloc(smem_u32(&taddr_s), 64);
+        tmem_relinquish();
+    }
+    if (tid == 0) {
+        for (int s = 0; s < LSTAGES; ++s) {
+            mbar_init(smem_u32(&full_b[s]), 1);
+            mbar_init(smem_u32(&empty_b[s]), 1);
+        }
+        for (int k = 0; k < 2; ++k) {
+            mbar_init(smem_u32(&tfull_b[k]), 1);
+            mbar_init(smem_u32(&tempty_b[k]), 4);
+        }
+        mbar_init(smem_u32(&done_b), 1);
+        abort_s = 0;
+        fence_mbar_init();
+        prefetch_tmap(&tmap);
+    }
+    for (int i = tid; i < 256; i += 192) reinterpret_cast<uint32_t *>(wsm)[i] = a.w[i];
+    fence_proxy_async_smem();
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t taddr = taddr_s;
+    const LastTiles lt = last_tiles(a.B, a.D, a.H, a.W);
+    const uint32_t ring_s = smem_u32(ring), w_s = smem_u32(wsm);
+
+    if (warp == 0) {
+        // ------------------------------------------------------------ producer
+        if (lane == 0) {
+            int s = 0;
+            uint32_t ph = 0;
+            long long issued = 0;
+            bool stop = false;
+            for (long long u = blockIdx.x; u < lt.units && !stop; u += gridDim.x) {
+                int tx, ty, zlo, zhi, b;
+                last_unit(u, lt, a.D, tx, ty, zlo, zhi, b);
+                for (int z = zlo - 1; z <= zhi; ++z) {
+                    if (!mbar_wait(smem_u32(&empty_b[s]), ph ^ 1, MBAR_LIMIT) || *(volatile int *)&abort_s) {
+                        atomicOr(a.status, ST_TIMEOUT);
+                        *(volatile int *)&abort_s = 1;
+                        stop = true;
+                        break;
+                    }
+                    const uint32_t fb = smem_u32(&full_b[s]);
+                    mbar_arrive_expect_tx(fb, LSTAGE);
+                    tma_load_5d(ring_s + (uint32_t)(s * LSTAGE), &tmap, 0, tx * LOX - 1, ty * LOY - 1, z, b, fb);
+                    ++issued;
+                    if (++s == LSTAGES) {
+                        s = 0;
+                        ph ^= 1;
+                    }
+                }
+            }
+            if (*(volatile int *)&abort_s) {
+                for (int k = 0; k < LSTAGES && issued > 0; ++k, --issued) {
+                    if (--s < 0) {
+                        s = LSTAGES - 1;
+                        ph ^= 1;
+                    }
+                    mbar_wait(smem_u32(&full_b[s]), ph, MBAR_LIMIT);
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            constexpr uint32_t idesc = idesc_bf16(128, 32);
+            const uint64_t a0 = smem_desc_sw32(ring_s, 8 * 32);
+            const uint64_t bd = smem_desc(w_s, 32 * 16, 128);
+            int s = 0;
+            uint32_t ph = 0;
+            long long it = 0;
+            bool stop = false;
+            for (long long u = blockIdx.x; u < lt.units && !stop; u += gridDim.x) {
+                int tx, ty, zlo, zhi, b;
+                last_unit(u, lt, a.D, tx, ty, zlo, zhi, b);
+                for (int z = zlo - 1; z <= zhi; ++z, ++it) {
+                    const int acc = (int)(it & 1);
+                    const uint32_t aph = (uint32_t)((it >> 1) & 1);
+                    if (!mbar_wait(smem_u32(&tempty_b[acc]), aph ^ 1, MBAR_LIMIT) ||
+                        !mbar_wait(smem_u32(&full_b[s]), ph, MBAR_LIMIT) || *(volatile int *)&abort_s) {
+                        atomicOr(a.status, ST_TIMEOUT);
+                        *(volatile int *)&abort_s = 1;
+                        stop = true;
+                        break;
+                    }
+                    fence_after_sync();
+                    umma_bf16(taddr + (uint32_t)(acc * 32), a0 + (uint64_t)((s * LSTAGE) >> 4), bd, idesc, 0);
+                    umma_commit(smem_u32(&empty_b[s]));
+                    umma_commit(smem_u32(&tfull_b[acc]));
+                    if (++s == LSTAGES) {
+                        s = 0;
+                        ph ^= 1;
+                    }
+                }
+            }
+            umma_commit(smem_u32(&done_b));
+            mbar_wait(smem_u32(&done_b), 0, MBAR_LIMIT);
+        }
+    } else {
+        // ------------------------------------------------------------ epilogue
+        // With P_z[c][t] the partials of plane z, the output of plane o at
+        // cell c is b + sum over (dy, dx) of Q_o[c + (dy - 1, dx - 1)][dy, dx],
+        // where Q_o[c][dy, dx] = sum over dz of P_{o + dz - 1}[c][(dz, dy, dx)]
+        // needs only the cell's own rows: each thread accumulates it in
+        // registers as the planes stream past (r1: plane o + 1's part so far,
+        // r2: plane o's), and only the 9 values of Q cross threads, through a
+        // double-buffered shared array and one barrier per plane.
+        const int q = warp & 3;
+        const int m = q * 32 + lane;                 // row = cell of the block
+        const int lx = m & (LTX - 1), ly = m >> 4;
+        const bool interior = lx >= 1 && lx <= LOX && ly >= 1 && ly <= LOY;
+        bool dead = false;
+        const long long V = (long long)a.D * a.H * a.W;
+        long long it = 0;
+        for (long long u = blockIdx.x; u < lt.units; u += gridDim.x) {
+            int tx, ty, zlo, zhi, b;
+            last_unit(u, lt, a.D, tx, ty, zlo, zhi, b);
+            const int cx = tx * LOX + lx - 1, cy = ty * LOY + ly - 1;
+            const bool valid = interior && cx < a.W && cy < a.H;
+            float r1[9], r2[9];
+#pragma unroll
+            for (int k = 0; k < 9; ++k) r1[k] = r2[k] = 0.0f;
+            // MC statistics of output planes zo .. zo + LPF - 1, read LPF planes
+            // ahead so that their latency spans several planes
+            // (at the top of the iteration for output plane zo, entry k holds plane zo + k)
+            const long long HW = (long long)a.H * a.W;
+            const long long t0 = (long long)b * V + ((long long)(zlo - 2) * a.H + cy) * a.W + cx;
+            float pmq[LPF], m2q[LPF];
+#pragma unroll
+            for (int k = 0; k < LPF; ++k) {
+                pmq[k] = m2q[k] = 0.0f;
+                const int zk = zlo - 2 + k;
+                if (valid && a.mc_k >= 2 && zk >= zlo && zk < zhi) {
+                    pmq[k] = a.pm[t0 + k * HW];
+                    m2q[k] = a.m2[t0 + k * HW];
+                }
+            }
+            for (int z = zlo - 1; z <= zhi; ++z, ++it) {
+                const int acc = (int)(it & 1);
+                const uint32_t aph = (uint32_t)((it >> 1) & 1);
+                const int zo = z - 1;                // output plane completed by plane z
+                const bool out = valid && zo >= zlo;
+                const long long t = (long long)b * V + ((long long)zo * a.H + cy) * a.W + cx;
+                const float mo = pmq[0], m2o = m2q[0];
+#pragma unroll
+                for (int k = 0; k + 1 < LPF; ++k) {
+                    pmq[k] = pmq[k + 1];
+                    m2q[k] = m2q[k + 1];
+                }
+                pmq[LPF - 1] = m2q[LPF - 1] = 0.0f;
+                if (valid && a.mc_k >= 2 && zo + LPF >= zlo && zo + LPF < zhi) {
+                    pmq[LPF - 1] = a.pm[t + LPF * HW];
+                    m2q[LPF - 1] = a.m2[t + LPF * HW];
+                }
+                if (!dead) {
+                    const bool ok = mbar_wait(smem_u32(&tfull_b[acc]), aph, MBAR_LIMIT) &&
+                                    !*(volatile int *)&abort_s;
+                    if (!__all_sync(0xffffffffu, ok)) {
+                        if (lane == 0) {
+                            atomicOr(a.status, ST_TIMEOUT);
+                            *(volatile int *)&abort_s = 1;
+                        }
+                        dead = true;
+                    }
+                }
+                float p[32];
+                if (!dead) {
+                    fence_after_sync();
+                    tmem_ld32(taddr + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * 32), p);
+                    fence_before_sync();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(smem_u32(&tempty_b[acc]));
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 32; ++k) p[k] = 0.0f;
+                }
+                // plane z is tap dz = 2 of output zo, dz = 1 of zo + 1, dz = 0 of zo + 2
+                float *qb = qs + (int)(it & 1) * (9 * 128);
+#pragma unroll
+                for (int k = 0; k < 9; ++k) {
+                    qb[k * 128 + m] = r2[k] + p[18 + k];
+                    r2[k] = r1[k] + p[9 + k];
+                    r1[k] = p[k];
+                }
+                // Q of plane zo is complete (and the buffer written two planes
+                // ago is no longer read): the four epilogue warps meet
+                asm volatile("bar.sync 1, 128;" ::: "memory");
+                if (!dead && out) {
+                    float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f;
+#pragma unroll
+                    for (int dx = 0; dx < 3; ++dx) {
+                        s0 += qb[(0 * 3 + dx) * 128 + m - LTX + dx - 1];
+                        s1 += qb[(1 * 3 + dx) * 128 + m + dx - 1];
+                        s2 += qb[(2 * 3 + dx) * 128 + m + LTX + dx - 1];
+                    }
+                    const float logit = a.bias + s0 + s1 + s2;
+                    if (a.mc_k == 0) {
+                        a.logit[t] = logit;
+                    } else {
+                        const float pv = 1.0f / (1.0f + expf(-logit));
+                        if (a.mc_k == 1) {
+                            a.pm[t] = pv;
+                            a.m2[t] = 0.0f;
+                        } else {
+                            const float d = pv - mo;
+                            const float mn = mo + d / (float)a.mc_k;
+                            a.pm[t] = mn;
+                            a.m2[t] = m2o + d * (pv - mn);
+                        }
+                    }
+                }
+            }
+        }
+    }
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    if (warp == 1) tmem_dealloc(taddr, 64);
+}
+
+hyb_status launch_conv_last_tc(const LastArgs &a, cudaStream_t st) {
+    if (a.B < 1 || a.D < 1 || a.H < 1 || a.W < 1) return set_error(HYB_EINVAL, "last layer: empty volume");
+    if (((uintptr_t)a.x & 15) || (a.mc_k == 0 && !a.logit) || (a.mc_k > 0 && (!a.pm || !a.m2)))
+        return set_error(HYB_EINVAL, "last layer: operands missing or not 16-byte aligned");
+    const LastTiles lt = last_tiles(a.B, a.D, a.H, a.W);
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return set_error(HYB_ECUDA, "cuTensorMapEncodeTiled is not available");
+    CUtensorMap tm;
+    const cuuint64_t dims[5] = {16, (cuuint64_t)a.W, (cuuint64_t)a.H, (cuuint64_t)a.D, (cuuint64_t)a.B};
+    const cuuint64_t strides[4] = {32ull, 32ull * a.W, 32ull * a.W * a.H, 32ull * a.W * a.H * a.D};
+    const cuuint32_t box[5] = {16, (cuuint32_t)LTX, (cuuint32_t)LTY, 1, 1};
+    const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    CUresult r = enc(&tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, (void *)a.x, dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return set_error(HYB_ECUDA, "last layer: tensor map (" + std::to_string((int)r) + ")");
+    static std::mutex mu;
+    static int ready_dev[64] = {0}, nsm_dev[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return set_error(HYB_EINVAL, "device index out of range");
+    int nsm;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (!ready_dev[dev]) {
+            cudaError_t e = cudaFuncSetAttribute(k_conv_last_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, LSMEM);
+            if (e != cudaSuccess)
+                return set_error(HYB_ECUDA, std::string("last layer smem attribute: ") + cudaGetErrorString(e));
+            cudaDeviceGetAttribute(&nsm_dev[dev], cudaDevAttrMultiProcessorCount, dev);
+            ready_dev[dev] = 1;
+        }
+        nsm = nsm_dev[dev];
+    }
+    // LCTAS CTAs per SM by registers and shared memory (the occupancy query
+    // answers 1 for kernels that allocate tensor memory); units are
+    // independent, so any residency gives the same result
+    const long long grid = std::min<long long>(lt.units, (long long)nsm * LCTAS);
+    k_conv_last_tc<<<(unsigned)grid, 192, LSMEM, st>>>(tm, a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return set_error(HYB_ECUDA, std::string("last layer launch: ") + cudaGetErrorString(e));
+    return HYB_OK;
 }
 
 }  // namespace hyb

@@ -155,6 +155,23 @@ __device__ __forceinline__ void tmem_ld8x3(uint32_t t0, uint32_t t1, uint32_t t2
     for (int i = 0; i < 24; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 32 lanes x 32 bits, 32 consecutive columns under one wait
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float v[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 // 32 lanes x 32 bits, 16 consecutive columns: thread i of the warp gets lane (32w + i)
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
     uint32_t r[16];
@@ -185,9 +202,25 @@ struct ConvArgs {
     int relu;
     uint32_t drop_thr;        // dropout threshold round(p 2^16) on 16-bit Philox fields; 0: no dropout
     float drop_scale;         // 1 / (1 - drop_thr 2^-16)
+    int scale_out;            // kept outputs are multiplied by drop_scale (set with dropout; alone: scaling only)
     uint32_t seed, pass, layer;
     int *status;
 };
 hyb_status launch_conv3_tc(const ConvArgs &a, cudaStream_t st);
+
+// the last layer (16 -> 1 channel, 3x3x3) on the tensor cores (see conv.cu);
+// mc_k = 0 writes the logit, mc_k = k >= 1 folds sigmoid(logit) into the
+// running mean / M2 of the MC passes (k = 1 starts them)
+struct LastArgs {
+    const __nv_bfloat16 *x;   // [B][D][H][W][16] channels-last
+    uint32_t w[256];          // BF16 weights as B operand: [ci / 8][tap (27, padded to 32)][ci % 8]
+    float bias;
+    int B, D, H, W;
+    float *logit;             // [B][D][H][W] (mc_k = 0)
+    int mc_k;
+    float *pm, *m2;           // MC mean and M2 (mc_k >= 1)
+    int *status;
+};
+hyb_status launch_conv_last_tc(const LastArgs &a, cudaStream_t st);
 
 }  // namespace hyb
