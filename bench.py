@@ -140,9 +140,9 @@ FDTD_BYTES_PER_CELL = 120
 FLUID_BYTES_PER_NODE = 32
 FLUID_FIELD_BYTES_PER_NODE = 24
 # DRAM read + write per cell of one launch of the 32 -> 32 convolution, from
-# the ncu capture on the 128 x 128 x 64 ramp + slab (67.2 + 22.4 MB for
+# the ncu capture on the 128 x 128 x 64 ramp + slab (67.2 + 20.2 MB for
 # 1,048,576 cells); scaled to a full launch by the cell count
-NCU_CONV_L1_BYTES_PER_CELL = 89.6e6 / 1048576
+NCU_CONV_L1_BYTES_PER_CELL = 87.4e6 / 1048576
 
 
 def make_model(P, stream):
