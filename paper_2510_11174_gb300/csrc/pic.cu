@@ -59,21 +59,18 @@ __device__ __forceinline__ AxisW axis_weights(const GridDev &g, int a, float p, 
     return r;
 }
 
+// trilinear interpolation as seven linear interpolations (x, then y, then z)
 __device__ __forceinline__ float interp8(const float *__restrict__ f, int F, int bx, int by, int bz, float fx,
                                          float fy, float fz) {
-    float acc = 0.0f;
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {
-        const float wz = c ? fz : 1.0f - fz;
-#pragma unroll
-        for (int b = 0; b < 2; ++b) {
-            const float wy = b ? fy : 1.0f - fy;
-            const float *row = f + ((bz + c) * F + (by + b)) * F + bx;
-            acc += (1.0f - fx) * wy * wz * row[0];
-            acc += fx * wy * wz * row[1];
-        }
-    }
-    return acc;
+    const float *r00 = f + (bz * F + by) * F + bx;   // rows (y, z), (y + 1, z), (y, z + 1), (y + 1, z + 1)
+    const float *r10 = r00 + F, *r01 = r00 + F * F, *r11 = r01 + F;
+    const float a00 = fmaf(fx, r00[1] - r00[0], r00[0]);
+    const float a10 = fmaf(fx, r10[1] - r10[0], r10[0]);
+    const float a01 = fmaf(fx, r01[1] - r01[0], r01[0]);
+    const float a11 = fmaf(fx, r11[1] - r11[0], r11[0]);
+    const float b0 = fmaf(fy, a10 - a00, a00);
+    const float b1 = fmaf(fy, a11 - a01, a01);
+    return fmaf(fz, b1 - b0, b0);
 }
 
 __device__ __forceinline__ void shape3(float p, int gbase, float S[3]) {
@@ -249,7 +246,7 @@ __global__ void __launch_bounds__(256, 3) k_push_deposit(GridDev g, const float 
                     // W_c is nonzero only at the cell's lower c-face, at the 2 x 2
                     // transverse nodes (the general form below with its zero terms dropped)
                     int lb[3];
-                    float s0[3][2], ds[3][2];
+                    float s0[3][2], ds[3][2], ca[3][2], cb[3][2];
 #pragma unroll
                     for (int a = 0; a < 3; ++a) {
                         const float c0 = floorf(x0[a]);
@@ -257,10 +254,15 @@ __global__ void __launch_bounds__(256, 3) k_push_deposit(GridDev g, const float 
                         float S0f[3], S1f[3];
                         shape3(x0[a], (int)c0, S0f);
                         shape3(x1[a], (int)c0, S1f);
-                        s0[a][0] = S0f[0];
-                        s0[a][1] = S0f[1];
-                        ds[a][0] = S1f[0] - S0f[0];
-                        ds[a][1] = S1f[1] - S0f[1];
+#pragma unroll
+                        for (int k = 0; k < 2; ++k) {
+                            s0[a][k] = S0f[k];
+                            ds[a][k] = S1f[k] - S0f[k];
+                            // the transverse factor S0p S0q + DSp S0q / 2 + S0p DSq / 2 + DSp DSq / 3
+                            // = S0p (S0q + DSq / 2) + DSp (S0q / 2 + DSq / 3)
+                            ca[a][k] = s0[a][k] + 0.5f * ds[a][k];
+                            cb[a][k] = 0.5f * s0[a][k] + ds[a][k] * (1.0f / 3.0f);
+                        }
                     }
                     const float qw = q * wgt;
 #pragma unroll
@@ -272,10 +274,8 @@ __global__ void __launch_bounds__(256, 3) k_push_deposit(GridDev g, const float 
                         for (int bq = 0; bq < 2; ++bq)
 #pragma unroll
                             for (int bp = 0; bp < 2; ++bp) {
-                                const float cross = s0[pa][bp] * s0[qa][bq] + 0.5f * ds[pa][bp] * s0[qa][bq] +
-                                                    0.5f * s0[pa][bp] * ds[qa][bq] +
-                                                    ds[pa][bp] * ds[qa][bq] * (1.0f / 3.0f);
-                                const float acc = 0.0f + ds[c][0] * cross;
+                                const float cross = fmaf(ds[pa][bp], cb[qa][bq], s0[pa][bp] * ca[qa][bq]);
+                                const float acc = ds[c][0] * cross;
                                 if (acc != 0.0f) {
                                     int l3[3];
                                     l3[c] = lb[c];
@@ -287,7 +287,7 @@ __global__ void __launch_bounds__(256, 3) k_push_deposit(GridDev g, const float 
                     }
                 } else if (q != 0.0f) {
                     int lb[3];
-                    float S0[3][3], DS[3][3];
+                    float S0[3][3], DS[3][3], CA[3][3], CB[3][3];
 #pragma unroll
                     for (int a = 0; a < 3; ++a) {
                         const int i0 = (int)floorf(x0[a]), i1 = (int)floorf(x1[a]);
@@ -297,7 +297,11 @@ __global__ void __launch_bounds__(256, 3) k_push_deposit(GridDev g, const float 
                         shape3(x0[a], gb, S0[a]);
                         shape3(x1[a], gb, S1);
 #pragma unroll
-                        for (int k = 0; k < 3; ++k) DS[a][k] = S1[k] - S0[a][k];
+                        for (int k = 0; k < 3; ++k) {
+                            DS[a][k] = S1[k] - S0[a][k];
+                            CA[a][k] = S0[a][k] + 0.5f * DS[a][k];
+                            CB[a][k] = 0.5f * S0[a][k] + DS[a][k] * (1.0f / 3.0f);
+                        }
                     }
                     const float qw = q * wgt;
 #pragma unroll
@@ -309,9 +313,7 @@ __global__ void __launch_bounds__(256, 3) k_push_deposit(GridDev g, const float 
                         for (int bq = 0; bq < 3; ++bq)
 #pragma unroll
                             for (int bp = 0; bp < 3; ++bp) {
-                                const float cross = S0[pa][bp] * S0[qa][bq] + 0.5f * DS[pa][bp] * S0[qa][bq] +
-                                                    0.5f * S0[pa][bp] * DS[qa][bq] +
-                                                    DS[pa][bp] * DS[qa][bq] * (1.0f / 3.0f);
+                                const float cross = fmaf(DS[pa][bp], CB[qa][bq], S0[pa][bp] * CA[qa][bq]);
                                 float acc = 0.0f;
 #pragma unroll
                                 for (int a = 0; a < 2; ++a) {
