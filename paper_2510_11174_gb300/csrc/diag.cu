@@ -29,42 +29,40 @@ __global__ void __launch_bounds__(RB) k_energy_fields(GridDev g, const float *__
                                                       const float *__restrict__ B, double *__restrict__ partials,
                                                       int nblocks, int *__restrict__ status) {
     __shared__ double sh[RB];
-    double se = 0.0, sb = 0.0;
+    ff se = {0.0f, 0.0f}, sb = {0.0f, 0.0f};  // each square is exact, the sums double-float
     bool finite = true;
     const long long n3 = 3 * g.N;
     for (long long c = blockIdx.x * (long long)RB + threadIdx.x; c < n3; c += (long long)nblocks * RB) {
-        const double e = E[c], b = B[c];
+        const float e = E[c], b = B[c];
         finite = finite && isfinite(e) && isfinite(b);
-        se += e * e;
-        sb += b * b;
+        se = ff_add(se, ff_two_prod(e, e));
+        sb = ff_add(sb, ff_two_prod(b, b));
     }
     if (!finite) atomicOr(status, ST_NAN);
-    se = block_sum(se, sh);
-    sb = block_sum(sb, sh);
+    const double te = block_sum(ff_to_double(se), sh);
+    const double tb = block_sum(ff_to_double(sb), sh);
     if (threadIdx.x == 0) {
-        partials[blockIdx.x] = se;
-        partials[nblocks + blockIdx.x] = sb;
+        partials[blockIdx.x] = te;
+        partials[nblocks + blockIdx.x] = tb;
     }
 }
 
-// m (gamma - 1) written as m u^2 / (gamma + 1) (no cancellation for slow particles)
+// sum over particles of w (gamma - 1) (massive; times m per block) or w |u| (photons)
 __global__ void __launch_bounds__(RB) k_energy_species(GridDev g, SpDev sp, double *__restrict__ partials,
                                                        int nblocks) {
     __shared__ double sh[RB];
-    double acc = 0.0;
+    ff acc = {0.0f, 0.0f};
     for (int t = blockIdx.x; t < g.ntiles; t += nblocks) {
         const int n = min(sp.count[t], sp.cap);
         const long long base = (long long)t * sp.cap;
         for (int p = threadIdx.x; p < n; p += RB) {
-            const double ux = sp.ux[base + p], uy = sp.uy[base + p], uz = sp.uz[base + p];
-            const double u2 = ux * ux + uy * uy + uz * uz;
-            // photons carry w |k| (m c^2 units); massive particles w m (gamma - 1)
-            acc += sp.kind == 1 ? (double)sp.w[base + p] * norm_from_sq(u2)
-                                : (double)sp.w[base + p] * sp.m_d * gamma_minus_one(u2);
+            const ff u2 = ff_u2(sp.ux[base + p], sp.uy[base + p], sp.uz[base + p]);
+            const ff term = sp.kind == 1 ? ff_norm(u2) : ff_gamma_minus_one(u2);
+            acc = ff_add(acc, ff_mulf(term, sp.w[base + p]));
         }
     }
-    acc = block_sum(acc, sh);
-    if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+    const double tot = block_sum(ff_to_double(acc), sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = sp.kind == 1 ? tot : tot * sp.m_d;
 }
 
 __global__ void __launch_bounds__(RB) k_final(const double *__restrict__ partials, int nq, int nblocks,

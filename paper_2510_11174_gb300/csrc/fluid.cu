@@ -151,13 +151,14 @@ static constexpr int FB = 256;
 __global__ void __launch_bounds__(FB) k_fluid_energy(GridDev g, FluidDev f, double *__restrict__ p_w,
                                                      double *__restrict__ p_n, int nblocks) {
     __shared__ double sh[FB];
-    double aw = 0.0, an = 0.0;
+    // double-float sums of n (gamma - 1) and n; m and dV applied to the block sums
+    ff sw = {0.0f, 0.0f}, sn = {0.0f, 0.0f};
     for (long long c = blockIdx.x * (long long)FB + threadIdx.x; c < g.N; c += (long long)nblocks * FB) {
-        const double n = f.n[c], ux = f.ux[c], uy = f.uy[c], uz = f.uz[c];
-        const double u2 = ux * ux + uy * uy + uz * uz;
-        aw += n * f.m_d * gamma_minus_one(u2);
-        an += n;
+        const float n = f.n[c];
+        sw = ff_add(sw, ff_mulf(ff_gamma_minus_one(ff_u2(f.ux[c], f.uy[c], f.uz[c])), n));
+        sn = ff_add(sn, ff{n, 0.0f});
     }
+    const double aw = ff_to_double(sw), an = ff_to_double(sn);
     const double dV = g.dd[0] * g.dd[1] * g.dd[2];
     for (int q = 0; q < 2; ++q) {
         sh[threadIdx.x] = q == 0 ? aw : an;
@@ -166,7 +167,7 @@ __global__ void __launch_bounds__(FB) k_fluid_energy(GridDev g, FluidDev f, doub
             if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
             __syncthreads();
         }
-        if (threadIdx.x == 0) (q == 0 ? p_w : p_n)[blockIdx.x] = sh[0] * dV;
+        if (threadIdx.x == 0) (q == 0 ? p_w : p_n)[blockIdx.x] = q == 0 ? sh[0] * f.m_d * dV : sh[0] * dV;
         __syncthreads();
     }
 }

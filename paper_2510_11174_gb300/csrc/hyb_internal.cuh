@@ -36,30 +36,63 @@ __host__ __device__ inline long long cidx(const GridDev &g, int i, int j, int k)
 }
 
 #ifdef __CUDACC__
-// FP64 kinetic-energy helpers of the reductions.  FP64 square roots and
-// divisions are slow on this part, so 1/sqrt(x) and 1/x start from the FP32
-// hardware estimates and take two Newton-Raphson steps in FP64
-// (y <- y (3 - x y^2) / 2 and r <- r (2 - x r)); each step squares the
-// relative error, so the FP32 estimate's ~1e-7 ends below FP64 rounding.
-__device__ __forceinline__ double rsqrt_f64(double x) {
-    double y = (double)rsqrtf((float)x);
-    y = y * (1.5 - 0.5 * x * y * y);
-    return y * (1.5 - 0.5 * x * y * y);
+// Kinetic-energy terms of the FP64 reductions in double-float arithmetic: a
+// value is an unevaluated sum hi + lo of two FP32 numbers (about 48 mantissa
+// bits).  FP64 arithmetic runs at a small fraction of the FP32 rate on this
+// part, so the per-particle and per-cell terms are formed on the FP32 units
+// with error-free transformations -- two-sum (Knuth), two-product by fused
+// multiply-add (Dekker's exact product) -- and only block partials are
+// converted to FP64.  Relative error of a term: a few units of 2^-48.
+struct ff {
+    float h, l;
+};
+__device__ __forceinline__ ff ff_two_sum(float a, float b) {
+    const float s = a + b, bb = s - a;
+    return {s, (a - (s - bb)) + (b - bb)};
 }
-__device__ __forceinline__ double rcp_f64(double x) {
-    double r = (double)(1.0f / (float)x);
-    r = r * (2.0 - x * r);
-    return r * (2.0 - x * r);
+__device__ __forceinline__ ff ff_fast_two_sum(float a, float b) {  // |a| >= |b| or a == 0
+    const float s = a + b;
+    return {s, b - (s - a)};
+}
+__device__ __forceinline__ ff ff_two_prod(float a, float b) {
+    const float p = a * b;
+    return {p, fmaf(a, b, -p)};
+}
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+    const ff s = ff_two_sum(a.h, b.h);
+    return ff_fast_two_sum(s.h, s.l + (a.l + b.l));
+}
+__device__ __forceinline__ ff ff_mulf(ff a, float b) {
+    const ff p = ff_two_prod(a.h, b);
+    return ff_fast_two_sum(p.h, fmaf(a.l, b, p.l));
+}
+// square root of a > 0: the correctly rounded FP32 root s plus the Newton
+// correction (a - s^2) / (2 s); a.h - s^2 is exact by the fused multiply-add
+__device__ __forceinline__ ff ff_sqrt(ff a) {
+    const float s = sqrtf(a.h);
+    const float r = fmaf(-s, s, a.h) + a.l;
+    return ff_fast_two_sum(s, r * (0.5f / s));
+}
+// a / b (b > 0): FP32 quotient q0, then the quotient of the exact residual
+__device__ __forceinline__ ff ff_div(ff a, ff b) {
+    const float rc = __frcp_rn(b.h);
+    const float q0 = a.h * rc;
+    const ff pb = ff_mulf(b, -q0);
+    const ff r = ff_add(a, pb);
+    return ff_fast_two_sum(q0, r.h * rc);
+}
+__device__ __forceinline__ double ff_to_double(ff a) { return (double)a.h + (double)a.l; }
+// u^2 = ux^2 + uy^2 + uz^2 of FP32 components (each square exact)
+__device__ __forceinline__ ff ff_u2(float ux, float uy, float uz) {
+    return ff_add(ff_add(ff_two_prod(ux, ux), ff_two_prod(uy, uy)), ff_two_prod(uz, uz));
 }
 // gamma - 1 = u^2 / (gamma + 1) (no cancellation for slow particles)
-__device__ __forceinline__ double gamma_minus_one(double u2) {
-    const double x = 1.0 + u2;
-    return u2 * rcp_f64(x * rsqrt_f64(x) + 1.0);
+__device__ __forceinline__ ff ff_gamma_minus_one(ff u2) {
+    const ff g = ff_sqrt(ff_add(u2, ff{1.0f, 0.0f}));
+    return ff_div(u2, ff_add(g, ff{1.0f, 0.0f}));
 }
 // |u| for photons (0 at u = 0)
-__device__ __forceinline__ double norm_from_sq(double u2) {
-    return u2 > 1e-30 ? u2 * rsqrt_f64(u2) : sqrt(u2);  // FP32 estimates need a normal FP32 argument
-}
+__device__ __forceinline__ ff ff_norm(ff u2) { return u2.h > 0.0f ? ff_sqrt(u2) : ff{0.0f, 0.0f}; }
 
 // Position of v on a grid uniform in log2 v with npo points per octave that
 // starts at 2^e0.  The octave comes from the binary exponent (exact) and the
