@@ -216,6 +216,7 @@ hyb_status hyb_init_grid(const hyb_grid_desc *d, hyb_ctx **out) {
         ctx_alloc(c, (void **)&c->jvalid, sizeof(int) * (size_t)g.ntiles) ||
         ctx_alloc(c, (void **)&c->red_partials, sizeof(double) * (2 + HYB_MAX_SPECIES + 2 * HYB_MAX_FLUIDS) * c->red_blocks) ||
         ctx_alloc(c, (void **)&c->red_out, sizeof(double) * (2 + HYB_MAX_SPECIES + 2 * HYB_MAX_FLUIDS)) ||
+        ctx_alloc(c, (void **)&c->diag_dev, sizeof(DiagSummary)) ||
         ctx_alloc(c, (void **)&c->status, sizeof(int)) || ctx_alloc(c, (void **)&c->step_dev, sizeof(long long)) ||
         ctx_alloc(c, (void **)&c->mig_counts, sizeof(int) * HYB_MAX_SPECIES) ||
         ctx_alloc(c, (void **)&c->fill_flags, sizeof(int)) ||
@@ -235,6 +236,7 @@ hyb_status hyb_init_grid(const hyb_grid_desc *d, hyb_ctx **out) {
     cudaMemsetAsync(c->mask, 0, (size_t)g.N, st);  // no node has switched to kinetic before a classification
     cudaMemsetAsync(c->fill_flags, 0, sizeof(int), st);
     if (cudaMallocHost((void **)&c->fill_host, sizeof(int)) != cudaSuccess ||
+        cudaMallocHost((void **)&c->diag_host, sizeof(DiagSummary)) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->fill_ev, cudaEventDisableTiming) != cudaSuccess)
         return fail(HYB_ENOMEM, "pinned fill flag");
     *c->fill_host = 0;
@@ -282,6 +284,7 @@ void hyb_destroy(hyb_ctx *c) {
     }
     for (void *p : c->owned) cudaFree(p);
     if (c->fill_host) cudaFreeHost(c->fill_host);
+    if (c->diag_host) cudaFreeHost(c->diag_host);
     if (c->fill_ev) cudaEventDestroy(c->fill_ev);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
@@ -1011,22 +1014,19 @@ hyb_status hyb_diagnostics(hyb_ctx *c, hyb_diag *out) {
         launch_fluid_energy(c->g, c->fluids[f], pw, pw + c->red_blocks, c->red_blocks, c->stream);
     }
     launch_energy(c->g, c->E, c->B, set, c->red_partials, c->red_blocks, c->red_out, c->status, c->stream, 2 * nfl);
-    double r[2 + HYB_MAX_SPECIES + 2 * HYB_MAX_FLUIDS];
-    HYB_CUDA_TRY(cudaMemcpyAsync(r, c->red_out, sizeof(double) * (2 + set.n + 2 * nfl), cudaMemcpyDeviceToHost,
-                                 c->stream));
-    int h = 0;
-    HYB_CUDA_TRY(cudaMemcpyAsync(&h, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-    std::vector<int> cnt((size_t)c->g.ntiles);
-    out->n_species = set.n;
-    for (int s = 0; s < set.n; ++s) {
-        HYB_CUDA_TRY(cudaMemcpyAsync(cnt.data(), set.s[s].count, sizeof(int) * cnt.size(), cudaMemcpyDeviceToHost,
-                                     c->stream));
-        HYB_CUDA_TRY(cudaStreamSynchronize(c->stream));
-        long long tot = 0;
-        for (int v : cnt) tot += std::min(v, set.s[s].cap);
-        out->count[s] = tot;
-    }
+    ClampPtrs cl;
+    memset(&cl, 0, sizeof(cl));
+    cl.n = nfl;
+    for (int f = 0; f < nfl; ++f) cl.p[f] = c->fluids[f].clamped;
+    launch_diag_summary(set, c->g.ntiles, c->red_out, 2 + set.n + 2 * nfl, cl, c->status, c->diag_dev, c->stream);
+    HYB_CUDA_TRY(cudaGetLastError());
+    HYB_CUDA_TRY(cudaMemcpyAsync(c->diag_host, c->diag_dev, sizeof(DiagSummary), cudaMemcpyDeviceToHost, c->stream));
     HYB_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    const DiagSummary &ds = *c->diag_host;
+    const double *r = ds.red;
+    const int h = ds.status;
+    out->n_species = set.n;
+    for (int s = 0; s < set.n; ++s) out->count[s] = ds.count[s];
     out->step = c->step;
     out->time = c->step * c->g.dt_d;
     out->w_e = r[0];
@@ -1040,30 +1040,16 @@ hyb_status hyb_diagnostics(hyb_ctx *c, hyb_diag *out) {
     for (int f = 0; f < nfl; ++f) {
         out->w_fluid[f] = r[2 + set.n + 2 * f];
         out->n_fluid[f] = r[2 + set.n + 2 * f + 1];
-        unsigned long long cl = 0;
-        HYB_CUDA_TRY(cudaMemcpyAsync(&cl, c->fluids[f].clamped, sizeof(cl), cudaMemcpyDeviceToHost, c->stream));
-        HYB_CUDA_TRY(cudaStreamSynchronize(c->stream));
-        out->n_clamped += (long long)cl;
+        out->n_clamped += (long long)ds.clamped[f];
     }
-    // event tallies: per-tile FP64 accumulators summed here in tile order
-    std::vector<double> te((size_t)c->g.ntiles * NTALLY);
-    std::vector<unsigned long long> tn((size_t)c->g.ntiles * NTALLY);
+    // event tallies: per-tile FP64 accumulators, summed on the device
     for (int s = 0; s < set.n; ++s) {
-        HYB_CUDA_TRY(cudaMemcpyAsync(te.data(), set.s[s].tal_e, sizeof(double) * te.size(), cudaMemcpyDeviceToHost,
-                                     c->stream));
-        HYB_CUDA_TRY(cudaMemcpyAsync(tn.data(), set.s[s].tal_n, sizeof(unsigned long long) * tn.size(),
-                                     cudaMemcpyDeviceToHost, c->stream));
-        HYB_CUDA_TRY(cudaStreamSynchronize(c->stream));
-        for (int t = 0; t < c->g.ntiles; ++t) {
-            const double *e = &te[(size_t)t * NTALLY];
-            const unsigned long long *k = &tn[(size_t)t * NTALLY];
-            out->w_ionize += e[TALLY_IONIZE];
-            out->n_ionize += (long long)k[TALLY_IONIZE];
-            out->w_photon_untracked += e[TALLY_EMIT];
-            out->n_emit += (long long)k[TALLY_EMIT];
-            out->w_pair_deficit += e[TALLY_PAIR];
-            out->n_pair += (long long)k[TALLY_PAIR];
-        }
+        out->w_ionize += ds.tal_e[s][TALLY_IONIZE];
+        out->n_ionize += (long long)ds.tal_n[s][TALLY_IONIZE];
+        out->w_photon_untracked += ds.tal_e[s][TALLY_EMIT];
+        out->n_emit += (long long)ds.tal_n[s][TALLY_EMIT];
+        out->w_pair_deficit += ds.tal_e[s][TALLY_PAIR];
+        out->n_pair += (long long)ds.tal_n[s][TALLY_PAIR];
     }
     if (h) {
         c->error_latched = true;

@@ -76,6 +76,47 @@ __global__ void __launch_bounds__(RB) k_final(const double *__restrict__ partial
     }
 }
 
+// block s < set.n: particle count and event tallies of species s, summed
+// over the tiles in a fixed order (thread-strided, then a shared-memory
+// tree); block set.n: the reduction results, clamp counters and status word
+__global__ void __launch_bounds__(RB) k_diag_summary(SpSet set, int ntiles, const double *__restrict__ red, int nred,
+                                                     ClampPtrs cl, const int *__restrict__ status,
+                                                     DiagSummary *__restrict__ out) {
+    __shared__ double sh[RB];
+    const int b = blockIdx.x;
+    if (b < set.n) {
+        const SpDev &sp = set.s[b];
+        double cnt = 0.0, te[NTALLY] = {0.0, 0.0, 0.0}, tn[NTALLY] = {0.0, 0.0, 0.0};  // exact below 2^53
+        for (int t = threadIdx.x; t < ntiles; t += RB) {
+            cnt += (double)min(sp.count[t], sp.cap);
+#pragma unroll
+            for (int k = 0; k < NTALLY; ++k) {
+                te[k] += sp.tal_e[(long long)t * NTALLY + k];
+                tn[k] += (double)sp.tal_n[(long long)t * NTALLY + k];
+            }
+        }
+        const double c = block_sum(cnt, sh);
+        if (threadIdx.x == 0) out->count[b] = (long long)c;
+#pragma unroll
+        for (int k = 0; k < NTALLY; ++k) {
+            const double e = block_sum(te[k], sh), n = block_sum(tn[k], sh);
+            if (threadIdx.x == 0) {
+                out->tal_e[b][k] = e;
+                out->tal_n[b][k] = (unsigned long long)n;
+            }
+        }
+    } else {
+        for (int i = threadIdx.x; i < nred; i += RB) out->red[i] = red[i];
+        if (threadIdx.x < cl.n) out->clamped[threadIdx.x] = *cl.p[threadIdx.x];
+        if (threadIdx.x == 0) out->status = *status;
+    }
+}
+
+void launch_diag_summary(const SpSet &set, int ntiles, const double *red, int nred, const ClampPtrs &cl,
+                         const int *status, DiagSummary *out, cudaStream_t st) {
+    k_diag_summary<<<set.n + 1, RB, 0, st>>>(set, ntiles, red, nred, cl, status, out);
+}
+
 void launch_energy(const GridDev &g, const float *E, const float *B, const SpSet &set, double *partials,
                    int nblocks, double *out, int *status, cudaStream_t st, int n_extra) {
     k_energy_fields<<<nblocks, RB, 0, st>>>(g, E, B, partials, nblocks, status);

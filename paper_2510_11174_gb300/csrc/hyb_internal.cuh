@@ -180,6 +180,21 @@ struct SpSet {
     SpDev s[HYB_MAX_SPECIES];
 };
 
+// what hyb_diagnostics reads back, gathered on the device so that one small
+// copy and one synchronisation serve the call
+struct DiagSummary {
+    double red[2 + HYB_MAX_SPECIES + 2 * HYB_MAX_FLUIDS];  // the energy reductions' results
+    long long count[HYB_MAX_SPECIES];                      // live particles per species
+    double tal_e[HYB_MAX_SPECIES][NTALLY];                 // event tallies summed over tiles
+    unsigned long long tal_n[HYB_MAX_SPECIES][NTALLY];
+    unsigned long long clamped[HYB_MAX_FLUIDS];            // fluid nodes clamped to n >= 0
+    int status;                                            // device status word
+};
+struct ClampPtrs {
+    const unsigned long long *p[HYB_MAX_FLUIDS];
+    int n;
+};
+
 // device status bits (latched; read by the synchronising calls)
 enum : int {
     ST_OVERFLOW = 1,   // tile or migration capacity exceeded
@@ -222,6 +237,8 @@ struct hyb_ctx {
     double *red_partials = nullptr;                  // FP64 block partials of reductions
     int red_blocks = 0;
     double *red_out = nullptr;                       // reduction results
+    hyb::DiagSummary *diag_dev = nullptr;            // device summary of hyb_diagnostics
+    hyb::DiagSummary *diag_host = nullptr;           // its pinned host copy
     int *status = nullptr;                           // device status word
     long long *step_dev = nullptr;                   // device step counter (read by graph replays)
     int *mig_counts = nullptr;                       // HYB_MAX_SPECIES migration counters
@@ -324,6 +341,8 @@ void launch_count_tiles(const GridDev &g, long long n, const float *x, const flo
 
 // FP64 reductions; results written to out[]: [0] = sum E^2 dV / 2, [1] = sum B^2 dV / 2,
 // [2 + s] = kinetic energy of species s; also sets ST_NAN on non-finite fields.
+void launch_diag_summary(const SpSet &set, int ntiles, const double *red, int nred, const ClampPtrs &cl,
+                         const int *status, DiagSummary *out, cudaStream_t st);
 void launch_energy(const GridDev &g, const float *E, const float *B, const SpSet &set,
                    double *partials, int nblocks, double *out, int *status, cudaStream_t st, int n_extra);
 
