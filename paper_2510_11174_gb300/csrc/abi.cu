@@ -208,7 +208,7 @@ hyb_status hyb_init_grid(const hyb_grid_desc *d, hyb_ctx **out) {
     c->mur_plane = std::max({(long long)n[1] * n[2], (long long)n[0] * n[2], (long long)n[0] * n[1]});
     const int G = T + 3;
     c->jframe = 3LL * G * G * G;
-    c->red_blocks = 152 * 2;
+    c->red_blocks = 152 * 8;   // enough warps for the loads of the reductions to cover the memory latency
     if (ctx_alloc(c, (void **)&c->E, fbytes) || ctx_alloc(c, (void **)&c->B, fbytes) ||
         ctx_alloc(c, (void **)&c->J, fbytes) ||
         ctx_alloc(c, (void **)&c->mur_old, sizeof(float) * 24 * (size_t)c->mur_plane) ||

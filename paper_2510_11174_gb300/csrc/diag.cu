@@ -29,18 +29,39 @@ __global__ void __launch_bounds__(RB) k_energy_fields(GridDev g, const float *__
                                                       const float *__restrict__ B, double *__restrict__ partials,
                                                       int nblocks, int *__restrict__ status) {
     __shared__ double sh[RB];
-    ff se = {0.0f, 0.0f}, sb = {0.0f, 0.0f};  // each square is exact, the sums double-float
+    // each square is exact, the sums double-float; four independent sums per
+    // thread keep four loads of each array in flight
+    ff se[4], sb[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) se[k] = sb[k] = ff{0.0f, 0.0f};
     bool finite = true;
-    const long long n3 = 3 * g.N;
-    for (long long c = blockIdx.x * (long long)RB + threadIdx.x; c < n3; c += (long long)nblocks * RB) {
+    const long long n3 = 3 * g.N, stride = (long long)nblocks * RB;
+    long long c = blockIdx.x * (long long)RB + threadIdx.x;
+    for (; c + 3 * stride < n3; c += 4 * stride) {
+        float e[4], b[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            e[k] = E[c + k * stride];
+            b[k] = B[c + k * stride];
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            finite = finite && isfinite(e[k]) && isfinite(b[k]);
+            se[k] = ff_add(se[k], ff_two_prod(e[k], e[k]));
+            sb[k] = ff_add(sb[k], ff_two_prod(b[k], b[k]));
+        }
+    }
+    for (; c < n3; c += stride) {
         const float e = E[c], b = B[c];
         finite = finite && isfinite(e) && isfinite(b);
-        se = ff_add(se, ff_two_prod(e, e));
-        sb = ff_add(sb, ff_two_prod(b, b));
+        se[0] = ff_add(se[0], ff_two_prod(e, e));
+        sb[0] = ff_add(sb[0], ff_two_prod(b, b));
     }
+    const ff se_t = ff_add(ff_add(se[0], se[1]), ff_add(se[2], se[3]));
+    const ff sb_t = ff_add(ff_add(sb[0], sb[1]), ff_add(sb[2], sb[3]));
     if (!finite) atomicOr(status, ST_NAN);
-    const double te = block_sum(ff_to_double(se), sh);
-    const double tb = block_sum(ff_to_double(sb), sh);
+    const double te = block_sum(ff_to_double(se_t), sh);
+    const double tb = block_sum(ff_to_double(sb_t), sh);
     if (threadIdx.x == 0) {
         partials[blockIdx.x] = te;
         partials[nblocks + blockIdx.x] = tb;
@@ -51,11 +72,16 @@ __global__ void __launch_bounds__(RB) k_energy_fields(GridDev g, const float *__
 __global__ void __launch_bounds__(RB) k_energy_species(GridDev g, SpDev sp, double *__restrict__ partials,
                                                        int nblocks) {
     __shared__ double sh[RB];
+    // warp w of block b takes the tiles b + (w + 8 k) nblocks, its lanes the
+    // tile's particles (a fixed assignment, so the sum order is fixed)
+    constexpr int NW = RB / 32;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     ff acc = {0.0f, 0.0f};
-    for (int t = blockIdx.x; t < g.ntiles; t += nblocks) {
+    for (int t = blockIdx.x + warp * nblocks; t < g.ntiles; t += nblocks * NW) {
         const int n = min(sp.count[t], sp.cap);
         const long long base = (long long)t * sp.cap;
-        for (int p = threadIdx.x; p < n; p += RB) {
+#pragma unroll 4
+        for (int p = lane; p < n; p += 32) {
             const ff u2 = ff_u2(sp.ux[base + p], sp.uy[base + p], sp.uz[base + p]);
             const ff term = sp.kind == 1 ? ff_norm(u2) : ff_gamma_minus_one(u2);
             acc = ff_add(acc, ff_mulf(term, sp.w[base + p]));
@@ -87,6 +113,7 @@ __global__ void __launch_bounds__(RB) k_diag_summary(SpSet set, int ntiles, cons
     if (b < set.n) {
         const SpDev &sp = set.s[b];
         double cnt = 0.0, te[NTALLY] = {0.0, 0.0, 0.0}, tn[NTALLY] = {0.0, 0.0, 0.0};  // exact below 2^53
+#pragma unroll 4
         for (int t = threadIdx.x; t < ntiles; t += RB) {
             cnt += (double)min(sp.count[t], sp.cap);
 #pragma unroll
