@@ -33,53 +33,59 @@ __device__ __forceinline__ int e_bmask(const GridDev &g, int comp, int i, int j,
     return m;
 }
 
+// grid (ceil(nx / blockDim.x), ny, nz): node (i, j, k) from the block and
+// thread indices, neighbours as offsets of the linear index (no divisions)
 __global__ void k_b_half(GridDev g, const float *__restrict__ E, float *__restrict__ B) {
-    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= g.N) return;
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
-    const int i = (int)(c % nx), j = (int)((c / nx) % ny), k = (int)(c / ((long long)nx * ny));
-    const int ip = i + 1 == nx ? 0 : i + 1, jp = j + 1 == ny ? 0 : j + 1, kp = k + 1 == nz ? 0 : k + 1;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
+    if (i >= nx) return;
+    const long long sy = nx, sz = (long long)nx * ny;
+    const long long c = k * sz + j * sy + i;
+    const long long oxp = i + 1 == nx ? 1 - nx : 1, oyp = j + 1 == ny ? (1 - ny) * sy : sy,
+                    ozp = k + 1 == nz ? (1 - nz) * sz : sz;
     const long long N = g.N;
     const float h = 0.5f * g.dt;
     const float idx = 1.0f / g.d[0], idy = 1.0f / g.d[1], idz = 1.0f / g.d[2];
     const float *Ex = E, *Ey = E + N, *Ez = E + 2 * N;
     const float ex = Ex[c], ey = Ey[c], ez = Ez[c];
     if (half_ok(g, 1, j) && half_ok(g, 2, k)) {
-        float cx = (Ez[cidx(g, i, jp, k)] - ez) * idy - (Ey[cidx(g, i, j, kp)] - ey) * idz;
+        float cx = (Ez[c + oyp] - ez) * idy - (Ey[c + ozp] - ey) * idz;
         B[c] -= h * cx;
     }
     if (half_ok(g, 0, i) && half_ok(g, 2, k)) {
-        float cy = (Ex[cidx(g, i, j, kp)] - ex) * idz - (Ez[cidx(g, ip, j, k)] - ez) * idx;
+        float cy = (Ex[c + ozp] - ex) * idz - (Ez[c + oxp] - ez) * idx;
         B[N + c] -= h * cy;
     }
     if (half_ok(g, 0, i) && half_ok(g, 1, j)) {
-        float cz = (Ey[cidx(g, ip, j, k)] - ey) * idx - (Ex[cidx(g, i, jp, k)] - ex) * idy;
+        float cz = (Ey[c + oxp] - ey) * idx - (Ex[c + oyp] - ex) * idy;
         B[2 * N + c] -= h * cz;
     }
 }
 
 __global__ void k_e_yee(GridDev g, float *__restrict__ E, const float *__restrict__ B,
                         const float *__restrict__ J) {
-    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= g.N) return;
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
-    const int i = (int)(c % nx), j = (int)((c / nx) % ny), k = (int)(c / ((long long)nx * ny));
-    const int im = i == 0 ? nx - 1 : i - 1, jm = j == 0 ? ny - 1 : j - 1, km = k == 0 ? nz - 1 : k - 1;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
+    if (i >= nx) return;
+    const long long sy = nx, sz = (long long)nx * ny;
+    const long long c = k * sz + j * sy + i;
+    const long long oxm = i == 0 ? nx - 1 : -1, oym = j == 0 ? (ny - 1) * sy : -sy,
+                    ozm = k == 0 ? (nz - 1) * sz : -sz;
     const long long N = g.N;
     const float dt = g.dt;
     const float idx = 1.0f / g.d[0], idy = 1.0f / g.d[1], idz = 1.0f / g.d[2];
     const float *Bx = B, *By = B + N, *Bz = B + 2 * N;
     const float bx = Bx[c], by = By[c], bz = Bz[c];
     if (half_ok(g, 0, i) && e_bmask(g, 0, i, j, k) == 0) {
-        float cx = (bz - Bz[cidx(g, i, jm, k)]) * idy - (by - By[cidx(g, i, j, km)]) * idz;
+        float cx = (bz - Bz[c + oym]) * idy - (by - By[c + ozm]) * idz;
         E[c] += dt * (cx - J[c]);
     }
     if (half_ok(g, 1, j) && e_bmask(g, 1, i, j, k) == 0) {
-        float cy = (bx - Bx[cidx(g, i, j, km)]) * idz - (bz - Bz[cidx(g, im, j, k)]) * idx;
+        float cy = (bx - Bx[c + ozm]) * idz - (bz - Bz[c + oxm]) * idx;
         E[N + c] += dt * (cy - J[N + c]);
     }
     if (half_ok(g, 2, k) && e_bmask(g, 2, i, j, k) == 0) {
-        float cz = (by - By[cidx(g, im, j, k)]) * idx - (bx - Bx[cidx(g, i, jm, k)]) * idy;
+        float cz = (by - By[c + oxm]) * idx - (bx - Bx[c + oym]) * idy;
         E[2 * N + c] += dt * (cz - J[2 * N + c]);
     }
 }
@@ -193,12 +199,19 @@ __global__ void k_laser_source(GridDev g, int x_src, int pol, double a0, double 
 
 static inline unsigned blocks_for(long long n, int b) { return (unsigned)((n + b - 1) / b); }
 
+// blocks of whole warps along x, one (y, z) row of nodes per block row
+static inline dim3 row_block(const GridDev &g) { return dim3(g.n[0] >= 256 ? 256 : 32 * ((g.n[0] + 31) / 32)); }
+static inline dim3 row_grid(const GridDev &g) {
+    const unsigned bx = row_block(g).x;
+    return dim3((unsigned)((g.n[0] + bx - 1) / bx), (unsigned)g.n[1], (unsigned)g.n[2]);
+}
+
 void launch_fdtd_b_half(const GridDev &g, const float *E, float *B, cudaStream_t st) {
-    k_b_half<<<blocks_for(g.N, 256), 256, 0, st>>>(g, E, B);
+    k_b_half<<<row_grid(g), row_block(g), 0, st>>>(g, E, B);
 }
 
 void launch_fdtd_e(const GridDev &g, float *E, const float *B, const float *J, cudaStream_t st) {
-    k_e_yee<<<blocks_for(g.N, 256), 256, 0, st>>>(g, E, B, J);
+    k_e_yee<<<row_grid(g), row_block(g), 0, st>>>(g, E, B, J);
 }
 
 void launch_mur(const GridDev &g, float *E, float *mur_old, long long plane, cudaStream_t st) {

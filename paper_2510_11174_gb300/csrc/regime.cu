@@ -114,19 +114,20 @@ __global__ void k_clamp_counts(int ntiles, SpDev sp) {
 }
 
 // max filter of radius r along axis a (Chebyshev dilation is three of these)
+// grid (ceil(nx / blockDim.x), ny, nz)
 __global__ void k_dilate(GridDev g, int a, int r, const uint8_t *__restrict__ in, uint8_t *__restrict__ out) {
-    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= g.N) return;
     const int nx = g.n[0], ny = g.n[1];
-    int idx[3] = {(int)(c % nx), (int)((c / nx) % ny), (int)(c / ((long long)nx * ny))};
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
+    if (i >= nx) return;
+    const long long c = ((long long)k * ny + j) * nx + i;
+    const int i0 = a == 0 ? i : (a == 1 ? j : k), n = g.n[a];
+    const long long st = a == 0 ? 1 : (a == 1 ? (long long)nx : (long long)nx * ny);
     uint8_t m = 0;
-    const int i0 = idx[a];
     for (int d = -r; d <= r && !m; ++d) {
         int q = i0 + d;
-        if (g.bc[a] == 0) q = ((q % g.n[a]) + g.n[a]) % g.n[a];
-        else if (q < 0 || q > g.n[a] - 1) continue;
-        idx[a] = q;
-        m = in[cidx(g, idx[0], idx[1], idx[2])];
+        if (g.bc[a] == 0) q = r < n ? (q < 0 ? q + n : (q >= n ? q - n : q)) : ((q % n) + n) % n;
+        else if (q < 0 || q > n - 1) continue;
+        m = in[c + (q - i0) * st];
     }
     out[c] = m;
 }
@@ -305,9 +306,11 @@ hyb_status regime_update(hyb_ctx *c, const float *pm, const float *ps) {
     }
     if (pm && !all && ++launches) k_decide<<<nblk(g.N), 256, 0, st>>>(g.N, pm, ps, (float)rd.k_sigma, physics ? 1 : 0, raw);
     // Chebyshev dilation: max filters along x, y, z (raw -> mask -> raw -> mask)
-    k_dilate<<<nblk(g.N), 256, 0, st>>>(g, 0, rd.dilate, raw, mask);
-    k_dilate<<<nblk(g.N), 256, 0, st>>>(g, 1, rd.dilate, mask, raw);
-    k_dilate<<<nblk(g.N), 256, 0, st>>>(g, 2, rd.dilate, raw, mask);
+    const dim3 db(g.n[0] >= 256 ? 256 : 32 * ((g.n[0] + 31) / 32));
+    const dim3 dg((unsigned)((g.n[0] + db.x - 1) / db.x), (unsigned)g.n[1], (unsigned)g.n[2]);
+    k_dilate<<<dg, db, 0, st>>>(g, 0, rd.dilate, raw, mask);
+    k_dilate<<<dg, db, 0, st>>>(g, 1, rd.dilate, mask, raw);
+    k_dilate<<<dg, db, 0, st>>>(g, 2, rd.dilate, raw, mask);
     launches += 3;
     // conversions
     for (size_t f = 0; f < c->fluids.size(); ++f) {
