@@ -108,10 +108,10 @@ __global__ void k_prep_patches_cl(const float *__restrict__ x, int B, long long 
 __global__ void k_prep_fields(GridDev g, const float *__restrict__ E, const float *__restrict__ Bf,
                               const float *__restrict__ mean, const float *__restrict__ sd,
                               __nv_bfloat16 *__restrict__ out) {
-    const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (c >= g.N) return;
     const int nx = g.n[0], ny = g.n[1];
-    const int i = (int)(c % nx), j = (int)((c / nx) % ny), k = (int)(c / ((long long)nx * ny));
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
+    if (i >= nx) return;
+    const long long c = ((long long)k * ny + j) * nx + i;
     auto fv = [&](const float *F, int a, int bb, int cc) -> float {
         int idx[3] = {a, bb, cc};
         for (int ax = 0; ax < 3; ++ax) {
@@ -311,7 +311,7 @@ hyb_status classifier_forward(hyb_ctx *c, const hyb_model *mc, float *p_mean_dev
     // the model runs on the context's stream for the classification
     cudaStream_t saved = m->stream;
     m->stream = c->stream;
-    k_prep_fields<<<nb(g.N), 256, 0, c->stream>>>(g, c->E, c->B, m->mean, m->std_, m->x0);
+    k_prep_fields<<<node_grid(g), node_block(g), 0, c->stream>>>(g, c->E, c->B, m->mean, m->std_, m->x0);
     const int K = m->d.mc_passes > 0 ? m->d.mc_passes : 1;
     const uint32_t thr = dropout_threshold(m->d.dropout);
     long long launches = 1;

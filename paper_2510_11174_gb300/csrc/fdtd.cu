@@ -199,19 +199,12 @@ __global__ void k_laser_source(GridDev g, int x_src, int pol, double a0, double 
 
 static inline unsigned blocks_for(long long n, int b) { return (unsigned)((n + b - 1) / b); }
 
-// blocks of whole warps along x, one (y, z) row of nodes per block row
-static inline dim3 row_block(const GridDev &g) { return dim3(g.n[0] >= 256 ? 256 : 32 * ((g.n[0] + 31) / 32)); }
-static inline dim3 row_grid(const GridDev &g) {
-    const unsigned bx = row_block(g).x;
-    return dim3((unsigned)((g.n[0] + bx - 1) / bx), (unsigned)g.n[1], (unsigned)g.n[2]);
-}
-
 void launch_fdtd_b_half(const GridDev &g, const float *E, float *B, cudaStream_t st) {
-    k_b_half<<<row_grid(g), row_block(g), 0, st>>>(g, E, B);
+    k_b_half<<<node_grid(g), node_block(g), 0, st>>>(g, E, B);
 }
 
 void launch_fdtd_e(const GridDev &g, float *E, const float *B, const float *J, cudaStream_t st) {
-    k_e_yee<<<row_grid(g), row_block(g), 0, st>>>(g, E, B, J);
+    k_e_yee<<<node_grid(g), node_block(g), 0, st>>>(g, E, B, J);
 }
 
 void launch_mur(const GridDev &g, float *E, float *mur_old, long long plane, cudaStream_t st) {

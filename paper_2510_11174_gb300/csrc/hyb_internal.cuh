@@ -180,6 +180,15 @@ struct SpSet {
     SpDev s[HYB_MAX_SPECIES];
 };
 
+// launch shape of the one-thread-per-node kernels: blocks of whole warps
+// along x, grid (x blocks, ny, nz), so that a kernel takes (i, j, k) from the
+// block and thread indices instead of dividing the linear index
+inline dim3 node_block(const GridDev &g) { return dim3(g.n[0] >= 256 ? 256 : 32 * ((g.n[0] + 31) / 32)); }
+inline dim3 node_grid(const GridDev &g) {
+    const unsigned bx = node_block(g).x;
+    return dim3((unsigned)((g.n[0] + bx - 1) / bx), (unsigned)g.n[1], (unsigned)g.n[2]);
+}
+
 // what hyb_diagnostics reads back, gathered on the device so that one small
 // copy and one synchronisation serve the call
 struct DiagSummary {

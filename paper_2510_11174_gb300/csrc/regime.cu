@@ -61,10 +61,10 @@ __global__ void k_density(GridDev g, SpDev sp, float scale, float *__restrict__ 
 __global__ void k_criterion(GridDev g, const float *__restrict__ E, const float *__restrict__ ne, FluidDev fe,
                             int has_fluid, float kappa, float a_thr, float n_thr, float c_thr, float chi_thr,
                             uint8_t *__restrict__ raw) {
-    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= g.N) return;
     const int nx = g.n[0], ny = g.n[1];
-    const int idx[3] = {(int)(c % nx), (int)((c / nx) % ny), (int)(c / ((long long)nx * ny))};
+    const int idx[3] = {(int)(blockIdx.x * blockDim.x + threadIdx.x), (int)blockIdx.y, (int)blockIdx.z};
+    if (idx[0] >= nx) return;
+    const long long c = ((long long)idx[2] * ny + idx[1]) * nx + idx[0];
     float e[3];
     const float emag = node_e(g, E, idx[0], idx[1], idx[2], e);
     float dens = ne[c] + (has_fluid ? fe.n[c] : 0.0f);
@@ -301,13 +301,12 @@ hyb_status regime_update(hyb_ctx *c, const float *pm, const float *ps) {
                                                    (9.1093837015e-31 * 299792458.0 * 299792458.0))
                                          : 0.0f;
         ++launches;
-        k_criterion<<<nblk(g.N), 256, 0, st>>>(g, c->E, c->ne, fd, fe >= 0, kappa, (float)rd.a_thr, (float)rd.n_thr,
+        k_criterion<<<node_grid(g), node_block(g), 0, st>>>(g, c->E, c->ne, fd, fe >= 0, kappa, (float)rd.a_thr, (float)rd.n_thr,
                                                (float)rd.c_thr, (float)rd.chi_thr, raw);
     }
     if (pm && !all && ++launches) k_decide<<<nblk(g.N), 256, 0, st>>>(g.N, pm, ps, (float)rd.k_sigma, physics ? 1 : 0, raw);
     // Chebyshev dilation: max filters along x, y, z (raw -> mask -> raw -> mask)
-    const dim3 db(g.n[0] >= 256 ? 256 : 32 * ((g.n[0] + 31) / 32));
-    const dim3 dg((unsigned)((g.n[0] + db.x - 1) / db.x), (unsigned)g.n[1], (unsigned)g.n[2]);
+    const dim3 db = node_block(g), dg = node_grid(g);
     k_dilate<<<dg, db, 0, st>>>(g, 0, rd.dilate, raw, mask);
     k_dilate<<<dg, db, 0, st>>>(g, 1, rd.dilate, mask, raw);
     k_dilate<<<dg, db, 0, st>>>(g, 2, rd.dilate, raw, mask);
