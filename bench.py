@@ -143,6 +143,10 @@ FLUID_FIELD_BYTES_PER_NODE = 24
 # the ncu capture on the 128 x 128 x 64 ramp + slab (67.2 + 20.2 MB for
 # 1,048,576 cells); scaled to a full launch by the cell count
 NCU_CONV_L1_BYTES_PER_CELL = 87.4e6 / 1048576
+# DRAM read + write per particle of one hybrid-step launch of the push, from
+# the ncu capture on the 128 x 128 x 64 ramp + slab (184.9 + 69.1 MB for its
+# 4.78 M particles); scaled to a full launch by the particle count
+NCU_PUSH_BYTES_PER_PARTICLE = 254.0e6 / 4784128
 
 
 def make_model(P, stream):
@@ -333,6 +337,9 @@ def run_ours(args, rank, world):
         r["frac"] = r["achieved"] / r["peak"]
         r["peak_kind"] = "measured" if peaks else "fallback"
         r["traffic"] = None
+    if "push" in roofs:
+        roofs["push"]["traffic"] = NCU_PUSH_BYTES_PER_PARTICLE * parts
+        roofs["push"]["traffic_note"] = "ncu dram bytes of a 128x128x64 hybrid-step launch scaled by particles"
     if "conv_l1" in roofs:
         roofs["conv_l1"]["traffic"] = NCU_CONV_L1_BYTES_PER_CELL * cells
         roofs["conv_l1"]["traffic_note"] = "ncu dram bytes of a 128x128x64 launch scaled by cells"
