@@ -72,19 +72,35 @@ __global__ void __launch_bounds__(RB) k_energy_fields(GridDev g, const float *__
 __global__ void __launch_bounds__(RB) k_energy_species(GridDev g, SpDev sp, double *__restrict__ partials,
                                                        int nblocks) {
     __shared__ double sh[RB];
-    // warp w of block b takes the tiles b + (w + 8 k) nblocks, its lanes the
-    // tile's particles (a fixed assignment, so the sum order is fixed)
-    constexpr int NW = RB / 32;
+    // work items are (chunk of LCH slots, tile), chunk-major: item i goes to
+    // warp i mod W (W = nblocks x 8 warps), its lanes take the chunk's
+    // particles -- a fixed assignment (fixed sum order) that spreads dense
+    // tiles over many warps; chunks past a tile's count end at once.  The
+    // item is stepped by W with a carry, not divided out.
+    constexpr int NW = RB / 32, LCH = 256;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nch = (sp.cap + LCH - 1) / LCH, nt = g.ntiles;
+    const int W = nblocks * NW, w = blockIdx.x * NW + warp;
+    const int dt = W % nt, dch = W / nt;
+    int t = w % nt, ch = w / nt;
     ff acc = {0.0f, 0.0f};
-    for (int t = blockIdx.x + warp * nblocks; t < g.ntiles; t += nblocks * NW) {
-        const int n = min(sp.count[t], sp.cap);
-        const long long base = (long long)t * sp.cap;
+    while (ch < nch) {
+        const int n = min(sp.count[t], sp.cap), p0 = ch * LCH;
+        if (p0 < n) {
+            const int p1 = min(n, p0 + LCH);
+            const long long base = (long long)t * sp.cap;
 #pragma unroll 4
-        for (int p = lane; p < n; p += 32) {
-            const ff u2 = ff_u2(sp.ux[base + p], sp.uy[base + p], sp.uz[base + p]);
-            const ff term = sp.kind == 1 ? ff_norm(u2) : ff_gamma_minus_one(u2);
-            acc = ff_add(acc, ff_mulf(term, sp.w[base + p]));
+            for (int p = p0 + lane; p < p1; p += 32) {
+                const ff u2 = ff_u2(sp.ux[base + p], sp.uy[base + p], sp.uz[base + p]);
+                const ff term = sp.kind == 1 ? ff_norm(u2) : ff_gamma_minus_one(u2);
+                acc = ff_add(acc, ff_mulf(term, sp.w[base + p]));
+            }
+        }
+        t += dt;
+        ch += dch;
+        if (t >= nt) {
+            t -= nt;
+            ++ch;
         }
     }
     const double tot = block_sum(ff_to_double(acc), sh);
