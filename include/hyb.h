@@ -218,8 +218,8 @@ typedef struct {
  * given, else the physics criterion.  UNION: a node is kinetic when the
  * classifier or the physics criterion says so (the thresholds act as prior
  * knowledge the network can only add to).  ALL_KINETIC: every node is
- * kinetic, i.e. all fluid becomes macro-particles (the full-PIC run that
- * judges the hybrid's error). */
+ * kinetic, i.e. all fluid becomes macro-particles (the full-PIC run, the
+ * reference for the hybrid's error). */
 #define HYB_REGIME_DEFAULT 0
 #define HYB_REGIME_UNION 1
 #define HYB_REGIME_ALL_KINETIC 2

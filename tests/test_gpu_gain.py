@@ -11,7 +11,7 @@ Training data: one hybrid run (physics criterion) of the 64 x 32 x 32 ramp +
 slab with a pulse of a0 = 2; the node fields and masks at every
 classification.  Evaluation on pulses the network has not seen (a0 = 1.5 and
 3): the hybrid with the learned mask alone against the hybrid with the
-physics criterion, both judged by the full-PIC run of the same state.  The
+physics criterion, both measured against the full-PIC run of the same state.  The
 learned mask keeps fewer cells kinetic and is closer to full PIC.
 """
 import numpy as np

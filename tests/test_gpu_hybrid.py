@@ -118,7 +118,7 @@ def _fields_after(P, inp, policy, seed, steps=40):
 
 
 def test_hybrid_field_error_against_full_pic():
-    """The full-PIC run (every node kinetic) judges the hybrid: same initial
+    """The full-PIC run (every node kinetic) is the reference for the hybrid: same initial
     state, same pulse, 40 steps.  Full PIC with Philox-random macro-particle
     positions carries shot noise: two full-PIC runs that differ only in the
     seed of those positions differ by the noise floor (~1e-2 relative L2 at 8
