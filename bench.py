@@ -50,9 +50,12 @@ def workloads():
         # plain full PIC: periodic 32^3, lambda/16, e-/p+ 0.1 n_c, 8 ppc, 1 keV, a0 = 1
         "periodic_plasma_32": ("pic", lambda seed: inputs.periodic_plasma(n=32, ppc=8, seed=seed)),
         # hybrid: 256 x 256 x 128, lambda/16, ramp 0.01 -> 1 n_c + 5 n_c slab, a0 log-uniform [10, 300]
-        "ramp_slab_256x256x128": ("hybrid", lambda seed: inputs.ramp_slab(seed=seed + 2)),
+        # tiles start at 16384 slots (four times a kinetic tile's 4096 particles), so the
+        # snowplow's compression does not make them grow during the run
+        "ramp_slab_256x256x128": ("hybrid", lambda seed: inputs.ramp_slab(seed=seed + 2, tile_capacity=16384)),
         # the same recipe at 1/8 of the cells (quick checks)
-        "ramp_slab_128x128x64": ("hybrid", lambda seed: inputs.ramp_slab(nx=128, ny=128, nz=64, seed=seed + 2)),
+        "ramp_slab_128x128x64": ("hybrid", lambda seed: inputs.ramp_slab(nx=128, ny=128, nz=64, seed=seed + 2,
+                                                                           tile_capacity=16384)),
         # laser-parameter scan: 32 independent hybrid runs of uneven grids 64..128 per axis
         "scan_32": ("scan", lambda seed: inputs.scan_runs(32, seed=seed + 4)),
     }
