@@ -30,8 +30,10 @@
 //               32 (w % 4) .. and channels 8 ((w - 2) / 4) ..): tcgen05.ld of
 //               the accumulator rows, the x-tap sum across lanes, bias, ReLU,
 //               Philox dropout with inverted scaling, channels-last stores.
-//               Many epilogue warps hide the latency of its dependent chains
-//               (the Philox rounds above all).
+//               What does not depend on the accumulator (the tile position,
+//               stepped with carries; the cell's validity; the dropout bits;
+//               the bias) is computed before waiting for it, so it overlaps
+//               the MMAs instead of lengthening the epilogue's chain.
 // The operand of tap (dz, dy) is the halo shifted by that tap: its 128 cells
 // are 128 consecutive 32-byte rows (one swizzle atom wide in K, 8-row groups
 // 256 bytes apart), so every tap and 16-channel block is a plain K-major SW32
