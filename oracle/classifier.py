@@ -126,3 +126,41 @@ def train_grads(net, x, y, pass_index, energy_weight, exact=False):
 
 def loss_only(net, x, y, pass_index, energy_weight):
     return train_grads(net, x, y, pass_index, energy_weight, exact=True)["loss"]
+
+
+def adam_update(w, g, m, v, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One Adam step (Kingma & Ba 2015) on FP64 tensors; returns (w', m', v').
+    t is the step count after this update (1 for the first step).  The paper
+    leaves the optimizer unstated; Adam with these defaults is the reading the
+    training step follows.
+      m' = beta1 m + (1 - beta1) g,   v' = beta2 v + (1 - beta2) g^2
+      w' = w - lr * (m' / (1 - beta1^t)) / (sqrt(v' / (1 - beta2^t)) + eps)"""
+    m = beta1 * m + (1.0 - beta1) * g
+    v = beta2 * v + (1.0 - beta2) * g * g
+    mhat = m / (1.0 - beta1 ** t)
+    vhat = v / (1.0 - beta2 ** t)
+    return w - lr * mhat / (torch.sqrt(vhat) + eps), m, v
+
+
+def train_run(weights, x, y, steps, dropout, seed, energy_weight, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8,
+              mean=None, std=None):
+    """`steps` training steps on one batch, as hyb_train_step takes them: the
+    forward/backward of train_grads with the dropout masks of pass = step
+    index (0, 1, ...), then Adam on FP64 master weights (the weights the
+    network uses are those masters rounded to BF16 inside train_grads).
+    Returns the final [(W, b)] as FP64 tensors and the per-step losses."""
+    net = OracleCNN(weights, dropout=dropout, seed=seed, mean=mean, std=std)
+    mw = [torch.zeros_like(w) for w in net.W]
+    vw = [torch.zeros_like(w) for w in net.W]
+    mb = [torch.zeros_like(b) for b in net.b]
+    vb = [torch.zeros_like(b) for b in net.b]
+    losses, grads = [], []
+    for t in range(steps):
+        out = train_grads(net, x, y, pass_index=t, energy_weight=energy_weight)
+        losses.append(out["loss"])
+        grads.append(out["grads"])
+        for l in range(4):
+            gw, gb = out["grads"][l]
+            net.W[l], mw[l], vw[l] = adam_update(net.W[l], gw, mw[l], vw[l], t + 1, lr, beta1, beta2, eps)
+            net.b[l], mb[l], vb[l] = adam_update(net.b[l], gb, mb[l], vb[l], t + 1, lr, beta1, beta2, eps)
+    return [(net.W[l], net.b[l]) for l in range(4)], losses, grads

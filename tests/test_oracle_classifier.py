@@ -84,3 +84,49 @@ def test_oracle_backward_matches_central_differences():
         lm = train_grads(net, x, y, 2, 0.1, exact=True)["loss"]
         net.b[l][0] = b0
         assert gb[0].item() == pytest.approx((lp - lm) / (2 * h), rel=1e-6, abs=1e-11), l
+
+
+def test_adam_first_step_is_lr_times_sign():
+    """First step: m_hat = g and v_hat = g^2 exactly, so w' = w - lr g / (|g| + eps)."""
+    from oracle.classifier import adam_update
+    rng = np.random.default_rng(8)
+    w = torch.from_numpy(rng.standard_normal(200))
+    g = torch.from_numpy(rng.standard_normal(200) * np.exp(rng.uniform(-20, 3, 200)))
+    z = torch.zeros_like(w)
+    w1, m1, v1 = adam_update(w, g, z, z, 1, lr=1e-3, eps=1e-8)
+    assert torch.allclose(w1, w - 1e-3 * g / (g.abs() + 1e-8), rtol=0, atol=1e-15)
+    assert torch.allclose(m1, 0.1 * g, rtol=1e-15, atol=0) and torch.allclose(v1, 1e-3 * g * g, rtol=1e-12, atol=0)
+
+
+def test_adam_constant_gradient_keeps_the_first_step():
+    """With a constant gradient the bias corrections are exact at every step:
+    m_t = (1 - beta1^t) g and v_t = (1 - beta2^t) g^2, so every update is the first one."""
+    from oracle.classifier import adam_update
+    g = torch.tensor([3e-2, -2.5, 7e-9, -1e-3], dtype=torch.float64)
+    w = torch.zeros(4, dtype=torch.float64)
+    m = torch.zeros(4, dtype=torch.float64)
+    v = torch.zeros(4, dtype=torch.float64)
+    step = -2e-3 * g / (g.abs() + 1e-8)
+    for t in range(1, 30):
+        w_new, m, v = adam_update(w, g, m, v, t, lr=2e-3, beta1=0.9, beta2=0.999, eps=1e-8)
+        assert torch.allclose(w_new - w, step, rtol=1e-12, atol=0), t
+        w = w_new
+
+
+def test_adam_matches_torch_optimizer():
+    """A sequence of random gradients against torch.optim.Adam in FP64 (an
+    independent implementation of the same update)."""
+    from oracle.classifier import adam_update
+    rng = np.random.default_rng(9)
+    w0 = rng.standard_normal(64)
+    p = torch.nn.Parameter(torch.from_numpy(w0.copy()))
+    opt = torch.optim.Adam([p], lr=3e-3, betas=(0.85, 0.995), eps=1e-7)
+    w = torch.from_numpy(w0.copy())
+    m = torch.zeros(64, dtype=torch.float64)
+    v = torch.zeros(64, dtype=torch.float64)
+    for t in range(1, 12):
+        g = torch.from_numpy(rng.standard_normal(64) * 10.0 ** rng.uniform(-4, 1))
+        p.grad = g.clone()
+        opt.step()
+        w, m, v = adam_update(w, g, m, v, t, lr=3e-3, beta1=0.85, beta2=0.995, eps=1e-7)
+        assert torch.allclose(w, p.detach(), rtol=0, atol=1e-13), t
