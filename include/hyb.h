@@ -361,6 +361,21 @@ hyb_status hyb_get_species(hyb_ctx *ctx, int species_id, long long max_n, float 
 /* Resets the latched device status word. */
 hyb_status hyb_clear_status(hyb_ctx *ctx);
 
+/* Failure detection (paper, Methodology: the stability of the run is checked,
+ * values are clamped and unstable steps are skipped).  The device latches
+ * overflow, non-finite fields and wait timeouts; these two calls let a caller
+ * exercise those paths without faulting the GPU.
+ * hyb_set_auto_grow(ctx, 0) turns off the growth of full particle tiles
+ * (on by default): a tile that overflows then drops the particles it cannot
+ * hold and latches HYB_EOVERFLOW.
+ * hyb_selftest_wait_timeout(ctx, polls) enqueues one kernel that waits, with
+ * the same bounded mbarrier wait as the tensor-core pipelines, on a barrier
+ * that nothing completes; after `polls` polls (1..2^20, HYB_EINVAL outside) it
+ * gives up and latches HYB_ETIMEOUT, which the next synchronising call
+ * returns.  The context stays usable; hyb_clear_status resets it. */
+hyb_status hyb_set_auto_grow(hyb_ctx *ctx, int on);
+hyb_status hyb_selftest_wait_timeout(hyb_ctx *ctx, long long polls);
+
 /* Per-phase timing of a step.  With profiling on, the captured step graph
  * records a CUDA event (on the context's stream) at every phase boundary;
  * hyb_phase_times synchronises and returns the device time of each phase of
@@ -418,7 +433,9 @@ hyb_status hyb_eval_qed(hyb_ctx *ctx, int what, const float *chi_host, const flo
  * 64 KiB that every GPU loading the library holds until exit, so n_cells is
  * limited to HYB_NOALLOC_MAX_CELLS (HYB_EINVAL beyond it).  The first call on a
  * device looks up that array's device address (make it before any stream
- * capture).  Every call overwrites the partial sums it reads, so nothing needs
+ * capture) and keeps it for the life of the process: after cudaDeviceReset, or
+ * anything else that destroys the device's primary context, that address is
+ * stale, so do not call this entry point again in that process.  Every call overwrites the partial sums it reads, so nothing needs
  * clearing, but all calls share the array: calls that overlap on the GPU (on
  * different streams, or from different threads) race and must be serialised
  * by the caller.  No cudaMalloc, cudaFree or allocating library routine is

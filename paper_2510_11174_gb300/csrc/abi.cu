@@ -985,6 +985,20 @@ hyb_status hyb_eval_qed(hyb_ctx *c, int what, const float *chi, const float *r, 
     return eval_qed(c, what, chi, r, n, out);
 }
 
+hyb_status hyb_set_auto_grow(hyb_ctx *c, int on) {
+    if (!c) return set_error(HYB_EINVAL, "null context");
+    c->auto_grow = on != 0;
+    return HYB_OK;
+}
+
+hyb_status hyb_selftest_wait_timeout(hyb_ctx *c, long long polls) {
+    if (!c) return set_error(HYB_EINVAL, "null context");
+    if (polls < 1 || polls > (1LL << 20)) return set_error(HYB_EINVAL, "polls must be in 1..2^20");
+    launch_wait_selftest(polls, c->status, c->stream);
+    HYB_CUDA_TRY(cudaGetLastError());
+    return HYB_OK;
+}
+
 hyb_status hyb_clear_status(hyb_ctx *c) {
     if (!c) return set_error(HYB_EINVAL, "null context");
     HYB_CUDA_TRY(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream));

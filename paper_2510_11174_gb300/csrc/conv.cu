@@ -778,4 +778,20 @@ hyb_status launch_conv_last_tc(const LastArgs &a, cudaStream_t st) {
     return HYB_OK;
 }
 
+// Self-test of the bounded barrier wait the convolutions use: one thread
+// waits on an mbarrier that nothing arrives at, gives up after `polls` polls
+// and latches ST_TIMEOUT -- the path a stalled tensor-core pipeline takes.
+__global__ void k_wait_selftest(long long polls, int *__restrict__ status) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(smem_u32(&bar), 1);
+        fence_mbar_init();
+        if (!mbar_wait(smem_u32(&bar), 0, polls)) atomicOr(status, ST_TIMEOUT);
+    }
+}
+
+void launch_wait_selftest(long long polls, int *status, cudaStream_t st) {
+    k_wait_selftest<<<1, 32, 0, st>>>(polls, status);
+}
+
 }  // namespace hyb

@@ -319,6 +319,7 @@ void launch_mur_save(const GridDev &g, const float *E, float *mur_old, long long
 void launch_laser_source(const GridDev &g, const hyb_grid_desc &d, const float *profile,
                          const long long *step_dev, float *J, cudaStream_t st);
 void launch_step_inc(long long *step_dev, cudaStream_t st);
+void launch_wait_selftest(long long polls, int *status, cudaStream_t st);
 
 size_t push_smem_bytes(int T);
 void launch_push_deposit(const GridDev &g, const float *E, const float *B, const SpDev *sps_dev, int nsp,

@@ -242,6 +242,14 @@ class Simulation:
     def clear_status(self):
         check(self._lib.hyb_clear_status(self._ctx))
 
+    def set_auto_grow(self, on=True):
+        """Turn the growth of full particle tiles on or off (hyb_set_auto_grow)."""
+        check(self._lib.hyb_set_auto_grow(self._ctx, int(bool(on))))
+
+    def selftest_wait_timeout(self, polls=4096):
+        """Run the bounded-wait self-test (hyb_selftest_wait_timeout): latches HYB_ETIMEOUT."""
+        check(self._lib.hyb_selftest_wait_timeout(self._ctx, int(polls)))
+
     # ------------------------------------------------------------------ read-back
     def diagnostics(self, raise_on_status=True):
         out = _abi.hyb_diag()
