@@ -132,6 +132,8 @@ def _declare(L):
     L.orc_particles_to_fluid.argtypes = [C.POINTER(Grid), _P, C.POINTER(Species), _P, _D3, C.c_double, _P]
     L.orc_particles_to_fluid.restype = C.c_long
     L.orc_dropout_mask.argtypes = [_P, C.c_int, C.c_int, C.c_long, C.c_uint32, C.c_uint32, C.c_uint32, C.c_double]
+    L.orc_dropout_mask_cells.argtypes = [_P, C.c_int, C.c_int, C.c_long, _P, C.c_uint32, C.c_uint32, C.c_uint32,
+                                         C.c_double]
     for name, fn in _EXTRA_DECLS:
         fn(L)
 
@@ -540,9 +542,17 @@ def particles_to_fluid(g, mask, sp, fl):
     return n
 
 
-def dropout_mask(B, C_, V, seed, pass_index, layer, p):
-    """uint8 keep mask [B][C][V] of the classifier's dropout."""
+def dropout_mask(B, C_, V, seed, pass_index, layer, p, cells=None):
+    """uint8 keep mask [B][C][V] of the classifier's dropout; `cells` (int64,
+    V values) names the cell whose stream each position takes (default:
+    position v is cell v)."""
     keep = np.zeros((B, C_, V), dtype=np.uint8)
-    lib().orc_dropout_mask(_ptr(keep), int(B), int(C_), int(V), int(seed) & 0xFFFFFFFF, int(pass_index),
-                           int(layer), float(p))
+    if cells is None:
+        lib().orc_dropout_mask(_ptr(keep), int(B), int(C_), int(V), int(seed) & 0xFFFFFFFF, int(pass_index),
+                               int(layer), float(p))
+    else:
+        cells = np.ascontiguousarray(cells, dtype=np.int64)
+        assert cells.size == V
+        lib().orc_dropout_mask_cells(_ptr(keep), int(B), int(C_), int(V), _ptr(cells), int(seed) & 0xFFFFFFFF,
+                                     int(pass_index), int(layer), float(p))
     return keep

@@ -43,8 +43,10 @@ class OracleCNN:
         xh = (x - self.mean.view(1, 6, 1, 1, 1)) / self.std.view(1, 6, 1, 1, 1)
         return bf16(xh)
 
-    def forward(self, x, pass_index=-1, return_acts=False):
-        """x: [B, 6, D, H, W] -> logits [B, D, H, W] (FP64)."""
+    def forward(self, x, pass_index=-1, return_acts=False, cells=None):
+        """x: [B, 6, D, H, W] -> logits [B, D, H, W] (FP64).  cells: optional
+        index of every position of the box in a larger volume, for the dropout
+        streams (a sub-box of a classified grid)."""
         a = self.normalise(x)
         acts = [a]
         B, _, D, H, W = a.shape
@@ -53,16 +55,16 @@ class OracleCNN:
             z = F.conv3d(a, bf16(self.W[l]), self.b[l], padding=1)
             h = torch.relu(z)
             if pass_index >= 0 and self.p > 0:
-                keep = dropout_mask(B, h.shape[1], V, self.seed, pass_index, l, self.p)
+                keep = dropout_mask(B, h.shape[1], V, self.seed, pass_index, l, self.p, cells=cells)
                 h = h * torch.from_numpy(keep.reshape(h.shape).astype(np.float64)) / (1.0 - self.p)
             a = bf16(h)
             acts.append(a)
         logit = F.conv3d(a, bf16(self.W[3]), self.b[3], padding=1)[:, 0]
         return (logit, acts) if return_acts else logit
 
-    def mc_statistics(self, x, passes):
+    def mc_statistics(self, x, passes, cells=None):
         """Mean and population standard deviation of sigmoid(logit) over the passes."""
-        ps = torch.stack([torch.sigmoid(self.forward(x, pass_index=k)) for k in range(passes)])
+        ps = torch.stack([torch.sigmoid(self.forward(x, pass_index=k, cells=cells)) for k in range(passes)])
         return ps.mean(0), ps.std(0, unbiased=False)
 
 

@@ -15,6 +15,25 @@
 
 #include <math.h>
 
+/* The same masks for cells named by their index in a larger volume: position
+ * v of the output takes the stream of cell cells[v] (a sub-box of a grid). */
+void orc_dropout_mask_cells(unsigned char *keep, int B, int C, long V, const long *cells, uint32_t seed,
+                            uint32_t pass, uint32_t layer, double p) {
+    const long thr = lround(p * 65536.0);
+    for (int b = 0; b < B; ++b)
+    for (int c0 = 0; c0 < C; c0 += 8)
+    for (long v = 0; v < V; ++v) {
+        const uint32_t ctr[4] = {(uint32_t)cells[v], (uint32_t)b, (layer << 16) | ((uint32_t)c0 / 8u), pass};
+        const uint32_t key[2] = {seed, 0xD0u};
+        uint32_t r[4];
+        orc_philox4x32_10(ctr, key, r);
+        for (int j = 0; j < 8 && c0 + j < C; ++j) {
+            const long field = (long)((r[j / 2] >> (16 * (j % 2))) & 0xFFFFu);
+            keep[((long)b * C + c0 + j) * V + v] = field >= thr;
+        }
+    }
+}
+
 void orc_dropout_mask(unsigned char *keep, int B, int C, long V, uint32_t seed, uint32_t pass, uint32_t layer,
                       double p) {
     const long thr = lround(p * 65536.0);

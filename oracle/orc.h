@@ -124,6 +124,8 @@ long orc_particles_to_fluid(const orc_grid *g, const unsigned char *mask, orc_sp
 /* ---- classifier dropout masks ----------------------------------------------- */
 void orc_dropout_mask(unsigned char *keep, int B, int C, long V, uint32_t seed, uint32_t pass, uint32_t layer,
                       double p);
+void orc_dropout_mask_cells(unsigned char *keep, int B, int C, long V, const long *cells, uint32_t seed,
+                            uint32_t pass, uint32_t layer, double p);
 
 /* ---- diagnostics --------------------------------------------------------- */
 void orc_energy_fields(const orc_grid *g, const double *E[3], const double *B[3], double out[2]);

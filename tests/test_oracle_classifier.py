@@ -130,3 +130,27 @@ def test_adam_matches_torch_optimizer():
         opt.step()
         w, m, v = adam_update(w, g, m, v, t, lr=3e-3, beta1=0.85, beta2=0.995, eps=1e-7)
         assert torch.allclose(w, p.detach(), rtol=0, atol=1e-13), t
+
+
+def test_dropout_streams_of_a_sub_box_are_those_of_the_whole_grid():
+    """A sub-box's masks taken by global cell index equal the whole grid's masks there."""
+    D, H, W = 6, 8, 10
+    full = oracle.dropout_mask(1, 16, D * H * W, 9, 2, 1, 0.2).reshape(16, D, H, W)
+    z, y, x = np.meshgrid(np.arange(1, 4), np.arange(2, 7), np.arange(5, 9), indexing="ij")
+    cells = ((z * H + y) * W + x).ravel()
+    sub = oracle.dropout_mask(1, 16, cells.size, 9, 2, 1, 0.2, cells=cells).reshape(16, 3, 5, 4)
+    assert np.array_equal(sub, full[:, 1:4, 2:7, 5:9])
+
+
+def test_sub_box_forward_equals_whole_grid_away_from_the_cut():
+    """Four 3x3x3 layers see 4 cells deep: a box with a 4-cell margin reproduces
+    the whole grid's logits in its interior (same dropout streams)."""
+    net = OracleCNN(_weights(6), dropout=0.2, seed=3)
+    x = np.random.default_rng(7).standard_normal((1, 6, 12, 16, 14)).astype(np.float32)
+    full = net.forward(x, pass_index=1)[0]
+    z0, y0, x0 = 2, 3, 1
+    box = x[:, :, z0:z0 + 10, y0:y0 + 12, x0:x0 + 11]
+    z, y, xx = np.meshgrid(np.arange(z0, z0 + 10), np.arange(y0, y0 + 12), np.arange(x0, x0 + 11), indexing="ij")
+    cells = ((z * 16 + y) * 14 + xx).ravel()
+    sub = net.forward(box, pass_index=1, cells=cells)[0]
+    assert torch.allclose(sub[4:6, 4:8, 4:7], full[z0 + 4:z0 + 6, y0 + 4:y0 + 8, x0 + 4:x0 + 7], rtol=0, atol=1e-12)
