@@ -11,9 +11,10 @@
 // memory, pushes every particle of every species in the tile, accumulates J in
 // a shared-memory frame of (T+3)^3 nodes (halo 1 below, 2 above, which holds
 // every node an Esirkepov stencil of a particle that started in the tile can
-// touch), and writes that frame to a per-tile scratch slab.  A second kernel
-// sums, for every node, the frames that cover it in a fixed order, so J is
-// assembled without global atomics and bit-reproducibly across tiles.
+// touch) in 64-bit fixed point (frames.cuh), and writes that frame to a
+// per-tile scratch slab.  A second kernel sums, for every node, the frames
+// that cover it in a fixed order, so J is assembled without global atomics and
+// repeats bit for bit whatever order the particles and warps take.
 // Particles that left their tile are copied to a migration buffer and
 // re-inserted by the rebin kernel; vacated slots are compacted afterwards.
 //
@@ -23,6 +24,7 @@
 // Esirkepov, CIC shape, on the 3-node window that holds both shapes:
 //   W_x = DS_x (S0_y S0_z + DS_y S0_z/2 + S0_y DS_z/2 + DS_y DS_z/3) (cyclic),
 //   J_x(i+1/2) - J_x(i-1/2) = -q w W_x / (dt dy dz).
+#include "frames.cuh"
 #include "hyb_internal.cuh"
 #include "ionize.cuh"
 #include "philox.cuh"
@@ -32,11 +34,11 @@
 namespace hyb {
 
 __host__ __device__ inline int frame_F(int T) { return T + 2; }  // field frame edge
-__host__ __device__ inline int frame_G(int T) { return T + 3; }  // current frame edge
 
+// the current frame (3 components, 64-bit fixed point) first, then the fields
 size_t push_smem_bytes(int T) {
     const int F = frame_F(T), G = frame_G(T);
-    return sizeof(float) * (6 * (size_t)F * F * F + 3 * (size_t)G * G * G);
+    return sizeof(unsigned long long) * 3 * (size_t)G * G * G + sizeof(float) * 6 * (size_t)F * F * F;
 }
 
 // CIC weights of one axis for integer and half-integer staggering, relative to
@@ -87,12 +89,14 @@ __global__ void __launch_bounds__(256, 3) k_push_deposit(GridDev g, const float 
                                                       float *__restrict__ jscratch, int *__restrict__ jvalid,
                                                       int *__restrict__ status,
                                                       const long long *__restrict__ step_dev, QedDev qd) {
-    extern __shared__ float sm[];
+    extern __shared__ __align__(16) unsigned char smraw[];
     const int T = g.T, F = frame_F(T), G = frame_G(T);
     const int F3 = F * F * F, G3 = G * G * G;
-    float *sf = sm;            // 6 field components, F^3 each
-    float *sj = sm + 6 * F3;   // 3 current components, G^3 each
+    unsigned long long *sj = reinterpret_cast<unsigned long long *>(smraw);  // 3 current components, G^3 each
+    float *sf = reinterpret_cast<float *>(sj + 3 * G3);                       // 6 field components, F^3 each
     __shared__ int s_holes;
+    __shared__ int s_qwmax[32];  // per warp: largest |q w| of the tile's particles (float bits)
+    __shared__ int s_kfix;       // fixed-point exponent of the tile's current frame
     __shared__ double s_tal_e[NTALLY];
     __shared__ unsigned long long s_tal_n[NTALLY];
     const long long step = *step_dev;
@@ -101,17 +105,29 @@ __global__ void __launch_bounds__(256, 3) k_push_deposit(GridDev g, const float 
 
     const int t = blockIdx.x;
     // a tile without particles writes no frame: the reduction skips it
-    {
-        int total = 0;
-        for (int si = 0; si < nsp; ++si) total += min(sps[si].count[t], sps[si].cap);
-        if (total == 0) {
-            if (threadIdx.x < nsp) {
-                sps[threadIdx.x].hole_count[t] = 0;
-                sps[threadIdx.x].hole_used[t] = 0;
-            }
-            if (threadIdx.x == 0) jvalid[t] = 0;
-            return;
+    int total = 0;
+    for (int si = 0; si < nsp; ++si) total += min(sps[si].count[t], sps[si].cap);
+    if (total == 0) {
+        if (threadIdx.x < nsp) {
+            sps[threadIdx.x].hole_count[t] = 0;
+            sps[threadIdx.x].hole_used[t] = 0;
         }
+        if (threadIdx.x == 0) jvalid[t] = 0;
+        return;
+    }
+    // the largest |q w| in the tile bounds every frame sum (fixed-point scale)
+    {
+        float qwm = 0.0f;
+        for (int si = 0; si < nsp; ++si) {
+            const SpDev &sp = sps[si];
+            const int n = min(sp.count[t], sp.cap);
+            const long long base = (long long)t * sp.cap;
+            for (int p = threadIdx.x; p < n; p += blockDim.x) {
+                const float qp = sp.zq ? sp.q * sp.zq[base + p] : sp.q;
+                qwm = fmaxf(qwm, fabsf(qp * sp.w[base + p]));
+            }
+        }
+        block_max_put(qwm, s_qwmax);
     }
     const int tx = t % g.nt[0], ty = (t / g.nt[0]) % g.nt[1], tz = t / (g.nt[0] * g.nt[1]);
     const int o[3] = {tx * T - 1, ty * T - 1, tz * T - 1};
@@ -136,7 +152,7 @@ __global__ void __launch_bounds__(256, 3) k_push_deposit(GridDev g, const float 
             sf[(3 + q) * F3 + l] = in ? B[q * N + c] : 0.0f;
         }
     }
-    for (int l = threadIdx.x; l < 3 * G3; l += blockDim.x) sj[l] = 0.0f;
+    for (int l = threadIdx.x; l < 3 * G3; l += blockDim.x) sj[l] = 0ULL;
     if (threadIdx.x == 0) {
         s_holes = 0;
         for (int k = 0; k < NTALLY; ++k) {
@@ -148,9 +164,16 @@ __global__ void __launch_bounds__(256, 3) k_push_deposit(GridDev g, const float 
 
     const float dt = g.dt;
     const float inv_d[3] = {1.0f / g.d[0], 1.0f / g.d[1], 1.0f / g.d[2]};
-    // current per unit q w of a face crossing: -1 / (dt dA_c)
-    const float jfac[3] = {-1.0f / (dt * g.d[1] * g.d[2]), -1.0f / (dt * g.d[0] * g.d[2]),
-                           -1.0f / (dt * g.d[0] * g.d[1])};
+    // current per unit q w of a face crossing: -1 / (dt dA_c), times the frame's
+    // fixed-point scale 2^k (every Esirkepov weight is at most 1 in magnitude,
+    // so a node's sum is at most total * max |q w| * max |jfac|)
+    const float j0 = -1.0f / (dt * g.d[1] * g.d[2]), j1 = -1.0f / (dt * g.d[0] * g.d[2]),
+                j2 = -1.0f / (dt * g.d[0] * g.d[1]);
+    const int kfix = fix_exponent((double)total * (double)block_max_read(s_qwmax) *
+                                  (double)fmaxf(fabsf(j0), fmaxf(fabsf(j1), fabsf(j2))));
+    const float fscale = pow2f(kfix);
+    const float jfac[3] = {j0 * fscale, j1 * fscale, j2 * fscale};
+    if (threadIdx.x == 0) s_kfix = kfix;  // read back after the species loop's barriers
     const float *sEx = sf, *sEy = sf + F3, *sEz = sf + 2 * F3;
     const float *sBx = sf + 3 * F3, *sBy = sf + 4 * F3, *sBz = sf + 5 * F3;
 
@@ -269,7 +292,7 @@ __global__ void __launch_bounds__(256, 3) k_push_deposit(GridDev g, const float 
                     for (int c = 0; c < 3; ++c) {
                         const int pa = (c + 1) % 3, qa = (c + 2) % 3;
                         const float fac = qw * jfac[c];
-                        float *Jc = sj + c * G3;
+                        unsigned long long *Jc = sj + c * G3;
 #pragma unroll
                         for (int bq = 0; bq < 2; ++bq)
 #pragma unroll
@@ -281,13 +304,13 @@ __global__ void __launch_bounds__(256, 3) k_push_deposit(GridDev g, const float 
                                     l3[c] = lb[c];
                                     l3[pa] = lb[pa] + bp;
                                     l3[qa] = lb[qa] + bq;
-                                    atomicAdd(&Jc[(l3[2] * G + l3[1]) * G + l3[0]], fac * acc);
+                                    atomicAdd(&Jc[(l3[2] * G + l3[1]) * G + l3[0]], fix_of(fac * acc));
                                 }
                             }
                     }
                 } else if (q != 0.0f) {
                     int lb[3];
-                    float S0[3][3], DS[3][3], CA[3][3], CB[3][3];
+                    float S0[3][3], DS[3][3];
 #pragma unroll
                     for (int a = 0; a < 3; ++a) {
                         const int i0 = (int)floorf(x0[a]), i1 = (int)floorf(x1[a]);
@@ -297,23 +320,22 @@ __global__ void __launch_bounds__(256, 3) k_push_deposit(GridDev g, const float 
                         shape3(x0[a], gb, S0[a]);
                         shape3(x1[a], gb, S1);
 #pragma unroll
-                        for (int k = 0; k < 3; ++k) {
-                            DS[a][k] = S1[k] - S0[a][k];
-                            CA[a][k] = S0[a][k] + 0.5f * DS[a][k];
-                            CB[a][k] = 0.5f * S0[a][k] + DS[a][k] * (1.0f / 3.0f);
-                        }
+                        for (int k = 0; k < 3; ++k) DS[a][k] = S1[k] - S0[a][k];
                     }
                     const float qw = q * wgt;
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
                         const int pa = (c + 1) % 3, qa = (c + 2) % 3;
                         const float fac = qw * jfac[c];
-                        float *Jc = sj + c * G3;
+                        unsigned long long *Jc = sj + c * G3;
 #pragma unroll
-                        for (int bq = 0; bq < 3; ++bq)
+                        for (int bq = 0; bq < 3; ++bq) {
+                            // transverse factor S0p (S0q + DSq/2) + DSp (S0q/2 + DSq/3)
+                            const float caq = fmaf(0.5f, DS[qa][bq], S0[qa][bq]);
+                            const float cbq = fmaf(1.0f / 3.0f, DS[qa][bq], 0.5f * S0[qa][bq]);
 #pragma unroll
                             for (int bp = 0; bp < 3; ++bp) {
-                                const float cross = fmaf(DS[pa][bp], CB[qa][bq], S0[pa][bp] * CA[qa][bq]);
+                                const float cross = fmaf(DS[pa][bp], cbq, S0[pa][bp] * caq);
                                 float acc = 0.0f;
 #pragma unroll
                                 for (int a = 0; a < 2; ++a) {
@@ -323,10 +345,11 @@ __global__ void __launch_bounds__(256, 3) k_push_deposit(GridDev g, const float 
                                         l3[c] = lb[c] + a;
                                         l3[pa] = lb[pa] + bp;
                                         l3[qa] = lb[qa] + bq;
-                                        atomicAdd(&Jc[(l3[2] * G + l3[1]) * G + l3[0]], fac * acc);
+                                        atomicAdd(&Jc[(l3[2] * G + l3[1]) * G + l3[0]], fix_of(fac * acc));
                                     }
                                 }
                             }
+                        }
                     }
                 }
 
@@ -486,33 +509,12 @@ __global__ void __launch_bounds__(256, 3) k_push_deposit(GridDev g, const float 
     }
 
     float *dst = jscratch + (long long)t * 3 * G3;
-    for (int l = threadIdx.x; l < 3 * G3; l += blockDim.x) dst[l] = sj[l];
+    const float inv_scale = pow2f(-s_kfix);
+    for (int l = threadIdx.x; l < 3 * G3; l += blockDim.x) dst[l] = fix_to_float(sj[l], inv_scale);
     if (threadIdx.x == 0) jvalid[t] = 1;
 }
 
 // For every node: J = sum of the tile frames that cover it, in a fixed order.
-// Frame of tile tt along an axis covers global nodes tt*T-1 .. tt*T+T+1; the
-// node i with own tile tt sits at local i - tt*T + 1 in [1, T]; the previous
-// tile covers it at local + T when local <= 2, the next at local - T when
-// local == T.
-__device__ __forceinline__ int axis_cands(const GridDev &g, int a, int i, int tile[2], int loc[2]) {
-    const int T = g.T, nt = g.nt[a];
-    const int own = i >> g.tshift, l = i - own * T + 1;
-    int n = 0;
-    if (l <= 2) {
-        int pt = own - 1;
-        if (pt < 0 && g.bc[a] == 0) pt += nt;
-        if (pt >= 0) { tile[n] = pt; loc[n] = l + T; ++n; }
-    }
-    tile[n] = own; loc[n] = l; ++n;
-    if (l == T) {
-        int nt2 = own + 1;
-        if (nt2 >= nt && g.bc[a] == 0) nt2 -= nt;
-        if (nt2 < nt) { tile[n] = nt2; loc[n] = 0; ++n; }
-    }
-    return n;
-}
-
 __global__ void k_j_reduce(GridDev g, const float *__restrict__ jscratch, const int *__restrict__ jvalid,
                            float *__restrict__ J) {
     // grid (ceil(nx / blockDim.x), ny, nz)
@@ -520,22 +522,8 @@ __global__ void k_j_reduce(GridDev g, const float *__restrict__ jscratch, const 
     const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
     if (i >= nx) return;
     const long long c = ((long long)k * ny + j) * nx + i;
-    const int G = frame_G(g.T), G3 = G * G * G;
-    int tx[2], lx[2], ty[2], ly[2], tz[2], lz[2];
-    const int nxc = axis_cands(g, 0, i, tx, lx);
-    const int nyc = axis_cands(g, 1, j, ty, ly);
-    const int nzc = axis_cands(g, 2, k, tz, lz);
-    float acc[3] = {0.0f, 0.0f, 0.0f};
-    for (int cz = 0; cz < nzc; ++cz)
-        for (int cy = 0; cy < nyc; ++cy)
-            for (int cx = 0; cx < nxc; ++cx) {
-                const long long t = tx[cx] + (long long)g.nt[0] * (ty[cy] + (long long)g.nt[1] * tz[cz]);
-                if (!jvalid[t]) continue;
-                const float *fr = jscratch + t * 3 * G3 + (lz[cz] * G + ly[cy]) * G + lx[cx];
-                acc[0] += fr[0];
-                acc[1] += fr[G3];
-                acc[2] += fr[2 * G3];
-            }
+    float acc[3];
+    frame_gather<3>(g, jscratch, jvalid, 3, i, j, k, acc);
     J[c] = acc[0];
     J[g.N + c] = acc[1];
     J[2 * g.N + c] = acc[2];
@@ -654,6 +642,11 @@ void launch_push_deposit(const GridDev &g, const float *E, const float *B, const
                          const QedDev &qd, float *jscratch, int *jvalid, int *status, const long long *step_dev,
                          cudaStream_t st) {
     const size_t smem = push_smem_bytes(g.T);
+    static size_t smem_set = 0;  // the opt-in size set so far (the largest tile's)
+    if (smem > smem_set && smem > 48 * 1024) {
+        cudaFuncSetAttribute(k_push_deposit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        smem_set = smem;
+    }
     k_push_deposit<<<g.ntiles, 256, smem, st>>>(g, E, B, sps_dev, nsp, jscratch, jvalid, status, step_dev, qd);
 }
 

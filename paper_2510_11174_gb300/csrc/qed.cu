@@ -182,7 +182,7 @@ __global__ void k_em_cdf(AiryTab T, float *cdf, double aip0) {
     const double l0 = log(QED_EM_CHI0), l1 = log(QED_EM_CHI1);
     const double chi = exp(l0 + (l1 - l0) * i / (QED_NROW - 1));
     const double dm = (QED_MU1 - QED_MU0) / (QED_NCOL - 1);
-    const int sub = 8;
+    const int sub = 4;  // Simpson panels per column (step dm / 4)
     const double h = dm / sub;
     // pass 0: the row total; pass 1: the normalised running integral
     double total = 0.0;
@@ -224,7 +224,7 @@ __global__ void k_pair_cdf(AiryTab T, float *cdf) {
     const double l0 = log(QED_PAIR_CHI0), l1 = log(QED_PAIR_CHI1);
     const double chi = exp(l0 + (l1 - l0) * i / (QED_NROW - 1));
     const double dx = 1.0 / (QED_NCOL - 1);
-    const int sub = 8;
+    const int sub = 4;  // Simpson panels per column (step dx / 4)
     const double h = dx / sub;
     double total = 0.0;
     for (int pass = 0; pass < 2; ++pass) {
@@ -282,9 +282,9 @@ hyb_status setup_qed(hyb_ctx *c) {
     AiryTab T{c->airy_ai, c->airy_aip, c->airy_aint};
     const double aip0 = -1.0 / (std::pow(3.0, 1.0 / 3.0) * std::tgamma(1.0 / 3.0));
     k_em_rates<<<(QED_EM_NH + 127) / 128, 128, 0, st>>>(T, em_lnh, aip0);
-    k_em_cdf<<<1, QED_NROW, 0, st>>>(T, em_cdf, aip0);
+    k_em_cdf<<<(QED_NROW + 31) / 32, 32, 0, st>>>(T, em_cdf, aip0);
     k_pair_rates<<<(QED_PAIR_NH + 127) / 128, 128, 0, st>>>(T, pair_lnT);
-    k_pair_cdf<<<1, QED_NROW, 0, st>>>(T, pair_cdf);
+    k_pair_cdf<<<(QED_NROW + 31) / 32, 32, 0, st>>>(T, pair_cdf);
     cudaError_t e = cudaStreamSynchronize(st);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return set_error(HYB_ECUDA, std::string("QED tables: ") + cudaGetErrorString(e));

@@ -18,8 +18,11 @@ static constexpr int QED_EM_E0 = -20, QED_EM_E1 = 10, QED_EM_NPO = 256;
 static constexpr int QED_EM_NH = (QED_EM_E1 - QED_EM_E0) * QED_EM_NPO + 1;
 static constexpr int QED_PAIR_E0 = -7, QED_PAIR_E1 = 10, QED_PAIR_NPO = 1024;
 static constexpr int QED_PAIR_NH = (QED_PAIR_E1 - QED_PAIR_E0) * QED_PAIR_NPO + 1;
-static constexpr int QED_NROW = 128;   // spectrum table rows (ln chi)
-static constexpr int QED_NCOL = 1024;  // spectrum table columns
+// Spectrum tables: rows uniform in ln chi, blended linearly between rows; the
+// blend's error, about (d ln chi)^2 / 8 times the curvature of the cumulative
+// spectrum in ln chi, sets the sampler's accuracy (d ln chi = 0.02 here)
+static constexpr int QED_NROW = 1024;  // spectrum table rows (ln chi)
+static constexpr int QED_NCOL = 2048;  // spectrum table columns
 static constexpr double QED_EM_CHI0 = 1e-6, QED_EM_CHI1 = 1e3;
 static constexpr double QED_PAIR_CHI0 = 1e-2, QED_PAIR_CHI1 = 1e3;
 static constexpr double QED_MU0 = -30.0, QED_MU1 = 5.0;

@@ -190,3 +190,41 @@ def scan_runs(n_runs=64, sizes=(64, 80, 96, 112), a0_range=(1.0, 300.0), density
         runs.append(ramp_slab(nx=nx, ny=ny, nz=nz, n_lo=0.01 * d, n_hi=d, n_slab=5.0 * d, a0=a0, seed=seed + r,
                               ppc=ppc, tile_capacity=3 * 512 * ppc, vacuum_lambda=1.0, slab_lambda=1.0))
     return runs
+
+
+CLASSIFIER_LAYERS = [(6, 32), (32, 32), (32, 16), (16, 1)]
+
+
+def classifier_weights(seed, out_bias=0.0, bias_scale=0.05):
+    """Seeded FP32 weights of the regime classifier, [(W [co][ci][3][3][3], b [co])]:
+    He-uniform W, U(-sqrt(6 / fan_in), sqrt(6 / fan_in)) with fan_in = 27 ci, small
+    random hidden biases and a fixed output bias.  Both the GPU model (through
+    hyb_model_set_layer) and the oracle take these."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for l, (ci, co) in enumerate(CLASSIFIER_LAYERS):
+        lim = math.sqrt(6.0 / (27 * ci))
+        w = rng.uniform(-lim, lim, (co, ci, 3, 3, 3)).astype(np.float32)
+        b = (bias_scale * rng.standard_normal(co)).astype(np.float32) if l < 3 else np.full(co, out_bias, np.float32)
+        out.append((w, b))
+    return out
+
+
+def field_packet(nx, ny, nz, dx, a0=10.0, x_c=None, w0=None, length=None, noise=0.05, seed=0):
+    """Seeded synthetic E, B (3 x nz x ny x nx FP32 each): a linearly polarised
+    wave packet along x (E_y, B_z) with a Gaussian envelope in x and in the
+    transverse radius, on top of Gaussian noise of amplitude `noise` * a0 in
+    every component."""
+    rng = np.random.default_rng(seed)
+    x = (np.arange(nx) * dx)[None, None, :]
+    y = ((np.arange(ny) - ny / 2) * dx)[None, :, None]
+    z = ((np.arange(nz) - nz / 2) * dx)[:, None, None]
+    x_c = nx * dx / 2 if x_c is None else x_c
+    w0 = ny * dx / 5 if w0 is None else w0
+    length = nx * dx / 8 if length is None else length
+    env = a0 * np.exp(-((x - x_c) / length) ** 2 - (y ** 2 + z ** 2) / w0 ** 2)
+    E = (noise * a0 * rng.standard_normal((3, nz, ny, nx))).astype(np.float32)
+    B = (noise * a0 * rng.standard_normal((3, nz, ny, nx))).astype(np.float32)
+    E[1] += (env * np.cos(x)).astype(np.float32)
+    B[2] += (env * np.cos(x)).astype(np.float32)
+    return E, B

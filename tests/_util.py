@@ -46,3 +46,16 @@ def make_pair(inp, laser=None, tile=8, with_oracle=True):
 def by_id(d):
     order = np.argsort(d["ids"], kind="stable")
     return {k: v[order] for k, v in d.items()}
+
+
+def seeded_classifier(P, seed, out_bias=0.0, **kw):
+    """A GPU Classifier holding seeded weights (inputs.classifier_weights) and
+    those weights, so that the oracle takes the same inputs and none of its
+    inputs comes from the CUDA path."""
+    from paper_2510_11174_gb300 import inputs
+    from paper_2510_11174_gb300.model import Classifier
+    weights = inputs.classifier_weights(seed, out_bias=out_bias)
+    m = Classifier(seed=seed, **kw)
+    for l, (w, b) in enumerate(weights):
+        m.set_layer(l, w, b)
+    return m, weights

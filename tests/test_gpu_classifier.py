@@ -13,13 +13,11 @@ pytestmark = pytest.mark.gpu
 
 
 def _model(P, dropout=0.2, seed=7, mean=None, std=None):
-    from paper_2510_11174_gb300.model import Classifier
-    return Classifier(dropout=dropout, mc_passes=4, seed=seed, mean=mean, std=std)
-
-
-def _oracle_from(model, dropout, seed, mean=None, std=None):
+    """A GPU classifier with seeded weights and the oracle network of the same weights."""
     from oracle.classifier import OracleCNN
-    return OracleCNN([model.get_layer(l) for l in range(4)], dropout=dropout, seed=seed, mean=mean, std=std)
+    from _util import seeded_classifier
+    m, weights = seeded_classifier(P, seed, dropout=dropout, mc_passes=4, mean=mean, std=std)
+    return m, OracleCNN(weights, dropout=dropout, seed=seed, mean=mean, std=std)
 
 
 @pytest.mark.parametrize("shape", [(2, 16, 16, 16), (1, 3, 32, 24), (1, 1, 16, 8)])
@@ -30,10 +28,10 @@ def test_forward_matches_oracle(shape, pass_index):
     B, D, H, W = shape
     mean = [0.1, -0.2, 0.0, 0.05, 0.0, -0.1]
     std = [0.5, 1.0, 2.0, 0.7, 1.5, 0.9]
-    m = _model(P, mean=mean, std=std)
+    m, net = _model(P, mean=mean, std=std)
     x = np.random.default_rng(3).standard_normal((B, 6, D, H, W)).astype(np.float32)
     y = m.forward(torch.from_numpy(x).cuda(), pass_index).cpu().numpy()
-    ref = _oracle_from(m, 0.2, 7, mean, std).forward(x, pass_index).numpy()
+    ref = net.forward(x, pass_index).numpy()
     assert rel_l2(y, ref) <= 1e-3, rel_l2(y, ref)
 
 
@@ -42,7 +40,7 @@ def test_center_tap_network_is_a_gemm_chain():
     compare against torch.matmul in FP32 on the same BF16-rounded operands."""
     P = require_gpu()
     import torch
-    m = _model(P, dropout=0.0)
+    m, _ = _model(P, dropout=0.0)
     rng = np.random.default_rng(5)
     mats = []
     for l, (ci, co) in enumerate([(6, 32), (32, 32), (32, 16), (16, 1)]):
@@ -71,7 +69,7 @@ def test_classify_context_fields_with_mc_dropout():
     E = (0.5 * rng.standard_normal((3, nz, ny, nx))).astype(np.float32)
     B = (0.5 * rng.standard_normal((3, nz, ny, nx))).astype(np.float32)
     sim, _ = make_pair(dict(grid=dict(nx=nx, ny=ny, nz=nz, dx=0.3), E=E, B=B), with_oracle=False)
-    m = _model(P, dropout=0.2, seed=13)
+    m, net = _model(P, dropout=0.2, seed=13)
     pm = torch.empty(nz * ny * nx, device="cuda")
     ps = torch.empty(nz * ny * nx, device="cuda")
     sim.classify(m, pm, ps)
@@ -81,6 +79,6 @@ def test_classify_context_fields_with_mc_dropout():
                   0.25 * (B[0] + r(B[0], 1, 1) + r(B[0], 1, 0) + r(r(B[0], 1, 1), 1, 0)),
                   0.25 * (B[1] + r(B[1], 1, 2) + r(B[1], 1, 0) + r(r(B[1], 1, 2), 1, 0)),
                   0.25 * (B[2] + r(B[2], 1, 2) + r(B[2], 1, 1) + r(r(B[2], 1, 2), 1, 1))])[None].astype(np.float32)
-    om, os_ = _oracle_from(m, 0.2, 13).mc_statistics(f, 4)
+    om, os_ = net.mc_statistics(f, 4)
     assert rel_l2(pm.cpu().numpy(), om.numpy().ravel()) <= 1e-3
     assert np.max(np.abs(ps.cpu().numpy() - os_.numpy().ravel())) <= 2e-3

@@ -193,21 +193,22 @@ def test_training_batch_32_of_32_cubed_patches():
     P = require_gpu()
     import torch
     from oracle.classifier import OracleCNN, train_grads
-    from paper_2510_11174_gb300.model import Classifier
     rng = np.random.default_rng(11)
     x = rng.standard_normal((32, 6, 32, 32, 32)).astype(np.float32)
     y = (x[:, 0] + 0.5 * x[:, 1] > 0.2).astype(np.float32)
-    m = Classifier(dropout=0.2, mc_passes=1, seed=4, energy_weight=0.1)
-    st = m.train_step(torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda())
-    assert math.isfinite(st["loss"]) and st["step"] == 1
-    # gradients of the next step on two of the patches, against the oracle
-    net = OracleCNN([m.get_layer(l) for l in range(4)], dropout=0.2, seed=4)
+    from _util import seeded_classifier
+    m, weights = seeded_classifier(None, 4, dropout=0.2, mc_passes=1, energy_weight=0.1)
+    net = OracleCNN(weights, dropout=0.2, seed=4)
+    # gradients of the first step on two of the patches, against the oracle
     x2, y2 = x[:2], y[:2]
     st2 = m.train_step(torch.from_numpy(x2).cuda(), torch.from_numpy(y2).cuda())
-    ref = train_grads(net, x2, y2, pass_index=1, energy_weight=0.1)
+    ref = train_grads(net, x2, y2, pass_index=0, energy_weight=0.1)
     assert st2["loss"] == pytest.approx(ref["loss"], rel=1e-3)
     for l in range(4):
         gw, gb = m.get_grad(l)
         rw, rb = ref["grads"][l]
         assert rel_l2(gw, rw.numpy()) <= 1e-2, (l, rel_l2(gw, rw.numpy()))
         assert rel_l2(gb, rb.numpy()) <= 1e-2, (l, rel_l2(gb, rb.numpy()))
+    # then a step of the whole batch of 32
+    st = m.train_step(torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda())
+    assert math.isfinite(st["loss"]) and st["step"] == 2

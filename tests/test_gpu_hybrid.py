@@ -39,10 +39,9 @@ def test_hybrid_step_matches_oracle():
     from paper_2510_11174_gb300.model import Classifier
     inp = _workload(ppc=2)
     g = inp["grid"]
-    model = Classifier(dropout=0.2, mc_passes=4, seed=9)
-    w, b = model.get_layer(3)
-    model.set_layer(3, w, np.full_like(b, -2.0))
-    net = OracleCNN([model.get_layer(l) for l in range(4)], dropout=0.2, seed=9)
+    from _util import seeded_classifier
+    model, weights = seeded_classifier(P, 9, out_bias=-2.0, dropout=0.2, mc_passes=4)
+    net = OracleCNN(weights, dropout=0.2, seed=9)
     sim = _gpu(P, inp, "union")
     orc = S.OracleSim(g["nx"], g["ny"], g["nz"], g["dx"], cfl_frac=g["cfl_frac"], bc=g["bc"], laser=inp["laser"])
     for sp in inp["species"]:
