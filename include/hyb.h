@@ -358,6 +358,34 @@ hyb_status hyb_get_species(hyb_ctx *ctx, int species_id, long long max_n, float 
                            float *z, float *ux, float *uy, float *uz, float *w, float *zq,
                            uint64_t *ids, long long *n_out);
 
+/* Checkpoint (paper, Methodology: runs are kept reproducible through stored
+ * parameters, data and fixed random streams).
+ * hyb_get_state writes the whole state of the context -- the fields E, B, J,
+ * the Mur history planes, the regime mask, the previous mask and the residual
+ * background charge, every species' particles (positions, momenta, weights,
+ * charge states, optical depths, ids), per-tile event tallies and tile
+ * capacity, every fluid with its clamp count, the step and conversion
+ * counters, the regime settings and the device status word -- into the host
+ * buffer buf_host of `cap` bytes, and its size into *size_out.  With buf_host
+ * NULL only the size is reported; a `cap` below the size gives HYB_EINVAL
+ * (with the size reported).  The image holds no pointers and no classifier
+ * (hyb_model_get_layer saves a network).  Synchronises.
+ * hyb_set_state restores such an image into a context created with the same
+ * grid descriptor (grid, cell size, time step, boundaries, seed, tile) and
+ * loaded with the same species (charge, mass, kind, ionization and QED
+ * flags) and fluids, in the same order; anything else returns HYB_EINVAL
+ * before the context is changed.  Particles are binned into their tiles again
+ * (their slot order inside a tile may differ; nothing the step computes
+ * depends on it), tile capacities become the saved ones and the step graph is
+ * captured again at the next hyb_step.  Random events draw from streams keyed
+ * by particle id and step, and the current deposition does not depend on the
+ * particle order, so N steps, a save, a restore into a fresh context and M
+ * more steps give the fields and particles of N + M uninterrupted steps bit
+ * for bit.  Temporary device memory for the particles comes from the arena
+ * when the context has one.  Synchronises. */
+hyb_status hyb_get_state(hyb_ctx *ctx, void *buf_host, size_t cap, size_t *size_out);
+hyb_status hyb_set_state(hyb_ctx *ctx, const void *buf_host, size_t size);
+
 /* Resets the latched device status word. */
 hyb_status hyb_clear_status(hyb_ctx *ctx);
 

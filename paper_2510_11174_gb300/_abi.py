@@ -112,6 +112,8 @@ PROTOTYPES = {
     "hyb_get_species": (C.c_int, [_ctx, C.c_int, C.c_longlong] + [_P] * 9 + [C.POINTER(C.c_longlong)]),
     "hyb_clear_status": (C.c_int, [_ctx]),
     "hyb_set_auto_grow": (C.c_int, [_ctx, C.c_int]),
+    "hyb_get_state": (C.c_int, [_ctx, _P, C.c_size_t, C.POINTER(C.c_size_t)]),
+    "hyb_set_state": (C.c_int, [_ctx, _P, C.c_size_t]),
     "hyb_selftest_wait_timeout": (C.c_int, [_ctx, C.c_longlong]),
     "hyb_last_error": (C.c_char_p, []),
     "hyb_set_profiling": (C.c_int, [_ctx, C.c_int]),

@@ -41,7 +41,7 @@ cudaError_t ctx_alloc(hyb_ctx *c, void **p, size_t bytes) {
     return e;
 }
 
-static SpSet species_set(const hyb_ctx *c) {
+SpSet species_set(const hyb_ctx *c) {
     SpSet s;
     memset(&s, 0, sizeof(s));
     s.n = (int)c->sp.size();
@@ -126,6 +126,51 @@ static void enqueue_step(hyb_ctx *c) {
     c->launches_per_step = k;
 }
 
+// the per-slot arrays (particles, hole list) and the migration buffer of a
+// species with `cap` slots per tile
+hyb_status alloc_slots(hyb_ctx *c, SpDev &s, int cap, bool has_zq, bool has_tau) {
+    const size_t slots = (size_t)cap * c->g.ntiles;
+    s.cap = cap;
+    s.zq = s.tau = s.mzq = s.mtau = nullptr;
+    float **fl[7] = {&s.x, &s.y, &s.z, &s.ux, &s.uy, &s.uz, &s.w};
+    for (auto f : fl)
+        if (ctx_alloc(c, (void **)f, sizeof(float) * slots)) return HYB_ENOMEM;
+    if (has_zq && ctx_alloc(c, (void **)&s.zq, sizeof(float) * slots)) return HYB_ENOMEM;
+    if (has_tau && ctx_alloc(c, (void **)&s.tau, sizeof(float) * slots)) return HYB_ENOMEM;
+    if (ctx_alloc(c, (void **)&s.id, sizeof(uint64_t) * slots) || ctx_alloc(c, (void **)&s.holes, sizeof(int) * slots))
+        return HYB_ENOMEM;
+    // a particle moves less than one cell per step, so only the shell of a tile can leave it
+    const long long mig = std::min<long long>((long long)slots, std::max<long long>(65536, (long long)slots / 2));
+    s.mig_cap = (int)std::min<long long>(mig, 0x7fffffffLL);
+    float **ml[7] = {&s.mx, &s.my, &s.mz, &s.mux, &s.muy, &s.muz, &s.mw};
+    for (auto f : ml)
+        if (ctx_alloc(c, (void **)f, sizeof(float) * s.mig_cap)) return HYB_ENOMEM;
+    if (has_zq && ctx_alloc(c, (void **)&s.mzq, sizeof(float) * s.mig_cap)) return HYB_ENOMEM;
+    if (has_tau && ctx_alloc(c, (void **)&s.mtau, sizeof(float) * s.mig_cap)) return HYB_ENOMEM;
+    if (ctx_alloc(c, (void **)&s.mid, sizeof(uint64_t) * s.mig_cap) ||
+        ctx_alloc(c, (void **)&s.mdest, sizeof(int) * s.mig_cap))
+        return HYB_ENOMEM;
+    return HYB_OK;
+}
+
+// release a buffer of the context (buffers carved from a caller's arena stay
+// until the context is destroyed)
+static void ctx_free(hyb_ctx *c, void *p) {
+    if (!p || c->arena.base) return;
+    for (auto it = c->owned.begin(); it != c->owned.end(); ++it)
+        if (*it == p) {
+            c->owned.erase(it);
+            cudaFree(p);
+            return;
+        }
+}
+
+void free_slots(hyb_ctx *c, const SpDev &s) {
+    void *ps[] = {s.x, s.y, s.z, s.ux, s.uy, s.uz, s.w, s.zq, s.tau, s.id, s.holes,
+                  s.mx, s.my, s.mz, s.mux, s.muy, s.muz, s.mw, s.mzq, s.mtau, s.mid, s.mdest};
+    for (void *p : ps) ctx_free(c, p);
+}
+
 }  // namespace hyb
 
 using namespace hyb;
@@ -207,7 +252,7 @@ hyb_status hyb_init_grid(const hyb_grid_desc *d, hyb_ctx **out) {
     const size_t fbytes = sizeof(float) * 3 * (size_t)g.N;
     c->mur_plane = std::max({(long long)n[1] * n[2], (long long)n[0] * n[2], (long long)n[0] * n[1]});
     const int G = T + 3;
-    c->jframe = 3LL * G * G * G;
+    c->jframe = 4LL * G * G * G;  // 3 current components in the step, 4 moments in a conversion
     c->red_blocks = 152 * 8;   // enough warps for the loads of the reductions to cover the memory latency
     if (ctx_alloc(c, (void **)&c->E, fbytes) || ctx_alloc(c, (void **)&c->B, fbytes) ||
         ctx_alloc(c, (void **)&c->J, fbytes) ||
@@ -288,51 +333,6 @@ void hyb_destroy(hyb_ctx *c) {
     if (c->fill_ev) cudaEventDestroy(c->fill_ev);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
-}
-
-// the per-slot arrays (particles, hole list) and the migration buffer of a
-// species with `cap` slots per tile
-static hyb_status alloc_slots(hyb_ctx *c, SpDev &s, int cap, bool has_zq, bool has_tau) {
-    const size_t slots = (size_t)cap * c->g.ntiles;
-    s.cap = cap;
-    s.zq = s.tau = s.mzq = s.mtau = nullptr;
-    float **fl[7] = {&s.x, &s.y, &s.z, &s.ux, &s.uy, &s.uz, &s.w};
-    for (auto f : fl)
-        if (ctx_alloc(c, (void **)f, sizeof(float) * slots)) return HYB_ENOMEM;
-    if (has_zq && ctx_alloc(c, (void **)&s.zq, sizeof(float) * slots)) return HYB_ENOMEM;
-    if (has_tau && ctx_alloc(c, (void **)&s.tau, sizeof(float) * slots)) return HYB_ENOMEM;
-    if (ctx_alloc(c, (void **)&s.id, sizeof(uint64_t) * slots) || ctx_alloc(c, (void **)&s.holes, sizeof(int) * slots))
-        return HYB_ENOMEM;
-    // a particle moves less than one cell per step, so only the shell of a tile can leave it
-    const long long mig = std::min<long long>((long long)slots, std::max<long long>(65536, (long long)slots / 2));
-    s.mig_cap = (int)std::min<long long>(mig, 0x7fffffffLL);
-    float **ml[7] = {&s.mx, &s.my, &s.mz, &s.mux, &s.muy, &s.muz, &s.mw};
-    for (auto f : ml)
-        if (ctx_alloc(c, (void **)f, sizeof(float) * s.mig_cap)) return HYB_ENOMEM;
-    if (has_zq && ctx_alloc(c, (void **)&s.mzq, sizeof(float) * s.mig_cap)) return HYB_ENOMEM;
-    if (has_tau && ctx_alloc(c, (void **)&s.mtau, sizeof(float) * s.mig_cap)) return HYB_ENOMEM;
-    if (ctx_alloc(c, (void **)&s.mid, sizeof(uint64_t) * s.mig_cap) ||
-        ctx_alloc(c, (void **)&s.mdest, sizeof(int) * s.mig_cap))
-        return HYB_ENOMEM;
-    return HYB_OK;
-}
-
-// release a buffer of the context (buffers carved from a caller's arena stay
-// until the context is destroyed)
-static void ctx_free(hyb_ctx *c, void *p) {
-    if (!p || c->arena.base) return;
-    for (auto it = c->owned.begin(); it != c->owned.end(); ++it)
-        if (*it == p) {
-            c->owned.erase(it);
-            cudaFree(p);
-            return;
-        }
-}
-
-static void free_slots(hyb_ctx *c, const SpDev &s) {
-    void *ps[] = {s.x, s.y, s.z, s.ux, s.uy, s.uz, s.w, s.zq, s.tau, s.id, s.holes,
-                  s.mx, s.my, s.mz, s.mux, s.muy, s.muz, s.mw, s.mzq, s.mtau, s.mid, s.mdest};
-    for (void *p : ps) ctx_free(c, p);
 }
 
 static hyb_status alloc_species(hyb_ctx *c, Species &sp, int cap, bool has_zq, bool has_tau) {
@@ -562,7 +562,7 @@ hyb_status hyb_load_species(hyb_ctx *c, const hyb_species_desc *d, int *species_
         }
     }
     launch_bin_particles(g, sp.dev, n, dsrc[0], dsrc[1], dsrc[2], dsrc[3], dsrc[4], dsrc[5], dsrc[6], dsrc[7], dids,
-                         c->status, st);
+                         nullptr, c->status, st);
     int hstatus = 0;
     cudaMemcpyAsync(&hstatus, c->status, sizeof(int), cudaMemcpyDeviceToHost, st);
     e = cudaStreamSynchronize(st);

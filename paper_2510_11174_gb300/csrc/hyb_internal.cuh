@@ -242,7 +242,7 @@ struct hyb_ctx {
     long long mur_plane = 0;                         // max plane size
     float *jscratch = nullptr;                       // per-tile J frames
     int *jvalid = nullptr;                           // per tile: 1 when its frame was written this step
-    long long jframe = 0;                            // floats per tile frame (3 * G^3)
+    long long jframe = 0;                            // floats per tile of the frame scratch (4 * G^3)
     double *red_partials = nullptr;                  // FP64 block partials of reductions
     int red_blocks = 0;
     double *red_out = nullptr;                       // reduction results
@@ -343,9 +343,16 @@ void launch_rebin(const GridDev &g, const SpDev &s, int *status, cudaStream_t st
 void launch_compact(const GridDev &g, const SpDev &s, cudaStream_t st);
 void launch_regrid(const GridDev &g, const SpDev &from, const SpDev &to, cudaStream_t st);
 void launch_bin_particles(const GridDev &g, const SpDev &s, long long n, const float *x, const float *y,
-                          const float *z, const float *ux, const float *uy, const float *uz,
-                          const float *w, const float *zq, const uint64_t *ids, int *status,
+                          const float *z, const float *ux, const float *uy, const float *uz, const float *w,
+                          const float *zq, const uint64_t *ids, const float *tau, int *status,
                           cudaStream_t st);
+void launch_tiles_to_arrays(const GridDev &g, const SpDev &s, const long long *offsets, float *x, float *y, float *z,
+                            float *ux, float *uy, float *uz, float *w, float *zq, float *tau, uint64_t *ids,
+                            cudaStream_t st);
+// species slot storage (abi.cu): allocate / release the per-slot arrays of a species
+hyb_status alloc_slots(hyb_ctx *c, SpDev &s, int cap, bool has_zq, bool has_tau);
+void free_slots(hyb_ctx *c, const SpDev &s);
+SpSet species_set(const hyb_ctx *c);
 void launch_count_tiles(const GridDev &g, long long n, const float *x, const float *y, const float *z,
                         int *counts, cudaStream_t st);
 

@@ -617,7 +617,7 @@ __global__ void k_count_tiles(GridDev g, long long n, const float *__restrict__ 
 __global__ void k_bin(GridDev g, SpDev sp, long long n, const float *__restrict__ x, const float *__restrict__ y,
                       const float *__restrict__ z, const float *__restrict__ ux, const float *__restrict__ uy,
                       const float *__restrict__ uz, const float *__restrict__ w, const float *__restrict__ zq,
-                      const uint64_t *__restrict__ ids, int *__restrict__ status) {
+                      const uint64_t *__restrict__ ids, const float *__restrict__ tau, int *__restrict__ status) {
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
          p += (long long)gridDim.x * blockDim.x) {
         const int t = tile_index(g, x[p], y[p], z[p]);
@@ -632,7 +632,27 @@ __global__ void k_bin(GridDev g, SpDev sp, long long n, const float *__restrict_
         sp.w[s] = w[p];
         if (sp.zq) sp.zq[s] = zq ? zq[p] : 0.0f;
         sp.id[s] = ids ? ids[p] : (uint64_t)p;
-        if (sp.tau) sp.tau[s] = tau_initial(sp.id[s], g.seed, sp.tau_index);
+        if (sp.tau) sp.tau[s] = tau ? tau[p] : tau_initial(sp.id[s], g.seed, sp.tau_index);
+    }
+}
+
+// the live slots of every tile, tile after tile, into contiguous arrays
+// (offsets: exclusive prefix sum of the tile counts); zq / tau / the outputs
+// for them may be null
+__global__ void k_tiles_to_arrays(SpDev sp, const long long *__restrict__ offsets, float *__restrict__ x,
+                                  float *__restrict__ y, float *__restrict__ z, float *__restrict__ ux,
+                                  float *__restrict__ uy, float *__restrict__ uz, float *__restrict__ w,
+                                  float *__restrict__ zq, float *__restrict__ tau, uint64_t *__restrict__ ids) {
+    const int t = blockIdx.x;
+    const int n = min(sp.count[t], sp.cap);
+    const long long a = (long long)t * sp.cap, b = offsets[t];
+    for (int p = threadIdx.x; p < n; p += blockDim.x) {
+        x[b + p] = sp.x[a + p]; y[b + p] = sp.y[a + p]; z[b + p] = sp.z[a + p];
+        ux[b + p] = sp.ux[a + p]; uy[b + p] = sp.uy[a + p]; uz[b + p] = sp.uz[a + p];
+        w[b + p] = sp.w[a + p];
+        if (zq && sp.zq) zq[b + p] = sp.zq[a + p];
+        if (tau && sp.tau) tau[b + p] = sp.tau[a + p];
+        ids[b + p] = sp.id[a + p];
     }
 }
 
@@ -677,9 +697,16 @@ void launch_count_tiles(const GridDev &g, long long n, const float *x, const flo
 
 void launch_bin_particles(const GridDev &g, const SpDev &s, long long n, const float *x, const float *y,
                           const float *z, const float *ux, const float *uy, const float *uz, const float *w,
-                          const float *zq, const uint64_t *ids, int *status, cudaStream_t st) {
+                          const float *zq, const uint64_t *ids, const float *tau, int *status, cudaStream_t st) {
     if (n == 0) return;
-    k_bin<<<min(blocks_for(n, 256), 152u * 16u), 256, 0, st>>>(g, s, n, x, y, z, ux, uy, uz, w, zq, ids, status);
+    k_bin<<<min(blocks_for(n, 256), 152u * 16u), 256, 0, st>>>(g, s, n, x, y, z, ux, uy, uz, w, zq, ids, tau,
+                                                               status);
+}
+
+void launch_tiles_to_arrays(const GridDev &g, const SpDev &s, const long long *offsets, float *x, float *y, float *z,
+                            float *ux, float *uy, float *uz, float *w, float *zq, float *tau, uint64_t *ids,
+                            cudaStream_t st) {
+    k_tiles_to_arrays<<<g.ntiles, 256, 0, st>>>(s, offsets, x, y, z, ux, uy, uz, w, zq, tau, ids);
 }
 
 }  // namespace hyb

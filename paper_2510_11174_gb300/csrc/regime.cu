@@ -4,6 +4,12 @@
 // the learned switch flags instability; charge and energy checked during
 // regime switches).  The paper does not define the criterion; the reading is
 // stated with hyb_regime_desc in include/hyb.h.
+//
+// Every scatter onto the nodes here (CIC electron density, particle moments
+// deposited into a fluid, the charge of converted particles) goes through the
+// per-tile fixed-point frames of frames.cuh and a fixed-order gather, so a
+// classification repeats bit for bit like the step.
+#include "frames.cuh"
 #include "hyb_internal.cuh"
 #include "particles.cuh"
 #include "qed.cuh"
@@ -27,35 +33,110 @@ __device__ __forceinline__ float node_e(const GridDev &g, const float *__restric
     return sqrtf(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
 }
 
-// electron density from the macro-particles (CIC, node arrays)
-__global__ void k_density(GridDev g, SpDev sp, float scale, float *__restrict__ ne) {
-    const int t = blockIdx.x;
-    const int n = min(sp.count[t], sp.cap);
-    const long long base = (long long)t * sp.cap;
-    for (int p = threadIdx.x; p < n; p += blockDim.x) {
-        const float pos[3] = {sp.x[base + p], sp.y[base + p], sp.z[base + p]};
-        const float val = scale * sp.w[base + p];
-        int b[3];
-        float f[3];
-        for (int a = 0; a < 3; ++a) {
-            int i = (int)floorf(pos[a]);
-            if (g.bc[a] && i > g.n[a] - 2) i = g.n[a] - 2;
-            b[a] = i;
-            f[a] = pos[a] - (float)i;
-        }
-        for (int c = 0; c < 8; ++c) {
-            int q[3] = {b[0] + (c & 1), b[1] + ((c >> 1) & 1), b[2] + (c >> 2)};
-            bool ok = true;
-            for (int a = 0; a < 3; ++a) {
-                if (g.bc[a] == 0) q[a] = q[a] >= g.n[a] ? q[a] - g.n[a] : q[a];
-                else if (q[a] > g.n[a] - 1) ok = false;
+// CIC weights of a particle position along axis a: base node (clamped below
+// the top wall of an absorbing axis) and the fraction toward the next node
+__device__ __forceinline__ void cic_axis(const GridDev &g, int a, float p, int &b, float &f) {
+    int i = (int)floorf(p);
+    if (g.bc[a] && i > g.n[a] - 2) i = g.n[a] - 2;
+    b = i;
+    f = p - (float)i;
+}
+
+// the tile's frame origin (one node below its first node) per axis
+__device__ __forceinline__ void tile_origin(const GridDev &g, int t, int o[3]) {
+    o[0] = (t % g.nt[0]) * g.T - 1;
+    o[1] = ((t / g.nt[0]) % g.nt[1]) * g.T - 1;
+    o[2] = (t / (g.nt[0] * g.nt[1])) * g.T - 1;
+}
+
+// add v times the CIC weights of a particle at pos (unwrapped, inside the
+// frame) to component q of a fixed-point frame
+__device__ __forceinline__ void frame_cic(const GridDev &g, unsigned long long *fr, int G, const int o[3],
+                                          const float pos[3], float v) {
+    int b[3];
+    float f[3];
+    for (int a = 0; a < 3; ++a) cic_axis(g, a, pos[a], b[a], f[a]);
+    for (int c = 0; c < 8; ++c) {
+        const float wgt = ((c & 1) ? f[0] : 1.0f - f[0]) * (((c >> 1) & 1) ? f[1] : 1.0f - f[1]) *
+                          ((c >> 2) ? f[2] : 1.0f - f[2]);
+        const int l0 = b[0] + (c & 1) - o[0], l1 = b[1] + ((c >> 1) & 1) - o[1], l2 = b[2] + (c >> 2) - o[2];
+        if (wgt != 0.0f) atomicAdd(&fr[(l2 * G + l1) * G + l0], fix_of(wgt * v));
+    }
+}
+
+// a particle position of tile t is inside the tile's cells (what the frames assume)
+__device__ __forceinline__ bool in_tile(const GridDev &g, const int o[3], const float pos[3]) {
+    bool ok = true;
+    for (int a = 0; a < 3; ++a) {
+        int ci = (int)floorf(pos[a]);
+        if (g.bc[a] && ci > g.n[a] - 2) ci = g.n[a] - 2;
+        ok = ok && isfinite(pos[a]) && ci >= o[a] + 1 && ci <= o[a] + g.T;
+    }
+    return ok;
+}
+
+// electron density from the macro-particles of the species in `which` (bit
+// s: species s), CIC: one fixed-point frame per tile, then a fixed-order
+// gather into ne
+__global__ void __launch_bounds__(256) k_density_frames(GridDev g, const SpDev *__restrict__ sps, int nsp,
+                                                         unsigned which, float *__restrict__ scratch,
+                                                         int *__restrict__ valid, int *__restrict__ status) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    unsigned long long *fr = reinterpret_cast<unsigned long long *>(smraw);
+    __shared__ int s_max[32];
+    const int t = blockIdx.x, G = frame_G(g.T), G3 = G * G * G;
+    const float idV = 1.0f / (g.d[0] * g.d[1] * g.d[2]);
+    int total = 0;
+    float vmax = 0.0f;
+    for (int si = 0; si < nsp; ++si) {
+        if (!((which >> si) & 1u)) continue;
+        const SpDev &sp = sps[si];
+        const int n = min(sp.count[t], sp.cap);
+        total += n;
+        for (int p = threadIdx.x; p < n; p += blockDim.x)
+            vmax = fmaxf(vmax, fabsf(sp.q * idV * sp.w[(long long)t * sp.cap + p]));
+    }
+    if (total == 0) {
+        if (threadIdx.x == 0) valid[t] = 0;
+        return;
+    }
+    block_max_put(vmax, s_max);
+    for (int l = threadIdx.x; l < G3; l += blockDim.x) fr[l] = 0ULL;
+    __syncthreads();
+    const int k = fix_exponent((double)total * (double)block_max_read(s_max));
+    const float sc = pow2f(k);
+    int o[3];
+    tile_origin(g, t, o);
+    for (int si = 0; si < nsp; ++si) {
+        if (!((which >> si) & 1u)) continue;
+        const SpDev &sp = sps[si];
+        const int n = min(sp.count[t], sp.cap);
+        const long long base = (long long)t * sp.cap;
+        const float qv = -sp.q * idV * sc;  // electrons: n_e = -q w / dV
+        for (int p = threadIdx.x; p < n; p += blockDim.x) {
+            const float pos[3] = {sp.x[base + p], sp.y[base + p], sp.z[base + p]};
+            if (!in_tile(g, o, pos)) {
+                atomicOr(status, ST_BADPOS);
+                continue;
             }
-            if (!ok) continue;
-            const float wgt = ((c & 1) ? f[0] : 1.0f - f[0]) * (((c >> 1) & 1) ? f[1] : 1.0f - f[1]) *
-                              ((c >> 2) ? f[2] : 1.0f - f[2]);
-            atomicAdd(&ne[cidx(g, q[0], q[1], q[2])], wgt * val);
+            frame_cic(g, fr, G, o, pos, qv * sp.w[base + p]);
         }
     }
+    __syncthreads();
+    float *dst = scratch + (long long)t * G3;
+    const float inv = pow2f(-k);
+    for (int l = threadIdx.x; l < G3; l += blockDim.x) dst[l] = fix_to_float(fr[l], inv);
+    if (threadIdx.x == 0) valid[t] = 1;
+}
+
+__global__ void k_density_gather(GridDev g, const float *__restrict__ scratch, const int *__restrict__ valid,
+                                 float *__restrict__ ne) {
+    const int nx = g.n[0], ny = g.n[1];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
+    if (i >= nx) return;
+    float acc[1];
+    frame_gather<1>(g, scratch, valid, 1, i, j, k, acc);
+    ne[((long long)k * ny + j) * nx + i] = acc[0];
 }
 
 __global__ void k_criterion(GridDev g, const float *__restrict__ E, const float *__restrict__ ne, FluidDev fe,
@@ -132,88 +213,125 @@ __global__ void k_dilate(GridDev g, int a, int r, const uint8_t *__restrict__ in
     out[c] = m;
 }
 
-// fluid -> particles at kinetic nodes; rho_bg takes (removed fluid charge) -
-// (CIC charge of the new particles)
-__global__ void k_fluid_to_particles(GridDev g, const uint8_t *__restrict__ mask, const uint8_t *__restrict__ prev,
-                                     FluidDev f, SpDev dst, int ppc, uint32_t epoch, float *__restrict__ rho_bg,
-                                     int *__restrict__ status) {
-    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= g.N) return;
+// fluid -> particles at the nodes that switch to kinetic; one CTA per tile
+// walks the tile's nodes.  rho_bg takes (removed fluid charge) - (CIC charge of
+// the new particles): both go into the tile's fixed-point frame, which
+// k_rho_gather adds to rho_bg in a fixed order.
+__global__ void __launch_bounds__(256) k_fluid_to_particles(GridDev g, const uint8_t *__restrict__ mask,
+                                                             const uint8_t *__restrict__ prev, FluidDev f, SpDev dst,
+                                                             int ppc, uint32_t epoch, float *__restrict__ scratch,
+                                                             int *__restrict__ valid, int *__restrict__ status) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    unsigned long long *fr = reinterpret_cast<unsigned long long *>(smraw);
+    __shared__ int s_max[32];
+    const int t = blockIdx.x, T = g.T, G = frame_G(T), G3 = G * G * G, T3 = T * T * T;
+    int o[3];
+    tile_origin(g, t, o);
+    const int nx = g.n[0], ny = g.n[1];
+    auto node_of = [&](int l, int idx[3]) -> long long {
+        idx[0] = o[0] + 1 + l % T;
+        idx[1] = o[1] + 1 + (l / T) % T;
+        idx[2] = o[2] + 1 + l / (T * T);
+        return ((long long)idx[2] * ny + idx[1]) * nx + idx[0];
+    };
     // only nodes that switch to kinetic now: fluid that flows into a node
     // that was kinetic already stays fluid there
-    if (!mask[c] || prev[c] || !(f.n[c] > f.n_floor)) return;
-    const int nx = g.n[0], ny = g.n[1];
-    const int idx[3] = {(int)(c % nx), (int)((c / nx) % ny), (int)(c / ((long long)nx * ny))};
-    const float dV = g.d[0] * g.d[1] * g.d[2];
-    const float n = f.n[c];
-    const float w = n * dV / (float)ppc;
-    atomicAdd(&rho_bg[c], f.q * n);
-    const float u[3] = {f.ux[c], f.uy[c], f.uz[c]};
-    for (int p = 0; p < ppc; ++p) {
-        const u32x4 r = philox4x32_10((uint32_t)c, epoch, (uint32_t)p, 6u, g.seed, dst.sp_index);
-        float pos[3];
-        for (int a = 0; a < 3; ++a) {
-            float lo = (float)idx[a] - 0.5f, hi = (float)idx[a] + 0.5f;
-            if (g.bc[a]) {
-                lo = fmaxf(lo, 0.0f);
-                hi = fminf(hi, (float)(g.n[a] - 1));
-            }
-            pos[a] = lo + (hi - lo) * u01f(r.v[a]);
-            if (g.bc[a] == 0) {
-                if (pos[a] < 0.0f) pos[a] += (float)g.n[a];
-                if (pos[a] >= (float)g.n[a]) pos[a] -= (float)g.n[a];
-                if (pos[a] >= (float)g.n[a]) pos[a] = 0.0f;
-            }
+    auto converts = [&](long long c) { return mask[c] && !prev[c] && f.n[c] > f.n_floor; };
+    float qmax = 0.0f;
+    int any = 0;
+    for (int l = threadIdx.x; l < T3; l += blockDim.x) {
+        int idx[3];
+        const long long c = node_of(l, idx);
+        if (converts(c)) {
+            qmax = fmaxf(qmax, fabsf(f.q * f.n[c]));
+            any = 1;
         }
-        // CIC charge of the new particle leaves rho_bg
-        int b[3];
-        float fr[3];
-        for (int a = 0; a < 3; ++a) {
-            int i = (int)floorf(pos[a]);
-            if (g.bc[a] && i > g.n[a] - 2) i = g.n[a] - 2;
-            b[a] = i;
-            fr[a] = pos[a] - (float)i;
-        }
-        for (int k8 = 0; k8 < 8; ++k8) {
-            int q[3] = {b[0] + (k8 & 1), b[1] + ((k8 >> 1) & 1), b[2] + (k8 >> 2)};
-            bool ok = true;
-            for (int a = 0; a < 3; ++a) {
-                if (g.bc[a] == 0) q[a] = q[a] >= g.n[a] ? q[a] - g.n[a] : q[a];
-                else if (q[a] > g.n[a] - 1) ok = false;
-            }
-            if (!ok) continue;
-            const float wgt = ((k8 & 1) ? fr[0] : 1.0f - fr[0]) * (((k8 >> 1) & 1) ? fr[1] : 1.0f - fr[1]) *
-                              ((k8 >> 2) ? fr[2] : 1.0f - fr[2]);
-            atomicAdd(&rho_bg[cidx(g, q[0], q[1], q[2])], -dst.q * w / dV * wgt);
-        }
-        const uint64_t id = (1ULL << 62) | (derived_id((uint64_t)c | ((uint64_t)epoch << 40), p, 6u) >> 2);
-        const float tau = dst.tau ? tau_initial(id, g.seed, dst.tau_index) : 0.0f;
-        tile_put(dst, tile_index(g, pos[0], pos[1], pos[2]), pos, u, w, id, tau, status);
     }
-    f.n[c] = 0.0f;
-    f.ux[c] = f.uy[c] = f.uz[c] = 0.0f;
-}
-
-__global__ void k_mom_init(long long N, FluidDev f) {
-    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= N) return;
-    f.usx[c] = f.n[c] * f.ux[c];
-    f.usy[c] = f.n[c] * f.uy[c];
-    f.usz[c] = f.n[c] * f.uz[c];
-}
-
-// particles whose nearest node is fluid: CIC-deposit n and n u, then remove
-__global__ void k_particles_to_fluid(GridDev g, const uint8_t *__restrict__ mask, SpDev sp, FluidDev f) {
-    __shared__ int s_holes;
-    const int t = blockIdx.x;
-    if (threadIdx.x == 0) s_holes = 0;
+    if (!__syncthreads_or(any)) {
+        if (threadIdx.x == 0) valid[t] = 0;
+        return;
+    }
+    block_max_put(qmax, s_max);
+    for (int l = threadIdx.x; l < G3; l += blockDim.x) fr[l] = 0ULL;
     __syncthreads();
+    // each converting node adds q n at itself and -q n spread by CIC: a node's
+    // sum is at most 2 T^3 max |q n|
+    const int k = fix_exponent(2.0 * (double)T3 * (double)block_max_read(s_max));
+    const float sc = pow2f(k);
+    const float dV = g.d[0] * g.d[1] * g.d[2];
+    for (int l = threadIdx.x; l < T3; l += blockDim.x) {
+        int idx[3];
+        const long long c = node_of(l, idx);
+        if (!converts(c)) continue;
+        const float n = f.n[c];
+        const float w = n * dV / (float)ppc;
+        {
+            const int l0 = idx[0] - o[0], l1 = idx[1] - o[1], l2 = idx[2] - o[2];
+            atomicAdd(&fr[(l2 * G + l1) * G + l0], fix_of(f.q * n * sc));
+        }
+        const float u[3] = {f.ux[c], f.uy[c], f.uz[c]};
+        for (int p = 0; p < ppc; ++p) {
+            const u32x4 r = philox4x32_10((uint32_t)c, epoch, (uint32_t)p, 6u, g.seed, dst.sp_index);
+            float pos[3], upos[3];
+            for (int a = 0; a < 3; ++a) {
+                float lo = (float)idx[a] - 0.5f, hi = (float)idx[a] + 0.5f;
+                if (g.bc[a]) {
+                    lo = fmaxf(lo, 0.0f);
+                    hi = fminf(hi, (float)(g.n[a] - 1));
+                }
+                upos[a] = lo + (hi - lo) * u01f(r.v[a]);
+                pos[a] = upos[a];
+                if (g.bc[a] == 0) {
+                    if (pos[a] < 0.0f) pos[a] += (float)g.n[a];
+                    if (pos[a] >= (float)g.n[a]) pos[a] -= (float)g.n[a];
+                    if (pos[a] >= (float)g.n[a]) pos[a] = 0.0f;
+                }
+            }
+            // CIC charge of the new particle leaves rho_bg (the unwrapped
+            // position indexes the frame; the gather wraps periodic axes)
+            frame_cic(g, fr, G, o, upos, -dst.q * w / dV * sc);
+            const uint64_t id = (1ULL << 62) | (derived_id((uint64_t)c | ((uint64_t)epoch << 40), p, 6u) >> 2);
+            const float tau = dst.tau ? tau_initial(id, g.seed, dst.tau_index) : 0.0f;
+            tile_put(dst, tile_index(g, pos[0], pos[1], pos[2]), pos, u, w, id, tau, status);
+        }
+        f.n[c] = 0.0f;
+        f.ux[c] = f.uy[c] = f.uz[c] = 0.0f;
+    }
+    __syncthreads();
+    float *out = scratch + (long long)t * G3;
+    const float inv = pow2f(-k);
+    for (int l = threadIdx.x; l < G3; l += blockDim.x) out[l] = fix_to_float(fr[l], inv);
+    if (threadIdx.x == 0) valid[t] = 1;
+}
+
+__global__ void k_rho_gather(GridDev g, const float *__restrict__ scratch, const int *__restrict__ valid,
+                             float *__restrict__ rho_bg) {
+    const int nx = g.n[0], ny = g.n[1];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
+    if (i >= nx) return;
+    float acc[1];
+    frame_gather<1>(g, scratch, valid, 1, i, j, k, acc);
+    const long long c = ((long long)k * ny + j) * nx + i;
+    if (acc[0] != 0.0f) rho_bg[c] += acc[0];
+}
+
+// particles whose nearest node is fluid: CIC-deposit n and n u into the tile's
+// fixed-point frame (4 components), then remove them; k_moments_gather adds
+// the frames to the fluid in a fixed order
+__global__ void __launch_bounds__(256) k_particles_to_fluid(GridDev g, const uint8_t *__restrict__ mask, SpDev sp,
+                                                             float *__restrict__ scratch, int *__restrict__ valid,
+                                                             int *__restrict__ status) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    unsigned long long *fr = reinterpret_cast<unsigned long long *>(smraw);  // n, n ux, n uy, n uz
+    __shared__ int s_holes;
+    __shared__ int s_max[2][32];
+    const int t = blockIdx.x, G = frame_G(g.T), G3 = G * G * G;
     const int n = min(sp.count[t], sp.cap);
     const long long base = (long long)t * sp.cap;
     const float idV = 1.0f / (g.d[0] * g.d[1] * g.d[2]);
-    for (int p = threadIdx.x; p < n; p += blockDim.x) {
-        const long long s = base + p;
-        const float pos[3] = {sp.x[s], sp.y[s], sp.z[s]};
+    int o[3];
+    tile_origin(g, t, o);
+    auto nearest_fluid = [&](const float pos[3]) {
         int nd[3];
         for (int a = 0; a < 3; ++a) {
             int i = (int)floorf(pos[a] + 0.5f);
@@ -221,52 +339,85 @@ __global__ void k_particles_to_fluid(GridDev g, const uint8_t *__restrict__ mask
             else if (i > g.n[a] - 1) i = g.n[a] - 1;
             nd[a] = i;
         }
-        if (mask[cidx(g, nd[0], nd[1], nd[2])]) continue;
+        return mask[cidx(g, nd[0], nd[1], nd[2])] == 0;
+    };
+    float wmax = 0.0f, wumax = 0.0f;
+    int any = 0;
+    for (int p = threadIdx.x; p < n; p += blockDim.x) {
+        const long long s = base + p;
+        const float pos[3] = {sp.x[s], sp.y[s], sp.z[s]};
+        if (!nearest_fluid(pos)) continue;
         const float wn = sp.w[s] * idV;
-        const float u[3] = {sp.ux[s], sp.uy[s], sp.uz[s]};
-        int b[3];
-        float fr[3];
-        for (int a = 0; a < 3; ++a) {
-            int i = (int)floorf(pos[a]);
-            if (g.bc[a] && i > g.n[a] - 2) i = g.n[a] - 2;
-            b[a] = i;
-            fr[a] = pos[a] - (float)i;
+        wmax = fmaxf(wmax, fabsf(wn));
+        wumax = fmaxf(wumax, fabsf(wn) * fmaxf(fabsf(sp.ux[s]), fmaxf(fabsf(sp.uy[s]), fabsf(sp.uz[s]))));
+        any = 1;
+    }
+    if (threadIdx.x == 0) s_holes = 0;
+    if (!__syncthreads_or(any)) {
+        if (threadIdx.x == 0) {
+            valid[t] = 0;
+            sp.hole_count[t] = 0;
+            sp.hole_used[t] = 0;
         }
-        for (int k8 = 0; k8 < 8; ++k8) {
-            int q[3] = {b[0] + (k8 & 1), b[1] + ((k8 >> 1) & 1), b[2] + (k8 >> 2)};
-            bool ok = true;
-            for (int a = 0; a < 3; ++a) {
-                if (g.bc[a] == 0) q[a] = q[a] >= g.n[a] ? q[a] - g.n[a] : q[a];
-                else if (q[a] > g.n[a] - 1) ok = false;
-            }
-            if (!ok) continue;
-            const float wgt = ((k8 & 1) ? fr[0] : 1.0f - fr[0]) * (((k8 >> 1) & 1) ? fr[1] : 1.0f - fr[1]) *
-                              ((k8 >> 2) ? fr[2] : 1.0f - fr[2]);
-            const long long cc = cidx(g, q[0], q[1], q[2]);
-            atomicAdd(&f.n[cc], wgt * wn);
-            atomicAdd(&f.usx[cc], wgt * wn * u[0]);
-            atomicAdd(&f.usy[cc], wgt * wn * u[1]);
-            atomicAdd(&f.usz[cc], wgt * wn * u[2]);
+        return;
+    }
+    block_max_put(wmax, s_max[0]);
+    block_max_put(wumax, s_max[1]);
+    for (int l = threadIdx.x; l < 4 * G3; l += blockDim.x) fr[l] = 0ULL;
+    __syncthreads();
+    const int kn = fix_exponent((double)n * (double)block_max_read(s_max[0]));
+    const int ku = fix_exponent((double)n * (double)block_max_read(s_max[1]));
+    const float sn = pow2f(kn), su = pow2f(ku);
+    for (int p = threadIdx.x; p < n; p += blockDim.x) {
+        const long long s = base + p;
+        const float pos[3] = {sp.x[s], sp.y[s], sp.z[s]};
+        if (!nearest_fluid(pos)) continue;
+        if (!in_tile(g, o, pos)) {
+            atomicOr(status, ST_BADPOS);
+            continue;
         }
+        const float wn = sp.w[s] * idV;
+        frame_cic(g, fr, G, o, pos, wn * sn);
+        frame_cic(g, fr + G3, G, o, pos, wn * sp.ux[s] * su);
+        frame_cic(g, fr + 2 * G3, G, o, pos, wn * sp.uy[s] * su);
+        frame_cic(g, fr + 3 * G3, G, o, pos, wn * sp.uz[s] * su);
         const int h = atomicAdd(&s_holes, 1);
         sp.holes[base + h] = p;
         sp.x[s] = -1.0f;
     }
     __syncthreads();
+    float *out = scratch + (long long)t * 4 * G3;
+    const float in_ = pow2f(-kn), iu = pow2f(-ku);
+    for (int l = threadIdx.x; l < 4 * G3; l += blockDim.x) out[l] = fix_to_float(fr[l], l < G3 ? in_ : iu);
     if (threadIdx.x == 0) {
+        valid[t] = 1;
         sp.hole_count[t] = s_holes;
         sp.hole_used[t] = 0;
     }
 }
 
-__global__ void k_mom_final(long long N, FluidDev f) {
-    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= N) return;
-    const float n = f.n[c];
-    const bool keep = n > f.n_floor;
-    f.ux[c] = keep ? f.usx[c] / n : 0.0f;
-    f.uy[c] = keep ? f.usy[c] / n : 0.0f;
-    f.uz[c] = keep ? f.usz[c] / n : 0.0f;
+// fluid += the deposited moments: n' = n + sum n_p, u' = (n u + sum n_p u_p) / n'
+// (u' = 0 where n' is at or below the floor)
+__global__ void k_moments_gather(GridDev g, const float *__restrict__ scratch, const int *__restrict__ valid,
+                                 FluidDev f) {
+    const int nx = g.n[0], ny = g.n[1];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
+    if (i >= nx) return;
+    float acc[4];
+    frame_gather<4>(g, scratch, valid, 4, i, j, k, acc);
+    const long long c = ((long long)k * ny + j) * nx + i;
+    const float n0 = f.n[c];
+    if (acc[0] == 0.0f && acc[1] == 0.0f && acc[2] == 0.0f && acc[3] == 0.0f) {
+        if (!(n0 > f.n_floor)) f.ux[c] = f.uy[c] = f.uz[c] = 0.0f;
+        return;
+    }
+    const float n1 = n0 + acc[0];
+    const bool keep = n1 > f.n_floor;
+    const float mx = n0 * f.ux[c] + acc[1], my = n0 * f.uy[c] + acc[2], mz = n0 * f.uz[c] + acc[3];
+    f.n[c] = n1;
+    f.ux[c] = keep ? mx / n1 : 0.0f;
+    f.uy[c] = keep ? my / n1 : 0.0f;
+    f.uz[c] = keep ? mz / n1 : 0.0f;
 }
 
 static inline unsigned nblk(long long n) { return (unsigned)((n + 255) / 256); }
@@ -281,12 +432,21 @@ hyb_status regime_update(hyb_ctx *c, const float *pm, const float *ps) {
     const bool all = rd.policy == HYB_REGIME_ALL_KINETIC;
     const bool physics = !all && (!pm || rd.policy == HYB_REGIME_UNION);
     long long launches = 0;
+    const int fG = frame_G(g.T), fG3 = fG * fG * fG;
     if (all) cudaMemsetAsync(raw, 1, (size_t)g.N, st);
     if (physics) {
-        cudaMemsetAsync(c->ne, 0, sizeof(float) * g.N, st);
-        for (const Species &s : c->sp)
-            if (s.dev.kind == 0 && s.q < 0.0 && !s.has_zq && ++launches)
-                k_density<<<g.ntiles, 256, 0, st>>>(g, s.dev, (float)(-s.q / (g.dd[0] * g.dd[1] * g.dd[2])), c->ne);
+        unsigned which = 0;
+        for (size_t si = 0; si < c->sp.size(); ++si)
+            if (c->sp[si].dev.kind == 0 && c->sp[si].q < 0.0 && !c->sp[si].has_zq) which |= 1u << si;
+        if (which) {
+            const size_t sm1 = sizeof(unsigned long long) * (size_t)fG3;
+            k_density_frames<<<g.ntiles, 256, sm1, st>>>(g, c->sp_dev, (int)c->sp.size(), which, c->jscratch,
+                                                         c->jvalid, c->status);
+            k_density_gather<<<node_grid(g), node_block(g), 0, st>>>(g, c->jscratch, c->jvalid, c->ne);
+            launches += 2;
+        } else {
+            cudaMemsetAsync(c->ne, 0, sizeof(float) * g.N, st);
+        }
         int fe = -1;
         for (size_t f = 0; f < c->fluids.size(); ++f)
             if (c->fluids[f].q < 0.0f) {
@@ -317,12 +477,14 @@ hyb_status regime_update(hyb_ctx *c, const float *pm, const float *ps) {
         if (sid < 0 || sid >= (int)c->sp.size()) continue;
         const SpDev &dst = c->sp[sid].dev;
         // the tiles are compact between steps: new particles go straight into them
-        k_fluid_to_particles<<<nblk(g.N), 256, 0, st>>>(g, mask, c->mask_prev, c->fluids[f], dst,
-                                                        rd.ppc > 0 ? rd.ppc : 8, c->epoch, c->rho_bg, c->status);
+        const size_t sm1 = sizeof(unsigned long long) * (size_t)fG3;
+        k_fluid_to_particles<<<g.ntiles, 256, sm1, st>>>(g, mask, c->mask_prev, c->fluids[f], dst,
+                                                         rd.ppc > 0 ? rd.ppc : 8, c->epoch, c->jscratch, c->jvalid,
+                                                         c->status);
+        k_rho_gather<<<node_grid(g), node_block(g), 0, st>>>(g, c->jscratch, c->jvalid, c->rho_bg);
         k_clamp_counts<<<(g.ntiles + 255) / 256, 256, 0, st>>>(g.ntiles, dst);
-        k_mom_init<<<nblk(g.N), 256, 0, st>>>(g.N, c->fluids[f]);
-        k_particles_to_fluid<<<g.ntiles, 256, 0, st>>>(g, mask, dst, c->fluids[f]);
-        k_mom_final<<<nblk(g.N), 256, 0, st>>>(g.N, c->fluids[f]);
+        k_particles_to_fluid<<<g.ntiles, 256, 4 * sm1, st>>>(g, mask, dst, c->jscratch, c->jvalid, c->status);
+        k_moments_gather<<<node_grid(g), node_block(g), 0, st>>>(g, c->jscratch, c->jvalid, c->fluids[f]);
         launch_compact(g, dst, st);
         launches += 6;
     }

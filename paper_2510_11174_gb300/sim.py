@@ -207,6 +207,11 @@ class Simulation:
         ptr = lambda t: None if t is None else t.data_ptr()
         check(self._lib.hyb_classify(self._ctx, None if model is None else model.handle, ptr(p_mean), ptr(p_std),
                                      None))
+        if (p_mean is not None or p_std is not None) and self.torch_stream is not None:
+            # the outputs are written on the context's stream: order torch's
+            # current stream (their consumer) after it
+            torch = _torch()
+            torch.cuda.current_stream().wait_stream(self.torch_stream)
 
     def get_regime(self):
         mask = np.empty(self.shape, np.uint8)
@@ -241,6 +246,19 @@ class Simulation:
 
     def clear_status(self):
         check(self._lib.hyb_clear_status(self._ctx))
+
+    def get_state(self):
+        """The context's whole state as a byte image (hyb_get_state); a numpy uint8 array."""
+        size = C.c_size_t()
+        check(self._lib.hyb_get_state(self._ctx, None, 0, C.byref(size)))
+        buf = np.empty(size.value, np.uint8)
+        check(self._lib.hyb_get_state(self._ctx, buf.ctypes.data, buf.size, C.byref(size)))
+        return buf
+
+    def set_state(self, image):
+        """Restore an image of get_state (hyb_set_state) into this context."""
+        buf = np.ascontiguousarray(image, dtype=np.uint8)
+        check(self._lib.hyb_set_state(self._ctx, buf.ctypes.data, buf.size))
 
     def set_auto_grow(self, on=True):
         """Turn the growth of full particle tiles on or off (hyb_set_auto_grow)."""

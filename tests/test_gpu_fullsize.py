@@ -207,8 +207,14 @@ def test_training_batch_32_of_32_cubed_patches():
     for l in range(4):
         gw, gb = m.get_grad(l)
         rw, rb = ref["grads"][l]
-        assert rel_l2(gw, rw.numpy()) <= 1e-2, (l, rel_l2(gw, rw.numpy()))
-        assert rel_l2(gb, rb.numpy()) <= 1e-2, (l, rel_l2(gb, rb.numpy()))
+        # 1e-3, except the first layer's weight gradient: BF16 rounding points
+        # shared with the oracle still flip where FP32 and FP64 sums straddle a
+        # rounding boundary, and the flips of every layer collect in layer 0
+        # (measured up to 1.0e-3 there; an FP32-summing copy of the oracle
+        # itself differs from the FP64 one by up to 1e-2 on such inputs)
+        tol = 2e-3 if l == 0 else 1e-3
+        assert rel_l2(gw, rw.numpy()) <= tol, (l, rel_l2(gw, rw.numpy()))
+        assert rel_l2(gb, rb.numpy()) <= tol, (l, rel_l2(gb, rb.numpy()))
     # then a step of the whole batch of 32
     st = m.train_step(torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda())
     assert math.isfinite(st["loss"]) and st["step"] == 2
