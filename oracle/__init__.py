@@ -127,7 +127,7 @@ def _declare(L):
     L.orc_fluid_energy.restype = C.c_double
     L.orc_regime_criterion.argtypes = [C.POINTER(Grid), _D3, _D3, _P, C.c_void_p] + [C.c_double] * 5 + [C.c_int, _P]
     L.orc_fluid_to_particles.argtypes = [C.POINTER(Grid), _P, C.c_double, _P, _D3, C.c_double, C.c_int, C.c_uint32,
-                                         C.c_uint32, C.c_uint32, C.POINTER(Species), C.c_long, _P]
+                                         C.c_uint32, C.c_uint32, C.POINTER(Species), C.c_long, _P, C.c_int]
     L.orc_fluid_to_particles.restype = C.c_long
     L.orc_particles_to_fluid.argtypes = [C.POINTER(Grid), _P, C.POINTER(Species), _P, _D3, C.c_double, _P]
     L.orc_particles_to_fluid.restype = C.c_long
@@ -520,14 +520,16 @@ def regime_criterion(g, E, B, ne, fluid_u=None, kappa=None, lambda_m=0.8e-6, **t
     return mask
 
 
-def fluid_to_particles(g, mask, fl, ppc, seed, sp_index, epoch, rho_bg):
-    """Convert the fluid at kinetic nodes into particles (returns Particles)."""
+def fluid_to_particles(g, mask, fl, ppc, seed, sp_index, epoch, rho_bg, quiet=False):
+    """Convert the fluid at kinetic nodes into particles (returns Particles):
+    Philox-uniform positions in the node's dual cell, or with quiet=True the
+    centres of an lx x ly x lz sub-lattice of it."""
     mask = np.ascontiguousarray(mask, dtype=np.uint8)
     cap = int(np.count_nonzero(mask)) * ppc
     out = _empty(max(cap, 1), fl.q, fl.m)
     n = lib().orc_fluid_to_particles(C.byref(g), _ptr(mask), fl.q, _ptr(fl.n), _f3(fl.u), fl.n_floor, int(ppc),
                                      int(seed) & 0xFFFFFFFF, int(sp_index), int(epoch), C.byref(out.cstruct()),
-                                     max(cap, 1), _ptr(rho_bg))
+                                     max(cap, 1), _ptr(rho_bg), int(bool(quiet)))
     out.select(np.arange(n))
     return out
 

@@ -117,7 +117,7 @@ void orc_regime_criterion(const orc_grid *g, const double *E[3], const double *B
                           double chi_thr, int dilate, unsigned char *mask);
 long orc_fluid_to_particles(const orc_grid *g, const unsigned char *mask, double q, double *n, double *u[3],
                             double n_floor, int ppc, uint32_t seed, uint32_t sp_index, uint32_t epoch,
-                            orc_species *out, long cap, double *rho_bg);
+                            orc_species *out, long cap, double *rho_bg, int quiet);
 long orc_particles_to_fluid(const orc_grid *g, const unsigned char *mask, orc_species *s, double *n,
                             double *u[3], double n_floor, unsigned char *alive);
 

@@ -133,9 +133,27 @@ static void cic_add(const orc_grid *g, double x, double y, double z, double val,
 }
 
 /* fluid -> particles; returns the number of particles written to out (cap) */
+/* quiet start: the ppc particles of a node sit on an lx x ly x lz lattice of the
+ * node's dual cell (lx >= ly >= lz, as close to cubic as ppc allows), at the
+ * centres of its sub-cells; lz is the largest divisor of ppc not above its
+ * cube root, ly the largest divisor of ppc / lz not above its square root */
+static void lattice_dims(int ppc, int l[3]) {
+    int lz = 1, ly = 1;
+    for (int d = 1; d * d * d <= ppc; ++d)
+        if (ppc % d == 0) lz = d;
+    const int r = ppc / lz;
+    for (int d = 1; d * d <= r; ++d)
+        if (r % d == 0) ly = d;
+    l[0] = r / ly;
+    l[1] = ly;
+    l[2] = lz;
+}
+
 long orc_fluid_to_particles(const orc_grid *g, const unsigned char *mask, double q, double *n, double *u[3],
                             double n_floor, int ppc, uint32_t seed, uint32_t sp_index, uint32_t epoch,
-                            orc_species *out, long cap, double *rho_bg) {
+                            orc_species *out, long cap, double *rho_bg, int quiet) {
+    int lat[3];
+    lattice_dims(ppc, lat);
     const int nn[3] = {g->nx, g->ny, g->nz};
     const double dV = g->dx * g->dy * g->dz;
     long m = 0;
@@ -153,10 +171,12 @@ long orc_fluid_to_particles(const orc_grid *g, const unsigned char *mask, double
             uint32_t r[4];
             orc_philox4x32_10(ctr, key, r);
             double pos[3];
+            const int lm[3] = {p % lat[0], (p / lat[0]) % lat[1], p / (lat[0] * lat[1])};
             for (int a = 0; a < 3; ++a) {
                 double lo = idx[a] - 0.5, hi = idx[a] + 0.5;
                 if (g->bc[a] != 0) { if (lo < 0.0) lo = 0.0; if (hi > nn[a] - 1) hi = nn[a] - 1; }
-                pos[a] = lo + (hi - lo) * orc_u01(r[a]);
+                const double frac = quiet ? (lm[a] + 0.5) / lat[a] : orc_u01(r[a]);
+                pos[a] = lo + (hi - lo) * frac;
                 if (g->bc[a] == 0) { if (pos[a] < 0.0) pos[a] += nn[a]; if (pos[a] >= nn[a]) pos[a] -= nn[a]; }
             }
             cic_add(g, pos[0], pos[1], pos[2], -q * w / dV, rho_bg);

@@ -99,7 +99,7 @@ class OracleSim:
         self.n_clamped = 0
         self.nstep = 0
         self.regime = dict(a_thr=1.0, n_thr=1.0, c_thr=0.1, chi_thr=1e-3, dilate=2, k_sigma=1.0, ppc=8,
-                           to_species=[], policy="default")
+                           to_species=[], policy="default", quiet=False)
         self.epoch = 0
         self.mask = np.zeros(self.g.shape, dtype=np.uint8)   # every node fluid before a classification
         self.rho_bg = np.zeros(self.g.shape)
@@ -128,9 +128,10 @@ class OracleSim:
         return len(self.fluids) - 1
 
     def set_regime(self, a_thr=1.0, n_thr=1.0, c_thr=0.1, chi_thr=1e-3, dilate=2, k_sigma=1.0, ppc=8,
-                   to_species=None, policy="default"):
+                   to_species=None, policy="default", quiet=False):
         self.regime = dict(a_thr=a_thr, n_thr=n_thr, c_thr=c_thr, chi_thr=chi_thr, dilate=dilate,
-                           k_sigma=k_sigma, ppc=ppc, to_species=list(to_species or []), policy=policy)
+                           k_sigma=k_sigma, ppc=ppc, to_species=list(to_species or []), policy=policy,
+                           quiet=bool(quiet))
 
     def classify(self, net=None, passes=16, mask=None):
         """Regime decision and conversions (Methodology: fluid where the flow
@@ -183,7 +184,7 @@ class OracleSim:
                 continue
             switched = (mask != 0) & (self.mask == 0)
             new = fluid_to_particles(g, switched.astype(np.uint8), fl, r["ppc"], self.seed, sid, self.epoch,
-                                     self.rho_bg)
+                                     self.rho_bg, quiet=r.get("quiet", False))
             dst = self.species[sid]
             if dst.tau is not None:
                 new.tau = qed_tau0(new.ids, self.seed, sid)

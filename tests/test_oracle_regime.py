@@ -190,3 +190,38 @@ def test_oracle_converts_only_nodes_that_switch_to_kinetic():
     m2[5, 5, 5] = 1
     o.classify(mask=m2)
     assert o.species[0].n == 2 * 9
+
+
+@pytest.mark.parametrize("ppc,lattice", [(8, (2, 2, 2)), (4, (2, 2, 1)), (27, (3, 3, 3)), (2, (2, 1, 1)),
+                                         (12, (3, 2, 2)), (1, (1, 1, 1))])
+def test_quiet_start_places_the_sub_lattice_centres(ppc, lattice):
+    """Quiet start: node c's particles sit at c - 1/2 + (m + 1/2) / l_a along each
+    axis, an l_x x l_y x l_z lattice as close to cubic as ppc allows."""
+    g = _grid()
+    fl = oracle.Fluid(-1.0, 1.0, np.zeros(g.shape), np.zeros((3,) + g.shape))
+    fl.n[3, 5, 7] = 0.4
+    mask = np.zeros(g.shape, np.uint8)
+    mask[3, 5, 7] = 1
+    sp = oracle.fluid_to_particles(g, mask, fl, ppc, 5, 0, 1, np.zeros(g.shape), quiet=True)
+    grid = np.stack(np.meshgrid(*[(np.arange(l) + 0.5) / l - 0.5 for l in lattice], indexing="ij"), -1)
+    want = grid.reshape(-1, 3) + [7, 5, 3]
+    got = np.stack([sp.x, sp.y, sp.z], -1)
+    lex = lambda a: a[np.lexsort((a[:, 2], a[:, 1], a[:, 0]))]
+    assert sp.n == ppc and np.allclose(lex(got), lex(want), rtol=0, atol=1e-14)
+
+
+@pytest.mark.parametrize("ppc", [8, 27])
+def test_quiet_start_of_a_uniform_fluid_leaves_no_residual_charge(ppc):
+    """A uniform periodic fluid converted everywhere with quiet start gives
+    particles whose CIC charge is the fluid's charge at every node, so the
+    residual background charge vanishes (random positions leave shot noise)."""
+    g = _grid()
+    fl = oracle.Fluid(-1.0, 1.0, np.full(g.shape, 0.3), np.zeros((3,) + g.shape))
+    mask = np.ones(g.shape, np.uint8)
+    rho_bg = np.zeros(g.shape)
+    oracle.fluid_to_particles(g, mask, fl, ppc, 5, 0, 1, rho_bg, quiet=True)
+    assert np.max(np.abs(rho_bg)) < 1e-13
+    fl2 = oracle.Fluid(-1.0, 1.0, np.full(g.shape, 0.3), np.zeros((3,) + g.shape))
+    rho_bg2 = np.zeros(g.shape)
+    oracle.fluid_to_particles(g, mask, fl2, ppc, 5, 0, 1, rho_bg2, quiet=False)
+    assert np.max(np.abs(rho_bg2)) > 1e-3
