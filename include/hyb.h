@@ -213,6 +213,13 @@ typedef struct {
     int ppc;                              /* macro-particles per node created from fluid */
     int to_species[HYB_MAX_FLUIDS];
     int policy;                           /* HYB_REGIME_* below */
+    int quiet;                            /* 1: quiet start -- the ppc particles of a converted node sit
+                                             at the centres of an lx x ly x lz sub-lattice of its dual
+                                             cell (lx >= ly >= lz, lz the largest divisor of ppc not
+                                             above its cube root, ly the largest divisor of ppc / lz not
+                                             above its square root), the same in every run, so that a
+                                             uniform fluid becomes particles without shot noise;
+                                             0: Philox-uniform positions */
 } hyb_regime_desc;
 /* Which decision hyb_classify takes.  DEFAULT: the classifier when a model is
  * given, else the physics criterion.  UNION: a node is kinetic when the

@@ -80,7 +80,7 @@ class hyb_phase_times_t(C.Structure):
 class hyb_regime_desc(C.Structure):
     _fields_ = [("a_thr", C.c_double), ("n_thr", C.c_double), ("c_thr", C.c_double), ("chi_thr", C.c_double),
                 ("dilate", C.c_int), ("k_sigma", C.c_double), ("ppc", C.c_int),
-                ("to_species", C.c_int * 4), ("policy", C.c_int)]
+                ("to_species", C.c_int * 4), ("policy", C.c_int), ("quiet", C.c_int)]
 
 
 HYB_REGIME_DEFAULT, HYB_REGIME_UNION, HYB_REGIME_ALL_KINETIC = 0, 1, 2

@@ -629,6 +629,7 @@ hyb_status hyb_set_regime(hyb_ctx *c, const hyb_regime_desc *d) {
     if (d->ppc < 0 || d->ppc > 64) return set_error(HYB_EINVAL, "ppc must be in 0..64");
     if (d->policy < HYB_REGIME_DEFAULT || d->policy > HYB_REGIME_ALL_KINETIC)
         return set_error(HYB_EINVAL, "policy must be one of HYB_REGIME_*");
+    if (d->quiet != 0 && d->quiet != 1) return set_error(HYB_EINVAL, "quiet must be 0 or 1");
     for (int f = 0; f < HYB_MAX_FLUIDS; ++f)
         if (d->to_species[f] >= (int)c->sp.size() ||
             (d->to_species[f] >= 0 && c->sp[d->to_species[f]].dev.kind != HYB_KIND_MASSIVE))

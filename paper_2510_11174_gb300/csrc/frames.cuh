@@ -18,7 +18,7 @@
 
 namespace hyb {
 
-__host__ __device__ inline int frame_G(int T) { return T + 3; }  // frame edge in nodes
+__host__ __device__ constexpr int frame_G(int T) { return T + 3; }  // frame edge in nodes
 
 // 2^k as FP32 for k in [-126, 127] (exact)
 __device__ __forceinline__ float pow2f(int k) { return __int_as_float((k + 127) << 23); }

@@ -33,12 +33,19 @@
 
 namespace hyb {
 
-__host__ __device__ inline int frame_F(int T) { return T + 2; }  // field frame edge
+__host__ __device__ constexpr int frame_F(int T) { return T + 2; }  // field frame edge
 
-// the current frame (3 components, 64-bit fixed point) first, then the fields
+static constexpr int PUSH_THREADS = 256;
+static constexpr int PUSH_QCAP = 64;  // per-warp queue of cell-crossing particles
+
+__host__ __device__ constexpr size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
+
+// the current frame (3 components, 64-bit fixed point), the fields, then the
+// per-warp queues (two float4 per entry)
 size_t push_smem_bytes(int T) {
     const int F = frame_F(T), G = frame_G(T);
-    return sizeof(unsigned long long) * 3 * (size_t)G * G * G + sizeof(float) * 6 * (size_t)F * F * F;
+    return align16(sizeof(unsigned long long) * 3 * (size_t)G * G * G) + align16(sizeof(float) * 6 * (size_t)F * F * F) +
+           2 * sizeof(float4) * (PUSH_THREADS / 32) * PUSH_QCAP;
 }
 
 // CIC weights of one axis for integer and half-integer staggering, relative to
@@ -62,8 +69,9 @@ __device__ __forceinline__ AxisW axis_weights(const GridDev &g, int a, float p, 
 }
 
 // trilinear interpolation as seven linear interpolations (x, then y, then z)
-__device__ __forceinline__ float interp8(const float *__restrict__ f, int F, int bx, int by, int bz, float fx,
-                                         float fy, float fz) {
+template <int F>
+__device__ __forceinline__ float interp8(const float *__restrict__ f, int bx, int by, int bz, float fx, float fy,
+                                         float fz) {
     const float *r00 = f + (bz * F + by) * F + bx;   // rows (y, z), (y + 1, z), (y, z + 1), (y + 1, z + 1)
     const float *r10 = r00 + F, *r01 = r00 + F * F, *r11 = r01 + F;
     const float a00 = fmaf(fx, r00[1] - r00[0], r00[0]);
@@ -83,17 +91,115 @@ __device__ __forceinline__ void shape3(float p, int gbase, float S[3]) {
     }
 }
 
-__global__ void __launch_bounds__(256, 3) k_push_deposit(GridDev g, const float *__restrict__ E,
-                                                      const float *__restrict__ B,
-                                                      const SpDev *__restrict__ sps, int nsp,
-                                                      float *__restrict__ jscratch, int *__restrict__ jvalid,
-                                                      int *__restrict__ status,
-                                                      const long long *__restrict__ step_dev, QedDev qd) {
+// Esirkepov deposit of a particle that stays in its cell.  Per axis the shape
+// is (1 - f, f) on the cell's two nodes, f moving from f0 to f1 = f0 + d; W_c
+// is nonzero only on the cell's lower c-face, at its 2 x 2 transverse nodes,
+// where the transverse factor is the mean of S_p S_q along the straight path:
+// with m = (f0 + f1) / 2, int f_p f_q = m_p m_q + d_p d_q / 12 = X, and the
+// other three nodes take m_q - X, m_p - X and 1 - m_p - m_q + X.
+// fac[c] = q w jfac_c 2^k; the current is fac[c] (S1 - S0)(lower node) = -fac[c] d_c.
+template <int G>
+__device__ __forceinline__ void deposit_same_cell(unsigned long long *__restrict__ sj, const float x0[3],
+                                                  const float x1[3], const int o[3], const float fac[3]) {
+    constexpr int G3 = G * G * G;
+    int lb[3];
+    float m[3], d[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float c0 = floorf(x0[a]);
+        lb[a] = (int)c0 - o[a];
+        const float f0 = x0[a] - c0, f1 = x1[a] - c0;
+        d[a] = f1 - f0;
+        m[a] = 0.5f * (f0 + f1);
+    }
+    const int base = (lb[2] * G + lb[1]) * G + lb[0];
+    constexpr int off[3] = {1, G, G * G};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        if (d[c] == 0.0f) continue;
+        const int pa = (c + 1) % 3, qa = (c + 2) % 3;
+        const float X = fmaf(d[pa] * d[qa], 1.0f / 12.0f, m[pa] * m[qa]);
+        const float v01 = m[qa] - X, v10 = m[pa] - X;
+        const float v00 = (1.0f - m[pa]) - v01;
+        const float sc = -fac[c] * d[c];
+        unsigned long long *J = sj + c * G3 + base;
+        atomicAdd(J, fix_of(sc * v00));
+        atomicAdd(J + off[pa], fix_of(sc * v10));
+        atomicAdd(J + off[qa], fix_of(sc * v01));
+        atomicAdd(J + off[pa] + off[qa], fix_of(sc * X));
+    }
+}
+
+// Esirkepov deposit on the 3-node window of each axis (a particle that
+// crossed a cell face): W_c = DS_c (S0_p S0_q + DS_p S0_q / 2 + S0_p DS_q / 2 +
+// DS_p DS_q / 3), prefix-summed along c
+template <int G>
+__device__ __forceinline__ void deposit_general(unsigned long long *__restrict__ sj, const float x0[3],
+                                                const float x1[3], const int o[3], float qw, const float jfac[3]) {
+    constexpr int G3 = G * G * G;
+    int lb[3];
+    float S0[3][3], DS[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int i0 = (int)floorf(x0[a]), i1 = (int)floorf(x1[a]);
+        const int gb = i0 < i1 ? i0 : i1;
+        lb[a] = gb - o[a];
+        float S1[3];
+        shape3(x0[a], gb, S0[a]);
+        shape3(x1[a], gb, S1);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) DS[a][k] = S1[k] - S0[a][k];
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const int pa = (c + 1) % 3, qa = (c + 2) % 3;
+        const float fac = qw * jfac[c];
+        unsigned long long *Jc = sj + c * G3;
+#pragma unroll
+        for (int bq = 0; bq < 3; ++bq) {
+            // transverse factor S0p (S0q + DSq/2) + DSp (S0q/2 + DSq/3)
+            const float caq = fmaf(0.5f, DS[qa][bq], S0[qa][bq]);
+            const float cbq = fmaf(1.0f / 3.0f, DS[qa][bq], 0.5f * S0[qa][bq]);
+#pragma unroll
+            for (int bp = 0; bp < 3; ++bp) {
+                const float cross = fmaf(DS[pa][bp], cbq, S0[pa][bp] * caq);
+                float acc = 0.0f;
+#pragma unroll
+                for (int a = 0; a < 2; ++a) {
+                    acc += DS[c][a] * cross;
+                    if (acc != 0.0f) {
+                        int l3[3];
+                        l3[c] = lb[c] + a;
+                        l3[pa] = lb[pa] + bp;
+                        l3[qa] = lb[qa] + bq;
+                        atomicAdd(&Jc[(l3[2] * G + l3[1]) * G + l3[0]], fix_of(fac * acc));
+                    }
+                }
+            }
+        }
+    }
+}
+
+// One CTA per tile: stage E, B of the tile and a one-node halo, push every
+// particle of every species, deposit its current into the tile's fixed-point
+// frame, apply the stochastic events, write it back or send it to the
+// migration buffer.  Particles that stay in their cell deposit at once;
+// particles that crossed a cell face wait in a per-warp queue and are
+// deposited 32 at a time with the full 3-node stencil, so that the long
+// stencil runs with every lane of the warp busy.
+template <int T>
+__global__ void __launch_bounds__(PUSH_THREADS, 3) k_push_deposit(GridDev g, const float *__restrict__ E,
+                                                                  const float *__restrict__ B,
+                                                                  const SpDev *__restrict__ sps, int nsp,
+                                                                  float *__restrict__ jscratch,
+                                                                  int *__restrict__ jvalid, int *__restrict__ status,
+                                                                  const long long *__restrict__ step_dev, QedDev qd) {
+    constexpr int F = frame_F(T), G = frame_G(T);
+    constexpr int F3 = F * F * F, G3 = G * G * G;
     extern __shared__ __align__(16) unsigned char smraw[];
-    const int T = g.T, F = frame_F(T), G = frame_G(T);
-    const int F3 = F * F * F, G3 = G * G * G;
     unsigned long long *sj = reinterpret_cast<unsigned long long *>(smraw);  // 3 current components, G^3 each
-    float *sf = reinterpret_cast<float *>(sj + 3 * G3);                       // 6 field components, F^3 each
+    float *sf = reinterpret_cast<float *>(smraw + align16(sizeof(unsigned long long) * 3 * G3));  // 6 x F^3
+    float4 *queue = reinterpret_cast<float4 *>(reinterpret_cast<unsigned char *>(sf) + align16(sizeof(float) * 6 * F3));
     __shared__ int s_holes;
     __shared__ int s_qwmax[32];  // per warp: largest |q w| of the tile's particles (float bits)
     __shared__ int s_kfix;       // fixed-point exponent of the tile's current frame
@@ -102,6 +208,9 @@ __global__ void __launch_bounds__(256, 3) k_push_deposit(GridDev g, const float 
     const long long step = *step_dev;
     double tal_e[NTALLY] = {0.0, 0.0, 0.0};
     int tal_n[NTALLY] = {0, 0, 0};
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float4 *qa = queue + warp * 2 * PUSH_QCAP;  // (x0, q w) of queued particles
+    float4 *qb = qa + PUSH_QCAP;                // (x1, -)
 
     const int t = blockIdx.x;
     // a tile without particles writes no frame: the reduction skips it
@@ -122,7 +231,7 @@ __global__ void __launch_bounds__(256, 3) k_push_deposit(GridDev g, const float 
             const SpDev &sp = sps[si];
             const int n = min(sp.count[t], sp.cap);
             const long long base = (long long)t * sp.cap;
-            for (int p = threadIdx.x; p < n; p += blockDim.x) {
+            for (int p = threadIdx.x; p < n; p += PUSH_THREADS) {
                 const float qp = sp.zq ? sp.q * sp.zq[base + p] : sp.q;
                 qwm = fmaxf(qwm, fabsf(qp * sp.w[base + p]));
             }
@@ -133,7 +242,7 @@ __global__ void __launch_bounds__(256, 3) k_push_deposit(GridDev g, const float 
     const int o[3] = {tx * T - 1, ty * T - 1, tz * T - 1};
     const long long N = g.N;
 
-    for (int l = threadIdx.x; l < F3; l += blockDim.x) {
+    for (int l = threadIdx.x; l < F3; l += PUSH_THREADS) {
         const int lx = l % F, ly = (l / F) % F, lz = l / (F * F);
         int gi[3] = {o[0] + lx, o[1] + ly, o[2] + lz};
         bool in = true;
@@ -152,7 +261,7 @@ __global__ void __launch_bounds__(256, 3) k_push_deposit(GridDev g, const float 
             sf[(3 + q) * F3 + l] = in ? B[q * N + c] : 0.0f;
         }
     }
-    for (int l = threadIdx.x; l < 3 * G3; l += blockDim.x) sj[l] = 0ULL;
+    for (int l = threadIdx.x; l < 3 * G3; l += PUSH_THREADS) sj[l] = 0ULL;
     if (threadIdx.x == 0) {
         s_holes = 0;
         for (int k = 0; k < NTALLY; ++k) {
@@ -183,15 +292,19 @@ __global__ void __launch_bounds__(256, 3) k_push_deposit(GridDev g, const float 
         const long long base = (long long)t * sp.cap;
         // times q_p below; photons (m = 0, q = 0) get no Lorentz force
         const float qm_half = sp.kind == 1 ? 0.0f : 0.5f * dt / sp.m;
-        for (int p0 = 0; p0 < n; p0 += blockDim.x) {
+        int qn = 0;  // entries in this warp's queue (warp-uniform)
+        for (int p0 = 0; p0 < n; p0 += PUSH_THREADS) {
             const int p = p0 + threadIdx.x;
-            if (p < n) {
-                const long long s = base + p;
-                const float x0[3] = {sp.x[s], sp.y[s], sp.z[s]};
-                float u[3] = {sp.ux[s], sp.uy[s], sp.uz[s]};
-                const float wgt = sp.w[s];
-                const float q = sp.zq ? sp.q * sp.zq[s] : sp.q;
-
+            bool act = p < n;
+            const long long s = base + p;
+            float x0[3] = {0.0f, 0.0f, 0.0f}, x1[3] = {0.0f, 0.0f, 0.0f}, u[3] = {0.0f, 0.0f, 0.0f};
+            float e[3] = {0.0f, 0.0f, 0.0f}, b[3] = {0.0f, 0.0f, 0.0f};
+            float wgt = 0.0f, q = 0.0f;
+            if (act) {
+                x0[0] = sp.x[s]; x0[1] = sp.y[s]; x0[2] = sp.z[s];
+                u[0] = sp.ux[s]; u[1] = sp.uy[s]; u[2] = sp.uz[s];
+                wgt = sp.w[s];
+                q = sp.zq ? sp.q * sp.zq[s] : sp.q;
                 // every shared-memory index below derives from a cell inside this
                 // tile; anything else is flagged and left untouched
                 bool inside = true;
@@ -204,20 +317,20 @@ __global__ void __launch_bounds__(256, 3) k_push_deposit(GridDev g, const float 
                 }
                 if (!inside) {
                     atomicOr(status, ST_BADPOS);
-                    continue;
+                    act = false;
                 }
-
+            }
+            if (act) {
                 // ---- gather E^n, B^n at x^n
                 const AxisW ax = axis_weights(g, 0, x0[0], o[0]);
                 const AxisW ay = axis_weights(g, 1, x0[1], o[1]);
                 const AxisW az = axis_weights(g, 2, x0[2], o[2]);
-                float e[3], b[3];
-                e[0] = interp8(sEx, F, ax.lh, ay.li, az.li, ax.fh, ay.fi, az.fi);
-                e[1] = interp8(sEy, F, ax.li, ay.lh, az.li, ax.fi, ay.fh, az.fi);
-                e[2] = interp8(sEz, F, ax.li, ay.li, az.lh, ax.fi, ay.fi, az.fh);
-                b[0] = interp8(sBx, F, ax.li, ay.lh, az.lh, ax.fi, ay.fh, az.fh);
-                b[1] = interp8(sBy, F, ax.lh, ay.li, az.lh, ax.fh, ay.fi, az.fh);
-                b[2] = interp8(sBz, F, ax.lh, ay.lh, az.li, ax.fh, ay.fh, az.fi);
+                e[0] = interp8<F>(sEx, ax.lh, ay.li, az.li, ax.fh, ay.fi, az.fi);
+                e[1] = interp8<F>(sEy, ax.li, ay.lh, az.li, ax.fi, ay.fh, az.fi);
+                e[2] = interp8<F>(sEz, ax.li, ay.li, az.lh, ax.fi, ay.fi, az.fh);
+                b[0] = interp8<F>(sBx, ax.li, ay.lh, az.lh, ax.fi, ay.fh, az.fh);
+                b[1] = interp8<F>(sBy, ax.lh, ay.li, az.lh, ax.fh, ay.fi, az.fh);
+                b[2] = interp8<F>(sBz, ax.lh, ay.lh, az.li, ax.fh, ay.fh, az.fi);
 
                 // ---- Boris
                 const float h = q * qm_half;
@@ -241,7 +354,6 @@ __global__ void __launch_bounds__(256, 3) k_push_deposit(GridDev g, const float 
                 // ---- move (photons at c: velocity k / |k|), reflect at absorbing walls
                 const float gam = sp.kind == 1 ? fmaxf(sqrtf(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]), 1e-30f)
                                                : sqrtf(1.0f + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-                float x1[3];
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
                     x1[a] = x0[a] + u[a] * (dt / gam) * inv_d[a];
@@ -251,108 +363,43 @@ __global__ void __launch_bounds__(256, 3) k_push_deposit(GridDev g, const float 
                         else if (x1[a] > L) { x1[a] = 2.0f * L - x1[a]; u[a] = -u[a]; }
                     }
                 }
-
                 bool finite = true;
 #pragma unroll
                 for (int a = 0; a < 3; ++a) finite = finite && isfinite(x1[a]) && fabsf(x1[a] - x0[a]) < 1.0f;
                 if (!finite) {
                     atomicOr(status, ST_BADPOS);
-                    continue;
+                    act = false;
                 }
+            }
 
-                // ---- Esirkepov deposit into the shared frame
-                bool same_cell = true;
+            // ---- Esirkepov deposit into the shared frame: particles that stay
+            // in their cell now, the others through the warp's queue
+            bool same_cell = true;
 #pragma unroll
-                for (int a = 0; a < 3; ++a) same_cell = same_cell && floorf(x0[a]) == floorf(x1[a]);
-                if (q != 0.0f && same_cell) {
-                    // no cell boundary crossed: per axis S0 = (1 - f0, f0), DS = (-d, d);
-                    // W_c is nonzero only at the cell's lower c-face, at the 2 x 2
-                    // transverse nodes (the general form below with its zero terms dropped)
-                    int lb[3];
-                    float s0[3][2], ds[3][2], ca[3][2], cb[3][2];
-#pragma unroll
-                    for (int a = 0; a < 3; ++a) {
-                        const float c0 = floorf(x0[a]);
-                        lb[a] = (int)c0 - o[a];
-                        float S0f[3], S1f[3];
-                        shape3(x0[a], (int)c0, S0f);
-                        shape3(x1[a], (int)c0, S1f);
-#pragma unroll
-                        for (int k = 0; k < 2; ++k) {
-                            s0[a][k] = S0f[k];
-                            ds[a][k] = S1f[k] - S0f[k];
-                            // the transverse factor S0p S0q + DSp S0q / 2 + S0p DSq / 2 + DSp DSq / 3
-                            // = S0p (S0q + DSq / 2) + DSp (S0q / 2 + DSq / 3)
-                            ca[a][k] = s0[a][k] + 0.5f * ds[a][k];
-                            cb[a][k] = 0.5f * s0[a][k] + ds[a][k] * (1.0f / 3.0f);
-                        }
-                    }
-                    const float qw = q * wgt;
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        const int pa = (c + 1) % 3, qa = (c + 2) % 3;
-                        const float fac = qw * jfac[c];
-                        unsigned long long *Jc = sj + c * G3;
-#pragma unroll
-                        for (int bq = 0; bq < 2; ++bq)
-#pragma unroll
-                            for (int bp = 0; bp < 2; ++bp) {
-                                const float cross = fmaf(ds[pa][bp], cb[qa][bq], s0[pa][bp] * ca[qa][bq]);
-                                const float acc = ds[c][0] * cross;
-                                if (acc != 0.0f) {
-                                    int l3[3];
-                                    l3[c] = lb[c];
-                                    l3[pa] = lb[pa] + bp;
-                                    l3[qa] = lb[qa] + bq;
-                                    atomicAdd(&Jc[(l3[2] * G + l3[1]) * G + l3[0]], fix_of(fac * acc));
-                                }
-                            }
-                    }
-                } else if (q != 0.0f) {
-                    int lb[3];
-                    float S0[3][3], DS[3][3];
-#pragma unroll
-                    for (int a = 0; a < 3; ++a) {
-                        const int i0 = (int)floorf(x0[a]), i1 = (int)floorf(x1[a]);
-                        const int gb = i0 < i1 ? i0 : i1;
-                        lb[a] = gb - o[a];
-                        float S1[3];
-                        shape3(x0[a], gb, S0[a]);
-                        shape3(x1[a], gb, S1);
-#pragma unroll
-                        for (int k = 0; k < 3; ++k) DS[a][k] = S1[k] - S0[a][k];
-                    }
-                    const float qw = q * wgt;
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        const int pa = (c + 1) % 3, qa = (c + 2) % 3;
-                        const float fac = qw * jfac[c];
-                        unsigned long long *Jc = sj + c * G3;
-#pragma unroll
-                        for (int bq = 0; bq < 3; ++bq) {
-                            // transverse factor S0p (S0q + DSq/2) + DSp (S0q/2 + DSq/3)
-                            const float caq = fmaf(0.5f, DS[qa][bq], S0[qa][bq]);
-                            const float cbq = fmaf(1.0f / 3.0f, DS[qa][bq], 0.5f * S0[qa][bq]);
-#pragma unroll
-                            for (int bp = 0; bp < 3; ++bp) {
-                                const float cross = fmaf(DS[pa][bp], cbq, S0[pa][bp] * caq);
-                                float acc = 0.0f;
-#pragma unroll
-                                for (int a = 0; a < 2; ++a) {
-                                    acc += DS[c][a] * cross;
-                                    if (acc != 0.0f) {
-                                        int l3[3];
-                                        l3[c] = lb[c] + a;
-                                        l3[pa] = lb[pa] + bp;
-                                        l3[qa] = lb[qa] + bq;
-                                        atomicAdd(&Jc[(l3[2] * G + l3[1]) * G + l3[0]], fix_of(fac * acc));
-                                    }
-                                }
-                            }
-                        }
-                    }
-                }
+            for (int a = 0; a < 3; ++a) same_cell = same_cell && floorf(x0[a]) == floorf(x1[a]);
+            const bool dep = act && q != 0.0f;
+            if (dep && same_cell) {
+                const float qw = q * wgt;
+                const float fac[3] = {qw * jfac[0], qw * jfac[1], qw * jfac[2]};
+                deposit_same_cell<G>(sj, x0, x1, o, fac);
+            }
+            const unsigned cross = __ballot_sync(0xffffffffu, dep && !same_cell);
+            if (dep && !same_cell) {
+                const int pos = qn + __popc(cross & ((1u << lane) - 1u));
+                qa[pos] = make_float4(x0[0], x0[1], x0[2], q * wgt);
+                qb[pos] = make_float4(x1[0], x1[1], x1[2], 0.0f);
+            }
+            qn += __popc(cross);
+            __syncwarp();
+            if (qn >= 32) {
+                const float4 A = qa[qn - 32 + lane], Bq = qb[qn - 32 + lane];
+                const float y0[3] = {A.x, A.y, A.z}, y1[3] = {Bq.x, Bq.y, Bq.z};
+                deposit_general<G>(sj, y0, y1, o, A.w, jfac);
+                qn -= 32;
+                __syncwarp();
+            }
 
+            if (act) {
                 // ---- periodic image, tile membership, write back or migrate
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
@@ -475,6 +522,13 @@ __global__ void __launch_bounds__(256, 3) k_push_deposit(GridDev g, const float 
                 }
             }
         }
+        // the warp's queue holds fewer than 32 crossing particles: deposit them
+        if (lane < qn) {
+            const float4 A = qa[lane], Bq = qb[lane];
+            const float y0[3] = {A.x, A.y, A.z}, y1[3] = {Bq.x, Bq.y, Bq.z};
+            deposit_general<G>(sj, y0, y1, o, A.w, jfac);
+        }
+        __syncwarp();
         // per-tile tallies: warp sums, then shared accumulators, then one add per tile
 #pragma unroll
         for (int k = 0; k < NTALLY; ++k) {
@@ -510,9 +564,10 @@ __global__ void __launch_bounds__(256, 3) k_push_deposit(GridDev g, const float 
 
     float *dst = jscratch + (long long)t * 3 * G3;
     const float inv_scale = pow2f(-s_kfix);
-    for (int l = threadIdx.x; l < 3 * G3; l += blockDim.x) dst[l] = fix_to_float(sj[l], inv_scale);
+    for (int l = threadIdx.x; l < 3 * G3; l += PUSH_THREADS) dst[l] = fix_to_float(sj[l], inv_scale);
     if (threadIdx.x == 0) jvalid[t] = 1;
 }
+
 
 // For every node: J = sum of the tile frames that cover it, in a fixed order.
 __global__ void k_j_reduce(GridDev g, const float *__restrict__ jscratch, const int *__restrict__ jvalid,
@@ -662,12 +717,19 @@ void launch_push_deposit(const GridDev &g, const float *E, const float *B, const
                          const QedDev &qd, float *jscratch, int *jvalid, int *status, const long long *step_dev,
                          cudaStream_t st) {
     const size_t smem = push_smem_bytes(g.T);
-    static size_t smem_set = 0;  // the opt-in size set so far (the largest tile's)
-    if (smem > smem_set && smem > 48 * 1024) {
-        cudaFuncSetAttribute(k_push_deposit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        smem_set = smem;
+    if (g.T == 8) {
+        static bool set8 = false;  // opt in to more than 48 KB of dynamic shared memory once
+        if (!set8) {
+            cudaFuncSetAttribute(k_push_deposit<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)push_smem_bytes(8));
+            set8 = true;
+        }
+        k_push_deposit<8><<<g.ntiles, PUSH_THREADS, smem, st>>>(g, E, B, sps_dev, nsp, jscratch, jvalid, status,
+                                                                step_dev, qd);
+    } else {
+        k_push_deposit<4><<<g.ntiles, PUSH_THREADS, smem, st>>>(g, E, B, sps_dev, nsp, jscratch, jvalid, status,
+                                                                step_dev, qd);
     }
-    k_push_deposit<<<g.ntiles, 256, smem, st>>>(g, E, B, sps_dev, nsp, jscratch, jvalid, status, step_dev, qd);
 }
 
 void launch_j_reduce(const GridDev &g, const float *jscratch, const int *jvalid, float *J, cudaStream_t st) {

@@ -217,10 +217,26 @@ __global__ void k_dilate(GridDev g, int a, int r, const uint8_t *__restrict__ in
 // walks the tile's nodes.  rho_bg takes (removed fluid charge) - (CIC charge of
 // the new particles): both go into the tile's fixed-point frame, which
 // k_rho_gather adds to rho_bg in a fixed order.
+// sub-lattice of a quiet start: lx >= ly >= lz with lx ly lz = ppc, lz the
+// largest divisor of ppc with lz^3 <= ppc, ly the largest divisor of ppc / lz
+// with ly^2 <= ppc / lz
+__host__ __device__ inline void quiet_lattice(int ppc, int l[3]) {
+    int lz = 1, ly = 1;
+    for (int d = 1; d * d * d <= ppc; ++d)
+        if (ppc % d == 0) lz = d;
+    const int r = ppc / lz;
+    for (int d = 1; d * d <= r; ++d)
+        if (r % d == 0) ly = d;
+    l[0] = r / ly;
+    l[1] = ly;
+    l[2] = lz;
+}
+
 __global__ void __launch_bounds__(256) k_fluid_to_particles(GridDev g, const uint8_t *__restrict__ mask,
                                                              const uint8_t *__restrict__ prev, FluidDev f, SpDev dst,
-                                                             int ppc, uint32_t epoch, float *__restrict__ scratch,
-                                                             int *__restrict__ valid, int *__restrict__ status) {
+                                                             int ppc, int quiet, uint32_t epoch,
+                                                             float *__restrict__ scratch, int *__restrict__ valid,
+                                                             int *__restrict__ status) {
     extern __shared__ __align__(16) unsigned char smraw[];
     unsigned long long *fr = reinterpret_cast<unsigned long long *>(smraw);
     __shared__ int s_max[32];
@@ -259,6 +275,8 @@ __global__ void __launch_bounds__(256) k_fluid_to_particles(GridDev g, const uin
     const int k = fix_exponent(2.0 * (double)T3 * (double)block_max_read(s_max));
     const float sc = pow2f(k);
     const float dV = g.d[0] * g.d[1] * g.d[2];
+    int lat[3];
+    quiet_lattice(ppc, lat);
     for (int l = threadIdx.x; l < T3; l += blockDim.x) {
         int idx[3];
         const long long c = node_of(l, idx);
@@ -272,6 +290,7 @@ __global__ void __launch_bounds__(256) k_fluid_to_particles(GridDev g, const uin
         const float u[3] = {f.ux[c], f.uy[c], f.uz[c]};
         for (int p = 0; p < ppc; ++p) {
             const u32x4 r = philox4x32_10((uint32_t)c, epoch, (uint32_t)p, 6u, g.seed, dst.sp_index);
+            const int lm[3] = {p % lat[0], (p / lat[0]) % lat[1], p / (lat[0] * lat[1])};
             float pos[3], upos[3];
             for (int a = 0; a < 3; ++a) {
                 float lo = (float)idx[a] - 0.5f, hi = (float)idx[a] + 0.5f;
@@ -279,7 +298,8 @@ __global__ void __launch_bounds__(256) k_fluid_to_particles(GridDev g, const uin
                     lo = fmaxf(lo, 0.0f);
                     hi = fminf(hi, (float)(g.n[a] - 1));
                 }
-                upos[a] = lo + (hi - lo) * u01f(r.v[a]);
+                const float frac = quiet ? ((float)lm[a] + 0.5f) / (float)lat[a] : u01f(r.v[a]);
+                upos[a] = lo + (hi - lo) * frac;
                 pos[a] = upos[a];
                 if (g.bc[a] == 0) {
                     if (pos[a] < 0.0f) pos[a] += (float)g.n[a];
@@ -479,8 +499,8 @@ hyb_status regime_update(hyb_ctx *c, const float *pm, const float *ps) {
         // the tiles are compact between steps: new particles go straight into them
         const size_t sm1 = sizeof(unsigned long long) * (size_t)fG3;
         k_fluid_to_particles<<<g.ntiles, 256, sm1, st>>>(g, mask, c->mask_prev, c->fluids[f], dst,
-                                                         rd.ppc > 0 ? rd.ppc : 8, c->epoch, c->jscratch, c->jvalid,
-                                                         c->status);
+                                                         rd.ppc > 0 ? rd.ppc : 8, rd.quiet ? 1 : 0, c->epoch,
+                                                         c->jscratch, c->jvalid, c->status);
         k_rho_gather<<<node_grid(g), node_block(g), 0, st>>>(g, c->jscratch, c->jvalid, c->rho_bg);
         k_clamp_counts<<<(g.ntiles + 255) / 256, 256, 0, st>>>(g.ntiles, dst);
         k_particles_to_fluid<<<g.ntiles, 256, 4 * sm1, st>>>(g, mask, dst, c->jscratch, c->jvalid, c->status);

@@ -187,12 +187,14 @@ class Simulation:
                 "all_kinetic": _abi.HYB_REGIME_ALL_KINETIC}
 
     def set_regime(self, a_thr=1.0, n_thr=1.0, c_thr=0.1, chi_thr=1e-3, dilate=2, k_sigma=1.0, ppc=8,
-                   to_species=None, policy="default"):
+                   to_species=None, policy="default", quiet=False):
         """Thresholds and conversion targets of hyb_classify; policy is
         "default" (classifier if given, else physics criterion), "union"
-        (classifier or criterion) or "all_kinetic" (full PIC)."""
+        (classifier or criterion) or "all_kinetic" (full PIC); quiet=True
+        places converted particles on a sub-lattice of the node's dual cell."""
         d = _abi.hyb_regime_desc()
         d.policy = self.POLICIES[policy]
+        d.quiet = int(bool(quiet))
         d.a_thr, d.n_thr, d.c_thr, d.chi_thr = a_thr, n_thr, c_thr, chi_thr
         d.dilate, d.k_sigma, d.ppc = dilate, k_sigma, ppc
         ts = list(to_species or [])

@@ -96,7 +96,7 @@ def _decide_only(orc, net, passes):
     return mask
 
 
-def _fields_after(P, inp, policy, seed, steps=40):
+def _fields_after(P, inp, policy, seed, steps=40, quiet=False):
     g = inp["grid"]
     sim = P.Simulation(g["nx"], g["ny"], g["nz"], g["dx"], cfl_frac=g["cfl_frac"], bc=g["bc"], laser=inp["laser"],
                        seed=seed)
@@ -104,7 +104,7 @@ def _fields_after(P, inp, policy, seed, steps=40):
         sim.load_species(**sp)
     for fl in inp["fluids"]:
         sim.load_fluid(**fl)
-    sim.set_regime(dilate=1, ppc=inp["ppc"], to_species=[0, 1], policy=policy)
+    sim.set_regime(dilate=1, ppc=inp["ppc"], to_species=[0, 1], policy=policy, quiet=quiet)
     sim.classify()
     assert sim.diagnostics()["status"] == 0
     frac = sim.get_regime()[0].mean()
@@ -136,3 +136,21 @@ def test_hybrid_field_error_against_full_pic():
     assert 0.0 < frac < 1.0
     assert 1e-3 < floor < 5e-2
     assert err <= 3.0 * floor, (err, floor)
+
+
+@pytest.mark.parametrize("a0", [0.5, 110.0])
+def test_hybrid_field_error_against_quiet_start_full_pic(a0):
+    """With quiet start (macro-particles at fixed sub-lattice positions in both
+    runs) the full-PIC reference has no shot noise: two full-PIC runs with
+    different seeds are identical, and the hybrid's field error against full
+    PIC is what the regime decision itself costs."""
+    P = require_gpu()
+    inp = _workload(nx=64, ny=32, nz=32, ppc=8, a0=a0)
+    full_a, _ = _fields_after(P, inp, "all_kinetic", seed=1, quiet=True)
+    full_b, _ = _fields_after(P, inp, "all_kinetic", seed=2, quiet=True)
+    hyb, frac = _fields_after(P, inp, "default", seed=1, quiet=True)
+    err = rel_l2(hyb, full_a)
+    print("a0 %.1f: kinetic fraction %.3f; field rel-L2 vs quiet full PIC %.3e" % (a0, frac, err))
+    assert np.array_equal(full_a, full_b)
+    assert 0.0 < frac < 1.0
+    assert err <= 1e-3, (a0, err)

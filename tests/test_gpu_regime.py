@@ -44,11 +44,12 @@ def _gauss(g, E, species_list, fluids, rho_bg):
     return oracle.div_e(g, E.astype(np.float64)) - rho - rho_bg.astype(np.float64)
 
 
-def test_physics_criterion_and_conversions_match_oracle():
+@pytest.mark.parametrize("quiet", [False, True])
+def test_physics_criterion_and_conversions_match_oracle(quiet):
     inp, fl = _setup()
     sim, _ = make_pair(inp, with_oracle=False)
     sim.load_fluid(**fl)
-    sim.set_regime(dilate=1, ppc=4, to_species=[0])
+    sim.set_regime(dilate=1, ppc=4, to_species=[0], quiet=quiet)
     g = oracle.Grid.make(NX, NY, NZ, DX, DX, DX, 0.1)
     sp0 = sim.get_species(0)
     before = _gauss(g, inp["E"], [oracle.Particles(-1, 1, sp0["x"], sp0["y"], sp0["z"], sp0["ux"], sp0["uy"], sp0["uz"],
@@ -65,7 +66,7 @@ def test_physics_criterion_and_conversions_match_oracle():
     # conversions with the GPU's mask in the oracle
     ofl = oracle.Fluid(-1.0, 1.0, fl["n"], np.stack([fl["ux"], fl["uy"], fl["uz"]]))
     orho = np.zeros(g.shape)
-    new = oracle.fluid_to_particles(g, mask, ofl, 4, 1, 0, 0, orho)
+    new = oracle.fluid_to_particles(g, mask, ofl, 4, 1, 0, 0, orho, quiet=quiet)
     osp = oracle.Particles(-1, 1, sp0["x"], sp0["y"], sp0["z"], sp0["ux"], sp0["uy"], sp0["uz"], sp0["w"],
                            ids=sp0["ids"])
     osp.append(new)
