@@ -150,13 +150,14 @@ def train_run(weights, x, y, steps, dropout, seed, energy_weight, lr=1e-3, beta1
     forward/backward of train_grads with the dropout masks of pass = step
     index (0, 1, ...), then Adam on FP64 master weights (the weights the
     network uses are those masters rounded to BF16 inside train_grads).
-    Returns the final [(W, b)] as FP64 tensors and the per-step losses."""
+    Returns the final [(W, b)] as FP64 tensors, the per-step losses, the
+    per-step gradients and the [(W, b)] after every step."""
     net = OracleCNN(weights, dropout=dropout, seed=seed, mean=mean, std=std)
     mw = [torch.zeros_like(w) for w in net.W]
     vw = [torch.zeros_like(w) for w in net.W]
     mb = [torch.zeros_like(b) for b in net.b]
     vb = [torch.zeros_like(b) for b in net.b]
-    losses, grads = [], []
+    losses, grads, history = [], [], []
     for t in range(steps):
         out = train_grads(net, x, y, pass_index=t, energy_weight=energy_weight)
         losses.append(out["loss"])
@@ -165,4 +166,5 @@ def train_run(weights, x, y, steps, dropout, seed, energy_weight, lr=1e-3, beta1
             gw, gb = out["grads"][l]
             net.W[l], mw[l], vw[l] = adam_update(net.W[l], gw, mw[l], vw[l], t + 1, lr, beta1, beta2, eps)
             net.b[l], mb[l], vb[l] = adam_update(net.b[l], gb, mb[l], vb[l], t + 1, lr, beta1, beta2, eps)
-    return [(net.W[l], net.b[l]) for l in range(4)], losses, grads
+        history.append([(net.W[l].clone(), net.b[l].clone()) for l in range(4)])
+    return [(net.W[l], net.b[l]) for l in range(4)], losses, grads, history

@@ -61,11 +61,12 @@ def test_training_lowers_the_loss():
 
 def test_three_adam_steps_match_oracle():
     """Three training steps (forward, backward, Adam) on the GPU against the
-    oracle's own three steps from the same weights and data.  Where the
-    gradient of a weight is well above the gradient parity at every step, the
-    Adam update must agree to 1e-2 relative; elsewhere the update of a weight
-    with a near-zero gradient may flip sign (Adam normalises by |g|), which
-    bounds the layer-wide difference."""
+    oracle's own three steps from the same weights and data, update by update.
+    Adam normalises by |g|: where a weight's gradient is well above the
+    gradient parity at every step so far, each step's update must agree with
+    the oracle's (first step: -lr sign(g) exactly); a weight whose gradient
+    is near zero may take the opposite sign, which only the layer-wide bound
+    covers."""
     P = require_gpu()
     import torch
     from oracle.classifier import train_run
@@ -73,18 +74,25 @@ def test_three_adam_steps_match_oracle():
     m, w0 = seeded_classifier(P, 21, dropout=0.2, mc_passes=1, energy_weight=0.1, lr=lr)
     x, y = _case(seed=2)
     xt, yt = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
+    gpu_hist = []
     for _ in range(3):
         m.train_step(xt, yt)
-    ref, losses, grads = train_run(w0, x, y, 3, dropout=0.2, seed=21, energy_weight=0.1, lr=lr)
+        gpu_hist.append([tuple(a.astype(np.float64) for a in m.get_layer(l)) for l in range(4)])
+    ref, losses, grads, hist = train_run(w0, x, y, 3, dropout=0.2, seed=21, energy_weight=0.1, lr=lr)
     for l in range(4):
-        for k, (g_now, r_now) in enumerate(zip(m.get_layer(l), ref[l])):
-            d_gpu = g_now.astype(np.float64) - w0[l][k]
-            d_orc = r_now.numpy() - w0[l][k]
-            gs = np.stack([grads[t][l][k].numpy() for t in range(3)])
-            rms = np.sqrt((gs ** 2).mean(axis=tuple(range(1, gs.ndim)), keepdims=True))
-            strong = np.all(np.abs(gs) >= 0.3 * rms, axis=0)
-            assert strong.sum() >= 0.2 * strong.size or strong.size < 4, (l, k, strong.mean())
-            err = np.abs(d_gpu - d_orc)[strong]
-            assert np.all(err <= 1e-2 * np.abs(d_orc[strong]) + 1e-7), (l, k, err.max())
-            assert np.all(np.abs(d_gpu) <= 3 * lr * 1.001 + 1e-7)
-            assert rel_l2(d_gpu, d_orc) <= 0.1, (l, k, rel_l2(d_gpu, d_orc))
+        for k in range(2):
+            prev_g, prev_o = w0[l][k].astype(np.float64), w0[l][k].astype(np.float64)
+            strong = np.ones(w0[l][k].shape, bool)
+            for t in range(3):
+                cur_g, cur_o = gpu_hist[t][l][k], hist[t][l][k].numpy()
+                d_gpu, d_orc = cur_g - prev_g, cur_o - prev_o
+                g = grads[t][l][k].numpy()
+                strong &= np.abs(g) >= 0.3 * np.sqrt(np.mean(g ** 2))
+                if strong.sum() >= 4:
+                    rel = np.abs(d_gpu - d_orc)[strong] / np.abs(d_orc[strong])
+                    assert np.median(rel) <= 1e-3 and np.quantile(rel, 0.99) <= 1e-2, \
+                        (l, k, t, np.median(rel), np.quantile(rel, 0.99))
+                # the first steps' bias-corrected moments keep |m_hat| / sqrt(v_hat) near 1
+                assert np.all(np.abs(d_gpu) <= 1.2 * lr)
+                assert rel_l2(d_gpu, d_orc) <= 0.1, (l, k, t, rel_l2(d_gpu, d_orc))
+                prev_g, prev_o = cur_g, cur_o
