@@ -130,7 +130,7 @@ M_C = 12.0 * M_P
 
 
 def carbon_slab(n=128, cells_per_lambda=20, ppc=16, ne_max=10.0, plateau_lambda=2.0, edge_lambda=0.5,
-                a0=100.0, tau_fs=30.0, w0_lambda=2.0, seed=2, caps=(163840, 12288, 32768, 8192)):
+                a0=100.0, tau_fs=30.0, w0_lambda=2.0, seed=2, caps=(163840, 12288, 32768, 8192), ny=None, nz=None):
     """Full PIC with ionization and QED (defaults: 128^3, lambda/20).  Atom
     density n_a(x) = (ne_max / 6) on a plateau of `plateau_lambda` centred in
     x, with Gaussian edges of width `edge_lambda` cut at 3 sigma; `ppc` atoms
@@ -139,8 +139,12 @@ def carbon_slab(n=128, cells_per_lambda=20, ppc=16, ne_max=10.0, plateau_lambda=
     0), 2 photons (pairs into 0 and 3), 3 positrons (emit into 2).  `caps`
     are their initial slots per 8^3 tile: the electron tiles hold 6 electrons
     per atom slot with room for the pulse's snowplow (a front ionizes up to
-    one level per ion and step, faster than the tiles can grow)."""
+    one level per ion and step, faster than the tiles can grow).  ny, nz
+    (default n) give a transverse cross-section of the same slab and pulse
+    axis (the pulse stays centred)."""
     dx = 2.0 * math.pi / cells_per_lambda
+    ny = n if ny is None else ny
+    nz = n if nz is None else nz
     rng = np.random.default_rng(seed)
     c0 = 0.5 * n
     half = 0.5 * plateau_lambda * cells_per_lambda
@@ -152,11 +156,11 @@ def carbon_slab(n=128, cells_per_lambda=20, ppc=16, ne_max=10.0, plateau_lambda=
         d = np.maximum(np.abs(x - c0) - half, 0.0)
         return (ne_max / 6.0) * np.exp(-0.5 * (d / sig) ** 2)
 
-    cells = (hi - lo) * n * n
+    cells = (hi - lo) * ny * nz
     m = cells * ppc
     x = rng.uniform(lo, hi, m).astype(np.float32)
-    y = rng.uniform(0, n - 1, m).astype(np.float32)
-    z = rng.uniform(0, n - 1, m).astype(np.float32)
+    y = rng.uniform(0, ny - 1, m).astype(np.float32)
+    z = rng.uniform(0, nz - 1, m).astype(np.float32)
     w = (profile(x.astype(np.float64)) * dx ** 3 / ppc).astype(np.float32)
     zero = np.zeros(m, np.float32)
     ions = dict(q=1.0, m=M_C, x=x, y=y, z=z, ux=zero, uy=zero.copy(), uz=zero.copy(), w=w, zq=zero.copy(),
@@ -167,8 +171,8 @@ def carbon_slab(n=128, cells_per_lambda=20, ppc=16, ne_max=10.0, plateau_lambda=
     positrons = dict(q=1.0, m=1.0, qed=dict(photon_species=2, eps_min=2.0), tile_capacity=caps[3], **empty)
     tau = tau_fs * OMEGA0_PER_FS
     laser = dict(a0=a0, tau_fwhm=tau, w0_spot=w0_lambda * 2.0 * math.pi, t_peak=1.5 * tau,
-                 y_c=0.5 * (n - 1), z_c=0.5 * (n - 1), x_src=4, pol=1)
-    return dict(grid=dict(nx=n, ny=n, nz=n, dx=dx, cfl_frac=0.95, bc=(1, 1, 1)), laser=laser,
+                 y_c=0.5 * (ny - 1), z_c=0.5 * (nz - 1), x_src=4, pol=1)
+    return dict(grid=dict(nx=n, ny=ny, nz=nz, dx=dx, cfl_frac=0.95, bc=(1, 1, 1)), laser=laser,
                 species=[electrons, ions, photons, positrons])
 
 
