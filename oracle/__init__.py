@@ -54,7 +54,8 @@ class Species(C.Structure):
     _fields_ = [("q", C.c_double), ("m", C.c_double), ("n", C.c_long),
                 ("x", C.c_void_p), ("y", C.c_void_p), ("z", C.c_void_p),
                 ("ux", C.c_void_p), ("uy", C.c_void_p), ("uz", C.c_void_p),
-                ("w", C.c_void_p), ("zq", C.c_void_p), ("id", C.c_void_p), ("eb", C.c_void_p)]
+                ("w", C.c_void_p), ("zq", C.c_void_p), ("id", C.c_void_p), ("eb", C.c_void_p),
+                ("pusher", C.c_int)]
 
 
 _P = C.c_void_p
@@ -69,6 +70,8 @@ def _declare(L):
     L.orc_fdtd_e.argtypes = [C.POINTER(Grid), _D3, _D3, _D3]
     L.orc_gather.argtypes = [C.POINTER(Grid), _D3, _D3, C.c_double, C.c_double, C.c_double, _P, _P]
     L.orc_boris.argtypes = [C.c_double, _P, _P, _P]
+    L.orc_vay.argtypes = [C.c_double, _P, _P, _P]
+    L.orc_higuera_cary.argtypes = [C.c_double, _P, _P, _P]
     L.orc_esirkepov.argtypes = [C.POINTER(Grid), C.c_double] + [C.c_double] * 6 + [_D3]
     L.orc_push_deposit.argtypes = [C.POINTER(Grid), _D3, _D3, _D3, C.POINTER(Species)]
     L.orc_energy_fields.argtypes = [C.POINTER(Grid), _D3, _D3, _P]
@@ -196,8 +199,11 @@ class Particles:
 
     FIELDS = ("x", "y", "z", "ux", "uy", "uz", "w")
 
-    def __init__(self, q, m, x, y, z, ux, uy, uz, w, zq=None, ids=None, tau=None):
+    PUSHERS = {"boris": 0, "vay": 1, "higuera_cary": 2}
+
+    def __init__(self, q, m, x, y, z, ux, uy, uz, w, zq=None, ids=None, tau=None, pusher="boris"):
         self.q, self.m = float(q), float(m)
+        self.pusher = self.PUSHERS[pusher]
         for name, v in zip(self.FIELDS, (x, y, z, ux, uy, uz, w)):
             setattr(self, name, np.ascontiguousarray(v, dtype=np.float64).copy())
         self.zq = None if zq is None else np.ascontiguousarray(zq, dtype=np.float64).copy()
@@ -218,6 +224,7 @@ class Particles:
         s.zq = None if self.zq is None else _ptr(self.zq).value
         s.id = _ptr(self.ids).value
         s.eb = None if self.eb is None else _ptr(self.eb).value
+        s.pusher = self.pusher
         return s
 
     def append(self, other):
@@ -247,11 +254,14 @@ def gather(g, E, B, pos):
     return e, b
 
 
-def boris(qm_dt_half, e, b, u):
+def boris(qm_dt_half, e, b, u, pusher="boris"):
+    """One momentum update u^{n-1/2} -> u^{n+1/2} in the fields e, b by the
+    Boris, Vay or Higuera-Cary pusher."""
     e = np.ascontiguousarray(e, dtype=np.float64)
     b = np.ascontiguousarray(b, dtype=np.float64)
     uu = np.ascontiguousarray(u, dtype=np.float64).copy()
-    lib().orc_boris(float(qm_dt_half), _ptr(e), _ptr(b), _ptr(uu))
+    fn = {"boris": lib().orc_boris, "vay": lib().orc_vay, "higuera_cary": lib().orc_higuera_cary}[pusher]
+    fn(float(qm_dt_half), _ptr(e), _ptr(b), _ptr(uu))
     return uu
 
 

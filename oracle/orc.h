@@ -59,11 +59,16 @@ typedef struct {
     double *zq;              /* per-particle charge state (ions) or NULL: q_p = q * zq[p] when set */
     uint64_t *id;            /* particle ids (keys of the random streams) */
     double *eb;              /* optional output of the push: E^n, B^n at x^n, 6 per particle */
+    int pusher;              /* ORC_PUSH_BORIS, ORC_PUSH_VAY or ORC_PUSH_HC */
 } orc_species;
+
+enum { ORC_PUSH_BORIS = 0, ORC_PUSH_VAY = 1, ORC_PUSH_HC = 2 };
 
 void orc_gather(const orc_grid *g, const double *E[3], const double *B[3],
                 double xi, double yi, double zi, double e[3], double b[3]);
 void orc_boris(double qm_dt_half, const double e[3], const double b[3], double u[3]);
+void orc_vay(double qm_dt_half, const double e[3], const double b[3], double u[3]);
+void orc_higuera_cary(double qm_dt_half, const double e[3], const double b[3], double u[3]);
 void orc_esirkepov(const orc_grid *g, double qw, double x0, double y0, double z0,
                    double x1, double y1, double z1, double *J[3]);
 void orc_push_deposit(const orc_grid *g, const double *E[3], const double *B[3],

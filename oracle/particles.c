@@ -98,6 +98,55 @@ void orc_boris(double qm_dt_half, const double e[3], const double b[3], double u
     for (int c = 0; c < 3; ++c) u[c] = up[c] + qm_dt_half * e[c];
 }
 
+/* The relativistic pushers of Vay (Phys. Plasmas 15, 056701 (2008)) and of
+ * Higuera & Cary (Phys. Plasmas 24, 052104 (2017)), both with h = q dt / 2m,
+ * tau = h B.  They share the implicit step that rotates a momentum w about B
+ * with the Lorentz factor of the new momentum:
+ *   sigma = gamma_w^2 - tau^2,  u* = w . tau,
+ *   gamma_new^2 = (sigma + sqrt(sigma^2 + 4 (tau^2 + u*^2))) / 2,
+ *   t = tau / gamma_new,  s = 1 / (1 + t^2),
+ *   R(w) = s (w + (w . t) t + w x t).
+ * Vay:  w = u + h (2E + v x B) with v = u / gamma(u);  u_new = R(w).
+ * HC:   w = u + h E;  u+ = R(w);  u_new = u+ + h E + u+ x t.
+ * Both move a particle whose velocity is the drift E x B / B^2 (E.B = 0,
+ * |E| < |B|) on a straight line with unchanged momentum, which Boris does not
+ * for relativistic drifts. */
+static void rotate_implicit(const double w[3], const double tau[3], double out[3], double t[3]) {
+    const double w2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+    const double tau2 = tau[0] * tau[0] + tau[1] * tau[1] + tau[2] * tau[2];
+    const double us = w[0] * tau[0] + w[1] * tau[1] + w[2] * tau[2];
+    const double sigma = 1.0 + w2 - tau2;
+    const double g = sqrt(0.5 * (sigma + sqrt(sigma * sigma + 4.0 * (tau2 + us * us))));
+    for (int c = 0; c < 3; ++c) t[c] = tau[c] / g;
+    const double t2 = t[0] * t[0] + t[1] * t[1] + t[2] * t[2];
+    const double s = 1.0 / (1.0 + t2);
+    const double wt = w[0] * t[0] + w[1] * t[1] + w[2] * t[2];
+    out[0] = s * (w[0] + wt * t[0] + (w[1] * t[2] - w[2] * t[1]));
+    out[1] = s * (w[1] + wt * t[1] + (w[2] * t[0] - w[0] * t[2]));
+    out[2] = s * (w[2] + wt * t[2] + (w[0] * t[1] - w[1] * t[0]));
+}
+
+void orc_vay(double h, const double e[3], const double b[3], double u[3]) {
+    const double g0 = sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    const double v[3] = {u[0] / g0, u[1] / g0, u[2] / g0};
+    const double tau[3] = {h * b[0], h * b[1], h * b[2]};
+    double w[3], t[3];
+    w[0] = u[0] + 2.0 * h * e[0] + (v[1] * tau[2] - v[2] * tau[1]);
+    w[1] = u[1] + 2.0 * h * e[1] + (v[2] * tau[0] - v[0] * tau[2]);
+    w[2] = u[2] + 2.0 * h * e[2] + (v[0] * tau[1] - v[1] * tau[0]);
+    rotate_implicit(w, tau, u, t);
+}
+
+void orc_higuera_cary(double h, const double e[3], const double b[3], double u[3]) {
+    const double tau[3] = {h * b[0], h * b[1], h * b[2]};
+    const double w[3] = {u[0] + h * e[0], u[1] + h * e[1], u[2] + h * e[2]};
+    double up[3], t[3];
+    rotate_implicit(w, tau, up, t);
+    u[0] = up[0] + h * e[0] + (up[1] * t[2] - up[2] * t[1]);
+    u[1] = up[1] + h * e[1] + (up[2] * t[0] - up[0] * t[2]);
+    u[2] = up[2] + h * e[2] + (up[0] * t[1] - up[1] * t[0]);
+}
+
 /* 1D CIC shape of a particle at position p on nodes base, base+1, base+2 */
 static void shape3(double p, int base, double S[3]) {
     for (int k = 0; k < 3; ++k) {
@@ -155,7 +204,9 @@ void orc_push_deposit(const orc_grid *g, const double *E[3], const double *B[3],
         if (s->eb) {
             for (int c = 0; c < 3; ++c) { s->eb[6 * p + c] = e[c]; s->eb[6 * p + 3 + c] = b[c]; }
         }
-        orc_boris(q * dt / (2.0 * s->m), e, b, u);
+        if (s->pusher == ORC_PUSH_VAY) orc_vay(q * dt / (2.0 * s->m), e, b, u);
+        else if (s->pusher == ORC_PUSH_HC) orc_higuera_cary(q * dt / (2.0 * s->m), e, b, u);
+        else orc_boris(q * dt / (2.0 * s->m), e, b, u);
         const double gam = sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
         double x1[3];
         for (int a = 0; a < 3; ++a) {

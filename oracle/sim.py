@@ -105,9 +105,9 @@ class OracleSim:
         self.rho_bg = np.zeros(self.g.shape)
 
     def load_species(self, q, m, x, y, z, ux, uy, uz, w, zq=None, ids=None, ionize=None, kind=0, qed=None,
-                     pairs=None, **_):
+                     pairs=None, pusher="boris", **_):
         sid = len(self.species)
-        sp = Particles(q, m, x, y, z, ux, uy, uz, w, zq=zq, ids=ids)
+        sp = Particles(q, m, x, y, z, ux, uy, uz, w, zq=zq, ids=ids, pusher=pusher)
         if qed or pairs:
             sp.tau = qed_tau0(sp.ids, self.seed, sid)
         self.species.append(sp)
