@@ -127,9 +127,15 @@ typedef struct {
     int photon_species;
     double photon_eps_min;
     int pair_electron, pair_positron;
+    /* Momentum update (paper, Methodology: relativistic particle pusher):
+     * HYB_PUSH_BORIS (Boris, the default), HYB_PUSH_VAY (Vay 2008) or
+     * HYB_PUSH_HIGUERA_CARY (Higuera & Cary 2017); the last two move a
+     * particle at the relativistic E x B drift velocity without spurious force. */
+    int pusher;
 } hyb_species_desc;
 
 enum { HYB_KIND_MASSIVE = 0, HYB_KIND_PHOTON = 1 };
+enum { HYB_PUSH_BORIS = 0, HYB_PUSH_VAY = 1, HYB_PUSH_HIGUERA_CARY = 2 };
 
 /*
  * A cold relativistic fluid species on the nodes (paper, Methodology: fluid

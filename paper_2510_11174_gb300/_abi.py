@@ -44,7 +44,8 @@ class hyb_species_desc(C.Structure):
                 ("zmax", C.c_int), ("ip_eV", C.c_double * 8), ("l_qn", C.c_int * 8),
                 ("ionize_into", C.c_int),
                 ("kind", C.c_int), ("qed", C.c_int), ("photon_species", C.c_int),
-                ("photon_eps_min", C.c_double), ("pair_electron", C.c_int), ("pair_positron", C.c_int)]
+                ("photon_eps_min", C.c_double), ("pair_electron", C.c_int), ("pair_positron", C.c_int),
+                ("pusher", C.c_int)]
 
 
 class hyb_diag(C.Structure):

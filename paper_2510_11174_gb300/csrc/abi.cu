@@ -362,6 +362,7 @@ static hyb_status alloc_species(hyb_ctx *c, Species &sp, int cap, bool has_zq, b
 
 // fill the species' kind / QED fields from its descriptor
 static void species_flags(SpDev &s, const hyb_species_desc *d, int sid) {
+    s.pusher = d->pusher;
     s.kind = d->kind;
     s.qed = d->qed;
     s.ph_species = d->qed ? d->photon_species : -1;
@@ -413,6 +414,8 @@ hyb_status hyb_load_species(hyb_ctx *c, const hyb_species_desc *d, int *species_
     if ((d->qed || (d->kind == HYB_KIND_PHOTON && d->pair_electron >= 0)) && !(c->desc.lambda_um > 0.0))
         return set_error(HYB_EINVAL, "QED needs lambda_um > 0");
     if (d->n < 0) return set_error(HYB_EINVAL, "negative particle count");
+    if (d->pusher < HYB_PUSH_BORIS || d->pusher > HYB_PUSH_HIGUERA_CARY)
+        return set_error(HYB_EINVAL, "pusher must be one of HYB_PUSH_*");
     if (d->n > 0 && (!d->x || !d->y || !d->z || !d->ux || !d->uy || !d->uz || !d->w))
         return set_error(HYB_EINVAL, "missing particle arrays");
     if (d->zmax < 0 || d->zmax > 8) return set_error(HYB_EINVAL, "zmax must be in 0..8");

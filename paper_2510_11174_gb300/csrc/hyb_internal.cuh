@@ -135,6 +135,7 @@ struct SpDev {
     float dt_au;           // dt in atomic units
     double ip_mc2[8];      // Ip of state Z in m_e c^2 (energy tally)
     // strong-field QED
+    int pusher;            // HYB_PUSH_* (momentum update of massive species)
     int kind;              // 0 massive, 1 photon (moves at c, no charge)
     int qed;               // lepton emits photons
     int ph_species;        // receiving photon species (-1: tally only)

@@ -83,6 +83,70 @@ __device__ __forceinline__ float interp8(const float *__restrict__ f, int bx, in
     return fmaf(fz, b1 - b0, b0);
 }
 
+// Boris (relativistic, Birdsall & Langdon), h = q dt / 2m
+__device__ __forceinline__ void boris_push(float h, const float e[3], const float b[3], float u[3]) {
+    float um[3], tt[3], ss[3], ud[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) um[c] = u[c] + h * e[c];
+    const float gm = sqrtf(1.0f + um[0] * um[0] + um[1] * um[1] + um[2] * um[2]);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) tt[c] = h * b[c] * (1.0f / gm);
+    const float t2 = tt[0] * tt[0] + tt[1] * tt[1] + tt[2] * tt[2];
+    const float s2 = 2.0f / (1.0f + t2);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) ss[c] = tt[c] * s2;
+    ud[0] = um[0] + (um[1] * tt[2] - um[2] * tt[1]);
+    ud[1] = um[1] + (um[2] * tt[0] - um[0] * tt[2]);
+    ud[2] = um[2] + (um[0] * tt[1] - um[1] * tt[0]);
+    u[0] = um[0] + (ud[1] * ss[2] - ud[2] * ss[1]) + h * e[0];
+    u[1] = um[1] + (ud[2] * ss[0] - ud[0] * ss[2]) + h * e[1];
+    u[2] = um[2] + (ud[0] * ss[1] - ud[1] * ss[0]) + h * e[2];
+}
+
+// the implicit rotation of the Vay and Higuera-Cary pushers: w turned about
+// tau = h B with the Lorentz factor of the result,
+//   gamma^2 = (sigma + sqrt(sigma^2 + 4 (tau^2 + (w.tau)^2))) / 2, sigma = 1 + w^2 - tau^2,
+//   t = tau / gamma, s = 1 / (1 + t^2), R(w) = s (w + (w.t) t + w x t)
+__device__ __forceinline__ void rotate_implicit(const float w[3], const float tau[3], float out[3], float t[3]) {
+    const float w2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+    const float tau2 = tau[0] * tau[0] + tau[1] * tau[1] + tau[2] * tau[2];
+    const float us = w[0] * tau[0] + w[1] * tau[1] + w[2] * tau[2];
+    const float sigma = 1.0f + w2 - tau2;
+    const float g = sqrtf(0.5f * (sigma + sqrtf(sigma * sigma + 4.0f * (tau2 + us * us))));
+    const float ig = 1.0f / g;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) t[c] = tau[c] * ig;
+    const float s = 1.0f / (1.0f + t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
+    const float wt = w[0] * t[0] + w[1] * t[1] + w[2] * t[2];
+    out[0] = s * (w[0] + wt * t[0] + (w[1] * t[2] - w[2] * t[1]));
+    out[1] = s * (w[1] + wt * t[1] + (w[2] * t[0] - w[0] * t[2]));
+    out[2] = s * (w[2] + wt * t[2] + (w[0] * t[1] - w[1] * t[0]));
+}
+
+// Vay (Phys. Plasmas 15, 056701, 2008): w = u + h (2E + v x B), u_new = R(w)
+__device__ __forceinline__ void vay_push(float h, const float e[3], const float b[3], float u[3]) {
+    const float ig = 1.0f / sqrtf(1.0f + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    const float tau[3] = {h * b[0], h * b[1], h * b[2]};
+    const float v[3] = {u[0] * ig, u[1] * ig, u[2] * ig};
+    const float w[3] = {u[0] + 2.0f * h * e[0] + (v[1] * tau[2] - v[2] * tau[1]),
+                        u[1] + 2.0f * h * e[1] + (v[2] * tau[0] - v[0] * tau[2]),
+                        u[2] + 2.0f * h * e[2] + (v[0] * tau[1] - v[1] * tau[0])};
+    float t[3];
+    rotate_implicit(w, tau, u, t);
+}
+
+// Higuera & Cary (Phys. Plasmas 24, 052104, 2017): w = u + h E, u+ = R(w),
+// u_new = u+ + h E + u+ x t
+__device__ __forceinline__ void higuera_cary_push(float h, const float e[3], const float b[3], float u[3]) {
+    const float tau[3] = {h * b[0], h * b[1], h * b[2]};
+    const float w[3] = {u[0] + h * e[0], u[1] + h * e[1], u[2] + h * e[2]};
+    float up[3], t[3];
+    rotate_implicit(w, tau, up, t);
+    u[0] = up[0] + h * e[0] + (up[1] * t[2] - up[2] * t[1]);
+    u[1] = up[1] + h * e[1] + (up[2] * t[0] - up[0] * t[2]);
+    u[2] = up[2] + h * e[2] + (up[0] * t[1] - up[1] * t[0]);
+}
+
 __device__ __forceinline__ void shape3(float p, int gbase, float S[3]) {
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
@@ -332,24 +396,11 @@ __global__ void __launch_bounds__(PUSH_THREADS, 3) k_push_deposit(GridDev g, con
                 b[1] = interp8<F>(sBy, ax.lh, ay.li, az.lh, ax.fh, ay.fi, az.fh);
                 b[2] = interp8<F>(sBz, ax.lh, ay.lh, az.li, ax.fh, ay.fh, az.fi);
 
-                // ---- Boris
+                // ---- momentum update (species-uniform choice: no divergence)
                 const float h = q * qm_half;
-                float um[3], tt[3], ss[3], ud[3];
-#pragma unroll
-                for (int c = 0; c < 3; ++c) um[c] = u[c] + h * e[c];
-                const float gm = sqrtf(1.0f + um[0] * um[0] + um[1] * um[1] + um[2] * um[2]);
-#pragma unroll
-                for (int c = 0; c < 3; ++c) tt[c] = h * b[c] * (1.0f / gm);
-                const float t2 = tt[0] * tt[0] + tt[1] * tt[1] + tt[2] * tt[2];
-                const float s2 = 2.0f / (1.0f + t2);
-#pragma unroll
-                for (int c = 0; c < 3; ++c) ss[c] = tt[c] * s2;
-                ud[0] = um[0] + (um[1] * tt[2] - um[2] * tt[1]);
-                ud[1] = um[1] + (um[2] * tt[0] - um[0] * tt[2]);
-                ud[2] = um[2] + (um[0] * tt[1] - um[1] * tt[0]);
-                u[0] = um[0] + (ud[1] * ss[2] - ud[2] * ss[1]) + h * e[0];
-                u[1] = um[1] + (ud[2] * ss[0] - ud[0] * ss[2]) + h * e[1];
-                u[2] = um[2] + (ud[0] * ss[1] - ud[1] * ss[0]) + h * e[2];
+                if (sp.pusher == HYB_PUSH_BORIS) boris_push(h, e, b, u);
+                else if (sp.pusher == HYB_PUSH_VAY) vay_push(h, e, b, u);
+                else higuera_cary_push(h, e, b, u);
 
                 // ---- move (photons at c: velocity k / |k|), reflect at absorbing walls
                 const float gam = sp.kind == 1 ? fmaxf(sqrtf(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]), 1e-30f)

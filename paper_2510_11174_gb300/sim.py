@@ -108,16 +108,20 @@ class Simulation:
         self.close()
 
     # ------------------------------------------------------------------ set-up
+    PUSHERS = {"boris": 0, "vay": 1, "higuera_cary": 2}
+
     def load_species(self, q, m, x, y, z, ux, uy, uz, w, zq=None, ids=None, tile_capacity=0, ionize=None,
-                     kind=0, qed=None, pairs=None):
+                     kind=0, qed=None, pairs=None, pusher="boris"):
         """Add a species; returns its id.  ``ionize`` = dict(zmax, ip_eV, l, into)
         makes it field-ionizable (zq = charge states required); kind = 1 makes
         a photon species; ``qed`` = dict(photon_species, eps_min) turns on
         photon emission by a lepton species; ``pairs`` = dict(electron,
-        positron) turns on pair creation by a photon species."""
+        positron) turns on pair creation by a photon species; ``pusher`` is
+        "boris", "vay" or "higuera_cary"."""
         d = _abi.hyb_species_desc()
         d.q, d.m = q, m
         d.kind = int(kind)
+        d.pusher = self.PUSHERS[pusher]
         d.photon_species = d.pair_electron = d.pair_positron = -1
         if qed:
             d.qed = 1
