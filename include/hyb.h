@@ -153,6 +153,12 @@ typedef struct {
     int ptr_on_device;
     const float *n, *ux, *uy, *uz;
     double n_floor;
+    /* Warm fluid (the paper's fluid model carries an adiabatic pressure):
+     * temperature_keV > 0 adds the pressure p = n_ref T (n / n_ref)^gamma_ad
+     * (gamma_ad 0 = 5/3, n_ref 0 = 1 n_c) to the momentum equation, -grad p / m,
+     * applied with the Lorentz force before the transport with central face
+     * pressures (a wall reflects the pressure).  0 keeps the fluid cold. */
+    double temperature_keV, gamma_ad, n_ref;
 } hyb_fluid_desc;
 
 /* Diagnostics: FP64 energy reductions (paper, Methodology: total energy from

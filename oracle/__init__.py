@@ -124,7 +124,8 @@ def _declare(L):
                                 C.POINTER(Species), _P, C.POINTER(Species), _P, C.c_long, _P]
     L.orc_qed_pairs.restype = C.c_long
     L.orc_node_fields.argtypes = [C.POINTER(Grid), _D3, _D3, C.c_int, C.c_int, C.c_int, _P, _P]
-    L.orc_fluid_step.argtypes = [C.POINTER(Grid), _D3, _D3, _D3, C.c_double, C.c_double, _P, _D3, C.c_double]
+    L.orc_fluid_step.argtypes = [C.POINTER(Grid), _D3, _D3, _D3, C.c_double, C.c_double, _P, _D3, C.c_double,
+                                 C.c_double, C.c_double]
     L.orc_fluid_step.restype = C.c_long
     L.orc_fluid_energy.argtypes = [C.POINTER(Grid), C.c_double, _P, _D3]
     L.orc_fluid_energy.restype = C.c_double
@@ -486,10 +487,12 @@ def qed_pairs(ph, kappa, dt, seed, sp_index, step):
 
 # --------------------------------------------------------------------------- cold fluid
 class Fluid:
-    """A cold fluid species on the nodes: density n [n_c] and u = gamma beta."""
+    """A fluid species on the nodes: density n [n_c] and u = gamma beta; cold,
+    or with the adiabatic pressure p = K n^gamma_ad (K [m_e c^2 n_c^(1 - gamma_ad)])."""
 
-    def __init__(self, q, m, n, u=None, n_floor=1e-10):
+    def __init__(self, q, m, n, u=None, n_floor=1e-10, K=0.0, gamma_ad=5.0 / 3.0):
         self.q, self.m, self.n_floor = float(q), float(m), float(n_floor)
+        self.K, self.gamma_ad = float(K), float(gamma_ad)
         self.n = np.ascontiguousarray(n, dtype=np.float64).copy()
         self.u = (np.zeros((3,) + self.n.shape) if u is None
                   else np.ascontiguousarray(u, dtype=np.float64).copy())
@@ -503,9 +506,9 @@ def node_fields(g, E, B, i, j, k):
 
 
 def fluid_step(g, E, B, J, fl):
-    """One cold-fluid step; adds the face currents to J.  Returns the number of clamped nodes."""
+    """One fluid step; adds the face currents to J.  Returns the number of clamped nodes."""
     return lib().orc_fluid_step(C.byref(g), _f3(E), _f3(B), _f3(J), fl.q, fl.m, _ptr(fl.n), _f3(fl.u),
-                                fl.n_floor)
+                                fl.n_floor, fl.K, fl.gamma_ad)
 
 
 def fluid_energy(g, fl):

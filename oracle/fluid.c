@@ -7,6 +7,14 @@
  * part:
  *   dn/dt + div(n v) = 0,   d(n u)/dt + div(n u v) = (q/m) n (E + v x B),
  *   u = gamma v, gamma = sqrt(1 + u^2).
+ * Warm variant (the paper's fluid model carries an adiabatic pressure): with
+ * p = K n^Gamma (K = 0: cold) the momentum equation gains -grad p / m, applied
+ * with the Lorentz force before the transport, so that the new velocity moves
+ * the density (a leapfrog, stable for sound waves with dt c_s < 2 d):
+ *   u* <- u* - dt (P(i+1/2) - P(i-1/2)) / (d m n_i) along each axis,
+ * P(i+1/2) = (p_i + p_{i+1}) / 2 on inner faces and the node's own p on the
+ * outer face of an absorbing axis (a wall reflects the pressure), evaluated
+ * with n^n at nodes with n > n_floor (elsewhere u* keeps its value).
  * The paper gives no discretisation.  Reading used here: first-order upwind
  * (donor cell) in conservative form on the control volumes around the nodes,
  * with the Lorentz force applied first as a Boris rotation of u at each node
@@ -62,8 +70,10 @@ void orc_node_fields(const orc_grid *g, const double *E[3], const double *B[3], 
                    fval(g, B[2], i, j, k));
 }
 
+static double pressure(double K, double gam, double n) { return K > 0.0 && n > 0.0 ? K * pow(n, gam) : 0.0; }
+
 long orc_fluid_step(const orc_grid *g, const double *E[3], const double *B[3], double *J[3], double q, double m,
-                    double *n, double *u[3], double n_floor) {
+                    double *n, double *u[3], double n_floor, double K, double gam) {
     const int nx = g->nx, ny = g->ny, nz = g->nz;
     const long N = (long)nx * ny * nz;
     const int nn[3] = {nx, ny, nz};
@@ -81,8 +91,19 @@ long orc_fluid_step(const orc_grid *g, const double *E[3], const double *B[3], d
         double e[3], b[3], uu[3] = {u[0][c], u[1][c], u[2][c]};
         orc_node_fields(g, E, B, i, j, k, e, b);
         orc_boris(q * g->dt / (2.0 * m), e, b, uu);
-        const double gam = sqrt(1.0 + uu[0] * uu[0] + uu[1] * uu[1] + uu[2] * uu[2]);
-        for (int a = 0; a < 3; ++a) { us[a][c] = uu[a]; vs[a][c] = uu[a] / gam; }
+        if (K > 0.0 && n[c] > n_floor) {
+            const int idx[3] = {i, j, k};
+            const double pc = pressure(K, gam, n[c]);
+            for (int a = 0; a < 3; ++a) {
+                int lo[3] = {i, j, k}, hi[3] = {i, j, k};
+                double plo = pc, phi = pc;       /* outer faces of an absorbing axis: the node's own p */
+                if (g->bc[a] == 0 || idx[a] > 0) { lo[a] = wrapi(idx[a] - 1, nn[a]); plo = 0.5 * (pc + pressure(K, gam, n[IDX(g, lo[0], lo[1], lo[2])])); }
+                if (g->bc[a] == 0 || idx[a] < nn[a] - 1) { hi[a] = wrapi(idx[a] + 1, nn[a]); phi = 0.5 * (pc + pressure(K, gam, n[IDX(g, hi[0], hi[1], hi[2])])); }
+                uu[a] -= g->dt * (phi - plo) / (d[a] * m * n[c]);
+            }
+        }
+        const double gmn = sqrt(1.0 + uu[0] * uu[0] + uu[1] * uu[1] + uu[2] * uu[2]);
+        for (int a = 0; a < 3; ++a) { us[a][c] = uu[a]; vs[a][c] = uu[a] / gmn; }
     }
     /* 2.-4. face fluxes (face i+1/2 of each node along each axis) */
     double *dn = (double *)calloc(N, sizeof(double));

@@ -113,7 +113,7 @@ long orc_qed_pairs(orc_species *s, double *tau, unsigned char *alive, double kap
 void orc_node_fields(const orc_grid *g, const double *E[3], const double *B[3], int i, int j, int k,
                      double e[3], double b[3]);
 long orc_fluid_step(const orc_grid *g, const double *E[3], const double *B[3], double *J[3], double q, double m,
-                    double *n, double *u[3], double n_floor);
+                    double *n, double *u[3], double n_floor, double K, double gam);
 double orc_fluid_energy(const orc_grid *g, double m, const double *n, const double *u[3]);
 
 /* ---- regime criterion and conversions ---------------------------------------- */

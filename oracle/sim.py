@@ -117,14 +117,17 @@ class OracleSim:
         self.pair_cfg.append(pairs)
         return sid
 
-    def load_fluid(self, q, m, n, ux=None, uy=None, uz=None, n_floor=1e-10, **_):
-        """A cold fluid species on the nodes (arrays shaped (nz, ny, nx))."""
+    def load_fluid(self, q, m, n, ux=None, uy=None, uz=None, n_floor=1e-10, temperature_keV=0.0, gamma_ad=5.0 / 3.0,
+                   n_ref=1.0, **_):
+        """A fluid species on the nodes (arrays shaped (nz, ny, nx)); warm with
+        p = n_ref T (n / n_ref)^gamma_ad when temperature_keV > 0."""
         n = np.asarray(n, dtype=np.float64)
         u = np.zeros((3,) + n.shape)
         for a, v in enumerate((ux, uy, uz)):
             if v is not None:
                 u[a] = np.asarray(v, dtype=np.float64)
-        self.fluids.append(Fluid(q, m, n, u, n_floor=n_floor))
+        K = (temperature_keV / 510.99895) / n_ref ** (gamma_ad - 1.0) if temperature_keV > 0 else 0.0
+        self.fluids.append(Fluid(q, m, n, u, n_floor=n_floor, K=K, gamma_ad=gamma_ad))
         return len(self.fluids) - 1
 
     def set_regime(self, a_thr=1.0, n_thr=1.0, c_thr=0.1, chi_thr=1e-3, dilate=2, k_sigma=1.0, ppc=8,

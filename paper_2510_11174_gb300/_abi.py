@@ -71,7 +71,8 @@ HYB_MAX_FLUIDS = 4
 class hyb_fluid_desc(C.Structure):
     _fields_ = [("q", C.c_double), ("m", C.c_double), ("ptr_on_device", C.c_int),
                 ("n", C.c_void_p), ("ux", C.c_void_p), ("uy", C.c_void_p), ("uz", C.c_void_p),
-                ("n_floor", C.c_double)]
+                ("n_floor", C.c_double), ("temperature_keV", C.c_double), ("gamma_ad", C.c_double),
+                ("n_ref", C.c_double)]
 
 
 class hyb_phase_times_t(C.Structure):

@@ -610,6 +610,14 @@ hyb_status hyb_load_fluid(hyb_ctx *c, const hyb_fluid_desc *d, int *fluid_id) {
     f.m = (float)d->m;
     f.m_d = d->m;
     f.n_floor = d->n_floor > 0.0 ? (float)d->n_floor : 1e-10f;
+    if (d->temperature_keV < 0.0 || d->gamma_ad < 0.0 || d->n_ref < 0.0)
+        return set_error(HYB_EINVAL, "fluid temperature, adiabatic index and reference density must be >= 0");
+    if (d->temperature_keV > 0.0) {
+        const double gam = d->gamma_ad > 0.0 ? d->gamma_ad : 5.0 / 3.0;
+        const double nref = d->n_ref > 0.0 ? d->n_ref : 1.0;
+        f.pK = (float)(d->temperature_keV / 510.99895 * std::pow(nref, 1.0 - gam));
+        f.pgam = (float)gam;
+    }
     const cudaMemcpyKind kind = d->ptr_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     const float *src[4] = {d->n, d->ux, d->uy, d->uz};
     float *dst[4] = {f.n, f.ux, f.uy, f.uz};

@@ -6,7 +6,10 @@
 //
 // Two kernels per fluid and step:
 //  1. k_fluid_lorentz: at every node, E and B averaged from their Yee
-//     positions, u* = Boris(u; E, B); u* and a copy of n go to scratch.
+//     positions, u* = Boris(u; E, B); a warm fluid (p = K n^Gamma) also takes
+//     u* -= dt (P(i+1/2) - P(i-1/2)) / (d m n) per axis, P the mean of the two
+//     nodes' p on inner faces and the node's own p on the outer face of an
+//     absorbing axis; u* and a copy of n go to scratch.
 //  2. k_fluid_update: donor-cell transport on the node control volumes; the
 //     flux through the face between nodes i and i+1 along axis a uses the
 //     mean face velocity s = (v*_a(i) + v*_a(i+1))/2 and the upwind node:
@@ -69,10 +72,31 @@ __global__ void __launch_bounds__(128) k_fluid_lorentz(GridDev g, const float *_
         ud[0] = um[0] + (um[1] * tt[2] - um[2] * tt[1]);
         ud[1] = um[1] + (um[2] * tt[0] - um[0] * tt[2]);
         ud[2] = um[2] + (um[0] * tt[1] - um[1] * tt[0]);
-        f.usx[c] = um[0] + (ud[1] * ss[2] - ud[2] * ss[1]) + h * e[0];
-        f.usy[c] = um[1] + (ud[2] * ss[0] - ud[0] * ss[2]) + h * e[1];
-        f.usz[c] = um[2] + (ud[0] * ss[1] - ud[1] * ss[0]) + h * e[2];
-        f.ns[c] = f.n[c];
+        float us[3] = {um[0] + (ud[1] * ss[2] - ud[2] * ss[1]) + h * e[0],
+                       um[1] + (ud[2] * ss[0] - ud[0] * ss[2]) + h * e[1],
+                       um[2] + (ud[0] * ss[1] - ud[1] * ss[0]) + h * e[2]};
+        const float nc = f.n[c];
+        if (f.pK > 0.0f && nc > f.n_floor) {
+            // adiabatic pressure force, central face pressures, walls reflect
+            auto pr = [&](float n) { return n > 0.0f ? f.pK * powf(n, f.pgam) : 0.0f; };
+            const float pc = pr(nc);
+            const int lo[3] = {im, jm, km};
+            const int hi[3] = {upper_nb(i, nx, g.bc[0] == 0), upper_nb(j, ny, g.bc[1] == 0),
+                               upper_nb(k, nz, g.bc[2] == 0)};
+            const long long st[3] = {1, nx, (long long)nx * ny};
+            const int idx[3] = {i, j, k};
+            const float coef = g.dt / (f.m * nc);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const float plo = lo[a] < 0 ? pc : 0.5f * (pc + pr(f.n[c + (lo[a] - idx[a]) * st[a]]));
+                const float phi = hi[a] < 0 ? pc : 0.5f * (pc + pr(f.n[c + (hi[a] - idx[a]) * st[a]]));
+                us[a] -= coef * (phi - plo) / g.d[a];
+            }
+        }
+        f.usx[c] = us[0];
+        f.usy[c] = us[1];
+        f.usz[c] = us[2];
+        f.ns[c] = nc;
     }
 }
 

@@ -158,6 +158,7 @@ struct FluidDev {
     float *n, *ux, *uy, *uz;       // state: density, u = gamma beta
     float *ns, *usx, *usy, *usz;   // scratch: density and u* after the Lorentz step
     float q, m, n_floor;
+    float pK, pgam;                // adiabatic pressure p = pK n^pgam (pK = 0: cold)
     double m_d;
     unsigned long long *clamped;   // accumulated clamp count
 };

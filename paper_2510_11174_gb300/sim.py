@@ -164,10 +164,13 @@ class Simulation:
         self.n_species += 1
         return sid.value
 
-    def load_fluid(self, q, m, n, ux=None, uy=None, uz=None, n_floor=0.0):
-        """Add a cold fluid species (node arrays shaped (nz, ny, nx)); returns its id."""
+    def load_fluid(self, q, m, n, ux=None, uy=None, uz=None, n_floor=0.0, temperature_keV=0.0, gamma_ad=0.0,
+                   n_ref=0.0):
+        """Add a fluid species (node arrays shaped (nz, ny, nx)); returns its id.
+        temperature_keV > 0 makes it warm: p = n_ref T (n / n_ref)^gamma_ad."""
         d = _abi.hyb_fluid_desc()
         d.q, d.m, d.n_floor = q, m, n_floor
+        d.temperature_keV, d.gamma_ad, d.n_ref = temperature_keV, gamma_ad, n_ref
         keep = []
         ptrs = []
         on_dev = None

@@ -84,3 +84,28 @@ def test_fluid_and_particles_together():
     E, B, J = sim.get_fields()
     assert rel_l2(E, orc.E) <= 1e-4
     assert rel_l2(sim.get_fluid(0)["n"], orc.fluids[0].n) <= 1e-5
+
+
+@pytest.mark.parametrize("bc", [(0, 0, 0), (1, 1, 0)])
+def test_warm_electron_and_positron_fluids_match_oracle(bc):
+    """A warm pair plasma (adiabatic pressure, Gamma = 5/3 and 3) against the
+    oracle over 50 steps: densities, velocities and the fields they drive."""
+    inp, fl = _fluid_case(bc=bc, seed=3)
+    rng = np.random.default_rng(8)
+    pos = dict(q=1.0, m=1.0, n=np.abs(_smooth((8, 16, 16), rng, 0.05, 0.4)).astype(np.float32),
+               temperature_keV=20.0, gamma_ad=3.0, n_ref=0.4)
+    fl.update(temperature_keV=5.0, gamma_ad=5.0 / 3.0, n_ref=0.5)
+    sim, orc = make_pair(inp)
+    for f in (fl, pos):
+        sim.load_fluid(**f)
+        orc.load_fluid(**f)
+    for _ in range(2):
+        sim.step(25)
+        orc.step(25)
+    for k in range(2):
+        gf = sim.get_fluid(k)
+        of = orc.fluids[k]
+        assert rel_l2(gf["n"], of.n) <= 1e-5, k
+        assert rel_l2(np.stack([gf["ux"], gf["uy"], gf["uz"]]), of.u) <= 1e-4, k
+    E, B, J = sim.get_fields()
+    assert rel_l2(E, orc.E) <= 1e-4 and rel_l2(B, orc.B) <= 1e-4
