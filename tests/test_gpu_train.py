@@ -89,9 +89,15 @@ def test_three_adam_steps_match_oracle():
                 g = grads[t][l][k].numpy()
                 strong &= np.abs(g) >= 0.3 * np.sqrt(np.mean(g ** 2))
                 if strong.sum() >= 4:
-                    rel = np.abs(d_gpu - d_orc)[strong] / np.abs(d_orc[strong])
-                    assert np.median(rel) <= 1e-3 and np.quantile(rel, 0.99) <= 1e-2, \
-                        (l, k, t, np.median(rel), np.quantile(rel, 0.99))
+                    # the update -lr m_hat / sqrt(v_hat) moves by about lr dg / sqrt(v_hat)
+                    # for a gradient error dg; sqrt(v_hat) >= 0.3 rms(g) here, so a gradient
+                    # parity of ~1e-3 rms(g) bounds the update error by a few 1e-3 lr (m_hat
+                    # itself may cancel between steps, so the error is taken relative to lr)
+                    err = np.abs(d_gpu - d_orc)[strong] / lr
+                    assert np.median(err) <= 1e-3 and np.quantile(err, 0.99) <= 1e-2, \
+                        (l, k, t, np.median(err), np.quantile(err, 0.99))
+                    if t == 0:   # the first step is -lr sign(g)
+                        assert np.all(np.abs(np.abs(d_gpu[strong]) / lr - 1.0) <= 1e-3)
                 # the first steps' bias-corrected moments keep |m_hat| / sqrt(v_hat) near 1
                 assert np.all(np.abs(d_gpu) <= 1.2 * lr)
                 assert rel_l2(d_gpu, d_orc) <= 0.1, (l, k, t, rel_l2(d_gpu, d_orc))
