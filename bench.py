@@ -535,6 +535,7 @@ def run_e2e(P, inp, steps, stream):
     sim.close()
     if model is not None:
         model.close()
+    steps += inp.get("preroll", 0)   # a workload's pre-roll steps ran inside the timed region too
     return {"value": steps / dt, "unit": "steps/s", "h2d_bytes_per_step": h2d / steps,
             "d2h_bytes_per_step": d2h / steps,
             "note": "context creation, host upload and the first classification amortised over the steps; "

@@ -357,6 +357,19 @@ __global__ void __launch_bounds__(PUSH_THREADS, 3) k_push_deposit(GridDev g, con
         // times q_p below; photons (m = 0, q = 0) get no Lorentz force
         const float qm_half = sp.kind == 1 ? 0.0f : 0.5f * dt / sp.m;
         int qn = 0;  // entries in this warp's queue (warp-uniform)
+        // the next particle's x, y, z, ux, uy, uz, w and charge state, loaded one
+        // iteration ahead so that the loads overlap the current particle's work
+        float pf[8];
+        auto prefetch = [&](int pp) {
+            if (pp < n) {
+                const long long s2 = base + pp;
+                pf[0] = sp.x[s2]; pf[1] = sp.y[s2]; pf[2] = sp.z[s2];
+                pf[3] = sp.ux[s2]; pf[4] = sp.uy[s2]; pf[5] = sp.uz[s2];
+                pf[6] = sp.w[s2];
+                pf[7] = sp.zq ? sp.zq[s2] : 1.0f;
+            }
+        };
+        prefetch(threadIdx.x);
         for (int p0 = 0; p0 < n; p0 += PUSH_THREADS) {
             const int p = p0 + threadIdx.x;
             bool act = p < n;
@@ -365,10 +378,13 @@ __global__ void __launch_bounds__(PUSH_THREADS, 3) k_push_deposit(GridDev g, con
             float e[3] = {0.0f, 0.0f, 0.0f}, b[3] = {0.0f, 0.0f, 0.0f};
             float wgt = 0.0f, q = 0.0f;
             if (act) {
-                x0[0] = sp.x[s]; x0[1] = sp.y[s]; x0[2] = sp.z[s];
-                u[0] = sp.ux[s]; u[1] = sp.uy[s]; u[2] = sp.uz[s];
-                wgt = sp.w[s];
-                q = sp.zq ? sp.q * sp.zq[s] : sp.q;
+                x0[0] = pf[0]; x0[1] = pf[1]; x0[2] = pf[2];
+                u[0] = pf[3]; u[1] = pf[4]; u[2] = pf[5];
+                wgt = pf[6];
+                q = sp.q * pf[7];
+            }
+            prefetch(p + PUSH_THREADS);
+            if (act) {
                 // every shared-memory index below derives from a cell inside this
                 // tile; anything else is flagged and left untouched
                 bool inside = true;

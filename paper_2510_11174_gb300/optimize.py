@@ -62,7 +62,7 @@ def de_minimize(f_batch, lo, hi, pop=16, generations=20, F=0.7, CR=0.9, seed=0, 
 
 def _ramp_slab_run(P, nx, ny, nz, a0, tau_fs, w0_lambda, ppc, tile, stream, seed):
     inp = inputs.ramp_slab(nx=nx, ny=ny, nz=nz, vacuum_lambda=0.25, slab_lambda=0.5, a0=a0, tau_fs=tau_fs,
-                           w0_lambda=w0_lambda, ppc=ppc, tile_capacity=4 * tile ** 3 * ppc, seed=seed)
+                           w0_lambda=w0_lambda, ppc=ppc, tile_capacity=8 * tile ** 3 * ppc, seed=seed)
     inp["laser"]["t_peak"] = inp["laser"]["tau_fwhm"]   # the pulse peaks one FWHM after the start
     g = inp["grid"]
     sim = P.Simulation(g["nx"], g["ny"], g["nz"], g["dx"], cfl_frac=g["cfl_frac"], bc=g["bc"], laser=inp["laser"],
