@@ -61,6 +61,8 @@ def workloads():
         # full PIC with ionization and QED: 128^3, lambda/20, neutral carbon slab (16 atoms per cell), a0 = 100;
         # the timed steps start PREROLL_CARBON steps in, when the pulse ionizes the slab
         "carbon_slab_128": ("pic", lambda seed: dict(inputs.carbon_slab(seed=seed + 1), preroll=PREROLL_CARBON)),
+        # classifier training: 4096 method-generated 32^3 x 6 patches, batch 32 (one step = one Adam step)
+        "train_classifier_4096x32": ("train", None),
     }
 
 
@@ -162,6 +164,34 @@ NCU_CONV_L1_BYTES_PER_CELL = 87.4e6 / 1048576
 # the ncu capture on the 128 x 128 x 64 ramp + slab (184.9 + 69.1 MB for its
 # 4.78 M particles); scaled to a full launch by the particle count
 NCU_PUSH_BYTES_PER_PARTICLE = 254.0e6 / 4784128
+
+
+# training FLOP per cell of one classifier training step: forward (94 176), data
+# gradient of layers 3..1 (2 * 27 * (32*32 + 32*16 + 16*1) = 83 808; layer 0 needs
+# none) and weight gradient (94 176)
+TRAIN_FLOP_PER_CELL = 94176 + 83808 + 94176
+
+
+def trained_model(P, stream, n_patches=1024, steps=300, runs=4):
+    """A classifier trained on method-generated data (config 4 in small):
+    patches of ramp + slab runs labelled by the physics criterion one
+    classification ahead, per-channel normalisation from the patches, `steps`
+    Adam steps at batch 32.  Returns (model, summary)."""
+    import torch
+    from paper_2510_11174_gb300 import training
+    t0 = time.perf_counter()
+    x, y = training.generate_patches(n_patches=n_patches, runs=runs, stream=stream)
+    t1 = time.perf_counter()
+    mean, std = training.channel_stats(x)
+    m = P.Classifier(dropout=0.2, mc_passes=MC_PASSES, seed=11, mean=mean, std=std, stream=stream.cuda_stream)
+    st = training.train(m, x, y, steps)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    frac = float(y.mean())
+    del x, y
+    return m, {"patches": n_patches, "steps": steps, "batch": 32, "final_loss": st[-1]["loss"],
+               "final_accuracy": st[-1]["accuracy"], "label_kinetic_fraction": frac,
+               "data_s": t1 - t0, "train_s": t2 - t1}
 
 
 def make_model(P, stream):
@@ -297,6 +327,8 @@ def run_ours(args, rank, world):
     kind, gen = workloads()[args.workload]
     if kind == "scan":
         return run_scan(args, P, torch)
+    if kind == "train":
+        return run_train(args, P, torch, stream)
     inp = gen(1 + rank)
     g = inp["grid"]
     cells = g["nx"] * g["ny"] * g["nz"]
@@ -308,7 +340,8 @@ def run_ours(args, rank, world):
     def allmax(v):
         return max_over_ranks(v, world, "cuda")
 
-    sim, model = make_sim(P, inp, stream.cuda_stream, policy="union")
+    trained, train_info = (trained_model(P, stream) if kind == "hybrid" else (None, None))
+    sim, model = make_sim(P, inp, stream.cuda_stream, policy="union", model=trained)
     probe = sim.diagnostics()
     flush_l2 = state_bytes(probe, cells) < 2 * L2_BYTES
     clocks = ClockSampler(dev)
@@ -320,7 +353,16 @@ def run_ours(args, rank, world):
     phases, cls = profile_phases(sim, model, args.warmup + args.steps)
     launches = after["launches_per_step"] * args.steps + ncls * after["launches_classify"]
     sim.close()
-    if model is not None:
+    learned = None
+    if trained is not None:
+        # the trained classifier alone decides the regime (the physics criterion only labels its data)
+        dsim, _ = make_sim(P, inp, stream.cuda_stream, policy="default", model=trained)
+        dms, _, db, da = timed_run(torch, dsim, trained, args.steps, args.warmup, stream, barrier, flush_l2)
+        learned = {"policy": "default (trained classifier alone)", "steps_per_s": job_rate(args.steps, world, dms),
+                   "ms_per_step": dms / args.steps, "kinetic_fraction": float(dsim.get_regime()[0].mean()),
+                   "particles_mean": 0.5 * (sum(db["count"]) + sum(da["count"])), "training": train_info}
+        dsim.close()
+    if model is not None and model is not trained:
         model.close()
 
     ms_per_step = total_ms / args.steps
@@ -394,7 +436,9 @@ def run_ours(args, rank, world):
                 "break_even_classify_every": ((cls["classify"] + cls["regime"]) / (full_step - plain)
                                               if cls and full_step > plain else None)}
 
-    e2e = run_e2e(P, inp, args.steps, stream) if rank == 0 else None
+    e2e = run_e2e(P, inp, args.steps, stream, trained) if rank == 0 else None
+    if trained is not None:
+        trained.close()
     out = {
         "metric": METRIC, "value": job_rate(args.steps, world, total_ms), "unit": "steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
@@ -404,12 +448,16 @@ def run_ours(args, rank, world):
                    "particles_mean": parts, "kinetic_fraction": kin_frac,
                    "classify_every": N_CLS if kind == "hybrid" else None,
                    "mc_passes": MC_PASSES if kind == "hybrid" else None,
+                   "policy": ("union: the trained classifier or the physics criterion" if kind == "hybrid" else None),
+                   "classifier": ("trained before the run on %d method-generated 32^3 patches, %d steps of batch "
+                                  "32" % (train_info["patches"], train_info["steps"]) if train_info else None),
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": ("flushed between timed steps (2 x L2 write outside the events)" if flush_l2 else
                           "resident state larger than L2 (%.0f MB); no flush" % (state_bytes(after, cells) / 1e6))},
         "particle_pushes_per_s": world * parts * args.steps / (total_ms * 1e-3),
         "cell_updates_per_s": world * cells * args.steps / (total_ms * 1e-3),
         "full_pic": full,
+        "learned_policy": learned,
         "phase_ms": phases, "classification_ms": cls,
         "roofline": roofs[dom], "roofline_all": roofs,
         "e2e": e2e,
@@ -417,6 +465,50 @@ def run_ours(args, rank, world):
         "clocks": clk,
     }
     return out
+
+
+def run_train(args, P, torch, stream):
+    """Classifier training on method-generated data: 4096 patches of 32^3 x 6
+    node fields from ramp + slab runs (seeded a0 and density), labels from the
+    physics criterion one classification ahead; W warm-up and K timed Adam
+    steps at batch 32 between CUDA events on the library's stream."""
+    from paper_2510_11174_gb300 import training
+    t0 = time.perf_counter()
+    x, y = training.generate_patches(n_patches=4096, runs=8, stream=stream)
+    gen_s = time.perf_counter() - t0
+    mean, std = training.channel_stats(x)
+    m = P.Classifier(dropout=0.2, mc_passes=MC_PASSES, seed=11, mean=mean, std=std, stream=stream.cuda_stream)
+    first = training.train(m, x, y, args.warmup)
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    st = training.train(m, x, y, args.steps, seed=6)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    cells = 32 * 32 ** 3
+    flop = TRAIN_FLOP_PER_CELL * cells
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    pk = peaks.get("bf16_tflops_sustained", 1700.0)
+    achieved = flop * args.steps / (ms * 1e-3) / 1e12
+    m.close()
+    return {"metric": "classifier training steps/s (batch 32 x 32^3 x 6, BF16 tensor cores)",
+            "value": args.steps / (ms * 1e-3), "unit": "steps/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16", "data": "synthetic (method-generated, seeded)",
+            "config": {"workload": args.workload, "patches": int(x.shape[0]), "batch": 32, "patch": [32, 32, 32],
+                       "label_kinetic_fraction": float(y.mean()), "data_generation_s": gen_s},
+            "roofline": {"kernel": "hyb_train_step: forward, backward and Adam of one batch", "bound": "tensor",
+                         "achieved": achieved, "peak": pk, "unit": "TFLOP/s", "frac": achieved / pk,
+                         "algorithmic_flop_per_launch": flop, "mean_launch_ms": ms / args.steps,
+                         "peak_kind": "measured" if peaks else "fallback", "traffic": None,
+                         "note": "272 160 FLOP per cell (forward, data gradient of layers 3..1, weight gradient); "
+                                 "the weight gradients run on the CUDA cores"},
+            "loss_first": first[0]["loss"] if first else None, "loss_last": st[-1]["loss"],
+            "accuracy_last": st[-1]["accuracy"], "clocks": clk, "gpu_launches": None}
 
 
 def run_scan(args, P, torch):
@@ -484,7 +576,7 @@ def run_scan(args, P, torch):
     return res
 
 
-def run_e2e(P, inp, steps, stream):
+def run_e2e(P, inp, steps, stream, model=None):
     """Whole job through the public API from pinned host buffers: create the
     context, upload the initial state (particles or fluids, fields), classify,
     then per step advance (reclassifying every N_CLS steps) and read the FP64
@@ -524,7 +616,8 @@ def run_e2e(P, inp, steps, stream):
         del pin["fluids"]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    sim, model = make_sim(P, pin, stream.cuda_stream, policy="union")
+    shared = model
+    sim, model = make_sim(P, pin, stream.cuda_stream, policy="union", model=shared)
     d2h = 0
     for k in range(steps):
         advance(sim, model, 1, k)
@@ -533,7 +626,7 @@ def run_e2e(P, inp, steps, stream):
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     sim.close()
-    if model is not None:
+    if model is not None and model is not shared:
         model.close()
     steps += inp.get("preroll", 0)   # a workload's pre-roll steps ran inside the timed region too
     return {"value": steps / dt, "unit": "steps/s", "h2d_bytes_per_step": h2d / steps,
@@ -614,10 +707,38 @@ def oracle_threads():
     return torch.get_num_threads()
 
 
+def run_oracle_train_sample(budget_s=15.0):
+    """The oracle's training step (FP64 forward, backward and Adam) on batches
+    of 2 patches of 32^3, timed for about budget_s; steps/s divided by 16 for
+    the batch of 32."""
+    import torch
+    from oracle.classifier import adam_update, train_grads, OracleCNN
+    from paper_2510_11174_gb300 import inputs
+    rng = np.random.default_rng(3)
+    x = rng.standard_normal((2, 6, 32, 32, 32)).astype(np.float32)
+    y = (x[:, 0] > 0.5).astype(np.float32)
+    net = OracleCNN(inputs.classifier_weights(11), dropout=0.2, seed=11)
+    mom = [(torch.zeros_like(w), torch.zeros_like(w)) for w in net.W]
+    t0 = time.perf_counter()
+    n = 0
+    while time.perf_counter() - t0 < budget_s:
+        out = train_grads(net, x, y, pass_index=n, energy_weight=0.1)
+        for l in range(4):
+            net.W[l], m_, v_ = adam_update(net.W[l], out["grads"][l][0], mom[l][0], mom[l][1], n + 1)
+            mom[l] = (m_, v_)
+        n += 1
+    dt = time.perf_counter() - t0
+    return {"value": n / dt / 16.0, "unit": "steps/s", "cores": torch.get_num_threads(), "kind": "oracle",
+            "sample": "%d FP64 training steps of batch 2 x 32^3 (PyTorch CPU convolutions on %d threads, weights "
+                      "only in Adam); steps/s divided by 16 for batch 32" % (n, torch.get_num_threads())}
+
+
 def run_oracle_sample(workload, budget_s=15.0, max_steps=None):
     """Time the oracle on its bounded sample for about budget_s; the value is
     scaled to the whole workload by the cell ratio (its work is linear in
     cells and particles, both proportional to the cross-section)."""
+    if workloads()[workload][0] == "train":
+        return run_oracle_train_sample(budget_s)
     o, net, ratio, what = oracle_sample(workload)
     t0 = time.perf_counter()
     n = 0
@@ -692,6 +813,14 @@ def run_reference(args, rank, world):
         return None
     from oracle import build as OB
     OB.build()
+    if workloads()[args.workload][0] == "train":
+        r = run_oracle_train_sample(budget_s=max(5.0, 2.0 * args.steps))
+        return {"metric": "classifier training steps/s (batch 32 x 32^3 x 6, BF16 tensor cores)", "value": r["value"],
+                "unit": "steps/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1e3 / r["value"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64", "data": "synthetic (seeded)", "impl": "reference",
+                "config": {"workload": args.workload, "batch": 32, "patch": [32, 32, 32]}, "cpu_baseline": r,
+                "e2e": {"value": r["value"], "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     o, net, ratio, what = oracle_sample(args.workload)
     oracle_advance(o, net, args.warmup, 0)
     parts0 = sum(sp.n for sp in o.species)
@@ -744,7 +873,8 @@ def main():
         if rank == 0 and world == 1 and not args.no_cpu_baseline:
             out["cpu_baseline"] = run_oracle_sample(args.workload, budget_s=15.0)
             out["cpu_baseline"]["cpu_model"] = cpu_model()
-            out["cpu_baseline_all_cores"] = run_oracle_all_cores(args.workload, budget_s=10.0)
+            if workloads()[args.workload][0] != "train":
+                out["cpu_baseline_all_cores"] = run_oracle_all_cores(args.workload, budget_s=10.0)
     if rank == 0 and out is not None:
         print(json.dumps(out))
     if world > 1 and args.impl == "ours":

@@ -321,6 +321,14 @@ hyb_status hyb_train_step(hyb_model *model, const float *patches_dev, const floa
  * hyb_model_get_layer). */
 hyb_status hyb_model_get_grad(hyb_model *model, int layer, float *gw_host, float *gb_host);
 
+/* The classifier's input channels at the nodes, as the classification forms
+ * them but not normalised: E_x, E_y, E_z averaged over the two Yee edges that
+ * meet at the node, B_x, B_y, B_z over the four faces around it (zero outside
+ * an absorbing axis), written to out_dev (device FP32, [6][nz][ny][nx]).  The
+ * paper trains its networks on data the simulation generates (Methodology):
+ * this is where training patches are cut from a run.  Stream-ordered. */
+hyb_status hyb_node_fields(hyb_ctx *ctx, float *out_dev);
+
 /* Copy the current mask (uint8, 1 = kinetic) and the residual background
  * charge rho_bg (FP32) to host arrays of nz*ny*nx values (either may be NULL;
  * synchronises). */

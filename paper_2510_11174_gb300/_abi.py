@@ -126,6 +126,7 @@ PROTOTYPES = {
     "hyb_set_regime": (C.c_int, [_ctx, C.POINTER(hyb_regime_desc)]),
     "hyb_classify": (C.c_int, [_ctx, _P, _P, _P, _P]),
     "hyb_get_regime": (C.c_int, [_ctx, _P, _P]),
+    "hyb_node_fields": (C.c_int, [_ctx, _P]),
     "hyb_model_create": (C.c_int, [C.POINTER(hyb_model_desc), C.POINTER(C.c_void_p)]),
     "hyb_model_destroy": (None, [_P]),
     "hyb_model_set_layer": (C.c_int, [_P, C.c_int, _P, _P]),

@@ -138,6 +138,33 @@ __global__ void k_prep_fields(GridDev g, const float *__restrict__ E, const floa
     dst[1] = reinterpret_cast<const uint4 *>(o)[1];
 }
 
+// the same node fields in FP32, not normalised, channel-first [6][nz][ny][nx]
+// (training patches cut from a run)
+__global__ void k_node_fields_f32(GridDev g, const float *__restrict__ E, const float *__restrict__ Bf,
+                                  float *__restrict__ out) {
+    const int nx = g.n[0], ny = g.n[1];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
+    if (i >= nx) return;
+    const long long c = ((long long)k * ny + j) * nx + i;
+    auto fv = [&](const float *F, int a, int bb, int cc) -> float {
+        int idx[3] = {a, bb, cc};
+        for (int ax = 0; ax < 3; ++ax) {
+            if (g.bc[ax] == 0) idx[ax] = idx[ax] < 0 ? idx[ax] + g.n[ax] : (idx[ax] >= g.n[ax] ? idx[ax] - g.n[ax] : idx[ax]);
+            else if (idx[ax] < 0 || idx[ax] > g.n[ax] - 1) return 0.0f;
+        }
+        return F[cidx(g, idx[0], idx[1], idx[2])];
+    };
+    const long long N = g.N;
+    out[c] = 0.5f * (fv(E, i - 1, j, k) + fv(E, i, j, k));
+    out[N + c] = 0.5f * (fv(E + N, i, j - 1, k) + fv(E + N, i, j, k));
+    out[2 * N + c] = 0.5f * (fv(E + 2 * N, i, j, k - 1) + fv(E + 2 * N, i, j, k));
+    out[3 * N + c] = 0.25f * (fv(Bf, i, j - 1, k - 1) + fv(Bf, i, j, k - 1) + fv(Bf, i, j - 1, k) + fv(Bf, i, j, k));
+    out[4 * N + c] = 0.25f * (fv(Bf + N, i - 1, j, k - 1) + fv(Bf + N, i, j, k - 1) + fv(Bf + N, i - 1, j, k) +
+                              fv(Bf + N, i, j, k));
+    out[5 * N + c] = 0.25f * (fv(Bf + 2 * N, i - 1, j - 1, k) + fv(Bf + 2 * N, i, j - 1, k) +
+                              fv(Bf + 2 * N, i - 1, j, k) + fv(Bf + 2 * N, i, j, k));
+}
+
 // layer-1 inputs of the passes pass0 .. pass0 + G - 1: a1[g] = h0s where the
 // layer-0 dropout mask of pass pass0 + g keeps the channel, else 0 (h0s holds
 // bf16(relu(layer 0) / (1 - p)), the kept value of every pass).  The 16-bit
@@ -500,6 +527,13 @@ hyb_status hyb_model_forward(hyb_model *m, const float *x, int B, int D, int H, 
     HYB_CUDA_TRY(cudaMemcpyAsync(&st, m->status, sizeof(int), cudaMemcpyDeviceToHost, m->stream));
     HYB_CUDA_TRY(cudaStreamSynchronize(m->stream));
     if (st) return set_error(HYB_ETIMEOUT, "a tensor-core wait gave up");
+    return HYB_OK;
+}
+
+hyb_status hyb_node_fields(hyb_ctx *c, float *out_dev) {
+    if (!c || !out_dev) return set_error(HYB_EINVAL, "null argument");
+    k_node_fields_f32<<<node_grid(c->g), node_block(c->g), 0, c->stream>>>(c->g, c->E, c->B, out_dev);
+    HYB_CUDA_TRY(cudaGetLastError());
     return HYB_OK;
 }
 

@@ -269,6 +269,7 @@ __global__ void __launch_bounds__(PUSH_THREADS, 3) k_push_deposit(GridDev g, con
     __shared__ int s_kfix;       // fixed-point exponent of the tile's current frame
     __shared__ double s_tal_e[NTALLY];
     __shared__ unsigned long long s_tal_n[NTALLY];
+    __shared__ SpDev s_sp;       // the species being pushed (its descriptor read once per tile)
     const long long step = *step_dev;
     double tal_e[NTALLY] = {0.0, 0.0, 0.0};
     int tal_n[NTALLY] = {0, 0, 0};
@@ -351,7 +352,14 @@ __global__ void __launch_bounds__(PUSH_THREADS, 3) k_push_deposit(GridDev g, con
     const float *sBx = sf + 3 * F3, *sBy = sf + 4 * F3, *sBz = sf + 5 * F3;
 
     for (int si = 0; si < nsp; ++si) {
-        const SpDev &sp = sps[si];
+        {
+            // the descriptor to shared memory: the loop reads it for every particle
+            const int *src = reinterpret_cast<const int *>(sps + si);
+            int *dst = reinterpret_cast<int *>(&s_sp);
+            for (int w = threadIdx.x; w < (int)(sizeof(SpDev) / sizeof(int)); w += PUSH_THREADS) dst[w] = src[w];
+            __syncthreads();
+        }
+        const SpDev &sp = s_sp;
         const int n = min(sp.count[t], sp.cap);
         const long long base = (long long)t * sp.cap;
         // times q_p below; photons (m = 0, q = 0) get no Lorentz force

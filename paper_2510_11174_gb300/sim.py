@@ -222,6 +222,17 @@ class Simulation:
             torch = _torch()
             torch.cuda.current_stream().wait_stream(self.torch_stream)
 
+    def node_fields(self, out=None):
+        """The classifier's six input channels at the nodes, not normalised
+        (hyb_node_fields): a torch CUDA tensor [6, nz, ny, nx]."""
+        torch = _torch()
+        if out is None:
+            out = torch.empty((6,) + self.shape, dtype=torch.float32, device="cuda")
+        check(self._lib.hyb_node_fields(self._ctx, out.data_ptr()))
+        if self.torch_stream is not None:
+            torch.cuda.current_stream().wait_stream(self.torch_stream)
+        return out
+
     def get_regime(self):
         mask = np.empty(self.shape, np.uint8)
         rho_bg = np.empty(self.shape, np.float32)

@@ -1,0 +1,99 @@
+"""Training data for the regime classifier from the method's own runs, and a
+training loop on it (paper, Methodology: the networks learn from data the
+simulation generates, the regime labels from the instability criterion the
+method uses; Results: training over epochs with a decreasing loss).
+
+``generate_patches`` runs ramp + slab hybrid simulations (the physics
+criterion decides the regime, fluid and particles are converted as the
+method does) with seeded pulse amplitudes (log-uniform) and densities
+(log-uniform), and at every classification cuts random 32^3 patches of the
+six node-field channels (``hyb_node_fields``).  A patch's label at a node is
+the criterion's decision there now or at the next classification ("kinetic
+now or soon"), so a network that learns it flags cells before the pulse
+reaches them.  ``train`` runs ``hyb_train_step`` over shuffled batches.
+
+Orchestration only: the runs, the node fields and every training step run in
+libhyb.so; torch indexing cuts the patches and stacks the batches.
+"""
+import math
+
+import numpy as np
+
+from . import inputs
+
+
+def _run(P, nx, ny, nz, a0, dens, seed, stream, tau_fs=12.0):
+    inp = inputs.ramp_slab(nx=nx, ny=ny, nz=nz, n_lo=0.01 * dens, n_hi=dens, n_slab=5.0 * dens, a0=a0,
+                           tau_fs=tau_fs, vacuum_lambda=0.5, slab_lambda=1.0, ppc=4, tile_capacity=4 * 512 * 8,
+                           seed=seed)
+    inp["laser"]["t_peak"] = inp["laser"]["tau_fwhm"]
+    g = inp["grid"]
+    sim = P.Simulation(g["nx"], g["ny"], g["nz"], g["dx"], cfl_frac=g["cfl_frac"], bc=g["bc"], laser=inp["laser"],
+                       stream=stream, seed=seed)
+    for sp in inp["species"]:
+        sim.load_species(**sp)
+    for fl in inp["fluids"]:
+        sim.load_fluid(**fl)
+    sim.set_regime(dilate=2, ppc=4, to_species=[0, 1], quiet=True)
+    return sim
+
+
+def generate_patches(n_patches=4096, grid=(128, 128, 64), patch=32, runs=8, classifications=16, every=10,
+                     a0_range=(10.0, 300.0), density_range=(0.2, 2.0), seed=11, stream=None):
+    """(x [n, 6, p, p, p], y [n, p, p, p]) as torch CUDA tensors (FP32)."""
+    import torch
+    import paper_2510_11174_gb300 as P
+    nx, ny, nz = grid
+    rng = np.random.default_rng(seed)
+    per_snap = int(math.ceil(n_patches / (runs * (classifications - 1))))
+    xs, ys = [], []
+    st = stream if stream is not None else torch.cuda.Stream()
+    for r in range(runs):
+        a0 = float(np.exp(rng.uniform(math.log(a0_range[0]), math.log(a0_range[1]))))
+        dens = float(np.exp(rng.uniform(math.log(density_range[0]), math.log(density_range[1]))))
+        sim = _run(P, nx, ny, nz, a0, dens, seed + r, st.cuda_stream)
+        snaps, masks = [], []
+        for c in range(classifications):
+            snaps.append(sim.node_fields())
+            sim.classify()
+            masks.append(torch.from_numpy(sim.get_regime()[0]).cuda())
+            sim.step(every)
+        sim.close()
+        for c in range(classifications - 1):
+            label = (masks[c] | masks[c + 1]).float()
+            for _ in range(per_snap):
+                z0, y0, x0 = (int(rng.integers(0, n - patch + 1)) for n in (nz, ny, nx))
+                xs.append(snaps[c][:, z0:z0 + patch, y0:y0 + patch, x0:x0 + patch])
+                ys.append(label[z0:z0 + patch, y0:y0 + patch, x0:x0 + patch])
+    x = torch.stack(xs[:n_patches]).contiguous()
+    y = torch.stack(ys[:n_patches]).contiguous()
+    return x, y
+
+
+def channel_stats(x):
+    """Per-channel mean and standard deviation of the patches (the
+    classifier's input normalisation)."""
+    m = x.mean(dim=(0, 2, 3, 4))
+    s = x.std(dim=(0, 2, 3, 4)).clamp_min(1e-6)
+    return [float(v) for v in m], [float(v) for v in s]
+
+
+def train(model, x, y, steps, batch=32, seed=5, log_every=0):
+    """`steps` training steps on shuffled batches; returns the list of step statistics."""
+    import torch
+    gen = torch.Generator(device="cpu").manual_seed(seed)
+    n = x.shape[0]
+    perm = torch.randperm(n, generator=gen)
+    pos = 0
+    stats = []
+    for k in range(steps):
+        if pos + batch > n:
+            perm = torch.randperm(n, generator=gen)
+            pos = 0
+        idx = perm[pos:pos + batch].cuda()
+        pos += batch
+        st = model.train_step(x.index_select(0, idx), y.index_select(0, idx))
+        stats.append(st)
+        if log_every and (k + 1) % log_every == 0:
+            print("step %d loss %.4f acc %.3f" % (k + 1, st["loss"], st["accuracy"]))
+    return stats
