@@ -34,11 +34,12 @@ def lib():
 class Grid(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
                 ("dx", C.c_double), ("dy", C.c_double), ("dz", C.c_double), ("dt", C.c_double),
-                ("bc", C.c_int * 3)]
+                ("bc", C.c_int * 3), ("order", C.c_int)]
 
     @classmethod
-    def make(cls, nx, ny, nz, dx, dy, dz, dt, bc=(0, 0, 0)):
+    def make(cls, nx, ny, nz, dx, dy, dz, dt, bc=(0, 0, 0), order=1):
         g = cls()
+        g.order = int(order)
         g.nx, g.ny, g.nz = int(nx), int(ny), int(nz)
         g.dx, g.dy, g.dz, g.dt = float(dx), float(dy), float(dz), float(dt)
         for a in range(3):
@@ -70,6 +71,8 @@ def _declare(L):
     L.orc_fdtd_e.argtypes = [C.POINTER(Grid), _D3, _D3, _D3]
     L.orc_gather.argtypes = [C.POINTER(Grid), _D3, _D3, C.c_double, C.c_double, C.c_double, _P, _P]
     L.orc_boris.argtypes = [C.c_double, _P, _P, _P]
+    L.orc_tsc.argtypes = [C.c_double]
+    L.orc_tsc.restype = C.c_double
     L.orc_vay.argtypes = [C.c_double, _P, _P, _P]
     L.orc_higuera_cary.argtypes = [C.c_double, _P, _P, _P]
     L.orc_esirkepov.argtypes = [C.POINTER(Grid), C.c_double] + [C.c_double] * 6 + [_D3]

@@ -43,6 +43,29 @@ double orc_energy_particles(const orc_species *s) {
 void orc_charge_density(const orc_grid *g, const orc_species *s, double *rho) {
     const double dV = g->dx * g->dy * g->dz;
     const int n[3] = {g->nx, g->ny, g->nz};
+    if (g->order == 2) {   /* quadratic shape on the nearest node and its two neighbours */
+        for (long p = 0; p < s->n; ++p) {
+            const double q = s->zq ? s->q * s->zq[p] : s->q;
+            const double pos[3] = {s->x[p], s->y[p], s->z[p]};
+            int m[3];
+            for (int a = 0; a < 3; ++a) m[a] = (int)floor(pos[a] + 0.5);
+            for (int c = -1; c <= 1; ++c)
+            for (int b = -1; b <= 1; ++b)
+            for (int a = -1; a <= 1; ++a) {
+                int idx[3] = {m[0] + a, m[1] + b, m[2] + c};
+                int skip = 0;
+                for (int ax = 0; ax < 3; ++ax) {
+                    if (g->bc[ax] == 0) idx[ax] = wrapi(idx[ax], n[ax]);
+                    else if (idx[ax] < 0 || idx[ax] >= n[ax]) skip = 1;
+                }
+                if (skip) continue;
+                const double wgt = orc_tsc(pos[0] - (m[0] + a)) * orc_tsc(pos[1] - (m[1] + b)) *
+                                   orc_tsc(pos[2] - (m[2] + c));
+                rho[IDX(g, idx[0], idx[1], idx[2])] += q * s->w[p] * wgt / dV;
+            }
+        }
+        return;
+    }
     for (long p = 0; p < s->n; ++p) {
         const double q = s->zq ? s->q * s->zq[p] : s->q;
         const double pos[3] = {s->x[p], s->y[p], s->z[p]};

@@ -32,6 +32,7 @@ typedef struct {
     int nx, ny, nz;
     double dx, dy, dz, dt;
     int bc[3];               /* 0 = periodic, 1 = first-order Mur fields + reflecting particles */
+    int order;               /* particle shape: 1 (CIC, also 0) or 2 (quadratic, TSC) */
 } orc_grid;
 
 /* field component staggering (Yee 1966): offset of each component in cell units */
@@ -71,6 +72,9 @@ void orc_vay(double qm_dt_half, const double e[3], const double b[3], double u[3
 void orc_higuera_cary(double qm_dt_half, const double e[3], const double b[3], double u[3]);
 void orc_esirkepov(const orc_grid *g, double qw, double x0, double y0, double z0,
                    double x1, double y1, double z1, double *J[3]);
+double orc_tsc(double d);
+void orc_esirkepov2(const orc_grid *g, double qw, double x0, double y0, double z0,
+                    double x1, double y1, double z1, double *J[3]);
 void orc_push_deposit(const orc_grid *g, const double *E[3], const double *B[3],
                       double *J[3], orc_species *s);
 void orc_gather_species(const orc_grid *g, const double *E[3], const double *B[3], orc_species *s);

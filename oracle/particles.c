@@ -69,6 +69,40 @@ static double interp(const orc_grid *g, const double *F, const double o[3], cons
     return acc;
 }
 
+/* Quadratic (TSC) shape, Esirkepov's order 2: S(d) = 3/4 - d^2 for |d| <= 1/2,
+ * (3/2 - |d|)^2 / 2 for 1/2 <= |d| <= 3/2, 0 beyond; a particle covers the
+ * node nearest to it and its two neighbours. */
+double orc_tsc(double d) {
+    const double a = fabs(d);
+    if (a <= 0.5) return 0.75 - a * a;
+    if (a <= 1.5) return 0.5 * (1.5 - a) * (1.5 - a);
+    return 0.0;
+}
+
+/* TSC interpolation of one staggered component (offsets o[3] in {0, 1/2}) */
+static double interp2(const orc_grid *g, const double *F, const double o[3], const double p[3]) {
+    int m[3];
+    double s[3];
+    for (int a = 0; a < 3; ++a) {
+        s[a] = p[a] - o[a];
+        m[a] = (int)floor(s[a] + 0.5);
+    }
+    double acc = 0.0;
+    for (int c = -1; c <= 1; ++c) {
+        int kk = resolve(g, 2, m[2] + c); if (kk < 0) continue;
+        double wz = orc_tsc(s[2] - (m[2] + c));
+        for (int b = -1; b <= 1; ++b) {
+            int jj = resolve(g, 1, m[1] + b); if (jj < 0) continue;
+            double wy = orc_tsc(s[1] - (m[1] + b));
+            for (int a = -1; a <= 1; ++a) {
+                int ii = resolve(g, 0, m[0] + a); if (ii < 0) continue;
+                acc += orc_tsc(s[0] - (m[0] + a)) * wy * wz * F[IDX(g, ii, jj, kk)];
+            }
+        }
+    }
+    return acc;
+}
+
 void orc_gather(const orc_grid *g, const double *E[3], const double *B[3],
                 double xi, double yi, double zi, double e[3], double b[3]) {
     static const double off[6][3] = {
@@ -77,8 +111,8 @@ void orc_gather(const orc_grid *g, const double *E[3], const double *B[3],
     };
     const double p[3] = {xi, yi, zi};
     for (int c = 0; c < 3; ++c) {
-        e[c] = interp(g, E[c], off[c], p);
-        b[c] = interp(g, B[c], off[3 + c], p);
+        e[c] = g->order == 2 ? interp2(g, E[c], off[c], p) : interp(g, E[c], off[c], p);
+        b[c] = g->order == 2 ? interp2(g, B[c], off[3 + c], p) : interp(g, B[c], off[3 + c], p);
     }
 }
 
@@ -191,6 +225,46 @@ void orc_esirkepov(const orc_grid *g, double qw, double x0, double y0, double z0
     }
 }
 
+/* Esirkepov with the quadratic shape: per axis the window of 4 nodes that
+ * holds both the old and the new 3-node support (base = the smaller of the
+ * two nearest nodes, minus one), the same W formula as for CIC, prefix-summed
+ * over the 3 faces between the window's nodes. */
+void orc_esirkepov2(const orc_grid *g, double qw, double x0, double y0, double z0,
+                    double x1, double y1, double z1, double *J[3]) {
+    const double p0[3] = {x0, y0, z0}, p1[3] = {x1, y1, z1};
+    int base[3];
+    double S0[3][4], DS[3][4];
+    for (int a = 0; a < 3; ++a) {
+        const int m0 = (int)floor(p0[a] + 0.5), m1 = (int)floor(p1[a] + 0.5);
+        base[a] = (m0 < m1 ? m0 : m1) - 1;
+        for (int k = 0; k < 4; ++k) {
+            S0[a][k] = orc_tsc(p0[a] - (base[a] + k));
+            DS[a][k] = orc_tsc(p1[a] - (base[a] + k)) - S0[a][k];
+        }
+    }
+    const double dvol[3] = {g->dy * g->dz, g->dx * g->dz, g->dx * g->dy};
+    for (int c = 0; c < 3; ++c) {
+        const int p = (c + 1) % 3, q = (c + 2) % 3;
+        const double fac = -qw / (g->dt * dvol[c]);
+        for (int bq = 0; bq < 4; ++bq)
+        for (int bp = 0; bp < 4; ++bp) {
+            double acc = 0.0;
+            for (int a = 0; a < 3; ++a) {
+                double W = DS[c][a] * (S0[p][bp] * S0[q][bq] + 0.5 * DS[p][bp] * S0[q][bq]
+                                       + 0.5 * S0[p][bp] * DS[q][bq] + DS[p][bp] * DS[q][bq] / 3.0);
+                acc += W;
+                if (acc == 0.0) continue;
+                int idx[3];
+                idx[c] = resolve(g, c, base[c] + a);
+                idx[p] = resolve(g, p, base[p] + bp);
+                idx[q] = resolve(g, q, base[q] + bq);
+                if (idx[0] < 0 || idx[1] < 0 || idx[2] < 0) continue;
+                J[c][IDX(g, idx[0], idx[1], idx[2])] += fac * acc;
+            }
+        }
+    }
+}
+
 void orc_push_deposit(const orc_grid *g, const double *E[3], const double *B[3],
                       double *J[3], orc_species *s) {
     const double dt = g->dt;
@@ -217,7 +291,8 @@ void orc_push_deposit(const orc_grid *g, const double *E[3], const double *B[3],
                 else if (x1[a] > L)   { x1[a] = 2.0 * L - x1[a]; u[a] = -u[a]; }
             }
         }
-        if (q != 0.0) orc_esirkepov(g, q * s->w[p], x0[0], x0[1], x0[2], x1[0], x1[1], x1[2], J);
+        if (q != 0.0 && g->order == 2) orc_esirkepov2(g, q * s->w[p], x0[0], x0[1], x0[2], x1[0], x1[1], x1[2], J);
+        else if (q != 0.0) orc_esirkepov(g, q * s->w[p], x0[0], x0[1], x0[2], x1[0], x1[1], x1[2], J);
         for (int a = 0; a < 3; ++a) {
             if (g->bc[a] == 0) {             /* periodic image in [0, n) */
                 double L = (double)n[a];

@@ -72,12 +72,12 @@ def courant_dt(d, cfl_frac):
 
 class OracleSim:
     def __init__(self, nx, ny, nz, dx, dy=None, dz=None, dt=0.0, cfl_frac=0.95, bc=(0, 0, 0), laser=None,
-                 lambda_um=0.8, seed=1):
+                 lambda_um=0.8, seed=1, shape_order=1):
         dy = dx if dy is None else dy
         dz = dx if dz is None else dz
         if not dt > 0:
             dt = courant_dt((dx, dy, dz), cfl_frac)
-        self.g = Grid.make(nx, ny, nz, dx, dy, dz, dt, bc)
+        self.g = Grid.make(nx, ny, nz, dx, dy, dz, dt, bc, order=shape_order)
         self.E = zeros_field(self.g)
         self.B = zeros_field(self.g)
         self.J = zeros_field(self.g)
