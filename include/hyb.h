@@ -81,6 +81,13 @@ typedef struct {
     void *stream;             /* cudaStream_t the context runs on (NULL = legacy default) */
     void *arena_dev;          /* optional caller-provided device arena (e.g. a torch tensor) */
     size_t arena_bytes;       /* its size; all library buffers come from it when non-NULL */
+    /* Particle shape of the gather and the Esirkepov deposition: 1 (or 0) the
+     * linear CIC shape, 2 the quadratic TSC shape (Esirkepov's scheme for any
+     * shape order; smoother, less grid noise).  The quadratic shape needs
+     * periodic axes (its stencil reaches past an absorbing wall) and a context
+     * without fluid <-> particle conversions (those deposit with CIC);
+     * HYB_EINVAL otherwise. */
+    int shape_order;
 } hyb_grid_desc;
 
 /*

@@ -32,7 +32,7 @@ class hyb_grid_desc(C.Structure):
                 ("t_peak", C.c_double), ("y_c", C.c_double), ("z_c", C.c_double),
                 ("x_src", C.c_int), ("pol", C.c_int),
                 ("seed", C.c_uint32), ("tile", C.c_int),
-                ("stream", C.c_void_p), ("arena_dev", C.c_void_p), ("arena_bytes", C.c_size_t)]
+                ("stream", C.c_void_p), ("arena_dev", C.c_void_p), ("arena_bytes", C.c_size_t), ("shape_order", C.c_int)]
 
 
 class hyb_species_desc(C.Structure):

@@ -202,6 +202,10 @@ hyb_status hyb_init_grid(const hyb_grid_desc *d, hyb_ctx **out) {
         dt = d->cfl_frac * courant;
     }
     if (dt >= courant) return set_error(HYB_EINVAL, "dt at or above the Courant limit");
+    const int order = d->shape_order == 0 ? 1 : d->shape_order;
+    if (order != 1 && order != 2) return set_error(HYB_EINVAL, "shape_order must be 1 or 2");
+    if (order == 2 && (d->bc[0] || d->bc[1] || d->bc[2]))
+        return set_error(HYB_EINVAL, "the quadratic shape needs periodic axes");
     if (d->laser_kind == HYB_LASER_GAUSS) {
         if (d->x_src < 0 || d->x_src >= n[0]) return set_error(HYB_EINVAL, "laser x_src outside the grid");
         if (d->pol != 1 && d->pol != 2) return set_error(HYB_EINVAL, "laser pol must be 1 (y) or 2 (z)");
@@ -229,6 +233,7 @@ hyb_status hyb_init_grid(const hyb_grid_desc *d, hyb_ctx **out) {
     g.dt = (float)dt;
     g.dt_d = dt;
     g.seed = d->seed;
+    g.order = order;
 
     if (d->stream) {
         c->stream = (cudaStream_t)d->stream;
@@ -251,8 +256,9 @@ hyb_status hyb_init_grid(const hyb_grid_desc *d, hyb_ctx **out) {
     };
     const size_t fbytes = sizeof(float) * 3 * (size_t)g.N;
     c->mur_plane = std::max({(long long)n[1] * n[2], (long long)n[0] * n[2], (long long)n[0] * n[1]});
-    const int G = T + 3;
-    c->jframe = 4LL * G * G * G;  // 3 current components in the step, 4 moments in a conversion
+    // 3 current components (of the shape order's frame) in the step, 4 CIC moments in a conversion
+    const long long G1 = T + 3, Gk = T + 2 * order + 1;
+    c->jframe = std::max(4 * G1 * G1 * G1, 3 * Gk * Gk * Gk);
     c->red_blocks = 152 * 8;   // enough warps for the loads of the reductions to cover the memory latency
     if (ctx_alloc(c, (void **)&c->E, fbytes) || ctx_alloc(c, (void **)&c->B, fbytes) ||
         ctx_alloc(c, (void **)&c->J, fbytes) ||
@@ -662,6 +668,8 @@ hyb_status hyb_classify(hyb_ctx *c, const hyb_model *model, float *p_mean_dev, f
         const int sid = c->regime.to_species[f];
         if (sid >= 0 && (c->sp[sid].q != (double)c->fluids[f].q || c->sp[sid].m != c->fluids[f].m_d))
             return set_error(HYB_EINVAL, "a fluid converts into a species of the same charge and mass");
+        if (sid >= 0 && c->g.order != 1)
+            return set_error(HYB_EINVAL, "conversions deposit with the CIC shape: not with shape_order 2");
     }
     hyb_status s;
     c->launches_classify = 0;

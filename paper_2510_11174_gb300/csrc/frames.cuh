@@ -18,7 +18,10 @@
 
 namespace hyb {
 
-__host__ __device__ constexpr int frame_G(int T) { return T + 3; }  // frame edge in nodes
+// frame edge in nodes: a shape of order k (1 CIC, 2 quadratic) reaches k nodes
+// below the tile and k + 1 above it, so the frame spans T + 2k + 1 nodes
+// starting k nodes below the tile's first node
+__host__ __device__ constexpr int frame_G(int T, int order = 1) { return T + 2 * order + 1; }
 
 // 2^k as FP32 for k in [-126, 127] (exact)
 __device__ __forceinline__ float pow2f(int k) { return __int_as_float((k + 127) << 23); }
@@ -55,24 +58,25 @@ __device__ __forceinline__ float block_max_read(const int *slots) {
     return __int_as_float(b);
 }
 
-// Frames that cover node i along axis a: the frame of tile tt covers nodes
-// tt*T-1 .. tt*T+T+1; node i of tile `own` sits at local i - own*T + 1 in
-// [1, T]; the previous tile covers it at local + T when local <= 2, the next
-// at local - T when local == T.
-__device__ __forceinline__ int frame_cands(const GridDev &g, int a, int i, int tile[3], int loc[3]) {
+// Frames that cover node i along axis a: the frame of tile tt (shape order k)
+// covers nodes tt*T - k .. tt*T + T + k; node i sits at r = i - own*T in
+// [0, T) of its own tile, at local r + k in that tile's frame; the previous
+// tile's frame reaches it when r <= k (at local r + T + k), the next tile's
+// when r >= T - k (at local r - T + k).
+__device__ __forceinline__ int frame_cands(const GridDev &g, int a, int i, int order, int tile[3], int loc[3]) {
     const int T = g.T, nt = g.nt[a];
-    const int own = i >> g.tshift, l = i - own * T + 1;
+    const int own = i >> g.tshift, r = i - own * T;
     int n = 0;
-    if (l <= 2) {
+    if (r <= order) {
         int pt = own - 1;
         if (pt < 0 && g.bc[a] == 0) pt += nt;
-        if (pt >= 0) { tile[n] = pt; loc[n] = l + T; ++n; }
+        if (pt >= 0) { tile[n] = pt; loc[n] = r + T + order; ++n; }
     }
-    tile[n] = own; loc[n] = l; ++n;
-    if (l == T) {
+    tile[n] = own; loc[n] = r + order; ++n;
+    if (r >= T - order) {
         int nt2 = own + 1;
         if (nt2 >= nt && g.bc[a] == 0) nt2 -= nt;
-        if (nt2 < nt) { tile[n] = nt2; loc[n] = 0; ++n; }
+        if (nt2 < nt) { tile[n] = nt2; loc[n] = r - T + order; ++n; }
     }
     return n;
 }
@@ -81,13 +85,13 @@ __device__ __forceinline__ int frame_cands(const GridDev &g, int a, int i, int t
 // with `ncomp` components per tile (frames of tiles whose flag is 0 are skipped)
 template <int NC>
 __device__ __forceinline__ void frame_gather(const GridDev &g, const float *__restrict__ scratch,
-                                             const int *__restrict__ valid, int ncomp, int i, int j, int k,
-                                             float acc[NC]) {
-    const int G = frame_G(g.T), G3 = G * G * G;
+                                             const int *__restrict__ valid, int ncomp, int order, int i, int j,
+                                             int k, float acc[NC]) {
+    const int G = frame_G(g.T, order), G3 = G * G * G;
     int tx[3], lx[3], ty[3], ly[3], tz[3], lz[3];
-    const int nxc = frame_cands(g, 0, i, tx, lx);
-    const int nyc = frame_cands(g, 1, j, ty, ly);
-    const int nzc = frame_cands(g, 2, k, tz, lz);
+    const int nxc = frame_cands(g, 0, i, order, tx, lx);
+    const int nyc = frame_cands(g, 1, j, order, ty, ly);
+    const int nzc = frame_cands(g, 2, k, order, tz, lz);
 #pragma unroll
     for (int q = 0; q < NC; ++q) acc[q] = 0.0f;
     for (int cz = 0; cz < nzc; ++cz)

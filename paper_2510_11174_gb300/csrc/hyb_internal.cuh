@@ -29,6 +29,7 @@ struct GridDev {
     double dd[3];      // dx, dy, dz in FP64 (reductions)
     double dt_d;       // the same step in FP64 (laser phase, time)
     uint32_t seed;     // Philox key word 0
+    int order;         // particle shape: 1 CIC, 2 quadratic (periodic axes only)
 };
 
 __host__ __device__ inline long long cidx(const GridDev &g, int i, int j, int k) {
@@ -323,7 +324,7 @@ void launch_laser_source(const GridDev &g, const hyb_grid_desc &d, const float *
 void launch_step_inc(long long *step_dev, cudaStream_t st);
 void launch_wait_selftest(long long polls, int *status, cudaStream_t st);
 
-size_t push_smem_bytes(int T);
+size_t push_smem_bytes(int T, int order);
 void launch_push_deposit(const GridDev &g, const float *E, const float *B, const SpDev *sps_dev, int nsp,
                          const QedDev &qd, float *jscratch, int *jvalid, int *status, const long long *step_dev,
                          cudaStream_t st);

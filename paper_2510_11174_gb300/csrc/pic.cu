@@ -33,7 +33,8 @@
 
 namespace hyb {
 
-__host__ __device__ constexpr int frame_F(int T) { return T + 2; }  // field frame edge
+// field frame edge: a shape of order k gathers from k nodes below the tile to k - 1 above it
+__host__ __device__ constexpr int frame_F(int T, int order = 1) { return T + 2 * order; }
 
 static constexpr int PUSH_THREADS = 256;
 static constexpr int PUSH_QCAP = 64;  // per-warp queue of cell-crossing particles
@@ -42,8 +43,8 @@ __host__ __device__ constexpr size_t align16(size_t b) { return (b + 15) & ~(siz
 
 // the current frame (3 components, 64-bit fixed point), the fields, then the
 // per-warp queues (two float4 per entry)
-size_t push_smem_bytes(int T) {
-    const int F = frame_F(T), G = frame_G(T);
+size_t push_smem_bytes(int T, int order) {
+    const int F = frame_F(T, order), G = frame_G(T, order);
     return align16(sizeof(unsigned long long) * 3 * (size_t)G * G * G) + align16(sizeof(float) * 6 * (size_t)F * F * F) +
            2 * sizeof(float4) * (PUSH_THREADS / 32) * PUSH_QCAP;
 }
@@ -244,6 +245,92 @@ __device__ __forceinline__ void deposit_general(unsigned long long *__restrict__
     }
 }
 
+// Quadratic (TSC) shape: S(d) = 3/4 - d^2 (|d| <= 1/2), (3/2 - |d|)^2 / 2
+// (1/2 <= |d| <= 3/2), 0 beyond
+__device__ __forceinline__ float tsc(float d) {
+    const float a = fabsf(d);
+    const float b = 1.5f - a;
+    return a <= 0.5f ? 0.75f - a * a : (a <= 1.5f ? 0.5f * b * b : 0.0f);
+}
+
+// TSC weights of one axis around the node nearest to s (staggering already
+// removed): local index of the first of the three nodes and their weights
+__device__ __forceinline__ void tsc_axis(float s, int o, int &l, float w[3]) {
+    const float m = floorf(s + 0.5f);
+    const float d = s - m;                 // in [-1/2, 1/2)
+    l = (int)m - 1 - o;
+    const float a = 0.5f - d, c = 0.5f + d;
+    w[0] = 0.5f * a * a;
+    w[1] = 0.75f - d * d;
+    w[2] = 0.5f * c * c;
+}
+
+template <int F>
+__device__ __forceinline__ float interp27(const float *__restrict__ f, int bx, int by, int bz, const float wx[3],
+                                          const float wy[3], const float wz[3]) {
+    float acc = 0.0f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        float row = 0.0f;
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            const float *r = f + ((bz + c) * F + by + b) * F + bx;
+            row = fmaf(wy[b], fmaf(wx[2], r[2], fmaf(wx[1], r[1], wx[0] * r[0])), row);
+        }
+        acc = fmaf(wz[c], row, acc);
+    }
+    return acc;
+}
+
+// Esirkepov with the quadratic shape: per axis the 4-node window holding the
+// old and new 3-node supports (base = the smaller nearest node, minus one),
+// W as for CIC, prefix-summed over the window's 3 inner faces
+template <int G>
+__device__ __forceinline__ void deposit_quadratic(unsigned long long *__restrict__ sj, const float x0[3],
+                                                  const float x1[3], const int o[3], float qw, const float jfac[3]) {
+    constexpr int G3 = G * G * G;
+    int lb[3];
+    float S0[3][4], DS[3][4];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int m0 = (int)floorf(x0[a] + 0.5f), m1 = (int)floorf(x1[a] + 0.5f);
+        const int gb = (m0 < m1 ? m0 : m1) - 1;
+        lb[a] = gb - o[a];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            S0[a][k] = tsc(x0[a] - (float)(gb + k));
+            DS[a][k] = tsc(x1[a] - (float)(gb + k)) - S0[a][k];
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const int pa = (c + 1) % 3, qa = (c + 2) % 3;
+        const float fac = qw * jfac[c];
+        unsigned long long *Jc = sj + c * G3;
+#pragma unroll
+        for (int bq = 0; bq < 4; ++bq) {
+            const float caq = fmaf(0.5f, DS[qa][bq], S0[qa][bq]);
+            const float cbq = fmaf(1.0f / 3.0f, DS[qa][bq], 0.5f * S0[qa][bq]);
+#pragma unroll
+            for (int bp = 0; bp < 4; ++bp) {
+                const float cross = fmaf(DS[pa][bp], cbq, S0[pa][bp] * caq);
+                float acc = 0.0f;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    acc += DS[c][a] * cross;
+                    if (acc != 0.0f) {
+                        int l3[3];
+                        l3[c] = lb[c] + a;
+                        l3[pa] = lb[pa] + bp;
+                        l3[qa] = lb[qa] + bq;
+                        atomicAdd(&Jc[(l3[2] * G + l3[1]) * G + l3[0]], fix_of(fac * acc));
+                    }
+                }
+            }
+        }
+    }
+}
+
 // One CTA per tile: stage E, B of the tile and a one-node halo, push every
 // particle of every species, deposit its current into the tile's fixed-point
 // frame, apply the stochastic events, write it back or send it to the
@@ -251,14 +338,14 @@ __device__ __forceinline__ void deposit_general(unsigned long long *__restrict__
 // particles that crossed a cell face wait in a per-warp queue and are
 // deposited 32 at a time with the full 3-node stencil, so that the long
 // stencil runs with every lane of the warp busy.
-template <int T>
+template <int T, int ORDER>
 __global__ void __launch_bounds__(PUSH_THREADS, 3) k_push_deposit(GridDev g, const float *__restrict__ E,
                                                                   const float *__restrict__ B,
                                                                   const SpDev *__restrict__ sps, int nsp,
                                                                   float *__restrict__ jscratch,
                                                                   int *__restrict__ jvalid, int *__restrict__ status,
                                                                   const long long *__restrict__ step_dev, QedDev qd) {
-    constexpr int F = frame_F(T), G = frame_G(T);
+    constexpr int F = frame_F(T, ORDER), G = frame_G(T, ORDER);
     constexpr int F3 = F * F * F, G3 = G * G * G;
     extern __shared__ __align__(16) unsigned char smraw[];
     unsigned long long *sj = reinterpret_cast<unsigned long long *>(smraw);  // 3 current components, G^3 each
@@ -304,7 +391,7 @@ __global__ void __launch_bounds__(PUSH_THREADS, 3) k_push_deposit(GridDev g, con
         block_max_put(qwm, s_qwmax);
     }
     const int tx = t % g.nt[0], ty = (t / g.nt[0]) % g.nt[1], tz = t / (g.nt[0] * g.nt[1]);
-    const int o[3] = {tx * T - 1, ty * T - 1, tz * T - 1};
+    const int o[3] = {tx * T - ORDER, ty * T - ORDER, tz * T - ORDER};  // frame origin
     const long long N = g.N;
 
     for (int l = threadIdx.x; l < F3; l += PUSH_THREADS) {
@@ -400,7 +487,7 @@ __global__ void __launch_bounds__(PUSH_THREADS, 3) k_push_deposit(GridDev g, con
                 for (int a = 0; a < 3; ++a) {
                     int ci = (int)floorf(x0[a]);
                     if (g.bc[a] && ci == g.n[a] - 1 && x0[a] == (float)(g.n[a] - 1)) ci = g.n[a] - 2;
-                    inside = inside && isfinite(x0[a]) && ci >= o[a] + 1 && ci <= o[a] + T &&
+                    inside = inside && isfinite(x0[a]) && ci >= o[a] + ORDER && ci <= o[a] + ORDER + T - 1 &&
                              (g.bc[a] == 0 || ci <= g.n[a] - 2);
                 }
                 if (!inside) {
@@ -410,15 +497,32 @@ __global__ void __launch_bounds__(PUSH_THREADS, 3) k_push_deposit(GridDev g, con
             }
             if (act) {
                 // ---- gather E^n, B^n at x^n
-                const AxisW ax = axis_weights(g, 0, x0[0], o[0]);
-                const AxisW ay = axis_weights(g, 1, x0[1], o[1]);
-                const AxisW az = axis_weights(g, 2, x0[2], o[2]);
-                e[0] = interp8<F>(sEx, ax.lh, ay.li, az.li, ax.fh, ay.fi, az.fi);
-                e[1] = interp8<F>(sEy, ax.li, ay.lh, az.li, ax.fi, ay.fh, az.fi);
-                e[2] = interp8<F>(sEz, ax.li, ay.li, az.lh, ax.fi, ay.fi, az.fh);
-                b[0] = interp8<F>(sBx, ax.li, ay.lh, az.lh, ax.fi, ay.fh, az.fh);
-                b[1] = interp8<F>(sBy, ax.lh, ay.li, az.lh, ax.fh, ay.fi, az.fh);
-                b[2] = interp8<F>(sBz, ax.lh, ay.lh, az.li, ax.fh, ay.fh, az.fi);
+                if constexpr (ORDER == 1) {
+                    const AxisW ax = axis_weights(g, 0, x0[0], o[0]);
+                    const AxisW ay = axis_weights(g, 1, x0[1], o[1]);
+                    const AxisW az = axis_weights(g, 2, x0[2], o[2]);
+                    e[0] = interp8<F>(sEx, ax.lh, ay.li, az.li, ax.fh, ay.fi, az.fi);
+                    e[1] = interp8<F>(sEy, ax.li, ay.lh, az.li, ax.fi, ay.fh, az.fi);
+                    e[2] = interp8<F>(sEz, ax.li, ay.li, az.lh, ax.fi, ay.fi, az.fh);
+                    b[0] = interp8<F>(sBx, ax.li, ay.lh, az.lh, ax.fi, ay.fh, az.fh);
+                    b[1] = interp8<F>(sBy, ax.lh, ay.li, az.lh, ax.fh, ay.fi, az.fh);
+                    b[2] = interp8<F>(sBz, ax.lh, ay.lh, az.li, ax.fh, ay.fh, az.fi);
+                } else {
+                    // quadratic shape: integer (i) and half-integer (h) staggering per axis
+                    int li[3], lh[3];
+                    float wi[3][3], wh[3][3];
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        tsc_axis(x0[a], o[a], li[a], wi[a]);
+                        tsc_axis(x0[a] - 0.5f, o[a], lh[a], wh[a]);
+                    }
+                    e[0] = interp27<F>(sEx, lh[0], li[1], li[2], wh[0], wi[1], wi[2]);
+                    e[1] = interp27<F>(sEy, li[0], lh[1], li[2], wi[0], wh[1], wi[2]);
+                    e[2] = interp27<F>(sEz, li[0], li[1], lh[2], wi[0], wi[1], wh[2]);
+                    b[0] = interp27<F>(sBx, li[0], lh[1], lh[2], wi[0], wh[1], wh[2]);
+                    b[1] = interp27<F>(sBy, lh[0], li[1], lh[2], wh[0], wi[1], wh[2]);
+                    b[2] = interp27<F>(sBz, lh[0], lh[1], li[2], wh[0], wh[1], wi[2]);
+                }
 
                 // ---- momentum update (species-uniform choice: no divergence)
                 const float h = q * qm_half;
@@ -449,7 +553,7 @@ __global__ void __launch_bounds__(PUSH_THREADS, 3) k_push_deposit(GridDev g, con
 
             // ---- Esirkepov deposit into the shared frame: particles that stay
             // in their cell now, the others through the warp's queue
-            bool same_cell = true;
+            bool same_cell = ORDER == 1;   // the quadratic stencil always takes the queue
 #pragma unroll
             for (int a = 0; a < 3; ++a) same_cell = same_cell && floorf(x0[a]) == floorf(x1[a]);
             const bool dep = act && q != 0.0f;
@@ -469,7 +573,8 @@ __global__ void __launch_bounds__(PUSH_THREADS, 3) k_push_deposit(GridDev g, con
             if (qn >= 32) {
                 const float4 A = qa[qn - 32 + lane], Bq = qb[qn - 32 + lane];
                 const float y0[3] = {A.x, A.y, A.z}, y1[3] = {Bq.x, Bq.y, Bq.z};
-                deposit_general<G>(sj, y0, y1, o, A.w, jfac);
+                if constexpr (ORDER == 1) deposit_general<G>(sj, y0, y1, o, A.w, jfac);
+                else deposit_quadratic<G>(sj, y0, y1, o, A.w, jfac);
                 qn -= 32;
                 __syncwarp();
             }
@@ -601,7 +706,8 @@ __global__ void __launch_bounds__(PUSH_THREADS, 3) k_push_deposit(GridDev g, con
         if (lane < qn) {
             const float4 A = qa[lane], Bq = qb[lane];
             const float y0[3] = {A.x, A.y, A.z}, y1[3] = {Bq.x, Bq.y, Bq.z};
-            deposit_general<G>(sj, y0, y1, o, A.w, jfac);
+            if constexpr (ORDER == 1) deposit_general<G>(sj, y0, y1, o, A.w, jfac);
+            else deposit_quadratic<G>(sj, y0, y1, o, A.w, jfac);
         }
         __syncwarp();
         // per-tile tallies: warp sums, then shared accumulators, then one add per tile
@@ -653,7 +759,7 @@ __global__ void k_j_reduce(GridDev g, const float *__restrict__ jscratch, const 
     if (i >= nx) return;
     const long long c = ((long long)k * ny + j) * nx + i;
     float acc[3];
-    frame_gather<3>(g, jscratch, jvalid, 3, i, j, k, acc);
+    frame_gather<3>(g, jscratch, jvalid, 3, g.order, i, j, k, acc);
     J[c] = acc[0];
     J[g.N + c] = acc[1];
     J[2 * g.N + c] = acc[2];
@@ -791,19 +897,22 @@ static inline unsigned blocks_for(long long n, int b) { return (unsigned)((n + b
 void launch_push_deposit(const GridDev &g, const float *E, const float *B, const SpDev *sps_dev, int nsp,
                          const QedDev &qd, float *jscratch, int *jvalid, int *status, const long long *step_dev,
                          cudaStream_t st) {
-    const size_t smem = push_smem_bytes(g.T);
-    if (g.T == 8) {
-        static bool set8 = false;  // opt in to more than 48 KB of dynamic shared memory once
-        if (!set8) {
-            cudaFuncSetAttribute(k_push_deposit<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)push_smem_bytes(8));
-            set8 = true;
+    const size_t smem = push_smem_bytes(g.T, g.order);
+    // opt in to more than 48 KB of dynamic shared memory, once per instance
+    static bool set[4] = {false, false, false, false};
+    auto launch = [&](auto kern, int slot) {
+        if (!set[slot]) {
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            set[slot] = true;
         }
-        k_push_deposit<8><<<g.ntiles, PUSH_THREADS, smem, st>>>(g, E, B, sps_dev, nsp, jscratch, jvalid, status,
-                                                                step_dev, qd);
+        kern<<<g.ntiles, PUSH_THREADS, smem, st>>>(g, E, B, sps_dev, nsp, jscratch, jvalid, status, step_dev, qd);
+    };
+    if (g.order == 2) {
+        if (g.T == 8) launch(k_push_deposit<8, 2>, 2);
+        else launch(k_push_deposit<4, 2>, 3);
     } else {
-        k_push_deposit<4><<<g.ntiles, PUSH_THREADS, smem, st>>>(g, E, B, sps_dev, nsp, jscratch, jvalid, status,
-                                                                step_dev, qd);
+        if (g.T == 8) launch(k_push_deposit<8, 1>, 0);
+        else launch(k_push_deposit<4, 1>, 1);
     }
 }
 

@@ -135,7 +135,7 @@ __global__ void k_density_gather(GridDev g, const float *__restrict__ scratch, c
     const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
     if (i >= nx) return;
     float acc[1];
-    frame_gather<1>(g, scratch, valid, 1, i, j, k, acc);
+    frame_gather<1>(g, scratch, valid, 1, 1, i, j, k, acc);
     ne[((long long)k * ny + j) * nx + i] = acc[0];
 }
 
@@ -330,7 +330,7 @@ __global__ void k_rho_gather(GridDev g, const float *__restrict__ scratch, const
     const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
     if (i >= nx) return;
     float acc[1];
-    frame_gather<1>(g, scratch, valid, 1, i, j, k, acc);
+    frame_gather<1>(g, scratch, valid, 1, 1, i, j, k, acc);
     const long long c = ((long long)k * ny + j) * nx + i;
     if (acc[0] != 0.0f) rho_bg[c] += acc[0];
 }
@@ -424,7 +424,7 @@ __global__ void k_moments_gather(GridDev g, const float *__restrict__ scratch, c
     const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
     if (i >= nx) return;
     float acc[4];
-    frame_gather<4>(g, scratch, valid, 4, i, j, k, acc);
+    frame_gather<4>(g, scratch, valid, 4, 1, i, j, k, acc);
     const long long c = ((long long)k * ny + j) * nx + i;
     const float n0 = f.n[c];
     if (acc[0] == 0.0f && acc[1] == 0.0f && acc[2] == 0.0f && acc[3] == 0.0f) {

@@ -38,7 +38,7 @@ struct StateHeader {
     uint32_t epoch;
     int32_t fluids_idle;
     int32_t status;
-    int32_t pad;
+    int32_t order;
     long long mur_plane;
     uint64_t total_bytes;
     hyb_regime_desc regime;
@@ -156,6 +156,7 @@ hyb_status hyb_get_state(hyb_ctx *c, void *buf, size_t cap, size_t *size_out) {
     h.epoch = c->epoch;
     h.fluids_idle = c->fluids_idle ? 1 : 0;
     h.status = status;
+    h.order = g.order;
     h.mur_plane = c->mur_plane;
     h.total_bytes = bytes;
     h.regime = c->regime;
@@ -240,7 +241,8 @@ hyb_status hyb_set_state(hyb_ctx *c, const void *buf, size_t size) {
     if (std::memcmp(h.magic, STATE_MAGIC, 8) != 0 || h.version != STATE_VERSION || h.header_bytes != sizeof(h))
         return set_error(HYB_EINVAL, "not a state image of this library version");
     if (h.total_bytes != size) return set_error(HYB_EINVAL, "state image size does not match its header");
-    bool same = h.T == g.T && h.seed == g.seed && h.dt == g.dt_d && h.mur_plane == c->mur_plane;
+    bool same = h.T == g.T && h.order == g.order && h.seed == g.seed && h.dt == g.dt_d &&
+                h.mur_plane == c->mur_plane;
     for (int a = 0; a < 3; ++a) same = same && h.n[a] == g.n[a] && h.bc[a] == g.bc[a] && h.d[a] == g.dd[a];
     if (!same) return set_error(HYB_EINVAL, "state image of a different grid, time step or seed");
     if (h.n_species != (int)c->sp.size() || h.n_fluids != (int)c->fluids.size())

@@ -48,7 +48,7 @@ class Simulation:
     """
 
     def __init__(self, nx, ny, nz, dx, dy=None, dz=None, dt=0.0, cfl_frac=0.95, bc=(0, 0, 0),
-                 lambda_um=0.8, laser=None, seed=1, tile=8, stream=None, arena=None):
+                 lambda_um=0.8, laser=None, seed=1, tile=8, stream=None, arena=None, shape_order=1):
         self._lib = _abi.load()
         d = _abi.hyb_grid_desc()
         d.nx, d.ny, d.nz = nx, ny, nz
@@ -66,6 +66,7 @@ class Simulation:
             d.x_src, d.pol = int(laser["x_src"]), int(laser.get("pol", 1))
         d.seed = seed
         d.tile = tile
+        d.shape_order = shape_order
         self.torch_stream = None
         if stream is None:
             # the legacy default stream cannot be captured into a CUDA graph:
