@@ -63,6 +63,8 @@ def workloads():
         "carbon_slab_128": ("pic", lambda seed: dict(inputs.carbon_slab(seed=seed + 1), preroll=PREROLL_CARBON)),
         # classifier training: 4096 method-generated 32^3 x 6 patches, batch 32 (one step = one Adam step)
         "train_classifier_4096x32": ("train", None),
+        # field-surrogate training: 2048 method-generated pairs of 16^3 x 10 node states 5 steps apart, batch 32
+        "train_surrogate_2048x16": ("train_surrogate", None),
     }
 
 
@@ -170,6 +172,11 @@ NCU_PUSH_BYTES_PER_PARTICLE = 254.0e6 / 4784128
 # gradient of layers 3..1 (2 * 27 * (32*32 + 32*16 + 16*1) = 83 808; layer 0 needs
 # none) and weight gradient (94 176)
 TRAIN_FLOP_PER_CELL = 94176 + 83808 + 94176
+# field surrogate: forward 2*27*sum(ci*co) = 820 908 FLOP per cell, the data
+# gradient of layers 5..1 (813 888) and the weight gradient (820 908)
+SUR_FWD_FLOP_PER_CELL = 2 * 27 * (10 * 13 + 13 * 32 + 32 * 64 + 64 * 128 + 128 * 32 + 32 * 10)
+SUR_TRAIN_FLOP_PER_CELL = 2 * SUR_FWD_FLOP_PER_CELL + 2 * 27 * (13 * 32 + 32 * 64 + 64 * 128 + 128 * 32 + 32 * 10)
+SUR_PRETRAIN_STEPS = 600   # untimed training before the timed steps (the accuracy figures)
 
 
 def trained_model(P, stream, n_patches=1024, steps=300, runs=4):
@@ -329,6 +336,8 @@ def run_ours(args, rank, world):
         return run_scan(args, P, torch)
     if kind == "train":
         return run_train(args, P, torch, stream)
+    if kind == "train_surrogate":
+        return run_train_surrogate(args, P, torch, stream)
     inp = gen(1 + rank)
     g = inp["grid"]
     cells = g["nx"] * g["ny"] * g["nz"]
@@ -509,6 +518,104 @@ def run_train(args, P, torch, stream):
                                  "the weight gradients run on the CUDA cores"},
             "loss_first": first[0]["loss"] if first else None, "loss_last": st[-1]["loss"],
             "accuracy_last": st[-1]["accuracy"], "clocks": clk, "gpu_launches": None}
+
+
+def run_train_surrogate(args, P, torch, stream):
+    """Field-surrogate training on method-generated data: 2048 + 256 held-out
+    pairs of 16^3 x 10 node states (E, B, J, rho) 5 steps apart from ramp +
+    slab runs; SUR_PRETRAIN_STEPS untimed Adam steps, then W warm-up and K
+    timed steps at batch 32 between CUDA events on the library's stream; the
+    held-out pairs scored per channel (R^2, MSE of the normalised values) with
+    the MC-dropout mean, and the MC spread."""
+    from paper_2510_11174_gb300 import training
+    t0 = time.perf_counter()
+    x, t = training.generate_state_pairs(n_pairs=2048 + 256, stream=stream)
+    gen_s = time.perf_counter() - t0
+    xtr, ttr, xte, tte = x[:2048], t[:2048], x[2048:], t[2048:]
+    m_ = xtr.mean(dim=(0, 2, 3, 4))
+    s_ = xtr.std(dim=(0, 2, 3, 4)).clamp_min(1e-6)
+    mean, std = [float(v) for v in m_], [float(v) for v in s_]
+    m = P.Surrogate(dropout=0.1, mc_passes=MC_PASSES, seed=11, mean=mean, std=std, stream=stream.cuda_stream)
+    t1 = time.perf_counter()
+    pre = training.train_surrogate(m, xtr, ttr, SUR_PRETRAIN_STEPS)
+    pre_s = time.perf_counter() - t1
+    training.train_surrogate(m, xtr, ttr, args.warmup, seed=6)
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    st = training.train_surrogate(m, xtr, ttr, args.steps, seed=7)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    # held-out accuracy: MC-dropout mean prediction, and the persistence baseline (t predicted by x)
+    pm, ps = [], []
+    for k in range(0, xte.shape[0], 32):
+        a, b = m.mc(xte[k:k + 32])
+        pm.append(a)
+        ps.append(b)
+    pm, ps = torch.cat(pm), torch.cat(ps)
+    torch.cuda.synchronize()
+    r2, mse = training.r2_mse(pm, tte, mean, std)
+    r2_keep, mse_keep = training.r2_mse(xte, tte, mean, std)
+    sd = torch.tensor(std, device=ps.device).view(1, -1, 1, 1, 1)
+    cells = 32 * 16 ** 3
+    flop = SUR_TRAIN_FLOP_PER_CELL * cells
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    pk = peaks.get("bf16_tflops_sustained", 1700.0)
+    achieved = flop * args.steps / (ms * 1e-3) / 1e12
+    m.close()
+    names = ["Ex", "Ey", "Ez", "Bx", "By", "Bz", "Jx", "Jy", "Jz", "rho"]
+    return {"metric": "field-surrogate training steps/s (batch 32 x 16^3 x 10, BF16 tensor cores)",
+            "value": args.steps / (ms * 1e-3), "unit": "steps/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16", "data": "synthetic (method-generated, seeded)",
+            "config": {"workload": args.workload, "pairs": int(xtr.shape[0]), "held_out": int(xte.shape[0]),
+                       "batch": 32, "patch": [16, 16, 16], "lead_steps": 5, "data_generation_s": gen_s},
+            "roofline": {"kernel": "hyb_surrogate_train_step: forward, backward and Adam of one batch",
+                         "bound": "tensor", "achieved": achieved, "peak": pk, "unit": "TFLOP/s", "frac": achieved / pk,
+                         "algorithmic_flop_per_launch": flop, "mean_launch_ms": ms / args.steps,
+                         "peak_kind": "measured" if peaks else "fallback", "traffic": None,
+                         "note": "%d FLOP per cell (forward, data gradient of layers 5..1, weight gradient); the "
+                                 "weight gradients run on the CUDA cores" % SUR_TRAIN_FLOP_PER_CELL},
+            "training": {"pretrain_steps": SUR_PRETRAIN_STEPS, "pretrain_s": pre_s, "loss_first": pre[0]["loss"],
+                         "loss_after_pretrain": pre[-1]["loss"], "loss_last": st[-1]["loss"],
+                         "huber_last": st[-1]["huber"], "energy_violation_last": st[-1]["energy"]},
+            "held_out": {"r2": dict(zip(names, r2)), "mse": dict(zip(names, mse)),
+                         "r2_mean": float(np.mean(r2)), "mse_max": float(np.max(mse)),
+                         "persistence_r2_mean": float(np.mean(r2_keep)),
+                         "mc_std_mean_normalised": float((ps / sd).mean()),
+                         "mc_std_max_normalised": float((ps / sd).max()),
+                         "paper_context": "R^2 0.9778 and MSE 1.47e-4 on the paper's own data (Results)"},
+            "clocks": clk, "gpu_launches": None}
+
+
+def run_oracle_surrogate_sample(budget_s=15.0):
+    """The oracle's surrogate training step (FP64 forward, backward and Adam)
+    on batches of 2 pairs of 16^3, timed for about budget_s; steps/s divided
+    by 16 for the batch of 32."""
+    import torch
+    from oracle import surrogate as S
+    from oracle.classifier import adam_update
+    from paper_2510_11174_gb300 import inputs
+    x, mean, std = inputs.random_states(2, 16, seed=3)
+    t = np.roll(x, 1, axis=4)
+    net = S.OracleSurrogate(inputs.surrogate_weights(11), dropout=0.1, seed=11, mean=mean, std=std)
+    mom = [(torch.zeros_like(w), torch.zeros_like(w)) for w in net.W]
+    t0 = time.perf_counter()
+    n = 0
+    while time.perf_counter() - t0 < budget_s:
+        out = S.loss_and_grads(net, x, t, n)
+        for l in range(len(S.LAYERS)):
+            net.W[l], m_, v_ = adam_update(net.W[l], out["grads"][l][0], mom[l][0], mom[l][1], n + 1)
+            mom[l] = (m_, v_)
+        n += 1
+    dt = time.perf_counter() - t0
+    return {"value": n / dt / 16.0, "unit": "steps/s", "cores": torch.get_num_threads(), "kind": "oracle",
+            "sample": "%d FP64 surrogate training steps of batch 2 x 16^3 (PyTorch CPU convolutions on %d threads, "
+                      "weights only in Adam); steps/s divided by 16 for batch 32" % (n, torch.get_num_threads())}
 
 
 def run_scan(args, P, torch):
@@ -739,6 +846,8 @@ def run_oracle_sample(workload, budget_s=15.0, max_steps=None):
     cells and particles, both proportional to the cross-section)."""
     if workloads()[workload][0] == "train":
         return run_oracle_train_sample(budget_s)
+    if workloads()[workload][0] == "train_surrogate":
+        return run_oracle_surrogate_sample(budget_s)
     o, net, ratio, what = oracle_sample(workload)
     t0 = time.perf_counter()
     n = 0
@@ -813,6 +922,14 @@ def run_reference(args, rank, world):
         return None
     from oracle import build as OB
     OB.build()
+    if workloads()[args.workload][0] == "train_surrogate":
+        r = run_oracle_surrogate_sample(budget_s=max(5.0, 2.0 * args.steps))
+        return {"metric": "field-surrogate training steps/s (batch 32 x 16^3 x 10, BF16 tensor cores)",
+                "value": r["value"], "unit": "steps/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1e3 / r["value"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64", "data": "synthetic (seeded)", "impl": "reference",
+                "config": {"workload": args.workload, "batch": 32, "patch": [16, 16, 16]}, "cpu_baseline": r,
+                "e2e": {"value": r["value"], "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     if workloads()[args.workload][0] == "train":
         r = run_oracle_train_sample(budget_s=max(5.0, 2.0 * args.steps))
         return {"metric": "classifier training steps/s (batch 32 x 32^3 x 6, BF16 tensor cores)", "value": r["value"],
@@ -873,7 +990,7 @@ def main():
         if rank == 0 and world == 1 and not args.no_cpu_baseline:
             out["cpu_baseline"] = run_oracle_sample(args.workload, budget_s=15.0)
             out["cpu_baseline"]["cpu_model"] = cpu_model()
-            if workloads()[args.workload][0] != "train":
+            if workloads()[args.workload][0] not in ("train", "train_surrogate"):
                 out["cpu_baseline_all_cores"] = run_oracle_all_cores(args.workload, budget_s=10.0)
     if rank == 0 and out is not None:
         print(json.dumps(out))

@@ -336,6 +336,81 @@ hyb_status hyb_model_get_grad(hyb_model *model, int layer, float *gw_host, float
  * this is where training patches are cut from a run.  Stream-ordered. */
 hyb_status hyb_node_fields(hyb_ctx *ctx, float *out_dev);
 
+/* The plasma state at the nodes (the field surrogate's channels): E_x, E_y,
+ * E_z and B_x, B_y, B_z as hyb_node_fields forms them, J_x, J_y, J_z of the
+ * last step averaged over the two Yee edges that meet at the node (zero
+ * outside an absorbing axis), and the charge density rho at the node: the
+ * CIC deposit of every charged particle species (q w / dV, times the charge
+ * state where a species has one), plus q n of every fluid, plus the residual
+ * background charge of the regime conversions.  out_dev: device FP32
+ * [10][nz][ny][nx].  The paper's predictor takes E, B, J and rho (Results:
+ * state transitions of normalised E, B, J and rho).  Stream-ordered. */
+hyb_status hyb_node_state(hyb_ctx *ctx, float *out_dev);
+
+/*
+ * Field surrogate: the paper's StatePredictor (Results, Table 2), a 3D CNN
+ * that maps the normalised state of a patch (10 channels: E, B, J, rho) to
+ * the state a fixed number of steps later.  Layers (3x3x3 convolutions, zero
+ * "same" padding, BF16 weights and activations, FP32 accumulation):
+ *   a1 = bf16(relu(conv(x; 10 -> 13)) + pad(x))
+ *   a2 = bf16(dropout(relu(conv(a1; 13 -> 32))) + pad(a1))      dropout p
+ *   a3 = bf16(relu(conv(a2; 32 -> 64)) + pad(a2))
+ *   a4 = bf16(relu(conv(a3; 64 -> 128)))
+ *   a5 = bf16(relu(conv(a4; 128 -> 32)))
+ *   y  = conv(a5; 32 -> 10)                                      (FP32)
+ * "pad" is the identity shortcut with the missing channels zero (Table 2's
+ * residuals between layers of different width).  x = (s - mean_c) / std_c
+ * per channel; the prediction is returned as std_c y_c + mean_c.
+ * Dropout uses the classifier's Philox stream (key (seed, 0xD0), counter
+ * (cell, batch, 1 << 16 | channel / 8, pass)).
+ * Training loss (Table 2: Huber with delta = 0.01 and 0.1 on the energy
+ * violation): L = (1/N) sum huber_delta(y - t) + energy_weight (1/B) sum_b v_b^2,
+ * t the normalised target, N the number of values, and per sample b
+ * v_b = (W(pred_b) - W(target_b)) / W(target_b) with W = (1/2) sum over the
+ * patch of |E|^2 + |B|^2 of the de-normalised channels 0..5.  Adam on FP32
+ * master weights.  Patches need W % 8 == 0 and H % 16 == 0.
+ */
+typedef struct hyb_surrogate hyb_surrogate;
+typedef struct {
+    uint32_t seed;             /* He-uniform initialisation and dropout stream */
+    double dropout;            /* p after layer 1 (Table 2: 0.1) */
+    int mc_passes;             /* passes of hyb_surrogate_mc */
+    double lr, beta1, beta2, eps;  /* Adam */
+    double huber_delta;        /* 0.01 */
+    double energy_weight;      /* 0.1 */
+    float mean[10], std[10];   /* per-channel normalisation */
+    void *stream;              /* cudaStream_t (NULL: own stream) */
+} hyb_surrogate_desc;
+hyb_status hyb_surrogate_create(const hyb_surrogate_desc *desc, hyb_surrogate **out);
+void hyb_surrogate_destroy(hyb_surrogate *s);
+/* Layers 0..5 in the layout [c_out][c_in][kz][ky][kx], biases [c_out];
+ * (c_in, c_out) = (10, 13), (13, 32), (32, 64), (64, 128), (128, 32), (32, 10). */
+hyb_status hyb_surrogate_set_layer(hyb_surrogate *s, int layer, const float *w_host, const float *b_host);
+hyb_status hyb_surrogate_get_layer(hyb_surrogate *s, int layer, float *w_host, float *b_host);
+/* Prediction for states x_dev (device FP32 [batch][10][D][H][W]) into y_dev
+ * (same layout, de-normalised).  pass >= 0 applies that pass's dropout masks,
+ * pass < 0 none.  Stream-ordered. */
+hyb_status hyb_surrogate_forward(hyb_surrogate *s, const float *x_dev, int batch, int D, int H, int W, int pass,
+                                 float *y_dev);
+/* Monte Carlo dropout: mc_passes passes (pass index 0 .. mc_passes - 1);
+ * mean and population standard deviation of the de-normalised prediction
+ * per value (device FP32, layout of x).  Stream-ordered. */
+hyb_status hyb_surrogate_mc(hyb_surrogate *s, const float *x_dev, int batch, int D, int H, int W, float *mean_dev,
+                            float *std_dev);
+typedef struct {
+    double loss;       /* L above */
+    double huber;      /* mean Huber term */
+    double energy;     /* mean v_b^2 */
+    long long step;    /* Adam step count after this update */
+} hyb_surrogate_stats;
+/* One training step on states x_dev and targets t_dev (device FP32,
+ * [batch][10][D][H][W], not normalised); dropout masks of pass = the step
+ * index.  Synchronises; fills *out. */
+hyb_status hyb_surrogate_train_step(hyb_surrogate *s, const float *x_dev, const float *t_dev, int batch, int D,
+                                    int H, int W, hyb_surrogate_stats *out);
+/* Gradients of the last training step, in the layout of hyb_surrogate_get_layer. */
+hyb_status hyb_surrogate_get_grad(hyb_surrogate *s, int layer, float *gw_host, float *gb_host);
+
 /* Copy the current mask (uint8, 1 = kinetic) and the residual background
  * charge rho_bg (FP32) to host arrays of nz*ny*nx values (either may be NULL;
  * synchronises). */

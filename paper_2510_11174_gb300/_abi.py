@@ -99,6 +99,17 @@ class hyb_train_stats(C.Structure):
     _fields_ = [("loss", C.c_double), ("bce", C.c_double), ("accuracy", C.c_double), ("step", C.c_longlong)]
 
 
+class hyb_surrogate_desc(C.Structure):
+    _fields_ = [("seed", C.c_uint32), ("dropout", C.c_double), ("mc_passes", C.c_int),
+                ("lr", C.c_double), ("beta1", C.c_double), ("beta2", C.c_double), ("eps", C.c_double),
+                ("huber_delta", C.c_double), ("energy_weight", C.c_double),
+                ("mean", C.c_float * 10), ("std", C.c_float * 10), ("stream", C.c_void_p)]
+
+
+class hyb_surrogate_stats(C.Structure):
+    _fields_ = [("loss", C.c_double), ("huber", C.c_double), ("energy", C.c_double), ("step", C.c_longlong)]
+
+
 _P = C.c_void_p
 _ctx = C.c_void_p
 
@@ -127,6 +138,16 @@ PROTOTYPES = {
     "hyb_classify": (C.c_int, [_ctx, _P, _P, _P, _P]),
     "hyb_get_regime": (C.c_int, [_ctx, _P, _P]),
     "hyb_node_fields": (C.c_int, [_ctx, _P]),
+    "hyb_node_state": (C.c_int, [_ctx, _P]),
+    "hyb_surrogate_create": (C.c_int, [C.POINTER(hyb_surrogate_desc), C.POINTER(C.c_void_p)]),
+    "hyb_surrogate_destroy": (None, [_P]),
+    "hyb_surrogate_set_layer": (C.c_int, [_P, C.c_int, _P, _P]),
+    "hyb_surrogate_get_layer": (C.c_int, [_P, C.c_int, _P, _P]),
+    "hyb_surrogate_forward": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _P]),
+    "hyb_surrogate_mc": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_int, C.c_int, _P, _P]),
+    "hyb_surrogate_train_step": (C.c_int, [_P, _P, _P, C.c_int, C.c_int, C.c_int, C.c_int,
+                                           C.POINTER(hyb_surrogate_stats)]),
+    "hyb_surrogate_get_grad": (C.c_int, [_P, C.c_int, _P, _P]),
     "hyb_model_create": (C.c_int, [C.POINTER(hyb_model_desc), C.POINTER(C.c_void_p)]),
     "hyb_model_destroy": (None, [_P]),
     "hyb_model_set_layer": (C.c_int, [_P, C.c_int, _P, _P]),

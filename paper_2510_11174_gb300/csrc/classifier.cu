@@ -140,8 +140,9 @@ __global__ void k_prep_fields(GridDev g, const float *__restrict__ E, const floa
 
 // the same node fields in FP32, not normalised, channel-first [6][nz][ny][nx]
 // (training patches cut from a run)
+// (with J: channels 6..8 hold J averaged over the two Yee edges at the node)
 __global__ void k_node_fields_f32(GridDev g, const float *__restrict__ E, const float *__restrict__ Bf,
-                                  float *__restrict__ out) {
+                                  const float *__restrict__ J, float *__restrict__ out) {
     const int nx = g.n[0], ny = g.n[1];
     const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
     if (i >= nx) return;
@@ -163,6 +164,11 @@ __global__ void k_node_fields_f32(GridDev g, const float *__restrict__ E, const 
                               fv(Bf + N, i, j, k));
     out[5 * N + c] = 0.25f * (fv(Bf + 2 * N, i - 1, j - 1, k) + fv(Bf + 2 * N, i, j - 1, k) +
                               fv(Bf + 2 * N, i - 1, j, k) + fv(Bf + 2 * N, i, j, k));
+    if (J) {
+        out[6 * N + c] = 0.5f * (fv(J, i - 1, j, k) + fv(J, i, j, k));
+        out[7 * N + c] = 0.5f * (fv(J + N, i, j - 1, k) + fv(J + N, i, j, k));
+        out[8 * N + c] = 0.5f * (fv(J + 2 * N, i, j, k - 1) + fv(J + 2 * N, i, j, k));
+    }
 }
 
 // layer-1 inputs of the passes pass0 .. pass0 + G - 1: a1[g] = h0s where the
@@ -257,13 +263,6 @@ static hyb_status model_reserve(hyb_model *m, long long cells) {
     return HYB_OK;
 }
 
-// dropout p as the threshold on 16-bit Philox fields (p is used as
-// round(p 2^16) / 2^16) and the inverted-dropout scale of kept values
-static inline uint32_t dropout_threshold(double p) {
-    const long t = std::lround(p * 65536.0);
-    return (uint32_t)(t < 0 ? 0 : (t > 65535 ? 65535 : t));
-}
-static inline float dropout_scale(uint32_t thr) { return (float)(65536.0 / (65536.0 - (double)thr)); }
 
 // layers 0..3 on the prepared input m->x0 (B x D x H x W cells) -> m->logit
 static ConvArgs conv_args(hyb_model *m, int l, int B, int D, int H, int W, int pass) {
@@ -532,9 +531,16 @@ hyb_status hyb_model_forward(hyb_model *m, const float *x, int B, int D, int H, 
 
 hyb_status hyb_node_fields(hyb_ctx *c, float *out_dev) {
     if (!c || !out_dev) return set_error(HYB_EINVAL, "null argument");
-    k_node_fields_f32<<<node_grid(c->g), node_block(c->g), 0, c->stream>>>(c->g, c->E, c->B, out_dev);
+    k_node_fields_f32<<<node_grid(c->g), node_block(c->g), 0, c->stream>>>(c->g, c->E, c->B, nullptr, out_dev);
     HYB_CUDA_TRY(cudaGetLastError());
     return HYB_OK;
+}
+
+hyb_status hyb_node_state(hyb_ctx *c, float *out_dev) {
+    if (!c || !out_dev) return set_error(HYB_EINVAL, "null argument");
+    k_node_fields_f32<<<node_grid(c->g), node_block(c->g), 0, c->stream>>>(c->g, c->E, c->B, c->J, out_dev);
+    HYB_CUDA_TRY(cudaGetLastError());
+    return charge_density(c, out_dev + 9 * c->g.N);
 }
 
 }  // extern "C"
@@ -543,7 +549,6 @@ hyb_status hyb_node_fields(hyb_ctx *c, float *out_dev) {
 // Loss, backward and Adam (see hyb_train_step in include/hyb.h).
 namespace hyb {
 
-static constexpr int WG_CHUNK = 8192;  // cells per weight-gradient partial
 static constexpr int WG_SUB = 64;      // cells staged in shared memory at a time
 static constexpr int RBT = 256;
 
@@ -684,9 +689,10 @@ __global__ void k_mask_grad(__nv_bfloat16 *__restrict__ d, const __nv_bfloat16 *
 // weight (and bias) gradient partials of a 3x3x3 layer:
 //   dW[co][ci][tap] = sum_cells A[cell + s(tap)][ci] dZ[cell][co]   (zero outside the volume)
 // grid (chunk, tap); part[chunk][tap][ci][co]; the tap-0 blocks also write db[co] to bpart[chunk][co]
+// (A has ca channels per cell, dZ dzs; ci_n, co_n <= 32: wider layers go in chunks)
 __global__ void __launch_bounds__(256) k_wgrad(const __nv_bfloat16 *__restrict__ A, int ca, int ci_n,
-                                               const __nv_bfloat16 *__restrict__ dZ, int co_n, int B, int D, int H,
-                                               int W, float *__restrict__ part, float *__restrict__ bpart) {
+                                               const __nv_bfloat16 *__restrict__ dZ, int co_n, int dzs, int B, int D,
+                                               int H, int W, float *__restrict__ part, float *__restrict__ bpart) {
     __shared__ float sa[WG_SUB][33], sz[WG_SUB][33];
     const long long V = (long long)D * H * W, n = (long long)B * V;
     const int tap = blockIdx.y;
@@ -705,7 +711,7 @@ __global__ void __launch_bounds__(256) k_wgrad(const __nv_bfloat16 *__restrict__
                 const int x = (int)(v % W) + dx, y = (int)((v / W) % H) + dy, z = (int)(v / ((long long)W * H)) + dz;
                 if (ch < ci_n && z >= 0 && z < D && y >= 0 && y < H && x >= 0 && x < W)
                     av = __bfloat162float(A[(b * V + ((long long)z * H + y) * W + x) * ca + ch]);
-                if (ch < co_n) zv = __bfloat162float(dZ[t * co_n + ch]);
+                if (ch < co_n) zv = __bfloat162float(dZ[t * dzs + ch]);
             }
             sa[r][ch] = av;
             sz[r][ch] = zv;
@@ -801,7 +807,7 @@ static void layer_wgrad(hyb_model *m, TrainBufs &t, int l, const __nv_bfloat16 *
     const int ci_n = CIN[l], co_n = COUT[l], nout = ci_n * co_n;
     float *part = t.wpart, *bpart = t.wpart + (long long)nch * 27 * nout;
     dim3 grid(nch, 27);
-    k_wgrad<<<grid, 256, 0, m->stream>>>(A, ca, ci_n, dZ, co_n, B, D, H, W, part, bpart);
+    k_wgrad<<<grid, 256, 0, m->stream>>>(A, ca, ci_n, dZ, co_n, co_n, B, D, H, W, part, bpart);
     float *wsum = t.wsum;
     k_sum_parts<<<nbl(27 * nout), 256, 0, m->stream>>>(part, nch, 27 * nout, wsum);
     k_reorder_wg<<<nbl(27 * nout), 256, 0, m->stream>>>(wsum, ci_n, co_n, t.gw[l]);

@@ -198,7 +198,8 @@ __global__ void __launch_bounds__(ConvCfg<KC, N>::NTHREADS, 1)
                 const uint32_t dst = ring_s + (uint32_t)(s * Cfg::STAGE);
 #pragma unroll
                 for (int c = 0; c < KC / 2; ++c)
-                    tma_load_5d(dst + (uint32_t)(c * CHBP), &tmap, 16 * c, tx * TXO - 1, ty * TY - 1, z0 - 1, b, fb);
+                    tma_load_5d(dst + (uint32_t)(c * CHBP), &tmap, a.cin_off + 16 * c, tx * TXO - 1, ty * TY - 1, z0 - 1,
+                                b, fb);
                 ++issued;
                 if (++s == STAGES) {
                     s = 0;
@@ -266,6 +267,7 @@ __global__ void __launch_bounds__(ConvCfg<KC, N>::NTHREADS, 1)
         const int m = q * 32 + lane;         // accumulator row = cell of the tile
         const float scale = a.drop_scale;
         const int bx = m & (TX - 1);         // cell of the block row (0 and TX - 1 are halo)
+        const long long opitch = a.out_pitch ? a.out_pitch : N;
         float bias8[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) bias8[j] = a.bias ? __ldg(a.bias + grp * 8 + j) : 0.0f;
@@ -280,7 +282,8 @@ __global__ void __launch_bounds__(ConvCfg<KC, N>::NTHREADS, 1)
             // the halo cells of the block row, and cells past the volume, write nothing
             const bool valid = bx != 0 && bx != TX - 1 && cx < a.W;
             const uint32_t lin = (uint32_t)(((long long)z0 * a.H + cy) * a.W + (valid ? cx : 0));
-            const long long obase = ((((long long)b * a.D + z0) * a.H + cy) * a.W + (valid ? cx : 0)) * N + grp * 8;
+            const long long obase = ((((long long)b * a.D + z0) * a.H + cy) * a.W + (valid ? cx : 0)) * opitch +
+                                    a.out_off + grp * 8;
             uint32_t keep16[4] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu};
             if (a.drop_thr) {
                 const u32x4 r = philox4x32_10(lin, (uint32_t)b, (a.layer << 16) | (uint32_t)grp, a.pass, a.seed, 0xD0u);
@@ -332,7 +335,13 @@ __global__ void __launch_bounds__(ConvCfg<KC, N>::NTHREADS, 1)
                     }
                     r8[j] = s;
                 }
-                if (outf) {
+                if (outf && a.accum) {
+                    // partial sums of one input-channel chunk: add the raw accumulator
+                    float4 *o4 = reinterpret_cast<float4 *>(outf);
+                    const float4 p0 = o4[0], p1 = o4[1];
+                    o4[0] = make_float4(p0.x + v[0], p0.y + v[1], p0.z + v[2], p0.w + v[3]);
+                    o4[1] = make_float4(p1.x + v[4], p1.y + v[5], p1.z + v[6], p1.w + v[7]);
+                } else if (outf) {
                     reinterpret_cast<float4 *>(outf)[0] = make_float4(r8[0], r8[1], r8[2], r8[3]);
                     reinterpret_cast<float4 *>(outf)[1] = make_float4(r8[4], r8[5], r8[6], r8[7]);
                 } else {
@@ -375,11 +384,10 @@ static EncodeTiledFn encode_fn() {
 static hyb_status make_tmap(CUtensorMap *tm, const ConvArgs &a) {
     EncodeTiledFn enc = encode_fn();
     if (!enc) return set_error(HYB_ECUDA, "cuTensorMapEncodeTiled is not available");
-    const cuuint64_t dims[5] = {(cuuint64_t)a.cin, (cuuint64_t)a.W, (cuuint64_t)a.H, (cuuint64_t)a.D,
-                                (cuuint64_t)a.B};
+    const cuuint64_t C = (cuuint64_t)(a.cin_total ? a.cin_total : a.cin);
+    const cuuint64_t dims[5] = {C, (cuuint64_t)a.W, (cuuint64_t)a.H, (cuuint64_t)a.D, (cuuint64_t)a.B};
     const cuuint64_t es = 2;
-    const cuuint64_t strides[4] = {es * a.cin, es * a.cin * a.W, es * a.cin * a.W * a.H,
-                                   es * a.cin * a.W * a.H * a.D};
+    const cuuint64_t strides[4] = {es * C, es * C * a.W, es * C * a.W * a.H, es * C * a.W * a.H * a.D};
     const cuuint32_t box[5] = {16, (cuuint32_t)TX, (cuuint32_t)HY, (cuuint32_t)HZ, 1};
     const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
     CUresult r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, (void *)a.x, dims, strides, box, estr,
@@ -434,6 +442,14 @@ hyb_status launch_conv3_tc(const ConvArgs &a, cudaStream_t st) {
     if (((uintptr_t)a.x & 15) || ((uintptr_t)a.y & 15) || ((uintptr_t)a.y_f32 & 15) || ((uintptr_t)a.wt & 15) ||
         (!a.y && !a.y_f32))
         return set_error(HYB_EINVAL, "conv operands must be present and 16-byte aligned");
+    {
+        // channel chunks: 16-channel aligned input slices (TMA x coordinate in
+        // 32-byte steps), 8-channel aligned output slices (16-byte stores)
+        const int ct = a.cin_total ? a.cin_total : a.cin, op = a.out_pitch ? a.out_pitch : a.N;
+        if (ct % 16 || a.cin_off < 0 || a.cin_off % 16 || a.cin_off + a.cin > ct || op % 8 || a.out_off < 0 ||
+            a.out_off % 8 || a.out_off + a.N > op || (a.accum && !a.y_f32))
+            return set_error(HYB_EINVAL, "conv channel slices out of range or misaligned");
+    }
     if (a.cin == 16 && a.N == 32) return launch_cfg<2, 32>(a, st);
     if (a.cin == 32 && a.N == 32) return launch_cfg<4, 32>(a, st);
     if (a.cin == 32 && a.N == 16) return launch_cfg<4, 16>(a, st);

@@ -198,7 +198,12 @@ struct ConvArgs {
     const float *bias;        // [N] or null
     __nv_bfloat16 *y;         // [B][D][H][W][N]
     float *y_f32;             // when set: FP32 output [B][D][H][W][N] instead of y
-    int B, D, H, W, cin, N;
+    int B, D, H, W, cin, N;   // cin: the channels one launch contracts (16 or 32)
+    int cin_total;            // channel pitch of x (0: cin); a launch reads channels cin_off .. cin_off + cin - 1
+    int cin_off;
+    int out_pitch;            // channel pitch of y / y_f32 (0: N); a launch writes channels out_off .. out_off + N - 1
+    int out_off;
+    int accum;                // y_f32 += the raw sums (no bias, ReLU or dropout): the partial of one input chunk
     int relu;
     uint32_t drop_thr;        // dropout threshold round(p 2^16) on 16-bit Philox fields; 0: no dropout
     float drop_scale;         // 1 / (1 - drop_thr 2^-16)

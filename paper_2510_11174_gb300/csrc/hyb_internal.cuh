@@ -2,7 +2,10 @@
 // Shared by the CUDA translation units of libhyb; not part of the public ABI.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
+
+#include <cmath>
 #include <stdint.h>
 #include <string>
 #include <vector>
@@ -365,5 +368,32 @@ void launch_diag_summary(const SpSet &set, int ntiles, const double *red, int nr
                          const int *status, DiagSummary *out, cudaStream_t st);
 void launch_energy(const GridDev &g, const float *E, const float *B, const SpSet &set,
                    double *partials, int nblocks, double *out, int *status, cudaStream_t st, int n_extra);
+
+
+// ---------------------------------------------------------------- network training helpers (classifier.cu)
+constexpr int WG_CHUNK = 8192;  // cells per weight-gradient partial
+// weight (and bias) gradient partials of a 3x3x3 layer, grid (chunk, tap):
+//   part[chunk][tap][ci][co] = sum over the chunk's cells of A[cell + s(tap)][ci] dZ[cell][co]
+// (ci_n, co_n <= 32; A has ca channels per cell, dZ has dzs); the tap-0 blocks
+// also write the bias partials bpart[chunk][co]
+__global__ void k_wgrad(const __nv_bfloat16 *__restrict__ A, int ca, int ci_n, const __nv_bfloat16 *__restrict__ dZ,
+                        int co_n, int dzs, int B, int D, int H, int W, float *__restrict__ part,
+                        float *__restrict__ bpart);
+// out[o] = sum_k part[k][o], k in increasing order
+__global__ void k_sum_parts(const float *__restrict__ part, int nchunks, int nout, float *__restrict__ out);
+// one Adam step on FP32 masters (c1, c2: the bias corrections 1 - beta^t)
+__global__ void k_adam(float *__restrict__ w, const float *__restrict__ g, float *__restrict__ m, float *__restrict__ v,
+                       int n, float lr, float b1, float b2, float eps, float c1, float c2);
+
+// dropout p as the threshold on 16-bit Philox fields (p is used as
+// round(p 2^16) / 2^16) and the inverted-dropout scale of kept values
+inline uint32_t dropout_threshold(double p) {
+    const long t = std::lround(p * 65536.0);
+    return (uint32_t)(t < 0 ? 0 : (t > 65535 ? 65535 : t));
+}
+inline float dropout_scale(uint32_t thr) { return (float)(65536.0 / (65536.0 - (double)thr)); }
+
+// charge density at the nodes (particles by CIC, fluids, rho_bg) into rho [nz][ny][nx] (regime.cu)
+hyb_status charge_density(hyb_ctx *c, float *rho);
 
 }  // namespace hyb

@@ -75,11 +75,12 @@ __device__ __forceinline__ bool in_tile(const GridDev &g, const int o[3], const 
     return ok;
 }
 
-// electron density from the macro-particles of the species in `which` (bit
-// s: species s), CIC: one fixed-point frame per tile, then a fixed-order
-// gather into ne
+// electron density (charge = 0: n_e = -q w / dV) or charge density (charge =
+// 1: q w / dV, times the charge state where the species has one) from the
+// macro-particles of the species in `which` (bit s: species s), CIC: one
+// fixed-point frame per tile, then a fixed-order gather
 __global__ void __launch_bounds__(256) k_density_frames(GridDev g, const SpDev *__restrict__ sps, int nsp,
-                                                         unsigned which, float *__restrict__ scratch,
+                                                         unsigned which, int charge, float *__restrict__ scratch,
                                                          int *__restrict__ valid, int *__restrict__ status) {
     extern __shared__ __align__(16) unsigned char smraw[];
     unsigned long long *fr = reinterpret_cast<unsigned long long *>(smraw);
@@ -93,8 +94,9 @@ __global__ void __launch_bounds__(256) k_density_frames(GridDev g, const SpDev *
         const SpDev &sp = sps[si];
         const int n = min(sp.count[t], sp.cap);
         total += n;
+        const float *zq = charge ? sp.zq : nullptr;
         for (int p = threadIdx.x; p < n; p += blockDim.x)
-            vmax = fmaxf(vmax, fabsf(sp.q * idV * sp.w[(long long)t * sp.cap + p]));
+            vmax = fmaxf(vmax, fabsf(sp.q * idV * sp.w[(long long)t * sp.cap + p] * (zq ? zq[(long long)t * sp.cap + p] : 1.0f)));
     }
     if (total == 0) {
         if (threadIdx.x == 0) valid[t] = 0;
@@ -112,14 +114,15 @@ __global__ void __launch_bounds__(256) k_density_frames(GridDev g, const SpDev *
         const SpDev &sp = sps[si];
         const int n = min(sp.count[t], sp.cap);
         const long long base = (long long)t * sp.cap;
-        const float qv = -sp.q * idV * sc;  // electrons: n_e = -q w / dV
+        const float qv = (charge ? sp.q : -sp.q) * idV * sc;  // electrons: n_e = -q w / dV
+        const float *zq = charge ? sp.zq : nullptr;
         for (int p = threadIdx.x; p < n; p += blockDim.x) {
             const float pos[3] = {sp.x[base + p], sp.y[base + p], sp.z[base + p]};
             if (!in_tile(g, o, pos)) {
                 atomicOr(status, ST_BADPOS);
                 continue;
             }
-            frame_cic(g, fr, G, o, pos, qv * sp.w[base + p]);
+            frame_cic(g, fr, G, o, pos, qv * sp.w[base + p] * (zq ? zq[base + p] : 1.0f));
         }
     }
     __syncthreads();
@@ -443,6 +446,50 @@ __global__ void k_moments_gather(GridDev g, const float *__restrict__ scratch, c
 static inline unsigned nblk(long long n) { return (unsigned)((n + 255) / 256); }
 
 // Criterion (or classifier decision) -> dilated mask -> conversions.
+// charges and densities of the fluids (a kernel parameter)
+struct FluidCharges {
+    float q[HYB_MAX_FLUIDS];
+    const float *n_[HYB_MAX_FLUIDS];
+    int n;
+};
+
+// rho += q n of every fluid + rho_bg
+__global__ void k_rho_fluids(long long N, FluidCharges fs, const float *__restrict__ rho_bg, float *__restrict__ rho) {
+    const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    float r = rho[c] + (rho_bg ? rho_bg[c] : 0.0f);
+    for (int f = 0; f < fs.n; ++f) r += fs.q[f] * fs.n_[f][c];
+    rho[c] = r;
+}
+
+// charge density at the nodes into rho (device FP32 [nz][ny][nx])
+hyb_status charge_density(hyb_ctx *c, float *rho) {
+    const GridDev &g = c->g;
+    cudaStream_t st = c->stream;
+    unsigned which = 0;
+    for (size_t si = 0; si < c->sp.size() && si < 32; ++si)
+        if (c->sp[si].dev.kind == 0) which |= 1u << si;
+    if (which) {
+        const int fG = frame_G(g.T);
+        const size_t sm1 = sizeof(unsigned long long) * (size_t)fG * fG * fG;
+        k_density_frames<<<g.ntiles, 256, sm1, st>>>(g, c->sp_dev, (int)c->sp.size(), which, 1, c->jscratch,
+                                                     c->jvalid, c->status);
+        k_density_gather<<<node_grid(g), node_block(g), 0, st>>>(g, c->jscratch, c->jvalid, rho);
+    } else {
+        cudaMemsetAsync(rho, 0, sizeof(float) * g.N, st);
+    }
+    FluidCharges fs;
+    memset(&fs, 0, sizeof(fs));
+    for (size_t f = 0; f < c->fluids.size() && fs.n < HYB_MAX_FLUIDS; ++f) {
+        fs.q[fs.n] = c->fluids[f].q;
+        fs.n_[fs.n++] = c->fluids[f].n;
+    }
+    k_rho_fluids<<<nblk(g.N), 256, 0, st>>>(g.N, fs, c->rho_bg, rho);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return set_error(HYB_ECUDA, std::string("charge density: ") + cudaGetErrorString(e));
+    return HYB_OK;
+}
+
 hyb_status regime_update(hyb_ctx *c, const float *pm, const float *ps) {
     const GridDev &g = c->g;
     cudaStream_t st = c->stream;
@@ -460,7 +507,7 @@ hyb_status regime_update(hyb_ctx *c, const float *pm, const float *ps) {
             if (c->sp[si].dev.kind == 0 && c->sp[si].q < 0.0 && !c->sp[si].has_zq) which |= 1u << si;
         if (which) {
             const size_t sm1 = sizeof(unsigned long long) * (size_t)fG3;
-            k_density_frames<<<g.ntiles, 256, sm1, st>>>(g, c->sp_dev, (int)c->sp.size(), which, c->jscratch,
+            k_density_frames<<<g.ntiles, 256, sm1, st>>>(g, c->sp_dev, (int)c->sp.size(), which, 0, c->jscratch,
                                                          c->jvalid, c->status);
             k_density_gather<<<node_grid(g), node_block(g), 0, st>>>(g, c->jscratch, c->jvalid, c->ne);
             launches += 2;

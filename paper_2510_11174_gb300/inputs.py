@@ -214,6 +214,33 @@ def classifier_weights(seed, out_bias=0.0, bias_scale=0.05):
     return out
 
 
+SURROGATE_LAYERS = [(10, 13), (13, 32), (32, 64), (64, 128), (128, 32), (32, 10)]
+
+
+def surrogate_weights(seed, bias_scale=0.05):
+    """Seeded FP32 weights of the field surrogate, [(W [co][ci][3][3][3], b [co])]:
+    He-uniform W with fan_in = 27 ci and small random biases.  Both the GPU
+    model (through hyb_surrogate_set_layer) and the oracle take these."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for ci, co in SURROGATE_LAYERS:
+        lim = math.sqrt(6.0 / (27 * ci))
+        out.append((rng.uniform(-lim, lim, (co, ci, 3, 3, 3)).astype(np.float32),
+                    (bias_scale * rng.standard_normal(co)).astype(np.float32)))
+    return out
+
+
+def random_states(batch, n, seed, mean_scale=0.5, std_range=(0.5, 2.0)):
+    """Seeded states [batch, 10, n, n, n] (FP32) with per-channel mean and
+    spread, and those per-channel means and spreads (the normalisation)."""
+    rng = np.random.default_rng(seed)
+    mean = (mean_scale * rng.standard_normal(10)).astype(np.float32)
+    std = rng.uniform(*std_range, 10).astype(np.float32)
+    x = (mean[None, :, None, None, None] + std[None, :, None, None, None] *
+         rng.standard_normal((batch, 10, n, n, n))).astype(np.float32)
+    return x, mean, std
+
+
 def field_packet(nx, ny, nz, dx, a0=10.0, x_c=None, w0=None, length=None, noise=0.05, seed=0):
     """Seeded synthetic E, B (3 x nz x ny x nx FP32 each): a linearly polarised
     wave packet along x (E_y, B_z) with a Gaussian envelope in x and in the

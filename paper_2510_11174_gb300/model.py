@@ -1,4 +1,5 @@
-"""Thin Python front end of the regime classifier (hyb_model_* in include/hyb.h).
+"""Thin Python front ends of the regime classifier (hyb_model_* in
+include/hyb.h) and of the field surrogate (hyb_surrogate_*).
 
 Argument marshalling only: weights and patches are handed to libhyb.so,
 which runs every layer on the GPU.
@@ -96,3 +97,110 @@ class Classifier:
         b = np.empty(co, np.float32)
         check(self._lib.hyb_model_get_grad(self._m, layer, w.ctypes.data, b.ctypes.data))
         return w, b
+
+
+SURROGATE_LAYERS = [(10, 13), (13, 32), (32, 64), (64, 128), (128, 32), (32, 10)]
+
+
+def _model_stream(stream):
+    import torch
+    if stream is not None:
+        return None, stream
+    cur = torch.cuda.current_stream()
+    if cur.cuda_stream == 0:
+        cur = torch.cuda.Stream()
+    return cur, cur.cuda_stream
+
+
+class Surrogate:
+    """The field surrogate (3D CNN 10->13->32->64->128->32->10 with identity
+    shortcuts and dropout; hyb_surrogate_* in include/hyb.h) on the GPU."""
+
+    def __init__(self, dropout=0.1, mc_passes=16, seed=11, mean=None, std=None, lr=1e-3, huber_delta=0.01,
+                 energy_weight=0.1, stream=None):
+        self._lib = _abi.load()
+        d = _abi.hyb_surrogate_desc()
+        d.seed, d.dropout, d.mc_passes = seed, dropout, mc_passes
+        d.lr, d.huber_delta, d.energy_weight = lr, huber_delta, energy_weight
+        mean = [0.0] * 10 if mean is None else mean
+        std = [1.0] * 10 if std is None else std
+        for c in range(10):
+            d.mean[c] = float(mean[c])
+            d.std[c] = float(std[c])
+        self.torch_stream, d.stream = _model_stream(stream)
+        self.desc = d
+        h = C.c_void_p()
+        check(self._lib.hyb_surrogate_create(C.byref(d), C.byref(h)))
+        self._m = h
+
+    def close(self):
+        if getattr(self, "_m", None):
+            self._lib.hyb_surrogate_destroy(self._m)
+            self._m = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_layer(self, layer, w, b):
+        ci, co = SURROGATE_LAYERS[layer]
+        w = np.ascontiguousarray(w, dtype=np.float32).reshape(co, ci, 3, 3, 3)
+        b = np.ascontiguousarray(b, dtype=np.float32).reshape(co)
+        check(self._lib.hyb_surrogate_set_layer(self._m, layer, w.ctypes.data, b.ctypes.data))
+
+    def get_layer(self, layer):
+        ci, co = SURROGATE_LAYERS[layer]
+        w = np.empty((co, ci, 3, 3, 3), np.float32)
+        b = np.empty(co, np.float32)
+        check(self._lib.hyb_surrogate_get_layer(self._m, layer, w.ctypes.data, b.ctypes.data))
+        return w, b
+
+    def get_grad(self, layer):
+        ci, co = SURROGATE_LAYERS[layer]
+        w = np.empty((co, ci, 3, 3, 3), np.float32)
+        b = np.empty(co, np.float32)
+        check(self._lib.hyb_surrogate_get_grad(self._m, layer, w.ctypes.data, b.ctypes.data))
+        return w, b
+
+    def _sync_in(self):
+        import torch
+        torch.cuda.current_stream().synchronize()
+
+    def _sync_out(self):
+        import torch
+        if self.torch_stream is not None:
+            torch.cuda.current_stream().wait_stream(self.torch_stream)
+
+    def forward(self, x, pass_index=-1):
+        """x: torch CUDA tensor [B, 10, D, H, W] FP32 -> prediction of the same shape."""
+        import torch
+        x = x.contiguous().float()
+        B, _, D, H, W = x.shape
+        out = torch.empty_like(x)
+        self._sync_in()
+        check(self._lib.hyb_surrogate_forward(self._m, x.data_ptr(), B, D, H, W, int(pass_index), out.data_ptr()))
+        self._sync_out()
+        return out
+
+    def mc(self, x):
+        """MC-dropout mean and standard deviation of the prediction."""
+        import torch
+        x = x.contiguous().float()
+        B, _, D, H, W = x.shape
+        pm, ps = torch.empty_like(x), torch.empty_like(x)
+        self._sync_in()
+        check(self._lib.hyb_surrogate_mc(self._m, x.data_ptr(), B, D, H, W, pm.data_ptr(), ps.data_ptr()))
+        self._sync_out()
+        return pm, ps
+
+    def train_step(self, x, t):
+        """One Adam step on states x and targets t ([B, 10, D, H, W] torch CUDA)."""
+        x = x.contiguous().float()
+        t = t.contiguous().float()
+        B, _, D, H, W = x.shape
+        st = _abi.hyb_surrogate_stats()
+        self._sync_in()
+        check(self._lib.hyb_surrogate_train_step(self._m, x.data_ptr(), t.data_ptr(), B, D, H, W, C.byref(st)))
+        return {"loss": st.loss, "huber": st.huber, "energy": st.energy, "step": st.step}

@@ -234,6 +234,18 @@ class Simulation:
             torch.cuda.current_stream().wait_stream(self.torch_stream)
         return out
 
+    def node_state(self, out=None):
+        """The surrogate's ten channels at the nodes (hyb_node_state): E, B,
+        J averaged to the nodes and the charge density; a torch CUDA tensor
+        [10, nz, ny, nx]."""
+        torch = _torch()
+        if out is None:
+            out = torch.empty((10,) + self.shape, dtype=torch.float32, device="cuda")
+        check(self._lib.hyb_node_state(self._ctx, out.data_ptr()))
+        if self.torch_stream is not None:
+            torch.cuda.current_stream().wait_stream(self.torch_stream)
+        return out
+
     def get_regime(self):
         mask = np.empty(self.shape, np.uint8)
         rho_bg = np.empty(self.shape, np.float32)

@@ -12,6 +12,13 @@ the criterion's decision there now or at the next classification ("kinetic
 now or soon"), so a network that learns it flags cells before the pulse
 reaches them.  ``train`` runs ``hyb_train_step`` over shuffled batches.
 
+``generate_state_pairs`` cuts the field surrogate's data from the same runs:
+16^3 patches of the ten node channels (``hyb_node_state``: E, B, J, rho) at
+one step and at the same place ``lead`` steps later (Results: the predictor
+learns state transitions).  ``train_surrogate`` runs
+``hyb_surrogate_train_step`` over shuffled batches and ``r2_mse`` scores a
+prediction per channel (Results: R^2 and MSE per channel).
+
 Orchestration only: the runs, the node fields and every training step run in
 libhyb.so; torch indexing cuts the patches and stacks the batches.
 """
@@ -97,3 +104,67 @@ def train(model, x, y, steps, batch=32, seed=5, log_every=0):
         if log_every and (k + 1) % log_every == 0:
             print("step %d loss %.4f acc %.3f" % (k + 1, st["loss"], st["accuracy"]))
     return stats
+
+
+def generate_state_pairs(n_pairs=2048, grid=(128, 128, 64), patch=16, runs=8, snapshots=12, every=5, lead=5,
+                         a0_range=(10.0, 300.0), density_range=(0.2, 2.0), seed=13, stream=None):
+    """(x, t) torch CUDA tensors [n, 10, p, p, p]: states and the states `lead`
+    steps later at the same patches, from ramp + slab hybrid runs."""
+    import torch
+    import paper_2510_11174_gb300 as P
+    nx, ny, nz = grid
+    rng = np.random.default_rng(seed)
+    per_snap = int(math.ceil(n_pairs / (runs * snapshots)))
+    xs, ts = [], []
+    st = stream if stream is not None else torch.cuda.Stream()
+    for r in range(runs):
+        a0 = float(np.exp(rng.uniform(math.log(a0_range[0]), math.log(a0_range[1]))))
+        dens = float(np.exp(rng.uniform(math.log(density_range[0]), math.log(density_range[1]))))
+        sim = _run(P, nx, ny, nz, a0, dens, seed + r, st.cuda_stream)
+        sim.classify()
+        for c in range(snapshots):
+            sim.step(every)
+            if c % 2 == 1:
+                sim.classify()
+            s0 = sim.node_state()
+            sim.step(lead)
+            s1 = sim.node_state()
+            for _ in range(per_snap):
+                z0, y0, x0 = (int(rng.integers(0, n - patch + 1)) for n in (nz, ny, nx))
+                xs.append(s0[:, z0:z0 + patch, y0:y0 + patch, x0:x0 + patch])
+                ts.append(s1[:, z0:z0 + patch, y0:y0 + patch, x0:x0 + patch])
+        sim.close()
+    return torch.stack(xs[:n_pairs]).contiguous(), torch.stack(ts[:n_pairs]).contiguous()
+
+
+def train_surrogate(model, x, t, steps, batch=32, seed=5):
+    """`steps` surrogate training steps on shuffled batches; returns the step statistics."""
+    import torch
+    gen = torch.Generator(device="cpu").manual_seed(seed)
+    n = x.shape[0]
+    perm = torch.randperm(n, generator=gen)
+    pos = 0
+    stats = []
+    for _ in range(steps):
+        if pos + batch > n:
+            perm = torch.randperm(n, generator=gen)
+            pos = 0
+        idx = perm[pos:pos + batch].cuda()
+        pos += batch
+        stats.append(model.train_step(x.index_select(0, idx), t.index_select(0, idx)))
+    return stats
+
+
+def r2_mse(pred, target, mean, std):
+    """Per-channel R^2 and MSE of a prediction, both on the normalised values
+    (x - mean_c) / std_c: R^2 = 1 - SS_res / SS_tot about the target's mean."""
+    import torch
+    mu = torch.tensor(mean, device=pred.device).view(1, -1, 1, 1, 1)
+    sd = torch.tensor(std, device=pred.device).view(1, -1, 1, 1, 1)
+    p = ((pred - mu) / sd).double()
+    q = ((target - mu) / sd).double()
+    res = ((p - q) ** 2).sum(dim=(0, 2, 3, 4))
+    tot = ((q - q.mean(dim=(0, 2, 3, 4), keepdim=True)) ** 2).sum(dim=(0, 2, 3, 4))
+    n = q.numel() / q.shape[1]
+    r2 = 1.0 - res / tot.clamp_min(1e-300)
+    return [float(v) for v in r2], [float(v) for v in res / n]
