@@ -165,7 +165,12 @@ NCU_CONV_L1_BYTES_PER_CELL = 87.4e6 / 1048576
 # DRAM read + write per particle of one hybrid-step launch of the push, from
 # the ncu capture on the 128 x 128 x 64 ramp + slab (184.9 + 69.1 MB for its
 # 4.78 M particles); scaled to a full launch by the particle count
-NCU_PUSH_BYTES_PER_PARTICLE = 254.0e6 / 4784128
+NCU_PUSH_BYTES_PER_PARTICLE = 261.9e6 / 4784128
+# warp instructions of the same capture: the push is bound by instruction
+# issue (its DRAM traffic is the algorithmic bytes), so it is also reported
+# against the SM's issue rate, 4 warp instructions per cycle and SM
+NCU_PUSH_WARP_INST_PER_PARTICLE = 1.11e8 / 4784128
+N_SM = 152
 
 
 # training FLOP per cell of one classifier training step: forward (94 176), data
@@ -420,6 +425,15 @@ def run_ours(args, rank, world):
     if "push" in roofs:
         roofs["push"]["traffic"] = NCU_PUSH_BYTES_PER_PARTICLE * parts
         roofs["push"]["traffic_note"] = "ncu dram bytes of a 128x128x64 hybrid-step launch scaled by particles"
+        mhz = clk.get("sm_mhz") or 2070.0
+        wi = NCU_PUSH_WARP_INST_PER_PARTICLE * parts
+        ach = wi / (phases["push"] * 1e-3)
+        pk_issue = N_SM * 4 * mhz * 1e6
+        roofs["push"]["issue"] = {"bound": "issue", "achieved": ach, "peak": pk_issue, "unit": "warp instructions/s",
+                                  "frac": ach / pk_issue, "warp_instructions_per_launch": wi,
+                                  "note": "warp instructions per particle from the ncu capture of a 128x128x64 "
+                                          "hybrid-step launch, times the particles; peak = 152 SMs x 4 issue "
+                                          "slots per cycle at the sampled SM clock"}
     if "conv_l1" in roofs:
         roofs["conv_l1"]["traffic"] = NCU_CONV_L1_BYTES_PER_CELL * cells
         roofs["conv_l1"]["traffic_note"] = "ncu dram bytes of a 128x128x64 launch scaled by cells"

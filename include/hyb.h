@@ -366,9 +366,10 @@ hyb_status hyb_node_state(hyb_ctx *ctx, float *out_dev);
  * Training loss (Table 2: Huber with delta = 0.01 and 0.1 on the energy
  * violation): L = (1/N) sum huber_delta(y - t) + energy_weight (1/B) sum_b v_b^2,
  * t the normalised target, N the number of values, and per sample b
- * v_b = (W(pred_b) - W(target_b)) / W(target_b) with W = (1/2) sum over the
- * patch of |E|^2 + |B|^2 of the de-normalised channels 0..5.  Adam on FP32
- * master weights.  Patches need W % 8 == 0 and H % 16 == 0.
+ * v_b = (W(pred_b) - W(target_b)) / mean over the batch of W(target) with
+ * W = (1/2) sum over the patch of |E|^2 + |B|^2 of the de-normalised
+ * channels 0..5 (a batch without field energy has no energy term).  Adam on
+ * FP32 master weights.  Patches need W % 8 == 0 and H % 16 == 0.
  */
 typedef struct hyb_surrogate hyb_surrogate;
 typedef struct {

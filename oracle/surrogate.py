@@ -22,8 +22,11 @@ the dropout mask of oracle.dropout_mask (layer index 1).
 
 Loss (Table 2: Huber with delta = 0.01 plus 0.1 times the energy violation):
   L = (1/N) sum huber(y - t_hat) + lambda (1/B) sum_b v_b^2,
-  v_b = (W(pred_b) - W(t_b)) / W(t_b),  W = (1/2) sum over the patch of the
-  squares of channels 0..5 (E and B) in physical units.
+  v_b = (W(pred_b) - W(t_b)) / mean_b' W(t_b'),  W = (1/2) sum over the patch
+  of the squares of channels 0..5 (E and B) in physical units.  The violation
+  is taken relative to the batch's mean target energy: a patch of empty
+  vacuum has no field energy, and a violation relative to its own would
+  diverge there.
 """
 import numpy as np
 import torch
@@ -124,11 +127,11 @@ def loss_and_grads(net, x, t, pass_index, delta=0.01, energy_weight=0.1, exact=F
     pred = y * sd + mu
     wp = 0.5 * (pred[:, :6] ** 2).sum(dim=(1, 2, 3, 4))
     wt = 0.5 * (tt[:, :6].to(torch.float64) ** 2).sum(dim=(1, 2, 3, 4))
-    ok = wt > 0
-    v = torch.where(ok, (wp - wt) / torch.where(ok, wt, torch.ones_like(wt)), torch.zeros_like(wt))
+    wbar = float(wt.mean())
+    v = (wp - wt) / wbar if wbar > 0 else torch.zeros_like(wt)
     loss = hub.sum() / N + energy_weight * (v * v).sum() / B
     G = dhub / N
-    coef = torch.where(ok, 2.0 * v / (torch.where(ok, wt, torch.ones_like(wt)) * B), torch.zeros_like(wt))
+    coef = 2.0 * v / (wbar * B) if wbar > 0 else torch.zeros_like(wt)
     G[:, :6] += energy_weight * coef.view(B, 1, 1, 1, 1) * sd[:, :6] * pred[:, :6]
     grads = [None] * len(LAYERS)
     for l in range(len(LAYERS) - 1, -1, -1):

@@ -58,7 +58,7 @@ def test_forward_matches_oracle(pass_index):
     y = m.forward(torch.from_numpy(x).cuda(), pass_index).cpu().numpy()
     ref = orc.predict(x, pass_index).numpy()
     err = rel_l2(y - mean[None, :, None, None, None], ref - mean[None, :, None, None, None])
-    assert err <= 2e-3, err
+    assert err <= 1e-3, err   # measured 4e-4 .. 6e-4
     m.close()
 
 
@@ -89,7 +89,10 @@ def test_one_step_gradients_match_oracle():
         gw, gb = m.get_grad(l)
         ow, ob = ref["grads"][l]
         errs.append((rel_l2(gw, ow.numpy()), rel_l2(gb, ob.numpy())))
-    assert all(ew <= 1e-2 and eb <= 1e-2 for ew, eb in errs), errs
+    # BF16 flips between the FP32 and FP64 sums collect in the first layer's
+    # weight gradient (measured 4.5e-3 .. 4.8e-3; the other layers 6e-5 .. 1.2e-3)
+    assert errs[0][0] <= 1e-2 and all(ew <= 2.5e-3 for ew, _ in errs[1:]), errs
+    assert all(eb <= 1e-3 for _, eb in errs), errs
     m.close()
 
 
