@@ -412,6 +412,53 @@ hyb_status hyb_surrogate_train_step(hyb_surrogate *s, const float *x_dev, const 
 /* Gradients of the last training step, in the layout of hyb_surrogate_get_layer. */
 hyb_status hyb_surrogate_get_grad(hyb_surrogate *s, int layer, float *gw_host, float *gb_host);
 
+/*
+ * SwitchNet: the paper's per-cell regime classifier (Table 1; Results: AUC
+ * against the convolutional classifier).  Input: the ten node channels of
+ * hyb_node_state for every cell, x = (s - mean_c) / std_c.  Layers (BF16
+ * weights and activations, FP32 accumulation):
+ *   h1 = bf16(relu(W0 x + b0) + pad(x))                        10 -> 128
+ *   h2 = bf16(dropout(relu(W1 h1 + b1)) + pad(h1))             128 -> 256, p
+ *   v  = bf16(Wv h2 + bv),  o = bf16(Wo v + bo)                 the attention layer
+ *   logit = w4 . o + b4,  p = sigmoid(logit)
+ * The attention layer (4 heads, 256 -> 256) sees one feature vector per cell,
+ * a sequence of one token: its softmax over the single key is 1, so it is the
+ * value projection followed by the output projection.  "pad" is the identity
+ * shortcut with the missing channels zero.  Dropout uses the classifier's
+ * Philox stream (layer index 1, counter (cell, 0, 1 << 16 | channel / 8,
+ * pass)).  Training: the classifier's energy-weighted BCE (w_c = 1 +
+ * energy_weight e_c / mean(e), e_c = (|E|^2 + |B|^2) / 2 of the raw
+ * features), Adam on FP32 masters.
+ */
+typedef struct hyb_switchnet hyb_switchnet;
+typedef struct {
+    uint32_t seed;             /* He-uniform initialisation and dropout stream */
+    double dropout;            /* p after layer 1 (Table 1: 0.2) */
+    int mc_passes;             /* passes of hyb_switchnet_mc */
+    double lr, beta1, beta2, eps;  /* Adam */
+    double energy_weight;      /* lambda of the energy-weighted BCE */
+    float mean[10], std[10];   /* per-channel normalisation */
+    void *stream;              /* cudaStream_t (NULL: own stream) */
+} hyb_switchnet_desc;
+hyb_status hyb_switchnet_create(const hyb_switchnet_desc *desc, hyb_switchnet **out);
+void hyb_switchnet_destroy(hyb_switchnet *s);
+/* Layers 0..4: W [c_out][c_in] and b [c_out] with (c_in, c_out) = (10, 128),
+ * (128, 256), (256, 256) value, (256, 256) output projection, (256, 1). */
+hyb_status hyb_switchnet_set_layer(hyb_switchnet *s, int layer, const float *w_host, const float *b_host);
+hyb_status hyb_switchnet_get_layer(hyb_switchnet *s, int layer, float *w_host, float *b_host);
+/* Logits of n cells, x_dev device FP32 [10][n]; pass >= 0 applies that
+ * pass's dropout.  Stream-ordered. */
+hyb_status hyb_switchnet_forward(hyb_switchnet *s, const float *x_dev, long long n, int pass, float *logit_dev);
+/* MC dropout: mean and population standard deviation of sigmoid(logit) over
+ * mc_passes passes (device FP32 [n] each).  Stream-ordered. */
+hyb_status hyb_switchnet_mc(hyb_switchnet *s, const float *x_dev, long long n, float *p_mean_dev, float *p_std_dev);
+/* One Adam step on n cells: features x_dev [10][n], labels y_dev [n] in {0, 1};
+ * dropout masks of pass = the step index.  Synchronises; fills *out. */
+hyb_status hyb_switchnet_train_step(hyb_switchnet *s, const float *x_dev, const float *y_dev, long long n,
+                                    hyb_train_stats *out);
+/* Gradients of the last training step, in the layout of hyb_switchnet_get_layer. */
+hyb_status hyb_switchnet_get_grad(hyb_switchnet *s, int layer, float *gw_host, float *gb_host);
+
 /* Copy the current mask (uint8, 1 = kinetic) and the residual background
  * charge rho_bg (FP32) to host arrays of nz*ny*nx values (either may be NULL;
  * synchronises). */

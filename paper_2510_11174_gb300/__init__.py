@@ -6,4 +6,4 @@ generators.
 """
 from ._abi import HybError, load  # noqa: F401
 from .sim import Batch, Simulation  # noqa: F401
-from .model import Classifier, Surrogate  # noqa: F401
+from .model import Classifier, Surrogate, SwitchNet  # noqa: F401

@@ -106,6 +106,13 @@ class hyb_surrogate_desc(C.Structure):
                 ("mean", C.c_float * 10), ("std", C.c_float * 10), ("stream", C.c_void_p)]
 
 
+class hyb_switchnet_desc(C.Structure):
+    _fields_ = [("seed", C.c_uint32), ("dropout", C.c_double), ("mc_passes", C.c_int),
+                ("lr", C.c_double), ("beta1", C.c_double), ("beta2", C.c_double), ("eps", C.c_double),
+                ("energy_weight", C.c_double), ("mean", C.c_float * 10), ("std", C.c_float * 10),
+                ("stream", C.c_void_p)]
+
+
 class hyb_surrogate_stats(C.Structure):
     _fields_ = [("loss", C.c_double), ("huber", C.c_double), ("energy", C.c_double), ("step", C.c_longlong)]
 
@@ -148,6 +155,14 @@ PROTOTYPES = {
     "hyb_surrogate_train_step": (C.c_int, [_P, _P, _P, C.c_int, C.c_int, C.c_int, C.c_int,
                                            C.POINTER(hyb_surrogate_stats)]),
     "hyb_surrogate_get_grad": (C.c_int, [_P, C.c_int, _P, _P]),
+    "hyb_switchnet_create": (C.c_int, [C.POINTER(hyb_switchnet_desc), C.POINTER(C.c_void_p)]),
+    "hyb_switchnet_destroy": (None, [_P]),
+    "hyb_switchnet_set_layer": (C.c_int, [_P, C.c_int, _P, _P]),
+    "hyb_switchnet_get_layer": (C.c_int, [_P, C.c_int, _P, _P]),
+    "hyb_switchnet_get_grad": (C.c_int, [_P, C.c_int, _P, _P]),
+    "hyb_switchnet_forward": (C.c_int, [_P, _P, C.c_longlong, C.c_int, _P]),
+    "hyb_switchnet_mc": (C.c_int, [_P, _P, C.c_longlong, _P, _P]),
+    "hyb_switchnet_train_step": (C.c_int, [_P, _P, _P, C.c_longlong, C.POINTER(hyb_train_stats)]),
     "hyb_model_create": (C.c_int, [C.POINTER(hyb_model_desc), C.POINTER(C.c_void_p)]),
     "hyb_model_destroy": (None, [_P]),
     "hyb_model_set_layer": (C.c_int, [_P, C.c_int, _P, _P]),

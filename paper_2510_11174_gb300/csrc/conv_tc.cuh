@@ -213,6 +213,18 @@ struct ConvArgs {
 };
 hyb_status launch_conv3_tc(const ConvArgs &a, cudaStream_t st);
 
+// one dense layer on the tensor cores (see gemm.cu): y[r][off + n] = sum_k
+// x[r][k] w[n][k] for r < rows, n < N, FP32 out
+struct GemmArgs {
+    const __nv_bfloat16 *x;   // [rows][K] BF16
+    const __nv_bfloat16 *w;   // packed K-major core layout [K/8][N][8]
+    float *y;                 // [rows][pitch] FP32
+    long long rows;
+    int K, N, pitch, off;
+    int *status;
+};
+hyb_status launch_gemm_tc(const GemmArgs &a, cudaStream_t st);
+
 // the last layer (16 -> 1 channel, 3x3x3) on the tensor cores (see conv.cu);
 // mc_k = 0 writes the logit, mc_k = k >= 1 folds sigmoid(logit) into the
 // running mean / M2 of the MC passes (k = 1 starts them)

@@ -396,4 +396,27 @@ inline float dropout_scale(uint32_t thr) { return (float)(65536.0 / (65536.0 - (
 // charge density at the nodes (particles by CIC, fluids, rho_bg) into rho [nz][ny][nx] (regime.cu)
 hyb_status charge_density(hyb_ctx *c, float *rho);
 
+// ---------------------------------------------------------------- layer activations (surrogate.cu)
+// dropout of one layer on the classifier's Philox stream: counter (cell %
+// V, cell / V, layer << 16 | channel / 8, pass), key (seed, 0xD0); a channel
+// keeps when its 16-bit field is >= thr (thr = 0: no dropout)
+struct DropArgs {
+    uint32_t thr, seed, pass, layer;
+    float scale;
+};
+// a = relu(s + b) [dropout] [+ res]: one thread per cell and 8-channel group;
+// BF16 out (out) or FP32 out (outf); cells = B V
+__global__ void k_act_finish(const float *__restrict__ s, const float *__restrict__ bias, int cop, int relu,
+                             const __nv_bfloat16 *__restrict__ res, int cres, DropArgs dr, int B, long long V,
+                             __nv_bfloat16 *__restrict__ out, float *__restrict__ outf);
+// dz = bf16(G [s + b > 0] keep / (1 - p)): the data gradient at a layer's pre-activation
+__global__ void k_act_dz(const float *__restrict__ G, const float *__restrict__ s, const float *__restrict__ bias,
+                         int cop, int relu, DropArgs dr, int B, long long V, __nv_bfloat16 *__restrict__ dz);
+// classifier loss pieces (classifier.cu): field energy density of [B][>=6][V]
+// inputs with FP64 block partials; energy-weighted BCE with its gradient
+__global__ void k_energy_density(const float *__restrict__ x, int B, long long V, float *__restrict__ e,
+                                 double *__restrict__ part);
+__global__ void k_loss(const float *__restrict__ logit, const float *__restrict__ y, const float *__restrict__ e,
+                       float inv_emean, float lam, long long n, float *__restrict__ dlogit, double *__restrict__ part);
+
 }  // namespace hyb

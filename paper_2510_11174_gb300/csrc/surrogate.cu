@@ -22,34 +22,8 @@
 #include "philox.cuh"
 
 namespace hyb {
-namespace {
 
-constexpr int SL = 6;                                            // convolutions
-constexpr int CI[SL] = {10, 13, 32, 64, 128, 32}, CO[SL] = {13, 32, 64, 128, 32, 10};
-constexpr int CIP[SL] = {16, 16, 32, 64, 128, 32}, COP[SL] = {16, 32, 64, 128, 32, 16};  // padded to 16
-constexpr int RES[SL] = {1, 1, 1, 0, 0, 0};                      // identity shortcut (zero-padded channels)
-constexpr int RELU[SL] = {1, 1, 1, 1, 1, 0};
-constexpr int DROP_LAYER = 1;                                    // dropout after layer 1's ReLU
-constexpr int NCH = 10;                                          // state channels: E, B, J, rho
-constexpr int RB = 256;
-
-inline int chunk_of(int c) { return c % 32 == 0 ? 32 : 16; }
-inline unsigned nbk(long long n, int b = RB) { return (unsigned)((n + b - 1) / b); }
-
-// states [B][10][V] FP32 -> normalised BF16 channels-last [B][V][16]
-__global__ void k_sur_prep(const float *__restrict__ x, int B, long long V, const float *__restrict__ mean,
-                           const float *__restrict__ sd, __nv_bfloat16 *__restrict__ out) {
-    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (t >= (long long)B * V) return;
-    const long long b = t / V, v = t % V;
-    __align__(16) __nv_bfloat16 o[16];
-#pragma unroll
-    for (int c = 0; c < 16; ++c) o[c] = __float2bfloat16_rn(c < NCH ? (x[(b * NCH + c) * V + v] - mean[c]) / sd[c] : 0.0f);
-    uint4 *dst = reinterpret_cast<uint4 *>(out + t * 16);
-    dst[0] = reinterpret_cast<const uint4 *>(o)[0];
-    dst[1] = reinterpret_cast<const uint4 *>(o)[1];
-}
-
+// ---------------------------------------------------------------- activations shared by the per-layer networks
 // keep bits (one per channel, bit j for channel 8 grp + j) of the dropout
 // stream: Philox counter (cell, batch, layer << 16 | grp, pass), key (seed,
 // 0xD0); channel j keeps when its 16-bit field is >= thr
@@ -62,15 +36,10 @@ __device__ __forceinline__ uint32_t keep_bits(uint32_t lin, uint32_t b, uint32_t
     return k;
 }
 
-struct Drop {
-    uint32_t thr, seed, pass, layer;  // thr = 0: no dropout
-    float scale;
-};
-
 // a = relu(s + b) [dropout] [+ res]: one thread per cell and 8-channel group;
 // BF16 out (hidden layers) or FP32 out (the last layer, no ReLU)
-__global__ void k_sur_finish(const float *__restrict__ s, const float *__restrict__ bias, int cop, int relu,
-                             const __nv_bfloat16 *__restrict__ res, int cres, Drop dr, int B, long long V,
+__global__ void k_act_finish(const float *__restrict__ s, const float *__restrict__ bias, int cop, int relu,
+                             const __nv_bfloat16 *__restrict__ res, int cres, DropArgs dr, int B, long long V,
                              __nv_bfloat16 *__restrict__ out, float *__restrict__ outf) {
     const int ng = cop / 8;
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -100,6 +69,59 @@ __global__ void k_sur_finish(const float *__restrict__ s, const float *__restric
         for (int j = 0; j < 8; ++j) o[j] = __float2bfloat16_rn(v[j]);
         *reinterpret_cast<uint4 *>(out + cell * cop + grp * 8) = *reinterpret_cast<const uint4 *>(o);
     }
+}
+
+// dz = bf16(G [s + b > 0] keep / (1 - p)): the data gradient at layer l's
+// pre-activation from the gradient G of its output; one thread per cell and
+// 8-channel group
+__global__ void k_act_dz(const float *__restrict__ G, const float *__restrict__ s, const float *__restrict__ bias,
+                         int cop, int relu, DropArgs dr, int B, long long V, __nv_bfloat16 *__restrict__ dz) {
+    const int ng = cop / 8;
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= (long long)B * V * ng) return;
+    const long long cell = t / ng;
+    const int grp = (int)(t % ng);
+    const uint32_t keep = dr.thr ? keep_bits((uint32_t)(cell % V), (uint32_t)(cell / V), dr.layer, (uint32_t)grp,
+                                             dr.pass, dr.seed, dr.thr)
+                                 : 0xFFu;
+    __align__(16) __nv_bfloat16 o[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const long long i = cell * cop + grp * 8 + j;
+        float g = G[i];
+        if (relu && !(s[i] + bias[grp * 8 + j] > 0.0f)) g = 0.0f;
+        if (dr.thr) g = ((keep >> j) & 1u) ? g * dr.scale : 0.0f;
+        o[j] = __float2bfloat16_rn(g);
+    }
+    *reinterpret_cast<uint4 *>(dz + cell * cop + grp * 8) = *reinterpret_cast<const uint4 *>(o);
+}
+
+namespace {
+
+constexpr int SL = 6;                                            // convolutions
+constexpr int CI[SL] = {10, 13, 32, 64, 128, 32}, CO[SL] = {13, 32, 64, 128, 32, 10};
+constexpr int CIP[SL] = {16, 16, 32, 64, 128, 32}, COP[SL] = {16, 32, 64, 128, 32, 16};  // padded to 16
+constexpr int RES[SL] = {1, 1, 1, 0, 0, 0};                      // identity shortcut (zero-padded channels)
+constexpr int RELU[SL] = {1, 1, 1, 1, 1, 0};
+constexpr int DROP_LAYER = 1;                                    // dropout after layer 1's ReLU
+constexpr int NCH = 10;                                          // state channels: E, B, J, rho
+constexpr int RB = 256;
+
+inline int chunk_of(int c) { return c % 32 == 0 ? 32 : 16; }
+inline unsigned nbk(long long n, int b = RB) { return (unsigned)((n + b - 1) / b); }
+
+// states [B][10][V] FP32 -> normalised BF16 channels-last [B][V][16]
+__global__ void k_sur_prep(const float *__restrict__ x, int B, long long V, const float *__restrict__ mean,
+                           const float *__restrict__ sd, __nv_bfloat16 *__restrict__ out) {
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= (long long)B * V) return;
+    const long long b = t / V, v = t % V;
+    __align__(16) __nv_bfloat16 o[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) o[c] = __float2bfloat16_rn(c < NCH ? (x[(b * NCH + c) * V + v] - mean[c]) / sd[c] : 0.0f);
+    uint4 *dst = reinterpret_cast<uint4 *>(out + t * 16);
+    dst[0] = reinterpret_cast<const uint4 *>(o)[0];
+    dst[1] = reinterpret_cast<const uint4 *>(o)[1];
 }
 
 // y [B][V][16] (normalised) -> [B][10][V] de-normalised
@@ -232,31 +254,6 @@ __global__ void __launch_bounds__(RB) k_sur_loss(const float *__restrict__ y, co
     }
     hs = blk_sum(hs, sh);
     if (threadIdx.x == 0) part[blockIdx.x] = hs;
-}
-
-// dz = bf16(G [s + b > 0] keep / (1 - p)): the data gradient at layer l's
-// pre-activation from the gradient G of its output; one thread per cell and
-// 8-channel group
-__global__ void k_sur_dz(const float *__restrict__ G, const float *__restrict__ s, const float *__restrict__ bias,
-                         int cop, int relu, Drop dr, int B, long long V, __nv_bfloat16 *__restrict__ dz) {
-    const int ng = cop / 8;
-    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (t >= (long long)B * V * ng) return;
-    const long long cell = t / ng;
-    const int grp = (int)(t % ng);
-    const uint32_t keep = dr.thr ? keep_bits((uint32_t)(cell % V), (uint32_t)(cell / V), dr.layer, (uint32_t)grp,
-                                             dr.pass, dr.seed, dr.thr)
-                                 : 0xFFu;
-    __align__(16) __nv_bfloat16 o[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        const long long i = cell * cop + grp * 8 + j;
-        float g = G[i];
-        if (relu && !(s[i] + bias[grp * 8 + j] > 0.0f)) g = 0.0f;
-        if (dr.thr) g = ((keep >> j) & 1u) ? g * dr.scale : 0.0f;
-        o[j] = __float2bfloat16_rn(g);
-    }
-    *reinterpret_cast<uint4 *>(dz + cell * cop + grp * 8) = *reinterpret_cast<const uint4 *>(o);
 }
 
 // the shortcut's share of the data gradient: G_in[c][ch] += G_out[c][ch] for ch < cin
@@ -427,8 +424,8 @@ hyb_status conv_chunks(hyb_surrogate *m, const __nv_bfloat16 *x, int nin, const 
     return HYB_OK;
 }
 
-Drop drop_of(const hyb_surrogate *m, int l, int pass) {
-    Drop dr;
+DropArgs drop_of(const hyb_surrogate *m, int l, int pass) {
+    DropArgs dr;
     memset(&dr, 0, sizeof(dr));
     if (l == DROP_LAYER && pass >= 0) {
         dr.thr = dropout_threshold(m->d.dropout);
@@ -448,7 +445,7 @@ hyb_status forward(hyb_surrogate *m, int B, int D, int H, int W, int pass) {
         hyb_status st = conv_chunks(m, m->a[l], CIP[l], m->pk[l], COP[l], m->s[l], B, D, H, W);
         if (st != HYB_OK) return st;
         const bool last = l == SL - 1;
-        k_sur_finish<<<nbk(cells * (COP[l] / 8)), RB, 0, m->stream>>>(
+        k_act_finish<<<nbk(cells * (COP[l] / 8)), RB, 0, m->stream>>>(
             m->s[l], m->b[l], COP[l], RELU[l], RES[l] ? m->a[l] : nullptr, CIP[l], drop_of(m, l, pass), B, V,
             last ? nullptr : m->a[l + 1], last ? m->y : nullptr);
     }
@@ -656,7 +653,7 @@ hyb_status hyb_surrogate_train_step(hyb_surrogate *m, const float *x, const floa
     // backward, last layer first
     for (int l = SL - 1; l >= 0; --l) {
         if (l < SL - 1)
-            k_sur_dz<<<nbk(cells * (COP[l] / 8)), RB, 0, st>>>(m->G[l + 1], m->s[l], m->b[l], COP[l], RELU[l],
+            k_act_dz<<<nbk(cells * (COP[l] / 8)), RB, 0, st>>>(m->G[l + 1], m->s[l], m->b[l], COP[l], RELU[l],
                                                               drop_of(m, l, pass), B, V, m->dz);
         layer_wgrad(m, l, B, D, H, W);
         if (l > 0) {

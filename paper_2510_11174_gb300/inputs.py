@@ -230,6 +230,21 @@ def surrogate_weights(seed, bias_scale=0.05):
     return out
 
 
+SWITCHNET_LAYERS = [(10, 128), (128, 256), (256, 256), (256, 256), (256, 1)]
+
+
+def switchnet_weights(seed, bias_scale=0.05):
+    """Seeded FP32 weights of SwitchNet, [(W [co][ci], b [co])]: He-uniform W
+    with fan_in = ci and small random biases (GPU model and oracle take these)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for ci, co in SWITCHNET_LAYERS:
+        lim = math.sqrt(6.0 / ci)
+        out.append((rng.uniform(-lim, lim, (co, ci)).astype(np.float32),
+                    (bias_scale * rng.standard_normal(co)).astype(np.float32)))
+    return out
+
+
 def random_states(batch, n, seed, mean_scale=0.5, std_range=(0.5, 2.0)):
     """Seeded states [batch, 10, n, n, n] (FP32) with per-channel mean and
     spread, and those per-channel means and spreads (the normalisation)."""

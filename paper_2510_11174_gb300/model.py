@@ -1,5 +1,6 @@
 """Thin Python front ends of the regime classifier (hyb_model_* in
-include/hyb.h) and of the field surrogate (hyb_surrogate_*).
+include/hyb.h), the field surrogate (hyb_surrogate_*) and the per-cell
+SwitchNet classifier (hyb_switchnet_*).
 
 Argument marshalling only: weights and patches are handed to libhyb.so,
 which runs every layer on the GPU.
@@ -204,3 +205,95 @@ class Surrogate:
         self._sync_in()
         check(self._lib.hyb_surrogate_train_step(self._m, x.data_ptr(), t.data_ptr(), B, D, H, W, C.byref(st)))
         return {"loss": st.loss, "huber": st.huber, "energy": st.energy, "step": st.step}
+
+
+SWITCHNET_LAYERS = [(10, 128), (128, 256), (256, 256), (256, 256), (256, 1)]
+
+
+class SwitchNet:
+    """The per-cell regime classifier of the paper's Table 1 (hyb_switchnet_*)
+    on the GPU: features [10, n] (the node channels E, B, J, rho) -> logits [n]."""
+
+    def __init__(self, dropout=0.2, mc_passes=16, seed=13, mean=None, std=None, lr=1e-3, energy_weight=0.1,
+                 stream=None):
+        self._lib = _abi.load()
+        d = _abi.hyb_switchnet_desc()
+        d.seed, d.dropout, d.mc_passes, d.lr, d.energy_weight = seed, dropout, mc_passes, lr, energy_weight
+        mean = [0.0] * 10 if mean is None else mean
+        std = [1.0] * 10 if std is None else std
+        for c in range(10):
+            d.mean[c] = float(mean[c])
+            d.std[c] = float(std[c])
+        self.torch_stream, d.stream = _model_stream(stream)
+        self.desc = d
+        h = C.c_void_p()
+        check(self._lib.hyb_switchnet_create(C.byref(d), C.byref(h)))
+        self._m = h
+
+    def close(self):
+        if getattr(self, "_m", None):
+            self._lib.hyb_switchnet_destroy(self._m)
+            self._m = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_layer(self, layer, w, b):
+        ci, co = SWITCHNET_LAYERS[layer]
+        w = np.ascontiguousarray(w, dtype=np.float32).reshape(co, ci)
+        b = np.ascontiguousarray(b, dtype=np.float32).reshape(co)
+        check(self._lib.hyb_switchnet_set_layer(self._m, layer, w.ctypes.data, b.ctypes.data))
+
+    def get_layer(self, layer):
+        ci, co = SWITCHNET_LAYERS[layer]
+        w = np.empty((co, ci), np.float32)
+        b = np.empty(co, np.float32)
+        check(self._lib.hyb_switchnet_get_layer(self._m, layer, w.ctypes.data, b.ctypes.data))
+        return w, b
+
+    def get_grad(self, layer):
+        ci, co = SWITCHNET_LAYERS[layer]
+        w = np.empty((co, ci), np.float32)
+        b = np.empty(co, np.float32)
+        check(self._lib.hyb_switchnet_get_grad(self._m, layer, w.ctypes.data, b.ctypes.data))
+        return w, b
+
+    def _sync_in(self):
+        import torch
+        torch.cuda.current_stream().synchronize()
+
+    def _sync_out(self):
+        import torch
+        if self.torch_stream is not None:
+            torch.cuda.current_stream().wait_stream(self.torch_stream)
+
+    def forward(self, x, pass_index=-1):
+        """x: torch CUDA tensor [10, n] FP32 -> logits [n]."""
+        import torch
+        x = x.contiguous().float()
+        out = torch.empty(x.shape[1], dtype=torch.float32, device=x.device)
+        self._sync_in()
+        check(self._lib.hyb_switchnet_forward(self._m, x.data_ptr(), x.shape[1], int(pass_index), out.data_ptr()))
+        self._sync_out()
+        return out
+
+    def mc(self, x):
+        import torch
+        x = x.contiguous().float()
+        pm = torch.empty(x.shape[1], dtype=torch.float32, device=x.device)
+        ps = torch.empty_like(pm)
+        self._sync_in()
+        check(self._lib.hyb_switchnet_mc(self._m, x.data_ptr(), x.shape[1], pm.data_ptr(), ps.data_ptr()))
+        self._sync_out()
+        return pm, ps
+
+    def train_step(self, x, y):
+        x = x.contiguous().float()
+        y = y.contiguous().float()
+        st = _abi.hyb_train_stats()
+        self._sync_in()
+        check(self._lib.hyb_switchnet_train_step(self._m, x.data_ptr(), y.data_ptr(), x.shape[1], C.byref(st)))
+        return {"loss": st.loss, "bce": st.bce, "accuracy": st.accuracy, "step": st.step}
