@@ -65,6 +65,8 @@ def workloads():
         "train_classifier_4096x32": ("train", None),
         # field-surrogate training: 2048 method-generated pairs of 16^3 x 10 node states 5 steps apart, batch 32
         "train_surrogate_2048x16": ("train_surrogate", None),
+        # the two regime classifiers on the same runs: SwitchNet (per cell) and the 3D CNN, AUC on held-out runs
+        "regime_classifiers_auc": ("auc", None),
     }
 
 
@@ -182,6 +184,12 @@ TRAIN_FLOP_PER_CELL = 94176 + 83808 + 94176
 SUR_FWD_FLOP_PER_CELL = 2 * 27 * (10 * 13 + 13 * 32 + 32 * 64 + 64 * 128 + 128 * 32 + 32 * 10)
 SUR_TRAIN_FLOP_PER_CELL = 2 * SUR_FWD_FLOP_PER_CELL + 2 * 27 * (13 * 32 + 32 * 64 + 64 * 128 + 128 * 32 + 32 * 10)
 SUR_PRETRAIN_STEPS = 600   # untimed training before the timed steps (the accuracy figures)
+# SwitchNet: forward 2 (16*128 + 128*256 + 2*256*256 + 256) FLOP per cell, data
+# gradient of layers 3..1, weight gradient
+SN_FWD_FLOP_PER_CELL = 2 * (16 * 128 + 128 * 256 + 2 * 256 * 256 + 256)
+SN_TRAIN_FLOP_PER_CELL = 2 * SN_FWD_FLOP_PER_CELL + 2 * (128 * 256 + 2 * 256 * 256)
+SN_CELLS_PER_STEP = 65536
+AUC_TRAIN_STEPS = 400
 
 
 def trained_model(P, stream, n_patches=1024, steps=300, runs=4):
@@ -343,6 +351,8 @@ def run_ours(args, rank, world):
         return run_train(args, P, torch, stream)
     if kind == "train_surrogate":
         return run_train_surrogate(args, P, torch, stream)
+    if kind == "auc":
+        return run_classifiers_auc(args, P, torch, stream)
     inp = gen(1 + rank)
     g = inp["grid"]
     cells = g["nx"] * g["ny"] * g["nz"]
@@ -606,6 +616,131 @@ def run_train_surrogate(args, P, torch, stream):
             "clocks": clk, "gpu_launches": None}
 
 
+def run_classifiers_auc(args, P, torch, stream):
+    """SwitchNet and the 3D CNN trained on the same method-generated runs (4
+    runs for training, 2 held out; labels: the physics criterion now or at the
+    next classification), AUC_TRAIN_STEPS steps each, scored by AUC on every
+    cell of the held-out snapshots (deterministic forward pass).  The timed
+    steps are SwitchNet training steps of SN_CELLS_PER_STEP cells."""
+    from paper_2510_11174_gb300 import training
+    t0 = time.perf_counter()
+    snaps = training.generate_snapshots(runs=6, stream=stream)
+    gen_s = time.perf_counter() - t0
+    per_run = len(snaps) // 6
+    train, test = snaps[:4 * per_run], snaps[4 * per_run:]
+    f6 = torch.stack([a for a, _, _ in train])
+    s10 = torch.stack([b for _, b, _ in train])
+    lab = torch.stack([c for _, _, c in train])
+    m6, sd6 = f6.mean(dim=(0, 2, 3, 4)), f6.std(dim=(0, 2, 3, 4)).clamp_min(1e-6)
+    m10, sd10 = s10.mean(dim=(0, 2, 3, 4)), s10.std(dim=(0, 2, 3, 4)).clamp_min(1e-6)
+    rng = np.random.default_rng(17)
+    # the CNN: random 32^3 patches of the training snapshots
+    nz, ny, nx = lab.shape[1:]
+    px, py = [], []
+    for _ in range(1024):
+        k = int(rng.integers(0, len(train)))
+        z0, y0, x0 = (int(rng.integers(0, n - 32 + 1)) for n in (nz, ny, nx))
+        px.append(f6[k, :, z0:z0 + 32, y0:y0 + 32, x0:x0 + 32])
+        py.append(lab[k, z0:z0 + 32, y0:y0 + 32, x0:x0 + 32])
+    px, py = torch.stack(px).contiguous(), torch.stack(py).contiguous()
+    cnn = P.Classifier(dropout=0.2, mc_passes=MC_PASSES, seed=11, mean=[float(v) for v in m6],
+                       std=[float(v) for v in sd6], stream=stream.cuda_stream)
+    t1 = time.perf_counter()
+    cnn_stats = training.train(cnn, px, py, AUC_TRAIN_STEPS)
+    cnn_s = time.perf_counter() - t1
+    # SwitchNet: random cells of the training snapshots
+    sn = P.SwitchNet(dropout=0.2, mc_passes=MC_PASSES, seed=13, mean=[float(v) for v in m10],
+                     std=[float(v) for v in sd10], stream=stream.cuda_stream)
+    flat_x = s10.permute(1, 0, 2, 3, 4).reshape(10, -1)
+    flat_y = lab.reshape(-1)
+    gen = torch.Generator(device="cuda").manual_seed(5)
+
+    def sn_steps(k):
+        out = []
+        for _ in range(k):
+            idx = torch.randint(0, flat_y.numel(), (SN_CELLS_PER_STEP,), device="cuda", generator=gen)
+            out.append(sn.train_step(flat_x.index_select(1, idx), flat_y.index_select(0, idx)))
+        return out
+
+    t1 = time.perf_counter()
+    sn_stats = sn_steps(AUC_TRAIN_STEPS)
+    sn_s = time.perf_counter() - t1
+    sn_steps(args.warmup)
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sn_steps(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    # held-out scores on every cell
+    sc_cnn, sc_sn, sc_now, ys = [], [], [], []
+    for k, (a, b, c) in enumerate(test):
+        sc_cnn.append(cnn.forward(a[None]).reshape(-1))
+        sc_sn.append(sn.forward(b.reshape(10, -1)))
+        ys.append(c.reshape(-1))
+    torch.cuda.synchronize()
+    y_all = torch.cat(ys)
+    auc_cnn = training.auc(torch.cat(sc_cnn), y_all)
+    auc_sn = training.auc(torch.cat(sc_sn), y_all)
+    cells = SN_CELLS_PER_STEP
+    flop = SN_TRAIN_FLOP_PER_CELL * cells
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    pk = peaks.get("bf16_tflops_sustained", 1700.0)
+    achieved = flop * args.steps / (ms * 1e-3) / 1e12
+    cnn.close()
+    sn.close()
+    return {"metric": "SwitchNet training steps/s (65536 cells per step, BF16 tensor cores)",
+            "value": args.steps / (ms * 1e-3), "unit": "steps/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16", "data": "synthetic (method-generated, seeded)",
+            "config": {"workload": args.workload, "runs_train": 4, "runs_held_out": 2,
+                       "snapshots": len(snaps), "grid": [nx, ny, nz], "train_steps_each": AUC_TRAIN_STEPS,
+                       "held_out_cells": int(y_all.numel()), "held_out_kinetic_fraction": float(y_all.mean()),
+                       "data_generation_s": gen_s},
+            "roofline": {"kernel": "hyb_switchnet_train_step: forward, backward and Adam of one batch",
+                         "bound": "tensor", "achieved": achieved, "peak": pk, "unit": "TFLOP/s",
+                         "frac": achieved / pk, "algorithmic_flop_per_launch": flop, "mean_launch_ms": ms / args.steps,
+                         "peak_kind": "measured" if peaks else "fallback", "traffic": None,
+                         "note": "%d FLOP per cell; the weight gradients run on the CUDA cores" % SN_TRAIN_FLOP_PER_CELL},
+            "auc_held_out": {"switchnet": auc_sn, "cnn": auc_cnn,
+                             "paper_context": "SwitchNet AUC 0.9689 on the paper's own labels (Results)"},
+            "training": {"cnn_loss_first": cnn_stats[0]["loss"], "cnn_loss_last": cnn_stats[-1]["loss"],
+                         "cnn_s": cnn_s, "switchnet_loss_first": sn_stats[0]["loss"],
+                         "switchnet_loss_last": sn_stats[-1]["loss"], "switchnet_s": sn_s},
+            "clocks": clk, "gpu_launches": None}
+
+
+def run_oracle_auc_sample(budget_s=15.0):
+    """The oracle's SwitchNet training step (FP64 forward, backward and Adam)
+    on 4096 cells, timed for about budget_s; steps/s divided by 16 for the
+    65536 cells of a step."""
+    import torch
+    from oracle import switchnet as S
+    from oracle.classifier import adam_update
+    from paper_2510_11174_gb300 import inputs
+    rng = np.random.default_rng(3)
+    x = rng.standard_normal((10, 4096)).astype(np.float32)
+    y = (np.abs(x[1]) > 1.0).astype(np.float32)
+    net = S.OracleSwitchNet(inputs.switchnet_weights(13), dropout=0.2, seed=13)
+    mom = [(torch.zeros_like(w), torch.zeros_like(w)) for w in net.W]
+    t0 = time.perf_counter()
+    n = 0
+    while time.perf_counter() - t0 < budget_s:
+        out = S.loss_and_grads(net, x, y, n)
+        for l in range(5):
+            net.W[l], m_, v_ = adam_update(net.W[l], out["grads"][l][0], mom[l][0], mom[l][1], n + 1)
+            mom[l] = (m_, v_)
+        n += 1
+    dt = time.perf_counter() - t0
+    return {"value": n / dt / 16.0, "unit": "steps/s", "cores": torch.get_num_threads(), "kind": "oracle",
+            "sample": "%d FP64 SwitchNet training steps of 4096 cells (PyTorch CPU on %d threads, weights only in "
+                      "Adam); steps/s divided by 16 for 65536 cells" % (n, torch.get_num_threads())}
+
+
 def run_oracle_surrogate_sample(budget_s=15.0):
     """The oracle's surrogate training step (FP64 forward, backward and Adam)
     on batches of 2 pairs of 16^3, timed for about budget_s; steps/s divided
@@ -862,6 +997,8 @@ def run_oracle_sample(workload, budget_s=15.0, max_steps=None):
         return run_oracle_train_sample(budget_s)
     if workloads()[workload][0] == "train_surrogate":
         return run_oracle_surrogate_sample(budget_s)
+    if workloads()[workload][0] == "auc":
+        return run_oracle_auc_sample(budget_s)
     o, net, ratio, what = oracle_sample(workload)
     t0 = time.perf_counter()
     n = 0
@@ -936,6 +1073,14 @@ def run_reference(args, rank, world):
         return None
     from oracle import build as OB
     OB.build()
+    if workloads()[args.workload][0] == "auc":
+        r = run_oracle_auc_sample(budget_s=max(5.0, 2.0 * args.steps))
+        return {"metric": "SwitchNet training steps/s (65536 cells per step, BF16 tensor cores)",
+                "value": r["value"], "unit": "steps/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1e3 / r["value"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64", "data": "synthetic (seeded)", "impl": "reference",
+                "config": {"workload": args.workload, "cells_per_step": SN_CELLS_PER_STEP}, "cpu_baseline": r,
+                "e2e": {"value": r["value"], "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     if workloads()[args.workload][0] == "train_surrogate":
         r = run_oracle_surrogate_sample(budget_s=max(5.0, 2.0 * args.steps))
         return {"metric": "field-surrogate training steps/s (batch 32 x 16^3 x 10, BF16 tensor cores)",
@@ -1004,7 +1149,7 @@ def main():
         if rank == 0 and world == 1 and not args.no_cpu_baseline:
             out["cpu_baseline"] = run_oracle_sample(args.workload, budget_s=15.0)
             out["cpu_baseline"]["cpu_model"] = cpu_model()
-            if workloads()[args.workload][0] not in ("train", "train_surrogate"):
+            if workloads()[args.workload][0] not in ("train", "train_surrogate", "auc"):
                 out["cpu_baseline_all_cores"] = run_oracle_all_cores(args.workload, budget_s=10.0)
     if rank == 0 and out is not None:
         print(json.dumps(out))

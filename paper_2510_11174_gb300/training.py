@@ -19,6 +19,12 @@ learns state transitions).  ``train_surrogate`` runs
 ``hyb_surrogate_train_step`` over shuffled batches and ``r2_mse`` scores a
 prediction per channel (Results: R^2 and MSE per channel).
 
+``generate_snapshots`` keeps whole grids instead (the six classifier
+channels, the ten node channels and the lookahead label), so that the
+convolutional classifier and the per-cell SwitchNet learn from the same runs
+and are scored on the same held-out cells by ``auc`` (Results: SwitchNet's
+AUC).
+
 Orchestration only: the runs, the node fields and every training step run in
 libhyb.so; torch indexing cuts the patches and stacks the batches.
 """
@@ -168,3 +174,55 @@ def r2_mse(pred, target, mean, std):
     n = q.numel() / q.shape[1]
     r2 = 1.0 - res / tot.clamp_min(1e-300)
     return [float(v) for v in r2], [float(v) for v in res / n]
+
+
+def generate_snapshots(grid=(128, 128, 64), runs=6, classifications=9, every=10, a0_range=(10.0, 300.0),
+                       density_range=(0.2, 2.0), seed=21, stream=None):
+    """List of (fields6 [6, nz, ny, nx], state10 [10, nz, ny, nx], label [nz, ny, nx])
+    torch CUDA tensors per run and classification: the label is the physics
+    criterion now or at the next classification."""
+    import torch
+    import paper_2510_11174_gb300 as P
+    nx, ny, nz = grid
+    rng = np.random.default_rng(seed)
+    out = []
+    st = stream if stream is not None else torch.cuda.Stream()
+    for r in range(runs):
+        a0 = float(np.exp(rng.uniform(math.log(a0_range[0]), math.log(a0_range[1]))))
+        dens = float(np.exp(rng.uniform(math.log(density_range[0]), math.log(density_range[1]))))
+        sim = _run(P, nx, ny, nz, a0, dens, seed + r, st.cuda_stream)
+        snaps, masks = [], []
+        for c in range(classifications):
+            snaps.append((sim.node_fields(), sim.node_state()))
+            sim.classify()
+            masks.append(torch.from_numpy(sim.get_regime()[0]).cuda())
+            sim.step(every)
+        sim.close()
+        for c in range(classifications - 1):
+            out.append((snaps[c][0], snaps[c][1], (masks[c] | masks[c + 1]).float()))
+    return out
+
+
+def auc(score, label):
+    """Area under the ROC curve (the probability that a random kinetic cell
+    scores above a random fluid cell, ties one half), from the ranks of the
+    scores (Mann-Whitney U); torch tensors on any device."""
+    import torch
+    s = score.reshape(-1).double()
+    y = label.reshape(-1) > 0.5
+    npos, nneg = int(y.sum()), int((~y).sum())
+    if npos == 0 or nneg == 0:
+        return float("nan")
+    order = torch.argsort(s, stable=True)
+    ss = s[order]
+    pos = torch.arange(1, len(ss) + 1, device=s.device, dtype=torch.float64)
+    # tied scores share the mean of their positions
+    new = torch.ones(len(ss), dtype=torch.bool, device=s.device)
+    new[1:] = ss[1:] != ss[:-1]
+    gid = torch.cumsum(new.long(), 0) - 1
+    ng = int(gid[-1]) + 1
+    sums = torch.zeros(ng, dtype=torch.float64, device=s.device).index_add_(0, gid, pos)
+    cnt = torch.zeros(ng, dtype=torch.float64, device=s.device).index_add_(0, gid, torch.ones_like(pos))
+    ranks = torch.empty_like(pos)
+    ranks[order] = (sums / cnt)[gid]
+    return float((ranks[y].sum() - npos * (npos + 1) / 2.0) / (npos * nneg))
