@@ -112,10 +112,13 @@ def train(model, x, y, steps, batch=32, seed=5, log_every=0):
     return stats
 
 
-def generate_state_pairs(n_pairs=2048, grid=(128, 128, 64), patch=16, runs=8, snapshots=12, every=5, lead=5,
-                         a0_range=(10.0, 300.0), density_range=(0.2, 2.0), seed=13, stream=None):
+def generate_state_pairs(n_pairs=2048, grid=(128, 128, 64), patch=16, runs=8, snapshots=12, every=5, lead=2,
+                         a0_range=(10.0, 300.0), density_range=(0.2, 2.0), seed=13, stream=None, focus=0.5):
     """(x, t) torch CUDA tensors [n, 10, p, p, p]: states and the states `lead`
-    steps later at the same patches, from ramp + slab hybrid runs."""
+    steps later at the same patches, from ramp + slab hybrid runs.  A fraction
+    `focus` of the patches is centred on cells where the field energy density
+    is in the top 1 % of the snapshot (where the pulse acts on the plasma),
+    the rest is placed uniformly."""
     import torch
     import paper_2510_11174_gb300 as P
     nx, ny, nz = grid
@@ -135,8 +138,15 @@ def generate_state_pairs(n_pairs=2048, grid=(128, 128, 64), patch=16, runs=8, sn
             s0 = sim.node_state()
             sim.step(lead)
             s1 = sim.node_state()
+            e = (s0[:6] ** 2).sum(0).reshape(-1)
+            hot = torch.nonzero(e >= torch.quantile(e[::97], 0.99)).reshape(-1).cpu().numpy()
             for _ in range(per_snap):
-                z0, y0, x0 = (int(rng.integers(0, n - patch + 1)) for n in (nz, ny, nx))
+                if len(hot) and rng.random() < focus:
+                    c = int(hot[int(rng.integers(0, len(hot)))])
+                    cz, cy, cx = c // (nx * ny), (c // nx) % ny, c % nx
+                    z0, y0, x0 = (min(max(v - patch // 2, 0), n - patch) for v, n in ((cz, nz), (cy, ny), (cx, nx)))
+                else:
+                    z0, y0, x0 = (int(rng.integers(0, n - patch + 1)) for n in (nz, ny, nx))
                 xs.append(s0[:, z0:z0 + patch, y0:y0 + patch, x0:x0 + patch])
                 ts.append(s1[:, z0:z0 + patch, y0:y0 + patch, x0:x0 + patch])
         sim.close()
