@@ -63,8 +63,8 @@ def workloads():
         "carbon_slab_128": ("pic", lambda seed: dict(inputs.carbon_slab(seed=seed + 1), preroll=PREROLL_CARBON)),
         # classifier training: 4096 method-generated 32^3 x 6 patches, batch 32 (one step = one Adam step)
         "train_classifier_4096x32": ("train", None),
-        # field-surrogate training: 2048 method-generated pairs of 16^3 x 10 node states 2 steps apart, batch 32
-        "train_surrogate_2048x16": ("train_surrogate", None),
+        # field-surrogate training: 4096 method-generated pairs of 16^3 x 10 node states 2 steps apart, batch 32
+        "train_surrogate_4096x16": ("train_surrogate", None),
         # the two regime classifiers on the same runs: SwitchNet (per cell) and the 3D CNN, AUC on held-out runs
         "regime_classifiers_auc": ("auc", None),
     }
@@ -184,6 +184,7 @@ TRAIN_FLOP_PER_CELL = 94176 + 83808 + 94176
 SUR_FWD_FLOP_PER_CELL = 2 * 27 * (10 * 13 + 13 * 32 + 32 * 64 + 64 * 128 + 128 * 32 + 32 * 10)
 SUR_TRAIN_FLOP_PER_CELL = 2 * SUR_FWD_FLOP_PER_CELL + 2 * 27 * (13 * 32 + 32 * 64 + 64 * 128 + 128 * 32 + 32 * 10)
 SUR_PRETRAIN_STEPS = 1500  # untimed training before the timed steps (the accuracy figures)
+SUR_PAIRS, SUR_HELD_OUT = 4096, 512
 # SwitchNet: forward 2 (16*128 + 128*256 + 2*256*256 + 256) FLOP per cell, data
 # gradient of layers 3..1, weight gradient
 SN_FWD_FLOP_PER_CELL = 2 * (16 * 128 + 128 * 256 + 2 * 256 * 256 + 256)
@@ -545,17 +546,20 @@ def run_train(args, P, torch, stream):
 
 
 def run_train_surrogate(args, P, torch, stream):
-    """Field-surrogate training on method-generated data: 2048 + 256 held-out
-    pairs of 16^3 x 10 node states (E, B, J, rho) 2 steps apart from ramp +
+    """Field-surrogate training on method-generated data: 4096 + 512 held-out
+    pairs (a seeded random split) of 16^3 x 10 node states (E, B, J, rho) 2 steps apart from ramp +
     slab runs, half of them centred where the pulse acts; SUR_PRETRAIN_STEPS untimed Adam steps, then W warm-up and K
     timed steps at batch 32 between CUDA events on the library's stream; the
     held-out pairs scored per channel (R^2, MSE of the normalised values) with
     the MC-dropout mean, and the MC spread."""
     from paper_2510_11174_gb300 import training
     t0 = time.perf_counter()
-    x, t = training.generate_state_pairs(n_pairs=2048 + 256, stream=stream)
+    x, t = training.generate_state_pairs(n_pairs=SUR_PAIRS + SUR_HELD_OUT, stream=stream)
     gen_s = time.perf_counter() - t0
-    xtr, ttr, xte, tte = x[:2048], t[:2048], x[2048:], t[2048:]
+    # a seeded random split, as the paper's 400 / 100 split of its transitions
+    perm = torch.randperm(x.shape[0], generator=torch.Generator().manual_seed(3)).cuda()
+    x, t = x.index_select(0, perm), t.index_select(0, perm)
+    xtr, ttr, xte, tte = x[:SUR_PAIRS], t[:SUR_PAIRS], x[SUR_PAIRS:], t[SUR_PAIRS:]
     m_ = xtr.mean(dim=(0, 2, 3, 4))
     s_ = xtr.std(dim=(0, 2, 3, 4)).clamp_min(1e-6)
     mean, std = [float(v) for v in m_], [float(v) for v in s_]
