@@ -114,7 +114,9 @@ def train_grads(net, x, y, pass_index, energy_weight, exact=False):
     p = torch.sigmoid(logit)
     dlogit = w * (p - yt) / N
     grads = [None] * 4
-    grads[3] = (_wgrad(acts[3], dlogit[:, None]), dlogit.sum().reshape(1))
+    # the last layer's weight gradient is a BF16 contraction like the others:
+    # its operand dL/dlogit is rounded to BF16 (its bias gradient is not)
+    grads[3] = (_wgrad(acts[3], rnd(dlogit)[:, None]), dlogit.sum().reshape(1))
     dA = F.conv_transpose3d(dlogit[:, None], W[3], padding=1)
     inv = 1.0 / (1.0 - net.p) if (pass_index >= 0 and net.p > 0) else 1.0
     for l in (2, 1, 0):

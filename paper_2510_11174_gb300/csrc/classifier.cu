@@ -549,18 +549,16 @@ hyb_status hyb_node_state(hyb_ctx *c, float *out_dev) {
 // Loss, backward and Adam (see hyb_train_step in include/hyb.h).
 namespace hyb {
 
-static constexpr int WG_SUB = 64;      // cells staged in shared memory at a time
 static constexpr int RBT = 256;
 
 struct TrainBufs {
     float *gw[NL] = {}, *gb[NL] = {};
     float *dlogit = nullptr, *edens = nullptr;
     __nv_bfloat16 *dz3 = nullptr, *dz2 = nullptr, *dz1 = nullptr;  // data gradients (BF16, channels-last)
-    float *wpart = nullptr;   // weight-gradient partials
-    float *wsum = nullptr;    // summed weight gradient in [tap][ci][co] order
     double *lpart = nullptr;  // loss partials
     long long cap = 0, wcap = 0;
     int lblocks = 0;
+    WgradScratch wg;          // operands of the tensor-core weight gradients
 };
 
 __device__ __forceinline__ double block_sum_d(double v, double *sh) {
@@ -655,88 +653,12 @@ __global__ void k_dgrad_last(const float *__restrict__ dlogit, const float *__re
     reinterpret_cast<uint4 *>(dz3 + t * 16)[1] = reinterpret_cast<const uint4 *>(o)[1];
 }
 
-// layer 3 weight gradient partials per chunk: [16 * 27] weights then 1 bias
-__global__ void k_wgrad_last(const __nv_bfloat16 *__restrict__ a3, const float *__restrict__ dlogit, int B, int D,
-                             int H, int W, float *__restrict__ part) {
-    const long long V = (long long)D * H * W, n = (long long)B * V;
-    const long long c0 = (long long)blockIdx.x * WG_CHUNK, c1 = min(c0 + WG_CHUNK, n);
-    for (int o = threadIdx.x; o < 16 * 27 + 1; o += blockDim.x) {
-        float acc = 0.0f;
-        if (o == 16 * 27) {
-            for (long long t = c0; t < c1; ++t) acc += dlogit[t];
-        } else {
-            const int ci = o / 27, tap = o % 27;
-            const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
-            for (long long t = c0; t < c1; ++t) {
-                const long long b = t / V, v = t % V;
-                const int x = (int)(v % W) + dx, y = (int)((v / W) % H) + dy, z = (int)(v / ((long long)W * H)) + dz;
-                if (z < 0 || z >= D || y < 0 || y >= H || x < 0 || x >= W) continue;
-                acc += __bfloat162float(a3[(b * V + ((long long)z * H + y) * W + x) * 16 + ci]) * dlogit[t];
-            }
-        }
-        part[(long long)blockIdx.x * (16 * 27 + 1) + o] = acc;
-    }
-}
-
 // dz = bf16(dA [a > 0] / (1 - p)) in place (dA from the tensor-core data gradient)
 __global__ void k_mask_grad(__nv_bfloat16 *__restrict__ d, const __nv_bfloat16 *__restrict__ a, long long n,
                             float inv_keep) {
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (t >= n) return;
     d[t] = __float2bfloat16_rn(__bfloat162float(a[t]) > 0.0f ? __bfloat162float(d[t]) * inv_keep : 0.0f);
-}
-
-// weight (and bias) gradient partials of a 3x3x3 layer:
-//   dW[co][ci][tap] = sum_cells A[cell + s(tap)][ci] dZ[cell][co]   (zero outside the volume)
-// grid (chunk, tap); part[chunk][tap][ci][co]; the tap-0 blocks also write db[co] to bpart[chunk][co]
-// (A has ca channels per cell, dZ dzs; ci_n, co_n <= 32: wider layers go in chunks)
-__global__ void __launch_bounds__(256) k_wgrad(const __nv_bfloat16 *__restrict__ A, int ca, int ci_n,
-                                               const __nv_bfloat16 *__restrict__ dZ, int co_n, int dzs, int B, int D,
-                                               int H, int W, float *__restrict__ part, float *__restrict__ bpart) {
-    __shared__ float sa[WG_SUB][33], sz[WG_SUB][33];
-    const long long V = (long long)D * H * W, n = (long long)B * V;
-    const int tap = blockIdx.y;
-    const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
-    const long long c0 = (long long)blockIdx.x * WG_CHUNK, c1 = min(c0 + WG_CHUNK, n);
-    const int nout = ci_n * co_n;
-    float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-    float bacc = 0.0f;
-    for (long long s0 = c0; s0 < c1; s0 += WG_SUB) {
-        for (int i = threadIdx.x; i < WG_SUB * 32; i += blockDim.x) {
-            const int r = i / 32, ch = i % 32;
-            const long long t = s0 + r;
-            float av = 0.0f, zv = 0.0f;
-            if (t < c1) {
-                const long long b = t / V, v = t % V;
-                const int x = (int)(v % W) + dx, y = (int)((v / W) % H) + dy, z = (int)(v / ((long long)W * H)) + dz;
-                if (ch < ci_n && z >= 0 && z < D && y >= 0 && y < H && x >= 0 && x < W)
-                    av = __bfloat162float(A[(b * V + ((long long)z * H + y) * W + x) * ca + ch]);
-                if (ch < co_n) zv = __bfloat162float(dZ[t * dzs + ch]);
-            }
-            sa[r][ch] = av;
-            sz[r][ch] = zv;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int o = threadIdx.x + k * 256;
-            if (o < nout) {
-                const int ci = o / co_n, co = o % co_n;
-                float s = 0.0f;
-                for (int r = 0; r < WG_SUB; ++r) s += sa[r][ci] * sz[r][co];
-                acc[k] += s;
-            }
-        }
-        if (tap == 0 && threadIdx.x < co_n)
-            for (int r = 0; r < WG_SUB; ++r) bacc += sz[r][threadIdx.x];
-        __syncthreads();
-    }
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const int o = threadIdx.x + k * 256;
-        if (o < nout) part[((long long)blockIdx.x * 27 + tap) * nout + o] = acc[k];
-    }
-    if (tap == 0 && threadIdx.x < co_n) bpart[(long long)blockIdx.x * co_n + threadIdx.x] = bacc;
 }
 
 // sum the chunk partials in chunk order: out[o] = sum_k part[k][o]
@@ -746,14 +668,6 @@ __global__ void k_sum_parts(const float *__restrict__ part, int nchunks, int nou
     float s = 0.0f;
     for (int k = 0; k < nchunks; ++k) s += part[(long long)k * nout + o];
     out[o] = s;
-}
-
-// reorder [tap][ci][co] -> [co][ci][tap] (the master-weight layout)
-__global__ void k_reorder_wg(const float *__restrict__ in, int ci_n, int co_n, float *__restrict__ out) {
-    const int o = blockIdx.x * blockDim.x + threadIdx.x;
-    if (o >= 27 * ci_n * co_n) return;
-    const int co = o % co_n, ci = (o / co_n) % ci_n, tap = o / (co_n * ci_n);
-    out[((long long)co * ci_n + ci) * 27 + tap] = in[o];
 }
 
 __global__ void k_adam(float *__restrict__ w, const float *__restrict__ g, float *__restrict__ m, float *__restrict__ v,
@@ -780,38 +694,46 @@ static hyb_status train_reserve(hyb_model *m, long long cells) {
                 m_alloc(m, (void **)&t.gb[l], sizeof(float) * COUT[l]))
                 return set_error(HYB_ENOMEM, "gradient buffers");
         t.lblocks = 152 * 2;
-        if (m_alloc(m, (void **)&t.lpart, sizeof(double) * 3 * t.lblocks) ||
-            m_alloc(m, (void **)&t.wsum, sizeof(float) * 27 * 32 * 32))
+        if (m_alloc(m, (void **)&t.lpart, sizeof(double) * 3 * t.lblocks))
             return set_error(HYB_ENOMEM, "loss partials");
     }
     if (cells > t.cap) {
         cudaStreamSynchronize(m->stream);
         // old buffers stay owned by the model until it is destroyed
-        const long long nch = (cells + WG_CHUNK - 1) / WG_CHUNK;
         if (m_alloc(m, (void **)&t.dlogit, sizeof(float) * cells) || m_alloc(m, (void **)&t.edens, sizeof(float) * cells) ||
             m_alloc(m, (void **)&t.dz3, sizeof(__nv_bfloat16) * 16 * cells) ||
             m_alloc(m, (void **)&t.dz2, sizeof(__nv_bfloat16) * 32 * cells) ||
-            m_alloc(m, (void **)&t.dz1, sizeof(__nv_bfloat16) * 32 * cells) ||
-            m_alloc(m, (void **)&t.wpart, sizeof(float) * nch * (27 * 32 * 32 + 32)))
+            m_alloc(m, (void **)&t.dz1, sizeof(__nv_bfloat16) * 32 * cells))
             return set_error(HYB_ENOMEM, "training buffers");
         t.cap = cells;
     }
     return HYB_OK;
 }
 
-// weight and bias gradient of layer l from its input A (channels ca, ci_n real) and dZ (co_n channels)
-static void layer_wgrad(hyb_model *m, TrainBufs &t, int l, const __nv_bfloat16 *A, int ca, const __nv_bfloat16 *dZ,
-                        int B, int D, int H, int W) {
-    const long long cells = (long long)B * D * H * W;
-    const int nch = (int)((cells + WG_CHUNK - 1) / WG_CHUNK);
-    const int ci_n = CIN[l], co_n = COUT[l], nout = ci_n * co_n;
-    float *part = t.wpart, *bpart = t.wpart + (long long)nch * 27 * nout;
-    dim3 grid(nch, 27);
-    k_wgrad<<<grid, 256, 0, m->stream>>>(A, ca, ci_n, dZ, co_n, co_n, B, D, H, W, part, bpart);
-    float *wsum = t.wsum;
-    k_sum_parts<<<nbl(27 * nout), 256, 0, m->stream>>>(part, nch, 27 * nout, wsum);
-    k_reorder_wg<<<nbl(27 * nout), 256, 0, m->stream>>>(wsum, ci_n, co_n, t.gw[l]);
-    k_sum_parts<<<nbl(co_n), 256, 0, m->stream>>>(bpart, nch, co_n, t.gb[l]);
+// weight and bias gradient of layer l on the tensor cores from its input A
+// (ca channels per cell, CIN[l] real) and dZ (COUT[l] channels), or, for the
+// last layer, from the FP32 dlogit
+static hyb_status layer_wgrad(hyb_model *m, TrainBufs &t, int l, const __nv_bfloat16 *A, int ca,
+                              const __nv_bfloat16 *dZ, const float *dZf, int B, int D, int H, int W) {
+    WgradJob j;
+    memset(&j, 0, sizeof(j));
+    j.x = A;
+    j.x_pitch = ca;
+    j.ci_n = CIN[l];
+    j.ci_tot = CIN[l];
+    j.dz = dZ;
+    j.dz_f32 = dZf;
+    j.dz_pitch = COUT[l];
+    j.co_n = COUT[l];
+    j.B = B;
+    j.D = D;
+    j.H = H;
+    j.W = W;
+    j.taps = 27;
+    j.gw = t.gw[l];
+    j.gb = t.gb[l];
+    j.status = m->status;
+    return wgrad_tc(j, t.wg, m->stream);
 }
 
 }  // namespace hyb
@@ -851,15 +773,11 @@ hyb_status hyb_train_step(hyb_model *m, const float *x, const float *y, int B, i
     const float inv_emean = emean > 0.0 ? (float)(1.0 / emean) : 0.0f;
     k_loss<<<t.lblocks, RBT, 0, st>>>(m->logit, y, t.edens, inv_emean, (float)m->d.energy_weight, cells, t.dlogit,
                                       t.lpart);
-    // layer 3 (16 -> 1) on the CUDA cores
-    const int nch = (int)((cells + WG_CHUNK - 1) / WG_CHUNK);
-    k_wgrad_last<<<nch, 256, 0, st>>>(m->a3, t.dlogit, B, D, H, W, t.wpart);
-    k_sum_parts<<<nbl(16 * 27 + 1), 256, 0, st>>>(t.wpart, nch, 16 * 27 + 1, t.wsum);
-    HYB_CUDA_TRY(cudaMemcpyAsync(t.gw[3], t.wsum, sizeof(float) * 16 * 27, cudaMemcpyDeviceToDevice, st));
-    HYB_CUDA_TRY(cudaMemcpyAsync(t.gb[3], t.wsum + 16 * 27, sizeof(float), cudaMemcpyDeviceToDevice, st));
+    // layer 3 (16 -> 1): weight gradient from bf16(dlogit), data gradient on the CUDA cores
+    if ((s = layer_wgrad(m, t, 3, m->a3, 16, nullptr, t.dlogit, B, D, H, W)) != HYB_OK) return s;
     k_dgrad_last<<<nbl(cells), 256, 0, st>>>(t.dlogit, m->w4r, m->a3, B, D, H, W, inv_keep, t.dz3);
     // layer 2 (32 -> 16): weight gradient, then the data gradient on the tensor cores
-    layer_wgrad(m, t, 2, m->a2, 32, t.dz3, B, D, H, W);
+    if ((s = layer_wgrad(m, t, 2, m->a2, 32, t.dz3, nullptr, B, D, H, W)) != HYB_OK) return s;
     ConvArgs a;
     memset(&a, 0, sizeof(a));
     a.B = B; a.D = D; a.H = H; a.W = W;
@@ -868,12 +786,12 @@ hyb_status hyb_train_step(hyb_model *m, const float *x, const float *y, int B, i
     if ((s = launch_conv3_tc(a, st)) != HYB_OK) return s;
     k_mask_grad<<<nbl(cells * 32), 256, 0, st>>>(t.dz2, m->a2, cells * 32, inv_keep);
     // layer 1 (32 -> 32)
-    layer_wgrad(m, t, 1, m->a1, 32, t.dz2, B, D, H, W);
+    if ((s = layer_wgrad(m, t, 1, m->a1, 32, t.dz2, nullptr, B, D, H, W)) != HYB_OK) return s;
     a.x = t.dz2; a.wt = m->wtT[1]; a.cin = 32; a.N = 32; a.y = t.dz1;
     if ((s = launch_conv3_tc(a, st)) != HYB_OK) return s;
     k_mask_grad<<<nbl(cells * 32), 256, 0, st>>>(t.dz1, m->a1, cells * 32, inv_keep);
     // layer 0 (6 -> 32): weight gradient only
-    layer_wgrad(m, t, 0, m->x0, 16, t.dz1, B, D, H, W);
+    if ((s = layer_wgrad(m, t, 0, m->x0, 16, t.dz1, nullptr, B, D, H, W)) != HYB_OK) return s;
     // Adam on the FP32 master weights, then the BF16 copies
     m->adam_t += 1;
     const float b1 = (float)m->d.beta1, b2 = (float)m->d.beta2;

@@ -371,14 +371,6 @@ void launch_energy(const GridDev &g, const float *E, const float *B, const SpSet
 
 
 // ---------------------------------------------------------------- network training helpers (classifier.cu)
-constexpr int WG_CHUNK = 8192;  // cells per weight-gradient partial
-// weight (and bias) gradient partials of a 3x3x3 layer, grid (chunk, tap):
-//   part[chunk][tap][ci][co] = sum over the chunk's cells of A[cell + s(tap)][ci] dZ[cell][co]
-// (ci_n, co_n <= 32; A has ca channels per cell, dZ has dzs); the tap-0 blocks
-// also write the bias partials bpart[chunk][co]
-__global__ void k_wgrad(const __nv_bfloat16 *__restrict__ A, int ca, int ci_n, const __nv_bfloat16 *__restrict__ dZ,
-                        int co_n, int dzs, int B, int D, int H, int W, float *__restrict__ part,
-                        float *__restrict__ bpart);
 // out[o] = sum_k part[k][o], k in increasing order
 __global__ void k_sum_parts(const float *__restrict__ part, int nchunks, int nout, float *__restrict__ out);
 // one Adam step on FP32 masters (c1, c2: the bias corrections 1 - beta^t)
@@ -418,5 +410,35 @@ __global__ void k_energy_density(const float *__restrict__ x, int B, long long V
                                  double *__restrict__ part);
 __global__ void k_loss(const float *__restrict__ logit, const float *__restrict__ y, const float *__restrict__ e,
                        float inv_emean, float lam, long long n, float *__restrict__ dlogit, double *__restrict__ part);
+
+// ---------------------------------------------------------------- weight gradients on the tensor cores (wgrad_tc.cu)
+// dW[co0 + co][ci0 + ci][t] = sum over cells of dZ[cell][co0 + co] X[cell + s(t)][ci0 + ci]
+// for a 3x3x3 convolution (taps = 27, zero outside the volume) or a dense
+// layer (taps = 1); co_n <= 32 (conv) or <= 128 (dense), ci_n <= 32 (conv) or
+// <= 256 (dense).  gw has the layout [co][ci_tot][taps]; gb (optional) gets
+// sum over cells of dZ.  dZ is BF16 channels-last [cells][dz_pitch], or FP32
+// [cells] with one channel (dz_f32, conv only).  Deterministic.
+struct WgradJob {
+    const __nv_bfloat16 *x;  // [cells][x_pitch]
+    int x_pitch, ci0, ci_n, ci_tot;
+    const __nv_bfloat16 *dz;  // [cells][dz_pitch]
+    const float *dz_f32;
+    int dz_pitch, co0, co_n;
+    int B, D, H, W;           // dense: B = D = H = 1, W = rows
+    int taps;
+    float *gw, *gb;
+    int *status;
+};
+struct WgradScratch {
+    void *buf = nullptr;
+    long long bytes = 0;
+    float *part = nullptr;
+    long long pbytes = 0;
+    ~WgradScratch() {
+        if (buf) cudaFree(buf);
+        if (part) cudaFree(part);
+    }
+};
+hyb_status wgrad_tc(const WgradJob &j, WgradScratch &ws, cudaStream_t st);
 
 }  // namespace hyb

@@ -10,7 +10,7 @@
 // finishing kernel adds the bias, applies ReLU, dropout and the identity
 // shortcut, and stores the BF16 activation.  The data gradient is the same
 // convolution with the transposed, flipped kernel; the weight gradient is the
-// classifier's fixed-order reduction (k_wgrad) in blocks of 32 x 32 channels;
+// tensor-core contraction over the cells (wgrad_tc) in blocks of 32 x 32 channels;
 // Adam updates FP32 masters.  See hyb_surrogate_* in include/hyb.h.
 #include <cuda_bf16.h>
 
@@ -323,8 +323,7 @@ struct hyb_surrogate {
     float *G[SL + 1] = {};                            // G[l]: dL/d a[l] ([cells][CIP[l]]), G[SL] = dL/dy
     float *y = nullptr;                               // prediction [cells][16] (normalised)
     __nv_bfloat16 *dz = nullptr;                      // data gradient of the current layer, [cells][<= 128]
-    float *wpart = nullptr, *wsum = nullptr;
-    long long wpart_n = 0;
+    WgradScratch *wg = nullptr;                       // operands of the tensor-core weight gradients
     double *lpart = nullptr, *epart = nullptr, *esum = nullptr;
     int lblocks = 2 * 152, eblocks = 64, ecap = 0;
     long long adam_t = 0;
@@ -377,19 +376,15 @@ hyb_status reserve(hyb_surrogate *m, long long cells) {
     }
     s_free(m, m->y);
     s_free(m, m->dz);
-    s_free(m, m->wpart);
     m->cap = 0;
     for (int l = 0; l < SL; ++l)
         if (s_alloc(m, (void **)&m->a[l], sizeof(__nv_bfloat16) * CIP[l] * cells) ||
             s_alloc(m, (void **)&m->s[l], sizeof(float) * COP[l] * cells) ||
             (l > 0 && s_alloc(m, (void **)&m->G[l], sizeof(float) * CIP[l] * cells)))
             return set_error(HYB_ENOMEM, "surrogate activation buffers");
-    const long long nch = (cells + WG_CHUNK - 1) / WG_CHUNK;
     if (s_alloc(m, (void **)&m->G[SL], sizeof(float) * 16 * cells) || s_alloc(m, (void **)&m->y, sizeof(float) * 16 * cells) ||
-        s_alloc(m, (void **)&m->dz, sizeof(__nv_bfloat16) * 128 * cells) ||
-        s_alloc(m, (void **)&m->wpart, sizeof(float) * nch * (27 * 32 * 32 + 32)))
+        s_alloc(m, (void **)&m->dz, sizeof(__nv_bfloat16) * 128 * cells))
         return set_error(HYB_ENOMEM, "surrogate activation buffers");
-    m->wpart_n = nch;
     m->cap = cells;
     return HYB_OK;
 }
@@ -468,21 +463,34 @@ hyb_status read_status(hyb_surrogate *m) {
     return HYB_OK;
 }
 
-// weight and bias gradient of layer l from its input a[l] and the BF16 data gradient dz
-void layer_wgrad(hyb_surrogate *m, int l, int B, int D, int H, int W) {
-    const long long cells = (long long)B * D * H * W;
-    const int nch = (int)((cells + WG_CHUNK - 1) / WG_CHUNK);
+// weight and bias gradient of layer l on the tensor cores, from its input
+// a[l] and the BF16 data gradient dz, in blocks of 32 x 32 channels
+hyb_status layer_wgrad(hyb_surrogate *m, int l, int B, int D, int H, int W) {
     for (int ci0 = 0; ci0 < CI[l]; ci0 += 32)
         for (int co0 = 0; co0 < CO[l]; co0 += 32) {
-            const int ci_n = CI[l] - ci0 < 32 ? CI[l] - ci0 : 32, co_n = CO[l] - co0 < 32 ? CO[l] - co0 : 32;
-            const int nout = ci_n * co_n;
-            float *part = m->wpart, *bpart = m->wpart + (long long)nch * 27 * nout;
-            k_wgrad<<<dim3(nch, 27), 256, 0, m->stream>>>(m->a[l] + ci0, CIP[l], ci_n, m->dz + co0, co_n, COP[l], B, D,
-                                                          H, W, part, bpart);
-            k_sum_parts<<<nbk(27 * nout), RB, 0, m->stream>>>(part, nch, 27 * nout, m->wsum);
-            k_sur_scatter_wg<<<nbk(27 * nout), RB, 0, m->stream>>>(m->wsum, ci_n, co_n, ci0, co0, CI[l], m->gw[l]);
-            if (ci0 == 0) k_sum_parts<<<nbk(co_n), RB, 0, m->stream>>>(bpart, nch, co_n, m->gb[l] + co0);
+            WgradJob j;
+            memset(&j, 0, sizeof(j));
+            j.x = m->a[l];
+            j.x_pitch = CIP[l];
+            j.ci0 = ci0;
+            j.ci_n = CI[l] - ci0 < 32 ? CI[l] - ci0 : 32;
+            j.ci_tot = CI[l];
+            j.dz = m->dz;
+            j.dz_pitch = COP[l];
+            j.co0 = co0;
+            j.co_n = CO[l] - co0 < 32 ? CO[l] - co0 : 32;
+            j.B = B;
+            j.D = D;
+            j.H = H;
+            j.W = W;
+            j.taps = 27;
+            j.gw = m->gw[l];
+            j.gb = ci0 == 0 ? m->gb[l] : nullptr;
+            j.status = m->status;
+            hyb_status s = wgrad_tc(j, *m->wg, m->stream);
+            if (s != HYB_OK) return s;
         }
+    return HYB_OK;
 }
 
 }  // namespace
@@ -493,6 +501,7 @@ void hyb_surrogate_destroy(hyb_surrogate *m) {
     if (!m) return;
     if (m->stream) cudaStreamSynchronize(m->stream);
     for (void *p : m->owned) cudaFree(p);
+    delete m->wg;
     if (m->own_stream && m->stream) cudaStreamDestroy(m->stream);
     delete m;
 }
@@ -504,6 +513,7 @@ hyb_status hyb_surrogate_create(const hyb_surrogate_desc *d, hyb_surrogate **out
     for (int c = 0; c < NCH; ++c)
         if (!(d->std[c] > 0.0f)) return set_error(HYB_EINVAL, "normalisation std must be > 0");
     hyb_surrogate *m = new hyb_surrogate();
+    m->wg = new WgradScratch();
     m->d = *d;
     m->d.dropout = dropout_threshold(d->dropout) / 65536.0;
     if (!(m->d.lr > 0)) m->d.lr = 1e-3;
@@ -542,8 +552,7 @@ hyb_status hyb_surrogate_create(const hyb_surrogate_desc *d, hyb_surrogate **out
         cudaMemsetAsync(m->gb[l], 0, sizeof(float) * COP[l], m->stream);
     }
     if (s_alloc(m, (void **)&m->mean, sizeof(float) * NCH) || s_alloc(m, (void **)&m->std_, sizeof(float) * NCH) ||
-        s_alloc(m, (void **)&m->status, sizeof(int)) || s_alloc(m, (void **)&m->wsum, sizeof(float) * 27 * 32 * 32) ||
-        s_alloc(m, (void **)&m->lpart, sizeof(double) * m->lblocks))
+        s_alloc(m, (void **)&m->status, sizeof(int)) || s_alloc(m, (void **)&m->lpart, sizeof(double) * m->lblocks))
         return fail("surrogate allocation");
     cudaMemcpyAsync(m->mean, d->mean, sizeof(float) * NCH, cudaMemcpyHostToDevice, m->stream);
     cudaMemcpyAsync(m->std_, d->std, sizeof(float) * NCH, cudaMemcpyHostToDevice, m->stream);
@@ -655,7 +664,7 @@ hyb_status hyb_surrogate_train_step(hyb_surrogate *m, const float *x, const floa
         if (l < SL - 1)
             k_act_dz<<<nbk(cells * (COP[l] / 8)), RB, 0, st>>>(m->G[l + 1], m->s[l], m->b[l], COP[l], RELU[l],
                                                               drop_of(m, l, pass), B, V, m->dz);
-        layer_wgrad(m, l, B, D, H, W);
+        if ((s = layer_wgrad(m, l, B, D, H, W)) != HYB_OK) return s;
         if (l > 0) {
             cudaMemsetAsync(m->G[l], 0, sizeof(float) * CIP[l] * cells, st);
             if ((s = conv_chunks(m, m->dz, COP[l], m->pkT[l], CIP[l], m->G[l], B, D, H, W)) != HYB_OK) return s;

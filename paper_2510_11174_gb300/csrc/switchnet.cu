@@ -10,8 +10,9 @@
 // k_act_finish adds bias, ReLU, dropout and the identity shortcut; the last
 // layer (256 -> 1) is a dot product per cell.  Training: the classifier's
 // energy-weighted BCE, data gradients through the same GEMM kernel with the
-// transposed weights, weight gradients as fixed-order FP32 reductions over
-// the cells, Adam on FP32 masters.  See hyb_switchnet_* in include/hyb.h.
+// transposed weights, weight gradients of the four dense layers as
+// tensor-core contractions over the cells (wgrad_tc; the output layer's 256
+// weights as a fixed-order FP32 reduction), Adam on FP32 masters.  See hyb_switchnet_* in include/hyb.h.
 #include <cuda_bf16.h>
 
 #include <cstring>
@@ -204,6 +205,7 @@ struct hyb_switchnet {
     double *lpart = nullptr;
     int lblocks = 2 * 152;
     long long adam_t = 0;
+    WgradScratch *wg = nullptr;                               // operands of the tensor-core weight gradients
     std::vector<void *> owned;
 };
 
@@ -360,6 +362,7 @@ void hyb_switchnet_destroy(hyb_switchnet *m) {
     if (!m) return;
     if (m->stream) cudaStreamSynchronize(m->stream);
     for (void *p : m->owned) cudaFree(p);
+    delete m->wg;
     if (m->own_stream && m->stream) cudaStreamDestroy(m->stream);
     delete m;
 }
@@ -371,6 +374,7 @@ hyb_status hyb_switchnet_create(const hyb_switchnet_desc *d, hyb_switchnet **out
     for (int c = 0; c < NF; ++c)
         if (!(d->std[c] > 0.0f)) return set_error(HYB_EINVAL, "normalisation std must be > 0");
     hyb_switchnet *m = new hyb_switchnet();
+    m->wg = new WgradScratch();
     m->d = *d;
     m->d.dropout = dropout_threshold(d->dropout) / 65536.0;
     if (!(m->d.lr > 0)) m->d.lr = 1e-3;
@@ -522,7 +526,25 @@ hyb_status hyb_switchnet_train_step(hyb_switchnet *m, const float *x, const floa
         if (l < SN_L - 1)
             k_act_dz<<<nbs(n * (SN_CO[l] / 8)), RBS, 0, st>>>(G, m->z[l], m->b[l], SN_CO[l], SN_RELU[l],
                                                               sn_drop(m, l, pass), 1, n, m->dz);
-        sn_wgrad(m, m->a[l], SN_KP[l], SN_CI[l], m->dz, SN_CO[l], SN_CO[l], n, m->gw[l], m->gb[l]);
+        for (int co0 = 0; co0 < SN_CO[l]; co0 += 128) {
+            WgradJob j;
+            memset(&j, 0, sizeof(j));
+            j.x = m->a[l];
+            j.x_pitch = SN_KP[l];
+            j.ci_n = SN_CI[l];
+            j.ci_tot = SN_CI[l];
+            j.dz = m->dz;
+            j.dz_pitch = SN_CO[l];
+            j.co0 = co0;
+            j.co_n = 128;
+            j.B = j.D = j.H = 1;
+            j.W = (int)n;
+            j.taps = 1;
+            j.gw = m->gw[l];
+            j.gb = m->gb[l];
+            j.status = m->status;
+            if ((s = wgrad_tc(j, *m->wg, st)) != HYB_OK) return s;
+        }
         if (l > 0) {
             float *Gn = (G == m->G1) ? m->G2 : m->G1;
             if ((s = sn_gemm(m, m->dz, SN_CO[l], m->pkT[l], SN_CI[l] / 128, Gn, SN_CI[l], n)) != HYB_OK) return s;
