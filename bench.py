@@ -539,8 +539,8 @@ def run_train(args, P, torch, stream):
                          "achieved": achieved, "peak": pk, "unit": "TFLOP/s", "frac": achieved / pk,
                          "algorithmic_flop_per_launch": flop, "mean_launch_ms": ms / args.steps,
                          "peak_kind": "measured" if peaks else "fallback", "traffic": None,
-                         "note": "272 160 FLOP per cell (forward, data gradient of layers 3..1, weight gradient); "
-                                 "the weight gradients run on the CUDA cores"},
+                         "note": "272 160 FLOP per cell (forward, data gradient of layers 3..1, weight gradient), "
+                                 "all on the tensor cores"},
             "loss_first": first[0]["loss"] if first else None, "loss_last": st[-1]["loss"],
             "accuracy_last": st[-1]["accuracy"], "clocks": clk, "gpu_launches": None}
 
@@ -607,8 +607,8 @@ def run_train_surrogate(args, P, torch, stream):
                          "bound": "tensor", "achieved": achieved, "peak": pk, "unit": "TFLOP/s", "frac": achieved / pk,
                          "algorithmic_flop_per_launch": flop, "mean_launch_ms": ms / args.steps,
                          "peak_kind": "measured" if peaks else "fallback", "traffic": None,
-                         "note": "%d FLOP per cell (forward, data gradient of layers 5..1, weight gradient); the "
-                                 "weight gradients run on the CUDA cores" % SUR_TRAIN_FLOP_PER_CELL},
+                         "note": "%d FLOP per cell (forward, data gradient of layers 5..1, weight gradient), all on "
+                                 "the tensor cores" % SUR_TRAIN_FLOP_PER_CELL},
             "training": {"pretrain_steps": SUR_PRETRAIN_STEPS, "pretrain_s": pre_s, "loss_first": pre[0]["loss"],
                          "loss_after_pretrain": pre[-1]["loss"], "loss_last": st[-1]["loss"],
                          "huber_last": st[-1]["huber"], "energy_violation_last": st[-1]["energy"]},
@@ -710,7 +710,8 @@ def run_classifiers_auc(args, P, torch, stream):
                          "bound": "tensor", "achieved": achieved, "peak": pk, "unit": "TFLOP/s",
                          "frac": achieved / pk, "algorithmic_flop_per_launch": flop, "mean_launch_ms": ms / args.steps,
                          "peak_kind": "measured" if peaks else "fallback", "traffic": None,
-                         "note": "%d FLOP per cell; the weight gradients run on the CUDA cores" % SN_TRAIN_FLOP_PER_CELL},
+                         "note": "%d FLOP per cell on the tensor cores (the 256 weights of the output layer on the "
+                                 "CUDA cores)" % SN_TRAIN_FLOP_PER_CELL},
             "auc_held_out": {"switchnet": auc_sn, "cnn": auc_cnn,
                              "paper_context": "SwitchNet AUC 0.9689 on the paper's own labels (Results)"},
             "training": {"cnn_loss_first": cnn_stats[0]["loss"], "cnn_loss_last": cnn_stats[-1]["loss"],

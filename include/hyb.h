@@ -312,7 +312,9 @@ hyb_status hyb_model_forward(hyb_model *model, const float *x_dev, int batch, in
  * energy term for a regime label).  Dropout is on with the masks of pass =
  * the step index; gradients flow through the same BF16 tensor-core
  * convolutions (data gradient = convolution with the transposed, flipped
- * kernel), weight gradients are FP32 reductions in a fixed order, and Adam
+ * kernel), weight gradients are tensor-core contractions over the cells
+ * (BF16 operands, among them bf16(dL/dlogit) for the last layer, FP32
+ * accumulation, partial sums of the SMs added in a fixed order), and Adam
  * updates the FP32 master weights.  Synchronises; fills *out.
  */
 typedef struct {
@@ -364,12 +366,13 @@ hyb_status hyb_node_state(hyb_ctx *ctx, float *out_dev);
  * Dropout uses the classifier's Philox stream (key (seed, 0xD0), counter
  * (cell, batch, 1 << 16 | channel / 8, pass)).
  * Training loss (Table 2: Huber with delta = 0.01 and 0.1 on the energy
- * violation): L = (1/N) sum huber_delta(y - t) + energy_weight (1/B) sum_b v_b^2,
- * t the normalised target, N the number of values, and per sample b
- * v_b = (W(pred_b) - W(target_b)) / mean over the batch of W(target) with
- * W = (1/2) sum over the patch of |E|^2 + |B|^2 of the de-normalised
- * channels 0..5 (a batch without field energy has no energy term).  Adam on
- * FP32 master weights.  Patches need W % 8 == 0 and H % 16 == 0.
+ * violation): L = (1/N) sum huber_delta(y - t) + energy_weight v^2, t the
+ * normalised target, N the number of values, and v the relative violation
+ * of the batch's total field energy, v = (sum_b W(pred_b) - sum_b
+ * W(target_b)) / sum_b W(target_b), W = (1/2) sum over a patch of |E|^2 +
+ * |B|^2 of the de-normalised channels 0..5 (a batch without field energy
+ * has no energy term).  Adam on FP32 master weights.  Patches need
+ * W % 8 == 0 and H % 16 == 0.
  */
 typedef struct hyb_surrogate hyb_surrogate;
 typedef struct {
@@ -401,7 +404,7 @@ hyb_status hyb_surrogate_mc(hyb_surrogate *s, const float *x_dev, int batch, int
 typedef struct {
     double loss;       /* L above */
     double huber;      /* mean Huber term */
-    double energy;     /* mean v_b^2 */
+    double energy;     /* v^2 */
     long long step;    /* Adam step count after this update */
 } hyb_surrogate_stats;
 /* One training step on states x_dev and targets t_dev (device FP32,

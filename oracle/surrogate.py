@@ -21,12 +21,13 @@ cross-correlation with zero "same" padding and BF16-rounded weights; keep is
 the dropout mask of oracle.dropout_mask (layer index 1).
 
 Loss (Table 2: Huber with delta = 0.01 plus 0.1 times the energy violation):
-  L = (1/N) sum huber(y - t_hat) + lambda (1/B) sum_b v_b^2,
-  v_b = (W(pred_b) - W(t_b)) / mean_b' W(t_b'),  W = (1/2) sum over the patch
-  of the squares of channels 0..5 (E and B) in physical units.  The violation
-  is taken relative to the batch's mean target energy: a patch of empty
-  vacuum has no field energy, and a violation relative to its own would
-  diverge there.
+  L = (1/N) sum huber(y - t_hat) + lambda v^2,
+  v = (sum_b W(pred_b) - sum_b W(t_b)) / sum_b W(t_b),  W = (1/2) sum over a
+  patch of the squares of channels 0..5 (E and B) in physical units: the
+  relative violation of the batch's total field energy.  (Relative to each
+  patch's own energy the violation diverges on patches of empty vacuum;
+  per patch relative to the mean it outweighs the Huber term some 70-fold
+  and the fit does not learn the fields.)
 """
 import numpy as np
 import torch
@@ -127,12 +128,12 @@ def loss_and_grads(net, x, t, pass_index, delta=0.01, energy_weight=0.1, exact=F
     pred = y * sd + mu
     wp = 0.5 * (pred[:, :6] ** 2).sum(dim=(1, 2, 3, 4))
     wt = 0.5 * (tt[:, :6].to(torch.float64) ** 2).sum(dim=(1, 2, 3, 4))
-    wbar = float(wt.mean())
-    v = (wp - wt) / wbar if wbar > 0 else torch.zeros_like(wt)
-    loss = hub.sum() / N + energy_weight * (v * v).sum() / B
+    wtot = float(wt.sum())
+    v = (float(wp.sum()) - wtot) / wtot if wtot > 0 else 0.0
+    loss = hub.sum() / N + energy_weight * v * v
     G = dhub / N
-    coef = 2.0 * v / (wbar * B) if wbar > 0 else torch.zeros_like(wt)
-    G[:, :6] += energy_weight * coef.view(B, 1, 1, 1, 1) * sd[:, :6] * pred[:, :6]
+    coef = 2.0 * v / wtot if wtot > 0 else 0.0
+    G[:, :6] += energy_weight * coef * sd[:, :6] * pred[:, :6]
     grads = [None] * len(LAYERS)
     for l in range(len(LAYERS) - 1, -1, -1):
         ci, co = LAYERS[l]
@@ -149,7 +150,7 @@ def loss_and_grads(net, x, t, pass_index, delta=0.01, energy_weight=0.1, exact=F
             if RESIDUAL[l]:
                 Gl = Gl + G[:, :ci]
             G = Gl
-    return dict(loss=float(loss), huber=float(hub.sum() / N), energy=float((v * v).sum() / B), grads=grads, y=y)
+    return dict(loss=float(loss), huber=float(hub.sum() / N), energy=v * v, grads=grads, y=y)
 
 
 def train_run(weights, x, t, steps, dropout, seed, delta=0.01, energy_weight=0.1, lr=1e-3, mean=None, std=None):

@@ -218,17 +218,18 @@ __global__ void __launch_bounds__(RB) k_sur_loss(const float *__restrict__ y, co
                                                  __nv_bfloat16 *__restrict__ dz, double *__restrict__ part) {
     __shared__ double sh[RB];
     const double inv_n = 1.0 / ((double)B * (double)V * NCH);
-    // the batch's mean target energy (the scale of the violation)
-    double wbar = 0.0;
-    for (int b = 0; b < B; ++b) wbar += esum[2 * b + 1];
-    wbar /= (double)B;
+    // the batch's total energies; d(v^2)/dW_pred,b = 2 v / W_true,tot with
+    // v = (W_pred,tot - W_true,tot) / W_true,tot (no energy term for W_true,tot = 0)
+    double wp = 0.0, wt = 0.0;
+    for (int b = 0; b < B; ++b) {
+        wp += esum[2 * b];
+        wt += esum[2 * b + 1];
+    }
+    const float ecoef = wt > 0.0 ? (float)(2.0 * (wp - wt) / (wt * wt)) : 0.0f;
     double hs = 0.0;
     for (long long t = blockIdx.x * (long long)RB + threadIdx.x; t < (long long)B * V;
          t += (long long)gridDim.x * RB) {
         const long long b = t / V, v = t % V;
-        const double wp = esum[2 * b], wt = esum[2 * b + 1];
-        // d(v_b^2)/dW_pred / B with v_b = (W_pred - W_true) / wbar; no energy term for wbar = 0
-        const float ecoef = wbar > 0.0 ? (float)(2.0 * (wp - wt) / (wbar * wbar) / (double)B) : 0.0f;
         __align__(16) float g[16];
         __align__(16) __nv_bfloat16 o[16];
 #pragma unroll
@@ -688,14 +689,14 @@ hyb_status hyb_surrogate_train_step(hyb_surrogate *m, const float *x, const floa
     HYB_CUDA_TRY(cudaMemcpyAsync(hp.data(), m->lpart, sizeof(double) * m->lblocks, cudaMemcpyDeviceToHost, st));
     HYB_CUDA_TRY(cudaMemcpyAsync(es.data(), m->esum, sizeof(double) * 2 * B, cudaMemcpyDeviceToHost, st));
     if ((s = read_status(m)) != HYB_OK) return s;
-    double hub = 0.0, ev = 0.0, wbar = 0.0;
+    double hub = 0.0, ev = 0.0, wp = 0.0, wt = 0.0;
     for (int k = 0; k < m->lblocks; ++k) hub += hp[k];
     hub /= (double)cells * NCH;
-    for (int b = 0; b < B; ++b) wbar += es[2 * b + 1];
-    wbar /= (double)B;
-    if (wbar > 0.0)
-        for (int b = 0; b < B; ++b) ev += ((es[2 * b] - es[2 * b + 1]) / wbar) * ((es[2 * b] - es[2 * b + 1]) / wbar);
-    ev /= (double)B;
+    for (int b = 0; b < B; ++b) {
+        wp += es[2 * b];
+        wt += es[2 * b + 1];
+    }
+    if (wt > 0.0) ev = ((wp - wt) / wt) * ((wp - wt) / wt);
     out->huber = hub;
     out->energy = ev;
     out->loss = hub + m->d.energy_weight * ev;
