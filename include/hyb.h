@@ -362,12 +362,14 @@ hyb_status hyb_node_state(hyb_ctx *ctx, float *out_dev);
  *   y  = conv(a5; 32 -> 10)                                      (FP32)
  * "pad" is the identity shortcut with the missing channels zero (Table 2's
  * residuals between layers of different width).  x = (s - mean_c) / std_c
- * per channel; the prediction is returned as std_c y_c + mean_c.
+ * per channel; y is the change of the state over the lead time in units of
+ * each channel's spread, and the prediction is s_c + std_c y_c (a residual
+ * forecast: with every weight zero it is the input state).
  * Dropout uses the classifier's Philox stream (key (seed, 0xD0), counter
  * (cell, batch, 1 << 16 | channel / 8, pass)).
  * Training loss (Table 2: Huber with delta = 0.01 and 0.1 on the energy
  * violation): L = (1/N) sum huber_delta(y - t) + energy_weight v^2, t the
- * normalised target, N the number of values, and v the relative violation
+ * target change (target - s) / std_c, N the number of values, and v the relative violation
  * of the batch's total field energy, v = (sum_b W(pred_b) - sum_b
  * W(target_b)) / sum_b W(target_b), W = (1/2) sum over a patch of |E|^2 +
  * |B|^2 of the de-normalised channels 0..5 (a batch without field energy

@@ -14,14 +14,17 @@ the second):
   a_3 = bf16(relu(conv(a_2; W_2) + b_2) + pad(a_2))
   a_4 = bf16(relu(conv(a_3; W_3) + b_3))
   a_5 = bf16(relu(conv(a_4; W_4) + b_4))
-  y   = conv(a_5; W_5) + b_5,  prediction = std_c y_c + mean_c
+  y   = conv(a_5; W_5) + b_5,  prediction = s_c + std_c y_c
+The output is the change of the state over the lead time in units of each
+channel's spread, added to the input state (a residual forecast: with every
+weight zero the prediction is the input, persistence).
 "pad" is the identity shortcut with the extra channels zero (the reading of
 a residual between layers of different width); conv is the 3x3x3
 cross-correlation with zero "same" padding and BF16-rounded weights; keep is
 the dropout mask of oracle.dropout_mask (layer index 1).
 
 Loss (Table 2: Huber with delta = 0.01 plus 0.1 times the energy violation):
-  L = (1/N) sum huber(y - t_hat) + lambda v^2,
+  L = (1/N) sum huber(y - t_hat) + lambda v^2,  t_hat = (t - s) / std_c,
   v = (sum_b W(pred_b) - sum_b W(t_b)) / sum_b W(t_b),  W = (1/2) sum over a
   patch of the squares of channels 0..5 (E and B) in physical units: the
   relative violation of the batch's total field energy.  (Relative to each
@@ -100,7 +103,8 @@ class OracleSurrogate:
 
     def predict(self, x, pass_index=-1, exact=False):
         y = self.forward(x, pass_index, exact)
-        return y * self.std.view(1, 10, 1, 1, 1).to(torch.float64) + self.mean.view(1, 10, 1, 1, 1).to(torch.float64)
+        xs = torch.as_tensor(np.asarray(x, dtype=np.float32)).to(torch.float64)
+        return xs + y * self.std.view(1, 10, 1, 1, 1).to(torch.float64)
 
     def mc_statistics(self, x, passes):
         """Mean and population standard deviation of the prediction over the passes."""
@@ -118,14 +122,15 @@ def loss_and_grads(net, x, t, pass_index, delta=0.01, energy_weight=0.1, exact=F
     sd = net.std.view(1, 10, 1, 1, 1).to(torch.float64)
     mu = net.mean.view(1, 10, 1, 1, 1).to(torch.float64)
     tt = torch.as_tensor(np.asarray(t, dtype=np.float32))
-    tn = ((tt - net.mean.view(1, 10, 1, 1, 1)) / net.std.view(1, 10, 1, 1, 1)).to(torch.float64)
+    xs = torch.as_tensor(np.asarray(x, dtype=np.float32))
+    tn = ((tt - xs) / net.std.view(1, 10, 1, 1, 1)).to(torch.float64)
     B = y.shape[0]
     N = y.numel()
     r = y - tn
     ar = r.abs()
     hub = torch.where(ar <= delta, 0.5 * r * r, delta * (ar - 0.5 * delta))
     dhub = torch.where(ar <= delta, r, delta * torch.sign(r))
-    pred = y * sd + mu
+    pred = xs.to(torch.float64) + y * sd
     wp = 0.5 * (pred[:, :6] ** 2).sum(dim=(1, 2, 3, 4))
     wt = 0.5 * (tt[:, :6].to(torch.float64) ** 2).sum(dim=(1, 2, 3, 4))
     wtot = float(wt.sum())

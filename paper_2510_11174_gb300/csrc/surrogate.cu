@@ -124,22 +124,22 @@ __global__ void k_sur_prep(const float *__restrict__ x, int B, long long V, cons
     dst[1] = reinterpret_cast<const uint4 *>(o)[1];
 }
 
-// y [B][V][16] (normalised) -> [B][10][V] de-normalised
-__global__ void k_sur_out(const float *__restrict__ y, int B, long long V, const float *__restrict__ mean,
+// prediction [B][10][V] = x + std_c y (y [B][V][16]: the change in units of the channel's spread)
+__global__ void k_sur_out(const float *__restrict__ y, const float *__restrict__ x, int B, long long V,
                           const float *__restrict__ sd, float *__restrict__ out) {
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (t >= (long long)B * V * NCH) return;
     const long long b = t / (V * NCH), c = (t / V) % NCH, v = t % V;
-    out[t] = y[(b * V + v) * 16 + c] * sd[c] + mean[c];
+    out[t] = x[t] + y[(b * V + v) * 16 + c] * sd[c];
 }
 
 // MC statistics: pass k (1-based) folded into the running mean and M2 (Welford)
-__global__ void k_sur_mc(const float *__restrict__ y, int B, long long V, const float *__restrict__ mean,
+__global__ void k_sur_mc(const float *__restrict__ y, const float *__restrict__ x, int B, long long V,
                          const float *__restrict__ sd, int k, float *__restrict__ pm, float *__restrict__ m2) {
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (t >= (long long)B * V * NCH) return;
     const long long b = t / (V * NCH), c = (t / V) % NCH, v = t % V;
-    const float val = y[(b * V + v) * 16 + c] * sd[c] + mean[c];
+    const float val = x[t] + y[(b * V + v) * 16 + c] * sd[c];
     if (k == 1) {
         pm[t] = val;
         m2[t] = 0.0f;
@@ -171,7 +171,7 @@ __device__ __forceinline__ double blk_sum(double v, double *sh) {
 // per-sample field energies of prediction and target (de-normalised channels
 // 0..5): grid (blocks, B), part[b][blk][2]
 __global__ void __launch_bounds__(RB) k_sur_energy(const float *__restrict__ y, const float *__restrict__ tg,
-                                                   long long V, const float *__restrict__ mean,
+                                                   const float *__restrict__ x, long long V,
                                                    const float *__restrict__ sd, double *__restrict__ part) {
     __shared__ double sh[RB];
     const int b = blockIdx.y;
@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(RB) k_sur_energy(const float *__restrict__ y, 
         float sp = 0.0f, st = 0.0f;
 #pragma unroll
         for (int c = 0; c < 6; ++c) {
-            const float p = y[((long long)b * V + v) * 16 + c] * sd[c] + mean[c];
+            const float p = x[((long long)b * NCH + c) * V + v] + y[((long long)b * V + v) * 16 + c] * sd[c];
             const float q = tg[((long long)b * NCH + c) * V + v];
             sp += p * p;
             st += q * q;
@@ -211,8 +211,8 @@ __global__ void k_sur_esum(const double *__restrict__ part, int B, int nblk, dou
 
 // loss gradient dL/dy (FP32 G and its BF16 copy dz, [cells][16]) and the
 // Huber partial sums
-__global__ void __launch_bounds__(RB) k_sur_loss(const float *__restrict__ y, const float *__restrict__ tg, int B,
-                                                 long long V, const float *__restrict__ mean,
+__global__ void __launch_bounds__(RB) k_sur_loss(const float *__restrict__ y, const float *__restrict__ tg,
+                                                 const float *__restrict__ x, int B, long long V,
                                                  const float *__restrict__ sd, float delta, float lam,
                                                  const double *__restrict__ esum, float *__restrict__ G,
                                                  __nv_bfloat16 *__restrict__ dz, double *__restrict__ part) {
@@ -237,11 +237,12 @@ __global__ void __launch_bounds__(RB) k_sur_loss(const float *__restrict__ y, co
             float gc = 0.0f;
             if (c < NCH) {
                 const float yc = y[t * 16 + c];
-                const float tn = (tg[(b * NCH + c) * V + v] - mean[c]) / sd[c];
+                const float xc = x[(b * NCH + c) * V + v];
+                const float tn = (tg[(b * NCH + c) * V + v] - xc) / sd[c];
                 const float r = yc - tn, ar = fabsf(r);
                 hs += ar <= delta ? 0.5 * (double)r * r : (double)delta * ((double)ar - 0.5 * delta);
                 gc = (ar <= delta ? r : copysignf(delta, r)) * (float)inv_n;
-                if (c < 6) gc += lam * ecoef * sd[c] * (yc * sd[c] + mean[c]);
+                if (c < 6) gc += lam * ecoef * sd[c] * (xc + yc * sd[c]);
             }
             g[c] = gc;
             o[c] = __float2bfloat16_rn(gc);
@@ -612,7 +613,7 @@ hyb_status hyb_surrogate_forward(hyb_surrogate *m, const float *x, int B, int D,
     if (s != HYB_OK) return s;
     k_sur_prep<<<nbk(cells), RB, 0, m->stream>>>(x, B, V, m->mean, m->std_, m->a[0]);
     if ((s = forward(m, B, D, H, W, pass)) != HYB_OK) return s;
-    k_sur_out<<<nbk(cells * NCH), RB, 0, m->stream>>>(m->y, B, V, m->mean, m->std_, y);
+    k_sur_out<<<nbk(cells * NCH), RB, 0, m->stream>>>(m->y, x, B, V, m->std_, y);
     HYB_CUDA_TRY(cudaGetLastError());
     return HYB_OK;
 }
@@ -627,7 +628,7 @@ hyb_status hyb_surrogate_mc(hyb_surrogate *m, const float *x, int B, int D, int 
     const int K = m->d.mc_passes;
     for (int k = 1; k <= K; ++k) {
         if ((s = forward(m, B, D, H, W, k - 1)) != HYB_OK) return s;
-        k_sur_mc<<<nbk(cells * NCH), RB, 0, m->stream>>>(m->y, B, V, m->mean, m->std_, k, pm, ps);
+        k_sur_mc<<<nbk(cells * NCH), RB, 0, m->stream>>>(m->y, x, B, V, m->std_, k, pm, ps);
     }
     k_sur_mc_final<<<nbk(cells * NCH), RB, 0, m->stream>>>(cells * NCH, K, ps);
     HYB_CUDA_TRY(cudaGetLastError());
@@ -656,9 +657,9 @@ hyb_status hyb_surrogate_train_step(hyb_surrogate *m, const float *x, const floa
     k_sur_prep<<<nbk(cells), RB, 0, st>>>(x, B, V, m->mean, m->std_, m->a[0]);
     if ((s = forward(m, B, D, H, W, pass)) != HYB_OK) return s;
     // loss: per-sample energies, then the gradient dL/dy (G[SL] and dz)
-    k_sur_energy<<<dim3(m->eblocks, B), RB, 0, st>>>(m->y, tg, V, m->mean, m->std_, m->epart);
+    k_sur_energy<<<dim3(m->eblocks, B), RB, 0, st>>>(m->y, tg, x, V, m->std_, m->epart);
     k_sur_esum<<<nbk(B), RB, 0, st>>>(m->epart, B, m->eblocks, m->esum);
-    k_sur_loss<<<m->lblocks, RB, 0, st>>>(m->y, tg, B, V, m->mean, m->std_, (float)m->d.huber_delta,
+    k_sur_loss<<<m->lblocks, RB, 0, st>>>(m->y, tg, x, B, V, m->std_, (float)m->d.huber_delta,
                                           (float)m->d.energy_weight, m->esum, m->G[SL], m->dz, m->lpart);
     // backward, last layer first
     for (int l = SL - 1; l >= 0; --l) {

@@ -1,6 +1,6 @@
 """The field surrogate on the GPU (hyb_surrogate_*, tcgen05 convolutions in
-channel chunks) against the oracle: the identity-map weights reproduce the
-state; forward passes with and without dropout, the MC-dropout statistics,
+channel chunks) against the oracle: the identity-map weights forecast
+2 x - mean; forward passes with and without dropout, the MC-dropout statistics,
 one step's gradients and three Adam steps on seeded weights and states; the
 ten-channel node state of a hybrid run; and a falling loss."""
 import numpy as np
@@ -38,7 +38,7 @@ def _identity_weights():
     return list(zip(w, b))
 
 
-def test_identity_weights_reproduce_the_state():
+def test_identity_weights_give_twice_the_state_less_the_mean():
     from paper_2510_11174_gb300 import inputs
     x, mean, std = inputs.random_states(2, 16, seed=1)
     m, orc, _ = _pair(mean=mean, std=std, weights=_identity_weights())
@@ -46,7 +46,8 @@ def test_identity_weights_reproduce_the_state():
     ref = orc.predict(x).numpy()
     np.testing.assert_allclose(y, ref, rtol=0, atol=1e-5)
     xh = (x - mean[None, :, None, None, None]) / std[None, :, None, None, None]
-    assert np.all(np.abs(y - x) <= 2.0 ** -8 * np.abs(xh) * std[None, :, None, None, None] + 1e-5)
+    target = 2.0 * x - mean[None, :, None, None, None]
+    assert np.all(np.abs(y - target) <= 2.0 ** -8 * np.abs(xh) * std[None, :, None, None, None] + 1e-5)
     m.close()
 
 
@@ -57,8 +58,8 @@ def test_forward_matches_oracle(pass_index):
     m, orc, _ = _pair(mean=mean, std=std)
     y = m.forward(torch.from_numpy(x).cuda(), pass_index).cpu().numpy()
     ref = orc.predict(x, pass_index).numpy()
-    err = rel_l2(y - mean[None, :, None, None, None], ref - mean[None, :, None, None, None])
-    assert err <= 1e-3, err   # measured 4e-4 .. 6e-4
+    err = rel_l2(y - x, ref - x)   # the predicted change
+    assert err <= 1e-3, err        # measured 4e-4 .. 6e-4
     m.close()
 
 
@@ -68,8 +69,7 @@ def test_mc_statistics_match_oracle():
     m, orc, _ = _pair(mean=mean, std=std, mc_passes=4)
     pm, ps = m.mc(torch.from_numpy(x).cuda())
     om, os_ = orc.mc_statistics(x, 4)
-    mu = mean[None, :, None, None, None]
-    assert rel_l2(pm.cpu().numpy() - mu, om.numpy() - mu) <= 2e-3
+    assert rel_l2(pm.cpu().numpy() - x, om.numpy() - x) <= 2e-3
     assert float(ps.min()) >= 0.0
     assert rel_l2(ps.cpu().numpy(), os_.numpy()) <= 2e-2
     m.close()

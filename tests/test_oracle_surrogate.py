@@ -1,11 +1,12 @@
 """Pins of the surrogate oracle (oracle/surrogate.py) that do not come from
-the oracle itself: a choice of weights for which the network is the
-identity map (zero kernels on the residual layers, centre-tap +/- identities
-on the others), so the prediction is the input itself, with no spread over
-MC-dropout passes; a zero loss for a perfect prediction and the Huber
-closed form for a constant offset; the backward pass against FP64 central
-differences; and the node state's charge against the particles' total
-charge."""
+the oracle itself: with every weight zero the residual forecast is the input
+state (persistence); a choice of weights for which the network's output is
+its normalised input (zero kernels on the shortcut layers, centre-tap +/-
+identities on the others), so the prediction is x + std (x - mean) / std =
+2 x - mean, with no spread over MC-dropout passes; a zero loss for a perfect
+prediction and the Huber closed form for an offset; the backward pass
+against FP64 central differences; and the node state's charge against the
+particles' total charge."""
 import math
 
 import numpy as np
@@ -41,16 +42,27 @@ def _states(B=2, n=6, seed=1):
     return x, mean, std
 
 
-def test_identity_weights_reproduce_the_state():
+def test_zero_weights_forecast_persistence():
+    x, mean, std = _states()
+    zero = [(np.zeros((co, ci, 3, 3, 3), np.float32), np.zeros(co, np.float32)) for ci, co in S.LAYERS]
+    net = S.OracleSurrogate(zero, mean=mean, std=std)
+    np.testing.assert_array_equal(net.predict(x).numpy(), x.astype(np.float64))
+    m, s = net.mc_statistics(x, 3)
+    np.testing.assert_array_equal(m.numpy(), x.astype(np.float64))
+    assert float(s.abs().max()) == 0.0
+
+
+def test_identity_weights_give_twice_the_state_less_the_mean():
     x, mean, std = _states()
     net = S.OracleSurrogate(_identity_weights(), mean=mean, std=std)
+    target = 2.0 * x.astype(np.float64) - mean[None, :, None, None, None]
     exact = net.predict(x, exact=True).numpy()
-    np.testing.assert_allclose(exact, x, rtol=0, atol=1e-6)
+    np.testing.assert_allclose(exact, target, rtol=0, atol=1e-5)
     # BF16 rounding of the normalised input (8 significant bits): |error| <= 2^-8 |x_hat| std
     rounded = net.predict(x).numpy()
     xh = (x - mean[None, :, None, None, None]) / std[None, :, None, None, None]
-    bound = 2.0 ** -8 * np.abs(xh) * std[None, :, None, None, None] + 1e-6
-    assert np.all(np.abs(rounded - x) <= bound)
+    bound = 2.0 ** -8 * np.abs(xh) * std[None, :, None, None, None] + 1e-5
+    assert np.all(np.abs(rounded - target) <= bound)
 
 
 def test_identity_weights_have_no_mc_spread():
@@ -64,23 +76,24 @@ def test_identity_weights_have_no_mc_spread():
 def test_loss_of_a_perfect_prediction_is_zero_and_huber_of_an_offset():
     x, mean, std = _states(seed=3)
     net = S.OracleSurrogate(_identity_weights(), mean=mean, std=std)
-    # zero up to the FP32 rounding of the normalisation (the target is
-    # normalised in FP32, the prediction de-normalised in FP64)
-    out = S.loss_and_grads(net, x, x, -1, exact=True)
-    assert out["loss"] == pytest.approx(0.0, abs=1e-12)
+    # zero up to the FP32 rounding of the normalisation (the target change is
+    # formed in FP32, the prediction in FP64)
+    t = net.predict(x, exact=True).numpy().astype(np.float32)
+    out = S.loss_and_grads(net, x, t, -1, exact=True)
+    assert out["loss"] == pytest.approx(0.0, abs=1e-10)
     for gw, gb in out["grads"]:
-        assert float(gw.abs().max()) < 1e-8 and float(gb.abs().max()) < 1e-8
+        assert float(gw.abs().max()) < 1e-6 and float(gb.abs().max()) < 1e-6
     # channel 9 (rho, outside the energy) off by c in normalised units: every
     # value of that channel contributes delta (|c| - delta / 2) (|c| > delta)
     # or c^2 / 2 (|c| <= delta)
     for c, delta in ((0.3, 0.01), (0.004, 0.01)):
-        t = x.copy()
-        t[:, 9] -= c * std[9]
-        out = S.loss_and_grads(net, x, t, -1, delta=delta, exact=True)
+        tc = t.copy()
+        tc[:, 9] -= c * std[9]
+        out = S.loss_and_grads(net, x, tc, -1, delta=delta, exact=True)
         per = delta * (c - 0.5 * delta) if c > delta else 0.5 * c * c
         # (the offset is applied in FP32 to values of order 1: rel 1e-3)
         assert out["huber"] == pytest.approx(per / 10.0, rel=1e-3)
-        assert out["energy"] == pytest.approx(0.0, abs=1e-12)
+        assert out["energy"] == pytest.approx(0.0, abs=1e-10)
 
 
 def test_backward_matches_central_differences():
