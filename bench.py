@@ -578,14 +578,30 @@ def run_train_surrogate(args, P, torch, stream):
     clk = clocks.stop()
     ms = e0.elapsed_time(e1)
     # held-out accuracy: MC-dropout mean prediction, and the persistence baseline (t predicted by x)
-    pm, ps = [], []
-    for k in range(0, xte.shape[0], 32):
-        a, b = m.mc(xte[k:k + 32])
-        pm.append(a)
-        ps.append(b)
-    pm, ps = torch.cat(pm), torch.cat(ps)
-    torch.cuda.synchronize()
+    def held_out(model):
+        pm, ps = [], []
+        for k in range(0, xte.shape[0], 32):
+            a, b = model.mc(xte[k:k + 32])
+            pm.append(a)
+            ps.append(b)
+        pm, ps = torch.cat(pm), torch.cat(ps)
+        torch.cuda.synchronize()
+        return pm, ps
+
+    pm, ps = held_out(m)
     r2, mse = training.r2_mse(pm, tte, mean, std)
+    # the same training with the Huber threshold at one spread of the
+    # normalised change: Table 2's delta = 0.01 sits far above the values of
+    # the paper's plasma-frequency units (|E| <= 3e-4 there), where the loss
+    # is quadratic; on z-scored values of order 1 it is L1-like instead
+    mq = P.Surrogate(dropout=0.1, mc_passes=MC_PASSES, seed=11, mean=mean, std=std, huber_delta=1.0,
+                     stream=stream.cuda_stream)
+    t2 = time.perf_counter()
+    training.train_surrogate(mq, xtr, ttr, SUR_PRETRAIN_STEPS)
+    q_s = time.perf_counter() - t2
+    pq, _ = held_out(mq)
+    r2q, mseq = training.r2_mse(pq, tte, mean, std)
+    mq.close()
     r2_keep, mse_keep = training.r2_mse(xte, tte, mean, std)
     sd = torch.tensor(std, device=ps.device).view(1, -1, 1, 1, 1)
     cells = 32 * 16 ** 3
@@ -617,6 +633,8 @@ def run_train_surrogate(args, P, torch, stream):
                          "persistence_r2_mean": float(np.mean(r2_keep)),
                          "mc_std_mean_normalised": float((ps / sd).mean()),
                          "mc_std_max_normalised": float((ps / sd).max()),
+                         "huber_delta_1": {"r2": dict(zip(names, r2q)), "mse": dict(zip(names, mseq)),
+                                           "r2_mean": float(np.mean(r2q)), "train_s": q_s},
                          "paper_context": "R^2 0.9778 and MSE 1.47e-4 on the paper's own data (Results)"},
             "clocks": clk, "gpu_launches": None}
 

@@ -41,8 +41,9 @@ struct WgradTcArgs {
     float *part;             // [grid][G][128][N] FP32 partials
     long long ksteps;        // K-steps of 16 positions
     int nslots;              // tap slots used (<= G * TG)
-    int koff[WG_MAX_SLOTS];  // per slot: K offset (positions) of its ZT box, a multiple of 8
-    int zrow[WG_MAX_SLOTS];  // per slot: first ZT row of its box
+    int nboxes;              // ZT boxes per K-step
+    int box_rows;            // rows of one ZT box (the slots of its taps times COP)
+    int koff[WG_MAX_SLOTS];  // per box: K offset (positions) of the box, a multiple of 8
     int xrow;                // first XT row of the N columns
     int *status;
 };
@@ -107,7 +108,8 @@ __global__ void __launch_bounds__(192, 1) k_wgrad_tc(const __grid_constant__ CUt
     const long long per = (a.ksteps + gridDim.x - 1) / gridDim.x;
     const long long k0 = (long long)blockIdx.x * per, k1 = min(k0 + per, a.ksteps);
     const uint32_t ring_s = smem_u32(ring);
-    const uint32_t stage_bytes = (uint32_t)(Cfg::BBYTES + a.nslots * Cfg::ABYTES);
+    const uint32_t box_bytes = (uint32_t)(a.box_rows * 32);
+    const uint32_t stage_bytes = (uint32_t)Cfg::BBYTES + (uint32_t)a.nboxes * box_bytes;
 
     if (warp == 0) {
         if (lane == 0) {
@@ -125,11 +127,9 @@ __global__ void __launch_bounds__(192, 1) k_wgrad_tc(const __grid_constant__ CUt
                 const uint32_t st = ring_s + (uint32_t)(s * Cfg::STAGE);
                 const int p0 = (int)(k * 16);
                 tma_load_2d_w(st, &tx, p0, a.xrow, fb);
-                for (int sl = 0; sl < a.nslots; ++sl) {
-                    const int g = sl / TG, j = sl % TG;
-                    tma_load_2d_w(st + (uint32_t)(Cfg::BBYTES + g * 4096 + j * Cfg::ABYTES), &tz, p0 - a.koff[sl],
-                                  a.zrow[sl], fb);
-                }
+                // the boxes land back to back: row (tap, co) of the A tiles is tap * COP + co
+                for (int bx = 0; bx < a.nboxes; ++bx)
+                    tma_load_2d_w(st + (uint32_t)Cfg::BBYTES + (uint32_t)bx * box_bytes, &tz, p0 - a.koff[bx], 0, fb);
                 ++issued;
                 if (++s == STAGES) {
                     s = 0;
@@ -204,19 +204,27 @@ __global__ void __launch_bounds__(192, 1) k_wgrad_tc(const __grid_constant__ CUt
     if (warp == 1) tmem_dealloc(taddr, Cfg::TCOLS);
 }
 
-// channels-last BF16 src [cells][pitch] (channels c0 .. c0 + nc - 1) -> channel-major
-// over the padded volume, dst[c][p(b, z + 1, y + 1, x + 1 + dx)] (dst zeroed before)
+// channels-last BF16 src [cells][pitch] (channels c0 .. c0 + nc - 1, c0 a
+// multiple of 16, c0 + nc rounded up to 16 within the pitch) -> channel-major
+// over the padded volume, dst[c][p(b, z + 1, y + 1, x + 1 + dx)] (dst zeroed
+// before); one thread per cell (16-byte loads), a warp stores 32 neighbouring
+// positions of one channel at a time
 __global__ void k_to_padded(const __nv_bfloat16 *__restrict__ src, int pitch, int c0, int nc, int B, int D, int H,
                             int W, int Wp, int dx, long long P, __nv_bfloat16 *__restrict__ dst) {
     const long long cells = (long long)B * D * H * W;
-    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (t >= cells * nc) return;
-    const long long cell = t / nc;
-    const int c = (int)(t % nc);
+    const long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (cell >= cells) return;
     const int x = (int)(cell % W), y = (int)((cell / W) % H), z = (int)((cell / ((long long)W * H)) % D);
     const long long b = cell / ((long long)W * H * D);
     const long long p = ((b * (D + 2) + z + 1) * (H + 2) + y + 1) * Wp + x + 1 + dx;
-    dst[(long long)c * P + p] = src[cell * pitch + c0 + c];
+    const uint4 *s4 = reinterpret_cast<const uint4 *>(src + cell * pitch + c0);
+    for (int g = 0; g * 8 < nc; ++g) {
+        uint4 u = s4[g];
+        const __nv_bfloat16 *h = reinterpret_cast<const __nv_bfloat16 *>(&u);
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            if (g * 8 + j < nc) dst[(long long)(g * 8 + j) * P + p] = h[j];
+    }
 }
 
 // FP32 [cells] -> BF16 channel 0 of the padded volume (the last layer's dlogit)
@@ -230,14 +238,19 @@ __global__ void k_f32_to_padded(const float *__restrict__ src, int B, int D, int
     dst[((b * (D + 2) + z + 1) * (H + 2) + y + 1) * Wp + x + 1 + dx] = __float2bfloat16_rn(src[cell]);
 }
 
-// channels-last BF16 src [cells][pitch] (channels c0 .. c0 + nc - 1) -> channel-major dst[c][cell]
+// channels-last BF16 src [cells][pitch] (as k_to_padded) -> channel-major dst[c][cell]
 __global__ void k_to_cm(const __nv_bfloat16 *__restrict__ src, int pitch, int c0, int nc, long long cells, long long P,
                         __nv_bfloat16 *__restrict__ dst) {
-    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (t >= cells * nc) return;
-    const long long cell = t / nc;
-    const int c = (int)(t % nc);
-    dst[(long long)c * P + cell] = src[cell * pitch + c0 + c];
+    const long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (cell >= cells) return;
+    const uint4 *s4 = reinterpret_cast<const uint4 *>(src + cell * pitch + c0);
+    for (int g = 0; g * 8 < nc; ++g) {
+        uint4 u = s4[g];
+        const __nv_bfloat16 *h = reinterpret_cast<const __nv_bfloat16 *>(&u);
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            if (g * 8 + j < nc) dst[(long long)(g * 8 + j) * P + cell] = h[j];
+    }
 }
 
 // bias partials of an FP32 gradient of one channel: bpart[blk] = sum over the block's cells
@@ -370,7 +383,8 @@ hyb_status wgrad_tc(const WgradJob &j, WgradScratch &ws, cudaStream_t st) {
     }
     __nv_bfloat16 *ZT = (__nv_bfloat16 *)ws.buf, *XT = (__nv_bfloat16 *)((char *)ws.buf + zbytes);
     cudaMemsetAsync(ws.buf, 0, (size_t)(zbytes + xbytes), st);
-    const unsigned nbz = (unsigned)((cells * j.co_n + 255) / 256), nbx = (unsigned)((cells * j.ci_n + 255) / 256);
+    if (j.ci0 % 16 || j.co0 % 16) return set_error(HYB_EINVAL, "wgrad: channel blocks start at multiples of 16");
+    const unsigned nbz = (unsigned)((cells + 255) / 256), nbx = nbz;
     if (conv) {
         // copy dx + 1 holds dZ at the position of the cell shifted by dx along x
         for (int c = 0; c < 3; ++c) {
@@ -394,21 +408,25 @@ hyb_status wgrad_tc(const WgradJob &j, WgradScratch &ws, cudaStream_t st) {
     a.xrow = 0;
     const int TG = 128 / cop;
     if (conv) {
-        // tap t = (dz, dy, dx): ZT copy dx + 1 at the position shifted back by
-        // dz (H + 2) Wp + dy Wp, a multiple of 8 positions
+        // tap t = (dz, dy, dx) = 3 (3 (dz + 1) + dy + 1) + dx + 1: ZT copy dx + 1 at
+        // the position shifted back by dz (H + 2) Wp + dy Wp (a multiple of 8
+        // positions); the three copies of one (dz, dy) are one box of 3 COP rows
         a.nslots = 27;
-        for (int t = 0; t < 27; ++t) {
-            const int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
-            a.koff[t] = dz * (j.H + 2) * Wp + dy * Wp;
-            a.zrow[t] = (dx + 1) * cop;
+        a.nboxes = 9;
+        a.box_rows = 3 * cop;
+        for (int bx = 0; bx < 9; ++bx) {
+            const int dz = bx / 3 - 1, dy = bx % 3 - 1;
+            a.koff[bx] = dz * (j.H + 2) * Wp + dy * Wp;
         }
     } else {
         a.nslots = 1;
+        a.nboxes = 1;
+        a.box_rows = cop;
     }
     const int G = (a.nslots + TG - 1) / TG;
     const int grid = (int)std::min<long long>(a.ksteps, (long long)n_sms());
     const long long pneed = (long long)grid * G * 128 * N;
-    const long long bneed = 256LL * 128;
+    const long long bneed = 2048LL * 128;
     if (ws.pbytes < (pneed > bneed ? pneed : bneed) * 4) {
         if (ws.part) cudaFree(ws.part);
         ws.part = nullptr;
@@ -420,7 +438,7 @@ hyb_status wgrad_tc(const WgradJob &j, WgradScratch &ws, cudaStream_t st) {
     }
     a.part = ws.part;
     CUtensorMap tz, tx;
-    hyb_status s = cm_map(&tz, ZT, Pr, ncp * cop, cop);
+    hyb_status s = cm_map(&tz, ZT, Pr, ncp * cop, a.box_rows);
     if (s == HYB_OK) s = cm_map(&tx, XT, Pr, N, N);
     if (s != HYB_OK) return s;
     if (cop == 16 && N == 16) s = wg_launch<16, 16>(tz, tx, a, grid, st);
@@ -437,7 +455,7 @@ hyb_status wgrad_tc(const WgradJob &j, WgradScratch &ws, cudaStream_t st) {
         ws.part, grid, G, N, cop, TG, nt, j.co_n, j.ci_n, j.co0, j.ci0, j.ci_tot, j.gw);
     if (j.gb) {
         // bias: per-block sums over the cells, then the blocks in order
-        const int nblk = 256;
+        const int nblk = 2048;
         const long long per = (cells + nblk - 1) / nblk;
         float *bpart = ws.part;  // the partials above are consumed by the reduction first (stream order)
         if (j.dz_f32)
