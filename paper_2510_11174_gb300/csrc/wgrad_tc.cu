@@ -5,11 +5,13 @@
 //
 //   dW[co][ci][t] = sum over cells of dZ[cell][co] X[cell + s(t)][ci]
 //
-// is a contraction over the cells.  Both operands are first laid out
-// channel-major over the zero-padded volume (positions p of B x (D+2) x
-// (H+2) x Wp, Wp = W + 2 rounded up to 8), so that a cell's neighbour along
-// z or y is a shift of p by a multiple of 8 (16 bytes); the x-shift comes
-// from three copies of dZ shifted by -1, 0, +1 in x.  With p' = p - s(t):
+// is a contraction over the cells.  Both operands are first laid out over
+// the zero-padded volume (positions p of B x (D+2) x (H+2) x Wp, Wp = W + 2
+// rounded up to 16) in chunks of 16 positions, [p / 16][channel][p % 16], so
+// that a cell's neighbour along z or y is a shift by whole chunks and the 16
+// positions of every channel of one chunk are one contiguous block (one TMA
+// box, one stretch of memory); the x-shift comes from three copies of dZ
+// shifted by -1, 0, +1 in x.  With p' = p - s(t):
 //   dW[co][ci][t] = sum_p ZT_dx[co][p - s_zy(t)] XT[ci][p],
 // so the MMA's M rows are (tap, co) pairs of several taps -- each a TMA box
 // of ZT at its own shifted coordinate -- and its N columns are ci; K runs
@@ -43,16 +45,17 @@ struct WgradTcArgs {
     int nslots;              // tap slots used (<= G * TG)
     int nboxes;              // ZT boxes per K-step
     int box_rows;            // rows of one ZT box (the slots of its taps times COP)
-    int koff[WG_MAX_SLOTS];  // per box: K offset (positions) of the box, a multiple of 8
+    int koff[WG_MAX_SLOTS];  // per box: shift of the box in chunks of 16 positions
     int xrow;                // first XT row of the N columns
     int *status;
 };
 
-__device__ __forceinline__ void tma_load_2d_w(uint32_t dst, const void *tmap, int c0, int c1, uint32_t mbar) {
+// box of (16 positions, rows) of the chunked layout at (row r0, chunk k)
+__device__ __forceinline__ void tma_load_chunk(uint32_t dst, const void *tmap, int r0, int k, uint32_t mbar) {
     asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
-        "[%4];" ::"r"(dst),
-        "l"(tmap), "r"(c0), "r"(c1), "r"(mbar)
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
+        "%4}], [%5];" ::"r"(dst),
+        "l"(tmap), "r"(0), "r"(r0), "r"(k), "r"(mbar)
         : "memory");
 }
 
@@ -125,11 +128,10 @@ __global__ void __launch_bounds__(192, 1) k_wgrad_tc(const __grid_constant__ CUt
                 const uint32_t fb = smem_u32(&full_b[s]);
                 mbar_arrive_expect_tx(fb, stage_bytes);
                 const uint32_t st = ring_s + (uint32_t)(s * Cfg::STAGE);
-                const int p0 = (int)(k * 16);
-                tma_load_2d_w(st, &tx, p0, a.xrow, fb);
+                tma_load_chunk(st, &tx, a.xrow, (int)k, fb);
                 // the boxes land back to back: row (tap, co) of the A tiles is tap * COP + co
                 for (int bx = 0; bx < a.nboxes; ++bx)
-                    tma_load_2d_w(st + (uint32_t)Cfg::BBYTES + (uint32_t)bx * box_bytes, &tz, p0 - a.koff[bx], 0, fb);
+                    tma_load_chunk(st + (uint32_t)Cfg::BBYTES + (uint32_t)bx * box_bytes, &tz, 0, (int)k - a.koff[bx], fb);
                 ++issued;
                 if (++s == STAGES) {
                     s = 0;
@@ -204,13 +206,16 @@ __global__ void __launch_bounds__(192, 1) k_wgrad_tc(const __grid_constant__ CUt
     if (warp == 1) tmem_dealloc(taddr, Cfg::TCOLS);
 }
 
+// element (row r, position p) of the chunked layout with R rows
+__device__ __forceinline__ long long chunk_idx(long long p, int r, int R) { return ((p >> 4) * R + r) * 16 + (p & 15); }
+
 // channels-last BF16 src [cells][pitch] (channels c0 .. c0 + nc - 1, c0 a
-// multiple of 16, c0 + nc rounded up to 16 within the pitch) -> channel-major
-// over the padded volume, dst[c][p(b, z + 1, y + 1, x + 1 + dx)] (dst zeroed
-// before); one thread per cell (16-byte loads), a warp stores 32 neighbouring
-// positions of one channel at a time
+// multiple of 16, c0 + nc rounded up to 16 within the pitch) -> rows r0 ..
+// r0 + nc - 1 of the chunked layout (R rows) over the padded volume, at the
+// position of the cell shifted by dx along x (dst zeroed before); one thread
+// per cell (16-byte loads)
 __global__ void k_to_padded(const __nv_bfloat16 *__restrict__ src, int pitch, int c0, int nc, int B, int D, int H,
-                            int W, int Wp, int dx, long long P, __nv_bfloat16 *__restrict__ dst) {
+                            int W, int Wp, int dx, int r0, int R, __nv_bfloat16 *__restrict__ dst) {
     const long long cells = (long long)B * D * H * W;
     const long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (cell >= cells) return;
@@ -223,23 +228,24 @@ __global__ void k_to_padded(const __nv_bfloat16 *__restrict__ src, int pitch, in
         const __nv_bfloat16 *h = reinterpret_cast<const __nv_bfloat16 *>(&u);
 #pragma unroll
         for (int j = 0; j < 8; ++j)
-            if (g * 8 + j < nc) dst[(long long)(g * 8 + j) * P + p] = h[j];
+            if (g * 8 + j < nc) dst[chunk_idx(p, r0 + g * 8 + j, R)] = h[j];
     }
 }
 
-// FP32 [cells] -> BF16 channel 0 of the padded volume (the last layer's dlogit)
-__global__ void k_f32_to_padded(const float *__restrict__ src, int B, int D, int H, int W, int Wp, int dx,
-                                __nv_bfloat16 *__restrict__ dst) {
+// FP32 [cells] -> BF16 row r0 of the chunked layout (the last layer's dlogit)
+__global__ void k_f32_to_padded(const float *__restrict__ src, int B, int D, int H, int W, int Wp, int dx, int r0,
+                                int R, __nv_bfloat16 *__restrict__ dst) {
     const long long cells = (long long)B * D * H * W;
     const long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (cell >= cells) return;
     const int x = (int)(cell % W), y = (int)((cell / W) % H), z = (int)((cell / ((long long)W * H)) % D);
     const long long b = cell / ((long long)W * H * D);
-    dst[((b * (D + 2) + z + 1) * (H + 2) + y + 1) * Wp + x + 1 + dx] = __float2bfloat16_rn(src[cell]);
+    dst[chunk_idx(((b * (D + 2) + z + 1) * (H + 2) + y + 1) * Wp + x + 1 + dx, r0, R)] = __float2bfloat16_rn(src[cell]);
 }
 
-// channels-last BF16 src [cells][pitch] (as k_to_padded) -> channel-major dst[c][cell]
-__global__ void k_to_cm(const __nv_bfloat16 *__restrict__ src, int pitch, int c0, int nc, long long cells, long long P,
+// channels-last BF16 src [cells][pitch] (as k_to_padded) -> rows 0 .. nc - 1 of
+// the chunked layout (R rows) over the cells (dense layers)
+__global__ void k_to_cm(const __nv_bfloat16 *__restrict__ src, int pitch, int c0, int nc, long long cells, int R,
                         __nv_bfloat16 *__restrict__ dst) {
     const long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (cell >= cells) return;
@@ -249,7 +255,7 @@ __global__ void k_to_cm(const __nv_bfloat16 *__restrict__ src, int pitch, int c0
         const __nv_bfloat16 *h = reinterpret_cast<const __nv_bfloat16 *>(&u);
 #pragma unroll
         for (int j = 0; j < 8; ++j)
-            if (g * 8 + j < nc) dst[(long long)(g * 8 + j) * P + cell] = h[j];
+            if (g * 8 + j < nc) dst[chunk_idx(cell, g * 8 + j, R)] = h[j];
     }
 }
 
@@ -304,15 +310,15 @@ static EncodeTiledFn3 encode_fn3() {
     return fn;
 }
 
-// 2D map over a channel-major BF16 array [rows][P], box (16 positions, box_rows)
+// 3D map over the chunked layout [P / 16][rows][16] (BF16), box (16 positions, box_rows, 1 chunk)
 static hyb_status cm_map(CUtensorMap *tm, const __nv_bfloat16 *base, long long P, int rows, int box_rows) {
     EncodeTiledFn3 enc = encode_fn3();
     if (!enc) return set_error(HYB_ECUDA, "cuTensorMapEncodeTiled is not available");
-    const cuuint64_t dims[2] = {(cuuint64_t)P, (cuuint64_t)rows};
-    const cuuint64_t strides[1] = {(cuuint64_t)P * 2};
-    const cuuint32_t box[2] = {16, (cuuint32_t)box_rows};
-    const cuuint32_t estr[2] = {1, 1};
-    CUresult r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void *)base, dims, strides, box, estr,
+    const cuuint64_t dims[3] = {16, (cuuint64_t)rows, (cuuint64_t)(P / 16)};
+    const cuuint64_t strides[2] = {32, (cuuint64_t)rows * 32};
+    const cuuint32_t box[3] = {16, (cuuint32_t)box_rows, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void *)base, dims, strides, box, estr,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return set_error(HYB_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
@@ -362,7 +368,7 @@ hyb_status wgrad_tc(const WgradJob &j, WgradScratch &ws, cudaStream_t st) {
     if (cells < 1 || j.co_n < 1 || j.ci_n < 1) return set_error(HYB_EINVAL, "wgrad: empty operand");
     if (cells >= (1LL << 30)) return set_error(HYB_EINVAL, "wgrad: more than 2^30 cells");
     // positions: the padded volume (conv) or the cells (dense)
-    const int Wp = conv ? (j.W + 2 + 7) / 8 * 8 : 1;
+    const int Wp = conv ? (j.W + 2 + 15) / 16 * 16 : 1;
     const long long P = conv ? (long long)j.B * (j.D + 2) * (j.H + 2) * Wp : cells;
     const long long Pr = (P + 15) / 16 * 16;
     const int cop = j.co_n <= 16 ? 16 : (j.co_n <= 32 ? 32 : 128);
@@ -388,18 +394,16 @@ hyb_status wgrad_tc(const WgradJob &j, WgradScratch &ws, cudaStream_t st) {
     if (conv) {
         // copy dx + 1 holds dZ at the position of the cell shifted by dx along x
         for (int c = 0; c < 3; ++c) {
-            __nv_bfloat16 *dstc = ZT + (long long)c * cop * Pr;
             if (j.dz_f32)
-                k_f32_to_padded<<<(unsigned)((cells + 255) / 256), 256, 0, st>>>(j.dz_f32, j.B, j.D, j.H, j.W, Wp,
-                                                                                c - 1, dstc);
+                k_f32_to_padded<<<nbz, 256, 0, st>>>(j.dz_f32, j.B, j.D, j.H, j.W, Wp, c - 1, c * cop, 3 * cop, ZT);
             else
-                k_to_padded<<<nbz, 256, 0, st>>>(j.dz, j.dz_pitch, j.co0, j.co_n, j.B, j.D, j.H, j.W, Wp, c - 1, Pr,
-                                                 dstc);
+                k_to_padded<<<nbz, 256, 0, st>>>(j.dz, j.dz_pitch, j.co0, j.co_n, j.B, j.D, j.H, j.W, Wp, c - 1,
+                                                 c * cop, 3 * cop, ZT);
         }
-        k_to_padded<<<nbx, 256, 0, st>>>(j.x, j.x_pitch, j.ci0, j.ci_n, j.B, j.D, j.H, j.W, Wp, 0, Pr, XT);
+        k_to_padded<<<nbx, 256, 0, st>>>(j.x, j.x_pitch, j.ci0, j.ci_n, j.B, j.D, j.H, j.W, Wp, 0, 0, N, XT);
     } else {
-        k_to_cm<<<nbz, 256, 0, st>>>(j.dz, j.dz_pitch, j.co0, j.co_n, cells, Pr, ZT);
-        k_to_cm<<<nbx, 256, 0, st>>>(j.x, j.x_pitch, j.ci0, j.ci_n, cells, Pr, XT);
+        k_to_cm<<<nbz, 256, 0, st>>>(j.dz, j.dz_pitch, j.co0, j.co_n, cells, cop, ZT);
+        k_to_cm<<<nbx, 256, 0, st>>>(j.x, j.x_pitch, j.ci0, j.ci_n, cells, N, XT);
     }
     WgradTcArgs a;
     memset(&a, 0, sizeof(a));
@@ -416,7 +420,7 @@ hyb_status wgrad_tc(const WgradJob &j, WgradScratch &ws, cudaStream_t st) {
         a.box_rows = 3 * cop;
         for (int bx = 0; bx < 9; ++bx) {
             const int dz = bx / 3 - 1, dy = bx % 3 - 1;
-            a.koff[bx] = dz * (j.H + 2) * Wp + dy * Wp;
+            a.koff[bx] = (dz * (j.H + 2) * Wp + dy * Wp) / 16;
         }
     } else {
         a.nslots = 1;
