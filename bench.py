@@ -365,7 +365,7 @@ def run_ours(args, rank, world):
     def allmax(v):
         return max_over_ranks(v, world, "cuda")
 
-    trained, train_info = (trained_model(P, stream) if kind == "hybrid" else (None, None))
+    trained, train_info = (trained_model(P, stream) if kind == "hybrid" and not args.untrained else (None, None))
     sim, model = make_sim(P, inp, stream.cuda_stream, policy="union", model=trained)
     probe = sim.diagnostics()
     flush_l2 = state_bytes(probe, cells) < 2 * L2_BYTES
@@ -482,9 +482,11 @@ def run_ours(args, rank, world):
                    "particles_mean": parts, "kinetic_fraction": kin_frac,
                    "classify_every": N_CLS if kind == "hybrid" else None,
                    "mc_passes": MC_PASSES if kind == "hybrid" else None,
-                   "policy": ("union: the trained classifier or the physics criterion" if kind == "hybrid" else None),
+                   "policy": ("union: the %s classifier or the physics criterion" % (
+                       "untrained" if args.untrained else "trained") if kind == "hybrid" else None),
                    "classifier": ("trained before the run on %d method-generated 32^3 patches, %d steps of batch "
-                                  "32" % (train_info["patches"], train_info["steps"]) if train_info else None),
+                                  "32" % (train_info["patches"], train_info["steps"]) if train_info else
+                                  ("seeded He-uniform weights, output bias -4" if kind == "hybrid" else None)),
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": ("flushed between timed steps (2 x L2 write outside the events)" if flush_l2 else
                           "resident state larger than L2 (%.0f MB); no flush" % (state_bytes(after, cells) / 1e6))},
@@ -1157,6 +1159,9 @@ def main():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-full-pic", action="store_true", help="skip the full-PIC comparison run")
+    ap.add_argument("--untrained", action="store_true",
+                    help="hybrid runs classify with seeded He-uniform weights instead of a classifier trained "
+                         "before the run (the same work per step; for profiling captures of the step)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         ap.error("--warmup must be >= 3")
