@@ -362,14 +362,15 @@ hyb_status hyb_node_state(hyb_ctx *ctx, float *out_dev);
  *   y  = conv(a5; 32 -> 10)                                      (FP32)
  * "pad" is the identity shortcut with the missing channels zero (Table 2's
  * residuals between layers of different width).  x = (s - mean_c) / std_c
- * per channel; y is the change of the state over the lead time in units of
- * each channel's spread, and the prediction is s_c + std_c y_c (a residual
- * forecast: with every weight zero it is the input state).
+ * per channel; y is the change of the state over the lead time in units
+ * dstd_c (the spread of that change, std_c when not given), and the
+ * prediction is s_c + dstd_c y_c (a residual forecast: with every weight zero
+ * it is the input state).
  * Dropout uses the classifier's Philox stream (key (seed, 0xD0), counter
  * (cell, batch, 1 << 16 | channel / 8, pass)).
  * Training loss (Table 2: Huber with delta = 0.01 and 0.1 on the energy
  * violation): L = (1/N) sum huber_delta(y - t) + energy_weight v^2, t the
- * target change (target - s) / std_c, N the number of values, and v the relative violation
+ * target change (target - s) / dstd_c, N the number of values, and v the relative violation
  * of the batch's total field energy, v = (sum_b W(pred_b) - sum_b
  * W(target_b)) / sum_b W(target_b), W = (1/2) sum over a patch of |E|^2 +
  * |B|^2 of the de-normalised channels 0..5 (a batch without field energy
@@ -384,7 +385,8 @@ typedef struct {
     double lr, beta1, beta2, eps;  /* Adam */
     double huber_delta;        /* 0.01 */
     double energy_weight;      /* 0.1 */
-    float mean[10], std[10];   /* per-channel normalisation */
+    float mean[10], std[10];   /* per-channel normalisation of the input state */
+    float dstd[10];            /* unit of the predicted change per channel (its spread); 0: std */
     void *stream;              /* cudaStream_t (NULL: own stream) */
 } hyb_surrogate_desc;
 hyb_status hyb_surrogate_create(const hyb_surrogate_desc *desc, hyb_surrogate **out);

@@ -14,17 +14,18 @@ the second):
   a_3 = bf16(relu(conv(a_2; W_2) + b_2) + pad(a_2))
   a_4 = bf16(relu(conv(a_3; W_3) + b_3))
   a_5 = bf16(relu(conv(a_4; W_4) + b_4))
-  y   = conv(a_5; W_5) + b_5,  prediction = s_c + std_c y_c
-The output is the change of the state over the lead time in units of each
-channel's spread, added to the input state (a residual forecast: with every
-weight zero the prediction is the input, persistence).
+  y   = conv(a_5; W_5) + b_5,  prediction = s_c + dstd_c y_c
+The output is the change of the state over the lead time in units dstd_c
+(the spread of that change; std_c when not given), added to the input state
+(a residual forecast: with every weight zero the prediction is the input,
+persistence).
 "pad" is the identity shortcut with the extra channels zero (the reading of
 a residual between layers of different width); conv is the 3x3x3
 cross-correlation with zero "same" padding and BF16-rounded weights; keep is
 the dropout mask of oracle.dropout_mask (layer index 1).
 
 Loss (Table 2: Huber with delta = 0.01 plus 0.1 times the energy violation):
-  L = (1/N) sum huber(y - t_hat) + lambda v^2,  t_hat = (t - s) / std_c,
+  L = (1/N) sum huber(y - t_hat) + lambda v^2,  t_hat = (t - s) / dstd_c,
   v = (sum_b W(pred_b) - sum_b W(t_b)) / sum_b W(t_b),  W = (1/2) sum over a
   patch of the squares of channels 0..5 (E and B) in physical units: the
   relative violation of the batch's total field energy.  (Relative to each
@@ -54,7 +55,7 @@ def _pad_channels(a, c):
 
 
 class OracleSurrogate:
-    def __init__(self, weights, dropout=0.1, seed=11, mean=None, std=None):
+    def __init__(self, weights, dropout=0.1, seed=11, mean=None, std=None, dstd=None):
         """weights: list of six (W [co][ci][3][3][3], b [co]) FP32 arrays."""
         self.W = [torch.from_numpy(np.asarray(w, dtype=np.float32)).to(torch.float64) for w, _ in weights]
         self.b = [torch.from_numpy(np.asarray(b, dtype=np.float32)).to(torch.float64) for _, b in weights]
@@ -62,6 +63,9 @@ class OracleSurrogate:
         self.seed = int(seed)
         self.mean = torch.tensor(np.zeros(10) if mean is None else np.asarray(mean, np.float32), dtype=torch.float32)
         self.std = torch.tensor(np.ones(10) if std is None else np.asarray(std, np.float32), dtype=torch.float32)
+        ds = self.std.numpy() if dstd is None else np.where(np.asarray(dstd, np.float32) > 0,
+                                                              np.asarray(dstd, np.float32), self.std.numpy())
+        self.dstd = torch.tensor(ds, dtype=torch.float32)
 
     def normalise(self, x):
         x = torch.as_tensor(np.asarray(x, dtype=np.float32))
@@ -104,7 +108,7 @@ class OracleSurrogate:
     def predict(self, x, pass_index=-1, exact=False):
         y = self.forward(x, pass_index, exact)
         xs = torch.as_tensor(np.asarray(x, dtype=np.float32)).to(torch.float64)
-        return xs + y * self.std.view(1, 10, 1, 1, 1).to(torch.float64)
+        return xs + y * self.dstd.view(1, 10, 1, 1, 1).to(torch.float64)
 
     def mc_statistics(self, x, passes):
         """Mean and population standard deviation of the prediction over the passes."""
@@ -119,11 +123,10 @@ def loss_and_grads(net, x, t, pass_index, delta=0.01, energy_weight=0.1, exact=F
     rounding).  Returns dict(loss, huber, energy, grads=[(gW, gb)] * 6, y)."""
     rnd = (lambda v: v) if exact else bf16
     y, acts, pres, keeps = net.forward(x, pass_index, exact=exact, record=True)
-    sd = net.std.view(1, 10, 1, 1, 1).to(torch.float64)
-    mu = net.mean.view(1, 10, 1, 1, 1).to(torch.float64)
+    sd = net.dstd.view(1, 10, 1, 1, 1).to(torch.float64)
     tt = torch.as_tensor(np.asarray(t, dtype=np.float32))
     xs = torch.as_tensor(np.asarray(x, dtype=np.float32))
-    tn = ((tt - xs) / net.std.view(1, 10, 1, 1, 1)).to(torch.float64)
+    tn = ((tt - xs) / net.dstd.view(1, 10, 1, 1, 1)).to(torch.float64)
     B = y.shape[0]
     N = y.numel()
     r = y - tn
@@ -158,11 +161,12 @@ def loss_and_grads(net, x, t, pass_index, delta=0.01, energy_weight=0.1, exact=F
     return dict(loss=float(loss), huber=float(hub.sum() / N), energy=v * v, grads=grads, y=y)
 
 
-def train_run(weights, x, t, steps, dropout, seed, delta=0.01, energy_weight=0.1, lr=1e-3, mean=None, std=None):
+def train_run(weights, x, t, steps, dropout, seed, delta=0.01, energy_weight=0.1, lr=1e-3, mean=None, std=None,
+              dstd=None):
     """`steps` steps on one batch as hyb_surrogate_train_step takes them
     (dropout masks of pass = step index, Adam on FP64 masters); returns the
     [(W, b)] after every step and the per-step losses."""
-    net = OracleSurrogate(weights, dropout=dropout, seed=seed, mean=mean, std=std)
+    net = OracleSurrogate(weights, dropout=dropout, seed=seed, mean=mean, std=std, dstd=dstd)
     mw = [torch.zeros_like(w) for w in net.W]
     vw = [torch.zeros_like(w) for w in net.W]
     mb = [torch.zeros_like(b) for b in net.b]

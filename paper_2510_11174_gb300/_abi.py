@@ -103,7 +103,7 @@ class hyb_surrogate_desc(C.Structure):
     _fields_ = [("seed", C.c_uint32), ("dropout", C.c_double), ("mc_passes", C.c_int),
                 ("lr", C.c_double), ("beta1", C.c_double), ("beta2", C.c_double), ("eps", C.c_double),
                 ("huber_delta", C.c_double), ("energy_weight", C.c_double),
-                ("mean", C.c_float * 10), ("std", C.c_float * 10), ("stream", C.c_void_p)]
+                ("mean", C.c_float * 10), ("std", C.c_float * 10), ("dstd", C.c_float * 10), ("stream", C.c_void_p)]
 
 
 class hyb_switchnet_desc(C.Structure):

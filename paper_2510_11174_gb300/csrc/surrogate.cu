@@ -124,7 +124,7 @@ __global__ void k_sur_prep(const float *__restrict__ x, int B, long long V, cons
     dst[1] = reinterpret_cast<const uint4 *>(o)[1];
 }
 
-// prediction [B][10][V] = x + std_c y (y [B][V][16]: the change in units of the channel's spread)
+// prediction [B][10][V] = x + dstd_c y (y [B][V][16]: the change in units of its spread)
 __global__ void k_sur_out(const float *__restrict__ y, const float *__restrict__ x, int B, long long V,
                           const float *__restrict__ sd, float *__restrict__ out) {
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -317,7 +317,7 @@ struct hyb_surrogate {
     float *mw[SL] = {}, *vw[SL] = {}, *mb[SL] = {}, *vb[SL] = {};
     float *gw[SL] = {}, *gb[SL] = {};                 // gradients of the last step
     __nv_bfloat16 *pk[SL] = {}, *pkT[SL] = {};        // channel-chunk packs (forward, data gradient)
-    float *mean = nullptr, *std_ = nullptr;
+    float *mean = nullptr, *std_ = nullptr, *dstd = nullptr;  // dstd: unit of the predicted change
     int *status = nullptr;
     long long cap = 0;                                // cells the activation buffers hold
     __nv_bfloat16 *a[SL] = {};                        // a[l]: input of layer l, [cells][CIP[l]]
@@ -554,10 +554,13 @@ hyb_status hyb_surrogate_create(const hyb_surrogate_desc *d, hyb_surrogate **out
         cudaMemsetAsync(m->gb[l], 0, sizeof(float) * COP[l], m->stream);
     }
     if (s_alloc(m, (void **)&m->mean, sizeof(float) * NCH) || s_alloc(m, (void **)&m->std_, sizeof(float) * NCH) ||
+        s_alloc(m, (void **)&m->dstd, sizeof(float) * NCH) ||
         s_alloc(m, (void **)&m->status, sizeof(int)) || s_alloc(m, (void **)&m->lpart, sizeof(double) * m->lblocks))
         return fail("surrogate allocation");
     cudaMemcpyAsync(m->mean, d->mean, sizeof(float) * NCH, cudaMemcpyHostToDevice, m->stream);
     cudaMemcpyAsync(m->std_, d->std, sizeof(float) * NCH, cudaMemcpyHostToDevice, m->stream);
+    for (int c = 0; c < NCH; ++c) m->d.dstd[c] = d->dstd[c] > 0.0f ? d->dstd[c] : d->std[c];
+    cudaMemcpyAsync(m->dstd, m->d.dstd, sizeof(float) * NCH, cudaMemcpyHostToDevice, m->stream);
     cudaMemsetAsync(m->status, 0, sizeof(int), m->stream);
     // He-uniform initialisation from the seed (Philox on the host):
     // w ~ U(-sqrt(6/fan_in), sqrt(6/fan_in)), b = 0
@@ -613,7 +616,7 @@ hyb_status hyb_surrogate_forward(hyb_surrogate *m, const float *x, int B, int D,
     if (s != HYB_OK) return s;
     k_sur_prep<<<nbk(cells), RB, 0, m->stream>>>(x, B, V, m->mean, m->std_, m->a[0]);
     if ((s = forward(m, B, D, H, W, pass)) != HYB_OK) return s;
-    k_sur_out<<<nbk(cells * NCH), RB, 0, m->stream>>>(m->y, x, B, V, m->std_, y);
+    k_sur_out<<<nbk(cells * NCH), RB, 0, m->stream>>>(m->y, x, B, V, m->dstd, y);
     HYB_CUDA_TRY(cudaGetLastError());
     return HYB_OK;
 }
@@ -628,7 +631,7 @@ hyb_status hyb_surrogate_mc(hyb_surrogate *m, const float *x, int B, int D, int 
     const int K = m->d.mc_passes;
     for (int k = 1; k <= K; ++k) {
         if ((s = forward(m, B, D, H, W, k - 1)) != HYB_OK) return s;
-        k_sur_mc<<<nbk(cells * NCH), RB, 0, m->stream>>>(m->y, x, B, V, m->std_, k, pm, ps);
+        k_sur_mc<<<nbk(cells * NCH), RB, 0, m->stream>>>(m->y, x, B, V, m->dstd, k, pm, ps);
     }
     k_sur_mc_final<<<nbk(cells * NCH), RB, 0, m->stream>>>(cells * NCH, K, ps);
     HYB_CUDA_TRY(cudaGetLastError());
@@ -657,9 +660,9 @@ hyb_status hyb_surrogate_train_step(hyb_surrogate *m, const float *x, const floa
     k_sur_prep<<<nbk(cells), RB, 0, st>>>(x, B, V, m->mean, m->std_, m->a[0]);
     if ((s = forward(m, B, D, H, W, pass)) != HYB_OK) return s;
     // loss: per-sample energies, then the gradient dL/dy (G[SL] and dz)
-    k_sur_energy<<<dim3(m->eblocks, B), RB, 0, st>>>(m->y, tg, x, V, m->std_, m->epart);
+    k_sur_energy<<<dim3(m->eblocks, B), RB, 0, st>>>(m->y, tg, x, V, m->dstd, m->epart);
     k_sur_esum<<<nbk(B), RB, 0, st>>>(m->epart, B, m->eblocks, m->esum);
-    k_sur_loss<<<m->lblocks, RB, 0, st>>>(m->y, tg, x, B, V, m->std_, (float)m->d.huber_delta,
+    k_sur_loss<<<m->lblocks, RB, 0, st>>>(m->y, tg, x, B, V, m->dstd, (float)m->d.huber_delta,
                                           (float)m->d.energy_weight, m->esum, m->G[SL], m->dz, m->lpart);
     // backward, last layer first
     for (int l = SL - 1; l >= 0; --l) {

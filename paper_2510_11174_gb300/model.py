@@ -118,16 +118,18 @@ class Surrogate:
     shortcuts and dropout; hyb_surrogate_* in include/hyb.h) on the GPU."""
 
     def __init__(self, dropout=0.1, mc_passes=16, seed=11, mean=None, std=None, lr=1e-3, huber_delta=0.01,
-                 energy_weight=0.1, stream=None):
+                 energy_weight=0.1, stream=None, dstd=None):
         self._lib = _abi.load()
         d = _abi.hyb_surrogate_desc()
         d.seed, d.dropout, d.mc_passes = seed, dropout, mc_passes
         d.lr, d.huber_delta, d.energy_weight = lr, huber_delta, energy_weight
         mean = [0.0] * 10 if mean is None else mean
         std = [1.0] * 10 if std is None else std
+        dstd = [0.0] * 10 if dstd is None else dstd
         for c in range(10):
             d.mean[c] = float(mean[c])
             d.std[c] = float(std[c])
+            d.dstd[c] = float(dstd[c])
         self.torch_stream, d.stream = _model_stream(stream)
         self.desc = d
         h = C.c_void_p()

@@ -12,16 +12,16 @@ from _util import rel_l2, require_gpu
 pytestmark = pytest.mark.gpu
 
 
-def _pair(seed=3, dropout=0.1, mc_passes=4, mean=None, std=None, weights=None):
+def _pair(seed=3, dropout=0.1, mc_passes=4, mean=None, std=None, weights=None, dstd=None):
     P = require_gpu()
     from oracle import surrogate as S
     from paper_2510_11174_gb300 import inputs
     from paper_2510_11174_gb300.model import Surrogate
     weights = inputs.surrogate_weights(seed) if weights is None else weights
-    m = Surrogate(dropout=dropout, mc_passes=mc_passes, seed=seed, mean=mean, std=std)
+    m = Surrogate(dropout=dropout, mc_passes=mc_passes, seed=seed, mean=mean, std=std, dstd=dstd)
     for l, (w, b) in enumerate(weights):
         m.set_layer(l, w, b)
-    return m, S.OracleSurrogate(weights, dropout=dropout, seed=seed, mean=mean, std=std), weights
+    return m, S.OracleSurrogate(weights, dropout=dropout, seed=seed, mean=mean, std=std, dstd=dstd), weights
 
 
 def _identity_weights():
@@ -60,6 +60,17 @@ def test_forward_matches_oracle(pass_index):
     ref = orc.predict(x, pass_index).numpy()
     err = rel_l2(y - x, ref - x)   # the predicted change
     assert err <= 1e-3, err        # measured 4e-4 .. 6e-4
+    m.close()
+
+
+def test_forward_with_a_change_unit_matches_oracle():
+    from paper_2510_11174_gb300 import inputs
+    x, mean, std = inputs.random_states(2, 16, seed=12)
+    dstd = (0.05 * std).astype(np.float32)
+    m, orc, _ = _pair(mean=mean, std=std, dstd=dstd)
+    y = m.forward(torch.from_numpy(x).cuda(), 2).cpu().numpy()
+    ref = orc.predict(x, 2).numpy()
+    assert rel_l2(y - x, ref - x) <= 1e-3, rel_l2(y - x, ref - x)
     m.close()
 
 

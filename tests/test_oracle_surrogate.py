@@ -73,6 +73,15 @@ def test_identity_weights_have_no_mc_spread():
     assert float(s.abs().max()) == 0.0
 
 
+def test_change_unit_scales_the_forecast_change():
+    x, mean, std = _states(seed=7)
+    dstd = (0.25 + np.arange(10)).astype(np.float32)
+    net = S.OracleSurrogate(_identity_weights(), mean=mean, std=std, dstd=dstd)
+    xh = (x - mean[None, :, None, None, None]) / std[None, :, None, None, None]
+    target = x.astype(np.float64) + dstd[None, :, None, None, None] * xh
+    np.testing.assert_allclose(net.predict(x, exact=True).numpy(), target, rtol=0, atol=1e-4)
+
+
 def test_loss_of_a_perfect_prediction_is_zero_and_huber_of_an_offset():
     x, mean, std = _states(seed=3)
     net = S.OracleSurrogate(_identity_weights(), mean=mean, std=std)
