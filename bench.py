@@ -161,17 +161,17 @@ FIELD_KERNELS = "k_b_half + k_e_yee + k_mur (split Yee step)"
 FLUID_BYTES_PER_NODE = 32
 FLUID_FIELD_BYTES_PER_NODE = 24
 # DRAM read + write per cell of one launch of the 32 -> 32 convolution, from
-# the ncu capture on the 128 x 128 x 64 ramp + slab (67.2 + 20.2 MB for
+# the ncu capture on the 128 x 128 x 64 ramp + slab (67.2 + 19.9 MB for
 # 1,048,576 cells); scaled to a full launch by the cell count
-NCU_CONV_L1_BYTES_PER_CELL = 87.4e6 / 1048576
+NCU_CONV_L1_BYTES_PER_CELL = 87.1e6 / 1048576
 # DRAM read + write per particle of one hybrid-step launch of the push, from
-# the ncu capture on the 128 x 128 x 64 ramp + slab (184.9 + 69.1 MB for its
+# the ncu capture on the 128 x 128 x 64 ramp + slab (190.3 + 69.5 MB for its
 # 4.78 M particles); scaled to a full launch by the particle count
-NCU_PUSH_BYTES_PER_PARTICLE = 261.9e6 / 4784128
+NCU_PUSH_BYTES_PER_PARTICLE = 259.7e6 / 4784128
 # warp instructions of the same capture: the push is bound by instruction
 # issue (its DRAM traffic is the algorithmic bytes), so it is also reported
 # against the SM's issue rate, 4 warp instructions per cycle and SM
-NCU_PUSH_WARP_INST_PER_PARTICLE = 1.11e8 / 4784128
+NCU_PUSH_WARP_INST_PER_PARTICLE = 1.074e8 / 4784128
 N_SM = 152
 
 
