@@ -259,6 +259,24 @@ __global__ void k_to_cm(const __nv_bfloat16 *__restrict__ src, int pitch, int c0
     }
 }
 
+// out[c] = sum over k of part[k][c] (nk rows of nc columns): one block per
+// column, thread i adds rows i, i + 256, ... in order, then a fixed-shape tree
+// (the same sum in every run)
+__global__ void __launch_bounds__(256) k_sum_cols(const float *__restrict__ part, int nk, int nc,
+                                                  float *__restrict__ out) {
+    __shared__ float sh[256];
+    const int c = blockIdx.x;
+    float s = 0.0f;
+    for (int k = threadIdx.x; k < nk; k += 256) s += part[(long long)k * nc + c];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[c] = sh[0];
+}
+
 // bias partials of an FP32 gradient of one channel: bpart[blk] = sum over the block's cells
 __global__ void k_bias_part_f32(const float *__restrict__ dz, long long cells, long long per, float *__restrict__ bpart) {
     if (threadIdx.x != 0) return;
@@ -466,7 +484,8 @@ hyb_status wgrad_tc(const WgradJob &j, WgradScratch &ws, cudaStream_t st) {
             k_bias_part_f32<<<nblk, 32, 0, st>>>(j.dz_f32, cells, per, bpart);
         else
             k_bias_part<<<nblk, 128, 0, st>>>(j.dz, j.dz_pitch, j.co0, j.co_n, cells, per, bpart);
-        k_sum_parts<<<1, 128, 0, st>>>(bpart, nblk, j.dz_f32 ? 1 : j.co_n, j.gb + j.co0);
+        const int nc = j.dz_f32 ? 1 : j.co_n;
+        k_sum_cols<<<nc, 256, 0, st>>>(bpart, nblk, nc, j.gb + j.co0);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return set_error(HYB_ECUDA, std::string("wgrad: ") + cudaGetErrorString(e));
