@@ -300,14 +300,23 @@ __global__ void k_wgrad_tc_reduce(const float *__restrict__ part, int ncta, int 
 }
 
 // bias gradient partials: bpart[blk][c] = sum over the block's cells of dZ[cell][c0 + c] (c < nc)
-__global__ void k_bias_part(const __nv_bfloat16 *__restrict__ dz, int pitch, int c0, int nc, long long cells,
-                            long long per, float *__restrict__ bpart) {
-    const int c = threadIdx.x;
-    if (c >= nc) return;
+__global__ void __launch_bounds__(256) k_bias_part(const __nv_bfloat16 *__restrict__ dz, int pitch, int c0, int nc,
+                                                   long long cells, long long per, float *__restrict__ bpart) {
+    // thread t: channel t % nc over the cells t / nc, t / nc + R, ... of the block's range (R = 256 / nc),
+    // then the R row sums of each channel in order
+    __shared__ float sh[256];
+    const int R = 256 / nc, t = threadIdx.x, c = t % nc, r = t / nc;
     const long long a0 = blockIdx.x * per, a1 = min(a0 + per, cells);
     float s = 0.0f;
-    for (long long i = a0; i < a1; ++i) s += __bfloat162float(dz[i * pitch + c0 + c]);
-    bpart[(long long)blockIdx.x * nc + c] = s;
+    if (r < R)
+        for (long long i = a0 + r; i < a1; i += R) s += __bfloat162float(dz[i * pitch + c0 + c]);
+    sh[t] = s;
+    __syncthreads();
+    if (t < nc) {
+        float b = 0.0f;
+        for (int k = 0; k < R; ++k) b += sh[k * nc + t];
+        bpart[(long long)blockIdx.x * nc + t] = b;
+    }
 }
 
 typedef CUresult (*EncodeTiledFn3)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
@@ -483,7 +492,7 @@ hyb_status wgrad_tc(const WgradJob &j, WgradScratch &ws, cudaStream_t st) {
         if (j.dz_f32)
             k_bias_part_f32<<<nblk, 32, 0, st>>>(j.dz_f32, cells, per, bpart);
         else
-            k_bias_part<<<nblk, 128, 0, st>>>(j.dz, j.dz_pitch, j.co0, j.co_n, cells, per, bpart);
+            k_bias_part<<<nblk, 256, 0, st>>>(j.dz, j.dz_pitch, j.co0, j.co_n, cells, per, bpart);
         const int nc = j.dz_f32 ? 1 : j.co_n;
         k_sum_cols<<<nc, 256, 0, st>>>(bpart, nblk, nc, j.gb + j.co0);
     }
