@@ -654,11 +654,18 @@ __global__ void k_dgrad_last(const float *__restrict__ dlogit, const float *__re
 }
 
 // dz = bf16(dA [a > 0] / (1 - p)) in place (dA from the tensor-core data gradient)
+// (n a multiple of 8: eight values per thread, 16-byte loads and stores)
 __global__ void k_mask_grad(__nv_bfloat16 *__restrict__ d, const __nv_bfloat16 *__restrict__ a, long long n,
                             float inv_keep) {
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (t >= n) return;
-    d[t] = __float2bfloat16_rn(__bfloat162float(a[t]) > 0.0f ? __bfloat162float(d[t]) * inv_keep : 0.0f);
+    if (t * 8 >= n) return;
+    uint4 dv = reinterpret_cast<const uint4 *>(d)[t], av = reinterpret_cast<const uint4 *>(a)[t];
+    __nv_bfloat16 *dh = reinterpret_cast<__nv_bfloat16 *>(&dv);
+    const __nv_bfloat16 *ah = reinterpret_cast<const __nv_bfloat16 *>(&av);
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+        dh[j] = __float2bfloat16_rn(__bfloat162float(ah[j]) > 0.0f ? __bfloat162float(dh[j]) * inv_keep : 0.0f);
+    reinterpret_cast<uint4 *>(d)[t] = dv;
 }
 
 // sum the chunk partials in chunk order: out[o] = sum_k part[k][o]
@@ -784,12 +791,12 @@ hyb_status hyb_train_step(hyb_model *m, const float *x, const float *y, int B, i
     a.status = m->status;
     a.x = t.dz3; a.wt = m->wtT[2]; a.cin = 16; a.N = 32; a.y = t.dz2;
     if ((s = launch_conv3_tc(a, st)) != HYB_OK) return s;
-    k_mask_grad<<<nbl(cells * 32), 256, 0, st>>>(t.dz2, m->a2, cells * 32, inv_keep);
+    k_mask_grad<<<nbl(cells * 4), 256, 0, st>>>(t.dz2, m->a2, cells * 32, inv_keep);
     // layer 1 (32 -> 32)
     if ((s = layer_wgrad(m, t, 1, m->a1, 32, t.dz2, nullptr, B, D, H, W)) != HYB_OK) return s;
     a.x = t.dz2; a.wt = m->wtT[1]; a.cin = 32; a.N = 32; a.y = t.dz1;
     if ((s = launch_conv3_tc(a, st)) != HYB_OK) return s;
-    k_mask_grad<<<nbl(cells * 32), 256, 0, st>>>(t.dz1, m->a1, cells * 32, inv_keep);
+    k_mask_grad<<<nbl(cells * 4), 256, 0, st>>>(t.dz1, m->a1, cells * 32, inv_keep);
     // layer 0 (6 -> 32): weight gradient only
     if ((s = layer_wgrad(m, t, 0, m->x0, 16, t.dz1, nullptr, B, D, H, W)) != HYB_OK) return s;
     // Adam on the FP32 master weights, then the BF16 copies
