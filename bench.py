@@ -437,7 +437,9 @@ def run_ours(args, rank, world):
         r["frac"] = r["achieved"] / r["peak"]
         r["peak_kind"] = "measured" if peaks else "fallback"
         r["traffic"] = None
-    if "push" in roofs:
+    if "push" in roofs and kind == "hybrid":
+        # DRAM bytes and warp instructions of a hybrid-step capture, scaled by
+        # the particles (other workloads push ionizing ions and QED leptons: null)
         roofs["push"]["traffic"] = NCU_PUSH_BYTES_PER_PARTICLE * parts
         roofs["push"]["traffic_note"] = "ncu dram bytes of a 128x128x64 hybrid-step launch scaled by particles"
         mhz = clk.get("sm_mhz") or 2070.0
