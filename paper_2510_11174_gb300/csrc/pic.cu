@@ -794,38 +794,75 @@ __global__ void k_rebin(SpDev sp, int *__restrict__ status) {
 
 // Close the holes no migrant filled: move live particles from the end of the
 // tile into them and shrink the count.  One thread per tile.
-__global__ void k_compact(GridDev g, SpDev sp) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= g.ntiles) return;
+__global__ void __launch_bounds__(32) k_compact(GridDev g, SpDev sp) {
+    // one warp per tile: the holes below the new count (in hole-list order)
+    // are filled with the live particles at or above it (in slot order), the
+    // same pairing as a serial walk of both lists; FIFO queues of up to 64
+    // entries in shared memory, refilled 32 candidates at a time
+    __shared__ int hq[64], sq[64];
+    const int t = blockIdx.x, lane = threadIdx.x;
+    (void)g;
     const int hc = sp.hole_count[t], hu = sp.hole_used[t];
-    int n = min(sp.count[t], sp.cap);
+    const int n = min(sp.count[t], sp.cap);
     if (hu >= hc) {
-        sp.count[t] = n;  // an overflowing append left count above the capacity
-        if (2 * n > sp.cap) atomicOr(sp.fill_flags, 1 << sp.sp_index);
+        if (lane == 0) {
+            sp.count[t] = n;  // an overflowing append left count above the capacity
+            if (2 * n > sp.cap) atomicOr(sp.fill_flags, 1 << sp.sp_index);
+        }
         return;
     }
     const long long base = (long long)t * sp.cap;
-    const int nh = hc - hu;
-    const int new_n = n - nh;
-    int src = new_n;  // scans [new_n, n) for live particles
-    for (int h = hu; h < hc; ++h) {
-        const int dst = sp.holes[base + h];
-        if (dst >= new_n) continue;  // the hole disappears with the shrink
-        while (src < n && sp.x[base + src] < 0.0f) ++src;
-        if (src >= n) break;
-        const long long a = base + dst, b = base + src;
-        sp.x[a] = sp.x[b]; sp.y[a] = sp.y[b]; sp.z[a] = sp.z[b];
-        sp.ux[a] = sp.ux[b]; sp.uy[a] = sp.uy[b]; sp.uz[a] = sp.uz[b];
-        sp.w[a] = sp.w[b];
-        if (sp.zq) sp.zq[a] = sp.zq[b];
-        sp.id[a] = sp.id[b];
-        if (sp.tau) sp.tau[a] = sp.tau[b];
-        ++src;
+    const int new_n = n - (hc - hu);
+    const unsigned below = (1u << lane) - 1u;
+    int h = hu, src = new_n, hn = 0, sn = 0;
+    for (;;) {
+        while (hn < 32 && h < hc) {
+            const int hh = h + lane;
+            const int dst = hh < hc ? sp.holes[base + hh] : new_n;
+            const bool ok = dst < new_n;  // holes at or above new_n vanish with the shrink
+            const unsigned m = __ballot_sync(0xffffffffu, ok);
+            if (ok) hq[hn + __popc(m & below)] = dst;
+            hn += __popc(m);
+            h += 32;
+        }
+        while (sn < 32 && src < n) {
+            const int s0 = src + lane;
+            const bool ok = s0 < n && !(sp.x[base + s0] < 0.0f);  // live slot (vacated slots hold x < 0)
+            const unsigned m = __ballot_sync(0xffffffffu, ok);
+            if (ok) sq[sn + __popc(m & below)] = s0;
+            sn += __popc(m);
+            src += 32;
+        }
+        __syncwarp();
+        const int k = min(hn, sn);
+        if (k == 0) break;
+        if (lane < k) {
+            const long long a = base + hq[lane], b = base + sq[lane];
+            sp.x[a] = sp.x[b]; sp.y[a] = sp.y[b]; sp.z[a] = sp.z[b];
+            sp.ux[a] = sp.ux[b]; sp.uy[a] = sp.uy[b]; sp.uz[a] = sp.uz[b];
+            sp.w[a] = sp.w[b];
+            if (sp.zq) sp.zq[a] = sp.zq[b];
+            sp.id[a] = sp.id[b];
+            if (sp.tau) sp.tau[a] = sp.tau[b];
+        }
+        // drop the k used entries of both queues
+        const int h0 = lane + k < hn ? hq[lane + k] : 0, h1 = lane + 32 + k < hn ? hq[lane + 32 + k] : 0;
+        const int q0 = lane + k < sn ? sq[lane + k] : 0, q1 = lane + 32 + k < sn ? sq[lane + 32 + k] : 0;
+        __syncwarp();
+        if (lane + k < hn) hq[lane] = h0;
+        if (lane + 32 + k < hn) hq[lane + 32] = h1;
+        if (lane + k < sn) sq[lane] = q0;
+        if (lane + 32 + k < sn) sq[lane + 32] = q1;
+        hn -= k;
+        sn -= k;
+        __syncwarp();
     }
-    sp.count[t] = new_n;
-    sp.hole_count[t] = 0;
-    sp.hole_used[t] = 0;
-    if (2 * new_n > sp.cap) atomicOr(sp.fill_flags, 1 << sp.sp_index);
+    if (lane == 0) {
+        sp.count[t] = new_n;
+        sp.hole_count[t] = 0;
+        sp.hole_used[t] = 0;
+        if (2 * new_n > sp.cap) atomicOr(sp.fill_flags, 1 << sp.sp_index);
+    }
 }
 
 // copy every tile's live slots into a species layout with a larger capacity
@@ -932,7 +969,7 @@ void launch_regrid(const GridDev &g, const SpDev &from, const SpDev &to, cudaStr
 }
 
 void launch_compact(const GridDev &g, const SpDev &s, cudaStream_t st) {
-    k_compact<<<blocks_for(g.ntiles, 128), 128, 0, st>>>(g, s);
+    k_compact<<<g.ntiles, 32, 0, st>>>(g, s);
 }
 
 void launch_count_tiles(const GridDev &g, long long n, const float *x, const float *y, const float *z,
