@@ -793,7 +793,7 @@ __global__ void k_rebin(SpDev sp, int *__restrict__ status) {
 }
 
 // Close the holes no migrant filled: move live particles from the end of the
-// tile into them and shrink the count.  One thread per tile.
+// tile into them and shrink the count.
 __global__ void __launch_bounds__(32) k_compact(GridDev g, SpDev sp) {
     // one warp per tile: the holes below the new count (in hole-list order)
     // are filled with the live particles at or above it (in slot order), the
