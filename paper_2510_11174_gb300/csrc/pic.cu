@@ -834,7 +834,7 @@ __global__ void __launch_bounds__(32) k_compact(GridDev g, SpDev sp) {
             src += 32;
         }
         __syncwarp();
-        const int k = min(hn, sn);
+        const int k = min(32, min(hn, sn));  // one pair per lane
         if (k == 0) break;
         if (lane < k) {
             const long long a = base + hq[lane], b = base + sq[lane];
