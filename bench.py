@@ -38,6 +38,9 @@ PUSH_BYTES_PER_CELL = 36
 
 
 N_CLS = 10          # classification interval of the hybrid step [steps]
+# the classifier runs only within REACH + dilate nodes (in x) of matter: exact for a
+# classification every N_CLS steps (fluid moves at most one node per step, particles less)
+REACH = N_CLS + 1
 MC_PASSES = 16      # MC-dropout passes per classification
 
 
@@ -154,7 +157,6 @@ CLS_FLOP_PER_CELL_PASS = 94176
 # split implementation (B half, E, B half) moves 120 B: read E,B (24) + write B (12);
 # read E,B,J (36) + write E (12); B half again
 FDTD_BYTES_PER_CELL = 60
-FDTD_SPLIT_BYTES_PER_CELL = 120
 FIELD_KERNELS = "k_b_half + k_e_yee + k_mur (split Yee step)"
 # cold fluid: read n, n u (16 B) + write (16 B) per node and fluid, + the E, B read (24 B) per
 # node that the fluids share
@@ -244,7 +246,8 @@ def make_sim(P, inp, stream, policy="union", model=None):
     if "E" in inp:
         sim.set_fields(inp["E"], inp["B"])
     if inp.get("fluids"):
-        sim.set_regime(dilate=2, ppc=inp["ppc"], to_species=list(range(len(inp["fluids"]))), policy=policy)
+        sim.set_regime(dilate=2, ppc=inp["ppc"], to_species=list(range(len(inp["fluids"]))), policy=policy,
+                       reach=REACH)
         if policy != "all_kinetic" and model is None:
             model = make_model(P, stream)
         sim.classify(model if policy != "all_kinetic" else None)
@@ -332,7 +335,9 @@ def profile_phases(sim, model, step0):
             sim.classify(model)
             pt = sim.phase_times()
             cls = {"classify": pt["classify"], "regime": pt["regime"], "conv_l1": pt.get("conv_l1", 0.0),
-                   "conv_l2": pt.get("conv_l2", 0.0)}
+                   "conv_l2": pt.get("conv_l2", 0.0),
+                   # the nodes the classifier evaluated (the x-range near matter)
+                   "classified_cells": sim.diagnostics()["classified_cells"]}
     sim.set_profiling(False)
     step_phases = ["push", "j_reduce", "source", "rebin", "field", "fluid"]
     mean = {k: statistics.mean(p.get(k, 0.0) for p in per) for k in step_phases}
@@ -415,11 +420,13 @@ def run_ours(args, rank, world):
                           bytes_note="60 B per cell update (read E, B, J; write E, B)")
     if nfl and phases["fluid"] > 0:
         b = (FLUID_BYTES_PER_NODE * nfl + FLUID_FIELD_BYTES_PER_NODE) * cells
-        roofs["fluid"] = dict(kernel="k_fluid_*", bound="hbm", achieved=b / (phases["fluid"] * 1e-3) / 1e9,
+        roofs["fluid"] = dict(kernel="k_fluid_lorentz + k_fluid_update", bound="hbm", achieved=b / (phases["fluid"] * 1e-3) / 1e9,
                               peak=peak_hbm, unit="GB/s", algorithmic_bytes_per_launch=b,
                               mean_launch_ms=phases["fluid"], share=phases["fluid"] / ms_per_step)
     if cls:
-        f = CLS_FLOP_PER_CELL_PASS * cells * MC_PASSES
+        # FLOPs of the nodes the classification evaluated (every node without a reach)
+        ccells = cls.get("classified_cells") or cells
+        f = CLS_FLOP_PER_CELL_PASS * ccells * MC_PASSES
         pk = peaks.get("bf16_tflops_sustained", 1700.0)
         roofs["classify"] = dict(kernel="hyb_classify: all kernels of one classification", bound="tensor",
                                  achieved=f / (cls["classify"] * 1e-3) / 1e12, peak=pk, unit="TFLOP/s",
@@ -428,7 +435,7 @@ def run_ours(args, rank, world):
         for key, name, ci, co in (("conv_l1", "k_conv3_tc<4, 32> (classifier layer 32 -> 32)", 32, 32),
                                   ("conv_l2", "k_conv3_tc<4, 16> (classifier layer 32 -> 16)", 32, 16)):
             if cls.get(key, 0.0) > 0:
-                f1 = 2 * 27 * ci * co * cells           # one launch = one MC pass over every cell
+                f1 = 2 * 27 * ci * co * ccells          # one launch = one MC pass over the classified nodes
                 per = cls[key] / MC_PASSES
                 roofs[key] = dict(kernel=name, bound="tensor", achieved=f1 / (per * 1e-3) / 1e12, peak=pk,
                                   unit="TFLOP/s", algorithmic_flop_per_launch=f1, mean_launch_ms=per,
@@ -475,6 +482,9 @@ def run_ours(args, rank, world):
                 "hybrid_ms_per_step_without_classification": plain,
                 "break_even_classify_every": ((cls["classify"] + cls["regime"]) / (full_step - plain)
                                               if cls and full_step > plain else None)}
+        if learned is not None:
+            # the trained classifier alone against the same full-PIC run
+            full["learned_policy_speedup"] = full_step / learned["ms_per_step"]
 
     e2e = run_e2e(P, inp, args.steps, stream, trained) if rank == 0 else None
     # the same with the diagnostics read back once per classification interval
@@ -489,6 +499,7 @@ def run_ours(args, rank, world):
         "config": {"workload": args.workload, "kind": kind, "grid": [g["nx"], g["ny"], g["nz"]],
                    "particles_mean": parts, "kinetic_fraction": kin_frac,
                    "classify_every": N_CLS if kind == "hybrid" else None,
+                   "classifier_reach": REACH if kind == "hybrid" else None,
                    "mc_passes": MC_PASSES if kind == "hybrid" else None,
                    "policy": ("union: the %s classifier or the physics criterion" % (
                        "untrained" if args.untrained else "trained") if kind == "hybrid" else None),
@@ -972,7 +983,8 @@ def oracle_sample(workload, with_classifier=True):
     net = None
     if inp.get("fluids") and not with_classifier:
         # the physics criterion alone decides the kinetic cells; no reclassification
-        o.set_regime(dilate=2, ppc=inp["ppc"], to_species=list(range(len(inp["fluids"]))), policy="default")
+        o.set_regime(dilate=2, ppc=inp["ppc"], to_species=list(range(len(inp["fluids"]))), policy="default",
+                     reach=REACH)
         o.classify(None)
     elif inp.get("fluids"):
         from oracle.classifier import OracleCNN, LAYERS
@@ -983,7 +995,8 @@ def oracle_sample(workload, with_classifier=True):
             ws.append((rng.uniform(-lim, lim, (co, ci, 3, 3, 3)).astype(np.float32), np.zeros(co, np.float32)))
         ws[-1] = (ws[-1][0], np.full(1, -4.0, np.float32))
         net = OracleCNN(ws, dropout=0.2, seed=11)
-        o.set_regime(dilate=2, ppc=inp["ppc"], to_species=list(range(len(inp["fluids"]))), policy="union")
+        o.set_regime(dilate=2, ppc=inp["ppc"], to_species=list(range(len(inp["fluids"]))), policy="union",
+                     reach=REACH)
         o.classify(net, passes=MC_PASSES)
     if inp.get("preroll"):
         o.step(inp["preroll"])

@@ -193,6 +193,9 @@ typedef struct {
     long long n_clamped;                   /* fluid nodes clamped from negative density so far */
     long long launches_classify;           /* kernels the most recent hyb_classify launched */
     long long tile_capacity[HYB_MAX_SPECIES];  /* current slots per tile of each species */
+    long long classified_cells;            /* nodes whose statistics the most recent classification with a
+                                              model computed (all of them unless hyb_regime_desc.reach
+                                              restricted it) */
 } hyb_diag;
 
 /* Create a context: validates the descriptor, allocates fields on the
@@ -239,6 +242,16 @@ typedef struct {
                                              above its square root), the same in every run, so that a
                                              uniform fluid becomes particles without shot noise;
                                              0: Philox-uniform positions */
+    int reach;                            /* 0: the classifier runs on every node.  r > 0: it runs only on
+                                             the nodes whose x lies within r + dilate nodes of an x-plane
+                                             holding matter (a fluid above its n_floor, or a tile with
+                                             particles); p_mean = p_std = 0 on the other nodes.  Fluid
+                                             moves at most one node per step and particles less, so with
+                                             r at least the number of steps to the next classification the
+                                             decision differs from the whole-grid one only where no matter
+                                             can be before then, and the run (conversions, fields,
+                                             particles) is the same.  hyb_classify then synchronises the
+                                             context stream once to read the matter's x-extent. */
 } hyb_regime_desc;
 /* Which decision hyb_classify takes.  DEFAULT: the classifier when a model is
  * given, else the physics criterion.  UNION: a node is kinetic when the

@@ -131,10 +131,23 @@ class OracleSim:
         return len(self.fluids) - 1
 
     def set_regime(self, a_thr=1.0, n_thr=1.0, c_thr=0.1, chi_thr=1e-3, dilate=2, k_sigma=1.0, ppc=8,
-                   to_species=None, policy="default", quiet=False):
+                   to_species=None, policy="default", quiet=False, reach=0):
         self.regime = dict(a_thr=a_thr, n_thr=n_thr, c_thr=c_thr, chi_thr=chi_thr, dilate=dilate,
                            k_sigma=k_sigma, ppc=ppc, to_species=list(to_species or []), policy=policy,
-                           quiet=bool(quiet))
+                           quiet=bool(quiet), reach=int(reach))
+
+    def matter_planes(self):
+        """x-indices of the planes that hold matter: a fluid above its floor at
+        a node of the plane, or a particle in a cell of the plane (floor(x),
+        at most nx - 1)."""
+        nx = self.g.shape[2]
+        hold = np.zeros(nx, dtype=bool)
+        for fl in self.fluids:
+            hold |= (fl.n > fl.n_floor).any(axis=(0, 1))
+        for sp in self.species:
+            if sp.n:
+                hold[np.clip(np.floor(sp.x).astype(np.int64), 0, nx - 1)] = True
+        return np.nonzero(hold)[0]
 
     def classify(self, net=None, passes=16, mask=None):
         """Regime decision and conversions (Methodology: fluid where the flow
@@ -174,6 +187,16 @@ class OracleSim:
             else:
                 import torch
                 pm, ps = torch.sigmoid(net.forward(x, pass_index=-1))[0].numpy(), np.zeros(g.shape)
+            if r.get("reach", 0) > 0:
+                # the classifier's statistics only near matter: within reach + dilate
+                # planes (in x) of a plane holding matter; zero elsewhere
+                planes, nx = self.matter_planes(), g.shape[2]
+                keep = np.zeros(nx, dtype=bool)
+                if planes.size:
+                    R = r["reach"] + r["dilate"]
+                    keep[max(0, planes.min() - R):min(nx, planes.max() + 1 + R)] = True
+                pm = np.where(keep[None, None, :], pm, 0.0)
+                ps = np.where(keep[None, None, :], ps, 0.0)
             mask |= dilate(g, pm + r["k_sigma"] * ps >= 0.5, r["dilate"])
         self._convert(mask)
         return pm, ps

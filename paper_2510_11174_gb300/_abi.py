@@ -60,7 +60,7 @@ class hyb_diag(C.Structure):
                 ("n_emit", C.c_longlong), ("n_pair", C.c_longlong),
                 ("n_fluids", C.c_int), ("w_fluid", C.c_double * 4), ("n_fluid", C.c_double * 4),
                 ("n_clamped", C.c_longlong), ("launches_classify", C.c_longlong),
-                ("tile_capacity", C.c_longlong * HYB_MAX_SPECIES)]
+                ("tile_capacity", C.c_longlong * HYB_MAX_SPECIES), ("classified_cells", C.c_longlong)]
 
 
 HYB_NPHASE = 10
@@ -82,7 +82,7 @@ class hyb_phase_times_t(C.Structure):
 class hyb_regime_desc(C.Structure):
     _fields_ = [("a_thr", C.c_double), ("n_thr", C.c_double), ("c_thr", C.c_double), ("chi_thr", C.c_double),
                 ("dilate", C.c_int), ("k_sigma", C.c_double), ("ppc", C.c_int),
-                ("to_species", C.c_int * 4), ("policy", C.c_int), ("quiet", C.c_int)]
+                ("to_species", C.c_int * 4), ("policy", C.c_int), ("quiet", C.c_int), ("reach", C.c_int)]
 
 
 HYB_REGIME_DEFAULT, HYB_REGIME_UNION, HYB_REGIME_ALL_KINETIC = 0, 1, 2

@@ -336,6 +336,7 @@ void hyb_destroy(hyb_ctx *c) {
     for (void *p : c->owned) cudaFree(p);
     if (c->fill_host) cudaFreeHost(c->fill_host);
     if (c->diag_host) cudaFreeHost(c->diag_host);
+    if (c->xflag_host) cudaFreeHost(c->xflag_host);
     if (c->fill_ev) cudaEventDestroy(c->fill_ev);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
@@ -647,6 +648,7 @@ hyb_status hyb_set_regime(hyb_ctx *c, const hyb_regime_desc *d) {
     if (d->policy < HYB_REGIME_DEFAULT || d->policy > HYB_REGIME_ALL_KINETIC)
         return set_error(HYB_EINVAL, "policy must be one of HYB_REGIME_*");
     if (d->quiet != 0 && d->quiet != 1) return set_error(HYB_EINVAL, "quiet must be 0 or 1");
+    if (d->reach < 0) return set_error(HYB_EINVAL, "reach must be >= 0");
     for (int f = 0; f < HYB_MAX_FLUIDS; ++f)
         if (d->to_species[f] >= (int)c->sp.size() ||
             (d->to_species[f] >= 0 && c->sp[d->to_species[f]].dev.kind != HYB_KIND_MASSIVE))
@@ -1069,6 +1071,7 @@ hyb_status hyb_diagnostics(hyb_ctx *c, hyb_diag *out) {
     out->status = status_to_code(h);
     out->launches_per_step = c->launches_per_step;
     out->launches_classify = c->launches_classify;
+    out->classified_cells = c->classified_cells;
     for (size_t i = 0; i < c->sp.size() && i < HYB_MAX_SPECIES; ++i) out->tile_capacity[i] = c->sp[i].dev.cap;
     out->n_fluids = nfl;
     for (int f = 0; f < nfl; ++f) {

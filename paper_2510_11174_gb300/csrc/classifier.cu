@@ -37,6 +37,7 @@ struct hyb_model {
     uint32_t w4pk[256] = {};             // w4r as BF16 B operand [ci / 8][tap (32)][ci % 8] (kernel parameter)
     float b4h = 0.0f;
     float *mean = nullptr, *std_ = nullptr;
+    int xr_lo = 0, xr_hi = 0;            // a classification's x-range of final outputs (xr_hi <= xr_lo: all)
     // activation buffers (capacity in cells)
     long long cap = 0;
     __nv_bfloat16 *x0 = nullptr, *a1 = nullptr, *a2 = nullptr, *a3 = nullptr;
@@ -179,10 +180,14 @@ __global__ void k_node_fields_f32(GridDev g, const float *__restrict__ E, const 
 // one SIMD compare per word gives the mask.
 __global__ void k_dropout_select(const __nv_bfloat16 *__restrict__ h0s, long long cells, long long V, uint32_t seed,
                                  uint32_t pass0, int G, uint32_t thr, __nv_bfloat16 *__restrict__ a1,
-                                 long long pitch) {
+                                 long long pitch, int W, int x_lo, int x_hi) {
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (t >= cells) return;
     const uint32_t b = (uint32_t)(t / V), lin = (uint32_t)(t % V);
+    if (x_hi > x_lo) {
+        const int x = (int)(lin % (uint32_t)W);
+        if (x < x_lo || x >= x_hi) return;  // outside the classified x-range
+    }
     const uint4 *src = reinterpret_cast<const uint4 *>(h0s + t * 32);
     uint4 h[4];
 #pragma unroll
@@ -259,6 +264,15 @@ static hyb_status model_reserve(hyb_model *m, long long cells) {
         m_alloc(m, (void **)&m->logit, sizeof(float) * cells) || m_alloc(m, (void **)&m->pm, sizeof(float) * cells) ||
         m_alloc(m, (void **)&m->ps, sizeof(float) * cells))
         return set_error(HYB_ENOMEM, "classifier activation buffers");
+    // defined contents: a classification restricted to an x-range reads, but does
+    // not use, activations just outside it
+    cudaMemsetAsync(m->x0, 0, sizeof(__nv_bfloat16) * 16 * cells, m->stream);
+    cudaMemsetAsync(m->a1, 0, sizeof(__nv_bfloat16) * 32 * cells * MC_GROUP, m->stream);
+    cudaMemsetAsync(m->a2, 0, sizeof(__nv_bfloat16) * 32 * cells, m->stream);
+    cudaMemsetAsync(m->a3, 0, sizeof(__nv_bfloat16) * 16 * cells, m->stream);
+    cudaMemsetAsync(m->h0s, 0, sizeof(__nv_bfloat16) * 32 * cells, m->stream);
+    const cudaError_t e = cudaStreamSynchronize(m->stream);
+    if (e != cudaSuccess) return set_error(HYB_ECUDA, std::string("activation buffers: ") + cudaGetErrorString(e));
     m->cap = cells;
     return HYB_OK;
 }
@@ -288,11 +302,17 @@ static ConvArgs conv_args(hyb_model *m, int l, int B, int D, int H, int W, int p
     a.pass = (uint32_t)(pass >= 0 ? pass : 0);
     a.layer = (uint32_t)l;
     a.status = m->status;
+    if (m->xr_hi > m->xr_lo) {
+        // layer l feeds 3 - l more 3x3x3 layers: its outputs are needed that far beyond the range
+        a.x_lo = std::max(0, m->xr_lo - (3 - l));
+        a.x_hi = std::min(W, m->xr_hi + (3 - l));
+    }
     return a;
 }
 
 static hyb_status launch_last(hyb_model *m, int B, int D, int H, int W, int mc_k, cudaStream_t st) {
     LastArgs a;
+    memset(&a, 0, sizeof(a));
     a.x = m->a3;
     memcpy(a.w, m->w4pk, sizeof(a.w));
     a.bias = m->b4h;
@@ -305,6 +325,8 @@ static hyb_status launch_last(hyb_model *m, int B, int D, int H, int W, int mc_k
     a.pm = m->pm;
     a.m2 = m->ps;
     a.status = m->status;
+    a.x_lo = m->xr_lo;
+    a.x_hi = m->xr_hi;
     return launch_conv_last_tc(a, st);
 }
 
@@ -335,6 +357,28 @@ hyb_status classifier_forward(hyb_ctx *c, const hyb_model *mc, float *p_mean_dev
     hyb_status s = model_reserve(m, g.N);
     if (s != HYB_OK) return s;
     // the model runs on the context's stream for the classification
+    // with a reach, only the x-range within reach + dilate nodes of matter is
+    // classified; p_mean = p_std = 0 elsewhere (see hyb_regime_desc.reach)
+    m->xr_lo = m->xr_hi = 0;
+    if (c->regime.reach > 0) {
+        int xa = 0, xb = 0;
+        s = matter_x_range(c, c->regime.reach + c->regime.dilate, &xa, &xb);
+        if (s != HYB_OK) return s;
+        HYB_CUDA_TRY(cudaMemsetAsync(m->pm, 0, sizeof(float) * g.N, c->stream));
+        HYB_CUDA_TRY(cudaMemsetAsync(m->ps, 0, sizeof(float) * g.N, c->stream));
+        if (xb <= xa) {
+            // no matter anywhere: nothing to classify
+            c->classified_cells = 0;
+            if (p_mean_dev) HYB_CUDA_TRY(cudaMemcpyAsync(p_mean_dev, m->pm, sizeof(float) * g.N, cudaMemcpyDeviceToDevice, c->stream));
+            if (p_std_dev) HYB_CUDA_TRY(cudaMemcpyAsync(p_std_dev, m->ps, sizeof(float) * g.N, cudaMemcpyDeviceToDevice, c->stream));
+            return HYB_OK;
+        }
+        if (xa > 0 || xb < W) {
+            m->xr_lo = xa;
+            m->xr_hi = xb;
+        }
+    }
+    c->classified_cells = m->xr_hi > m->xr_lo ? (long long)(m->xr_hi - m->xr_lo) * H * D : g.N;
     cudaStream_t saved = m->stream;
     m->stream = c->stream;
     k_prep_fields<<<node_grid(g), node_block(g), 0, c->stream>>>(g, c->E, c->B, m->mean, m->std_, m->x0);
@@ -369,8 +413,10 @@ hyb_status classifier_forward(hyb_ctx *c, const hyb_model *mc, float *p_mean_dev
             if (slot == 0) {
                 // the layer-0 dropout of the next MC_GROUP passes, one read of h0s
                 const int G = std::min(MC_GROUP, K - (k - 1));
+                const int dlo = m->xr_hi > m->xr_lo ? std::max(0, m->xr_lo - 3) : 0;
+                const int dhi = m->xr_hi > m->xr_lo ? std::min(W, m->xr_hi + 3) : 0;
                 k_dropout_select<<<nb(g.N), 256, 0, c->stream>>>(m->h0s, g.N, g.N, m->d.seed, (uint32_t)(k - 1), G,
-                                                                 thr, m->a1, g.N * 32);
+                                                                 thr, m->a1, g.N * 32, W, dlo, dhi);
                 ++launches;
             }
             for (int l = 1; l < 3 && s == HYB_OK; ++l) {
@@ -397,6 +443,7 @@ hyb_status classifier_forward(hyb_ctx *c, const hyb_model *mc, float *p_mean_dev
         if (p_std_dev) cudaMemcpyAsync(p_std_dev, m->ps, sizeof(float) * g.N, cudaMemcpyDeviceToDevice, c->stream);
     }
     m->stream = saved;
+    m->xr_lo = m->xr_hi = 0;
     return s;
 }
 

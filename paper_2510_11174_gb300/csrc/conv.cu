@@ -71,6 +71,21 @@ __host__ __device__ inline bool dropout_keep(uint32_t seed, uint32_t pass, uint3
     return f >= thr;
 }
 
+// the tile columns (x) a launch covers: all, or those whose 14 outputs per
+// row meet the requested x-range
+__host__ __device__ inline void conv_tiles_x(int W, int x_lo, int x_hi, int &tx0, int &ntx) {
+    const int all = (W + TXO - 1) / TXO;
+    if (x_hi > x_lo) {
+        tx0 = x_lo / TXO;
+        const int tx1 = (x_hi + TXO - 1) / TXO;
+        ntx = (tx1 < all ? tx1 : all) - tx0;
+        if (ntx < 0) ntx = 0;
+    } else {
+        tx0 = 0;
+        ntx = all;
+    }
+}
+
 // position of a persistent CTA's tile in (x tile, y tile, z, batch) digits,
 // stepped by the grid size with carries instead of divisions
 struct TileCursor {
@@ -174,7 +189,9 @@ __global__ void __launch_bounds__(ConvCfg<KC, N>::NTHREADS, 1)
     __syncthreads();
     fence_after_sync();
     const uint32_t taddr = taddr_s;
-    const int tiles_x = (a.W + TXO - 1) / TXO, tiles_y = a.H / TY;
+    int tx0, tiles_x;
+    conv_tiles_x(a.W, a.x_lo, a.x_hi, tx0, tiles_x);
+    const int tiles_y = a.H / TY;
     const long long ntiles = (long long)a.B * a.D * tiles_y * tiles_x;
     const uint32_t ring_s = smem_u32(ring), w_s = smem_u32(wsm);
 
@@ -192,7 +209,7 @@ __global__ void __launch_bounds__(ConvCfg<KC, N>::NTHREADS, 1)
                     *(volatile int *)&abort_s = 1;
                     break;
                 }
-                const int tx = cur.tx, ty = cur.ty, z0 = cur.z, b = cur.b;
+                const int tx = cur.tx + tx0, ty = cur.ty, z0 = cur.z, b = cur.b;
                 const uint32_t fb = smem_u32(&full_b[s]);
                 mbar_arrive_expect_tx(fb, (KC / 2) * CHB);
                 const uint32_t dst = ring_s + (uint32_t)(s * Cfg::STAGE);
@@ -277,7 +294,7 @@ __global__ void __launch_bounds__(ConvCfg<KC, N>::NTHREADS, 1)
         for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it, cur.next()) {
             // first what does not need the accumulator (it overlaps the MMAs):
             // the cell, its validity and its dropout bits
-            const int tx = cur.tx, ty = cur.ty, z0 = cur.z, b = cur.b;
+            const int tx = cur.tx + tx0, ty = cur.ty, z0 = cur.z, b = cur.b;
             const int cx = tx * TXO + bx - 1, cy = ty * TY + (m >> 4);
             // the halo cells of the block row, and cells past the volume, write nothing
             const bool valid = bx != 0 && bx != TX - 1 && cx < a.W;
@@ -426,7 +443,10 @@ static hyb_status launch_cfg(const ConvArgs &a, cudaStream_t st) {
         per_sm = per_sm_dev[dev];
     }
     cudaError_t e;
-    const long long ntiles = (long long)a.B * a.D * (a.H / TY) * ((a.W + TXO - 1) / TXO);
+    int tx0, ntx;
+    conv_tiles_x(a.W, a.x_lo, a.x_hi, tx0, ntx);
+    const long long ntiles = (long long)a.B * a.D * (a.H / TY) * ntx;
+    if (ntiles == 0) return HYB_OK;
     const long long grid = std::min<long long>(ntiles, (long long)nsm * std::max(per_sm, 1));
     k_conv3_tc<KC, N><<<(unsigned)grid, Cfg::NTHREADS, Cfg::SMEM, st>>>(tm, a);
     e = cudaGetLastError();
@@ -491,13 +511,24 @@ static constexpr int LSTAGE = LTX * LTY * 32;      // bytes of one plane block (
 static constexpr int LSMEM = LSTAGES * LSTAGE + 2 * 9 * 128 * 4 + 1024 + 1024;  // ring, 2 x Q, weights, slack
 
 struct LastTiles {
-    int tx_n, ty_n, zc_n;
+    int tx0, tx_n, ty_n, zc_n;
     long long units;
 };
 
-__host__ __device__ inline LastTiles last_tiles(int B, int D, int H, int W) {
+// work units of the last layer: all block columns, or those whose outputs
+// meet x_lo <= x < x_hi when x_hi > x_lo
+__host__ __device__ inline LastTiles last_tiles(int B, int D, int H, int W, int x_lo, int x_hi) {
     LastTiles t;
-    t.tx_n = (W + LOX - 1) / LOX;
+    const int all = (W + LOX - 1) / LOX;
+    if (x_hi > x_lo) {
+        t.tx0 = x_lo / LOX;
+        const int tx1 = (x_hi + LOX - 1) / LOX;
+        t.tx_n = (tx1 < all ? tx1 : all) - t.tx0;
+        if (t.tx_n < 0) t.tx_n = 0;
+    } else {
+        t.tx0 = 0;
+        t.tx_n = all;
+    }
     t.ty_n = (H + LOY - 1) / LOY;
     t.zc_n = (D + LZC - 1) / LZC;
     t.units = (long long)B * t.zc_n * t.ty_n * t.tx_n;
@@ -507,7 +538,7 @@ __host__ __device__ inline LastTiles last_tiles(int B, int D, int H, int W) {
 // unit u -> block position and z range; planes z = zlo - 1 .. zhi
 __device__ inline void last_unit(long long u, const LastTiles &t, int D, int &tx, int &ty, int &zlo, int &zhi,
                                  int &b) {
-    tx = (int)(u % t.tx_n);
+    tx = (int)(u % t.tx_n) + t.tx0;
     u /= t.tx_n;
     ty = (int)(u % t.ty_n);
     u /= t.ty_n;
@@ -553,7 +584,7 @@ __global__ void __launch_bounds__(192, LCTAS) k_conv_last_tc(const __grid_consta
     __syncthreads();
     fence_after_sync();
     const uint32_t taddr = taddr_s;
-    const LastTiles lt = last_tiles(a.B, a.D, a.H, a.W);
+    const LastTiles lt = last_tiles(a.B, a.D, a.H, a.W, a.x_lo, a.x_hi);
     const uint32_t ring_s = smem_u32(ring), w_s = smem_u32(wsm);
 
     if (warp == 0) {
@@ -649,7 +680,8 @@ __global__ void __launch_bounds__(192, LCTAS) k_conv_last_tc(const __grid_consta
             int tx, ty, zlo, zhi, b;
             last_unit(u, lt, a.D, tx, ty, zlo, zhi, b);
             const int cx = tx * LOX + lx - 1, cy = ty * LOY + ly - 1;
-            const bool valid = interior && cx < a.W && cy < a.H;
+            // with an x-range, the block's cells outside it keep their statistics
+            const bool valid = interior && cx < a.W && cy < a.H && (a.x_hi <= a.x_lo || (cx >= a.x_lo && cx < a.x_hi));
             float r1[9], r2[9];
 #pragma unroll
             for (int k = 0; k < 9; ++k) r1[k] = r2[k] = 0.0f;
@@ -755,7 +787,7 @@ hyb_status launch_conv_last_tc(const LastArgs &a, cudaStream_t st) {
     if (a.B < 1 || a.D < 1 || a.H < 1 || a.W < 1) return set_error(HYB_EINVAL, "last layer: empty volume");
     if (((uintptr_t)a.x & 15) || (a.mc_k == 0 && !a.logit) || (a.mc_k > 0 && (!a.pm || !a.m2)))
         return set_error(HYB_EINVAL, "last layer: operands missing or not 16-byte aligned");
-    const LastTiles lt = last_tiles(a.B, a.D, a.H, a.W);
+    const LastTiles lt = last_tiles(a.B, a.D, a.H, a.W, a.x_lo, a.x_hi);
     EncodeTiledFn enc = encode_fn();
     if (!enc) return set_error(HYB_ECUDA, "cuTensorMapEncodeTiled is not available");
     CUtensorMap tm;
@@ -787,6 +819,7 @@ hyb_status launch_conv_last_tc(const LastArgs &a, cudaStream_t st) {
     // LCTAS CTAs per SM by registers and shared memory (the occupancy query
     // answers 1 for kernels that allocate tensor memory); units are
     // independent, so any residency gives the same result
+    if (lt.units == 0) return HYB_OK;
     const long long grid = std::min<long long>(lt.units, (long long)nsm * LCTAS);
     k_conv_last_tc<<<(unsigned)grid, 192, LSMEM, st>>>(tm, a);
     cudaError_t e = cudaGetLastError();

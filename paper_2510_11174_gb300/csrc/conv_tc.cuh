@@ -210,6 +210,7 @@ struct ConvArgs {
     int scale_out;            // kept outputs are multiplied by drop_scale (set with dropout; alone: scaling only)
     uint32_t seed, pass, layer;
     int *status;
+    int x_lo, x_hi;           // when x_hi > x_lo: only the tiles whose outputs meet x_lo <= x < x_hi
 };
 hyb_status launch_conv3_tc(const ConvArgs &a, cudaStream_t st);
 
@@ -237,6 +238,7 @@ struct LastArgs {
     int mc_k;
     float *pm, *m2;           // MC mean and M2 (mc_k >= 1)
     int *status;
+    int x_lo, x_hi;           // when x_hi > x_lo: only the blocks whose outputs meet x_lo <= x < x_hi
 };
 hyb_status launch_conv_last_tc(const LastArgs &a, cudaStream_t st);
 

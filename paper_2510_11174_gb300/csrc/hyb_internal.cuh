@@ -276,6 +276,7 @@ struct hyb_ctx {
     float *rho_bg = nullptr;                       // residual background charge
     float *ne = nullptr;                           // electron density scratch
     uint32_t epoch = 0;                            // conversion counter (Philox counter word)
+    int *xflag = nullptr, *xflag_host = nullptr;   // x-planes holding matter (device, pinned copy; nx each)
     bool fluids_idle = false;                      // every fluid was converted by an all-kinetic classification
 
     // LCFA QED tables (built on first use)
@@ -298,6 +299,7 @@ struct hyb_ctx {
     int conv_ev_passes = 0;                         // passes recorded by the most recent classification
     long long launches_per_step = 0;
     long long launches_classify = 0;               // kernels the most recent hyb_classify launched
+    long long classified_cells = 0;                // nodes the most recent classifier pass computed
 
     // laser transverse profile (FP32, ny*nz) when a Gaussian source is set
     float *laser_profile = nullptr;
@@ -333,6 +335,10 @@ void launch_push_deposit(const GridDev &g, const float *E, const float *B, const
                          cudaStream_t st);
 hyb_status setup_qed(hyb_ctx *c);  // builds the QED tables once per context
 hyb_status regime_update(hyb_ctx *c, const float *p_mean, const float *p_std);
+// the x-range [*xa, *xb) of nodes within `reach` nodes (along x) of an
+// x-plane holding matter (fluid above its floor, or particles); empty
+// (*xa == *xb) without matter.  Synchronises the context stream.
+hyb_status matter_x_range(hyb_ctx *c, int reach, int *xa, int *xb);
 hyb_status classifier_forward(hyb_ctx *c, const hyb_model *m, float *p_mean_dev, float *p_std_dev);
 const float *model_p_mean(const hyb_model *m);
 const float *model_p_std(const hyb_model *m);

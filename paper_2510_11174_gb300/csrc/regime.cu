@@ -9,6 +9,8 @@
 // deposited into a fluid, the charge of converted particles) goes through the
 // per-tile fixed-point frames of frames.cuh and a fixed-order gather, so a
 // classification repeats bit for bit like the step.
+#include <algorithm>
+
 #include "frames.cuh"
 #include "hyb_internal.cuh"
 #include "particles.cuh"
@@ -487,6 +489,81 @@ hyb_status charge_density(hyb_ctx *c, float *rho) {
     k_rho_fluids<<<nblk(g.N), 256, 0, st>>>(g.N, fs, c->rho_bg, rho);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return set_error(HYB_ECUDA, std::string("charge density: ") + cudaGetErrorString(e));
+    return HYB_OK;
+}
+
+struct FluidFloors {
+    float floor_[HYB_MAX_FLUIDS];
+};
+
+// x-planes that hold matter: a fluid above its floor at some node of the
+// plane, or a particle in a cell of the plane (plane floor(x), at most nx - 1)
+__global__ void k_matter_fluid(GridDev g, FluidCharges fs, FluidFloors fl, int *__restrict__ flag) {
+    const int nx = g.n[0];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
+    if (i >= nx) return;
+    const long long c = ((long long)k * g.n[1] + j) * nx + i;
+    bool any = false;
+    for (int f = 0; f < fs.n; ++f) any = any || fs.n_[f][c] > fl.floor_[f];
+    if (any) flag[i] = 1;  // every writer stores the same value
+}
+
+// one block per tile: the planes of its particles gathered in shared memory
+// first (a tile spans T planes), then written once
+__global__ void __launch_bounds__(256) k_matter_particles(GridDev g, SpDev sp, int *__restrict__ flag) {
+    __shared__ int sflag[32];
+    const int t = blockIdx.x, T = g.T, nx = g.n[0];
+    const int x0 = (t % g.nt[0]) * T;
+    if (threadIdx.x < 32) sflag[threadIdx.x] = 0;
+    __syncthreads();
+    const int n = sp.count[t];
+    const long long base = (long long)t * sp.cap;
+    for (int l = threadIdx.x; l < n; l += blockDim.x) {
+        const float x = sp.x[base + l];
+        int p = (int)floorf(x);
+        p = p < 0 ? 0 : (p > nx - 1 ? nx - 1 : p);
+        if (p >= x0 && p < x0 + T && T <= 32) sflag[p - x0] = 1;
+        else flag[p] = 1;
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < T && T <= 32 && sflag[threadIdx.x] && x0 + (int)threadIdx.x < nx) flag[x0 + threadIdx.x] = 1;
+}
+
+hyb_status matter_x_range(hyb_ctx *c, int reach, int *xa, int *xb) {
+    const GridDev &g = c->g;
+    cudaStream_t st = c->stream;
+    const int nx = g.n[0];
+    if (!c->xflag) {
+        if (ctx_alloc(c, (void **)&c->xflag, sizeof(int) * (size_t)nx)) return set_error(HYB_ENOMEM, "matter flags");
+        if (cudaMallocHost((void **)&c->xflag_host, sizeof(int) * (size_t)nx) != cudaSuccess)
+            return set_error(HYB_ENOMEM, "pinned matter flags");
+    }
+    HYB_CUDA_TRY(cudaMemsetAsync(c->xflag, 0, sizeof(int) * (size_t)nx, st));
+    FluidCharges fs;
+    FluidFloors fl;
+    memset(&fs, 0, sizeof(fs));
+    memset(&fl, 0, sizeof(fl));
+    for (size_t f = 0; f < c->fluids.size() && fs.n < HYB_MAX_FLUIDS; ++f) {
+        fl.floor_[fs.n] = c->fluids[f].n_floor;
+        fs.n_[fs.n++] = c->fluids[f].n;
+    }
+    if (fs.n > 0) k_matter_fluid<<<node_grid(g), node_block(g), 0, st>>>(g, fs, fl, c->xflag);
+    for (size_t si = 0; si < c->sp.size(); ++si)
+        k_matter_particles<<<g.ntiles, 256, 0, st>>>(g, c->sp[si].dev, c->xflag);
+    HYB_CUDA_TRY(cudaMemcpyAsync(c->xflag_host, c->xflag, sizeof(int) * (size_t)nx, cudaMemcpyDeviceToHost, st));
+    HYB_CUDA_TRY(cudaStreamSynchronize(st));
+    int lo = nx, hi = -1;
+    for (int x = 0; x < nx; ++x)
+        if (c->xflag_host[x]) {
+            lo = std::min(lo, x);
+            hi = x;
+        }
+    if (hi < 0) {
+        *xa = *xb = 0;
+        return HYB_OK;
+    }
+    *xa = std::max(0, lo - reach);
+    *xb = std::min(nx, hi + 1 + reach);
     return HYB_OK;
 }
 

@@ -195,14 +195,18 @@ class Simulation:
                 "all_kinetic": _abi.HYB_REGIME_ALL_KINETIC}
 
     def set_regime(self, a_thr=1.0, n_thr=1.0, c_thr=0.1, chi_thr=1e-3, dilate=2, k_sigma=1.0, ppc=8,
-                   to_species=None, policy="default", quiet=False):
+                   to_species=None, policy="default", quiet=False, reach=0):
         """Thresholds and conversion targets of hyb_classify; policy is
         "default" (classifier if given, else physics criterion), "union"
         (classifier or criterion) or "all_kinetic" (full PIC); quiet=True
-        places converted particles on a sub-lattice of the node's dual cell."""
+        places converted particles on a sub-lattice of the node's dual cell;
+        reach > 0 runs the classifier only within reach + dilate nodes (in x)
+        of matter (exact when the next classification is at most `reach`
+        steps away)."""
         d = _abi.hyb_regime_desc()
         d.policy = self.POLICIES[policy]
         d.quiet = int(bool(quiet))
+        d.reach = int(reach)
         d.a_thr, d.n_thr, d.c_thr, d.chi_thr = a_thr, n_thr, c_thr, chi_thr
         d.dilate, d.k_sigma, d.ppc = dilate, k_sigma, ppc
         ts = list(to_species or [])
@@ -317,6 +321,7 @@ class Simulation:
                 "w_fluid": [out.w_fluid[i] for i in range(out.n_fluids)],
                 "n_fluid": [out.n_fluid[i] for i in range(out.n_fluids)], "n_clamped": out.n_clamped,
                 "launches_classify": out.launches_classify,
+                "classified_cells": out.classified_cells,
                 "tile_capacity": [out.tile_capacity[i] for i in range(ns)]}
 
     def eval_qed(self, what, chi, r=None):

@@ -225,3 +225,37 @@ def test_quiet_start_of_a_uniform_fluid_leaves_no_residual_charge(ppc):
     rho_bg2 = np.zeros(g.shape)
     oracle.fluid_to_particles(g, mask, fl2, ppc, 5, 0, 1, rho_bg2, quiet=False)
     assert np.max(np.abs(rho_bg2)) > 1e-3
+
+
+def test_reach_zeroes_the_statistics_away_from_matter_and_keeps_them_near_it():
+    """With a reach the classifier's statistics stay those of the whole grid on
+    the x-planes within reach + dilate of matter (fluid above its floor in
+    planes 10..12, one particle in plane 30) and are zero elsewhere; the
+    planes are found by brute force over the nodes and particles."""
+    from oracle.classifier import OracleCNN
+    from oracle.sim import OracleSim
+    from paper_2510_11174_gb300 import inputs
+    nx, ny, nz = 48, 8, 4
+    rng = np.random.default_rng(3)
+    E = (0.3 * rng.standard_normal((3, nz, ny, nx))).astype(np.float32)
+    B = (0.3 * rng.standard_normal((3, nz, ny, nx))).astype(np.float32)
+    n = np.zeros((nz, ny, nx))
+    n[:, :, 10:13] = 0.5
+    n[1, 2, 9] = 1e-12                        # below the floor: not matter
+    net = OracleCNN(inputs.classifier_weights(4), dropout=0.2, seed=4)
+    out = {}
+    for reach in (0, 3):
+        o = OracleSim(nx, ny, nz, 0.3, bc=(1, 1, 1))
+        one = lambda v: np.array([v], np.float32)
+        o.load_species(-1.0, 1.0, one(30.5), one(4.0), one(2.0), one(0.0), one(0.0), one(0.0), one(1e-3))
+        o.load_fluid(-1.0, 1.0, n, n_floor=1e-10)
+        o.set_fields(E, B)
+        o.set_regime(ppc=1, to_species=[-1], dilate=1, reach=reach)
+        assert list(o.matter_planes()) == [10, 11, 12, 30]
+        out[reach] = o.classify(net, passes=2)
+    (pm0, ps0), (pm3, ps3) = out[0], out[3]
+    keep = np.zeros(nx, dtype=bool)
+    keep[10 - 4:30 + 1 + 4] = True            # reach 3 + dilate 1 around planes 10 .. 30
+    assert np.array_equal(pm3[:, :, keep], pm0[:, :, keep]) and np.array_equal(ps3[:, :, keep], ps0[:, :, keep])
+    assert not pm3[:, :, ~keep].any() and not ps3[:, :, ~keep].any()
+    assert pm0[:, :, ~keep].all()
