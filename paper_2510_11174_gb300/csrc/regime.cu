@@ -221,6 +221,25 @@ __global__ void k_dilate(GridDev g, int a, int r, const uint8_t *__restrict__ in
     out[c] = m ? 1 : 0;
 }
 
+// the maximum filter along x over whole 32-bit words (four nodes per thread,
+// nx % 4 == 0, r <= 4): the words left and right of a node's word hold every
+// byte within r of it
+__global__ void k_dilate4x(GridDev g, int r, const uint32_t *__restrict__ in, uint32_t *__restrict__ out) {
+    const int nx4 = g.n[0] >> 2, ny = g.n[1];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
+    if (i >= nx4) return;
+    const long long row = ((long long)k * ny + j) * nx4;
+    const bool per = g.bc[0] == 0;
+    const uint32_t w = in[row + i];
+    const uint32_t L = i > 0 ? in[row + i - 1] : (per ? in[row + nx4 - 1] : 0u);
+    const uint32_t R = i < nx4 - 1 ? in[row + i + 1] : (per ? in[row] : 0u);
+    const uint64_t lw = ((uint64_t)w << 32) | L;  // byte b: node 4 i - 4 + b
+    const uint64_t rw = ((uint64_t)R << 32) | w;  // byte b: node 4 i + b
+    uint32_t m = w;
+    for (int d = 1; d <= r; ++d) m |= (uint32_t)(lw >> (8 * (4 - d))) | (uint32_t)(rw >> (8 * d));
+    out[row + i] = m;
+}
+
 // the same maximum filter along y or z (a = 1, 2) for four consecutive x
 // nodes at once (nx % 4 == 0): whole 32-bit words of the mask
 __global__ void k_dilate4(GridDev g, int a, int r, const uint32_t *__restrict__ in, uint32_t *__restrict__ out) {
@@ -635,14 +654,16 @@ hyb_status regime_update(hyb_ctx *c, const float *pm, const float *ps) {
     if (pm && !all && ++launches) k_decide<<<nblk(g.N), 256, 0, st>>>(g.N, pm, ps, (float)rd.k_sigma, physics ? 1 : 0, raw);
     // Chebyshev dilation: max filters along x, y, z (raw -> mask -> raw -> mask)
     const dim3 db = node_block(g), dg = node_grid(g);
-    k_dilate<<<dg, db, 0, st>>>(g, 0, rd.dilate, raw, mask);
     if (g.n[0] % 4 == 0 && ((uintptr_t)mask & 3) == 0 && ((uintptr_t)raw & 3) == 0) {
-        // word-wide along y and z
+        // word-wide: four nodes per thread
         const int nx4 = g.n[0] / 4, b4 = nx4 >= 128 ? 128 : 32 * ((nx4 + 31) / 32);
         const dim3 dg4((unsigned)((nx4 + b4 - 1) / b4), (unsigned)g.n[1], (unsigned)g.n[2]);
+        if (rd.dilate <= 4) k_dilate4x<<<dg4, b4, 0, st>>>(g, rd.dilate, (const uint32_t *)raw, (uint32_t *)mask);
+        else k_dilate<<<dg, db, 0, st>>>(g, 0, rd.dilate, raw, mask);
         k_dilate4<<<dg4, b4, 0, st>>>(g, 1, rd.dilate, (const uint32_t *)mask, (uint32_t *)raw);
         k_dilate4<<<dg4, b4, 0, st>>>(g, 2, rd.dilate, (const uint32_t *)raw, (uint32_t *)mask);
     } else {
+        k_dilate<<<dg, db, 0, st>>>(g, 0, rd.dilate, raw, mask);
         k_dilate<<<dg, db, 0, st>>>(g, 1, rd.dilate, mask, raw);
         k_dilate<<<dg, db, 0, st>>>(g, 2, rd.dilate, raw, mask);
     }

@@ -104,3 +104,31 @@ def test_reach_restricted_classification_repeats_the_whole_grid_run():
     full.close()
     near.close()
     model.close()
+
+
+def test_reach_without_matter_classifies_nothing():
+    """No fluid above its floor and no particle: nothing to classify, the
+    statistics are zero everywhere, and a negative reach is rejected."""
+    P = require_gpu()
+    import torch
+    inp = _workload()
+    g = inp["grid"]
+    sim = P.Simulation(g["nx"], g["ny"], g["nz"], g["dx"], cfl_frac=g["cfl_frac"], bc=g["bc"], laser=inp["laser"])
+    for sp in inp["species"]:
+        sim.load_species(**sp)
+    for fl in inp["fluids"]:
+        sim.load_fluid(**dict(fl, n=np.zeros_like(fl["n"])))
+    with pytest.raises(Exception):
+        sim.set_regime(dilate=1, ppc=inp["ppc"], to_species=[0, 1], policy="union", reach=-1)
+    sim.set_regime(dilate=1, ppc=inp["ppc"], to_species=[0, 1], policy="union", reach=REACH)
+    model, _ = seeded_classifier(P, 9, out_bias=-2.0, dropout=0.2, mc_passes=4)
+    cells = g["nx"] * g["ny"] * g["nz"]
+    pm = torch.full((cells,), 7.0, dtype=torch.float32, device="cuda")
+    ps = torch.full((cells,), 7.0, dtype=torch.float32, device="cuda")
+    sim.classify(model, p_mean=pm, p_std=ps)
+    torch.cuda.synchronize()
+    assert not pm.any().item() and not ps.any().item()
+    d = sim.diagnostics()
+    assert d["classified_cells"] == 0 and d["status"] == 0
+    sim.close()
+    model.close()
