@@ -486,6 +486,11 @@ def run_ours(args, rank, world):
         if learned is not None:
             # the trained classifier alone against the same full-PIC run
             full["learned_policy_speedup"] = full_step / learned["ms_per_step"]
+        if cls and full["hybrid_speedup"] < 1.0:
+            full["why_below_one"] = (
+                "every %d steps the %d-pass classification (%.1f ms) and its regime work (%.1f ms) cost more "
+                "than the %.2f ms per step the hybrid step saves over full PIC (%.2f against %.2f ms)"
+                % (N_CLS, MC_PASSES, cls["classify"], cls["regime"], full_step - plain, plain, full_step))
 
     e2e = run_e2e(P, inp, args.steps, stream, trained) if rank == 0 else None
     # the same with the diagnostics read back once per classification interval
