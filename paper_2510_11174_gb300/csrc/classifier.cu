@@ -401,6 +401,7 @@ hyb_status classifier_forward(hyb_ctx *c, const hyb_model *mc, float *p_mean_dev
                 cudaEvent_t e;
                 if (cudaEventCreate(&e) != cudaSuccess) {
                     m->stream = saved;
+                    m->xr_lo = m->xr_hi = 0;
                     return set_error(HYB_ECUDA, "profiling event creation");
                 }
                 c->conv_ev.push_back(e);
