@@ -460,8 +460,9 @@ def run_ours(args, rank, world):
                                           "hybrid-step launch, times the particles; peak = 152 SMs x 4 issue "
                                           "slots per cycle at the sampled SM clock"}
     if "conv_l1" in roofs:
-        roofs["conv_l1"]["traffic"] = NCU_CONV_L1_BYTES_PER_CELL * cells
-        roofs["conv_l1"]["traffic_note"] = "ncu dram bytes of a 128x128x64 launch scaled by cells"
+        # scaled by the nodes the classification evaluated (the launch's tiles cover them and a few more)
+        roofs["conv_l1"]["traffic"] = NCU_CONV_L1_BYTES_PER_CELL * (cls.get("classified_cells") or cells)
+        roofs["conv_l1"]["traffic_note"] = "ncu dram bytes of a 128x128x64 launch scaled by the classified cells"
     # the dominant single kernel (the classification as a whole is reported beside it)
     dom = max((k for k in roofs if k != "classify"), key=lambda k: roofs[k]["share"])
 
