@@ -644,6 +644,18 @@ def run_train_surrogate(args, P, torch, stream):
     pq, _ = held_out(mq)
     r2q, mseq = training.r2_mse(pq, tte, mean, std)
     mq.close()
+    # physics-loss ablation: the same training without the energy-conservation term
+    m0 = P.Surrogate(dropout=0.1, mc_passes=MC_PASSES, seed=11, mean=mean, std=std, dstd=dstd, lr=SUR_LR,
+                     energy_weight=0.0, stream=stream.cuda_stream)
+    st0 = training.train_surrogate(m0, xtr, ttr, SUR_PRETRAIN_STEPS)
+    p0, _ = held_out(m0)
+    r20, mse0 = training.r2_mse(p0, tte, mean, std)
+    m0.close()
+
+    def energy_violation(pred):
+        # relative error of the held-out set's total field energy (1/2) sum (E^2 + B^2)
+        w = lambda st_: 0.5 * (st_[:, :6].double() ** 2).sum()
+        return float(abs(w(pred) - w(tte)) / w(tte))
     r2_keep, mse_keep = training.r2_mse(xte, tte, mean, std)
     sd = torch.tensor(std, device=ps.device).view(1, -1, 1, 1, 1)
     cells = 32 * 16 ** 3
@@ -677,6 +689,11 @@ def run_train_surrogate(args, P, torch, stream):
                          "mc_std_max_normalised": float((ps / sd).max()),
                          "huber_delta_1": {"r2": dict(zip(names, r2q)), "mse": dict(zip(names, mseq)),
                                            "r2_mean": float(np.mean(r2q)), "train_s": q_s},
+                         "energy_violation": energy_violation(pm),
+                         "without_energy_term": {"r2": dict(zip(names, r20)), "mse": dict(zip(names, mse0)),
+                                                 "r2_mean": float(np.mean(r20)), "mse_max": float(np.max(mse0)),
+                                                 "energy_violation": energy_violation(p0),
+                                                 "train_energy_violation_last": st0[-1]["energy"]},
                          "paper_context": "R^2 0.9778 and MSE 1.47e-4 on the paper's own data (Results)"},
             "clocks": clk, "gpu_launches": None}
 
