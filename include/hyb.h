@@ -244,10 +244,11 @@ typedef struct {
                                              0: Philox-uniform positions */
     int reach;                            /* 0: the classifier runs on every node.  r > 0: it runs only on
                                              the nodes whose x lies within r + dilate nodes of an x-plane
-                                             holding matter (a fluid above its n_floor, or a tile with
-                                             particles); p_mean = p_std = 0 on the other nodes.  Fluid
-                                             moves at most one node per step and particles less, so with
-                                             r at least the number of steps to the next classification the
+                                             holding matter (a fluid above its n_floor at a node of the
+                                             plane, or a particle with floor(x) in it); p_mean = p_std = 0
+                                             on the other nodes.  Fluid moves at most one node per step and
+                                             particles less, so with r at least the number of steps to the
+                                             next classification plus one (a particle's CIC node) the
                                              decision differs from the whole-grid one only where no matter
                                              can be before then, and the run (conversions, fields,
                                              particles) is the same.  hyb_classify then synchronises the
