@@ -201,7 +201,7 @@ class Simulation:
         (classifier or criterion) or "all_kinetic" (full PIC); quiet=True
         places converted particles on a sub-lattice of the node's dual cell;
         reach > 0 runs the classifier only within reach + dilate nodes (in x)
-        of matter (exact when the next classification is at most `reach`
+        of matter (exact when the next classification is at most reach - 1
         steps away)."""
         d = _abi.hyb_regime_desc()
         d.policy = self.POLICIES[policy]
