@@ -387,6 +387,17 @@ def run_ours(args, rank, world):
     kin_frac = float(sim.get_regime()[0].mean()) if kind == "hybrid" else 1.0
     phases, cls = profile_phases(sim, model, args.warmup + args.steps)
     launches = after["launches_per_step"] * args.steps + ncls * after["launches_classify"]
+    if cls and inp.get("fluids"):
+        # the same classification of every node (no reach), once, on the state the
+        # run ended with: what the reach restriction saves
+        sim.set_regime(dilate=2, ppc=inp["ppc"], to_species=list(range(len(inp["fluids"]))), policy="union",
+                       reach=0)
+        sim.set_profiling(True)
+        sim.classify(model)
+        pt = sim.phase_times()
+        sim.set_profiling(False)
+        cls["classify_every_node"] = pt["classify"]
+        cls["every_node_cells"] = sim.diagnostics()["classified_cells"]
     sim.close()
     learned = None
     if trained is not None:
