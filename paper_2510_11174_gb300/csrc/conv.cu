@@ -673,6 +673,7 @@ __global__ void __launch_bounds__(192, LCTAS) k_conv_last_tc(const __grid_consta
         const int m = q * 32 + lane;                 // row = cell of the block
         const int lx = m & (LTX - 1), ly = m >> 4;
         const bool interior = lx >= 1 && lx <= LOX && ly >= 1 && ly <= LOY;
+        const float inv_k = a.mc_k > 0 ? 1.0f / (float)a.mc_k : 0.0f;  // the Welford weight of this pass
         bool dead = false;
         const long long V = (long long)a.D * a.H * a.W;
         long long it = 0;
@@ -762,13 +763,13 @@ __global__ void __launch_bounds__(192, LCTAS) k_conv_last_tc(const __grid_consta
                     if (a.mc_k == 0) {
                         a.logit[t] = logit;
                     } else {
-                        const float pv = 1.0f / (1.0f + expf(-logit));
+                        const float pv = __frcp_rn(1.0f + __expf(-logit));
                         if (a.mc_k == 1) {
                             a.pm[t] = pv;
                             a.m2[t] = 0.0f;
                         } else {
                             const float d = pv - mo;
-                            const float mn = mo + d / (float)a.mc_k;
+                            const float mn = mo + d * inv_k;
                             a.pm[t] = mn;
                             a.m2[t] = m2o + d * (pv - mn);
                         }
