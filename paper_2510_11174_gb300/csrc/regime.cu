@@ -559,7 +559,7 @@ __global__ void __launch_bounds__(256) k_matter_particles(GridDev g, SpDev sp, i
     const int x0 = (t % g.nt[0]) * T;
     if (threadIdx.x < 32) sflag[threadIdx.x] = 0;
     __syncthreads();
-    const int n = sp.count[t];
+    const int n = min(sp.count[t], sp.cap);
     const long long base = (long long)t * sp.cap;
     for (int l = threadIdx.x; l < n; l += blockDim.x) {
         const float x = sp.x[base + l];
