@@ -194,7 +194,10 @@ class OracleSim:
                 keep = np.zeros(nx, dtype=bool)
                 if planes.size:
                     R = r["reach"] + r["dilate"]
-                    keep[max(0, planes.min() - R):min(nx, planes.max() + 1 + R)] = True
+                    lo, hi = planes.min() - R, planes.max() + 1 + R
+                    if self.g.bc[0] == 0 and (lo < 0 or hi > nx):
+                        lo, hi = 0, nx   # a periodic x-axis: a range that reaches an end wraps round
+                    keep[max(0, lo):min(nx, hi)] = True
                 pm = np.where(keep[None, None, :], pm, 0.0)
                 ps = np.where(keep[None, None, :], ps, 0.0)
             mask |= dilate(g, pm + r["k_sigma"] * ps >= 0.5, r["dilate"])

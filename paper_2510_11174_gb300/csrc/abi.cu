@@ -93,7 +93,7 @@ static void enqueue_step(hyb_ctx *c) {
     const bool fluid_phase = !c->fluids.empty() && !c->fluids_idle;
     if (fluid_phase) {
         pm.begin(HYB_PH_FLUID);
-        launch_fluids(g, c->E, c->B, c->fluids.data(), (int)c->fluids.size(), c->J, st);
+        launch_fluids(g, c->E, c->B, c->fluids.data(), (int)c->fluids.size(), c->J, c->fluid_xr, st);
         pm.end(HYB_PH_FLUID);
     }
     if (c->desc.laser_kind == HYB_LASER_GAUSS) {
@@ -275,7 +275,8 @@ hyb_status hyb_init_grid(const hyb_grid_desc *d, hyb_ctx **out) {
         ctx_alloc(c, (void **)&c->mask, (size_t)g.N) || ctx_alloc(c, (void **)&c->mask_tmp, (size_t)g.N) ||
         ctx_alloc(c, (void **)&c->mask_prev, (size_t)g.N) ||
         ctx_alloc(c, (void **)&c->rho_bg, sizeof(float) * (size_t)g.N) ||
-        ctx_alloc(c, (void **)&c->ne, sizeof(float) * (size_t)g.N))
+        ctx_alloc(c, (void **)&c->ne, sizeof(float) * (size_t)g.N) ||
+        ctx_alloc(c, (void **)&c->fluid_xr, 2 * sizeof(int)))
         return fail(HYB_ENOMEM, "device allocation for the grid failed (arena too small?)");
     cudaStream_t st = c->stream;
     cudaMemsetAsync(c->E, 0, fbytes, st);
@@ -286,7 +287,9 @@ hyb_status hyb_init_grid(const hyb_grid_desc *d, hyb_ctx **out) {
     cudaMemsetAsync(c->step_dev, 0, sizeof(long long), st);
     cudaMemsetAsync(c->mask, 0, (size_t)g.N, st);  // no node has switched to kinetic before a classification
     cudaMemsetAsync(c->fill_flags, 0, sizeof(int), st);
+    cudaMemsetAsync(c->fluid_xr, 0, 2 * sizeof(int), st);  // every plane
     if (cudaMallocHost((void **)&c->fill_host, sizeof(int)) != cudaSuccess ||
+        cudaMallocHost((void **)&c->fluid_xr_host, 2 * sizeof(int)) != cudaSuccess ||
         cudaMallocHost((void **)&c->diag_host, sizeof(DiagSummary)) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->fill_ev, cudaEventDisableTiming) != cudaSuccess)
         return fail(HYB_ENOMEM, "pinned fill flag");
@@ -337,6 +340,7 @@ void hyb_destroy(hyb_ctx *c) {
     if (c->fill_host) cudaFreeHost(c->fill_host);
     if (c->diag_host) cudaFreeHost(c->diag_host);
     if (c->xflag_host) cudaFreeHost(c->xflag_host);
+    if (c->fluid_xr_host) cudaFreeHost(c->fluid_xr_host);
     if (c->fill_ev) cudaEventDestroy(c->fill_ev);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
@@ -635,6 +639,9 @@ hyb_status hyb_load_fluid(hyb_ctx *c, const hyb_fluid_desc *d, int *fluid_id) {
     HYB_CUDA_TRY(cudaMemsetAsync(f.clamped, 0, sizeof(unsigned long long), c->stream));
     HYB_CUDA_TRY(cudaStreamSynchronize(c->stream));
     c->fluids_idle = false;
+    // a new fluid's u where n = 0 is whatever was loaded: no fluid range until a step has run
+    c->fluid_fresh_step = c->step;
+    if (clear_fluid_range(c, c->stream) != HYB_OK) return set_error(HYB_ECUDA, "fluid range reset");
     *fluid_id = (int)c->fluids.size();
     c->fluids.push_back(f);
     c->graph_valid = false;
@@ -688,6 +695,7 @@ hyb_status hyb_classify(hyb_ctx *c, const hyb_model *model, float *p_mean_dev, f
     c->phase_ran[HYB_PH_REGIME] = c->profiling;
     mark(c->ev_start[HYB_PH_REGIME]);
     s = model ? regime_update(c, model_p_mean(model), model_p_std(model)) : regime_update(c, nullptr, nullptr);
+    if (s == HYB_OK) s = set_fluid_range(c);
     mark(c->ev_end[HYB_PH_REGIME]);
     if (s != HYB_OK) return s;
     if (mask_dev) HYB_CUDA_TRY(cudaMemcpyAsync(mask_dev, c->mask, (size_t)c->g.N, cudaMemcpyDeviceToDevice, c->stream));
@@ -807,7 +815,13 @@ hyb_status hyb_step(hyb_ctx *c, int nsteps) {
             if (cs != HYB_OK) return cs;
         }
         const int chunk = std::min(nsteps - done, GROW_CHECK_STEPS);
-        for (int i = 0; i < chunk; ++i) HYB_CUDA_TRY(cudaGraphLaunch(c->graph, c->stream));
+        for (int i = 0; i < chunk; ++i) {
+            if (c->fluid_xr_until >= 0 && c->step + i >= c->fluid_xr_until) {
+                hyb_status fs = clear_fluid_range(c, c->stream);  // the range has lapsed: every plane again
+                if (fs != HYB_OK) return fs;
+            }
+            HYB_CUDA_TRY(cudaGraphLaunch(c->graph, c->stream));
+        }
         done += chunk;
         c->step += chunk;
         c->steps_since_copy += chunk;
@@ -936,7 +950,14 @@ hyb_status hyb_batch_step(hyb_batch *b, int nsteps) {
             if (bs != HYB_OK) return bs;
         }
         const int chunk = std::min(nsteps - done, GROW_CHECK_STEPS);
-        for (int k = 0; k < chunk; ++k) HYB_CUDA_TRY(cudaGraphLaunch(b->exec, b->stream));
+        for (int k = 0; k < chunk; ++k) {
+            for (hyb_ctx *c : b->ctx)
+                if (c->fluid_xr_until >= 0 && c->step + k >= c->fluid_xr_until) {
+                    hyb_status fs = clear_fluid_range(c, b->stream);  // a lapsed range: every plane again
+                    if (fs != HYB_OK) return fs;
+                }
+            HYB_CUDA_TRY(cudaGraphLaunch(b->exec, b->stream));
+        }
         done += chunk;
         for (hyb_ctx *c : b->ctx) {
             c->step += chunk;

@@ -34,12 +34,22 @@ struct FluidSet {
 __device__ __forceinline__ int lower_nb(int i, int n, int periodic) { return i > 0 ? i - 1 : (periodic ? n - 1 : -1); }
 __device__ __forceinline__ int upper_nb(int i, int n, int periodic) { return i < n - 1 ? i + 1 : (periodic ? 0 : -1); }
 
+// node plane i outside the x-range [xr[0], xr[1]) that a classification with a
+// reach set (xr[1] <= xr[0]: every plane counts as inside).  Outside it every
+// fluid is empty (n = 0, u = 0) and stays so until the range lapses: each face
+// there joins two empty nodes and carries no flux whatever their u*
+__device__ __forceinline__ bool outside_range(const int *__restrict__ xr, int i) {
+    const int lo = __ldg(xr), hi = __ldg(xr + 1);
+    return hi > lo && (i < lo || i >= hi);
+}
+
 // grid: (ceil(nx / blockDim.x), ny, nz); one thread per node
 __global__ void __launch_bounds__(128) k_fluid_lorentz(GridDev g, const float *__restrict__ E,
-                                                       const float *__restrict__ B, FluidSet fs) {
+                                                       const float *__restrict__ B, FluidSet fs,
+                                                       const int *__restrict__ xr) {
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
     const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
-    if (i >= nx) return;
+    if (i >= nx || outside_range(xr, i)) return;
     const int im = lower_nb(i, nx, g.bc[0] == 0), jm = lower_nb(j, ny, g.bc[1] == 0),
               km = lower_nb(k, nz, g.bc[2] == 0);
     const long long N = g.N;
@@ -100,10 +110,11 @@ __global__ void __launch_bounds__(128) k_fluid_lorentz(GridDev g, const float *_
     }
 }
 
-__global__ void __launch_bounds__(128) k_fluid_update(GridDev g, FluidSet fs, float *__restrict__ J) {
+__global__ void __launch_bounds__(128) k_fluid_update(GridDev g, FluidSet fs, float *__restrict__ J,
+                                                      const int *__restrict__ xr) {
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
     const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
-    if (i >= nx) return;
+    if (i >= nx || outside_range(xr, i)) return;
     const int idx[3] = {i, j, k};
     // neighbour nodes (lower, upper) per axis; -1 = closed outer face
     int nbi[3][2];
@@ -197,15 +208,15 @@ __global__ void __launch_bounds__(FB) k_fluid_energy(GridDev g, FluidDev f, doub
 }
 
 void launch_fluids(const GridDev &g, const float *E, const float *B, const FluidDev *f, int nf, float *J,
-                   cudaStream_t st) {
+                   const int *xr, cudaStream_t st) {
     FluidSet fs;
     memset(&fs, 0, sizeof(fs));
     fs.n = nf < HYB_MAX_FLUIDS ? nf : HYB_MAX_FLUIDS;
     for (int q = 0; q < fs.n; ++q) fs.f[q] = f[q];
     const int bx = g.n[0] >= 128 ? 128 : 32 * ((g.n[0] + 31) / 32);
     const dim3 grid((unsigned)((g.n[0] + bx - 1) / bx), (unsigned)g.n[1], (unsigned)g.n[2]);
-    k_fluid_lorentz<<<grid, bx, 0, st>>>(g, E, B, fs);
-    k_fluid_update<<<grid, bx, 0, st>>>(g, fs, J);
+    k_fluid_lorentz<<<grid, bx, 0, st>>>(g, E, B, fs, xr);
+    k_fluid_update<<<grid, bx, 0, st>>>(g, fs, J, xr);
 }
 
 void launch_fluid_energy(const GridDev &g, const FluidDev &f, double *p_w, double *p_n, int nblocks,

@@ -277,6 +277,11 @@ struct hyb_ctx {
     float *ne = nullptr;                           // electron density scratch
     uint32_t epoch = 0;                            // conversion counter (Philox counter word)
     int *xflag = nullptr, *xflag_host = nullptr;   // x-planes holding matter (device, pinned copy; nx each)
+    // the fluid kernels' x-range [lo, hi) (device; hi <= lo: every plane), set by a
+    // classification with a reach and valid for the steps before fluid_xr_until
+    int *fluid_xr = nullptr, *fluid_xr_host = nullptr;
+    long long fluid_xr_until = -1;                 // -1: no range in force
+    long long fluid_fresh_step = 0;                // the step of the latest fluid load or state restore
     bool fluids_idle = false;                      // every fluid was converted by an all-kinetic classification
 
     // LCFA QED tables (built on first use)
@@ -339,11 +344,16 @@ hyb_status regime_update(hyb_ctx *c, const float *p_mean, const float *p_std);
 // x-plane holding matter (fluid above its floor, or particles); empty
 // (*xa == *xb) without matter.  Synchronises the context stream.
 hyb_status matter_x_range(hyb_ctx *c, int reach, int *xa, int *xb);
+// after a classification with a reach: restrict the fluid kernels to the
+// x-planes within the reach of nonzero fluid density for the next `reach` steps
+hyb_status set_fluid_range(hyb_ctx *c);
+// back to every plane (stream-ordered)
+hyb_status clear_fluid_range(hyb_ctx *c, cudaStream_t st);
 hyb_status classifier_forward(hyb_ctx *c, const hyb_model *m, float *p_mean_dev, float *p_std_dev);
 const float *model_p_mean(const hyb_model *m);
 const float *model_p_std(const hyb_model *m);
 void launch_fluids(const GridDev &g, const float *E, const float *B, const FluidDev *f, int nf, float *J,
-                   cudaStream_t st);
+                   const int *xr, cudaStream_t st);
 // FP64 partials of sum n m (gamma-1) (into p_w) and sum n (into p_n), nblocks each
 void launch_fluid_energy(const GridDev &g, const FluidDev &f, double *p_w, double *p_n, int nblocks,
                          cudaStream_t st);

@@ -605,8 +605,74 @@ hyb_status matter_x_range(hyb_ctx *c, int reach, int *xa, int *xb) {
         *xa = *xb = 0;
         return HYB_OK;
     }
+    // on a periodic x-axis a range that reaches an end wraps round: take every plane
+    if (g.bc[0] == 0 && (lo - reach < 0 || hi + 1 + reach > nx)) {
+        *xa = 0;
+        *xb = nx;
+        return HYB_OK;
+    }
     *xa = std::max(0, lo - reach);
     *xb = std::min(nx, hi + 1 + reach);
+    return HYB_OK;
+}
+
+// x-planes where some fluid's density is not exactly zero
+__global__ void k_fluid_nonzero(GridDev g, FluidCharges fs, int *__restrict__ flag) {
+    const int nx = g.n[0];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
+    if (i >= nx) return;
+    const long long c = ((long long)k * g.n[1] + j) * nx + i;
+    bool any = false;
+    for (int f = 0; f < fs.n; ++f) any = any || fs.n_[f][c] != 0.0f;
+    if (any) flag[i] = 1;  // every writer stores the same value
+}
+
+hyb_status clear_fluid_range(hyb_ctx *c, cudaStream_t st) {
+    c->fluid_xr_until = -1;
+    HYB_CUDA_TRY(cudaMemsetAsync(c->fluid_xr, 0, 2 * sizeof(int), st));
+    return HYB_OK;
+}
+
+// The fluid kernels may skip the planes farther than `reach` from every plane
+// with nonzero fluid density for the next `reach` steps: fluid spreads at most
+// one node per step, and the transport of step k needs u* only where the
+// density may be nonzero after k steps (a face between two empty nodes carries
+// no flux).  An empty node outside the range keeps u = 0, which the update of
+// every node has set since the latest load (so at least one step must have
+// run since then); conversions happen only in hyb_classify, before this.
+hyb_status set_fluid_range(hyb_ctx *c) {
+    const GridDev &g = c->g;
+    cudaStream_t st = c->stream;
+    const int nx = g.n[0], reach = c->regime.reach;
+    if (reach <= 0 || c->fluids.empty() || c->fluids_idle || c->step <= c->fluid_fresh_step)
+        return clear_fluid_range(c, st);
+    if (!c->xflag) {
+        if (ctx_alloc(c, (void **)&c->xflag, sizeof(int) * (size_t)nx)) return set_error(HYB_ENOMEM, "matter flags");
+        if (cudaMallocHost((void **)&c->xflag_host, sizeof(int) * (size_t)nx) != cudaSuccess)
+            return set_error(HYB_ENOMEM, "pinned matter flags");
+    }
+    HYB_CUDA_TRY(cudaMemsetAsync(c->xflag, 0, sizeof(int) * (size_t)nx, st));
+    FluidCharges fs;
+    memset(&fs, 0, sizeof(fs));
+    for (size_t f = 0; f < c->fluids.size() && fs.n < HYB_MAX_FLUIDS; ++f) fs.n_[fs.n++] = c->fluids[f].n;
+    k_fluid_nonzero<<<node_grid(g), node_block(g), 0, st>>>(g, fs, c->xflag);
+    HYB_CUDA_TRY(cudaMemcpyAsync(c->xflag_host, c->xflag, sizeof(int) * (size_t)nx, cudaMemcpyDeviceToHost, st));
+    HYB_CUDA_TRY(cudaStreamSynchronize(st));
+    int lo = nx, hi = -1;
+    for (int x = 0; x < nx; ++x)
+        if (c->xflag_host[x]) {
+            lo = std::min(lo, x);
+            hi = x;
+        }
+    if (hi < 0) return clear_fluid_range(c, st);  // no fluid density anywhere
+    const int xa = std::max(0, lo - reach), xb = std::min(nx, hi + 1 + reach);
+    if ((g.bc[0] == 0 && (lo - reach < 0 || hi + 1 + reach > nx)) || (xa == 0 && xb == nx))
+        return clear_fluid_range(c, st);  // nothing to gain (or a periodic range that wraps round)
+    c->fluid_xr_host[0] = xa;
+    c->fluid_xr_host[1] = xb;
+    HYB_CUDA_TRY(cudaMemcpyAsync(c->fluid_xr, c->fluid_xr_host, 2 * sizeof(int), cudaMemcpyHostToDevice, st));
+    HYB_CUDA_TRY(cudaStreamSynchronize(st));  // the pinned source may change at the next classification
+    c->fluid_xr_until = c->step + reach;
     return HYB_OK;
 }
 

@@ -343,6 +343,9 @@ hyb_status hyb_set_state(hyb_ctx *c, const void *buf, size_t size) {
     c->step = h.step;
     c->epoch = h.epoch;
     c->regime = h.regime;
+    // the fluid kernels cover every plane again until the next classification (after a step)
+    c->fluid_fresh_step = h.step;
+    if (clear_fluid_range(c, c->stream) != HYB_OK) return set_error(HYB_ECUDA, "fluid range reset");
     if (c->fluids_idle != (h.fluids_idle != 0)) c->fluids_idle = h.fluids_idle != 0;
     HYB_CUDA_TRY(cudaMemcpyAsync(c->step_dev, &h.step, sizeof(long long), cudaMemcpyHostToDevice, c->stream));
     HYB_CUDA_TRY(cudaMemcpyAsync(c->status, &h.status, sizeof(int), cudaMemcpyHostToDevice, c->stream));
