@@ -329,7 +329,9 @@ def profile_phases(sim, model, step0):
     sim.set_profiling(True)
     per = []
     cls = {}
+    fc = []
     for k in range(N_CLS):
+        fc.append(sim.diagnostics()["fluid_cells"])  # the range the next step's fluid update covers
         sim.step(1)
         per.append(sim.phase_times())
         if model is not None and (step0 + k + 1) % N_CLS == 0:
@@ -342,6 +344,7 @@ def profile_phases(sim, model, step0):
     sim.set_profiling(False)
     step_phases = ["push", "j_reduce", "source", "rebin", "field", "fluid"]
     mean = {k: statistics.mean(p.get(k, 0.0) for p in per) for k in step_phases}
+    mean["fluid_cells"] = statistics.mean(fc)
     return mean, cls
 
 
@@ -386,6 +389,7 @@ def run_ours(args, rank, world):
     parts = 0.5 * (sum(before["count"]) + sum(after["count"]))
     kin_frac = float(sim.get_regime()[0].mean()) if kind == "hybrid" else 1.0
     phases, cls = profile_phases(sim, model, args.warmup + args.steps)
+    fluid_cells = phases.pop("fluid_cells")
     launches = after["launches_per_step"] * args.steps + ncls * after["launches_classify"]
     if cls and inp.get("fluids"):
         # the same classification of every node (no reach), once, on the state the
@@ -431,10 +435,12 @@ def run_ours(args, rank, world):
                           share=phases["field"] / ms_per_step,
                           bytes_note="60 B per cell update (read E, B, J; write E, B)")
     if nfl and phases["fluid"] > 0:
-        b = (FLUID_BYTES_PER_NODE * nfl + FLUID_FIELD_BYTES_PER_NODE) * cells
+        # the nodes the fluid update covered in the profiled steps (the range near fluid density)
+        b = (FLUID_BYTES_PER_NODE * nfl + FLUID_FIELD_BYTES_PER_NODE) * fluid_cells
         roofs["fluid"] = dict(kernel="k_fluid_lorentz + k_fluid_update", bound="hbm", achieved=b / (phases["fluid"] * 1e-3) / 1e9,
                               peak=peak_hbm, unit="GB/s", algorithmic_bytes_per_launch=b,
-                              mean_launch_ms=phases["fluid"], share=phases["fluid"] / ms_per_step)
+                              mean_launch_ms=phases["fluid"], share=phases["fluid"] / ms_per_step,
+                              nodes=fluid_cells)
     if cls:
         # FLOPs of the nodes the classification evaluated (every node without a reach)
         ccells = cls.get("classified_cells") or cells
@@ -484,6 +490,7 @@ def run_ours(args, rank, world):
         fms = allmax(fms)
         fparts = 0.5 * (sum(fb["count"]) + sum(fa["count"]))
         fphases, _ = profile_phases(fsim, None, args.warmup + args.steps)
+        fphases.pop("fluid_cells", None)
         fsim.close()
         full_step = fms / args.steps
         # the hybrid step without its classification, and the classification

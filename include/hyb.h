@@ -196,6 +196,8 @@ typedef struct {
     long long classified_cells;            /* nodes whose statistics the most recent classification with a
                                               model computed (all of them unless hyb_regime_desc.reach
                                               restricted it) */
+    long long fluid_cells;                 /* nodes the fluid update covers now (all of them unless a
+                                              classification with a reach restricted it) */
 } hyb_diag;
 
 /* Create a context: validates the descriptor, allocates fields on the
@@ -252,7 +254,12 @@ typedef struct {
                                              decision differs from the whole-grid one only where no matter
                                              can be before then, and the run (conversions, fields,
                                              particles) is the same.  hyb_classify then synchronises the
-                                             context stream once to read the matter's x-extent. */
+                                             context stream to read the matter's x-extent, and, once a step
+                                             has run since the fluids were loaded, restricts the fluid
+                                             update of the next r steps to the planes within r of nonzero
+                                             fluid density (fluid spreads one node per step; the planes
+                                             left out stay empty): also exact; hyb_step lifts the
+                                             restriction when it lapses. */
 } hyb_regime_desc;
 /* Which decision hyb_classify takes.  DEFAULT: the classifier when a model is
  * given, else the physics criterion.  UNION: a node is kinetic when the

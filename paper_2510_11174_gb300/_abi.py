@@ -60,7 +60,8 @@ class hyb_diag(C.Structure):
                 ("n_emit", C.c_longlong), ("n_pair", C.c_longlong),
                 ("n_fluids", C.c_int), ("w_fluid", C.c_double * 4), ("n_fluid", C.c_double * 4),
                 ("n_clamped", C.c_longlong), ("launches_classify", C.c_longlong),
-                ("tile_capacity", C.c_longlong * HYB_MAX_SPECIES), ("classified_cells", C.c_longlong)]
+                ("tile_capacity", C.c_longlong * HYB_MAX_SPECIES), ("classified_cells", C.c_longlong),
+                ("fluid_cells", C.c_longlong)]
 
 
 HYB_NPHASE = 10

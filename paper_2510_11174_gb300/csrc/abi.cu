@@ -1093,6 +1093,9 @@ hyb_status hyb_diagnostics(hyb_ctx *c, hyb_diag *out) {
     out->launches_per_step = c->launches_per_step;
     out->launches_classify = c->launches_classify;
     out->classified_cells = c->classified_cells;
+    out->fluid_cells = c->fluid_xr_until >= 0
+                           ? (long long)(c->fluid_xr_host[1] - c->fluid_xr_host[0]) * c->g.n[1] * c->g.n[2]
+                           : c->g.N;
     for (size_t i = 0; i < c->sp.size() && i < HYB_MAX_SPECIES; ++i) out->tile_capacity[i] = c->sp[i].dev.cap;
     out->n_fluids = nfl;
     for (int f = 0; f < nfl; ++f) {

@@ -322,6 +322,7 @@ class Simulation:
                 "n_fluid": [out.n_fluid[i] for i in range(out.n_fluids)], "n_clamped": out.n_clamped,
                 "launches_classify": out.launches_classify,
                 "classified_cells": out.classified_cells,
+                "fluid_cells": out.fluid_cells,
                 "tile_capacity": [out.tile_capacity[i] for i in range(ns)]}
 
     def eval_qed(self, what, chi, r=None):
