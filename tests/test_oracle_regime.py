@@ -259,3 +259,33 @@ def test_reach_zeroes_the_statistics_away_from_matter_and_keeps_them_near_it():
     assert np.array_equal(pm3[:, :, keep], pm0[:, :, keep]) and np.array_equal(ps3[:, :, keep], ps0[:, :, keep])
     assert not pm3[:, :, ~keep].any() and not ps3[:, :, ~keep].any()
     assert pm0[:, :, ~keep].all()
+
+
+def test_reach_on_a_periodic_axis_keeps_every_plane_when_the_range_wraps():
+    """Matter near x = 0 of a periodic box: its neighbourhood wraps round to the
+    last planes, so the restricted statistics equal the whole grid's
+    everywhere; away from the ends only the range is kept."""
+    from oracle.classifier import OracleCNN
+    from oracle.sim import OracleSim
+    from paper_2510_11174_gb300 import inputs
+    nx, ny, nz = 32, 8, 4
+    rng = np.random.default_rng(5)
+    E = (0.3 * rng.standard_normal((3, nz, ny, nx))).astype(np.float32)
+    B = (0.3 * rng.standard_normal((3, nz, ny, nx))).astype(np.float32)
+    net = OracleCNN(inputs.classifier_weights(6), dropout=0.2, seed=6)
+    out = {}
+    for lo_plane in (1, 14):
+        n = np.zeros((nz, ny, nx))
+        n[:, :, lo_plane:lo_plane + 2] = 0.5
+        for reach in (0, 2):
+            o = OracleSim(nx, ny, nz, 0.3, bc=(0, 0, 0))
+            o.load_species(-1.0, 1.0, *[np.zeros(0, np.float32)] * 7)
+            o.load_fluid(-1.0, 1.0, n, n_floor=1e-10)
+            o.set_fields(E, B)
+            o.set_regime(ppc=1, to_species=[-1], dilate=1, reach=reach)
+            out[lo_plane, reach] = o.classify(net, passes=2)[0]
+    assert np.array_equal(out[1, 2], out[1, 0])           # wraps: every plane kept
+    keep = np.zeros(nx, dtype=bool)
+    keep[14 - 3:16 + 3] = True
+    assert np.array_equal(out[14, 2][:, :, keep], out[14, 0][:, :, keep])
+    assert not out[14, 2][:, :, ~keep].any()
