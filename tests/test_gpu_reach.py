@@ -132,3 +132,32 @@ def test_reach_without_matter_classifies_nothing():
     assert d["classified_cells"] == 0 and d["status"] == 0
     sim.close()
     model.close()
+
+
+def test_reach_on_a_periodic_axis_keeps_every_plane_when_the_range_wraps():
+    """A periodic box with fluid near x = 0: the range near matter would wrap
+    round, so the classifier runs on every plane and its statistics equal the
+    whole grid's everywhere."""
+    P = require_gpu()
+    import torch
+    nx, ny, nz, dx = 64, 16, 16, 0.3
+    n = np.zeros((nz, ny, nx), np.float32)
+    n[:, :, 1:4] = 0.5
+    rng = np.random.default_rng(8)
+    E = (0.3 * rng.standard_normal((3, nz, ny, nx))).astype(np.float32)
+    B = (0.3 * rng.standard_normal((3, nz, ny, nx))).astype(np.float32)
+    model, _ = seeded_classifier(P, 9, out_bias=-2.0, dropout=0.2, mc_passes=4)
+    outs = []
+    for reach in (0, REACH):
+        sim = P.Simulation(nx, ny, nz, dx, cfl_frac=0.95, bc=(0, 0, 0))
+        sim.load_fluid(q=-1.0, m=1.0, n=n, n_floor=1e-10)
+        sim.set_fields(E, B)
+        sim.set_regime(dilate=1, ppc=2, to_species=[], policy="default", reach=reach)
+        pm = torch.empty(nx * ny * nz, dtype=torch.float32, device="cuda")
+        sim.classify(model, p_mean=pm)
+        torch.cuda.synchronize()
+        outs.append(pm.cpu().numpy())
+        assert sim.diagnostics()["classified_cells"] == nx * ny * nz
+        sim.close()
+    assert np.array_equal(outs[0], outs[1])
+    model.close()
