@@ -1,6 +1,7 @@
 """Pins of the oracle's classifier: the orientation of the 3x3x3 taps (a
-one-hot kernel is a shift), BF16 rounding points, the dropout mask law and
-the MC statistics definitions."""
+one-hot kernel is a shift), BF16 rounding points, the dropout mask law,
+the MC statistics definitions, and the layers' composition against an
+explicit-loop evaluation."""
 import numpy as np
 import pytest
 import torch
@@ -154,3 +155,52 @@ def test_sub_box_forward_equals_whole_grid_away_from_the_cut():
     cells = ((z * 16 + y) * 14 + xx).ravel()
     sub = net.forward(box, pass_index=1, cells=cells)[0]
     assert torch.allclose(sub[4:6, 4:8, 4:7], full[z0 + 4:z0 + 6, y0 + 4:y0 + 8, x0 + 4:x0 + 7], rtol=0, atol=1e-12)
+
+
+def _bf16(a):
+    # round to nearest even BF16 through torch's own dtype conversion
+    return torch.from_numpy(np.asarray(a, np.float64)).to(torch.bfloat16).to(torch.float64).numpy()
+
+
+def _brute_layer(a, W, b):
+    """3x3x3 convolution with zero padding by explicit loops over the output
+    cells and the taps: a [ci][D][H][W], W [co][ci][3][3][3] -> [co][D][H][W]."""
+    ci, D, H, Wd = a.shape
+    out = np.zeros((W.shape[0], D, H, Wd))
+    for z in range(D):
+        for y in range(H):
+            for x in range(Wd):
+                acc = b.astype(np.float64).copy()
+                for kz in range(3):
+                    for ky in range(3):
+                        for kx in range(3):
+                            zz, yy, xx = z + kz - 1, y + ky - 1, x + kx - 1
+                            if 0 <= zz < D and 0 <= yy < H and 0 <= xx < Wd:
+                                acc += W[:, :, kz, ky, kx] @ a[:, zz, yy, xx]
+                out[:, z, y, x] = acc
+    return out
+
+
+@pytest.mark.parametrize("pass_index", [-1, 0])
+def test_layer_composition_matches_brute_force(pass_index):
+    """The whole 6 -> 32 -> 32 -> 16 -> 1 network on a tiny box, computed here
+    by explicit loops (BF16 inputs and weights, ReLU and dropout with inverted
+    scaling after each hidden layer, BF16 activations, linear last layer),
+    against the oracle's forward pass."""
+    weights = _weights(3)
+    net = OracleCNN(weights, dropout=0.25, seed=4)
+    x = np.random.default_rng(9).standard_normal((1, 6, 3, 4, 5)).astype(np.float32)
+    a = _bf16(x[0])
+    D, H, Wd = a.shape[1:]
+    for l, (W, b) in enumerate(weights):
+        z = _brute_layer(a, _bf16(W), b)
+        if l == 3:
+            ref = z[0]
+            break
+        h = np.maximum(z, 0.0)
+        if pass_index >= 0:
+            keep = oracle.dropout_mask(1, h.shape[0], D * H * Wd, 4, pass_index, l, net.p).reshape(h.shape)
+            h = h * keep / (1.0 - net.p)
+        a = _bf16(h)
+    got = net.forward(x, pass_index=pass_index)[0].numpy()
+    assert np.allclose(got, ref, rtol=1e-12, atol=1e-12)
