@@ -151,3 +151,57 @@ def test_node_state_charge_sums_to_the_particle_charge():
     total = st[9].sum() * 0.5 ** 3
     expect = float(np.sum(sp["w"] * sp["zq"])) - fl_n.sum() * 0.5 ** 3
     assert total == pytest.approx(expect, rel=1e-12)
+
+
+def _bf16(a):
+    # round to nearest even BF16 through torch's own dtype conversion
+    return torch.from_numpy(np.asarray(a, np.float64)).to(torch.bfloat16).to(torch.float64).numpy()
+
+
+def _brute_conv(a, W, b):
+    """3x3x3 cross-correlation with zero padding by explicit loops over the
+    output cells and taps: a [ci][D][H][W] -> [co][D][H][W]."""
+    ci, D, H, Wd = a.shape
+    out = np.zeros((W.shape[0], D, H, Wd))
+    for z in range(D):
+        for y in range(H):
+            for x in range(Wd):
+                acc = b.astype(np.float64).copy()
+                for kz in range(3):
+                    for ky in range(3):
+                        for kx in range(3):
+                            zz, yy, xx = z + kz - 1, y + ky - 1, x + kx - 1
+                            if 0 <= zz < D and 0 <= yy < H and 0 <= xx < Wd:
+                                acc += W[:, :, kz, ky, kx] @ a[:, zz, yy, xx]
+                out[:, z, y, x] = acc
+    return out
+
+
+@pytest.mark.parametrize("pass_index", [-1, 1])
+def test_layer_composition_matches_brute_force(pass_index):
+    """The six layers on a tiny box by explicit loops (identity shortcuts on
+    layers 0..2 with the extra channels zero, ReLU on 0..4, dropout with
+    inverted scaling after layer 1, BF16 activations between layers, a linear
+    last layer, the forecast added to the input) against the oracle."""
+    rng = np.random.default_rng(12)
+    weights = [((rng.standard_normal((co, ci, 3, 3, 3)) / np.sqrt(27 * ci)).astype(np.float32),
+                (0.05 * rng.standard_normal(co)).astype(np.float32)) for ci, co in S.LAYERS]
+    net = S.OracleSurrogate(weights, dropout=0.25, seed=13)
+    x = rng.standard_normal((1, 10, 2, 3, 4)).astype(np.float32)
+    a = _bf16(x[0])
+    D, H, Wd = a.shape[1:]
+    for l, (W, b) in enumerate(weights):
+        co = W.shape[0]
+        h = _brute_conv(a, _bf16(W), b)
+        if l < 5:
+            h = np.maximum(h, 0.0)
+        if l == 1 and pass_index >= 0:
+            keep = oracle.dropout_mask(1, (co + 7) // 8 * 8, D * H * Wd, 13, pass_index, 1, net.p)
+            h = h * keep.reshape(-1, D, H, Wd)[:co] / (1.0 - net.p)
+        if l < 3:
+            pad = np.zeros_like(h)
+            pad[:a.shape[0]] = a
+            h = h + pad
+        a = h if l == 5 else _bf16(h)
+    pred = net.predict(x, pass_index=pass_index)[0].numpy()
+    assert np.allclose(pred, x[0].astype(np.float64) + a, rtol=1e-12, atol=1e-12)
