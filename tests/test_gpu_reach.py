@@ -161,3 +161,36 @@ def test_reach_on_a_periodic_axis_keeps_every_plane_when_the_range_wraps():
         sim.close()
     assert np.array_equal(outs[0], outs[1])
     model.close()
+
+
+def test_fluid_range_lapses_after_reach_steps():
+    """A classification with reach 3 restricts the fluid update for 3 steps
+    only: stepping 12 steps past it (the restriction lifted after 3) repeats
+    the run without a reach bit for bit."""
+    P = require_gpu()
+    inp = _workload()
+    model, _ = seeded_classifier(P, 9, out_bias=-2.0, dropout=0.2, mc_passes=4)
+    runs = []
+    for reach in (0, 3):
+        sim = _sim(P, inp, reach)
+        sim.classify(model)
+        sim.step(4)                 # a step since the fluids were loaded: the next range is taken
+        sim.classify(model)
+        d = sim.diagnostics()
+        g = inp["grid"]
+        assert (d["fluid_cells"] < g["nx"] * g["ny"] * g["nz"]) == (reach > 0) and d["status"] == 0
+        sim.step(12)
+        runs.append((sim.get_fields(), [sim.get_fluid(f) for f in range(2)],
+                     [by_id(sim.get_species(s)) for s in range(2)], sim.diagnostics()))
+        sim.close()
+    (fa, la, pa, da), (fb, lb, pb, db) = runs
+    assert db["fluid_cells"] == da["fluid_cells"] == inp["grid"]["nx"] * inp["grid"]["ny"] * inp["grid"]["nz"]
+    for a, b in zip(fa, fb):
+        assert np.array_equal(a, b)
+    for f in range(2):
+        for k in la[f]:
+            assert np.array_equal(la[f][k], lb[f][k]), (f, k)
+    for s in range(2):
+        for k in pa[s]:
+            assert np.array_equal(pa[s][k], pb[s][k]), (s, k)
+    model.close()
